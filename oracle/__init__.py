@@ -1,0 +1,266 @@
+"""Oracle: plain FP64 CPU reference of the augmented-Lagrangian FFT scheme with
+the discrete Green operator (Willot & Pellegrini, arXiv:0802.2488, Sec. 2).
+
+TEST INFRASTRUCTURE ONLY.  The test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The product path (the
+CUDA library and its binding) never imports this package, and this package
+never imports the product.
+
+This module compiles ``oracle.c`` with gcc into ``_liboracle.so`` (beside it)
+and wraps it with ctypes and numpy.  Every function names the passage of the
+paper it follows; the arithmetic itself lives in ``oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "_liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c (gcc, -O2, OpenMP, IEEE arithmetic) if stale."""
+    with _lock:
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+            tmp = _LIB + f".{os.getpid()}.tmp"
+            subprocess.check_call(
+                ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                 "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Material(C.Structure):
+    """Matrix Lame moduli, Mises flow stress Y (inf = elastic) and the
+    reference medium C0 of the augmented Lagrangian."""
+    _fields_ = [("lambda_", C.c_double), ("mu", C.c_double), ("yield_", C.c_double),
+                ("lambda0", C.c_double), ("mu0", C.c_double)]
+
+
+class Control(C.Structure):
+    _fields_ = [("tol_eq", C.c_double), ("tol_macro", C.c_double),
+                ("max_iter", C.c_int32), ("pad", C.c_int32)]
+
+
+class Record(C.Structure):
+    _fields_ = [("sig_mean", C.c_double * 4), ("eps_mean", C.c_double * 4),
+                ("eta1", C.c_double), ("eta2", C.c_double), ("eta3", C.c_double),
+                ("iterations", C.c_int32), ("n_plastic", C.c_int32),
+                ("n_clusters", C.c_int32), ("status", C.c_int32)]
+
+
+def material(lam=1.5, mu=1.0, Y=1.0, lam0=None, mu0=None) -> Material:
+    return Material(lam, mu, Y, lam if lam0 is None else lam0, mu if mu0 is None else mu0)
+
+
+_D = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_U8 = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+_I32 = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_VP = C.c_void_p
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        L.orc_splitmix64.restype = C.c_uint64
+        L.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
+        L.orc_void_threshold.restype = C.c_uint64
+        L.orc_void_threshold.argtypes = [C.c_double]
+        L.orc_mask.argtypes = [C.c_int, C.c_double, C.c_uint64, _U8]
+        L.orc_fft2.argtypes = [_VP, C.c_int, C.c_int]
+        L.orc_green.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, _D]
+        L.orc_green_apply.argtypes = [C.c_int, C.c_double, C.c_double, _D, _VP, _VP]
+        L.orc_sigma_field.argtypes = [C.c_int64, _D, _U8, C.POINTER(Material), _D, _VP]
+        L.orc_local_field.argtypes = [C.c_int64, _D, _U8, C.POINTER(Material), _D, _VP]
+        L.orc_al_step.argtypes = [C.c_int, _U8, C.POINTER(Material), _D, _D, _D, _VP, _VP]
+        L.orc_stats.argtypes = [C.c_int, _U8, C.POINTER(Material), _D, _D, _D,
+                                C.POINTER(C.c_double), C.POINTER(C.c_int32), _VP]
+        L.orc_label.restype = C.c_int32
+        L.orc_label.argtypes = [C.c_int, _U8, C.c_int, _I32]
+        L.orc_solve.restype = C.c_int32
+        L.orc_solve.argtypes = [C.c_int, _U8, C.POINTER(Material), C.POINTER(Control),
+                                C.c_int, _D, C.POINTER(Record), _VP, _VP, _VP]
+        _lib = L
+    return _lib
+
+
+def _check_L(L: int) -> None:
+    if L < 2 or (L & (L - 1)) != 0:
+        raise ValueError(f"lattice side {L} is not a power of two >= 2")
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+# --------------------------------------------------------------------------
+# Sec. 2: random void pixels
+# --------------------------------------------------------------------------
+
+def splitmix64(seed: int, i: int) -> int:
+    """i-th output of the SplitMix64 stream seeded with `seed`."""
+    return int(lib().orc_splitmix64(seed & (2**64 - 1), i))
+
+
+def void_threshold(f: float) -> int:
+    return int(lib().orc_void_threshold(float(f)))
+
+
+def mask(L: int, f: float, seed: int) -> np.ndarray:
+    """uint8 (L, L), 1 = void: i.i.d. Bernoulli(f) pixels (Sec. 2)."""
+    out = np.empty((L, L), dtype=np.uint8)
+    lib().orc_mask(L, float(f), seed & (2**64 - 1), out)
+    return out
+
+
+# --------------------------------------------------------------------------
+# FFT and the Green operator, Eqs. 2-3
+# --------------------------------------------------------------------------
+
+def fft2(a: np.ndarray, sign: int = -1) -> np.ndarray:
+    """Unnormalised 2D DFT with kernel exp(sign i q.x) (oracle's own FFT)."""
+    b = np.ascontiguousarray(a, dtype=np.complex128).copy()
+    L = b.shape[0]
+    assert b.shape == (L, L)
+    _check_L(L)
+    lib().orc_fft2(_ptr(b), L, sign)
+    return b
+
+
+def green(L: int, lam0: float, mu0: float, m1: int, m2: int) -> np.ndarray:
+    """G_ijkl(q) of Eq. 3 as a complex (2, 2, 2, 2) array."""
+    g = np.zeros(32, dtype=np.float64)
+    lib().orc_green(L, lam0, mu0, m1, m2, g)
+    return g.view(np.complex128).reshape(2, 2, 2, 2)
+
+
+def green_apply(L, lam0, mu0, E, phat):
+    """e^ = G p^ on a full (3, L, L) spectrum (11, 22, 12); e^(0) = L^2 E."""
+    _check_L(L)
+    ph = np.ascontiguousarray(phat, dtype=np.complex128)
+    eh = np.empty_like(ph)
+    lib().orc_green_apply(L, lam0, mu0, np.ascontiguousarray(E, dtype=np.float64),
+                          _ptr(ph), _ptr(eh))
+    return eh
+
+
+# --------------------------------------------------------------------------
+# Constitutive law and the local step
+# --------------------------------------------------------------------------
+
+def sigma(eps: np.ndarray, void: np.ndarray, mat: Material):
+    """sigma(eps) on (..., 4) arrays; returns (sigma, plastic_branch)."""
+    e = np.ascontiguousarray(eps, dtype=np.float64)
+    v = np.ascontiguousarray(np.broadcast_to(void, e.shape[:-1]), dtype=np.uint8)
+    s = np.empty_like(e)
+    pl = np.empty(v.shape, dtype=np.uint8)
+    lib().orc_sigma_field(v.size, e, v, C.byref(mat), s, _ptr(pl))
+    return s, pl
+
+
+def local_solve(tau: np.ndarray, void: np.ndarray, mat: Material):
+    """Solution of sigma(eps) + C0:eps = tau on (..., 4) arrays."""
+    t = np.ascontiguousarray(tau, dtype=np.float64)
+    v = np.ascontiguousarray(np.broadcast_to(void, t.shape[:-1]), dtype=np.uint8)
+    e = np.empty_like(t)
+    pl = np.empty(v.shape, dtype=np.uint8)
+    lib().orc_local_field(v.size, t, v, C.byref(mat), e, _ptr(pl))
+    return e, pl
+
+
+# --------------------------------------------------------------------------
+# The augmented-Lagrangian iteration and its indicators
+# --------------------------------------------------------------------------
+
+def al_step(mask_: np.ndarray, mat: Material, E, eps: np.ndarray, lam: np.ndarray | None = None):
+    """One AL iteration from (eps, lam) (lam defaults to sigma(eps)).
+    Returns (eps_new, lam_new, e, plastic) as (L, L, 4) / (L, L) arrays."""
+    L = mask_.shape[0]
+    _check_L(L)
+    m = np.ascontiguousarray(mask_, dtype=np.uint8)
+    ep = np.ascontiguousarray(eps, dtype=np.float64).copy()
+    la = sigma(ep, m, mat)[0] if lam is None else np.ascontiguousarray(lam, dtype=np.float64).copy()
+    e = np.empty_like(ep)
+    pl = np.empty((L, L), dtype=np.uint8)
+    lib().orc_al_step(L, m, C.byref(mat), np.ascontiguousarray(E, dtype=np.float64),
+                      ep, la, _ptr(e), _ptr(pl))
+    return ep, la, e, pl
+
+
+@dataclass
+class Stats:
+    sig_mean: np.ndarray
+    eps_mean: np.ndarray
+    div2_mean: float
+    n_plastic: int
+    plastic: np.ndarray
+
+
+def stats(mask_: np.ndarray, mat: Material, eps: np.ndarray) -> Stats:
+    """Mean stress / strain, <|div sigma|^2> (backward differences, Eq. 1)
+    and plastic pixels of sigma(eps) (Sec. 2 "Convergence issues", Sec. 3)."""
+    L = mask_.shape[0]
+    m = np.ascontiguousarray(mask_, dtype=np.uint8)
+    sm = np.empty(4)
+    em = np.empty(4)
+    d2 = C.c_double()
+    npl = C.c_int32()
+    pl = np.empty((L, L), dtype=np.uint8)
+    lib().orc_stats(L, m, C.byref(mat), np.ascontiguousarray(eps, dtype=np.float64),
+                    sm, em, C.byref(d2), C.byref(npl), _ptr(pl))
+    return Stats(sm, em, d2.value, npl.value, pl)
+
+
+def label(flag: np.ndarray, periodic: bool = True):
+    """Nearest-neighbour clusters (Sec. 3, Hoshen-Kopelman); label = smallest
+    linear index of the cluster, -1 off the flag.  Returns (labels, count)."""
+    f = np.ascontiguousarray(flag, dtype=np.uint8)
+    L = f.shape[0]
+    lab = np.empty((L, L), dtype=np.int32)
+    n = lib().orc_label(L, f, 1 if periodic else 0, lab)
+    return lab, int(n)
+
+
+RECORD_DTYPE = np.dtype([("sig_mean", "f8", 4), ("eps_mean", "f8", 4), ("eta1", "f8"),
+                         ("eta2", "f8"), ("eta3", "f8"), ("iterations", "i4"),
+                         ("n_plastic", "i4"), ("n_clusters", "i4"), ("status", "i4")])
+assert RECORD_DTYPE.itemsize == C.sizeof(Record)
+
+
+@dataclass
+class Solution:
+    status: int
+    records: np.ndarray          # RECORD_DTYPE, one per increment
+    eps: np.ndarray              # (L, L, 4) final local strain
+    plastic: np.ndarray | None   # (n_inc, L, L)
+    labels: np.ndarray | None    # (n_inc, L, L)
+
+
+def solve(mask_: np.ndarray, mat: Material, path: np.ndarray, tol_eq=1e-8, tol_macro=1e-8,
+          max_iter=10000, fields=False) -> Solution:
+    """Strain-controlled loading by increments (Sec. 2) with the AL scheme;
+    path is (n_inc, 4) prescribed mean strains (11, 22, 33, 12)."""
+    L = mask_.shape[0]
+    _check_L(L)
+    m = np.ascontiguousarray(mask_, dtype=np.uint8)
+    P = np.ascontiguousarray(path, dtype=np.float64).reshape(-1, 4)
+    n_inc = P.shape[0]
+    recs = (Record * n_inc)()
+    eps = np.empty((L, L, 4))
+    pl = np.empty((n_inc, L, L), dtype=np.uint8) if fields else None
+    lab = np.empty((n_inc, L, L), dtype=np.int32) if fields else None
+    st = lib().orc_solve(L, m, C.byref(mat), C.byref(Control(tol_eq, tol_macro, max_iter, 0)),
+                         n_inc, P, recs, _ptr(eps), _ptr(pl), _ptr(lab))
+    arr = np.frombuffer(bytes(recs), dtype=RECORD_DTYPE).copy()
+    return Solution(int(st), arr, eps, pl, lab)
