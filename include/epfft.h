@@ -1,0 +1,212 @@
+/*
+ * epfft.h -- C ABI of the GB300 (sm_103a) implementation of the
+ * augmented-Lagrangian FFT scheme with the discrete Green operator of
+ *
+ *   F. Willot, Y.-P. Pellegrini, "Fast Fourier Transform computations and
+ *   build-up of plastic deformation in 2D, elastic-perfectly plastic,
+ *   pixelwise disordered porous media", arXiv:0802.2488.
+ *
+ * Problem (Sec. 2): an L x L periodic square lattice of pixels, each either a
+ * void (stress-free) or an elastic-perfectly plastic Mises element with
+ * flow stress Y under deformation theory, loaded by a prescribed mean
+ * strain increased by increments.  Strain is the forward difference of the
+ * displacement and equilibrium the backward difference of the stress (Eq. 1);
+ * the compatible-strain projection uses the discrete Green operator of
+ * Eqs. 2-3 (generalized plane strain, q3 = 0).  The nonlinear problem is
+ * solved with the augmented-Lagrangian / Uzawa iteration the paper cites
+ * (Sec. 1), and each increment stops on the two indicators of Sec. 2
+ * ("Convergence issues"):
+ *     <|div sigma|^2>               < eta1^2 <sigma>:<sigma>
+ *     |<sigma^{n+1}> - <sigma^n>|^2 < eta2^2 <sigma^{n+1}>:<sigma^{n+1}>
+ * with a:b = a11 b11 + a22 b22 + 2 a12 b12.
+ *
+ * Conventions of every call:
+ *   - lattice side L: a power of two, 4 <= L <= 4096 (FP64: L <= 2048);
+ *   - pixel x = (x1, x2) at linear index x2 * L + x1 (x1 fastest);
+ *   - symmetric tensors are 4 reals per pixel in the order (11, 22, 33, 12);
+ *   - forward DFT kernel exp(-i q.x), q_j = 2 pi m_j / L (the sign for which
+ *     the forward difference of Eq. 1 has the symbol i k_j of Eq. 2).
+ *
+ * Errors: every int-returning call returns EPFFT_OK (0) or a code below;
+ * epfft_strerror() names it.  Invalid arguments never reach the GPU.  There
+ * is no CPU fallback: without a usable CUDA device the calls return
+ * EPFFT_ERR_CUDA.  A context is used by one host thread at a time.
+ */
+#ifndef EPFFT_H
+#define EPFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EPFFT_OK 0
+#define EPFFT_PENDING 1             /* not finished yet                          */
+#define EPFFT_ERR_ARG (-1)          /* invalid argument (nothing was launched)   */
+#define EPFFT_ERR_OOM (-2)          /* device allocation failed                  */
+#define EPFFT_ERR_NUMERIC (-3)      /* NaN / Inf in a residual or mean stress    */
+#define EPFFT_NOT_CONVERGED (-4)    /* some increment hit max_iter; results kept */
+#define EPFFT_ERR_DEVICE_TIMEOUT (-5) /* the device loop exceeded its pass bound */
+#define EPFFT_ERR_CUDA (-6)         /* a CUDA runtime call failed                */
+#define EPFFT_ERR_UNSUPPORTED (-7)  /* size / precision not built                */
+
+#define EPFFT_FP64 0 /* FP64 fields, FFTs and reductions                        */
+#define EPFFT_FP32 1 /* FP32 fields and FFTs, FP64 reductions and macro values  */
+
+#define EPFFT_GREEN_EQ3 0 /* discrete Green operator of Eq. 3                   */
+
+typedef struct epfft_ctx epfft_ctx;
+
+/* Device memory hook.  alloc returns a device pointer usable on `stream`
+ * (NULL on failure); free releases it.  With both NULL the library uses
+ * cudaMallocAsync / cudaFreeAsync on its stream. */
+typedef void *(*epfft_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*epfft_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+typedef struct {
+  int32_t device;          /* CUDA device ordinal                                */
+  int32_t reserved;
+  void *stream;            /* cudaStream_t to work on; NULL: the context creates  *
+                            * its own non-blocking stream                         */
+  epfft_alloc_fn alloc;    /* optional allocator hook (see above)                */
+  epfft_free_fn free;
+  void *alloc_user;
+} epfft_options;
+
+/* One solve (Sec. 2): the lattice, its voids, the matrix and the iteration
+ * controls.  Copied at call time; the caller keeps ownership of `mask`. */
+typedef struct {
+  int32_t L;               /* lattice side (see conventions)                      */
+  int32_t precision;       /* EPFFT_FP64 or EPFFT_FP32                            */
+  double void_fraction;    /* f in [0, 1]: used when mask == NULL                 */
+  uint64_t seed;           /* mask seed: pixel x is void iff the top 53 bits of   *
+                            * the x-th output of SplitMix64(seed) are below       *
+                            * floor(f 2^53) (i.i.d. Bernoulli(f) voids, Sec. 2)   */
+  const uint8_t *mask;     /* optional L*L mask, 1 = void; host or device         */
+  int32_t mask_on_device;  /* 1 if `mask` is a device pointer                     */
+  int32_t green;           /* EPFFT_GREEN_EQ3                                     */
+  double mu, lambda;       /* matrix Lame moduli (> 0, lambda + 2 mu / 3 > 0)     */
+  double yield_stress;     /* Mises flow stress Y > 0; +inf = elastic matrix      */
+  double mu0, lambda0;     /* reference medium C0 of the augmented Lagrangian     */
+  double tol_eq;           /* eta1 >= 0                                           */
+  double tol_macro;        /* eta2 >= 0                                           */
+  int32_t max_iter;        /* >= 1 iterations per increment                       */
+  int32_t reserved;
+} epfft_problem;
+
+/* Prescribed mean strain per increment, n_inc x (E11, E22, E33, E12), host
+ * memory.  The lattice starts unstrained; increment k warm-starts from the
+ * accepted state of increment k-1 shifted by E_k - E_{k-1}. */
+typedef struct {
+  int32_t n_inc;
+  int32_t reserved;
+  const double *E;
+} epfft_path;
+
+/* Result of one increment (the accepted iterate). */
+typedef struct {
+  double sig_mean[4];      /* <sigma> (11, 22, 33, 12)                            */
+  double eps_mean[4];      /* <eps>                                               */
+  double eta1;             /* (<|div sigma|^2> / <sigma>:<sigma>)^(1/2)           */
+  double eta2;             /* |<sigma^{n}> - <sigma^{n-1}>| / |<sigma^{n}>|       */
+  double eta3;             /* (<(eps - e):(eps - e)> / E:E)^(1/2), e compatible   */
+  int32_t iterations;      /* iterations of this increment                        */
+  int32_t n_plastic;       /* matrix pixels with sigma_eq = Y (Sec. 3)            */
+  int32_t n_clusters;      /* 4-connected periodic clusters of plastic pixels     */
+  int32_t status;          /* 0 converged, 1 max_iter reached, 2 NaN / Inf        */
+} epfft_record;
+
+/* Optional field outputs of a solve; NULL members are skipped. */
+typedef struct {
+  void *eps;               /* L*L*4 reals of the problem's precision: final state */
+  uint8_t *plastic;        /* n_inc*L*L: plastic pixels of each accepted state    */
+  int32_t *labels;         /* n_inc*L*L: their clusters, label = smallest linear  *
+                            * index of the cluster, -1 off the plastic set        */
+  int32_t on_device;       /* 1: the pointers are device pointers; 0: host        */
+  int32_t reserved;
+} epfft_fields;
+
+/* ---------------------------------------------------------------------- */
+/* Context                                                                 */
+/* ---------------------------------------------------------------------- */
+
+/* Creates a context on opt->device (opt may be NULL: device 0, own stream,
+ * cudaMallocAsync).  *out is NULL on error. */
+int epfft_create(epfft_ctx **out, const epfft_options *opt);
+/* Releases the context and everything it allocated; waits for its stream. */
+void epfft_destroy(epfft_ctx *ctx);
+/* Static string naming an error code. */
+const char *epfft_strerror(int code);
+/* 1 if the library was built for lattice side L in `precision`, else 0. */
+int epfft_supported(int32_t L, int32_t precision);
+
+/* ---------------------------------------------------------------------- */
+/* Solves (Sec. 2: strain-controlled loading by increments)                */
+/* ---------------------------------------------------------------------- */
+
+/* Blocking solve of one problem along `path`.  records: host array of
+ * path->n_inc entries (filled).  fields: optional outputs (may be NULL).
+ * Returns EPFFT_OK when every increment converged, EPFFT_NOT_CONVERGED when
+ * some increment stopped at max_iter (its record has status 1), or an
+ * error.  The device state is released before returning. */
+int epfft_solve(epfft_ctx *ctx, const epfft_problem *problem, const epfft_path *path,
+                epfft_record *records, const epfft_fields *fields);
+
+/* Blocking solve of n independent problems advanced together on the
+ * device, one augmented-Lagrangian pass of every unfinished problem per
+ * step of a single device-side loop (one CUDA graph launch).  All problems
+ * share L and precision (else EPFFT_ERR_ARG).  records[i] is a host array
+ * of paths[i].n_inc entries; fields may be NULL or an array of n.  The
+ * arithmetic of each problem does not depend on the others in the batch. */
+int epfft_solve_batch(epfft_ctx *ctx, int32_t n, const epfft_problem *problems,
+                      const epfft_path *paths, epfft_record *const *records,
+                      const epfft_fields *fields);
+
+/* ---------------------------------------------------------------------- */
+/* Steps of the iteration, for parity checks and measurement               */
+/* ---------------------------------------------------------------------- */
+
+/* Void mask of Sec. 2 (see epfft_problem.seed) into mask_dev (L*L bytes,
+ * device).  stream: cudaStream_t or NULL for the legacy default stream.
+ * Asynchronous. */
+int epfft_mask(int32_t L, double void_fraction, uint64_t seed, uint8_t *mask_dev, void *stream);
+
+/* n_iter augmented-Lagrangian iterations of `problem` (mask from the
+ * problem) at fixed mean strain E[4], starting from the local strain
+ * eps_dev (device, L*L*4 reals of the problem's precision; the multiplier
+ * starts at sigma(eps)), which is overwritten with the n_iter-th iterate.
+ * out receives the indicators of that iterate (tolerances are ignored).
+ * Blocking. */
+int epfft_iterate(epfft_ctx *ctx, const epfft_problem *problem, const double E[4],
+                  void *eps_dev, int32_t n_iter, epfft_record *out);
+
+/* Compatible strain of a polarization (Eqs. 2-3):
+ *   e = E + IDFT( G(q) DFT(p) ),  G(0) = 0,
+ * p_dev: 3 planes of L*L reals (p11, p22, p12), e_dev the same for
+ * (e11, e22, e12); reals of `precision`; device memory.  Blocking. */
+int epfft_project(epfft_ctx *ctx, int32_t L, int32_t precision, double lambda0, double mu0,
+                  const double E[4], const void *p_dev, void *e_dev);
+
+/* Nearest-neighbour clusters of the flagged pixels of n_img images
+ * (Sec. 3, Hoshen-Kopelman connectivity), periodic when `periodic` != 0.
+ * flags_dev: n_img*L*L bytes; labels_dev: n_img*L*L int32 (smallest linear
+ * index of the cluster, -1 off the flags); counts (host, n_img, optional):
+ * clusters per image.  Blocking. */
+int epfft_label(epfft_ctx *ctx, int32_t L, int32_t n_img, const uint8_t *flags_dev,
+                int32_t periodic, int32_t *labels_dev, int32_t *counts);
+
+/* Mean device time of the two fused passes of one iteration, measured with
+ * CUDA events around n_iter launch pairs of each on the context stream,
+ * from the uniform state eps = E (iterations never stop early).
+ * col_ms: forward column FFT + Green operator + inverse column FFT;
+ * row_ms: inverse row FFT + local step + residual partials + forward row FFT.
+ * Blocking. */
+int epfft_time_passes(epfft_ctx *ctx, const epfft_problem *problem, const double E[4],
+                      int32_t n_iter, float *col_ms, float *row_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EPFFT_H */

@@ -1,0 +1,342 @@
+"""Thin ctypes binding of libepfft.so (include/epfft.h): argument marshalling
+only, every step of the computation runs in the library's CUDA kernels.
+
+The functions keep the C names.  Device memory is torch's: the context
+allocates through torch's caching allocator (the C ABI's allocator hook),
+device-side inputs and outputs are torch CUDA tensors, and host-side ones are
+numpy arrays.  There is no fallback: if the library is missing or cannot be
+loaded every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libepfft.so")
+
+EPFFT_OK = 0
+EPFFT_PENDING = 1
+EPFFT_ERR_ARG = -1
+EPFFT_ERR_OOM = -2
+EPFFT_ERR_NUMERIC = -3
+EPFFT_NOT_CONVERGED = -4
+EPFFT_ERR_DEVICE_TIMEOUT = -5
+EPFFT_ERR_CUDA = -6
+EPFFT_ERR_UNSUPPORTED = -7
+EPFFT_FP64 = 0
+EPFFT_FP32 = 1
+EPFFT_GREEN_EQ3 = 0
+
+SYMBOLS = ["epfft_create", "epfft_destroy", "epfft_strerror", "epfft_supported", "epfft_solve",
+           "epfft_solve_batch", "epfft_mask", "epfft_iterate", "epfft_project", "epfft_label",
+           "epfft_time_passes"]
+
+
+class EpfftError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+AllocFn = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FreeFn = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class _Options(C.Structure):
+    _fields_ = [("device", C.c_int32), ("reserved", C.c_int32), ("stream", C.c_void_p),
+                ("alloc", AllocFn), ("free", FreeFn), ("alloc_user", C.c_void_p)]
+
+
+class _Problem(C.Structure):
+    _fields_ = [("L", C.c_int32), ("precision", C.c_int32), ("void_fraction", C.c_double),
+                ("seed", C.c_uint64), ("mask", C.c_void_p), ("mask_on_device", C.c_int32),
+                ("green", C.c_int32), ("mu", C.c_double), ("lambda_", C.c_double),
+                ("yield_stress", C.c_double), ("mu0", C.c_double), ("lambda0", C.c_double),
+                ("tol_eq", C.c_double), ("tol_macro", C.c_double), ("max_iter", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class _Path(C.Structure):
+    _fields_ = [("n_inc", C.c_int32), ("reserved", C.c_int32), ("E", C.c_void_p)]
+
+
+class _Fields(C.Structure):
+    _fields_ = [("eps", C.c_void_p), ("plastic", C.c_void_p), ("labels", C.c_void_p),
+                ("on_device", C.c_int32), ("reserved", C.c_int32)]
+
+
+RECORD_DTYPE = np.dtype([("sig_mean", "f8", 4), ("eps_mean", "f8", 4), ("eta1", "f8"), ("eta2", "f8"),
+                         ("eta3", "f8"), ("iterations", "i4"), ("n_plastic", "i4"),
+                         ("n_clusters", "i4"), ("status", "i4")])
+assert RECORD_DTYPE.itemsize == 104
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it is missing (no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_0802_2488_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, dbl = C.c_void_p, C.c_int32, C.c_double
+        L.epfft_create.argtypes = [C.POINTER(vp), C.POINTER(_Options)]
+        L.epfft_destroy.argtypes = [vp]
+        L.epfft_destroy.restype = None
+        L.epfft_strerror.argtypes = [C.c_int]
+        L.epfft_strerror.restype = C.c_char_p
+        L.epfft_supported.argtypes = [i32, i32]
+        L.epfft_solve.argtypes = [vp, C.POINTER(_Problem), C.POINTER(_Path), vp, C.POINTER(_Fields)]
+        L.epfft_solve_batch.argtypes = [vp, i32, C.POINTER(_Problem), C.POINTER(_Path), C.POINTER(vp),
+                                        C.POINTER(_Fields)]
+        L.epfft_mask.argtypes = [i32, dbl, C.c_uint64, vp, vp]
+        L.epfft_iterate.argtypes = [vp, C.POINTER(_Problem), C.POINTER(dbl), vp, i32, vp]
+        L.epfft_project.argtypes = [vp, i32, i32, dbl, dbl, C.POINTER(dbl), vp, vp]
+        L.epfft_label.argtypes = [vp, i32, i32, vp, i32, vp, vp]
+        L.epfft_time_passes.argtypes = [vp, C.POINTER(_Problem), C.POINTER(dbl), i32, C.POINTER(C.c_float),
+                                        C.POINTER(C.c_float)]
+        for s in SYMBOLS:
+            if s not in ("epfft_destroy", "epfft_strerror"):
+                getattr(L, s).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().epfft_strerror(int(code)).decode()
+
+
+def _check(rc: int, what: str, allow=(EPFFT_OK,)) -> int:
+    if rc not in allow:
+        raise EpfftError(rc, what)
+    return rc
+
+
+# --------------------------------------------------------------------------
+# Problem description (Sec. 2) and the default material of the workloads
+# --------------------------------------------------------------------------
+
+@dataclass
+class Problem:
+    L: int
+    precision: str = "fp64"          # 'fp64' | 'fp32'
+    void_fraction: float = 0.0
+    seed: int = 0
+    mask: Optional[object] = None    # numpy uint8 (L, L) or torch CUDA uint8 tensor; None: generated
+    mu: float = 1.0
+    lambda_: float = 1.5
+    yield_stress: float = 1.0
+    mu0: Optional[float] = None      # reference medium; None: the matrix moduli
+    lambda0: Optional[float] = None
+    tol_eq: float = 1e-8
+    tol_macro: float = 1e-8
+    max_iter: int = 10000
+
+    def _c(self) -> tuple[_Problem, object]:
+        keep = None
+        mptr, mdev = None, 0
+        if self.mask is not None:
+            if isinstance(self.mask, np.ndarray):
+                keep = np.ascontiguousarray(self.mask, dtype=np.uint8)
+                assert keep.size == self.L * self.L
+                mptr = keep.ctypes.data
+            else:  # torch tensor on the device
+                keep = self.mask.contiguous()
+                assert keep.is_cuda and keep.numel() == self.L * self.L
+                mptr, mdev = keep.data_ptr(), 1
+        prec = {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[self.precision]
+        p = _Problem(self.L, prec, float(self.void_fraction), int(self.seed) & (2**64 - 1), mptr, mdev,
+                     EPFFT_GREEN_EQ3, self.mu, self.lambda_, self.yield_stress,
+                     self.mu if self.mu0 is None else self.mu0,
+                     self.lambda_ if self.lambda0 is None else self.lambda0,
+                     self.tol_eq, self.tol_macro, int(self.max_iter), 0)
+        return p, keep
+
+    @property
+    def real_dtype(self):
+        return np.float64 if self.precision == "fp64" else np.float32
+
+
+def _path(E) -> tuple[_Path, np.ndarray]:
+    a = np.ascontiguousarray(E, dtype=np.float64).reshape(-1, 4)
+    return _Path(a.shape[0], 0, a.ctypes.data), a
+
+
+# --------------------------------------------------------------------------
+# Context (epfft_create / epfft_destroy)
+# --------------------------------------------------------------------------
+
+class Context:
+    """epfft_ctx on one CUDA device, allocating through torch's caching
+    allocator on its own non-blocking stream."""
+
+    def __init__(self, device: int = 0, torch_allocator: bool = True):
+        import torch
+        self.device = device
+        self._torch = torch
+        torch.cuda.init()
+        self.handle = C.c_void_p()
+        if torch_allocator:
+            def _alloc(nbytes, stream, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream or 0)
+                except Exception:
+                    return None
+
+            def _free(ptr, nbytes, stream, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._cbs = (AllocFn(_alloc), FreeFn(_free))
+            opts = _Options(device, 0, None, self._cbs[0], self._cbs[1], None)
+        else:
+            self._cbs = None
+            opts = _Options(device, 0, None, AllocFn(), FreeFn(), None)
+        _check(lib().epfft_create(C.byref(self.handle), C.byref(opts)), "epfft_create")
+
+    def close(self):
+        if self.handle:
+            lib().epfft_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def epfft_create(device: int = 0) -> Context:
+    return Context(device)
+
+
+def epfft_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def epfft_strerror(code: int) -> str:
+    return strerror(code)
+
+
+def epfft_supported(L: int, precision: str) -> bool:
+    return bool(lib().epfft_supported(L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision]))
+
+
+@dataclass
+class Fields:
+    eps: Optional[np.ndarray] = None       # (L, L, 4) final local strain
+    plastic: Optional[np.ndarray] = None   # (n_inc, L, L) uint8
+    labels: Optional[np.ndarray] = None    # (n_inc, L, L) int32
+
+
+def _host_fields(prob: Problem, n_inc: int):
+    L = prob.L
+    f = Fields(np.empty((L, L, 4), dtype=prob.real_dtype), np.empty((n_inc, L, L), np.uint8),
+               np.empty((n_inc, L, L), np.int32))
+    cf = _Fields(f.eps.ctypes.data, f.plastic.ctypes.data, f.labels.ctypes.data, 0, 0)
+    return f, cf
+
+
+def epfft_solve(ctx: Context, problem: Problem, path, fields: bool = False):
+    """Blocking solve along `path` ((n_inc, 4) mean strains).  Returns
+    (rc, records[, Fields]); rc is EPFFT_OK or EPFFT_NOT_CONVERGED."""
+    p, keep = problem._c()
+    cp, parr = _path(path)
+    rec = np.zeros(cp.n_inc, dtype=RECORD_DTYPE)
+    f, cf = _host_fields(problem, cp.n_inc) if fields else (None, None)
+    rc = lib().epfft_solve(ctx.handle, C.byref(p), C.byref(cp), rec.ctypes.data,
+                           C.byref(cf) if cf is not None else None)
+    _check(rc, "epfft_solve", (EPFFT_OK, EPFFT_NOT_CONVERGED))
+    return (rc, rec, f) if fields else (rc, rec)
+
+
+def epfft_solve_batch(ctx: Context, problems: Sequence[Problem], paths: Sequence, fields: bool = False):
+    """Blocking solve of problems sharing L and precision, advanced together
+    in one device loop.  Returns (rc, [records][, [Fields]])."""
+    n = len(problems)
+    cps, keeps = zip(*(p._c() for p in problems))
+    arr = (_Problem * n)(*cps)
+    pth = [_path(P) for P in paths]
+    carr = (_Path * n)(*(x[0] for x in pth))
+    recs = [np.zeros(x[0].n_inc, dtype=RECORD_DTYPE) for x in pth]
+    rptr = (C.c_void_p * n)(*(r.ctypes.data for r in recs))
+    if fields:
+        fl = [_host_fields(problems[i], pth[i][0].n_inc) for i in range(n)]
+        farr = (_Fields * n)(*(x[1] for x in fl))
+    rc = lib().epfft_solve_batch(ctx.handle, n, arr, carr, rptr, farr if fields else None)
+    _check(rc, "epfft_solve_batch", (EPFFT_OK, EPFFT_NOT_CONVERGED))
+    return (rc, recs, [x[0] for x in fl]) if fields else (rc, recs)
+
+
+def epfft_mask(L: int, void_fraction: float, seed: int, device: int = 0):
+    """Void mask of Sec. 2 as a torch uint8 (L, L) CUDA tensor."""
+    import torch
+    m = torch.empty((L, L), dtype=torch.uint8, device=f"cuda:{device}")
+    s = torch.cuda.current_stream(device)
+    _check(lib().epfft_mask(L, float(void_fraction), int(seed) & (2**64 - 1), m.data_ptr(), s.cuda_stream),
+           "epfft_mask")
+    return m
+
+
+def epfft_iterate(ctx: Context, problem: Problem, E, eps, n_iter: int):
+    """n_iter AL iterations from the CUDA tensor eps ((L, L, 4), the
+    problem's real dtype), in place.  Returns the record of the last iterate."""
+    import torch
+    p, keep = problem._c()
+    assert eps.is_cuda and eps.is_contiguous() and eps.numel() == 4 * problem.L ** 2
+    assert eps.dtype == (torch.float64 if problem.precision == "fp64" else torch.float32)
+    Ea = (C.c_double * 4)(*[float(x) for x in E])
+    rec = np.zeros(1, dtype=RECORD_DTYPE)
+    torch.cuda.current_stream(ctx.device).synchronize()
+    _check(lib().epfft_iterate(ctx.handle, C.byref(p), Ea, eps.data_ptr(), int(n_iter), rec.ctypes.data),
+           "epfft_iterate")
+    return rec[0]
+
+
+def epfft_project(ctx: Context, L: int, precision: str, lambda0: float, mu0: float, E, p):
+    """e = E + IDFT(G DFT(p)) (Eqs. 2-3) for a CUDA tensor p (3, L, L)."""
+    import torch
+    assert p.is_cuda and p.is_contiguous() and tuple(p.shape) == (3, L, L)
+    e = torch.empty_like(p)
+    Ea = (C.c_double * 4)(*[float(x) for x in E])
+    torch.cuda.current_stream(ctx.device).synchronize()
+    _check(lib().epfft_project(ctx.handle, L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision],
+                               float(lambda0), float(mu0), Ea, p.data_ptr(), e.data_ptr()), "epfft_project")
+    return e
+
+
+def epfft_label(ctx: Context, flags, periodic: bool = True):
+    """Clusters of flagged pixels of a CUDA uint8 tensor (n, L, L).
+    Returns (labels int32 tensor, counts numpy)."""
+    import torch
+    assert flags.is_cuda and flags.dtype == torch.uint8 and flags.is_contiguous()
+    n, L, L2 = flags.shape
+    assert L == L2
+    lab = torch.empty((n, L, L), dtype=torch.int32, device=flags.device)
+    counts = np.zeros(n, dtype=np.int32)
+    torch.cuda.current_stream(ctx.device).synchronize()
+    _check(lib().epfft_label(ctx.handle, L, n, flags.data_ptr(), 1 if periodic else 0, lab.data_ptr(),
+                             counts.ctypes.data), "epfft_label")
+    return lab, counts
+
+
+def epfft_time_passes(ctx: Context, problem: Problem, E, n_iter: int):
+    """(column-pass ms, row-pass ms): mean CUDA-event durations over n_iter
+    launches of each, from the uniform state eps = E."""
+    p, keep = problem._c()
+    Ea = (C.c_double * 4)(*[float(x) for x in E])
+    a, b = C.c_float(), C.c_float()
+    _check(lib().epfft_time_passes(ctx.handle, C.byref(p), Ea, int(n_iter), C.byref(a), C.byref(b)),
+           "epfft_time_passes")
+    return a.value, b.value

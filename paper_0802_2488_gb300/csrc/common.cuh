@@ -1,0 +1,111 @@
+// Common device types for the epfft CUDA path (sm_103a).
+//
+// Conventions shared by every kernel of the library:
+//   * lattice L x L (L a power of two), pixel x = (x1, x2), linear index
+//     x2 * L + x1 (x1 fastest);
+//   * strain / stress per pixel: 4 reals (11, 22, 33, 12);
+//   * forward DFT kernel exp(-i q.x), q_j = 2 pi m_j / L, which makes the
+//     forward difference of Eq. 1 the multiplication by i k_j of Eq. 2.
+#pragma once
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+namespace epfft {
+
+template <typename T>
+struct C2 {
+  T re, im;
+};
+
+template <typename T>
+__device__ __forceinline__ C2<T> mk(T a, T b) {
+  C2<T> r;
+  r.re = a;
+  r.im = b;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ C2<T> operator+(C2<T> a, C2<T> b) { return mk(a.re + b.re, a.im + b.im); }
+template <typename T>
+__device__ __forceinline__ C2<T> operator-(C2<T> a, C2<T> b) { return mk(a.re - b.re, a.im - b.im); }
+template <typename T>
+__device__ __forceinline__ C2<T> operator*(C2<T> a, C2<T> b) {
+  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename T>
+__device__ __forceinline__ C2<T> operator*(T s, C2<T> a) { return mk(s * a.re, s * a.im); }
+template <typename T>
+__device__ __forceinline__ C2<T> conj(C2<T> a) { return mk(a.re, -a.im); }
+// multiply by -i (forward) or +i (inverse)
+template <typename T, bool INV>
+__device__ __forceinline__ C2<T> mul_mi(C2<T> a) {
+  return INV ? mk(-a.im, a.re) : mk(a.im, -a.re);
+}
+template <typename T>
+__device__ __forceinline__ C2<T> mul_i(C2<T> a) { return mk(-a.im, a.re); }
+template <typename T>
+__device__ __forceinline__ T norm2(C2<T> a) { return a.re * a.re + a.im * a.im; }
+
+// Solve phases of the per-solve state machine driven on the device.
+enum Phase : int32_t {
+  PH_INIT = 0,   // warm start of increment `inc` from the accepted state
+  PH_ITER = 1,   // augmented-Lagrangian iterations of increment `inc`
+  PH_FINAL = 2,  // write the plastic flags of the last accepted state
+  PH_DONE = 3,
+};
+
+// Per-increment result, written by the device (layout of epfft_record).
+struct Record {
+  double sig_mean[4];
+  double eps_mean[4];
+  double eta1, eta2, eta3;
+  int32_t iterations, n_plastic, n_clusters, status;
+};
+
+// Accumulators of the row pass (per CTA), FP64, in this order.
+enum Acc : int {
+  A_S11 = 0, A_S22, A_S33, A_S12,  // sum sigma(eps^n)
+  A_E11, A_E22, A_E33, A_E12,      // sum eps^n
+  A_DIV2,                          // sum |div sigma(eps^n)|^2
+  A_COMP,                          // sum (eps^{n+1} - e^{n+1}):(same)
+  A_NPL,                           // plastic pixels of eps^n (matrix)
+  N_ACC
+};
+constexpr int PART_STRIDE = 12;  // doubles per CTA partial record
+
+// Device-resident state of one solve of a batch.
+struct Solve {
+  // material: matrix lambda, mu, Y; reference medium lambda0, mu0
+  double lam, mu, Y, lam0, mu0;
+  double tol_eq, tol_macro;
+  int32_t max_iter, n_inc;
+  const double* path;  // n_inc * 4 prescribed mean strains (11,22,33,12)
+  Record* rec;         // n_inc records
+  uint8_t* flags;      // n_inc * L * L plastic flags (may be null)
+  const uint8_t* mask; // L * L, 1 = void
+  void* eps[2];        // ping-pong local strain, L*L*4 reals
+  void* spec;          // 3 * L * L/2 complex, tiled column layout
+  double* partials;    // n_row_ctas * PART_STRIDE
+  // mutable state
+  int32_t phase, inc, iter, cur;
+  int32_t status;
+  uint32_t arrive;
+  double Eprev[4];
+  double sig_prev[4];
+  double eta3_cur;
+  int64_t total_iters;  // pixel-iteration accounting: passes that did work
+};
+
+// Batch-level control shared by all solves of one launch.
+struct BatchCtl {
+  uint32_t arrive;          // row-pass CTAs finished in the current step
+  int32_t active;           // solves not yet DONE after the last row pass
+  int64_t body_iters;       // loop steps executed
+  int64_t max_body_iters;   // bound on loop steps (a solve needs at most
+                            // n_inc * (max_iter + 2) + 1)
+  int32_t timed_out;        // the bound stopped the loop with work left
+  int32_t pad;
+};
+
+}  // namespace epfft

@@ -1,0 +1,124 @@
+// Instantiation of the launch table for one real type EPFFT_REAL over the
+// supported lattice sides EPFFT_LMAX.
+#pragma once
+#include "launch.cuh"
+#include "passes.cuh"
+
+namespace epfft {
+
+#define EPFFT_FOR_L(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) EPFFT_L4096(X)
+
+template <typename T, int L>
+static bool shape_of(PassShape* o) {
+  using C = Cfg<T, L>;
+  o->rows_per_cta = C::RR;
+  o->tile_w = C::W;
+  o->row_ctas = L / C::RR;
+  o->col_ctas = (L / 2) / C::W;
+  o->nt_row = C::NT_ROW;
+  o->nt_col = C::NT_COL;
+  o->row_smem = C::ROW_SMEM;
+  o->col_smem = C::COL_SMEM;
+  return true;
+}
+
+template <typename T, int L>
+static cudaError_t prepare_L() {
+  using C = Cfg<T, L>;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(row_pass<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::ROW_SMEM)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(col_pass<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::COL_SMEM)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(row_forward<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::ROW_SMEM)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(row_inverse<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::ROW_SMEM);
+}
+
+template <>
+bool pass_shape<EPFFT_REAL>(int L, PassShape* out) {
+  switch (L) {
+#define X(n) case n: return shape_of<EPFFT_REAL, n>(out);
+    EPFFT_FOR_L(X)
+#undef X
+    default: return false;
+  }
+}
+
+template <>
+cudaError_t prepare<EPFFT_REAL>(int L) {
+  switch (L) {
+#define X(n) case n: return prepare_L<EPFFT_REAL, n>();
+    EPFFT_FOR_L(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <>
+cudaError_t launch_row<EPFFT_REAL>(int L, int nb, cudaStream_t s, Solve* solves, BatchCtl* bc, const void* tw,
+                                   cudaGraphConditionalHandle cond, int use_cond) {
+  switch (L) {
+#define X(n)                                                                                         \
+  case n: {                                                                                          \
+    using C = Cfg<EPFFT_REAL, n>;                                                                    \
+    row_pass<EPFFT_REAL, n><<<dim3(n / C::RR, nb), C::NT_ROW, C::ROW_SMEM, s>>>(                     \
+        solves, nb, bc, reinterpret_cast<const C2<EPFFT_REAL>*>(tw), cond, use_cond);                \
+    return cudaGetLastError();                                                                       \
+  }
+    EPFFT_FOR_L(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <>
+cudaError_t launch_col<EPFFT_REAL>(int L, int nb, cudaStream_t s, Solve* solves, const void* tw, const void* ktab,
+                                   cudaGraphConditionalHandle cond, int use_cond) {
+  switch (L) {
+#define X(n)                                                                                         \
+  case n: {                                                                                          \
+    using C = Cfg<EPFFT_REAL, n>;                                                                    \
+    col_pass<EPFFT_REAL, n><<<dim3((n / 2) / C::W, nb), C::NT_COL, C::COL_SMEM, s>>>(                \
+        solves, reinterpret_cast<const C2<EPFFT_REAL>*>(tw),                                         \
+        reinterpret_cast<const C2<EPFFT_REAL>*>(ktab), cond, use_cond);                              \
+    return cudaGetLastError();                                                                       \
+  }
+    EPFFT_FOR_L(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <>
+cudaError_t launch_row_forward<EPFFT_REAL>(int L, cudaStream_t s, const void* p, void* spec, const void* tw) {
+  switch (L) {
+#define X(n)                                                                                         \
+  case n: {                                                                                          \
+    using C = Cfg<EPFFT_REAL, n>;                                                                    \
+    row_forward<EPFFT_REAL, n><<<n / C::RR, C::NT_ROW, C::ROW_SMEM, s>>>(                            \
+        reinterpret_cast<const EPFFT_REAL*>(p), reinterpret_cast<C2<EPFFT_REAL>*>(spec),             \
+        reinterpret_cast<const C2<EPFFT_REAL>*>(tw));                                                \
+    return cudaGetLastError();                                                                       \
+  }
+    EPFFT_FOR_L(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <>
+cudaError_t launch_row_inverse<EPFFT_REAL>(int L, cudaStream_t s, const void* spec, void* e, const void* tw) {
+  switch (L) {
+#define X(n)                                                                                         \
+  case n: {                                                                                          \
+    using C = Cfg<EPFFT_REAL, n>;                                                                    \
+    row_inverse<EPFFT_REAL, n><<<n / C::RR, C::NT_ROW, C::ROW_SMEM, s>>>(                            \
+        reinterpret_cast<const C2<EPFFT_REAL>*>(spec), reinterpret_cast<EPFFT_REAL*>(e),             \
+        reinterpret_cast<const C2<EPFFT_REAL>*>(tw));                                                \
+    return cudaGetLastError();                                                                       \
+  }
+    EPFFT_FOR_L(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace epfft

@@ -1,0 +1,604 @@
+// The two fused passes of one augmented-Lagrangian iteration and their
+// helpers.
+//
+// Spectrum layout (per solve): 3 components (11, 22, 12) of the half
+// spectrum along x1, packed: element m1 = 0 holds X(0) + i X(L/2) (both real
+// after a real row transform), m1 = 1 .. L/2-1 hold X(m1).  After the column
+// pass the same layout holds the column-transformed data.  In HBM it is
+// tiled by W columns: index ((c * L/(2W) + b) * L + x2) * W + w for column
+// m1 = b * W + w, so a column pass CTA reads one contiguous slab and a row
+// pass CTA reads RR * W contiguous complex numbers per slab.
+//
+// Row pass (iteration n -> n+1, one CTA per RR rows):
+//   inverse row transform of e^{n+1} -> pixelwise: sigma(eps^n) (kept for the
+//   residual of eps^n), tau = sigma(eps^n) + C0:e^{n+1}, local step ->
+//   eps^{n+1}, p^{n+1} = sigma(eps^{n+1}) - C0:eps^{n+1} -> forward row
+//   transform.  The residual of eps^n (backward divergence of Eq. 1 with a
+//   halo row) and the means are reduced in FP64 per CTA; the last CTA of a
+//   solve finalizes the indicators of Sec. 2 and advances the solve.
+// Column pass (one CTA per W columns): forward column transform, the Green
+//   operator of Eq. 3 per frequency (scaled by 1/L^2, mean strain at q = 0),
+//   inverse column transform.
+#pragma once
+#include "common.cuh"
+#include "fft.cuh"
+#include "physics.cuh"
+
+namespace epfft {
+
+// Tiling of one lattice size in one precision.
+template <typename T, int L>
+struct Cfg {
+  static constexpr bool F64 = sizeof(T) == 8;
+  static constexpr int M = L / 2;
+  // rows per row-pass CTA
+  static constexpr int RR = F64 ? (L <= 256 ? 2 : 4) : (L <= 128 ? 2 : (L <= 256 ? 4 : (L <= 2048 ? 8 : 4)));
+  // columns per column-pass CTA (= tile width of the spectrum layout)
+  static constexpr int W0 = F64 ? (L <= 256 ? 2 : (L <= 1024 ? 4 : 2))
+                                : (L <= 64 ? 2 : (L <= 256 ? 4 : (L <= 1024 ? 8 : (L <= 2048 ? 4 : 2))));
+  static constexpr int W = W0 < M ? W0 : M;
+  static constexpr int NT_ROW = L < 32 ? 32 : (L > 512 ? 512 : L);
+  static constexpr int NT_COL0 = ((3 * W * L / 8 + 31) / 32) * 32;
+  static constexpr int NT_COL = NT_COL0 < 32 ? 32 : (NT_COL0 > 512 ? 512 : NT_COL0);
+  static constexpr size_t ROW_SMEM = (size_t)3 * RR * M * sizeof(C2<T>) + (size_t)2 * L * sizeof(T);
+  static constexpr size_t COL_SMEM = (size_t)3 * W * L * sizeof(C2<T>);
+  static_assert(L >= 4 && (L & (L - 1)) == 0, "L must be a power of two >= 4");
+  static_assert(M % W == 0, "tile width must divide L/2");
+  static_assert(L % RR == 0, "rows per CTA must divide L");
+  static_assert(ROW_SMEM <= 232448 && COL_SMEM <= 232448, "shared memory per CTA");
+  static_assert(NT_ROW % 32 == 0 && NT_COL % 32 == 0, "whole warps");
+  static_assert(L <= NT_ROW || L % NT_ROW == 0, "pixel mapping");
+};
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  static __device__ __forceinline__ void load(const float* p, float e[4]) {
+    float4 v = *reinterpret_cast<const float4*>(p);
+    e[0] = v.x; e[1] = v.y; e[2] = v.z; e[3] = v.w;
+  }
+  static __device__ __forceinline__ void store(float* p, const float e[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(e[0], e[1], e[2], e[3]);
+  }
+};
+template <>
+struct Vec4<double> {
+  static __device__ __forceinline__ void load(const double* p, double e[4]) {
+    double2 a = reinterpret_cast<const double2*>(p)[0];
+    double2 b = reinterpret_cast<const double2*>(p)[1];
+    e[0] = a.x; e[1] = a.y; e[2] = b.x; e[3] = b.y;
+  }
+  static __device__ __forceinline__ void store(double* p, const double e[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(e[0], e[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(e[2], e[3]);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Row-side helpers.  Shared-memory layout of the RR rows: element n of
+// component c of row r at sp[n * 3RR + c * RR + r].
+// ---------------------------------------------------------------------------
+template <typename T, int L, int RR, int W, int NT>
+struct RowIO {
+  static constexpr int M = L / 2, NB = 3 * RR, NBK = M / W;
+
+  static __device__ __forceinline__ void load(C2<T>* sp, const C2<T>* __restrict__ spec, int r0) {
+    for (int e = threadIdx.x; e < 3 * M * RR; e += NT) {
+      const int c = e / (M * RR);
+      const int rem = e - c * (M * RR);
+      const int b = rem / (RR * W);
+      const int rem2 = rem - b * (RR * W);
+      const int r = rem2 / W, w = rem2 - r * W;
+      sp[(b * W + w) * NB + c * RR + r] = spec[((size_t)(c * NBK + b) * L + r0 + r) * W + w];
+    }
+  }
+  static __device__ __forceinline__ void store(const C2<T>* sp, C2<T>* __restrict__ spec, int r0) {
+    for (int e = threadIdx.x; e < 3 * M * RR; e += NT) {
+      const int c = e / (M * RR);
+      const int rem = e - c * (M * RR);
+      const int b = rem / (RR * W);
+      const int rem2 = rem - b * (RR * W);
+      const int r = rem2 / W, w = rem2 - r * W;
+      spec[((size_t)(c * NBK + b) * L + r0 + r) * W + w] = sp[(b * W + w) * NB + c * RR + r];
+    }
+  }
+  // Half spectrum (packed) -> Z for the half-length inverse transform:
+  // Z(k) = (Y(k) + Y*(M-k)) + i exp(+2 pi i k / L) (Y(k) - Y*(M-k)),
+  // with Y(0) = Re S(0), Y(M) = Im S(0).  Unnormalised: the inverse
+  // half-length transform of Z then yields x(2n) + i x(2n+1) of
+  // x(x1) = sum_m Y(m) exp(+2 pi i m x1 / L).
+  static __device__ __forceinline__ void c2r_twist(C2<T>* sp, const C2<T>* __restrict__ tw) {
+    constexpr int NP = M / 2 + 1;
+    for (int e = threadIdx.x; e < NB * NP; e += NT) {
+      const int k = e / NB, cr = e - k * NB;
+      C2<T>* s = sp + cr;
+      if (k == 0) {
+        const C2<T> s0 = s[0];
+        s[0] = mk(s0.re + s0.im, s0.re - s0.im);
+      } else {
+        const int kk = M - k;
+        const C2<T> a = s[k * NB], b = s[kk * NB];
+        const C2<T> wk = conj(tw[k]);
+        const C2<T> zk = (a + conj(b)) + mul_i(wk * (a - conj(b)));
+        s[k * NB] = zk;
+        if (kk != k) s[kk * NB] = (b + conj(a)) - mul_i(conj(wk) * (b - conj(a)));
+      }
+    }
+  }
+  // Z = transform of z(n) = x(2n) + i x(2n+1) -> packed half spectrum of x:
+  // X(k) = [(Z(k) + Z*(M-k)) - i exp(-2 pi i k / L) (Z(k) - Z*(M-k))] / 2,
+  // S(0) = X(0) + i X(M).
+  static __device__ __forceinline__ void r2c_twist(C2<T>* sp, const C2<T>* __restrict__ tw) {
+    constexpr int NP = M / 2 + 1;
+    for (int e = threadIdx.x; e < NB * NP; e += NT) {
+      const int k = e / NB, cr = e - k * NB;
+      C2<T>* s = sp + cr;
+      if (k == 0) {
+        const C2<T> z = s[0];
+        s[0] = mk(z.re + z.im, z.re - z.im);
+      } else {
+        const int kk = M - k;
+        const C2<T> a = s[k * NB], b = s[kk * NB];
+        const C2<T> wk = tw[k];
+        s[k * NB] = T(0.5) * ((a + conj(b)) - mul_i(wk * (a - conj(b))));
+        if (kk != k) s[kk * NB] = T(0.5) * ((b + conj(a)) + mul_i(conj(wk) * (b - conj(a))));
+      }
+    }
+  }
+  template <bool INV>
+  static __device__ __forceinline__ void fft(C2<T>* sp, const C2<T>* __restrict__ tw) {
+    // three groups (components) of RR rows each
+    fft_block<T, M, 3, RR, NT, INV>(sp, tw, 2);
+  }
+  // real value of pixel x1 of component c, row r
+  static __device__ __forceinline__ T& px(C2<T>* sp, int c, int r, int x1) {
+    return reinterpret_cast<T*>(sp)[2 * ((x1 >> 1) * NB + c * RR + r) + (x1 & 1)];
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ void load_E(const double* p, T E[4]) {
+  E[0] = T(p[0]); E[1] = T(p[1]); E[2] = T(p[2]); E[3] = T(p[3]);
+}
+
+// Reduce N_ACC per-thread values (promoted to FP64) over the CTA in a fixed
+// order; thread 0 returns the sums in out.
+template <int NT>
+__device__ __forceinline__ void block_reduce(double v[N_ACC], double* out) {
+  __shared__ double red[NT / 32][N_ACC];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < N_ACC; i++) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < N_ACC; i++) red[wid][i] = v[i];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int i = 0; i < N_ACC; i++) {
+      double x = lane < NT / 32 ? red[lane][i] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) out[i] = x;
+    }
+  }
+}
+
+// Last CTA of a solve's row pass: indicators of Sec. 2 and the state
+// machine.  Runs on one thread after all partials are visible.
+__device__ __forceinline__ void finalize_solve(Solve& S, int phase, int n_ctas, int L) {
+  if (phase == PH_INIT) {
+    const double* E = S.path + 4 * S.inc;
+    for (int c = 0; c < 4; c++) S.Eprev[c] = E[c];
+    S.cur = 1 - S.cur;
+    S.iter = 0;
+    S.phase = PH_ITER;
+    return;
+  }
+  if (phase == PH_FINAL) {
+    S.phase = PH_DONE;
+    return;
+  }
+  // PH_ITER: sums over the CTAs in a fixed order
+  double A[N_ACC];
+  for (int i = 0; i < N_ACC; i++) A[i] = 0.0;
+  for (int b = 0; b < n_ctas; b++)
+    for (int i = 0; i < N_ACC; i++) A[i] += __ldcg(S.partials + (size_t)b * PART_STRIDE + i);
+  const double inv = 1.0 / ((double)L * (double)L);
+  double sig[4], epsm[4];
+  for (int c = 0; c < 4; c++) {
+    sig[c] = A[A_S11 + c] * inv;
+    epsm[c] = A[A_E11 + c] * inv;
+  }
+  const double div2 = A[A_DIV2] * inv, comp = A[A_COMP] * inv;
+  const double* E = S.path + 4 * S.inc;
+  double EE = E[0] * E[0] + E[1] * E[1] + E[2] * E[2] + 2.0 * E[3] * E[3];
+  if (EE == 0.0) EE = 1.0;
+  const double eta3_next = sqrt(comp / EE);
+  const int n = S.iter;
+  S.total_iters += 1;
+  if (n >= 1) {
+    const double ss = sig[0] * sig[0] + sig[1] * sig[1] + 2.0 * sig[3] * sig[3];
+    double ds[4];
+    for (int c = 0; c < 4; c++) ds[c] = sig[c] - S.sig_prev[c];
+    const double dd = ds[0] * ds[0] + ds[1] * ds[1] + 2.0 * ds[3] * ds[3];
+    double eta1, eta2;
+    if (ss > 0.0) {
+      eta1 = sqrt(div2 / ss);
+      eta2 = sqrt(dd / ss);
+    } else {
+      eta1 = div2 == 0.0 ? 0.0 : CUDART_INF;
+      eta2 = dd == 0.0 ? 0.0 : CUDART_INF;
+    }
+    const bool finite = isfinite(eta1) && isfinite(eta2) && isfinite(sig[0]) && isfinite(sig[1]) &&
+                        isfinite(sig[3]);
+    const bool conv = eta1 < S.tol_eq && eta2 < S.tol_macro;
+    if (!finite || conv || n >= S.max_iter) {
+      Record& R = S.rec[S.inc];
+      for (int c = 0; c < 4; c++) {
+        R.sig_mean[c] = sig[c];
+        R.eps_mean[c] = epsm[c];
+      }
+      R.eta1 = eta1;
+      R.eta2 = eta2;
+      R.eta3 = S.eta3_cur;
+      R.iterations = n;
+      R.n_plastic = (int32_t)A[A_NPL];
+      R.n_clusters = 0;
+      R.status = !finite ? 2 : (conv ? 0 : 1);
+      if (!finite) {
+        S.status = 2;
+        S.phase = PH_DONE;
+      } else if (S.inc + 1 < S.n_inc) {
+        S.inc += 1;
+        S.phase = PH_INIT;  // eps^n (buffer cur) is the accepted state
+      } else {
+        S.phase = PH_FINAL;
+      }
+      return;
+    }
+  }
+  for (int c = 0; c < 4; c++) S.sig_prev[c] = sig[c];
+  S.eta3_cur = eta3_next;
+  S.iter = n + 1;
+  S.cur = 1 - S.cur;
+}
+
+// After every CTA of the row pass: the last one decides whether the
+// device-side loop runs another step (condition of the graph's while node).
+__device__ __forceinline__ void batch_arrive(Solve* solves, int nb, BatchCtl* bc,
+                                             cudaGraphConditionalHandle cond, int use_cond) {
+  __threadfence();
+  const unsigned total = gridDim.x * gridDim.y;
+  const unsigned prev = atomicAdd(&bc->arrive, 1u);
+  if (prev == total - 1) {
+    __threadfence();
+    int active = 0;
+    for (int i = 0; i < nb; i++) active += (*(volatile int32_t*)&solves[i].phase) != PH_DONE;
+    bc->active = active;
+    bc->body_iters += 1;
+    const bool go = active > 0 && bc->body_iters < bc->max_body_iters;
+    if (!go && active > 0) bc->timed_out = 1;
+    if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
+    bc->arrive = 0;
+    __threadfence();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Row pass
+// ---------------------------------------------------------------------------
+template <typename T, int L>
+__global__ void __launch_bounds__(Cfg<T, L>::NT_ROW)
+row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restrict__ tw,
+         cudaGraphConditionalHandle cond, int use_cond) {
+  using C = Cfg<T, L>;
+  constexpr int RR = C::RR, W = C::W, NT = C::NT_ROW, M = C::M;
+  constexpr int P = L >= NT ? L / NT : 1;
+  using IO = RowIO<T, L, RR, W, NT>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C2<T>* sp = reinterpret_cast<C2<T>*>(smraw);
+  T* sb = reinterpret_cast<T*>(sp + 3 * RR * M);  // sigma11, sigma12 of the current row
+  __shared__ bool s_last;
+
+  Solve& S = solves[blockIdx.y];
+  const int phase = S.phase;
+  const int tid = threadIdx.x;
+  if (phase != PH_DONE) {
+    const int r0 = blockIdx.x * RR;
+    const int cur = S.cur;
+    const T* __restrict__ ein = reinterpret_cast<const T*>(S.eps[cur]);
+    T* __restrict__ eout = reinterpret_cast<T*>(S.eps[1 - cur]);
+    C2<T>* spec = reinterpret_cast<C2<T>*>(S.spec);
+    const uint8_t* __restrict__ mask = S.mask;
+    const Mat<T> m = make_mat<T>(S);
+    const size_t LL = (size_t)L * L;
+    T acc[N_ACC];
+#pragma unroll
+    for (int i = 0; i < N_ACC; i++) acc[i] = T(0);
+
+    if (phase == PH_FINAL) {
+      // plastic flags of the accepted state of the last increment
+      uint8_t* fl = S.flags ? S.flags + (size_t)(S.n_inc - 1) * LL : nullptr;
+      for (int r = 0; r < RR && fl; r++)
+        for (int j = 0; j < P; j++) {
+          const int x1 = tid + j * NT;
+          if (x1 >= L) continue;
+          const size_t x = (size_t)(r0 + r) * L + x1;
+          T e[4];
+          Vec4<T>::load(ein + 4 * x, e);
+          fl[x] = is_plastic(e, mask[x] != 0, m);
+        }
+    } else if (phase == PH_INIT) {
+      // warm start: eps^0 = accepted state + (E_inc - E_{inc-1}); p^0 -> spectrum
+      T dE[4];
+      const double* E = S.path + 4 * S.inc;
+      for (int c = 0; c < 4; c++) dE[c] = T(E[c] - S.Eprev[c]);
+      uint8_t* fl = (S.flags && S.inc > 0) ? S.flags + (size_t)(S.inc - 1) * LL : nullptr;
+      for (int r = 0; r < RR; r++)
+        for (int j = 0; j < P; j++) {
+          const int x1 = tid + j * NT;
+          if (x1 >= L) continue;
+          const size_t x = (size_t)(r0 + r) * L + x1;
+          const bool v = mask[x] != 0;
+          T e[4], s[4], c0[4];
+          Vec4<T>::load(ein + 4 * x, e);
+          if (fl) fl[x] = is_plastic(e, v, m);
+          for (int c = 0; c < 4; c++) e[c] += dE[c];
+          Vec4<T>::store(eout + 4 * x, e);
+          sigma(e, v, m, s);
+          c0_apply(e, m, c0);
+          IO::px(sp, 0, r, x1) = s[0] - c0[0];
+          IO::px(sp, 1, r, x1) = s[1] - c0[1];
+          IO::px(sp, 2, r, x1) = s[3] - c0[3];
+        }
+    } else {  // PH_ITER
+      T E[4];
+      load_E(S.path + 4 * S.inc, E);
+      IO::load(sp, spec, r0);
+      __syncthreads();
+      IO::c2r_twist(sp, tw);
+      __syncthreads();
+      IO::template fft<true>(sp, tw);
+      // halo row x2 = r0 - 1: sigma12 and sigma22 of eps^n for the backward
+      // difference along x2
+      T prev12[P], prev22[P];
+      {
+        const int xh = (r0 + L - 1) & (L - 1);
+#pragma unroll
+        for (int j = 0; j < P; j++) {
+          const int x1 = tid + j * NT;
+          prev12[j] = prev22[j] = T(0);
+          if (x1 >= L) continue;
+          const size_t x = (size_t)xh * L + x1;
+          T e[4], s[4];
+          Vec4<T>::load(ein + 4 * x, e);
+          sigma(e, mask[x] != 0, m, s);
+          prev12[j] = s[3];
+          prev22[j] = s[1];
+        }
+      }
+      for (int r = 0; r < RR; r++) {
+        T en[P][4], s[P][4];
+        bool vv[P];
+#pragma unroll
+        for (int j = 0; j < P; j++) {
+          const int x1 = tid + j * NT;
+          if (x1 >= L) continue;
+          const size_t x = (size_t)(r0 + r) * L + x1;
+          vv[j] = mask[x] != 0;
+          Vec4<T>::load(ein + 4 * x, en[j]);
+          const bool pl = sigma(en[j], vv[j], m, s[j]);
+          acc[A_NPL] += pl ? T(1) : T(0);
+          sb[x1] = s[j][0];
+          sb[L + x1] = s[j][3];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < P; j++) {
+          const int x1 = tid + j * NT;
+          if (x1 >= L) continue;
+          const size_t x = (size_t)(r0 + r) * L + x1;
+          const int xl = (x1 + L - 1) & (L - 1);
+          // Eq. 1: div_i = sum_j sigma_ij(x) - sigma_ij(x - e^j)
+          const T d1 = (s[j][0] - sb[xl]) + (s[j][3] - prev12[j]);
+          const T d2 = (s[j][3] - sb[L + xl]) + (s[j][1] - prev22[j]);
+          prev12[j] = s[j][3];
+          prev22[j] = s[j][1];
+#pragma unroll
+          for (int c = 0; c < 4; c++) {
+            acc[A_S11 + c] += s[j][c];
+            acc[A_E11 + c] += en[j][c];
+          }
+          acc[A_DIV2] += d1 * d1 + d2 * d2;
+          // augmented-Lagrangian update of this pixel
+          T e[4] = {IO::px(sp, 0, r, x1), IO::px(sp, 1, r, x1), E[2], IO::px(sp, 2, r, x1)};
+          T c0[4], tau[4], e1[4];
+          c0_apply(e, m, c0);
+#pragma unroll
+          for (int c = 0; c < 4; c++) tau[c] = s[j][c] + c0[c];
+          local_solve(tau, vv[j], m, e1);
+          Vec4<T>::store(eout + 4 * x, e1);
+          const T q0 = e1[0] - e[0], q1 = e1[1] - e[1], q2 = e1[2] - e[2], q3 = e1[3] - e[3];
+          acc[A_COMP] += q0 * q0 + q1 * q1 + q2 * q2 + T(2) * q3 * q3;
+          T s1[4];
+          sigma(e1, vv[j], m, s1);
+          c0_apply(e1, m, c0);
+          IO::px(sp, 0, r, x1) = s1[0] - c0[0];
+          IO::px(sp, 1, r, x1) = s1[1] - c0[1];
+          IO::px(sp, 2, r, x1) = s1[3] - c0[3];
+        }
+        __syncthreads();
+      }
+    }
+
+    if (phase == PH_ITER || phase == PH_INIT) {
+      __syncthreads();
+      IO::template fft<false>(sp, tw);
+      IO::r2c_twist(sp, tw);
+      __syncthreads();
+      IO::store(sp, spec, r0);
+    }
+    if (phase == PH_ITER) {
+      double v[N_ACC];
+#pragma unroll
+      for (int i = 0; i < N_ACC; i++) v[i] = (double)acc[i];
+      block_reduce<NT>(v, S.partials + (size_t)blockIdx.x * PART_STRIDE);
+    }
+    if (tid == 0) {
+      __threadfence();
+      const unsigned prev = atomicAdd(&S.arrive, 1u);
+      s_last = prev == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && tid == 0) {
+      __threadfence();
+      finalize_solve(S, phase, gridDim.x, L);
+      S.arrive = 0;
+    }
+  }
+  if (tid == 0) batch_arrive(solves, nb, bc, cond, use_cond);
+}
+
+// ---------------------------------------------------------------------------
+// Column pass
+// ---------------------------------------------------------------------------
+template <typename T, int L>
+__global__ void __launch_bounds__(Cfg<T, L>::NT_COL)
+col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* __restrict__ ktab,
+         cudaGraphConditionalHandle cond, int use_cond) {
+  using C = Cfg<T, L>;
+  constexpr int W = C::W, NT = C::NT_COL, M = C::M, NB = 3 * W, NBK = M / W;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C2<T>* sp = reinterpret_cast<C2<T>*>(smraw);  // element (c, w) of row x2 at sp[x2*NB + c*W + w]
+  const int tid = threadIdx.x;
+  // The row pass that follows re-arms the loop; a body that never reaches
+  // it must not loop again.
+  if (use_cond && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) cudaGraphSetConditional(cond, 0u);
+  Solve& S = solves[blockIdx.y];
+  if (S.phase != PH_ITER) return;
+  const int b = blockIdx.x;
+  C2<T>* spec = reinterpret_cast<C2<T>*>(S.spec);
+  for (int e = tid; e < 3 * L * W; e += NT) {
+    const int c = e / (L * W);
+    const int rem = e - c * (L * W);
+    const int x2 = rem / W, w = rem - x2 * W;
+    sp[x2 * NB + c * W + w] = spec[(size_t)(c * NBK + b) * L * W + rem];
+  }
+  __syncthreads();
+  fft_block<T, L, 3, W, NT, false>(sp, tw, 1);
+
+  const T lam0 = T(S.lam0), mu0 = T(S.mu0);
+  const T scale = T(1.0 / ((double)L * (double)L));
+  // frequencies with m1 = b*W + w != 0
+  for (int f = tid; f < W * L; f += NT) {
+    const int m2 = f / W, w = f - m2 * W;
+    const int m1 = b * W + w;
+    if (m1 == 0) continue;
+    C2<T>* q = sp + m2 * NB + w;
+    C2<T> p11 = q[0], p22 = q[W], p12 = q[2 * W];
+    green_apply(ktab[m1], ktab[m2], lam0, mu0, scale, p11, p22, p12);
+    q[0] = p11;
+    q[W] = p22;
+    q[2 * W] = p12;
+  }
+  if (b == 0) {
+    // packed column: Z = A + i B with A the m1 = 0 column and B the
+    // m1 = L/2 column, both transforms of real sequences (Hermitian)
+    const double* Ep = S.path + 4 * S.inc;
+    for (int m2 = tid; m2 <= L / 2; m2 += NT) {
+      const int mp = (L - m2) & (L - 1);
+      C2<T> A[3], B[3], Ap[3], Bp[3];
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const C2<T> z = sp[m2 * NB + c * W], zp = sp[mp * NB + c * W];
+        A[c] = T(0.5) * (z + conj(zp));
+        const C2<T> d = z - conj(zp);  // B = d / (2i)
+        B[c] = mk(T(0.5) * d.im, T(-0.5) * d.re);
+        Ap[c] = conj(A[c]);
+        Bp[c] = conj(B[c]);
+      }
+      if (m2 == 0) {
+        A[0] = mk(T(Ep[0]), T(0));
+        A[1] = mk(T(Ep[1]), T(0));
+        A[2] = mk(T(Ep[3]), T(0));
+      } else {
+        green_apply(ktab[0], ktab[m2], lam0, mu0, scale, A[0], A[1], A[2]);
+        green_apply(ktab[0], ktab[mp], lam0, mu0, scale, Ap[0], Ap[1], Ap[2]);
+      }
+      green_apply(ktab[M], ktab[m2], lam0, mu0, scale, B[0], B[1], B[2]);
+      green_apply(ktab[M], ktab[mp], lam0, mu0, scale, Bp[0], Bp[1], Bp[2]);
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        sp[m2 * NB + c * W] = A[c] + mul_i(B[c]);
+        if (mp != m2) sp[mp * NB + c * W] = Ap[c] + mul_i(Bp[c]);
+      }
+    }
+  }
+  __syncthreads();
+  fft_block<T, L, 3, W, NT, true>(sp, tw, 1);
+  for (int e = tid; e < 3 * L * W; e += NT) {
+    const int c = e / (L * W);
+    const int rem = e - c * (L * W);
+    const int x2 = rem / W, w = rem - x2 * W;
+    spec[(size_t)(c * NBK + b) * L * W + rem] = sp[x2 * NB + c * W + w];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Row transforms alone (compatible-strain projection of a given field)
+// ---------------------------------------------------------------------------
+template <typename T, int L>
+__global__ void __launch_bounds__(Cfg<T, L>::NT_ROW)
+row_forward(const T* __restrict__ p, C2<T>* __restrict__ spec, const C2<T>* __restrict__ tw) {
+  using C = Cfg<T, L>;
+  constexpr int RR = C::RR, W = C::W, NT = C::NT_ROW, P = L >= NT ? L / NT : 1;
+  using IO = RowIO<T, L, RR, W, NT>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C2<T>* sp = reinterpret_cast<C2<T>*>(smraw);
+  const int r0 = blockIdx.x * RR;
+  const size_t LL = (size_t)L * L;
+  for (int r = 0; r < RR; r++)
+    for (int j = 0; j < P; j++) {
+      const int x1 = threadIdx.x + j * NT;
+      if (x1 >= L) continue;
+      const size_t x = (size_t)(r0 + r) * L + x1;
+      for (int c = 0; c < 3; c++) IO::px(sp, c, r, x1) = p[c * LL + x];
+    }
+  __syncthreads();
+  IO::template fft<false>(sp, tw);
+  IO::r2c_twist(sp, tw);
+  __syncthreads();
+  IO::store(sp, spec, r0);
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(Cfg<T, L>::NT_ROW)
+row_inverse(const C2<T>* __restrict__ spec, T* __restrict__ e, const C2<T>* __restrict__ tw) {
+  using C = Cfg<T, L>;
+  constexpr int RR = C::RR, W = C::W, NT = C::NT_ROW, P = L >= NT ? L / NT : 1;
+  using IO = RowIO<T, L, RR, W, NT>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C2<T>* sp = reinterpret_cast<C2<T>*>(smraw);
+  const int r0 = blockIdx.x * RR;
+  const size_t LL = (size_t)L * L;
+  IO::load(sp, spec, r0);
+  __syncthreads();
+  IO::c2r_twist(sp, tw);
+  __syncthreads();
+  IO::template fft<true>(sp, tw);
+  for (int r = 0; r < RR; r++)
+    for (int j = 0; j < P; j++) {
+      const int x1 = threadIdx.x + j * NT;
+      if (x1 >= L) continue;
+      const size_t x = (size_t)(r0 + r) * L + x1;
+      for (int c = 0; c < 3; c++) e[c * LL + x] = IO::px(sp, c, r, x1);
+    }
+}
+
+}  // namespace epfft

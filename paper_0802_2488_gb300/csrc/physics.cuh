@@ -1,0 +1,147 @@
+// Pixelwise constitutive law, local step of the augmented Lagrangian and the
+// per-frequency discrete Green operator (Willot & Pellegrini, Sec. 2, Eqs. 2-3).
+#pragma once
+#include "common.cuh"
+
+namespace epfft {
+
+// Material constants of one solve in the working precision, with the
+// derived quantities the hot loop needs.
+template <typename T>
+struct Mat {
+  T K, two_mu;      // matrix bulk modulus lambda + 2 mu / 3, 2 mu
+  T lam0, two_mu0;  // reference medium C0
+  T ylim, ylim2;    // sqrt(2/3) Y and its square (Mises cap on 2 mu |dev eps|)
+  T inv_3KK0;       // 1 / (3 (K + K0))
+  T inv_3K0;        // 1 / (3 K0)
+  T inv_2mumu0;     // 1 / (2 (mu + mu0))
+  T inv_2mu0;       // 1 / (2 mu0)
+  T trial2;         // (mu / (mu + mu0))^2: |dev| of the elastic trial vs |tau'|
+};
+
+template <typename T>
+__device__ __forceinline__ Mat<T> make_mat(const Solve& S) {
+  // Derived constants are formed in FP64 and rounded once to T.
+  const double K = S.lam + 2.0 * S.mu / 3.0, K0 = S.lam0 + 2.0 * S.mu0 / 3.0;
+  const double yl = sqrt(2.0 / 3.0) * S.Y;
+  Mat<T> m;
+  m.K = T(K);
+  m.two_mu = T(2.0 * S.mu);
+  m.lam0 = T(S.lam0);
+  m.two_mu0 = T(2.0 * S.mu0);
+  m.ylim = T(yl);
+  m.ylim2 = T(yl * yl);
+  m.inv_3KK0 = T(1.0 / (3.0 * (K + K0)));
+  m.inv_3K0 = T(1.0 / (3.0 * K0));
+  m.inv_2mumu0 = T(1.0 / (2.0 * (S.mu + S.mu0)));
+  m.inv_2mu0 = T(1.0 / (2.0 * S.mu0));
+  const double r = S.mu / (S.mu + S.mu0);
+  m.trial2 = T(r * r);
+  return m;
+}
+
+// sigma(eps): void -> 0; matrix -> K tr(eps) I + g dev(eps) with g = 2 mu on
+// the elastic branch and g = sqrt(2/3) Y / |dev| once 2 mu |dev| exceeds
+// sqrt(2/3) Y (Mises stress capped at Y, deformation theory).  The deviator
+// is the 3D one (with eps33).  Returns true on the plastic branch.
+template <typename T>
+__device__ __forceinline__ bool sigma(const T e[4], bool is_void, const Mat<T>& m, T s[4]) {
+  if (is_void) {
+    s[0] = s[1] = s[2] = s[3] = T(0);
+    return false;
+  }
+  const T tr = e[0] + e[1] + e[2];
+  const T mth = tr * T(1.0 / 3.0);
+  const T d0 = e[0] - mth, d1 = e[1] - mth, d2 = e[2] - mth, d3 = e[3];
+  const T nd2 = d0 * d0 + d1 * d1 + d2 * d2 + T(2) * d3 * d3;
+  const bool pl = m.two_mu * m.two_mu * nd2 > m.ylim2;
+  const T g = pl ? m.ylim * rsqrt(nd2) : m.two_mu;
+  const T p = m.K * tr;
+  s[0] = p + g * d0;
+  s[1] = p + g * d1;
+  s[2] = p + g * d2;
+  s[3] = g * d3;
+  return pl;
+}
+
+// Plastic-branch test of sigma alone (for the per-increment plastic flags).
+template <typename T>
+__device__ __forceinline__ bool is_plastic(const T e[4], bool is_void, const Mat<T>& m) {
+  if (is_void) return false;
+  const T tr = e[0] + e[1] + e[2];
+  const T mth = tr * T(1.0 / 3.0);
+  const T d0 = e[0] - mth, d1 = e[1] - mth, d2 = e[2] - mth, d3 = e[3];
+  const T nd2 = d0 * d0 + d1 * d1 + d2 * d2 + T(2) * d3 * d3;
+  return m.two_mu * m.two_mu * nd2 > m.ylim2;
+}
+
+// C0:a, the isotropic reference stiffness (lambda0, mu0).
+template <typename T>
+__device__ __forceinline__ void c0_apply(const T a[4], const Mat<T>& m, T out[4]) {
+  const T l = m.lam0 * (a[0] + a[1] + a[2]);
+  out[0] = l + m.two_mu0 * a[0];
+  out[1] = l + m.two_mu0 * a[1];
+  out[2] = l + m.two_mu0 * a[2];
+  out[3] = m.two_mu0 * a[3];
+}
+
+// Local step of the augmented Lagrangian: eps solving
+//   sigma(eps) + C0:eps = tau,
+// split into its mean part (3 (K + K0) eps_m = tau_m, voids 3 K0 eps_m = tau_m)
+// and a deviator parallel to tau' = tau - tau_m I:
+//   elastic  dev = tau' / (2 (mu + mu0)),
+//   plastic  dev = tau' (1 - sqrt(2/3) Y / |tau'|) / (2 mu0),
+//   void     dev = tau' / (2 mu0).
+// The elastic branch holds while 2 mu |dev| <= sqrt(2/3) Y, i.e.
+// (mu / (mu + mu0))^2 |tau'|^2 <= 2/3 Y^2.  Returns true on the plastic branch.
+template <typename T>
+__device__ __forceinline__ bool local_solve(const T t[4], bool is_void, const Mat<T>& m, T e[4]) {
+  const T tm = (t[0] + t[1] + t[2]) * T(1.0 / 3.0);
+  const T d0 = t[0] - tm, d1 = t[1] - tm, d2 = t[2] - tm, d3 = t[3];
+  T em, sc;
+  bool pl = false;
+  if (is_void) {
+    em = tm * m.inv_3K0;
+    sc = m.inv_2mu0;
+  } else {
+    em = tm * m.inv_3KK0;
+    const T nt2 = d0 * d0 + d1 * d1 + d2 * d2 + T(2) * d3 * d3;
+    pl = m.trial2 * nt2 > m.ylim2;
+    sc = pl ? (T(1) - m.ylim * rsqrt(nt2)) * m.inv_2mu0 : m.inv_2mumu0;
+  }
+  e[0] = d0 * sc + em;
+  e[1] = d1 * sc + em;
+  e[2] = d2 * sc + em;
+  e[3] = d3 * sc;
+  return pl;
+}
+
+// Discrete Green operator of Eq. 3 applied at one frequency q != 0 to the
+// polarization spectrum (p11, p22, p12), in place, times `scale`.
+// With the acoustic tensor N_ab = k*_c C0_acdb k_d (Hermitian 2x2),
+// w_a = k*_b p_ab and v = N^{-1} w, Eq. 3 contracts to
+//   e_ab = -(k_a v_b + k_b v_a) / 2.
+// For the isotropic C0, N11 = (lam0+mu0)|k1|^2 + mu0|k|^2,
+// N22 = (lam0+mu0)|k2|^2 + mu0|k|^2, N12 = lam0 k1* k2 + mu0 k1 k2*, and
+// det N = mu0 (lam0 + 2 mu0) |k|^4 + 4 lam0 mu0 (Im k1* k2)^2 (a sum of
+// non-negative terms, evaluated without cancellation).
+template <typename T>
+__device__ __forceinline__ void green_apply(C2<T> k1, C2<T> k2, T lam0, T mu0, T scale,
+                                            C2<T>& p11, C2<T>& p22, C2<T>& p12) {
+  const T a1 = norm2(k1), a2 = norm2(k2), K2 = a1 + a2;
+  const T lm = lam0 + mu0;
+  const T N11 = lm * a1 + mu0 * K2, N22 = lm * a2 + mu0 * K2;
+  const C2<T> c = conj(k1) * k2;
+  const C2<T> N12 = mk(lm * c.re, (lam0 - mu0) * c.im);
+  const T det = mu0 * (lam0 + T(2) * mu0) * K2 * K2 + T(4) * lam0 * mu0 * c.im * c.im;
+  const T idet = scale / det;
+  const C2<T> w1 = conj(k1) * p11 + conj(k2) * p12;
+  const C2<T> w2 = conj(k1) * p12 + conj(k2) * p22;
+  const C2<T> v1 = idet * (N22 * w1 - N12 * w2);
+  const C2<T> v2 = idet * (N11 * w2 - conj(N12) * w1);
+  p11 = T(-1) * (k1 * v1);
+  p22 = T(-1) * (k2 * v2);
+  p12 = T(-0.5) * (k1 * v2 + k2 * v1);
+}
+
+}  // namespace epfft

@@ -1,0 +1,54 @@
+"""The C ABI library loads and exports every entry point include/epfft.h
+declares; its host-only calls work without a GPU (no compute is launched)."""
+import os
+import re
+
+import pytest
+
+from paper_0802_2488_gb300 import binding as B
+from paper_0802_2488_gb300 import build as build_mod
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "epfft.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(epfft_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_mod.build()
+    return B.lib()
+
+
+def test_every_declared_entry_point_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 11
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(B.SYMBOLS) == names
+
+
+def test_binding_keeps_the_c_names():
+    for n in declared_symbols():
+        assert callable(getattr(B, n)), n
+
+
+def test_host_only_calls(lib):
+    assert B.strerror(B.EPFFT_OK) == "ok"
+    assert "argument" in B.strerror(B.EPFFT_ERR_ARG)
+    assert B.epfft_supported(256, "fp64") and B.epfft_supported(4096, "fp32")
+    assert not B.epfft_supported(4096, "fp64")
+    assert lib.epfft_supported(100, 1) == 0 and lib.epfft_supported(2, 1) == 0
+
+
+def test_no_cpu_fallback_without_device(lib):
+    import ctypes as C
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = C.c_void_p()
+    rc = lib.epfft_create(C.byref(h), None)
+    assert rc == B.EPFFT_ERR_CUDA and not h.value

@@ -1,0 +1,241 @@
+"""CUDA path (through the C ABI) against the oracle on the same seeded inputs.
+
+Tolerances.  FP64: every kernel does the oracle's arithmetic in a different
+order (radix-8 Stockham vs radix-2 FFT, restructured Green contraction), so
+fields agree to a few hundred ulps after an iteration: relative L2 <= 1e-12
+per iteration step and <= 1e-10 for converged solves (the stated bar).
+FP32: rounding u = 6e-8, an FFT of length N loses ~u log2(N) relative to the
+field norm, one iteration chains 4 transforms and the pixelwise update, so a
+few iterations stay within ~1e-5 relative L2; the bound used is stated per
+test.  Integer results (masks, labels, cluster counts) are bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_0802_2488_gb300 import binding as B
+from paper_0802_2488_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_0802_2488_gb300 import build
+    build.build()
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+TDT = {"fp64": torch.float64, "fp32": torch.float32}
+
+
+# --------------------------------------------------------------------------
+# S1: void mask, bit-exact
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("L,f,seed", [(4, 0.5, 0), (64, 0.10, 0), (256, 0.20, 0), (512, 0.3, 15),
+                                      (128, 0.0, 7), (128, 1.0, 7), (4096, 0.35, 0)])
+def test_mask_bitexact(L, f, seed):
+    m = B.epfft_mask(L, f, seed).cpu().numpy()
+    np.testing.assert_array_equal(m, O.mask(L, f, seed))
+
+
+# --------------------------------------------------------------------------
+# S3-S4 (+ row inverse): compatible strain of a polarization, Eqs. 2-3
+# --------------------------------------------------------------------------
+def oracle_project(L, lam0, mu0, E, p):
+    ph = np.stack([O.fft2(p[c], -1) for c in range(3)])
+    eh = O.green_apply(L, lam0, mu0, E, ph)
+    return np.stack([O.fft2(eh[c], +1).real / (L * L) for c in range(3)])
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 3e-6)])
+@pytest.mark.parametrize("L", [4, 8, 16, 32, 64, 128, 256, 512])
+def test_project_parity(ctx, L, prec, tol):
+    rng = np.random.default_rng(L)
+    p = rng.standard_normal((3, L, L))
+    E = np.array([0.3, -0.2, 0.0, 0.15])
+    ref = oracle_project(L, 1.5, 1.0, E, p)
+    pt = torch.tensor(p, dtype=TDT[prec], device="cuda")
+    e = B.epfft_project(ctx, L, prec, 1.5, 1.0, E, pt).cpu().numpy()
+    assert rel(e, ref) < tol, rel(e, ref)
+    # mean strain is the prescribed one
+    np.testing.assert_allclose(e.reshape(3, -1).mean(1), E[[0, 1, 3]], atol=50 * tol)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 3e-6)])
+@pytest.mark.parametrize("L", [1024, 2048])
+def test_project_parity_large(ctx, L, prec, tol):
+    if not B.epfft_supported(L, prec):
+        pytest.skip("not built")
+    rng = np.random.default_rng(L)
+    p = rng.standard_normal((3, L, L))
+    E = np.array([0.1, 0.2, 0.0, -0.3])
+    ref = oracle_project(L, 1.5, 1.0, E, p)
+    e = B.epfft_project(ctx, L, prec, 1.5, 1.0, E, torch.tensor(p, dtype=TDT[prec], device="cuda")).cpu().numpy()
+    assert rel(e, ref) < tol, rel(e, ref)
+
+
+# --------------------------------------------------------------------------
+# S3-S6: iterate parity (same number of iterations from the same state)
+# --------------------------------------------------------------------------
+def oracle_iterate(mask, mat, E, eps, k):
+    lam = None
+    for _ in range(k):
+        eps, lam, e, _ = O.al_step(mask, mat, E, eps, lam)
+    return eps
+
+
+def ratio_stats(mask, mat, eps, eps_prev):
+    st = O.stats(mask, mat, eps)
+    sp = O.stats(mask, mat, eps_prev)
+    s = st.sig_mean
+    ss = s[0] ** 2 + s[1] ** 2 + 2 * s[3] ** 2
+    d = s - sp.sig_mean
+    return st, np.sqrt(st.div2_mean / ss), np.sqrt((d[0] ** 2 + d[1] ** 2 + 2 * d[3] ** 2) / ss)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("L,f,k", [(4, 0.25, 1), (8, 0.2, 3), (32, 0.15, 5), (64, 0.10, 4), (128, 0.3, 2)])
+def test_iterate_parity(ctx, L, f, k, prec, tol):
+    mask = O.mask(L, f, 5)
+    mat = O.material()
+    E = np.array([0.45, 0.35, 0.0, 0.2])
+    eps0 = inputs.random_strain(L, E, 0.3, seed=L + k)
+    ref = oracle_iterate(mask, mat, E, eps0.copy(), k)
+    ref_prev = oracle_iterate(mask, mat, E, eps0.copy(), k - 1) if k > 1 else eps0
+    prob = B.Problem(L=L, precision=prec, mask=mask)
+    t = torch.tensor(eps0, dtype=TDT[prec], device="cuda").contiguous()
+    rec = B.epfft_iterate(ctx, prob, E, t, k)
+    got = t.cpu().numpy()
+    assert rel(got, ref) < tol, rel(got, ref)
+    st, eta1, eta2 = ratio_stats(mask, mat, ref, ref_prev)
+    assert rec["iterations"] == k
+    np.testing.assert_allclose(rec["sig_mean"], st.sig_mean, rtol=10 * tol, atol=10 * tol)
+    np.testing.assert_allclose(rec["eta1"], eta1, rtol=1e-9 if prec == "fp64" else 1e-2)
+    if prec == "fp64":
+        np.testing.assert_allclose(rec["eta2"], eta2, rtol=1e-6, atol=1e-14)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_iterate_parity_config2_size(ctx, prec, tol):
+    """L = 256, f = 0.20 (the shear workload's lattice), 3 iterations from a
+    perturbed state, in the launch shape the benchmark uses."""
+    L = 256
+    mask = O.mask(L, 0.20, 0)
+    mat = O.material()
+    E = inputs.load_path("shear", 40, 3.0)[20]
+    eps0 = inputs.random_strain(L, E, 0.05, seed=1)
+    ref = oracle_iterate(mask, mat, E, eps0.copy(), 3)
+    t = torch.tensor(eps0, dtype=TDT[prec], device="cuda").contiguous()
+    B.epfft_iterate(ctx, B.Problem(L=L, precision=prec, void_fraction=0.20, seed=0), E, t, 3)
+    assert rel(t.cpu().numpy(), ref) < tol
+
+
+# --------------------------------------------------------------------------
+# S2-S7: loading by increments
+# --------------------------------------------------------------------------
+def test_solve_parity_small(ctx):
+    L = 16
+    path = inputs.load_path("equibiaxial", 4, 1.5)
+    mask = O.mask(L, 0.1, 3)
+    ref = O.solve(mask, O.material(), path, tol_eq=1e-8, tol_macro=1e-8, max_iter=4000, fields=True)
+    prob = B.Problem(L=L, precision="fp64", void_fraction=0.1, seed=3, max_iter=4000)
+    rc, rec, f = B.epfft_solve(ctx, prob, path, fields=True)
+    assert rc == (B.EPFFT_OK if ref.status == 0 else B.EPFFT_NOT_CONVERGED)
+    np.testing.assert_array_equal(rec["iterations"], ref.records["iterations"])
+    np.testing.assert_array_equal(rec["status"], ref.records["status"])
+    assert rel(rec["sig_mean"], ref.records["sig_mean"]) < 1e-10
+    assert rel(rec["eps_mean"], ref.records["eps_mean"]) < 1e-12
+    assert rel(f.eps, ref.eps) < 1e-10
+    np.testing.assert_array_equal(f.plastic, ref.plastic)
+    np.testing.assert_array_equal(rec["n_plastic"], ref.records["n_plastic"])
+    np.testing.assert_array_equal(f.labels, ref.labels)
+    np.testing.assert_array_equal(rec["n_clusters"], ref.records["n_clusters"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_homogeneous_closed_form(ctx, prec):
+    """f = 0: one iteration per increment, uniform fields, yield at the
+    Mises limit (values of tests/golden/homogeneous.json)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "homogeneous.json")))["baseline"]
+    L = 16
+    tol = 1e-13 if prec == "fp64" else 1e-6
+    for mode in ("equibiaxial", "shear"):
+        path = np.array([c["E"] for c in g[mode]])
+        prob = B.Problem(L=L, precision=prec, void_fraction=0.0, tol_eq=1e-6, tol_macro=1e-6, max_iter=5)
+        rc, rec, f = B.epfft_solve(ctx, prob, path, fields=True)
+        assert rc == B.EPFFT_OK
+        assert (rec["iterations"] == 1).all()
+        for k, c in enumerate(g[mode]):
+            np.testing.assert_allclose(rec["sig_mean"][k], c["sigma"], rtol=tol, atol=tol)
+            assert rec["n_plastic"][k] == (L * L if c["plastic"] else 0)
+            assert rec["n_clusters"][k] == (1 if c["plastic"] else 0)
+
+
+def test_all_void_and_elastic_edge_cases(ctx):
+    L = 8
+    rc, rec = B.epfft_solve(ctx, B.Problem(L=L, void_fraction=1.0, max_iter=10), np.array([[0.1, 0.1, 0, 0]]))
+    assert rc == B.EPFFT_OK and rec["iterations"][0] == 1 and np.all(rec["sig_mean"][0] == 0)
+    # purely elastic porous lattice: the solve is linear in E
+    m = O.mask(32, 0.2, 1)
+    P = np.array([[0.1, -0.05, 0.0, 0.02]])
+    prob = B.Problem(L=32, mask=m, yield_stress=np.inf, tol_eq=1e-10, tol_macro=1e-10, max_iter=20000)
+    _, r1 = B.epfft_solve(ctx, prob, P)
+    _, r3 = B.epfft_solve(ctx, prob, 3 * P)
+    ref = O.solve(m, O.material(Y=np.inf), P, tol_eq=1e-10, tol_macro=1e-10, max_iter=20000)
+    assert r1["iterations"][0] == ref.records["iterations"][0]
+    assert rel(r1["sig_mean"], ref.records["sig_mean"]) < 1e-10
+    assert rel(r3["sig_mean"], 3 * r1["sig_mean"]) < 1e-9
+
+
+def test_invalid_arguments_are_rejected(ctx):
+    for bad in (dict(L=12), dict(L=2), dict(mu=-1.0), dict(max_iter=0), dict(void_fraction=1.5),
+                dict(tol_eq=-1.0), dict(L=4096, precision="fp64")):
+        kw = dict(L=16, void_fraction=0.1)
+        kw.update(bad)
+        with pytest.raises(B.EpfftError):
+            B.epfft_solve(ctx, B.Problem(**kw), np.array([[0.1, 0.1, 0, 0]]))
+
+
+# --------------------------------------------------------------------------
+# S7: cluster labels, bit-exact against the oracle on identical flags
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("L,p", [(4, 0.5), (16, 0.4), (64, 0.55), (512, 0.59), (1024, 0.3)])
+def test_labels_bitexact(ctx, L, p):
+    rng = np.random.default_rng(L)
+    flags = (rng.random((3, L, L)) < p).astype(np.uint8)
+    lab, counts = B.epfft_label(ctx, torch.tensor(flags, device="cuda"))
+    lab = lab.cpu().numpy()
+    for i in range(3):
+        ref, n = O.label(flags[i], True)
+        np.testing.assert_array_equal(lab[i], ref)
+        assert counts[i] == n
+
+
+# --------------------------------------------------------------------------
+# S8: a batch gives the same results as the solves alone
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_equals_single(ctx, prec):
+    L = 32
+    probs = [B.Problem(L=L, precision=prec, void_fraction=f, seed=s, max_iter=m)
+             for f, s, m in ((0.05, 1, 300), (0.2, 2, 500), (0.1, 3, 200))]
+    paths = [inputs.load_path("equibiaxial", 3, 2.0), inputs.load_path("shear", 5, 3.0),
+             inputs.load_path("equibiaxial", 2, 1.0)]
+    rc, recs, fs = B.epfft_solve_batch(ctx, probs, paths, fields=True)
+    for i in range(3):
+        _, r1, f1 = B.epfft_solve(ctx, probs[i], paths[i], fields=True)
+        assert r1.tobytes() == recs[i].tobytes()
+        assert np.array_equal(f1.eps, fs[i].eps)
+        assert np.array_equal(f1.labels, fs[i].labels)
