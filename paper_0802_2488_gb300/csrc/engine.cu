@@ -3,6 +3,8 @@
 // one column pass and one row pass until every solve is done), cluster
 // labelling and copy-out.
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <utility>
@@ -313,6 +315,41 @@ int run_graph(epfft_ctx* c, Batch& B) {
   return rc;
 }
 
+// Diagnostic loop (EPFFT_SYNC_CHECK=1 in the environment): the same passes
+// launched from the host one by one, each followed by a synchronisation
+// and an error check that names the pass, phase and step that failed.
+int run_checked(epfft_ctx* c, Batch& B) {
+  BatchCtl bc;
+  std::vector<Solve> hs(B.nb);
+  for (int64_t step = 0;; step++) {
+    CK(cudaMemcpy(hs.data(), B.d_solves, sizeof(Solve) * B.nb, cudaMemcpyDeviceToHost));
+    cudaError_t e;
+    if (B.prec == EPFFT_FP32) e = launch_col<float>(B.L, B.nb, c->stream, B.d_solves, B.tw, B.ktab, 0, 0);
+    else e = launch_col<double>(B.L, B.nb, c->stream, B.d_solves, B.tw, B.ktab, 0, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      fprintf(stderr, "epfft check: column pass failed at step %lld (phase %d inc %d iter %d): %s\n",
+              (long long)step, hs[0].phase, hs[0].inc, hs[0].iter, cudaGetErrorString(e));
+      return EPFFT_ERR_CUDA;
+    }
+    if (B.prec == EPFFT_FP32) e = launch_row<float>(B.L, B.nb, c->stream, B.d_solves, B.d_ctl, B.tw, 0, 0);
+    else e = launch_row<double>(B.L, B.nb, c->stream, B.d_solves, B.d_ctl, B.tw, 0, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      fprintf(stderr, "epfft check: row pass failed at step %lld (phase %d inc %d iter %d): %s\n",
+              (long long)step, hs[0].phase, hs[0].inc, hs[0].iter, cudaGetErrorString(e));
+      return EPFFT_ERR_CUDA;
+    }
+    CK(cudaMemcpy(&bc, B.d_ctl, sizeof(bc), cudaMemcpyDeviceToHost));
+    if (bc.active == 0) return EPFFT_OK;
+    if (bc.body_iters >= bc.max_body_iters) {
+      bc.timed_out = 1;
+      CK(cudaMemcpy(B.d_ctl, &bc, sizeof(bc), cudaMemcpyHostToDevice));
+      return EPFFT_OK;
+    }
+  }
+}
+
 // Labels the per-increment plastic flags of every solve; fills n_clusters.
 int label_batch(epfft_ctx* c, Arena& A, Batch& B, std::vector<std::vector<Record>>& recs, bool keep_labels) {
   const size_t LL = (size_t)B.L * B.L;
@@ -337,6 +374,13 @@ int label_batch(epfft_ctx* c, Arena& A, Batch& B, std::vector<std::vector<Record
     int32_t* counts = (int32_t*)A.get(sizeof(int32_t) * n);
     if (!lab || !counts) return EPFFT_ERR_OOM;
     CK(launch_label(B.h_solves[i].flags, lab, (int64_t)n, B.L, 1, counts, err, c->stream));
+    if (getenv("EPFFT_SYNC_CHECK")) {
+      cudaError_t e = cudaStreamSynchronize(c->stream);
+      if (e != cudaSuccess) {
+        fprintf(stderr, "epfft check: labelling failed for solve %d: %s\n", i, cudaGetErrorString(e));
+        return EPFFT_ERR_CUDA;
+      }
+    }
     std::vector<int32_t> hc(n);
     CK(cudaMemcpyAsync(hc.data(), counts, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -377,7 +421,8 @@ int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_
   Batch B;
   int rc = setup_batch(c, A, B, n, probs, paths, eps0);
   if (rc) return rc;
-  rc = run_graph(c, B);
+  const char* chk = getenv("EPFFT_SYNC_CHECK");
+  rc = (chk && chk[0] == '1') ? run_checked(c, B) : run_graph(c, B);
   if (rc) return rc;
   // read back the solve states and records
   CK(cudaMemcpyAsync(B.h_solves.data(), B.d_solves, sizeof(Solve) * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
