@@ -228,7 +228,7 @@ def main():
                 b.record(stream)
             ev.append((a, b))
             pix_its += P.L * P.L * int(rec["iterations"].sum())
-            launches += B.epfft_last_launches(ctx)
+            launches += B.epfft_last_stats(ctx)["kernel_launches"]
         barrier()
         wall = time.perf_counter() - t0
     dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3

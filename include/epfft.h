@@ -142,6 +142,20 @@ const char *epfft_strerror(int code);
 /* 1 if the library was built for lattice side L in `precision`, else 0. */
 int epfft_supported(int32_t L, int32_t precision);
 
+/* Accounting of the last solve-type call on a context (epfft_solve,
+ * epfft_solve_batch, epfft_iterate). */
+typedef struct {
+  int64_t loop_steps;       /* steps of the device-side loop (one column and one *
+                             * row pass each)                                     */
+  int64_t kernel_launches;  /* kernels the call launched on the device           */
+  int64_t iterations;       /* augmented-Lagrangian iterations executed, all      *
+                             * solves, including the one per increment that only  *
+                             * served to evaluate the accepted iterate            */
+} epfft_stats;
+
+/* Fills *out for the last solve-type call (zeros before the first). */
+int epfft_last_stats(const epfft_ctx *ctx, epfft_stats *out);
+
 /* ---------------------------------------------------------------------- */
 /* Solves (Sec. 2: strain-controlled loading by increments)                */
 /* ---------------------------------------------------------------------- */

@@ -32,8 +32,8 @@ EPFFT_FP64 = 0
 EPFFT_FP32 = 1
 EPFFT_GREEN_EQ3 = 0
 
-SYMBOLS = ["epfft_create", "epfft_destroy", "epfft_strerror", "epfft_supported", "epfft_solve",
-           "epfft_solve_batch", "epfft_mask", "epfft_iterate", "epfft_project", "epfft_label",
+SYMBOLS = ["epfft_create", "epfft_destroy", "epfft_last_stats", "epfft_strerror", "epfft_supported",
+           "epfft_solve", "epfft_solve_batch", "epfft_mask", "epfft_iterate", "epfft_project", "epfft_label",
            "epfft_time_passes"]
 
 
@@ -65,6 +65,10 @@ class _Path(C.Structure):
     _fields_ = [("n_inc", C.c_int32), ("reserved", C.c_int32), ("E", C.c_void_p)]
 
 
+class _Stats(C.Structure):
+    _fields_ = [("loop_steps", C.c_int64), ("kernel_launches", C.c_int64), ("iterations", C.c_int64)]
+
+
 class _Fields(C.Structure):
     _fields_ = [("eps", C.c_void_p), ("plastic", C.c_void_p), ("labels", C.c_void_p),
                 ("on_device", C.c_int32), ("reserved", C.c_int32)]
@@ -92,6 +96,7 @@ def lib():
         L.epfft_strerror.argtypes = [C.c_int]
         L.epfft_strerror.restype = C.c_char_p
         L.epfft_supported.argtypes = [i32, i32]
+        L.epfft_last_stats.argtypes = [vp, C.POINTER(_Stats)]
         L.epfft_solve.argtypes = [vp, C.POINTER(_Problem), C.POINTER(_Path), vp, C.POINTER(_Fields)]
         L.epfft_solve_batch.argtypes = [vp, i32, C.POINTER(_Problem), C.POINTER(_Path), C.POINTER(vp),
                                         C.POINTER(_Fields)]
@@ -174,9 +179,10 @@ def _path(E) -> tuple[_Path, np.ndarray]:
 
 class Context:
     """epfft_ctx on one CUDA device, allocating through torch's caching
-    allocator on its own non-blocking stream."""
+    allocator; it works on `stream` (a cudaStream_t as int, e.g.
+    torch.cuda.Stream().cuda_stream) or on a stream of its own."""
 
-    def __init__(self, device: int = 0, torch_allocator: bool = True):
+    def __init__(self, device: int = 0, torch_allocator: bool = True, stream: Optional[int] = None):
         import torch
         self.device = device
         self._torch = torch
@@ -193,10 +199,10 @@ class Context:
                 torch.cuda.caching_allocator_delete(ptr)
 
             self._cbs = (AllocFn(_alloc), FreeFn(_free))
-            opts = _Options(device, 0, None, self._cbs[0], self._cbs[1], None)
+            opts = _Options(device, 0, stream, self._cbs[0], self._cbs[1], None)
         else:
             self._cbs = None
-            opts = _Options(device, 0, None, AllocFn(), FreeFn(), None)
+            opts = _Options(device, 0, stream, AllocFn(), FreeFn(), None)
         _check(lib().epfft_create(C.byref(self.handle), C.byref(opts)), "epfft_create")
 
     def close(self):
@@ -223,6 +229,13 @@ def epfft_create(device: int = 0) -> Context:
 
 def epfft_destroy(ctx: Context) -> None:
     ctx.close()
+
+
+def epfft_last_stats(ctx: Context) -> dict:
+    """Device-loop steps, kernel launches and iterations of the last solve-type call."""
+    st = _Stats()
+    _check(lib().epfft_last_stats(ctx.handle, C.byref(st)), "epfft_last_stats")
+    return {"loop_steps": st.loop_steps, "kernel_launches": st.kernel_launches, "iterations": st.iterations}
 
 
 def epfft_strerror(code: int) -> str:

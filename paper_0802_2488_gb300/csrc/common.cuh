@@ -108,4 +108,26 @@ struct BatchCtl {
   int32_t pad;
 };
 
+// First failed self-check of a build with EPFFT_CHECKS (debug builds only):
+// the access is skipped and its code, index and bound are recorded.
+struct CheckRec {
+  int32_t code, where;
+  int64_t index, bound;
+};
+
 }  // namespace epfft
+
+#ifdef EPFFT_CHECKS
+static __device__ epfft::CheckRec g_check;
+__device__ __forceinline__ bool epfft_chk(bool ok, int code, long long index, long long bound) {
+  if (!ok && atomicCAS(&g_check.code, 0, code) == 0) {
+    g_check.where = (int32_t)(blockIdx.x * 1024 + threadIdx.x);
+    g_check.index = index;
+    g_check.bound = bound;
+  }
+  return ok;
+}
+#define ECHK(idx, bound, code) epfft_chk((long long)(idx) >= 0 && (long long)(idx) < (long long)(bound), (code), (long long)(idx), (long long)(bound))
+#else
+#define ECHK(idx, bound, code) true
+#endif

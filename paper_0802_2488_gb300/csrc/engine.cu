@@ -27,6 +27,7 @@ struct epfft_ctx {
   // (L, precision) -> device table: tw[L] then ktab[L] (complex of precision)
   std::map<std::pair<int, int>, void*> tables;
   std::map<std::pair<int, int>, bool> prepared;
+  epfft_stats last{};
 };
 
 namespace {
@@ -340,6 +341,11 @@ int run_checked(epfft_ctx* c, Batch& B) {
               (long long)step, hs[0].phase, hs[0].inc, hs[0].iter, cudaGetErrorString(e));
       return EPFFT_ERR_CUDA;
     }
+    CheckRec cr;
+    CK(B.prec == EPFFT_FP32 ? read_check<float>(&cr) : read_check<double>(&cr));
+    if (cr.code)
+      fprintf(stderr, "epfft check: step %lld phase %d: self-check %d failed: index %lld bound %lld at %d\n",
+              (long long)step, hs[0].phase, cr.code, (long long)cr.index, (long long)cr.bound, cr.where);
     CK(cudaMemcpy(&bc, B.d_ctl, sizeof(bc), cudaMemcpyDeviceToHost));
     if (bc.active == 0) return EPFFT_OK;
     if (bc.body_iters >= bc.max_body_iters) {
@@ -438,6 +444,17 @@ int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_
     CK(cudaMemcpyAsync(recs[i].data(), B.h_solves[i].rec, sizeof(Record) * (size_t)B.n_inc[i],
                        cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  {
+    int64_t its = 0;
+    for (int i = 0; i < n; i++) its += B.h_solves[i].total_iters;
+    c->last.loop_steps = bc.body_iters;
+    // per step a column and a row pass; per solve the mask kernel (when
+    // generated) and the four labelling kernels
+    int64_t k = 2 * bc.body_iters;
+    for (int i = 0; i < n; i++) k += (probs[i].mask ? 0 : 1) + 4;
+    c->last.kernel_launches = k;
+    c->last.iterations = its;
+  }
   if (bc.timed_out) return EPFFT_ERR_DEVICE_TIMEOUT;
   bool keep_labels = false;
   if (fields)
@@ -542,6 +559,12 @@ const char* epfft_strerror(int code) {
 }
 
 int epfft_supported(int32_t L, int32_t precision) { return supported(L, precision) ? 1 : 0; }
+
+int epfft_last_stats(const epfft_ctx* ctx, epfft_stats* out) {
+  if (!ctx || !out) return EPFFT_ERR_ARG;
+  *out = ctx->last;
+  return EPFFT_OK;
+}
 
 int epfft_solve(epfft_ctx* ctx, const epfft_problem* problem, const epfft_path* path, epfft_record* records,
                 const epfft_fields* fields) {

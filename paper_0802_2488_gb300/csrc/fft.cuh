@@ -92,12 +92,16 @@ __device__ __forceinline__ void stockham_stage(C2<T>* s, const C2<T>* __restrict
     if (NBF % NT == 0 || g < NBF) {
       const int b = g % NB, j = g / NB;
 #pragma unroll
-      for (int r = 0; r < R; r++) v[q][r] = s[(j + r * (N / R)) * XS + b];
+      for (int r = 0; r < R; r++) {
+        const int ix = (j + r * (N / R)) * XS + b;
+        v[q][r] = ECHK(ix, N * XS, 101) ? s[ix] : v[q][r];
+      }
       if (NS > 1) {
         const int jm = j % NS;
 #pragma unroll
         for (int r = 1; r < R; r++) {
-          C2<T> w = tw[(jm * r * (N / (NS * R))) * twstride];
+          const int it = (jm * r * (N / (NS * R))) * twstride;
+          C2<T> w = ECHK(it, N * twstride, 102) ? tw[it] : mk(T(1), T(0));
           if (INV) w.im = -w.im;
           v[q][r] = v[q][r] * w;
         }
@@ -114,7 +118,10 @@ __device__ __forceinline__ void stockham_stage(C2<T>* s, const C2<T>* __restrict
       const int jm = j % NS;
       const int base = (j / NS) * NS * R + jm;
 #pragma unroll
-      for (int r = 0; r < R; r++) s[(base + r * NS) * XS + b] = v[q][r];
+      for (int r = 0; r < R; r++) {
+        const int ix = (base + r * NS) * XS + b;
+        if (ECHK(ix, N * XS, 103)) s[ix] = v[q][r];
+      }
     }
   }
   __syncthreads();

@@ -121,4 +121,17 @@ cudaError_t launch_row_inverse<EPFFT_REAL>(int L, cudaStream_t s, const void* sp
   }
 }
 
+template <>
+cudaError_t read_check<EPFFT_REAL>(CheckRec* out) {
+#ifdef EPFFT_CHECKS
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_check, sizeof(CheckRec));
+  if (e != cudaSuccess) return e;
+  CheckRec z = {};
+  return cudaMemcpyToSymbol(g_check, &z, sizeof(CheckRec));
+#else
+  *out = CheckRec{};
+  return cudaSuccess;
+#endif
+}
+
 }  // namespace epfft

@@ -28,6 +28,9 @@ cudaError_t launch_col(int L, int nb, cudaStream_t s, Solve* solves, const void*
                        cudaGraphConditionalHandle cond, int use_cond);
 template <typename T>
 cudaError_t launch_row_forward(int L, cudaStream_t s, const void* p, void* spec, const void* tw);
+// Reads and clears the self-check record (zero unless built with EPFFT_CHECKS).
+template <typename T>
+cudaError_t read_check(CheckRec* out);
 template <typename T>
 cudaError_t launch_row_inverse(int L, cudaStream_t s, const void* spec, void* e, const void* tw);
 

@@ -90,7 +90,9 @@ struct RowIO {
       const int b = rem / (RR * W);
       const int rem2 = rem - b * (RR * W);
       const int r = rem2 / W, w = rem2 - r * W;
-      sp[(b * W + w) * NB + c * RR + r] = spec[((size_t)(c * NBK + b) * L + r0 + r) * W + w];
+      const int is = (b * W + w) * NB + c * RR + r;
+      const size_t ig = ((size_t)(c * NBK + b) * L + r0 + r) * W + w;
+      if (ECHK(is, M * NB, 1) && ECHK(ig, (size_t)3 * M * L, 2)) sp[is] = spec[ig];
     }
   }
   static __device__ __forceinline__ void store(const C2<T>* sp, C2<T>* __restrict__ spec, int r0) {
@@ -100,7 +102,9 @@ struct RowIO {
       const int b = rem / (RR * W);
       const int rem2 = rem - b * (RR * W);
       const int r = rem2 / W, w = rem2 - r * W;
-      spec[((size_t)(c * NBK + b) * L + r0 + r) * W + w] = sp[(b * W + w) * NB + c * RR + r];
+      const int is = (b * W + w) * NB + c * RR + r;
+      const size_t ig = ((size_t)(c * NBK + b) * L + r0 + r) * W + w;
+      if (ECHK(is, M * NB, 3) && ECHK(ig, (size_t)3 * M * L, 4)) spec[ig] = sp[is];
     }
   }
   // Half spectrum (packed) -> Z for the half-length inverse transform:
@@ -118,6 +122,7 @@ struct RowIO {
         s[0] = mk(s0.re + s0.im, s0.re - s0.im);
       } else {
         const int kk = M - k;
+        if (!ECHK(k * NB + cr, M * NB, 5) || !ECHK(kk * NB + cr, M * NB, 6)) continue;
         const C2<T> a = s[k * NB], b = s[kk * NB];
         const C2<T> wk = conj(tw[k]);
         const C2<T> zk = (a + conj(b)) + mul_i(wk * (a - conj(b)));
@@ -139,6 +144,7 @@ struct RowIO {
         s[0] = mk(z.re + z.im, z.re - z.im);
       } else {
         const int kk = M - k;
+        if (!ECHK(k * NB + cr, M * NB, 7) || !ECHK(kk * NB + cr, M * NB, 8)) continue;
         const C2<T> a = s[k * NB], b = s[kk * NB];
         const C2<T> wk = tw[k];
         s[k * NB] = T(0.5) * ((a + conj(b)) - mul_i(wk * (a - conj(b))));
@@ -153,7 +159,8 @@ struct RowIO {
   }
   // real value of pixel x1 of component c, row r
   static __device__ __forceinline__ T& px(C2<T>* sp, int c, int r, int x1) {
-    return reinterpret_cast<T*>(sp)[2 * ((x1 >> 1) * NB + c * RR + r) + (x1 & 1)];
+    const int ix = 2 * ((x1 >> 1) * NB + c * RR + r) + (x1 & 1);
+    return reinterpret_cast<T*>(sp)[ECHK(ix, 2 * M * NB, 9) ? ix : 0];
   }
 };
 
@@ -307,11 +314,16 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
   __shared__ bool s_last;
 
   Solve& S = solves[blockIdx.y];
-  const int phase = S.phase;
+  // The mutable control fields are rewritten by the last CTA of this launch
+  // (finalize_solve); every thread reads them exactly once, through
+  // volatile loads, so no later re-load can observe the new values.
+  const volatile Solve& Sv = S;
+  const int phase = Sv.phase;
+  const int cur = Sv.cur;
+  const int inc = Sv.inc;
   const int tid = threadIdx.x;
   if (phase != PH_DONE) {
     const int r0 = blockIdx.x * RR;
-    const int cur = S.cur;
     const T* __restrict__ ein = reinterpret_cast<const T*>(S.eps[cur]);
     T* __restrict__ eout = reinterpret_cast<T*>(S.eps[1 - cur]);
     C2<T>* spec = reinterpret_cast<C2<T>*>(S.spec);
@@ -324,7 +336,7 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
 
     if (phase == PH_FINAL) {
       // plastic flags of the accepted state of the last increment
-      uint8_t* fl = S.flags ? S.flags + (size_t)(S.n_inc - 1) * LL : nullptr;
+      uint8_t* fl = S.flags ? S.flags + (size_t)(S.n_inc - 1) * LL : nullptr;  // inc == n_inc - 1
       for (int r = 0; r < RR && fl; r++)
         for (int j = 0; j < P; j++) {
           const int x1 = tid + j * NT;
@@ -337,14 +349,15 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
     } else if (phase == PH_INIT) {
       // warm start: eps^0 = accepted state + (E_inc - E_{inc-1}); p^0 -> spectrum
       T dE[4];
-      const double* E = S.path + 4 * S.inc;
-      for (int c = 0; c < 4; c++) dE[c] = T(E[c] - S.Eprev[c]);
-      uint8_t* fl = (S.flags && S.inc > 0) ? S.flags + (size_t)(S.inc - 1) * LL : nullptr;
+      const double* E = S.path + 4 * (ECHK(inc, S.n_inc, 26) ? inc : 0);
+      for (int c = 0; c < 4; c++) dE[c] = T(E[c] - Sv.Eprev[c]);
+      uint8_t* fl = (S.flags && inc > 0) ? S.flags + (size_t)(inc - 1) * LL : nullptr;
       for (int r = 0; r < RR; r++)
         for (int j = 0; j < P; j++) {
           const int x1 = tid + j * NT;
           if (x1 >= L) continue;
           const size_t x = (size_t)(r0 + r) * L + x1;
+          if (!ECHK(x, LL, 20)) continue;
           const bool v = mask[x] != 0;
           T e[4], s[4], c0[4];
           Vec4<T>::load(ein + 4 * x, e);
@@ -359,7 +372,7 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
         }
     } else {  // PH_ITER
       T E[4];
-      load_E(S.path + 4 * S.inc, E);
+      load_E(S.path + 4 * inc, E);
       IO::load(sp, spec, r0);
       __syncthreads();
       IO::c2r_twist(sp, tw);
@@ -376,6 +389,7 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
           prev12[j] = prev22[j] = T(0);
           if (x1 >= L) continue;
           const size_t x = (size_t)xh * L + x1;
+          if (!ECHK(x, LL, 22)) continue;
           T e[4], s[4];
           Vec4<T>::load(ein + 4 * x, e);
           sigma(e, mask[x] != 0, m, s);
@@ -391,6 +405,7 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
           const int x1 = tid + j * NT;
           if (x1 >= L) continue;
           const size_t x = (size_t)(r0 + r) * L + x1;
+          if (!ECHK(x, LL, 23) || !ECHK(L + x1, 2 * L, 24)) continue;
           vv[j] = mask[x] != 0;
           Vec4<T>::load(ein + 4 * x, en[j]);
           const bool pl = sigma(en[j], vv[j], m, s[j]);
@@ -448,8 +463,11 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
       double v[N_ACC];
 #pragma unroll
       for (int i = 0; i < N_ACC; i++) v[i] = (double)acc[i];
-      block_reduce<NT>(v, S.partials + (size_t)blockIdx.x * PART_STRIDE);
+      if (ECHK(blockIdx.x, L / RR, 25)) block_reduce<NT>(v, S.partials + (size_t)blockIdx.x * PART_STRIDE);
     }
+    // every thread of this CTA is done with the solve state before the CTA
+    // counts itself in
+    __syncthreads();
     if (tid == 0) {
       __threadfence();
       const unsigned prev = atomicAdd(&S.arrive, 1u);
@@ -481,7 +499,9 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
   // it must not loop again.
   if (use_cond && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) cudaGraphSetConditional(cond, 0u);
   Solve& S = solves[blockIdx.y];
-  if (S.phase != PH_ITER) return;
+  const volatile Solve& Sv = S;
+  if (Sv.phase != PH_ITER) return;
+  const int inc = Sv.inc;
   const int b = blockIdx.x;
   C2<T>* spec = reinterpret_cast<C2<T>*>(S.spec);
   for (int e = tid; e < 3 * L * W; e += NT) {
@@ -510,7 +530,7 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
   if (b == 0) {
     // packed column: Z = A + i B with A the m1 = 0 column and B the
     // m1 = L/2 column, both transforms of real sequences (Hermitian)
-    const double* Ep = S.path + 4 * S.inc;
+    const double* Ep = S.path + 4 * inc;
     for (int m2 = tid; m2 <= L / 2; m2 += NT) {
       const int mp = (L - m2) & (L - 1);
       C2<T> A[3], B[3], Ap[3], Bp[3];
