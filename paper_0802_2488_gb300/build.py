@@ -20,7 +20,9 @@ LIB = os.path.join(HERE, "libepfft.so")
 UNITS = ["inst_f32.cu", "inst_f64.cu", "engine.cu", "aux_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", f"-I{INCLUDE}"]
-if os.environ.get("EPFFT_CHECKS") == "1":  # debug build: device bounds self-checks
+# Device bounds self-checks (record the first out-of-range index and skip the
+# access) are on unless EPFFT_CHECKS=0.
+if os.environ.get("EPFFT_CHECKS", "1") != "0":
     FLAGS.append("-DEPFFT_CHECKS")
 
 

@@ -445,6 +445,15 @@ int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_
                        cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   {
+    CheckRec cr;
+    CK(B.prec == EPFFT_FP32 ? read_check<float>(&cr) : read_check<double>(&cr));
+    if (cr.code) {
+      fprintf(stderr, "epfft: device self-check %d failed (index %lld, bound %lld, at %d)\n", cr.code,
+              (long long)cr.index, (long long)cr.bound, cr.where);
+      return EPFFT_ERR_CUDA;
+    }
+  }
+  {
     int64_t its = 0;
     for (int i = 0; i < n; i++) its += B.h_solves[i].total_iters;
     c->last.loop_steps = bc.body_iters;
