@@ -196,9 +196,24 @@ __device__ __forceinline__ void block_reduce(double v[N_ACC], double* out) {
   }
 }
 
+// Sums of the per-CTA partials of a solve, computed by all threads of the
+// last CTA: thread t adds the records t, t + NT, ... in order, then a fixed
+// tree combines the threads, so the result does not depend on timing.
+template <int NT>
+__device__ __forceinline__ void sum_partials(const double* partials, int n_ctas, double* out) {
+  double v[N_ACC];
+#pragma unroll
+  for (int i = 0; i < N_ACC; i++) v[i] = 0.0;
+  for (int b = threadIdx.x; b < n_ctas; b += NT) {
+#pragma unroll
+    for (int i = 0; i < N_ACC; i++) v[i] += __ldcg(partials + (size_t)b * PART_STRIDE + i);
+  }
+  block_reduce<NT>(v, out);
+}
+
 // Last CTA of a solve's row pass: indicators of Sec. 2 and the state
-// machine.  Runs on one thread after all partials are visible.
-__device__ __forceinline__ void finalize_solve(Solve& S, int phase, int n_ctas, int L) {
+// machine.  Runs on one thread; A holds the sums of the partials (ITER).
+__device__ __forceinline__ void finalize_solve(Solve& S, int phase, const double* A, int L) {
   if (phase == PH_INIT) {
     const double* E = S.path + 4 * S.inc;
     for (int c = 0; c < 4; c++) S.Eprev[c] = E[c];
@@ -211,11 +226,6 @@ __device__ __forceinline__ void finalize_solve(Solve& S, int phase, int n_ctas, 
     S.phase = PH_DONE;
     return;
   }
-  // PH_ITER: sums over the CTAs in a fixed order
-  double A[N_ACC];
-  for (int i = 0; i < N_ACC; i++) A[i] = 0.0;
-  for (int b = 0; b < n_ctas; b++)
-    for (int i = 0; i < N_ACC; i++) A[i] += __ldcg(S.partials + (size_t)b * PART_STRIDE + i);
   const double inv = 1.0 / ((double)L * (double)L);
   double sig[4], epsm[4];
   for (int c = 0; c < 4; c++) {
@@ -474,10 +484,17 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
       s_last = prev == gridDim.x - 1;
     }
     __syncthreads();
-    if (s_last && tid == 0) {
+    if (s_last) {
+      __shared__ double tot[N_ACC];
       __threadfence();
-      finalize_solve(S, phase, gridDim.x, L);
-      S.arrive = 0;
+      if (phase == PH_ITER) {
+        sum_partials<NT>(S.partials, gridDim.x, tot);
+        __syncthreads();
+      }
+      if (tid == 0) {
+        finalize_solve(S, phase, tot, L);
+        S.arrive = 0;
+      }
     }
   }
   if (tid == 0) batch_arrive(solves, nb, bc, cond, use_cond);

@@ -177,10 +177,15 @@ def test_homogeneous_closed_form(ctx, prec):
         rc, rec, f = B.epfft_solve(ctx, prob, path, fields=True)
         assert rc == B.EPFFT_OK
         assert (rec["iterations"] == 1).all()
+        y = g[mode + "_yield"]
         for k, c in enumerate(g[mode]):
             np.testing.assert_allclose(rec["sig_mean"][k], c["sigma"], rtol=tol, atol=tol)
-            assert rec["n_plastic"][k] == (L * L if c["plastic"] else 0)
-            assert rec["n_clusters"][k] == (1 if c["plastic"] else 0)
+            # the yield decision is exact in FP64; FP32 (u = 6e-8) cannot resolve
+            # the 1e-9 margins of the cases next to the yield point
+            r = max(abs(x) for x in c["E"]) / y
+            if prec == "fp64" or abs(r - 1.0) > 1e-5:
+                assert rec["n_plastic"][k] == (L * L if c["plastic"] else 0)
+                assert rec["n_clusters"][k] == (1 if c["plastic"] else 0)
 
 
 def test_all_void_and_elastic_edge_cases(ctx):
