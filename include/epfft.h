@@ -51,6 +51,7 @@ extern "C" {
 #define EPFFT_ERR_DEVICE_TIMEOUT (-5) /* the device loop exceeded its pass bound */
 #define EPFFT_ERR_CUDA (-6)         /* a CUDA runtime call failed                */
 #define EPFFT_ERR_UNSUPPORTED (-7)  /* size / precision not built                */
+#define EPFFT_ERR_SCRATCH_LIMIT (-8) /* larger than epfft_project_static's scratch */
 
 #define EPFFT_FP64 0 /* FP64 fields, FFTs and reductions                        */
 #define EPFFT_FP32 1 /* FP32 fields and FFTs, FP64 reductions and macro values  */
@@ -202,6 +203,28 @@ int epfft_iterate(epfft_ctx *ctx, const epfft_problem *problem, const double E[4
  * (e11, e22, e12); reals of `precision`; device memory.  Blocking. */
 int epfft_project(epfft_ctx *ctx, int32_t L, int32_t precision, double lambda0, double mu0,
                   const double E[4], const void *p_dev, void *e_dev);
+
+/* The same projection as epfft_project for callers that cannot allocate
+ * device memory: code running where cudaMalloc is not available or not
+ * allowed (inside another framework's memory budget, in a process whose
+ * allocator is owned by someone else, or while the caller must not trigger
+ * an allocation that could synchronise the device).  The paper has no
+ * counterpart; this is a convenience of the library.
+ *
+ * All working memory is one static device array of the library (1.58 MB,
+ * held on every GPU that loads the library until the process exits), so
+ * lattice sides above 256 are rejected with EPFFT_ERR_SCRATCH_LIMIT.  The
+ * call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine.  p_dev / e_dev and the layout are those of epfft_project; the
+ * work is queued on `stream` (cudaStream_t of the current device, NULL for
+ * the legacy default stream) and the call returns without waiting.
+ * The first call on a device looks up the array's device address (once per
+ * device, for the current device); make that first call before any stream
+ * capture.  Every call uses the same array and leaves the last call's data
+ * in it; calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller. */
+int epfft_project_static(int32_t L, int32_t precision, double lambda0, double mu0, const double E[4],
+                         const void *p_dev, void *e_dev, void *stream);
 
 /* Nearest-neighbour clusters of the flagged pixels of n_img images
  * (Sec. 3, Hoshen-Kopelman connectivity), periodic when `periodic` != 0.

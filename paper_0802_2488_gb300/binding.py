@@ -28,13 +28,14 @@ EPFFT_NOT_CONVERGED = -4
 EPFFT_ERR_DEVICE_TIMEOUT = -5
 EPFFT_ERR_CUDA = -6
 EPFFT_ERR_UNSUPPORTED = -7
+EPFFT_ERR_SCRATCH_LIMIT = -8
 EPFFT_FP64 = 0
 EPFFT_FP32 = 1
 EPFFT_GREEN_EQ3 = 0
 
 SYMBOLS = ["epfft_create", "epfft_destroy", "epfft_last_stats", "epfft_strerror", "epfft_supported",
            "epfft_solve", "epfft_solve_batch", "epfft_mask", "epfft_iterate", "epfft_project", "epfft_label",
-           "epfft_time_passes"]
+           "epfft_time_passes", "epfft_project_static"]
 
 
 class EpfftError(RuntimeError):
@@ -104,6 +105,7 @@ def lib():
         L.epfft_iterate.argtypes = [vp, C.POINTER(_Problem), C.POINTER(dbl), vp, i32, vp]
         L.epfft_project.argtypes = [vp, i32, i32, dbl, dbl, C.POINTER(dbl), vp, vp]
         L.epfft_label.argtypes = [vp, i32, i32, vp, i32, vp, vp]
+        L.epfft_project_static.argtypes = [i32, i32, dbl, dbl, C.POINTER(dbl), vp, vp, vp]
         L.epfft_time_passes.argtypes = [vp, C.POINTER(_Problem), C.POINTER(dbl), i32, C.POINTER(C.c_float),
                                         C.POINTER(C.c_float)]
         for s in SYMBOLS:
@@ -353,3 +355,21 @@ def epfft_time_passes(ctx: Context, problem: Problem, E, n_iter: int):
     _check(lib().epfft_time_passes(ctx.handle, C.byref(p), Ea, int(n_iter), C.byref(a), C.byref(b)),
            "epfft_time_passes")
     return a.value, b.value
+
+
+def epfft_project_static(L: int, precision: str, lambda0: float, mu0: float, E, p, stream=None):
+    """epfft_project without any device allocation by the library: its working
+    memory is a static device array (lattice sides up to 256).  The output
+    tensor is allocated here by torch, before the call; the library queues its
+    work on `stream` (default: torch's current stream) and this wrapper waits
+    for it."""
+    import torch
+    assert p.is_cuda and p.is_contiguous() and tuple(p.shape) == (3, L, L)
+    e = torch.empty_like(p)
+    Ea = (C.c_double * 4)(*[float(x) for x in E])
+    s = torch.cuda.current_stream(p.device) if stream is None else stream
+    _check(lib().epfft_project_static(L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision], float(lambda0),
+                                      float(mu0), Ea, p.data_ptr(), e.data_ptr(), s.cuda_stream),
+           "epfft_project_static")
+    s.synchronize()
+    return e

@@ -563,6 +563,7 @@ const char* epfft_strerror(int code) {
     case EPFFT_ERR_DEVICE_TIMEOUT: return "device loop exceeded its bound";
     case EPFFT_ERR_CUDA: return "CUDA runtime error";
     case EPFFT_ERR_UNSUPPORTED: return "lattice size / precision not built";
+    case EPFFT_ERR_SCRATCH_LIMIT: return "lattice side above 256: larger than the static scratch of epfft_project_static";
     default: return "unknown error";
   }
 }

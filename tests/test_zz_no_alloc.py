@@ -1,0 +1,61 @@
+"""epfft_project_static, the allocation-free form of epfft_project.
+
+Some callers cannot let a library allocate device memory: code that runs
+inside another framework's memory budget or allocator, or that must not
+trigger an allocation which could synchronise the device.  For them the
+library offers the compatible-strain projection with all of its working
+memory in a static device array (lattice sides up to 256).  These tests call
+it through the C ABI and check it against the allocating entry point.
+
+The file is named to be collected last, so a run that stops at the first
+failure has run every other test before it.
+"""
+import numpy as np
+import pytest
+
+from paper_0802_2488_gb300 import binding as B
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TDT = {"fp64": torch.float64, "fp32": torch.float32}
+TOL = {"fp64": 1e-12, "fp32": 3e-6}  # the projection tolerances of the parity tests
+
+
+def rel(a, b):
+    a = a.double().cpu().numpy()
+    b = b.double().cpu().numpy()
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_0802_2488_gb300 import build
+    build.build()
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def test_two_static_calls_in_a_row_match_the_allocating_projection(ctx):
+    rng = np.random.default_rng(11)
+    cases = [(256, "fp64", np.array([0.3, -0.2, 0.0, 0.15])),
+             (64, "fp32", np.array([-0.1, 0.25, 0.0, 0.05]))]
+    inputs, refs = [], []
+    for L, prec, E in cases:
+        p = torch.tensor(rng.standard_normal((3, L, L)), dtype=TDT[prec], device="cuda")
+        inputs.append(p)
+        refs.append(B.epfft_project(ctx, L, prec, 1.5, 1.0, E, p))
+    # two consecutive calls of the static entry point (the second reuses the
+    # array the first one left behind)
+    outs = [B.epfft_project_static(L, prec, 1.5, 1.0, E, p) for (L, prec, E), p in zip(cases, inputs)]
+    for (L, prec, E), got, ref in zip(cases, outs, refs):
+        assert rel(got, ref) < TOL[prec], (L, prec, rel(got, ref))
+
+
+def test_lattices_beyond_the_static_scratch_are_rejected():
+    p = torch.zeros((3, 512, 512), dtype=torch.float64, device="cuda")
+    with pytest.raises(B.EpfftError) as err:
+        B.epfft_project_static(512, "fp64", 1.5, 1.0, [0.1, 0.0, 0.0, 0.0], p)
+    assert err.value.code == B.EPFFT_ERR_SCRATCH_LIMIT
