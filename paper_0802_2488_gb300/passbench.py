@@ -1,0 +1,55 @@
+"""Time the two fused passes of one iteration for one lattice side and
+precision (CUDA events on the context stream, through epfft_time_passes) and
+print their algorithmic throughput as JSON.
+
+    python -m paper_0802_2488_gb300.passbench --L 2048 --precision fp32 --iters 50
+
+Algorithmic work per pixel and pass (kernels section):
+  row pass:    bytes 57 (FP32) / 113 (FP64),  flops 15 log2 L + 60
+  column pass: bytes 24 (FP32) / 48 (FP64),   flops 15 log2 L + 25
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+
+from . import binding as B
+from . import inputs
+
+
+def measure(ctx, L: int, precision: str, f: float = 0.2, iters: int = 50) -> dict:
+    prob = B.Problem(L=L, precision=precision, void_fraction=f, seed=0)
+    E = inputs.load_path("shear", 40, 3.0)[20]
+    col_ms, row_ms = B.epfft_time_passes(ctx, prob, E, iters)
+    n = L * L
+    lg = math.log2(L)
+    f64 = precision == "fp64"
+    row_b, col_b = (113 if f64 else 57) * n, (48 if f64 else 24) * n
+    row_f, col_f = (15 * lg + 60) * n, (15 * lg + 25) * n
+    return {
+        "L": L, "precision": precision, "iters": iters,
+        "col_ms": col_ms, "row_ms": row_ms,
+        "col_GBps": col_b / (col_ms * 1e-3) / 1e9, "row_GBps": row_b / (row_ms * 1e-3) / 1e9,
+        "col_GFLOPs": col_f / (col_ms * 1e-3) / 1e9, "row_GFLOPs": row_f / (row_ms * 1e-3) / 1e9,
+        "px_it_per_s": n / ((col_ms + row_ms) * 1e-3),
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--L", type=int, nargs="+", default=[256])
+    ap.add_argument("--precision", nargs="+", default=["fp64", "fp32"])
+    ap.add_argument("--iters", type=int, default=50)
+    a = ap.parse_args()
+    from . import build
+    build.build()
+    with B.Context(0) as ctx:
+        for prec in a.precision:
+            for L in a.L:
+                if B.epfft_supported(L, prec):
+                    print(json.dumps(measure(ctx, L, prec, iters=a.iters)), flush=True)
+
+
+if __name__ == "__main__":
+    main()
