@@ -46,10 +46,18 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="epfft", choices=["epfft", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
-    ap.add_argument("--cap", type=int, default=1000, help="max iterations per increment")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
+                    help="default: fp64 for c1/c2, fp32 for c3/c4")
+    ap.add_argument("--cap", type=int, default=None, help="max iterations per increment")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU-baseline leg")
-    return ap.parse_args()
+    ap.add_argument("--no-fp32", action="store_true", help="c2: skip the FP32 companion measurement")
+    a = ap.parse_args()
+    if a.precision is None:
+        a.precision = "fp64" if a.workload in ("c1", "c2") else "fp32"
+    if a.cap is None:
+        a.cap = {"c1": 2000, "c2": 300, "c3": 100, "c4": 60}[a.workload]
+    return a
 
 
 def dist_env():
@@ -59,14 +67,23 @@ def dist_env():
     return ws, rank, local
 
 
-def workload(cap: int):
+def workload(name: str, cap: int):
+    """The problems of one step and the config block of the JSON line."""
     from paper_0802_2488_gb300 import inputs
-    P = inputs.config2()
-    return P, dict(workload=f"{P.name}: L=256, f=0.20 Bernoulli voids (seed 0), shear E12 to 3x yield "
-                            f"in 40 increments, mu=1 lambda=1.5 Y=1, C0=matrix, tol 1e-8 (eta1, eta2), "
-                            f"max {cap} iterations per increment, clusters labelled per increment",
-                   L=P.L, void_fraction=P.f, seed=P.seed, loading=P.mode, n_inc=P.n_inc,
-                   max_iter_per_increment=cap, tol=1e-8)
+    if name == "c3":
+        probs = inputs.config3()
+        desc = ("64 realizations of L=512 (f in {0.05,0.10,0.20,0.30} x seeds 0-15; seeds 0-7 equibiaxial to "
+                "2x yield, 8-15 shear to 3x yield), 30 increments each, advanced together in one device loop")
+    else:
+        P = {"c1": inputs.config1, "c2": inputs.config2, "c4": inputs.config4}[name]()
+        probs = [P]
+        desc = (f"{P.name}: L={P.L}, f={P.f:.2f} Bernoulli voids (seed {P.seed}), {P.mode} to "
+                f"{P.multiple:g}x yield in {P.n_inc} increments")
+    cfg = dict(workload=f"{desc}; mu=1 lambda=1.5 Y=1, C0=matrix, tol 1e-8 (eta1, eta2), at most {cap} "
+                        f"iterations per increment, plastic clusters labelled per increment",
+               L=probs[0].L, n_solves=len(probs), n_inc=[p.n_inc for p in probs][0] if len(probs) == 1 else 30,
+               max_iter_per_increment=cap, tol=1e-8)
+    return probs, cfg
 
 
 class ClockSampler:
@@ -117,28 +134,26 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(cap: int, budget_s: float = 15.0):
+def cpu_baseline(probs, budget_s: float = 15.0):
     """The oracle as it stands, on this machine's host cores (OpenMP), on a
-    bounded sample of the workload: the first increment of the shear path
-    on the same lattice, with as many iterations as fit in ~budget_s."""
+    bounded sample of the workload: the first increment of the first problem
+    of the workload, with as many iterations as fit in ~budget_s."""
     import oracle as O
-    from paper_0802_2488_gb300 import inputs
-    P = inputs.config2()
+    P = probs[0]
     mask = O.mask(P.L, P.f, P.seed)
     mat = O.material()
     O.build()
     t = time.perf_counter()
-    O.solve(mask, mat, P.path[:1], max_iter=3)
-    per_it = (time.perf_counter() - t) / 3
-    n_it = max(3, min(cap, int(budget_s / max(per_it, 1e-6))))
+    O.solve(mask, mat, P.path[:1], max_iter=2)
+    per_it = (time.perf_counter() - t) / 2
+    n_it = max(2, int(budget_s / max(per_it, 1e-6)))
     t = time.perf_counter()
     sol = O.solve(mask, mat, P.path[:1], max_iter=n_it)
     dt = time.perf_counter() - t
     its = int(sol.records["iterations"].sum())
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": P.L * P.L * its / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first increment of the L=256 shear workload, {its} iterations "
-                      f"({dt:.1f} s, OpenMP over {cores} threads)"}
+            "sample": f"first increment of {P.name}, {its} iterations ({dt:.1f} s, OpenMP over {cores} threads)"}
 
 
 def run_reference(args):
@@ -146,14 +161,18 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle as O
-    from paper_0802_2488_gb300 import inputs
-    P, cfg = workload(args.cap)
+    probs, cfg = workload(args.workload, args.cap)
+    P = probs[0]
     mask = O.mask(P.L, P.f, P.seed)
     mat = O.material()
     O.build()
-    n_it = 20  # iterations per step: a bounded sample of one increment
+    t = time.perf_counter()
+    O.solve(mask, mat, P.path[:1], max_iter=2)
+    per_it = (time.perf_counter() - t) / 2
+    # iterations per step: a bounded sample of one increment (~20 s for the whole run)
+    n_it = max(2, int(20.0 / max(per_it, 1e-6) / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        O.solve(mask, mat, P.path[:1], max_iter=2)
+        O.solve(mask, mat, P.path[:1], max_iter=n_it)
     times = []
     its = 0
     for _ in range(args.steps):
@@ -170,8 +189,32 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{n_it} iterations of the first increment per step"},
+                         "sample": f"{n_it} iterations of the first increment of {P.name} per step"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def timed_solves(B, ctx, stream, flush, probs, paths, steps, torch):
+    """`steps` batch solves, each bracketed by CUDA events on the context
+    stream after an L2 flush; returns (seconds, pixel-iterations, launches,
+    last records)."""
+    ev = []
+    pix_its = 0
+    launches = 0
+    recs = None
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        rc, recs = B.epfft_solve_batch(ctx, probs, paths)
+        with torch.cuda.stream(stream):
+            b.record(stream)
+        ev.append((a, b))
+        pix_its += sum(p.L * p.L * int(r["iterations"].sum()) for p, r in zip(probs, recs))
+        launches += B.epfft_last_stats(ctx)["kernel_launches"]
+    stream.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / 1e3, pix_its, launches, recs
 
 
 def main():
@@ -187,17 +230,22 @@ def main():
     from paper_0802_2488_gb300 import binding as B
     from paper_0802_2488_gb300 import build
     build.build()
-    P, cfg = workload(args.cap)
+    probs, cfg = workload(args.workload, args.cap)
+    L = probs[0].L
     stream = torch.cuda.Stream(device=local)
     ctx = B.Context(local, stream=stream.cuda_stream)
-    mask_dev = B.epfft_mask(P.L, P.f, P.seed, device=local)
-    mask_host = torch.empty((P.L, P.L), dtype=torch.uint8, pin_memory=True)
-    mask_host.copy_(mask_dev.cpu())
-    mask_host_np = mask_host.numpy()
-    prob_dev = B.Problem(L=P.L, precision=args.precision, mask=mask_dev, tol_eq=1e-8, tol_macro=1e-8,
-                         max_iter=args.cap)
-    prob_host = B.Problem(L=P.L, precision=args.precision, mask=mask_host_np, tol_eq=1e-8, tol_macro=1e-8,
-                          max_iter=args.cap)
+    masks_dev = [B.epfft_mask(P.L, P.f, P.seed, device=local) for P in probs]
+    masks_host = []
+    for m in masks_dev:
+        h = torch.empty((L, L), dtype=torch.uint8, pin_memory=True)
+        h.copy_(m.cpu())
+        masks_host.append(h.numpy())
+    paths = [P.path for P in probs]
+
+    def problems(prec, host):
+        return [B.Problem(L=L, precision=prec, mask=(masks_host[i] if host else masks_dev[i]), tol_eq=1e-8,
+                          tol_macro=1e-8, max_iter=args.cap) for i in range(len(probs))]
+
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=local)
 
     def barrier():
@@ -206,52 +254,51 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(local)
 
-    # warm-up
+    pd = problems(args.precision, False)
     for _ in range(args.warmup):
-        B.epfft_solve(ctx, prob_dev, P.path)
-
-    # timed region (device): inputs resident in HBM
-    pix_its = 0
-    launches = 0
-    ev = []
+        B.epfft_solve_batch(ctx, pd, paths)
     barrier()
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(1)
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-            rc, rec = B.epfft_solve(ctx, prob_dev, P.path)
-            with torch.cuda.stream(stream):
-                b.record(stream)
-            ev.append((a, b))
-            pix_its += P.L * P.L * int(rec["iterations"].sum())
-            launches += B.epfft_last_stats(ctx)["kernel_launches"]
+        dev_s, pix_its, launches, recs = timed_solves(B, ctx, stream, flush, pd, paths, args.steps, torch)
         barrier()
         wall = time.perf_counter() - t0
-    dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     clocks = clk.summary()
 
-    # end to end through the C ABI with host buffers
-    for _ in range(1):
-        B.epfft_solve(ctx, prob_host, P.path, fields=True)
+    # end to end through the C ABI with host buffers (pinned masks in; records,
+    # final strain, plastic flags and cluster labels out)
+    ph = problems(args.precision, True)
+    B.epfft_solve_batch(ctx, ph, paths, fields=True)
     barrier()
     t0 = time.perf_counter()
     e2e_its = 0
     for _ in range(args.steps):
-        rc, rec, f = B.epfft_solve(ctx, prob_host, P.path, fields=True)
-        e2e_its += P.L * P.L * int(rec["iterations"].sum())
+        rc, rr, ff = B.epfft_solve_batch(ctx, ph, paths, fields=True)
+        e2e_its += sum(p.L * p.L * int(r["iterations"].sum()) for p, r in zip(ph, rr))
     barrier()
     e2e_s = time.perf_counter() - t0
     rs = 8 if args.precision == "fp64" else 4
-    h2d = P.L * P.L + 4 * 8 * P.n_inc
-    d2h = P.n_inc * 104 + P.L * P.L * 4 * rs + 2 * P.n_inc * P.L * P.L * 5
+    h2d = sum(L * L + 4 * 8 * P.n_inc for P in probs)
+    d2h = sum(P.n_inc * 104 + L * L * 4 * rs + P.n_inc * L * L * 5 for P in probs)
 
     # pass timing (CUDA events on the context stream) for the roofline
-    E_mid = P.path[P.n_inc // 2]
-    col_ms, row_ms = B.epfft_time_passes(ctx, prob_dev, E_mid, 200)
+    E_mid = probs[0].path[probs[0].n_inc // 2]
+    col_ms, row_ms = B.epfft_time_passes(ctx, pd[0], E_mid, 50, n_batch=len(probs))
+
+    companion = None
+    if args.workload == "c2" and args.precision == "fp64" and not args.no_fp32:
+        pf = problems("fp32", False)
+        for _ in range(args.warmup):
+            B.epfft_solve_batch(ctx, pf, paths)
+        f_s, f_its, _, frecs = timed_solves(B, ctx, stream, flush, pf, paths, args.steps, torch)
+        fcol, frow = B.epfft_time_passes(ctx, pf[0], E_mid, 50)
+        s64, s32 = recs[0]["sig_mean"], frecs[0]["sig_mean"]
+        curve_err = float(np.max(np.linalg.norm(s32 - s64, axis=1) / np.linalg.norm(s64, axis=1)))
+        companion = {"value": f_its / f_s, "unit": UNIT, "ms_per_step": 1e3 * f_s / args.steps,
+                     "solves_per_s": args.steps / f_s, "col_pass_ms": fcol, "row_pass_ms": frow,
+                     "macro_curve_max_rel_err_vs_fp64": curve_err,
+                     "eta1_last_increment": float(frecs[0]["eta1"][-1]),
+                     "dtype": "f32 fields and FFTs, f64 reductions"}
 
     t_step = dev_s / args.steps
     if ws > 1:
@@ -261,30 +308,30 @@ def main():
         t_step, dev_s, e2e_s = tt.tolist()
     value = ws * pix_its / dev_s
     if rank == 0:
-        L = P.L
         lg = int(np.log2(L))
+        nb = len(probs)
         if args.precision == "fp64":
             # FP64 arithmetic bound: row pass 15 log2 L + 60 flops per pixel
             # (row transforms, local step); column pass 15 log2 L + 25 (column
             # transforms, Green operator)
-            row_flops = (15 * lg + 60) * L * L
-            col_flops = (15 * lg + 25) * L * L
-            dom_ms, dom_flops, dom = (row_ms, row_flops, "row") if row_ms >= col_ms else (col_ms, col_flops, "col")
+            row_w, col_w = (15 * lg + 60) * L * L * nb, (15 * lg + 25) * L * L * nb
+            dom_ms, dom_w, dom = (row_ms, row_w, "row") if row_ms >= col_ms else (col_ms, col_w, "col")
             sm = clocks.get("sm_max_mhz") or 2070.0
             peak = 152 * 2 * 2 * sm * 1e6 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 flop
-            achieved = dom_flops / (dom_ms * 1e-3) / 1e12
+            achieved = dom_w / (dom_ms * 1e-3) / 1e12
             roof = {"bound": "alu", "kernel": f"{dom}_pass<double,{L}>", "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock"}
         else:
-            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-                os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
-            row_b, col_b = 57 * L * L, 24 * L * L
+            mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+            hbm = json.load(open(mp))["hbm_gbs"] if os.path.exists(mp) else 6800.0
+            row_b, col_b = 57 * L * L * nb, 24 * L * L * nb
             dom_ms, dom_b, dom = (row_ms, row_b, "row") if row_ms >= col_ms else (col_ms, col_b, "col")
             achieved = dom_b / (dom_ms * 1e-3) / 1e9
-            roof = {"bound": "hbm", "kernel": f"{dom}_pass<float,{L}>", "achieved": achieved,
-                    "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                    "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+            roof = {"bound": "hbm", "kernel": f"{dom}_pass<float,{L}>", "achieved": achieved, "peak": hbm,
+                    "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if os.path.exists(mp)
+                    else "fallback 6800 GB/s (of fallback)"}
         roof.update({"col_pass_ms": col_ms, "row_pass_ms": row_ms})
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -293,7 +340,7 @@ def main():
             "data": "synthetic",
             "config": dict(cfg, l2="flushed between steps (512 MiB write, outside the step events)",
                            parallelism="replicas" if ws > 1 else "single GPU",
-                           solves_per_s=ws * args.steps / dev_s, precision=args.precision),
+                           solves_per_s=ws * args.steps * len(probs) / dev_s, precision=args.precision),
             "roofline": roof,
             "e2e": {"value": ws * e2e_its / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -301,8 +348,10 @@ def main():
             "clocks": clocks,
             "wall_s": wall,
         }
+        if companion:
+            out["fp32"] = companion
         if ws == 1 and not args.no_baseline:
-            out["cpu_baseline"] = cpu_baseline(args.cap)
+            out["cpu_baseline"] = cpu_baseline(probs)
         print(json.dumps(out), flush=True)
     ctx.close()
     if ws > 1:

@@ -235,12 +235,13 @@ int epfft_label(epfft_ctx *ctx, int32_t L, int32_t n_img, const uint8_t *flags_d
                 int32_t periodic, int32_t *labels_dev, int32_t *counts);
 
 /* Mean device time of the two fused passes of one iteration, measured with
- * CUDA events around n_iter launch pairs of each on the context stream,
+ * CUDA events around n_iter launch pairs of each on the context stream, for
+ * a batch of n_batch copies of `problem` (one launch covers the batch),
  * from the uniform state eps = E (iterations never stop early).
  * col_ms: forward column FFT + Green operator + inverse column FFT;
  * row_ms: inverse row FFT + local step + residual partials + forward row FFT.
  * Blocking. */
-int epfft_time_passes(epfft_ctx *ctx, const epfft_problem *problem, const double E[4],
+int epfft_time_passes(epfft_ctx *ctx, const epfft_problem *problem, int32_t n_batch, const double E[4],
                       int32_t n_iter, float *col_ms, float *row_ms);
 
 #ifdef __cplusplus

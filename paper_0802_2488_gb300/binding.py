@@ -106,7 +106,7 @@ def lib():
         L.epfft_project.argtypes = [vp, i32, i32, dbl, dbl, C.POINTER(dbl), vp, vp]
         L.epfft_label.argtypes = [vp, i32, i32, vp, i32, vp, vp]
         L.epfft_project_static.argtypes = [i32, i32, dbl, dbl, C.POINTER(dbl), vp, vp, vp]
-        L.epfft_time_passes.argtypes = [vp, C.POINTER(_Problem), C.POINTER(dbl), i32, C.POINTER(C.c_float),
+        L.epfft_time_passes.argtypes = [vp, C.POINTER(_Problem), i32, C.POINTER(dbl), i32, C.POINTER(C.c_float),
                                         C.POINTER(C.c_float)]
         for s in SYMBOLS:
             if s not in ("epfft_destroy", "epfft_strerror"):
@@ -346,14 +346,14 @@ def epfft_label(ctx: Context, flags, periodic: bool = True):
     return lab, counts
 
 
-def epfft_time_passes(ctx: Context, problem: Problem, E, n_iter: int):
+def epfft_time_passes(ctx: Context, problem: Problem, E, n_iter: int, n_batch: int = 1):
     """(column-pass ms, row-pass ms): mean CUDA-event durations over n_iter
-    launches of each, from the uniform state eps = E."""
+    launches of each for a batch of n_batch copies, from the state eps = E."""
     p, keep = problem._c()
     Ea = (C.c_double * 4)(*[float(x) for x in E])
     a, b = C.c_float(), C.c_float()
-    _check(lib().epfft_time_passes(ctx.handle, C.byref(p), Ea, int(n_iter), C.byref(a), C.byref(b)),
-           "epfft_time_passes")
+    _check(lib().epfft_time_passes(ctx.handle, C.byref(p), int(n_batch), Ea, int(n_iter), C.byref(a),
+                                   C.byref(b)), "epfft_time_passes")
     return a.value, b.value
 
 

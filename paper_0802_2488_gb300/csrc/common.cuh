@@ -74,10 +74,31 @@ enum Acc : int {
 };
 constexpr int PART_STRIDE = 12;  // doubles per CTA partial record
 
+// Derived material constants of a solve, formed once on the host in FP64
+// (and rounded once to FP32 for the FP32 kernels), so that no kernel thread
+// divides or takes square roots to build them.
+enum MatConst : int {
+  MC_K = 0,       // matrix bulk modulus lambda + 2 mu / 3
+  MC_TWO_MU,      // 2 mu
+  MC_LAM0,        // lambda0
+  MC_TWO_MU0,     // 2 mu0
+  MC_YLIM,        // sqrt(2/3) Y
+  MC_YLIM2,       // 2/3 Y^2
+  MC_INV_3KK0,    // 1 / (3 (K + K0))
+  MC_INV_3K0,     // 1 / (3 K0)
+  MC_INV_2MUMU0,  // 1 / (2 (mu + mu0))
+  MC_INV_2MU0,    // 1 / (2 mu0)
+  MC_TRIAL2,      // (mu / (mu + mu0))^2
+  MC_MU0,         // mu0
+  N_MC
+};
+
 // Device-resident state of one solve of a batch.
 struct Solve {
   // material: matrix lambda, mu, Y; reference medium lambda0, mu0
   double lam, mu, Y, lam0, mu0;
+  double mcd[N_MC];  // derived constants (MatConst), FP64
+  float mcf[N_MC];   // the same rounded to FP32
   double tol_eq, tol_macro;
   int32_t max_iter, n_inc;
   const double* path;  // n_inc * 4 prescribed mean strains (11,22,33,12)

@@ -159,6 +159,27 @@ int check_problem(const epfft_problem* p) {
   return EPFFT_OK;
 }
 
+// Derived material constants of a solve (see MatConst), FP64 and FP32.
+void fill_consts(Solve& S) {
+  const double K = S.lam + 2.0 * S.mu / 3.0, K0 = S.lam0 + 2.0 * S.mu0 / 3.0;
+  const double yl = std::sqrt(2.0 / 3.0) * S.Y;
+  const double r = S.mu / (S.mu + S.mu0);
+  double* c = S.mcd;
+  c[MC_K] = K;
+  c[MC_TWO_MU] = 2.0 * S.mu;
+  c[MC_LAM0] = S.lam0;
+  c[MC_TWO_MU0] = 2.0 * S.mu0;
+  c[MC_YLIM] = yl;
+  c[MC_YLIM2] = std::isinf(yl) ? yl : yl * yl;
+  c[MC_INV_3KK0] = 1.0 / (3.0 * (K + K0));
+  c[MC_INV_3K0] = 1.0 / (3.0 * K0);
+  c[MC_INV_2MUMU0] = 1.0 / (2.0 * (S.mu + S.mu0));
+  c[MC_INV_2MU0] = 1.0 / (2.0 * S.mu0);
+  c[MC_TRIAL2] = r * r;
+  c[MC_MU0] = S.mu0;
+  for (int i = 0; i < N_MC; i++) S.mcf[i] = (float)c[i];
+}
+
 // Device state of one batch.
 struct Batch {
   int L = 0, prec = 0, nb = 0;
@@ -215,6 +236,7 @@ int setup_batch(epfft_ctx* c, Arena& A, Batch& B, int n, const epfft_problem* pr
     S.tol_macro = p.tol_macro;
     S.max_iter = p.max_iter;
     S.n_inc = path.n_inc;
+    fill_consts(S);
     B.n_inc[i] = path.n_inc;
     void* eps0d = A.get(4 * LL * rs);
     void* eps1d = A.get(4 * LL * rs);
@@ -667,9 +689,9 @@ int epfft_label(epfft_ctx* ctx, int32_t L, int32_t n_img, const uint8_t* flags_d
   return herr ? EPFFT_ERR_DEVICE_TIMEOUT : EPFFT_OK;
 }
 
-int epfft_time_passes(epfft_ctx* ctx, const epfft_problem* problem, const double E[4], int32_t n_iter,
-                      float* col_ms, float* row_ms) {
-  if (!ctx || !problem || !E || n_iter < 1 || !col_ms || !row_ms) return EPFFT_ERR_ARG;
+int epfft_time_passes(epfft_ctx* ctx, const epfft_problem* problem, int32_t n_batch, const double E[4],
+                      int32_t n_iter, float* col_ms, float* row_ms) {
+  if (!ctx || !problem || !E || n_iter < 1 || n_batch < 1 || !col_ms || !row_ms) return EPFFT_ERR_ARG;
   int rc = check_problem(problem);
   if (rc) return rc;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return EPFFT_ERR_CUDA;
@@ -677,23 +699,25 @@ int epfft_time_passes(epfft_ctx* ctx, const epfft_problem* problem, const double
   p.tol_eq = 0.0;
   p.tol_macro = 0.0;
   p.max_iter = 1 << 30;
-  epfft_path path = {1, 0, E};
+  std::vector<epfft_problem> ps(n_batch, p);
+  std::vector<epfft_path> paths(n_batch, epfft_path{1, 0, E});
   Arena A(ctx);
   Batch B;
-  rc = setup_batch(ctx, A, B, 1, &p, &path, nullptr);
+  rc = setup_batch(ctx, A, B, n_batch, ps.data(), paths.data(), nullptr);
   if (rc) return rc;
+  const int nb = n_batch;
   // first row pass: warm start (eps = E, spectrum of its polarization)
-  if (B.prec == EPFFT_FP32) CK(launch_row<float>(B.L, 1, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
-  else CK(launch_row<double>(B.L, 1, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
+  if (B.prec == EPFFT_FP32) CK(launch_row<float>(B.L, nb, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
+  else CK(launch_row<double>(B.L, nb, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
   std::vector<cudaEvent_t> ev(3 * (size_t)n_iter);
   for (auto& e : ev) CK(cudaEventCreate(&e));
   for (int it = 0; it < n_iter; it++) {
     CK(cudaEventRecord(ev[3 * it], ctx->stream));
-    if (B.prec == EPFFT_FP32) CK(launch_col<float>(B.L, 1, ctx->stream, B.d_solves, B.tw, B.ktab, 0, 0));
-    else CK(launch_col<double>(B.L, 1, ctx->stream, B.d_solves, B.tw, B.ktab, 0, 0));
+    if (B.prec == EPFFT_FP32) CK(launch_col<float>(B.L, nb, ctx->stream, B.d_solves, B.tw, B.ktab, 0, 0));
+    else CK(launch_col<double>(B.L, nb, ctx->stream, B.d_solves, B.tw, B.ktab, 0, 0));
     CK(cudaEventRecord(ev[3 * it + 1], ctx->stream));
-    if (B.prec == EPFFT_FP32) CK(launch_row<float>(B.L, 1, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
-    else CK(launch_row<double>(B.L, 1, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
+    if (B.prec == EPFFT_FP32) CK(launch_row<float>(B.L, nb, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
+    else CK(launch_row<double>(B.L, nb, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
     CK(cudaEventRecord(ev[3 * it + 2], ctx->stream));
   }
   CK(cudaStreamSynchronize(ctx->stream));

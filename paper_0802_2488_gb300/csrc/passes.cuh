@@ -31,11 +31,13 @@ template <typename T, int L>
 struct Cfg {
   static constexpr bool F64 = sizeof(T) == 8;
   static constexpr int M = L / 2;
-  // rows per row-pass CTA
-  static constexpr int RR = F64 ? (L <= 256 ? 2 : 4) : (L <= 128 ? 2 : (L <= 256 ? 4 : (L <= 2048 ? 8 : 4)));
+  // rows per row-pass CTA (small lattices: more, smaller CTAs to fill the
+  // SMs; large ones: RR x W complex numbers of a tile row span >= 64 bytes)
+  static constexpr int RR = F64 ? (L <= 256 ? 1 : (L <= 512 ? 2 : 4))
+                                : (L <= 256 ? 2 : (L <= 1024 ? 8 : 4));
   // columns per column-pass CTA (= tile width of the spectrum layout)
-  static constexpr int W0 = F64 ? (L <= 256 ? 2 : (L <= 1024 ? 4 : 2))
-                                : (L <= 64 ? 2 : (L <= 256 ? 4 : (L <= 1024 ? 8 : (L <= 2048 ? 4 : 2))));
+  static constexpr int W0 = F64 ? (L <= 256 ? 1 : (L <= 512 ? 2 : (L <= 1024 ? 4 : 2)))
+                                : (L <= 256 ? 2 : (L <= 512 ? 8 : (L <= 2048 ? 4 : 2)));
   static constexpr int W = W0 < M ? W0 : M;
   static constexpr int NT_ROW = L < 32 ? 32 : (L > 512 ? 512 : L);
   static constexpr int NT_COL0 = ((3 * W * L / 8 + 31) / 32) * 32;
@@ -189,6 +191,46 @@ __device__ __forceinline__ void block_reduce(double v[N_ACC], double* out) {
 #pragma unroll
     for (int i = 0; i < N_ACC; i++) {
       double x = lane < NT / 32 ? red[lane][i] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) out[i] = x;
+    }
+  }
+}
+
+// CTA sums of the per-thread accumulators.  FP64: shuffles in FP64.  FP32:
+// each warp adds its 32 values as FP32 (hi, lo) pairs with the error-free
+// TwoSum of Knuth/Moller (s = a + b, e = exact rounding error of the add), so
+// the warp total carries about twice FP32 precision without FP64 work; each
+// warp's total is then promoted to FP64 and the warps are added in FP64.
+template <int NT>
+__device__ __forceinline__ void block_reduce_acc(double acc[N_ACC], double* out) {
+  block_reduce<NT>(acc, out);
+}
+template <int NT>
+__device__ __forceinline__ void block_reduce_acc(float acc[N_ACC], double* out) {
+  __shared__ double red2[NT / 32][N_ACC];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < N_ACC; i++) {
+    float hi = acc[i], lo = 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float bh = __shfl_down_sync(0xffffffffu, hi, o);
+      const float bl = __shfl_down_sync(0xffffffffu, lo, o);
+      const float sum = hi + bh;
+      const float bb = sum - hi;
+      const float err = (hi - (sum - bb)) + (bh - bb);
+      hi = sum;
+      lo = lo + bl + err;
+    }
+    if (lane == 0) red2[wid][i] = (double)hi + (double)lo;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int i = 0; i < N_ACC; i++) {
+      double x = lane < NT / 32 ? red2[lane][i] : 0.0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
       if (lane == 0) out[i] = x;
@@ -470,10 +512,7 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
       IO::store(sp, spec, r0);
     }
     if (phase == PH_ITER) {
-      double v[N_ACC];
-#pragma unroll
-      for (int i = 0; i < N_ACC; i++) v[i] = (double)acc[i];
-      if (ECHK(blockIdx.x, L / RR, 25)) block_reduce<NT>(v, S.partials + (size_t)blockIdx.x * PART_STRIDE);
+      if (ECHK(blockIdx.x, L / RR, 25)) block_reduce_acc<NT>(acc, S.partials + (size_t)blockIdx.x * PART_STRIDE);
     }
     // every thread of this CTA is done with the solve state before the CTA
     // counts itself in

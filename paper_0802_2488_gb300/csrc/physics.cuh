@@ -20,24 +20,61 @@ struct Mat {
 };
 
 template <typename T>
+__device__ __forceinline__ const T* mat_consts(const Solve& S);
+template <>
+__device__ __forceinline__ const float* mat_consts<float>(const Solve& S) { return S.mcf; }
+template <>
+__device__ __forceinline__ const double* mat_consts<double>(const Solve& S) { return S.mcd; }
+
+// Loads the solve's derived constants (formed on the host).
+template <typename T>
 __device__ __forceinline__ Mat<T> make_mat(const Solve& S) {
-  // Derived constants are formed in FP64 and rounded once to T.
-  const double K = S.lam + 2.0 * S.mu / 3.0, K0 = S.lam0 + 2.0 * S.mu0 / 3.0;
-  const double yl = sqrt(2.0 / 3.0) * S.Y;
+  const T* c = mat_consts<T>(S);
   Mat<T> m;
-  m.K = T(K);
-  m.two_mu = T(2.0 * S.mu);
-  m.lam0 = T(S.lam0);
-  m.two_mu0 = T(2.0 * S.mu0);
-  m.ylim = T(yl);
-  m.ylim2 = T(yl * yl);
-  m.inv_3KK0 = T(1.0 / (3.0 * (K + K0)));
-  m.inv_3K0 = T(1.0 / (3.0 * K0));
-  m.inv_2mumu0 = T(1.0 / (2.0 * (S.mu + S.mu0)));
-  m.inv_2mu0 = T(1.0 / (2.0 * S.mu0));
-  const double r = S.mu / (S.mu + S.mu0);
-  m.trial2 = T(r * r);
+  m.K = c[MC_K];
+  m.two_mu = c[MC_TWO_MU];
+  m.lam0 = c[MC_LAM0];
+  m.two_mu0 = c[MC_TWO_MU0];
+  m.ylim = c[MC_YLIM];
+  m.ylim2 = c[MC_YLIM2];
+  m.inv_3KK0 = c[MC_INV_3KK0];
+  m.inv_3K0 = c[MC_INV_3K0];
+  m.inv_2mumu0 = c[MC_INV_2MUMU0];
+  m.inv_2mu0 = c[MC_INV_2MU0];
+  m.trial2 = c[MC_TRIAL2];
   return m;
+}
+
+// 1/sqrt(x) for x > 0 in normal FP32 range.  FP32: the hardware estimate.
+// FP64: the FP32 estimate refined by two Newton-Raphson steps
+// y <- y (3/2 - x y^2 / 2), each of which squares the relative error
+// (2e-7 -> 1e-13 -> below FP64 rounding), so that the kernel uses FP64 FMAs
+// only.
+template <typename T>
+__device__ __forceinline__ T rsq(T x);
+template <>
+__device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ double rsq<double>(double x) {
+  double y = (double)rsqrtf((float)x);
+  const double h = 0.5 * x;
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return y;
+}
+
+// 1/x for x > 0 in normal FP32 range.  FP32: IEEE division.  FP64: the FP32
+// reciprocal refined by two Newton-Raphson steps r <- r + r (1 - x r).
+template <typename T>
+__device__ __forceinline__ T rcp(T x);
+template <>
+__device__ __forceinline__ float rcp<float>(float x) { return 1.0f / x; }
+template <>
+__device__ __forceinline__ double rcp<double>(double x) {
+  double r = (double)__frcp_rn((float)x);
+  r = fma(r, fma(-x, r, 1.0), r);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return r;
 }
 
 // sigma(eps): void -> 0; matrix -> K tr(eps) I + g dev(eps) with g = 2 mu on
@@ -55,7 +92,7 @@ __device__ __forceinline__ bool sigma(const T e[4], bool is_void, const Mat<T>& 
   const T d0 = e[0] - mth, d1 = e[1] - mth, d2 = e[2] - mth, d3 = e[3];
   const T nd2 = d0 * d0 + d1 * d1 + d2 * d2 + T(2) * d3 * d3;
   const bool pl = m.two_mu * m.two_mu * nd2 > m.ylim2;
-  const T g = pl ? m.ylim * rsqrt(nd2) : m.two_mu;
+  const T g = pl ? m.ylim * rsq(nd2) : m.two_mu;
   const T p = m.K * tr;
   s[0] = p + g * d0;
   s[1] = p + g * d1;
@@ -107,7 +144,7 @@ __device__ __forceinline__ bool local_solve(const T t[4], bool is_void, const Ma
     em = tm * m.inv_3KK0;
     const T nt2 = d0 * d0 + d1 * d1 + d2 * d2 + T(2) * d3 * d3;
     pl = m.trial2 * nt2 > m.ylim2;
-    sc = pl ? (T(1) - m.ylim * rsqrt(nt2)) * m.inv_2mu0 : m.inv_2mumu0;
+    sc = pl ? (T(1) - m.ylim * rsq(nt2)) * m.inv_2mu0 : m.inv_2mumu0;
   }
   e[0] = d0 * sc + em;
   e[1] = d1 * sc + em;
@@ -134,7 +171,7 @@ __device__ __forceinline__ void green_apply(C2<T> k1, C2<T> k2, T lam0, T mu0, T
   const C2<T> c = conj(k1) * k2;
   const C2<T> N12 = mk(lm * c.re, (lam0 - mu0) * c.im);
   const T det = mu0 * (lam0 + T(2) * mu0) * K2 * K2 + T(4) * lam0 * mu0 * c.im * c.im;
-  const T idet = scale / det;
+  const T idet = scale * rcp(det);
   const C2<T> w1 = conj(k1) * p11 + conj(k2) * p12;
   const C2<T> w2 = conj(k1) * p12 + conj(k2) * p22;
   const C2<T> v1 = idet * (N22 * w1 - N12 * w2);
