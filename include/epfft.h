@@ -180,6 +180,45 @@ int epfft_solve_batch(epfft_ctx *ctx, int32_t n, const epfft_problem *problems,
                       const epfft_fields *fields);
 
 /* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of independent solves                      */
+/* ---------------------------------------------------------------------- */
+/* Requests of any lattice side and precision queue in submission order.
+ * Each (L, precision) class advances up to slots_per_class solves together
+ * in one device-side loop (the epfft_solve_batch machinery); classes run
+ * concurrently on their own streams.  epfft_serve_step admits queued
+ * requests into free slots while the device state of the running solves
+ * stays within hbm_budget_bytes, runs every class with live solves for at
+ * most steps_per_launch loop steps, and harvests the solves that finished
+ * (cluster labels, records, optionally the final strain) and releases their
+ * device state.  A solve's results do not depend on the solves running
+ * beside it.  Results stay with the context until epfft_poll returns them. */
+typedef struct {
+  int64_t hbm_budget_bytes;  /* device bytes the resident solves may hold    */
+  int32_t slots_per_class;   /* solves of one class advanced together         */
+  int32_t steps_per_launch;  /* loop steps between admissions and harvests    */
+} epfft_serve_options;
+
+/* Starts serving on the context (one server per context). */
+int epfft_serve_open(epfft_ctx *ctx, const epfft_serve_options *opt);
+/* Stops serving; drops queued and running requests and their results. */
+int epfft_serve_close(epfft_ctx *ctx);
+/* Queues one solve (problem and path copied; a device mask is copied to the
+ * host now).  *ticket identifies it.  EPFFT_ERR_OOM if its device state
+ * alone exceeds the budget.  want_eps != 0 keeps its final strain. */
+int epfft_submit(epfft_ctx *ctx, const epfft_problem *problem, const epfft_path *path, int32_t want_eps,
+                 int64_t *ticket);
+/* One admission / device / harvest round (blocking for the device work).
+ * n_running, n_queued (optional): solves on the device, still queued. */
+int epfft_serve_step(epfft_ctx *ctx, int32_t *n_running, int32_t *n_queued);
+/* EPFFT_PENDING while the request runs or waits; then its final code
+ * (EPFFT_OK / EPFFT_NOT_CONVERGED / EPFFT_ERR_NUMERIC) with records
+ * (host, n_inc entries), the final strain in eps_host (host, L*L*4 reals of
+ * the precision, when requested at submission; may be NULL) and the time
+ * from submission to harvest in *latency_s (may be NULL).  The ticket is
+ * released once it has returned a final code. */
+int epfft_poll(epfft_ctx *ctx, int64_t ticket, epfft_record *records, void *eps_host, double *latency_s);
+
+/* ---------------------------------------------------------------------- */
 /* Steps of the iteration, for parity checks and measurement               */
 /* ---------------------------------------------------------------------- */
 

@@ -6,6 +6,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <chrono>
+#include <deque>
 #include <map>
 #include <utility>
 #include <vector>
@@ -15,6 +17,10 @@
 #include "launch.cuh"
 
 using namespace epfft;
+
+namespace {
+struct Server;
+}
 
 struct epfft_ctx {
   int device = 0;
@@ -28,6 +34,7 @@ struct epfft_ctx {
   std::map<std::pair<int, int>, void*> tables;
   std::map<std::pair<int, int>, bool> prepared;
   epfft_stats last{};
+  Server* server = nullptr;
 };
 
 namespace {
@@ -205,6 +212,66 @@ int launch_body(epfft_ctx* c, Batch& B, cudaStream_t s, cudaGraphConditionalHand
   return EPFFT_OK;
 }
 
+// Bytes of device state one solve holds while it runs.
+size_t solve_footprint(int L, int prec, int row_ctas, int n_inc) {
+  const size_t LL = (size_t)L * L, rs = real_size(prec);
+  auto r = [](size_t b) { return (b + 511) & ~(size_t)511; };
+  return r(4 * LL * rs) * 2 + r(3 * LL * rs) + r(sizeof(double) * PART_STRIDE * (size_t)row_ctas) + r(LL) +
+         r(LL * (size_t)n_inc) + r(sizeof(double) * 4 * (size_t)n_inc) + r(sizeof(Record) * (size_t)n_inc);
+}
+
+// Allocates (through `get`) and initialises the device state of one solve on
+// stream s: buffers, path, mask, starting strain (eps0: device pointer or
+// null for an unstrained lattice).  Fills the host record S.
+template <typename Get>
+int init_solve(Get&& get, const PassShape& sh, int L, int prec, const epfft_problem& p, const double* path,
+               int n_inc, const void* eps0, cudaStream_t s, Solve& S) {
+  const size_t LL = (size_t)L * L, rs = real_size(prec);
+  std::memset(&S, 0, sizeof(S));
+  S.lam = p.lambda;
+  S.mu = p.mu;
+  S.Y = p.yield_stress;
+  S.lam0 = p.lambda0;
+  S.mu0 = p.mu0;
+  S.tol_eq = p.tol_eq;
+  S.tol_macro = p.tol_macro;
+  S.max_iter = p.max_iter;
+  S.n_inc = n_inc;
+  fill_consts(S);
+  void* eps0d = get(4 * LL * rs);
+  void* eps1d = get(4 * LL * rs);
+  void* spec = get(3 * LL * rs);
+  double* part = (double*)get(sizeof(double) * PART_STRIDE * (size_t)sh.row_ctas);
+  uint8_t* mask = (uint8_t*)get(LL);
+  uint8_t* flags = (uint8_t*)get(LL * (size_t)n_inc);
+  double* dpath = (double*)get(sizeof(double) * 4 * (size_t)n_inc);
+  Record* rec = (Record*)get(sizeof(Record) * (size_t)n_inc);
+  if (!eps0d || !eps1d || !spec || !part || !mask || !flags || !dpath || !rec) return EPFFT_ERR_OOM;
+  S.eps[0] = eps0d;
+  S.eps[1] = eps1d;
+  S.spec = spec;
+  S.partials = part;
+  S.mask = mask;
+  S.flags = flags;
+  S.path = dpath;
+  S.rec = rec;
+  S.phase = PH_INIT;
+  CK(cudaMemcpyAsync(dpath, path, sizeof(double) * 4 * (size_t)n_inc, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(rec, 0, sizeof(Record) * (size_t)n_inc, s));
+  if (p.mask) {
+    CK(cudaMemcpyAsync(mask, p.mask, LL, p.mask_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  } else {
+    CK(launch_mask(mask, (int64_t)LL, p.seed, void_threshold(p.void_fraction), s));
+  }
+  if (eps0) {
+    CK(cudaMemcpyAsync(eps0d, eps0, 4 * LL * rs, cudaMemcpyDeviceToDevice, s));
+    for (int k = 0; k < 4; k++) S.Eprev[k] = path[k];
+  } else {
+    CK(cudaMemsetAsync(eps0d, 0, 4 * LL * rs, s));
+  }
+  return EPFFT_OK;
+}
+
 // Builds the device state of n problems.  eps0 (optional, device) gives the
 // starting local strain of every solve (then the first increment starts
 // from it unshifted); otherwise the lattice starts unstrained.
@@ -217,60 +284,16 @@ int setup_batch(epfft_ctx* c, Arena& A, Batch& B, int n, const epfft_problem* pr
   if (rc) return rc;
   rc = get_tables(c, B.L, B.prec, &B.tw, &B.ktab);
   if (rc) return rc;
-  const int L = B.L;
-  const size_t LL = (size_t)L * L, rs = real_size(B.prec);
   B.h_solves.resize(n);
   B.n_inc.resize(n);
   int64_t max_body = 0;
   for (int i = 0; i < n; i++) {
     const epfft_problem& p = probs[i];
-    const epfft_path& path = paths[i];
-    Solve& S = B.h_solves[i];
-    std::memset(&S, 0, sizeof(S));
-    S.lam = p.lambda;
-    S.mu = p.mu;
-    S.Y = p.yield_stress;
-    S.lam0 = p.lambda0;
-    S.mu0 = p.mu0;
-    S.tol_eq = p.tol_eq;
-    S.tol_macro = p.tol_macro;
-    S.max_iter = p.max_iter;
-    S.n_inc = path.n_inc;
-    fill_consts(S);
-    B.n_inc[i] = path.n_inc;
-    void* eps0d = A.get(4 * LL * rs);
-    void* eps1d = A.get(4 * LL * rs);
-    void* spec = A.get(3 * LL * rs);
-    double* part = (double*)A.get(sizeof(double) * PART_STRIDE * (size_t)B.sh.row_ctas);
-    uint8_t* mask = (uint8_t*)A.get(LL);
-    uint8_t* flags = (uint8_t*)A.get(LL * (size_t)path.n_inc);
-    double* dpath = (double*)A.get(sizeof(double) * 4 * (size_t)path.n_inc);
-    Record* rec = (Record*)A.get(sizeof(Record) * (size_t)path.n_inc);
-    if (!eps0d || !eps1d || !spec || !part || !mask || !flags || !dpath || !rec) return EPFFT_ERR_OOM;
-    S.eps[0] = eps0d;
-    S.eps[1] = eps1d;
-    S.spec = spec;
-    S.partials = part;
-    S.mask = mask;
-    S.flags = flags;
-    S.path = dpath;
-    S.rec = rec;
-    S.phase = PH_INIT;
-    CK(cudaMemcpyAsync(dpath, path.E, sizeof(double) * 4 * (size_t)path.n_inc, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemsetAsync(rec, 0, sizeof(Record) * (size_t)path.n_inc, c->stream));
-    if (p.mask) {
-      CK(cudaMemcpyAsync(mask, p.mask, LL, p.mask_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                         c->stream));
-    } else {
-      CK(launch_mask(mask, (int64_t)LL, p.seed, void_threshold(p.void_fraction), c->stream));
-    }
-    if (eps0 && eps0[i]) {
-      CK(cudaMemcpyAsync(eps0d, eps0[i], 4 * LL * rs, cudaMemcpyDeviceToDevice, c->stream));
-      for (int k = 0; k < 4; k++) S.Eprev[k] = path.E[k];
-    } else {
-      CK(cudaMemsetAsync(eps0d, 0, 4 * LL * rs, c->stream));
-    }
-    const int64_t need = (int64_t)path.n_inc * ((int64_t)p.max_iter + 2) + 1;
+    B.n_inc[i] = paths[i].n_inc;
+    rc = init_solve([&](size_t b) { return A.get(b); }, B.sh, B.L, B.prec, p, paths[i].E, paths[i].n_inc,
+                    eps0 ? eps0[i] : nullptr, c->stream, B.h_solves[i]);
+    if (rc) return rc;
+    const int64_t need = (int64_t)paths[i].n_inc * ((int64_t)p.max_iter + 2) + 1;
     if (need > max_body) max_body = need;
   }
   B.d_solves = (Solve*)A.get(sizeof(Solve) * (size_t)n);
@@ -285,10 +308,10 @@ int setup_batch(epfft_ctx* c, Arena& A, Batch& B, int n, const epfft_problem* pr
   return EPFFT_OK;
 }
 
-// Runs the device-side loop to completion: one graph launch whose while
-// node repeats [column pass, row pass]; the row pass's last CTA sets the
-// loop condition.
-int run_graph(epfft_ctx* c, Batch& B) {
+// One CUDA graph whose while node repeats [column pass, row pass] over the
+// batch; the row pass's last CTA sets the loop condition.  The executable
+// graph can be launched again (the loop state lives in BatchCtl).
+int build_loop_graph(epfft_ctx* c, Batch& B, cudaGraph_t* graph_out, cudaGraphExec_t* exec_out) {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int rc = EPFFT_OK;
@@ -326,15 +349,30 @@ int run_graph(epfft_ctx* c, Batch& B) {
       rc = EPFFT_ERR_CUDA;
       break;
     }
-    if (cudaGraphLaunch(exec, c->stream) != cudaSuccess) {
-      rc = EPFFT_ERR_CUDA;
-      break;
-    }
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = EPFFT_ERR_CUDA;
   } while (0);
-  if (exec) cudaGraphExecDestroy(exec);
-  if (graph) cudaGraphDestroy(graph);
-  if (rc != EPFFT_OK) cudaGetLastError();
+  if (rc != EPFFT_OK) {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return rc;
+  }
+  *graph_out = graph;
+  *exec_out = exec;
+  return EPFFT_OK;
+}
+
+// Runs the device-side loop of a batch to completion (one graph launch).
+int run_graph(epfft_ctx* c, Batch& B) {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int rc = build_loop_graph(c, B, &graph, &exec);
+  if (rc) return rc;
+  if (cudaGraphLaunch(exec, c->stream) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    rc = EPFFT_ERR_CUDA;
+    cudaGetLastError();
+  }
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
   return rc;
 }
 
@@ -514,6 +552,232 @@ int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_
   return status;
 }
 
+// ---------------------------------------------------------------------------
+// Serving: continuous batching of solves of any size
+// ---------------------------------------------------------------------------
+// Requests queue in submission order.  Each (L, precision) class owns a slot
+// table on the device (capacity fixed when the class is first used), its
+// own stream and an executable loop graph over the whole table.  A step
+// admits queued requests into free slots while the HBM budget allows, runs
+// every class with live slots for a bounded number of loop steps (the
+// classes run concurrently on their streams), then harvests the solves that
+// finished: their clusters are labelled, their records (and optionally the
+// final strain) copied to the host, and their device state released.  Empty
+// and finished slots are DONE, so the kernels skip them; a solve's
+// arithmetic does not depend on which slot it occupies or on its neighbours.
+
+struct ServeSlot {
+  bool used = false;
+  int64_t ticket = 0;
+  size_t bytes = 0;
+  std::vector<std::pair<void*, size_t>> blocks;
+};
+
+struct ServeClass {
+  int L = 0, prec = 0, cap = 0;
+  Batch B;  // L, prec, nb = cap, shape, tables, device slot table and control
+  std::vector<ServeSlot> slots;
+  cudaStream_t stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool launched = false;
+};
+
+struct Ticket {
+  int state = 0;  // 0 queued, 1 running, 2 finished
+  epfft_problem prob{};
+  std::vector<double> path;
+  std::vector<uint8_t> mask;  // caller mask copied at submission (empty: generated)
+  bool want_eps = false;
+  std::vector<Record> rec;
+  std::vector<unsigned char> eps;
+  int status = 0;
+  size_t bytes = 0;
+  double t_submit = 0, t_done = 0;
+};
+
+struct Server {
+  size_t budget = 0, used = 0;
+  int steps = 64;
+  int cap = 16;
+  int64_t next = 1;
+  std::deque<int64_t> queue;
+  std::map<int64_t, Ticket> tickets;
+  std::map<std::pair<int, int>, ServeClass*> classes;
+};
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+void free_class(epfft_ctx* c, ServeClass* k) {
+  if (k->stream) cudaStreamSynchronize(k->stream);
+  for (auto& sl : k->slots)
+    for (auto& b : sl.blocks) dev_free(c, b.first, b.second);
+  if (k->B.d_solves) dev_free(c, k->B.d_solves, sizeof(Solve) * (size_t)k->cap);
+  if (k->B.d_ctl) dev_free(c, k->B.d_ctl, sizeof(BatchCtl));
+  if (k->exec) cudaGraphExecDestroy(k->exec);
+  if (k->graph) cudaGraphDestroy(k->graph);
+  cudaStreamSynchronize(c->stream);
+  if (k->stream) cudaStreamDestroy(k->stream);
+  delete k;
+}
+
+int get_class(epfft_ctx* c, Server& S, int L, int prec, ServeClass** out) {
+  auto key = std::make_pair(L, prec);
+  auto it = S.classes.find(key);
+  if (it != S.classes.end()) {
+    *out = it->second;
+    return EPFFT_OK;
+  }
+  ServeClass* k = new ServeClass();
+  k->L = L;
+  k->prec = prec;
+  k->cap = S.cap;
+  k->slots.resize(S.cap);
+  Batch& B = k->B;
+  B.L = L;
+  B.prec = prec;
+  B.nb = S.cap;
+  int rc = shape(L, prec, &B.sh);
+  if (!rc) rc = get_tables(c, L, prec, &B.tw, &B.ktab);
+  if (!rc && cudaStreamCreateWithFlags(&k->stream, cudaStreamNonBlocking) != cudaSuccess) rc = EPFFT_ERR_CUDA;
+  if (!rc) {
+    B.d_solves = (Solve*)dev_alloc(c, sizeof(Solve) * (size_t)S.cap);
+    B.d_ctl = (BatchCtl*)dev_alloc(c, sizeof(BatchCtl));
+    if (!B.d_solves || !B.d_ctl) rc = EPFFT_ERR_OOM;
+  }
+  if (!rc) {
+    B.h_solves.assign(S.cap, Solve{});
+    for (auto& x : B.h_solves) {
+      std::memset(&x, 0, sizeof(x));
+      x.phase = PH_DONE;
+    }
+    B.n_inc.assign(S.cap, 0);
+    if (cudaMemcpyAsync(B.d_solves, B.h_solves.data(), sizeof(Solve) * (size_t)S.cap, cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      rc = EPFFT_ERR_CUDA;
+  }
+  if (!rc) rc = build_loop_graph(c, B, &k->graph, &k->exec);
+  if (rc) {
+    free_class(c, k);
+    return rc;
+  }
+  S.classes[key] = k;
+  *out = k;
+  return EPFFT_OK;
+}
+
+// Admits queued requests in submission order into free slots while the
+// budget allows; a request that does not fit yet stays queued (later ones
+// may still be admitted).
+int serve_admit(epfft_ctx* c, Server& S) {
+  for (auto qi = S.queue.begin(); qi != S.queue.end();) {
+    Ticket& t = S.tickets[*qi];
+    if (S.used + t.bytes > S.budget) {
+      ++qi;
+      continue;
+    }
+    ServeClass* k = nullptr;
+    int rc = get_class(c, S, t.prob.L, t.prob.precision, &k);
+    if (rc) return rc;
+    int slot = -1;
+    for (int i = 0; i < k->cap; i++)
+      if (!k->slots[i].used) {
+        slot = i;
+        break;
+      }
+    if (slot < 0) {
+      ++qi;
+      continue;
+    }
+    ServeSlot& sl = k->slots[slot];
+    sl.blocks.clear();
+    epfft_problem p = t.prob;
+    p.mask = t.mask.empty() ? nullptr : t.mask.data();
+    p.mask_on_device = 0;
+    Solve hs;
+    rc = init_solve(
+        [&](size_t b) {
+          void* q = dev_alloc(c, b);
+          if (q) sl.blocks.push_back({q, b});
+          return q;
+        },
+        k->B.sh, k->L, k->prec, p, t.path.data(), (int)(t.path.size() / 4), nullptr, k->stream, hs);
+    if (rc) {
+      for (auto& b : sl.blocks) dev_free(c, b.first, b.second);
+      sl.blocks.clear();
+      return rc;
+    }
+    k->B.h_solves[slot] = hs;
+    k->B.n_inc[slot] = (int)(t.path.size() / 4);
+    CK(cudaMemcpyAsync(k->B.d_solves + slot, &k->B.h_solves[slot], sizeof(Solve), cudaMemcpyHostToDevice,
+                       k->stream));
+    sl.used = true;
+    sl.ticket = *qi;
+    sl.bytes = t.bytes;
+    S.used += t.bytes;
+    t.state = 1;
+    qi = S.queue.erase(qi);
+  }
+  return EPFFT_OK;
+}
+
+// Harvests the finished solves of a class (after its stream is idle).
+int serve_harvest(epfft_ctx* c, Server& S, ServeClass* k) {
+  Batch& B = k->B;
+  std::vector<Solve> hs(k->cap);
+  CK(cudaMemcpyAsync(hs.data(), B.d_solves, sizeof(Solve) * (size_t)k->cap, cudaMemcpyDeviceToHost, k->stream));
+  CK(cudaStreamSynchronize(k->stream));
+  const size_t LL = (size_t)k->L * k->L, rs = real_size(k->prec);
+  for (int i = 0; i < k->cap; i++) {
+    ServeSlot& sl = k->slots[i];
+    if (!sl.used || hs[i].phase != PH_DONE) continue;
+    Ticket& t = S.tickets[sl.ticket];
+    const int n = B.n_inc[i];
+    t.rec.resize(n);
+    CK(cudaMemcpyAsync(t.rec.data(), hs[i].rec, sizeof(Record) * (size_t)n, cudaMemcpyDeviceToHost, k->stream));
+    if (t.want_eps) {
+      t.eps.resize(4 * LL * rs);
+      CK(cudaMemcpyAsync(t.eps.data(), hs[i].eps[hs[i].cur], 4 * LL * rs, cudaMemcpyDeviceToHost, k->stream));
+    }
+    // clusters of every accepted increment
+    int32_t* lab = (int32_t*)dev_alloc(c, sizeof(int32_t) * LL * (size_t)n);
+    int32_t* cnt = (int32_t*)dev_alloc(c, sizeof(int32_t) * ((size_t)n + 1));
+    if (!lab || !cnt) return EPFFT_ERR_OOM;
+    CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ((size_t)n + 1), k->stream));
+    CK(launch_label(hs[i].flags, lab, n, k->L, 1, cnt, cnt + n, k->stream));
+    std::vector<int32_t> hc(n + 1);
+    CK(cudaMemcpyAsync(hc.data(), cnt, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost, k->stream));
+    CK(cudaStreamSynchronize(k->stream));
+    dev_free(c, lab, sizeof(int32_t) * LL * (size_t)n);
+    dev_free(c, cnt, sizeof(int32_t) * ((size_t)n + 1));
+    int st = EPFFT_OK;
+    for (int q = 0; q < n; q++) {
+      t.rec[q].n_clusters = hc[q];
+      if (t.rec[q].status == 2) st = EPFFT_ERR_NUMERIC;
+      else if (t.rec[q].status == 1 && st == EPFFT_OK) st = EPFFT_NOT_CONVERGED;
+    }
+    if (hs[i].status == 2) st = EPFFT_ERR_NUMERIC;
+    t.status = st;
+    t.state = 2;
+    t.t_done = now_s();
+    for (auto& b : sl.blocks) dev_free(c, b.first, b.second);
+    CK(cudaStreamSynchronize(c->stream));
+    sl.blocks.clear();
+    sl.used = false;
+    S.used -= sl.bytes;
+    sl.bytes = 0;
+    // the slot is empty again (DONE state, zero pointers)
+    std::memset(&B.h_solves[i], 0, sizeof(Solve));
+    B.h_solves[i].phase = PH_DONE;
+    CK(cudaMemcpyAsync(B.d_solves + i, &B.h_solves[i], sizeof(Solve), cudaMemcpyHostToDevice, k->stream));
+  }
+  CK(cudaStreamSynchronize(k->stream));
+  return EPFFT_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -567,6 +831,7 @@ int epfft_create(epfft_ctx** out, const epfft_options* opt) {
 void epfft_destroy(epfft_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
+  if (c->server) epfft_serve_close(c);
   cudaStreamSynchronize(c->stream);
   for (auto& t : c->tables) cudaFree(t.second);
   cudaStreamDestroy(c->cap);
@@ -687,6 +952,122 @@ int epfft_label(epfft_ctx* ctx, int32_t L, int32_t n_img, const uint8_t* flags_d
   CK(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return herr ? EPFFT_ERR_DEVICE_TIMEOUT : EPFFT_OK;
+}
+
+int epfft_serve_open(epfft_ctx* ctx, const epfft_serve_options* opt) {
+  if (!ctx || !opt || opt->hbm_budget_bytes <= 0 || opt->slots_per_class < 1 || opt->steps_per_launch < 1)
+    return EPFFT_ERR_ARG;
+  if (ctx->server) return EPFFT_ERR_ARG;
+  Server* S = new Server();
+  S->budget = (size_t)opt->hbm_budget_bytes;
+  S->cap = opt->slots_per_class;
+  S->steps = opt->steps_per_launch;
+  ctx->server = S;
+  return EPFFT_OK;
+}
+
+int epfft_serve_close(epfft_ctx* ctx) {
+  if (!ctx || !ctx->server) return EPFFT_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  for (auto& kv : ctx->server->classes) free_class(ctx, kv.second);
+  delete ctx->server;
+  ctx->server = nullptr;
+  return EPFFT_OK;
+}
+
+int epfft_submit(epfft_ctx* ctx, const epfft_problem* problem, const epfft_path* path, int32_t want_eps,
+                 int64_t* ticket) {
+  if (!ctx || !ctx->server || !problem || !path || !ticket) return EPFFT_ERR_ARG;
+  int rc = check_problem(problem);
+  if (rc) return rc;
+  if (path->n_inc < 1 || !path->E) return EPFFT_ERR_ARG;
+  for (int k = 0; k < 4 * path->n_inc; k++)
+    if (!std::isfinite(path->E[k])) return EPFFT_ERR_ARG;
+  Server& S = *ctx->server;
+  PassShape sh;
+  rc = shape(problem->L, problem->precision, &sh);
+  if (rc) return rc;
+  Ticket t;
+  t.prob = *problem;
+  t.path.assign(path->E, path->E + 4 * (size_t)path->n_inc);
+  t.want_eps = want_eps != 0;
+  t.bytes = solve_footprint(problem->L, problem->precision, sh.row_ctas, path->n_inc);
+  if (t.bytes > S.budget) return EPFFT_ERR_OOM;
+  const size_t LL = (size_t)problem->L * problem->L;
+  if (problem->mask) {
+    t.mask.resize(LL);
+    if (problem->mask_on_device) {
+      if (cudaSetDevice(ctx->device) != cudaSuccess ||
+          cudaMemcpy(t.mask.data(), problem->mask, LL, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return EPFFT_ERR_CUDA;
+    } else {
+      std::memcpy(t.mask.data(), problem->mask, LL);
+    }
+  }
+  t.t_submit = now_s();
+  const int64_t id = S.next++;
+  S.tickets.emplace(id, std::move(t));
+  S.queue.push_back(id);
+  *ticket = id;
+  return EPFFT_OK;
+}
+
+int epfft_serve_step(epfft_ctx* ctx, int32_t* n_running, int32_t* n_queued) {
+  if (!ctx || !ctx->server) return EPFFT_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return EPFFT_ERR_CUDA;
+  Server& S = *ctx->server;
+  int rc = serve_admit(ctx, S);
+  if (rc) return rc;
+  std::vector<ServeClass*> live;
+  for (auto& kv : S.classes) {
+    ServeClass* k = kv.second;
+    int used = 0;
+    for (auto& sl : k->slots) used += sl.used;
+    if (!used) continue;
+    BatchCtl bc;
+    std::memset(&bc, 0, sizeof(bc));
+    bc.active = used;
+    bc.max_body_iters = S.steps;
+    CK(cudaMemcpyAsync(k->B.d_ctl, &bc, sizeof(bc), cudaMemcpyHostToDevice, k->stream));
+    CK(cudaGraphLaunch(k->exec, k->stream));
+    live.push_back(k);
+  }
+  for (ServeClass* k : live) CK(cudaStreamSynchronize(k->stream));
+  {
+    CheckRec cr;
+    CK(read_check<float>(&cr));
+    if (!cr.code) CK(read_check<double>(&cr));
+    if (cr.code) {
+      fprintf(stderr, "epfft: device self-check %d failed (index %lld, bound %lld, at %d)\n", cr.code,
+              (long long)cr.index, (long long)cr.bound, cr.where);
+      return EPFFT_ERR_CUDA;
+    }
+  }
+  for (ServeClass* k : live) {
+    rc = serve_harvest(ctx, S, k);
+    if (rc) return rc;
+  }
+  int running = 0;
+  for (auto& kv : S.classes)
+    for (auto& sl : kv.second->slots) running += sl.used;
+  if (n_running) *n_running = running;
+  if (n_queued) *n_queued = (int32_t)S.queue.size();
+  return EPFFT_OK;
+}
+
+int epfft_poll(epfft_ctx* ctx, int64_t ticket, epfft_record* records, void* eps_host, double* latency_s) {
+  if (!ctx || !ctx->server) return EPFFT_ERR_ARG;
+  Server& S = *ctx->server;
+  auto it = S.tickets.find(ticket);
+  if (it == S.tickets.end()) return EPFFT_ERR_ARG;
+  Ticket& t = it->second;
+  if (t.state != 2) return EPFFT_PENDING;
+  if (records) std::memcpy(records, t.rec.data(), sizeof(Record) * t.rec.size());
+  if (eps_host && !t.eps.empty()) std::memcpy(eps_host, t.eps.data(), t.eps.size());
+  if (latency_s) *latency_s = t.t_done - t.t_submit;
+  const int st = t.status;
+  S.tickets.erase(it);
+  return st;
 }
 
 int epfft_time_passes(epfft_ctx* ctx, const epfft_problem* problem, int32_t n_batch, const double E[4],
