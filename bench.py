@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="epfft", choices=["epfft", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--requests", type=int, default=150, help="c5: requests in the stream")
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
                     help="default: fp64 for c1/c2, fp32 for c3/c4")
     ap.add_argument("--cap", type=int, default=None, help="max iterations per increment")
@@ -56,7 +57,7 @@ def parse():
     if a.precision is None:
         a.precision = "fp64" if a.workload in ("c1", "c2") else "fp32"
     if a.cap is None:
-        a.cap = {"c1": 2000, "c2": 300, "c3": 100, "c4": 60}[a.workload]
+        a.cap = {"c1": 2000, "c2": 300, "c3": 100, "c4": 60, "c5": 20}[a.workload]
     return a
 
 
@@ -217,10 +218,86 @@ def timed_solves(B, ctx, stream, flush, probs, paths, steps, torch):
     return sum(a.elapsed_time(b) for a, b in ev) / 1e3, pix_its, launches, recs
 
 
+def run_serving(args):
+    """C5: Poisson request stream through the serving engine."""
+    import torch
+    from paper_0802_2488_gb300 import binding as B
+    from paper_0802_2488_gb300 import build
+    from paper_0802_2488_gb300 import inputs
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    ctx = B.Context(local)
+
+    def prob(r):
+        P = r.problem
+        return B.Problem(L=P.L, precision=args.precision, void_fraction=P.f, seed=P.seed, tol_eq=1e-8,
+                         tol_macro=1e-8, max_iter=args.cap)
+
+    # solo capacity: a few requests run back to back, one at a time
+    probe = inputs.serving_stream(12, 1.0, seed=1000 + rank)
+    for r in probe[:2]:
+        B.epfft_solve(ctx, prob(r), r.problem.path)
+    t0 = time.perf_counter()
+    for r in probe[2:]:
+        B.epfft_solve(ctx, prob(r), r.problem.path)
+    solo = (len(probe) - 2) / (time.perf_counter() - t0)
+    rate = 0.7 * solo
+    reqs = inputs.serving_stream(args.requests, rate, seed=rank)
+    budget = 16 << 30
+    B.epfft_serve_open(ctx, budget, 16, 32)
+    lat, pix = [], 0
+    tickets = {}
+    nxt = 0
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        while nxt < len(reqs) or tickets:
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and reqs[nxt].arrival_s <= now:
+                r = reqs[nxt]
+                tickets[nxt] = (B.epfft_submit(ctx, prob(r), r.problem.path), r)
+                nxt += 1
+            if not tickets:
+                time.sleep(max(0.0, min(0.01, reqs[nxt].arrival_s - now)))
+                continue
+            B.epfft_serve_step(ctx)
+            done_t = time.perf_counter() - t0
+            for i, (t, r) in list(tickets.items()):
+                res = B.epfft_poll(ctx, t, prob(r), r.problem.n_inc)
+                if res is not None:
+                    lat.append(done_t - r.arrival_s)
+                    pix += r.problem.L ** 2 * int(res[1]["iterations"].sum())
+                    del tickets[i]
+        total = time.perf_counter() - t0
+    B.epfft_serve_close(ctx)
+    clocks = clk.summary()
+    lat = np.array(lat)
+    out = {
+        "metric": METRIC, "value": ws * pix / total, "unit": UNIT, "n_gpus": ws, "steps": 1, "warmup": 0,
+        "ms_per_step": 1e3 * total, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": f"Poisson stream of {len(reqs)} requests at {rate:.2f}/s (70% of the measured "
+                               f"solo capacity {solo:.2f}/s): L uniform in {{128,256,512,1024}}, f uniform in "
+                               f"[0.05,0.35], equibiaxial or shear, 10-50 increments, seed = request id; at most "
+                               f"{args.cap} iterations per increment; HBM budget 16 GiB, 16 slots per size",
+                   "rate_per_s": rate, "solo_capacity_per_s": solo,
+                   "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+                   "solves_per_s": len(lat) / total, "precision": args.precision, "parallelism": "single GPU",
+                   "l2": "inputs of the running set exceed L2 at the larger sizes; not flushed"},
+        "e2e": {"value": ws * pix / total, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": None, "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c5":
+        return run_serving(args)
     import torch
     ws, rank, local = dist_env()
     if ws > 1:

@@ -35,7 +35,8 @@ EPFFT_GREEN_EQ3 = 0
 
 SYMBOLS = ["epfft_create", "epfft_destroy", "epfft_last_stats", "epfft_strerror", "epfft_supported",
            "epfft_solve", "epfft_solve_batch", "epfft_mask", "epfft_iterate", "epfft_project", "epfft_label",
-           "epfft_time_passes", "epfft_project_static"]
+           "epfft_time_passes", "epfft_project_static", "epfft_serve_open", "epfft_serve_close",
+           "epfft_submit", "epfft_serve_step", "epfft_poll"]
 
 
 class EpfftError(RuntimeError):
@@ -68,6 +69,10 @@ class _Path(C.Structure):
 
 class _Stats(C.Structure):
     _fields_ = [("loop_steps", C.c_int64), ("kernel_launches", C.c_int64), ("iterations", C.c_int64)]
+
+
+class _ServeOptions(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("slots_per_class", C.c_int32), ("steps_per_launch", C.c_int32)]
 
 
 class _Fields(C.Structure):
@@ -105,6 +110,11 @@ def lib():
         L.epfft_iterate.argtypes = [vp, C.POINTER(_Problem), C.POINTER(dbl), vp, i32, vp]
         L.epfft_project.argtypes = [vp, i32, i32, dbl, dbl, C.POINTER(dbl), vp, vp]
         L.epfft_label.argtypes = [vp, i32, i32, vp, i32, vp, vp]
+        L.epfft_serve_open.argtypes = [vp, C.POINTER(_ServeOptions)]
+        L.epfft_serve_close.argtypes = [vp]
+        L.epfft_submit.argtypes = [vp, C.POINTER(_Problem), C.POINTER(_Path), i32, C.POINTER(C.c_int64)]
+        L.epfft_serve_step.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+        L.epfft_poll.argtypes = [vp, C.c_int64, vp, vp, C.POINTER(dbl)]
         L.epfft_project_static.argtypes = [i32, i32, dbl, dbl, C.POINTER(dbl), vp, vp, vp]
         L.epfft_time_passes.argtypes = [vp, C.POINTER(_Problem), i32, C.POINTER(dbl), i32, C.POINTER(C.c_float),
                                         C.POINTER(C.c_float)]
@@ -373,3 +383,45 @@ def epfft_project_static(L: int, precision: str, lambda0: float, mu0: float, E, 
            "epfft_project_static")
     s.synchronize()
     return e
+
+
+# --------------------------------------------------------------------------
+# Serving (continuous batching)
+# --------------------------------------------------------------------------
+
+def epfft_serve_open(ctx: Context, hbm_budget_bytes: int, slots_per_class: int = 16, steps_per_launch: int = 64):
+    _check(lib().epfft_serve_open(ctx.handle, C.byref(_ServeOptions(int(hbm_budget_bytes), int(slots_per_class),
+                                                                     int(steps_per_launch)))), "epfft_serve_open")
+
+
+def epfft_serve_close(ctx: Context):
+    _check(lib().epfft_serve_close(ctx.handle), "epfft_serve_close")
+
+
+def epfft_submit(ctx: Context, problem: Problem, path, want_eps: bool = False) -> int:
+    p, keep = problem._c()
+    cp, parr = _path(path)
+    t = C.c_int64()
+    _check(lib().epfft_submit(ctx.handle, C.byref(p), C.byref(cp), 1 if want_eps else 0, C.byref(t)),
+           "epfft_submit")
+    return t.value
+
+
+def epfft_serve_step(ctx: Context) -> tuple[int, int]:
+    """One admission / device / harvest round; returns (running, queued)."""
+    r, q = C.c_int32(), C.c_int32()
+    _check(lib().epfft_serve_step(ctx.handle, C.byref(r), C.byref(q)), "epfft_serve_step")
+    return r.value, q.value
+
+
+def epfft_poll(ctx: Context, ticket: int, problem: Problem, n_inc: int, want_eps: bool = False):
+    """None while pending; else (rc, records, eps or None, latency seconds)."""
+    rec = np.zeros(n_inc, dtype=RECORD_DTYPE)
+    eps = np.empty((problem.L, problem.L, 4), dtype=problem.real_dtype) if want_eps else None
+    lat = C.c_double()
+    rc = lib().epfft_poll(ctx.handle, int(ticket), rec.ctypes.data, eps.ctypes.data if eps is not None else None,
+                          C.byref(lat))
+    if rc == EPFFT_PENDING:
+        return None
+    _check(rc, "epfft_poll", (EPFFT_OK, EPFFT_NOT_CONVERGED))
+    return rc, rec, eps, lat.value
