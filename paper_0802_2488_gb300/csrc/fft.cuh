@@ -136,14 +136,16 @@ __device__ __forceinline__ void fft_stages(C2<T>* s, const C2<T>* __restrict__ t
   }
 }
 
-// NG groups of NB sequences interleaved with stride XS = NG * NB (group g
-// starts at s + g * NB).  The groups are transformed together when every
-// thread holds at most 16 elements per stage, else one group at a time.
-template <typename T, int N, int NG, int NB, int NT, bool INV>
+// NG groups of NB sequences; element x of sequence b of group g is at
+// s[x * XS + g * NB + b] (XS >= NG * NB; XS is chosen odd by the callers so
+// that element strides do not fold onto few shared-memory banks).  The groups
+// are transformed together when every thread holds at most 16 elements per
+// stage, else one group at a time.
+template <typename T, int N, int NG, int NB, int XS, int NT, bool INV>
 __device__ __forceinline__ void fft_block(C2<T>* s, const C2<T>* __restrict__ tw, int twstride) {
-  constexpr int XS = NG * NB;
-  if constexpr ((XS * N + NT - 1) / NT <= 16) {
-    fft_stages<T, N, XS, XS, NT, INV>(s, tw, twstride);
+  static_assert(XS >= NG * NB, "element stride too small");
+  if constexpr ((NG * NB * N + NT - 1) / NT <= 16) {
+    fft_stages<T, N, NG * NB, XS, NT, INV>(s, tw, twstride);
   } else {
 #pragma unroll 1
     for (int g = 0; g < NG; g++) fft_stages<T, N, NB, XS, NT, INV>(s + g * NB, tw, twstride);

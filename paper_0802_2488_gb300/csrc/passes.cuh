@@ -33,17 +33,23 @@ struct Cfg {
   static constexpr int M = L / 2;
   // rows per row-pass CTA (small lattices: more, smaller CTAs to fill the
   // SMs; large ones: RR x W complex numbers of a tile row span >= 64 bytes)
-  static constexpr int RR = F64 ? (L <= 256 ? 1 : (L <= 512 ? 2 : 4))
+  static constexpr int RR = F64 ? (L <= 512 ? 2 : 4)
                                 : (L <= 256 ? 2 : (L <= 1024 ? 8 : 4));
   // columns per column-pass CTA (= tile width of the spectrum layout)
   static constexpr int W0 = F64 ? (L <= 256 ? 1 : (L <= 512 ? 2 : (L <= 1024 ? 4 : 2)))
                                 : (L <= 256 ? 2 : (L <= 512 ? 8 : (L <= 2048 ? 4 : 2)));
   static constexpr int W = W0 < M ? W0 : M;
-  static constexpr int NT_ROW = L < 32 ? 32 : (L > 512 ? 512 : L);
+  // threads per row-pass CTA: 256 from L = 512 to 2048 so that two CTAs
+  // (each with up to 128 registers per thread) share an SM
+  static constexpr int NT_ROW = L < 32 ? 32 : (L <= 256 ? L : (L <= 2048 ? 256 : 512));
   static constexpr int NT_COL0 = ((3 * W * L / 8 + 31) / 32) * 32;
   static constexpr int NT_COL = NT_COL0 < 32 ? 32 : (NT_COL0 > 512 ? 512 : NT_COL0);
-  static constexpr size_t ROW_SMEM = (size_t)3 * RR * M * sizeof(C2<T>) + (size_t)2 * L * sizeof(T);
-  static constexpr size_t COL_SMEM = (size_t)3 * W * L * sizeof(C2<T>);
+  // element strides of the interleaved shared-memory batches, made odd so
+  // that consecutive elements of one sequence fall on distinct banks
+  static constexpr int XR = (3 * RR) % 2 == 0 ? 3 * RR + 1 : 3 * RR;
+  static constexpr int XC = (3 * W) % 2 == 0 ? 3 * W + 1 : 3 * W;
+  static constexpr size_t ROW_SMEM = (size_t)XR * M * sizeof(C2<T>);
+  static constexpr size_t COL_SMEM = (size_t)XC * L * sizeof(C2<T>);
   static_assert(L >= 4 && (L & (L - 1)) == 0, "L must be a power of two >= 4");
   static_assert(M % W == 0, "tile width must divide L/2");
   static_assert(L % RR == 0, "rows per CTA must divide L");
@@ -79,34 +85,73 @@ struct Vec4<double> {
 
 // ---------------------------------------------------------------------------
 // Row-side helpers.  Shared-memory layout of the RR rows: element n of
-// component c of row r at sp[n * 3RR + c * RR + r].
+// component c of row r at sp[n * XS + c * RR + r], XS = 3RR rounded up to odd.
 // ---------------------------------------------------------------------------
 template <typename T, int L, int RR, int W, int NT>
 struct RowIO {
   static constexpr int M = L / 2, NB = 3 * RR, NBK = M / W;
+  static constexpr int XS = NB % 2 == 0 ? NB + 1 : NB;  // element stride (odd)
+
+  // Position of chunk element e (c, b, r, w) in shared and global memory.
+  static __device__ __forceinline__ void where(int e, int r0, int& is, size_t& ig) {
+    const int c = e / (M * RR);
+    const int rem = e - c * (M * RR);
+    const int b = rem / (RR * W);
+    const int rem2 = rem - b * (RR * W);
+    const int r = rem2 / W, w = rem2 - r * W;
+    is = (b * W + w) * XS + c * RR + r;
+    ig = ((size_t)(c * NBK + b) * L + r0 + r) * W + w;
+  }
+  // FP32 complex numbers are moved two at a time (16-byte accesses) when a
+  // tile chunk (RR x W numbers, contiguous in HBM) has even length.
+  static constexpr bool PAIRS = sizeof(C2<T>) == 8 && (RR * W) % 2 == 0;
 
   static __device__ __forceinline__ void load(C2<T>* sp, const C2<T>* __restrict__ spec, int r0) {
-    for (int e = threadIdx.x; e < 3 * M * RR; e += NT) {
-      const int c = e / (M * RR);
-      const int rem = e - c * (M * RR);
-      const int b = rem / (RR * W);
-      const int rem2 = rem - b * (RR * W);
-      const int r = rem2 / W, w = rem2 - r * W;
-      const int is = (b * W + w) * NB + c * RR + r;
-      const size_t ig = ((size_t)(c * NBK + b) * L + r0 + r) * W + w;
-      if (ECHK(is, M * NB, 1) && ECHK(ig, (size_t)3 * M * L, 2)) sp[is] = spec[ig];
+    if constexpr (PAIRS) {
+#pragma unroll 4
+      for (int e2 = threadIdx.x; e2 < 3 * M * RR / 2; e2 += NT) {
+        int is0, is1;
+        size_t ig0, ig1;
+        where(2 * e2, r0, is0, ig0);
+        where(2 * e2 + 1, r0, is1, ig1);
+        if (ECHK(is0, M * XS, 1) && ECHK(is1, M * XS, 1) && ECHK(ig0 + 1, (size_t)3 * M * L, 2)) {
+          const float4 v = *reinterpret_cast<const float4*>(spec + ig0);
+          reinterpret_cast<float2*>(sp)[is0] = make_float2(v.x, v.y);
+          reinterpret_cast<float2*>(sp)[is1] = make_float2(v.z, v.w);
+        }
+      }
+    } else {
+#pragma unroll 4
+      for (int e = threadIdx.x; e < 3 * M * RR; e += NT) {
+        int is;
+        size_t ig;
+        where(e, r0, is, ig);
+        if (ECHK(is, M * XS, 1) && ECHK(ig, (size_t)3 * M * L, 2)) sp[is] = spec[ig];
+      }
     }
   }
   static __device__ __forceinline__ void store(const C2<T>* sp, C2<T>* __restrict__ spec, int r0) {
-    for (int e = threadIdx.x; e < 3 * M * RR; e += NT) {
-      const int c = e / (M * RR);
-      const int rem = e - c * (M * RR);
-      const int b = rem / (RR * W);
-      const int rem2 = rem - b * (RR * W);
-      const int r = rem2 / W, w = rem2 - r * W;
-      const int is = (b * W + w) * NB + c * RR + r;
-      const size_t ig = ((size_t)(c * NBK + b) * L + r0 + r) * W + w;
-      if (ECHK(is, M * NB, 3) && ECHK(ig, (size_t)3 * M * L, 4)) spec[ig] = sp[is];
+    if constexpr (PAIRS) {
+#pragma unroll 4
+      for (int e2 = threadIdx.x; e2 < 3 * M * RR / 2; e2 += NT) {
+        int is0, is1;
+        size_t ig0, ig1;
+        where(2 * e2, r0, is0, ig0);
+        where(2 * e2 + 1, r0, is1, ig1);
+        if (ECHK(is0, M * XS, 3) && ECHK(is1, M * XS, 3) && ECHK(ig0 + 1, (size_t)3 * M * L, 4)) {
+          const float2 a = reinterpret_cast<const float2*>(sp)[is0];
+          const float2 b = reinterpret_cast<const float2*>(sp)[is1];
+          *reinterpret_cast<float4*>(spec + ig0) = make_float4(a.x, a.y, b.x, b.y);
+        }
+      }
+    } else {
+#pragma unroll 4
+      for (int e = threadIdx.x; e < 3 * M * RR; e += NT) {
+        int is;
+        size_t ig;
+        where(e, r0, is, ig);
+        if (ECHK(is, M * XS, 3) && ECHK(ig, (size_t)3 * M * L, 4)) spec[ig] = sp[is];
+      }
     }
   }
   // Half spectrum (packed) -> Z for the half-length inverse transform:
@@ -124,12 +169,12 @@ struct RowIO {
         s[0] = mk(s0.re + s0.im, s0.re - s0.im);
       } else {
         const int kk = M - k;
-        if (!ECHK(k * NB + cr, M * NB, 5) || !ECHK(kk * NB + cr, M * NB, 6)) continue;
-        const C2<T> a = s[k * NB], b = s[kk * NB];
+        if (!ECHK(k * XS + cr, M * XS, 5) || !ECHK(kk * XS + cr, M * XS, 6)) continue;
+        const C2<T> a = s[k * XS], b = s[kk * XS];
         const C2<T> wk = conj(tw[k]);
         const C2<T> zk = (a + conj(b)) + mul_i(wk * (a - conj(b)));
-        s[k * NB] = zk;
-        if (kk != k) s[kk * NB] = (b + conj(a)) - mul_i(conj(wk) * (b - conj(a)));
+        s[k * XS] = zk;
+        if (kk != k) s[kk * XS] = (b + conj(a)) - mul_i(conj(wk) * (b - conj(a)));
       }
     }
   }
@@ -146,23 +191,23 @@ struct RowIO {
         s[0] = mk(z.re + z.im, z.re - z.im);
       } else {
         const int kk = M - k;
-        if (!ECHK(k * NB + cr, M * NB, 7) || !ECHK(kk * NB + cr, M * NB, 8)) continue;
-        const C2<T> a = s[k * NB], b = s[kk * NB];
+        if (!ECHK(k * XS + cr, M * XS, 7) || !ECHK(kk * XS + cr, M * XS, 8)) continue;
+        const C2<T> a = s[k * XS], b = s[kk * XS];
         const C2<T> wk = tw[k];
-        s[k * NB] = T(0.5) * ((a + conj(b)) - mul_i(wk * (a - conj(b))));
-        if (kk != k) s[kk * NB] = T(0.5) * ((b + conj(a)) + mul_i(conj(wk) * (b - conj(a))));
+        s[k * XS] = T(0.5) * ((a + conj(b)) - mul_i(wk * (a - conj(b))));
+        if (kk != k) s[kk * XS] = T(0.5) * ((b + conj(a)) + mul_i(conj(wk) * (b - conj(a))));
       }
     }
   }
   template <bool INV>
   static __device__ __forceinline__ void fft(C2<T>* sp, const C2<T>* __restrict__ tw) {
     // three groups (components) of RR rows each
-    fft_block<T, M, 3, RR, NT, INV>(sp, tw, 2);
+    fft_block<T, M, 3, RR, XS, NT, INV>(sp, tw, 2);
   }
   // real value of pixel x1 of component c, row r
   static __device__ __forceinline__ T& px(C2<T>* sp, int c, int r, int x1) {
-    const int ix = 2 * ((x1 >> 1) * NB + c * RR + r) + (x1 & 1);
-    return reinterpret_cast<T*>(sp)[ECHK(ix, 2 * M * NB, 9) ? ix : 0];
+    const int ix = 2 * ((x1 >> 1) * XS + c * RR + r) + (x1 & 1);
+    return reinterpret_cast<T*>(sp)[ECHK(ix, 2 * M * XS, 9) ? ix : 0];
   }
 };
 
@@ -362,7 +407,6 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
   using IO = RowIO<T, L, RR, W, NT>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C2<T>* sp = reinterpret_cast<C2<T>*>(smraw);
-  T* sb = reinterpret_cast<T*>(sp + 3 * RR * M);  // sigma11, sigma12 of the current row
   __shared__ bool s_last;
 
   Solve& S = solves[blockIdx.y];
@@ -449,32 +493,56 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
           prev22[j] = s[1];
         }
       }
+      // Left neighbours (x - e^1) for the divergence: the previous lane by a
+      // warp shuffle; lane 0 takes the last lane of the previous warp (or of
+      // the last warp, one pixel group back) from a small per-row exchange,
+      // double-buffered by row parity so one barrier per row suffices.
+      constexpr int NW = NT / 32;
+      __shared__ T edge[2][2][NW][P];
+      const int lane = tid & 31, wid = tid >> 5;
       for (int r = 0; r < RR; r++) {
+        const int par = r & 1;
         T en[P][4], s[P][4];
         bool vv[P];
 #pragma unroll
         for (int j = 0; j < P; j++) {
           const int x1 = tid + j * NT;
-          if (x1 >= L) continue;
           const size_t x = (size_t)(r0 + r) * L + x1;
-          if (!ECHK(x, LL, 23) || !ECHK(L + x1, 2 * L, 24)) continue;
-          vv[j] = mask[x] != 0;
-          Vec4<T>::load(ein + 4 * x, en[j]);
+          const bool act = x1 < L && ECHK(x, LL, 23);
+          vv[j] = act ? mask[x] != 0 : true;
+          if (act) Vec4<T>::load(ein + 4 * x, en[j]);
+          else en[j][0] = en[j][1] = en[j][2] = en[j][3] = T(0);
           const bool pl = sigma(en[j], vv[j], m, s[j]);
           acc[A_NPL] += pl ? T(1) : T(0);
-          sb[x1] = s[j][0];
-          sb[L + x1] = s[j][3];
+          if (L >= 32 && lane == 31) {
+            edge[par][0][wid][j] = s[j][0];
+            edge[par][1][wid][j] = s[j][3];
+          }
         }
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < P; j++) {
+          T l11, l12;
+          if constexpr (L < 32) {
+            const int src = (lane + L - 1) & (L - 1);
+            l11 = __shfl_sync(0xffffffffu, s[j][0], src);
+            l12 = __shfl_sync(0xffffffffu, s[j][3], src);
+          } else {
+            l11 = __shfl_up_sync(0xffffffffu, s[j][0], 1);
+            l12 = __shfl_up_sync(0xffffffffu, s[j][3], 1);
+            if (lane == 0) {
+              const int pw = wid > 0 ? wid - 1 : NW - 1;
+              const int pj = wid > 0 ? j : (j + P - 1) % P;
+              l11 = edge[par][0][pw][pj];
+              l12 = edge[par][1][pw][pj];
+            }
+          }
           const int x1 = tid + j * NT;
           if (x1 >= L) continue;
           const size_t x = (size_t)(r0 + r) * L + x1;
-          const int xl = (x1 + L - 1) & (L - 1);
           // Eq. 1: div_i = sum_j sigma_ij(x) - sigma_ij(x - e^j)
-          const T d1 = (s[j][0] - sb[xl]) + (s[j][3] - prev12[j]);
-          const T d2 = (s[j][3] - sb[L + xl]) + (s[j][1] - prev22[j]);
+          const T d1 = (s[j][0] - l11) + (s[j][3] - prev12[j]);
+          const T d2 = (s[j][3] - l12) + (s[j][1] - prev22[j]);
           prev12[j] = s[j][3];
           prev22[j] = s[j][1];
 #pragma unroll
@@ -500,7 +568,6 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
           IO::px(sp, 1, r, x1) = s1[1] - c0[1];
           IO::px(sp, 2, r, x1) = s1[3] - c0[3];
         }
-        __syncthreads();
       }
     }
 
@@ -547,9 +614,10 @@ __global__ void __launch_bounds__(Cfg<T, L>::NT_COL)
 col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* __restrict__ ktab,
          cudaGraphConditionalHandle cond, int use_cond) {
   using C = Cfg<T, L>;
-  constexpr int W = C::W, NT = C::NT_COL, M = C::M, NB = 3 * W, NBK = M / W;
+  constexpr int W = C::W, NT = C::NT_COL, M = C::M, NBK = M / W;
+  constexpr int XS = C::XC;  // element stride (3W rounded up to odd)
   extern __shared__ __align__(16) unsigned char smraw[];
-  C2<T>* sp = reinterpret_cast<C2<T>*>(smraw);  // element (c, w) of row x2 at sp[x2*NB + c*W + w]
+  C2<T>* sp = reinterpret_cast<C2<T>*>(smraw);  // element (c, w) of row x2 at sp[x2*XS + c*W + w]
   const int tid = threadIdx.x;
   // The row pass that follows re-arms the loop; a body that never reaches
   // it must not loop again.
@@ -560,14 +628,29 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
   const int inc = Sv.inc;
   const int b = blockIdx.x;
   C2<T>* spec = reinterpret_cast<C2<T>*>(S.spec);
-  for (int e = tid; e < 3 * L * W; e += NT) {
-    const int c = e / (L * W);
-    const int rem = e - c * (L * W);
-    const int x2 = rem / W, w = rem - x2 * W;
-    sp[x2 * NB + c * W + w] = spec[(size_t)(c * NBK + b) * L * W + rem];
+  // the slab of each component is contiguous in HBM; FP32 numbers move in pairs
+  if constexpr (sizeof(C2<T>) == 8) {
+#pragma unroll 4
+    for (int e2 = tid; e2 < 3 * L * W / 2; e2 += NT) {
+      const int e = 2 * e2;
+      const int c = e / (L * W);
+      const int rem = e - c * (L * W);
+      const int xa = rem / W, wa = rem - xa * W, xb = (rem + 1) / W, wb = rem + 1 - xb * W;
+      const float4 v = *reinterpret_cast<const float4*>(spec + (size_t)(c * NBK + b) * L * W + rem);
+      reinterpret_cast<float2*>(sp)[xa * XS + c * W + wa] = make_float2(v.x, v.y);
+      reinterpret_cast<float2*>(sp)[xb * XS + c * W + wb] = make_float2(v.z, v.w);
+    }
+  } else {
+#pragma unroll 4
+    for (int e = tid; e < 3 * L * W; e += NT) {
+      const int c = e / (L * W);
+      const int rem = e - c * (L * W);
+      const int x2 = rem / W, w = rem - x2 * W;
+      sp[x2 * XS + c * W + w] = spec[(size_t)(c * NBK + b) * L * W + rem];
+    }
   }
   __syncthreads();
-  fft_block<T, L, 3, W, NT, false>(sp, tw, 1);
+  fft_block<T, L, 3, W, XS, NT, false>(sp, tw, 1);
 
   const T lam0 = T(S.lam0), mu0 = T(S.mu0);
   const T scale = T(1.0 / ((double)L * (double)L));
@@ -576,7 +659,7 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
     const int m2 = f / W, w = f - m2 * W;
     const int m1 = b * W + w;
     if (m1 == 0) continue;
-    C2<T>* q = sp + m2 * NB + w;
+    C2<T>* q = sp + m2 * XS + w;
     C2<T> p11 = q[0], p22 = q[W], p12 = q[2 * W];
     green_apply(ktab[m1], ktab[m2], lam0, mu0, scale, p11, p22, p12);
     q[0] = p11;
@@ -592,7 +675,7 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
       C2<T> A[3], B[3], Ap[3], Bp[3];
 #pragma unroll
       for (int c = 0; c < 3; c++) {
-        const C2<T> z = sp[m2 * NB + c * W], zp = sp[mp * NB + c * W];
+        const C2<T> z = sp[m2 * XS + c * W], zp = sp[mp * XS + c * W];
         A[c] = T(0.5) * (z + conj(zp));
         const C2<T> d = z - conj(zp);  // B = d / (2i)
         B[c] = mk(T(0.5) * d.im, T(-0.5) * d.re);
@@ -611,18 +694,32 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
       green_apply(ktab[M], ktab[mp], lam0, mu0, scale, Bp[0], Bp[1], Bp[2]);
 #pragma unroll
       for (int c = 0; c < 3; c++) {
-        sp[m2 * NB + c * W] = A[c] + mul_i(B[c]);
-        if (mp != m2) sp[mp * NB + c * W] = Ap[c] + mul_i(Bp[c]);
+        sp[m2 * XS + c * W] = A[c] + mul_i(B[c]);
+        if (mp != m2) sp[mp * XS + c * W] = Ap[c] + mul_i(Bp[c]);
       }
     }
   }
   __syncthreads();
-  fft_block<T, L, 3, W, NT, true>(sp, tw, 1);
-  for (int e = tid; e < 3 * L * W; e += NT) {
-    const int c = e / (L * W);
-    const int rem = e - c * (L * W);
-    const int x2 = rem / W, w = rem - x2 * W;
-    spec[(size_t)(c * NBK + b) * L * W + rem] = sp[x2 * NB + c * W + w];
+  fft_block<T, L, 3, W, XS, NT, true>(sp, tw, 1);
+  if constexpr (sizeof(C2<T>) == 8) {
+#pragma unroll 4
+    for (int e2 = tid; e2 < 3 * L * W / 2; e2 += NT) {
+      const int e = 2 * e2;
+      const int c = e / (L * W);
+      const int rem = e - c * (L * W);
+      const int xa = rem / W, wa = rem - xa * W, xb = (rem + 1) / W, wb = rem + 1 - xb * W;
+      const float2 u = reinterpret_cast<const float2*>(sp)[xa * XS + c * W + wa];
+      const float2 v = reinterpret_cast<const float2*>(sp)[xb * XS + c * W + wb];
+      *reinterpret_cast<float4*>(spec + (size_t)(c * NBK + b) * L * W + rem) = make_float4(u.x, u.y, v.x, v.y);
+    }
+  } else {
+#pragma unroll 4
+    for (int e = tid; e < 3 * L * W; e += NT) {
+      const int c = e / (L * W);
+      const int rem = e - c * (L * W);
+      const int x2 = rem / W, w = rem - x2 * W;
+      spec[(size_t)(c * NBK + b) * L * W + rem] = sp[x2 * XS + c * W + w];
+    }
   }
 }
 
