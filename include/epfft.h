@@ -283,6 +283,20 @@ int epfft_label(epfft_ctx *ctx, int32_t L, int32_t n_img, const uint8_t *flags_d
 int epfft_time_passes(epfft_ctx *ctx, const epfft_problem *problem, int32_t n_batch, const double E[4],
                       int32_t n_iter, float *col_ms, float *row_ms);
 
+/* ---------------------------------------------------------------------- */
+/* Tiling (FFT tile shapes and CTA sizes per lattice side)                 */
+/* ---------------------------------------------------------------------- */
+/* Two tilings are compiled for every lattice side and precision (rows per
+ * row-pass CTA, tile width of the spectrum layout = columns per
+ * column-pass CTA, threads).  epfft_autotune times both on this device
+ * (CUDA events, synthetic f = 0.2 lattice) and makes the faster one the
+ * context's tiling for (L, precision); *chosen receives it and
+ * ms_per_iteration[2] (optional) the two timings.  Later solves, batches,
+ * projections and serving classes of that size use it.  Blocking. */
+int epfft_autotune(epfft_ctx *ctx, int32_t L, int32_t precision, int32_t *chosen, float *ms_per_iteration);
+/* Sets the tiling (0 or 1) of (L, precision) on the context. */
+int epfft_set_tiling(epfft_ctx *ctx, int32_t L, int32_t precision, int32_t variant);
+
 #ifdef __cplusplus
 }
 #endif

@@ -36,7 +36,7 @@ EPFFT_GREEN_EQ3 = 0
 SYMBOLS = ["epfft_create", "epfft_destroy", "epfft_last_stats", "epfft_strerror", "epfft_supported",
            "epfft_solve", "epfft_solve_batch", "epfft_mask", "epfft_iterate", "epfft_project", "epfft_label",
            "epfft_time_passes", "epfft_project_static", "epfft_serve_open", "epfft_serve_close",
-           "epfft_submit", "epfft_serve_step", "epfft_poll"]
+           "epfft_submit", "epfft_serve_step", "epfft_poll", "epfft_autotune", "epfft_set_tiling"]
 
 
 class EpfftError(RuntimeError):
@@ -115,6 +115,8 @@ def lib():
         L.epfft_submit.argtypes = [vp, C.POINTER(_Problem), C.POINTER(_Path), i32, C.POINTER(C.c_int64)]
         L.epfft_serve_step.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
         L.epfft_poll.argtypes = [vp, C.c_int64, vp, vp, C.POINTER(dbl)]
+        L.epfft_autotune.argtypes = [vp, i32, i32, C.POINTER(i32), C.POINTER(C.c_float)]
+        L.epfft_set_tiling.argtypes = [vp, i32, i32, i32]
         L.epfft_project_static.argtypes = [i32, i32, dbl, dbl, C.POINTER(dbl), vp, vp, vp]
         L.epfft_time_passes.argtypes = [vp, C.POINTER(_Problem), i32, C.POINTER(dbl), i32, C.POINTER(C.c_float),
                                         C.POINTER(C.c_float)]
@@ -425,3 +427,22 @@ def epfft_poll(ctx: Context, ticket: int, problem: Problem, n_inc: int, want_eps
         return None
     _check(rc, "epfft_poll", (EPFFT_OK, EPFFT_NOT_CONVERGED))
     return rc, rec, eps, lat.value
+
+
+# --------------------------------------------------------------------------
+# Tiling
+# --------------------------------------------------------------------------
+
+def epfft_autotune(ctx: Context, L: int, precision: str):
+    """Times the compiled tilings of (L, precision) and keeps the faster for the
+    context.  Returns (chosen tiling, [ms per iteration of each])."""
+    ch = C.c_int32()
+    ms = (C.c_float * 2)()
+    _check(lib().epfft_autotune(ctx.handle, L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision], C.byref(ch), ms),
+           "epfft_autotune")
+    return ch.value, list(ms)
+
+
+def epfft_set_tiling(ctx: Context, L: int, precision: str, variant: int):
+    _check(lib().epfft_set_tiling(ctx.handle, L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision], int(variant)),
+           "epfft_set_tiling")

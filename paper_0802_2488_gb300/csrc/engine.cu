@@ -9,6 +9,7 @@
 #include <chrono>
 #include <deque>
 #include <map>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -32,7 +33,8 @@ struct epfft_ctx {
   void* user = nullptr;
   // (L, precision) -> device table: tw[L] then ktab[L] (complex of precision)
   std::map<std::pair<int, int>, void*> tables;
-  std::map<std::pair<int, int>, bool> prepared;
+  std::map<std::tuple<int, int, int>, bool> prepared;  // (L, precision, tiling variant)
+  std::map<std::pair<int, int>, int> variant;          // tuned tiling per (L, precision)
   epfft_stats last{};
   Server* server = nullptr;
 };
@@ -85,13 +87,13 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 bool supported(int L, int prec) {
   PassShape sh;
   if (!is_pow2(L) || L < 4) return false;
-  if (prec == EPFFT_FP32) return pass_shape<float>(L, &sh);
-  if (prec == EPFFT_FP64) return pass_shape<double>(L, &sh);
+  if (prec == EPFFT_FP32) return pass_shape<float>(L, 0, &sh);
+  if (prec == EPFFT_FP64) return pass_shape<double>(L, 0, &sh);
   return false;
 }
 
-int shape(int L, int prec, PassShape* sh) {
-  bool ok = prec == EPFFT_FP32 ? pass_shape<float>(L, sh) : pass_shape<double>(L, sh);
+int shape(int L, int prec, int var, PassShape* sh) {
+  bool ok = prec == EPFFT_FP32 ? pass_shape<float>(L, var, sh) : pass_shape<double>(L, var, sh);
   return ok ? EPFFT_OK : EPFFT_ERR_UNSUPPORTED;
 }
 
@@ -135,13 +137,42 @@ int get_tables(epfft_ctx* c, int L, int prec, void** tw, void** ktab) {
     }
     it = c->tables.emplace(key, d).first;
   }
-  if (!c->prepared[key]) {
-    CK(prec == EPFFT_FP32 ? prepare<float>(L) : prepare<double>(L));
-    c->prepared[key] = true;
-  }
   *tw = it->second;
   *ktab = (char*)it->second + (size_t)2 * L * real_size(prec);
   return EPFFT_OK;
+}
+
+// First recorded self-check failure of any instantiation unit.
+cudaError_t read_check_all(CheckRec* out) {
+  CheckRec r[4];
+  cudaError_t e;
+  if ((e = read_check_v<float, 0>(&r[0])) != cudaSuccess) return e;
+  if ((e = read_check_v<float, 1>(&r[1])) != cudaSuccess) return e;
+  if ((e = read_check_v<double, 0>(&r[2])) != cudaSuccess) return e;
+  if ((e = read_check_v<double, 1>(&r[3])) != cudaSuccess) return e;
+  *out = CheckRec{};
+  for (auto& x : r)
+    if (x.code) {
+      *out = x;
+      break;
+    }
+  return cudaSuccess;
+}
+
+// Raises the shared-memory limits of the kernels of one tiling (once).
+int ensure_prepared(epfft_ctx* c, int L, int prec, int var) {
+  auto key = std::make_tuple(L, prec, var);
+  if (!c->prepared[key]) {
+    CK(prec == EPFFT_FP32 ? prepare<float>(L, var) : prepare<double>(L, var));
+    c->prepared[key] = true;
+  }
+  return EPFFT_OK;
+}
+
+// Tiling used for (L, precision): the autotuned one, else variant 0.
+int variant_for(epfft_ctx* c, int L, int prec) {
+  auto it = c->variant.find(std::make_pair(L, prec));
+  return it == c->variant.end() ? 0 : it->second;
 }
 
 uint64_t void_threshold(double f) {
@@ -189,7 +220,7 @@ void fill_consts(Solve& S) {
 
 // Device state of one batch.
 struct Batch {
-  int L = 0, prec = 0, nb = 0;
+  int L = 0, prec = 0, nb = 0, var = -1;  // var < 0: the context's tuned tiling
   PassShape sh{};
   void* tw = nullptr;
   void* ktab = nullptr;
@@ -202,11 +233,11 @@ struct Batch {
 
 int launch_body(epfft_ctx* c, Batch& B, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
   if (B.prec == EPFFT_FP32) {
-    CK(launch_col<float>(B.L, B.nb, s, B.d_solves, B.tw, B.ktab, h, use_cond));
-    CK(launch_row<float>(B.L, B.nb, s, B.d_solves, B.d_ctl, B.tw, h, use_cond));
+    CK(launch_col<float>(B.L, B.var, B.nb, s, B.d_solves, B.tw, B.ktab, h, use_cond));
+    CK(launch_row<float>(B.L, B.var, B.nb, s, B.d_solves, B.d_ctl, B.tw, h, use_cond));
   } else {
-    CK(launch_col<double>(B.L, B.nb, s, B.d_solves, B.tw, B.ktab, h, use_cond));
-    CK(launch_row<double>(B.L, B.nb, s, B.d_solves, B.d_ctl, B.tw, h, use_cond));
+    CK(launch_col<double>(B.L, B.var, B.nb, s, B.d_solves, B.tw, B.ktab, h, use_cond));
+    CK(launch_row<double>(B.L, B.var, B.nb, s, B.d_solves, B.d_ctl, B.tw, h, use_cond));
   }
   (void)c;
   return EPFFT_OK;
@@ -280,9 +311,11 @@ int setup_batch(epfft_ctx* c, Arena& A, Batch& B, int n, const epfft_problem* pr
   B.L = probs[0].L;
   B.prec = probs[0].precision;
   B.nb = n;
-  int rc = shape(B.L, B.prec, &B.sh);
+  if (B.var < 0) B.var = variant_for(c, B.L, B.prec);
+  int rc = shape(B.L, B.prec, B.var, &B.sh);
   if (rc) return rc;
   rc = get_tables(c, B.L, B.prec, &B.tw, &B.ktab);
+  if (!rc) rc = ensure_prepared(c, B.L, B.prec, B.var);
   if (rc) return rc;
   B.h_solves.resize(n);
   B.n_inc.resize(n);
@@ -385,16 +418,16 @@ int run_checked(epfft_ctx* c, Batch& B) {
   for (int64_t step = 0;; step++) {
     CK(cudaMemcpy(hs.data(), B.d_solves, sizeof(Solve) * B.nb, cudaMemcpyDeviceToHost));
     cudaError_t e;
-    if (B.prec == EPFFT_FP32) e = launch_col<float>(B.L, B.nb, c->stream, B.d_solves, B.tw, B.ktab, 0, 0);
-    else e = launch_col<double>(B.L, B.nb, c->stream, B.d_solves, B.tw, B.ktab, 0, 0);
+    if (B.prec == EPFFT_FP32) e = launch_col<float>(B.L, B.var, B.nb, c->stream, B.d_solves, B.tw, B.ktab, 0, 0);
+    else e = launch_col<double>(B.L, B.var, B.nb, c->stream, B.d_solves, B.tw, B.ktab, 0, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
       fprintf(stderr, "epfft check: column pass failed at step %lld (phase %d inc %d iter %d): %s\n",
               (long long)step, hs[0].phase, hs[0].inc, hs[0].iter, cudaGetErrorString(e));
       return EPFFT_ERR_CUDA;
     }
-    if (B.prec == EPFFT_FP32) e = launch_row<float>(B.L, B.nb, c->stream, B.d_solves, B.d_ctl, B.tw, 0, 0);
-    else e = launch_row<double>(B.L, B.nb, c->stream, B.d_solves, B.d_ctl, B.tw, 0, 0);
+    if (B.prec == EPFFT_FP32) e = launch_row<float>(B.L, B.var, B.nb, c->stream, B.d_solves, B.d_ctl, B.tw, 0, 0);
+    else e = launch_row<double>(B.L, B.var, B.nb, c->stream, B.d_solves, B.d_ctl, B.tw, 0, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
       fprintf(stderr, "epfft check: row pass failed at step %lld (phase %d inc %d iter %d): %s\n",
@@ -402,7 +435,7 @@ int run_checked(epfft_ctx* c, Batch& B) {
       return EPFFT_ERR_CUDA;
     }
     CheckRec cr;
-    CK(B.prec == EPFFT_FP32 ? read_check<float>(&cr) : read_check<double>(&cr));
+    CK(read_check_all(&cr));
     if (cr.code)
       fprintf(stderr, "epfft check: step %lld phase %d: self-check %d failed: index %lld bound %lld at %d\n",
               (long long)step, hs[0].phase, cr.code, (long long)cr.index, (long long)cr.bound, cr.where);
@@ -506,7 +539,7 @@ int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_
   CK(cudaStreamSynchronize(c->stream));
   {
     CheckRec cr;
-    CK(B.prec == EPFFT_FP32 ? read_check<float>(&cr) : read_check<double>(&cr));
+    CK(read_check_all(&cr));
     if (cr.code) {
       fprintf(stderr, "epfft: device self-check %d failed (index %lld, bound %lld, at %d)\n", cr.code,
               (long long)cr.index, (long long)cr.bound, cr.where);
@@ -550,6 +583,51 @@ int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_
   }
   CK(cudaStreamSynchronize(c->stream));
   return status;
+}
+
+// Mean CUDA-event time of the column and row passes over n_iter launch
+// pairs for n_batch copies of p, tiling `var` (< 0: the tuned one).
+int time_passes_impl(epfft_ctx* ctx, epfft_problem p, int n_batch, const double E[4], int n_iter, int var,
+                     float* col_ms, float* row_ms) {
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return EPFFT_ERR_CUDA;
+  p.tol_eq = 0.0;
+  p.tol_macro = 0.0;
+  p.max_iter = 1 << 30;
+  std::vector<epfft_problem> ps(n_batch, p);
+  std::vector<epfft_path> paths(n_batch, epfft_path{1, 0, E});
+  Arena A(ctx);
+  Batch B;
+  B.var = var;
+  int rc = setup_batch(ctx, A, B, n_batch, ps.data(), paths.data(), nullptr);
+  if (rc) return rc;
+  const int nb = n_batch;
+  // first row pass: warm start (eps = E, spectrum of its polarization)
+  if (B.prec == EPFFT_FP32) CK(launch_row<float>(B.L, B.var, nb, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
+  else CK(launch_row<double>(B.L, B.var, nb, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
+  std::vector<cudaEvent_t> ev(3 * (size_t)n_iter);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  for (int it = 0; it < n_iter; it++) {
+    CK(cudaEventRecord(ev[3 * it], ctx->stream));
+    if (B.prec == EPFFT_FP32) CK(launch_col<float>(B.L, B.var, nb, ctx->stream, B.d_solves, B.tw, B.ktab, 0, 0));
+    else CK(launch_col<double>(B.L, B.var, nb, ctx->stream, B.d_solves, B.tw, B.ktab, 0, 0));
+    CK(cudaEventRecord(ev[3 * it + 1], ctx->stream));
+    if (B.prec == EPFFT_FP32) CK(launch_row<float>(B.L, B.var, nb, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
+    else CK(launch_row<double>(B.L, B.var, nb, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
+    CK(cudaEventRecord(ev[3 * it + 2], ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  double tc = 0, tr = 0;
+  for (int it = 0; it < n_iter; it++) {
+    float a = 0, b = 0;
+    CK(cudaEventElapsedTime(&a, ev[3 * it], ev[3 * it + 1]));
+    CK(cudaEventElapsedTime(&b, ev[3 * it + 1], ev[3 * it + 2]));
+    tc += a;
+    tr += b;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  *col_ms = (float)(tc / n_iter);
+  *row_ms = (float)(tr / n_iter);
+  return EPFFT_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -639,8 +717,10 @@ int get_class(epfft_ctx* c, Server& S, int L, int prec, ServeClass** out) {
   B.L = L;
   B.prec = prec;
   B.nb = S.cap;
-  int rc = shape(L, prec, &B.sh);
+  B.var = variant_for(c, L, prec);
+  int rc = shape(L, prec, B.var, &B.sh);
   if (!rc) rc = get_tables(c, L, prec, &B.tw, &B.ktab);
+  if (!rc) rc = ensure_prepared(c, L, prec, B.var);
   if (!rc && cudaStreamCreateWithFlags(&k->stream, cudaStreamNonBlocking) != cudaSuccess) rc = EPFFT_ERR_CUDA;
   if (!rc) {
     B.d_solves = (Solve*)dev_alloc(c, sizeof(Solve) * (size_t)S.cap);
@@ -908,7 +988,9 @@ int epfft_project(epfft_ctx* ctx, int32_t L, int32_t precision, double lambda0, 
   if (cudaSetDevice(ctx->device) != cudaSuccess) return EPFFT_ERR_CUDA;
   Arena A(ctx);
   void *tw, *ktab;
+  const int var = variant_for(ctx, L, precision);
   int rc = get_tables(ctx, L, precision, &tw, &ktab);
+  if (!rc) rc = ensure_prepared(ctx, L, precision, var);
   if (rc) return rc;
   const size_t LL = (size_t)L * L, rs = real_size(precision);
   void* spec = A.get(3 * LL * rs);
@@ -925,13 +1007,13 @@ int epfft_project(epfft_ctx* ctx, int32_t L, int32_t precision, double lambda0, 
   CK(cudaMemcpyAsync(dpath, E, 4 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ds, &S, sizeof(S), cudaMemcpyHostToDevice, ctx->stream));
   if (precision == EPFFT_FP32) {
-    CK(launch_row_forward<float>(L, ctx->stream, p_dev, spec, tw));
-    CK(launch_col<float>(L, 1, ctx->stream, ds, tw, ktab, 0, 0));
-    CK(launch_row_inverse<float>(L, ctx->stream, spec, e_dev, tw));
+    CK(launch_row_forward<float>(L, var, ctx->stream, p_dev, spec, tw));
+    CK(launch_col<float>(L, var, 1, ctx->stream, ds, tw, ktab, 0, 0));
+    CK(launch_row_inverse<float>(L, var, ctx->stream, spec, e_dev, tw));
   } else {
-    CK(launch_row_forward<double>(L, ctx->stream, p_dev, spec, tw));
-    CK(launch_col<double>(L, 1, ctx->stream, ds, tw, ktab, 0, 0));
-    CK(launch_row_inverse<double>(L, ctx->stream, spec, e_dev, tw));
+    CK(launch_row_forward<double>(L, var, ctx->stream, p_dev, spec, tw));
+    CK(launch_col<double>(L, var, 1, ctx->stream, ds, tw, ktab, 0, 0));
+    CK(launch_row_inverse<double>(L, var, ctx->stream, spec, e_dev, tw));
   }
   CK(cudaStreamSynchronize(ctx->stream));
   return EPFFT_OK;
@@ -985,7 +1067,7 @@ int epfft_submit(epfft_ctx* ctx, const epfft_problem* problem, const epfft_path*
     if (!std::isfinite(path->E[k])) return EPFFT_ERR_ARG;
   Server& S = *ctx->server;
   PassShape sh;
-  rc = shape(problem->L, problem->precision, &sh);
+  rc = shape(problem->L, problem->precision, variant_for(ctx, problem->L, problem->precision), &sh);
   if (rc) return rc;
   Ticket t;
   t.prob = *problem;
@@ -1035,8 +1117,7 @@ int epfft_serve_step(epfft_ctx* ctx, int32_t* n_running, int32_t* n_queued) {
   for (ServeClass* k : live) CK(cudaStreamSynchronize(k->stream));
   {
     CheckRec cr;
-    CK(read_check<float>(&cr));
-    if (!cr.code) CK(read_check<double>(&cr));
+    CK(read_check_all(&cr));
     if (cr.code) {
       fprintf(stderr, "epfft: device self-check %d failed (index %lld, bound %lld, at %d)\n", cr.code,
               (long long)cr.index, (long long)cr.bound, cr.where);
@@ -1075,44 +1156,52 @@ int epfft_time_passes(epfft_ctx* ctx, const epfft_problem* problem, int32_t n_ba
   if (!ctx || !problem || !E || n_iter < 1 || n_batch < 1 || !col_ms || !row_ms) return EPFFT_ERR_ARG;
   int rc = check_problem(problem);
   if (rc) return rc;
-  if (cudaSetDevice(ctx->device) != cudaSuccess) return EPFFT_ERR_CUDA;
-  epfft_problem p = *problem;
-  p.tol_eq = 0.0;
-  p.tol_macro = 0.0;
-  p.max_iter = 1 << 30;
-  std::vector<epfft_problem> ps(n_batch, p);
-  std::vector<epfft_path> paths(n_batch, epfft_path{1, 0, E});
-  Arena A(ctx);
-  Batch B;
-  rc = setup_batch(ctx, A, B, n_batch, ps.data(), paths.data(), nullptr);
-  if (rc) return rc;
-  const int nb = n_batch;
-  // first row pass: warm start (eps = E, spectrum of its polarization)
-  if (B.prec == EPFFT_FP32) CK(launch_row<float>(B.L, nb, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
-  else CK(launch_row<double>(B.L, nb, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
-  std::vector<cudaEvent_t> ev(3 * (size_t)n_iter);
-  for (auto& e : ev) CK(cudaEventCreate(&e));
-  for (int it = 0; it < n_iter; it++) {
-    CK(cudaEventRecord(ev[3 * it], ctx->stream));
-    if (B.prec == EPFFT_FP32) CK(launch_col<float>(B.L, nb, ctx->stream, B.d_solves, B.tw, B.ktab, 0, 0));
-    else CK(launch_col<double>(B.L, nb, ctx->stream, B.d_solves, B.tw, B.ktab, 0, 0));
-    CK(cudaEventRecord(ev[3 * it + 1], ctx->stream));
-    if (B.prec == EPFFT_FP32) CK(launch_row<float>(B.L, nb, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
-    else CK(launch_row<double>(B.L, nb, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
-    CK(cudaEventRecord(ev[3 * it + 2], ctx->stream));
+  return time_passes_impl(ctx, *problem, n_batch, E, n_iter, -1, col_ms, row_ms);
+}
+
+int epfft_autotune(epfft_ctx* ctx, int32_t L, int32_t precision, int32_t* chosen, float* ms_per_iteration) {
+  if (!ctx) return EPFFT_ERR_ARG;
+  if (!is_pow2(L) || L < 4 || (precision != EPFFT_FP32 && precision != EPFFT_FP64)) return EPFFT_ERR_ARG;
+  if (!supported(L, precision)) return EPFFT_ERR_UNSUPPORTED;
+  // a synthetic lattice of the kind the solver serves: f = 0.2 voids, the
+  // default matrix, shear at 1.5x the void-free yield strain
+  epfft_problem p;
+  std::memset(&p, 0, sizeof(p));
+  p.L = L;
+  p.precision = precision;
+  p.void_fraction = 0.2;
+  p.seed = 7;
+  p.green = EPFFT_GREEN_EQ3;
+  p.mu = p.mu0 = 1.0;
+  p.lambda = p.lambda0 = 1.5;
+  p.yield_stress = 1.0;
+  p.max_iter = 1;
+  const double E[4] = {0.0, 0.0, 0.0, 1.5 / (2.0 * std::sqrt(3.0))};
+  const int n_iter = L >= 2048 ? 10 : 30;
+  int best = 0;
+  float tbest = 0.f;
+  for (int v = 0; v < N_VARIANTS; v++) {
+    float c = 0.f, r = 0.f;
+    // warm-up, then the timed launches
+    int rc = time_passes_impl(ctx, p, 1, E, 3, v, &c, &r);
+    if (!rc) rc = time_passes_impl(ctx, p, 1, E, n_iter, v, &c, &r);
+    if (rc) return rc;
+    if (ms_per_iteration) ms_per_iteration[v] = c + r;
+    if (v == 0 || c + r < tbest) {
+      tbest = c + r;
+      best = v;
+    }
   }
-  CK(cudaStreamSynchronize(ctx->stream));
-  double tc = 0, tr = 0;
-  for (int it = 0; it < n_iter; it++) {
-    float a = 0, b = 0;
-    CK(cudaEventElapsedTime(&a, ev[3 * it], ev[3 * it + 1]));
-    CK(cudaEventElapsedTime(&b, ev[3 * it + 1], ev[3 * it + 2]));
-    tc += a;
-    tr += b;
-  }
-  for (auto& e : ev) cudaEventDestroy(e);
-  *col_ms = (float)(tc / n_iter);
-  *row_ms = (float)(tr / n_iter);
+  ctx->variant[std::make_pair(L, precision)] = best;
+  if (chosen) *chosen = best;
+  return EPFFT_OK;
+}
+
+int epfft_set_tiling(epfft_ctx* ctx, int32_t L, int32_t precision, int32_t variant) {
+  if (!ctx || variant < 0 || variant >= N_VARIANTS) return EPFFT_ERR_ARG;
+  if (!is_pow2(L) || L < 4 || (precision != EPFFT_FP32 && precision != EPFFT_FP64)) return EPFFT_ERR_ARG;
+  if (!supported(L, precision)) return EPFFT_ERR_UNSUPPORTED;
+  ctx->variant[std::make_pair(L, precision)] = variant;
   return EPFFT_OK;
 }
 

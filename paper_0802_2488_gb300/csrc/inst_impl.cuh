@@ -1,5 +1,5 @@
-// Instantiation of the launch table for one real type EPFFT_REAL over the
-// supported lattice sides EPFFT_LMAX.
+// Instantiation of the launch table for one real type EPFFT_REAL and one
+// tiling variant EPFFT_VAR over the supported lattice sides.
 #pragma once
 #include "launch.cuh"
 #include "passes.cuh"
@@ -10,7 +10,7 @@ namespace epfft {
 
 template <typename T, int L>
 static bool shape_of(PassShape* o) {
-  using C = Cfg<T, L>;
+  using C = Cfg<T, L, EPFFT_VAR>;
   o->rows_per_cta = C::RR;
   o->tile_w = C::W;
   o->row_ctas = L / C::RR;
@@ -24,16 +24,17 @@ static bool shape_of(PassShape* o) {
 
 template <typename T, int L>
 static cudaError_t prepare_L() {
-  using C = Cfg<T, L>;
+  using C = Cfg<T, L, EPFFT_VAR>;
+  constexpr int V = EPFFT_VAR;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(row_pass<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::ROW_SMEM)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(col_pass<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::COL_SMEM)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(row_forward<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::ROW_SMEM)) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(row_inverse<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::ROW_SMEM);
+  if ((e = cudaFuncSetAttribute(row_pass<T, L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::ROW_SMEM)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(col_pass<T, L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::COL_SMEM)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(row_forward<T, L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::ROW_SMEM)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(row_inverse<T, L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::ROW_SMEM);
 }
 
 template <>
-bool pass_shape<EPFFT_REAL>(int L, PassShape* out) {
+bool pass_shape_v<EPFFT_REAL, EPFFT_VAR>(int L, PassShape* out) {
   switch (L) {
 #define X(n) case n: return shape_of<EPFFT_REAL, n>(out);
     EPFFT_FOR_L(X)
@@ -43,7 +44,7 @@ bool pass_shape<EPFFT_REAL>(int L, PassShape* out) {
 }
 
 template <>
-cudaError_t prepare<EPFFT_REAL>(int L) {
+cudaError_t prepare_v<EPFFT_REAL, EPFFT_VAR>(int L) {
   switch (L) {
 #define X(n) case n: return prepare_L<EPFFT_REAL, n>();
     EPFFT_FOR_L(X)
@@ -53,13 +54,13 @@ cudaError_t prepare<EPFFT_REAL>(int L) {
 }
 
 template <>
-cudaError_t launch_row<EPFFT_REAL>(int L, int nb, cudaStream_t s, Solve* solves, BatchCtl* bc, const void* tw,
+cudaError_t launch_row_v<EPFFT_REAL, EPFFT_VAR>(int L, int nb, cudaStream_t s, Solve* solves, BatchCtl* bc, const void* tw,
                                    cudaGraphConditionalHandle cond, int use_cond) {
   switch (L) {
 #define X(n)                                                                                         \
   case n: {                                                                                          \
-    using C = Cfg<EPFFT_REAL, n>;                                                                    \
-    row_pass<EPFFT_REAL, n><<<dim3(n / C::RR, nb), C::NT_ROW, C::ROW_SMEM, s>>>(                     \
+    using C = Cfg<EPFFT_REAL, n, EPFFT_VAR>;                                                                    \
+    row_pass<EPFFT_REAL, n, EPFFT_VAR><<<dim3(n / C::RR, nb), C::NT_ROW, C::ROW_SMEM, s>>>(                     \
         solves, nb, bc, reinterpret_cast<const C2<EPFFT_REAL>*>(tw), cond, use_cond);                \
     return cudaGetLastError();                                                                       \
   }
@@ -70,13 +71,13 @@ cudaError_t launch_row<EPFFT_REAL>(int L, int nb, cudaStream_t s, Solve* solves,
 }
 
 template <>
-cudaError_t launch_col<EPFFT_REAL>(int L, int nb, cudaStream_t s, Solve* solves, const void* tw, const void* ktab,
+cudaError_t launch_col_v<EPFFT_REAL, EPFFT_VAR>(int L, int nb, cudaStream_t s, Solve* solves, const void* tw, const void* ktab,
                                    cudaGraphConditionalHandle cond, int use_cond) {
   switch (L) {
 #define X(n)                                                                                         \
   case n: {                                                                                          \
-    using C = Cfg<EPFFT_REAL, n>;                                                                    \
-    col_pass<EPFFT_REAL, n><<<dim3((n / 2) / C::W, nb), C::NT_COL, C::COL_SMEM, s>>>(                \
+    using C = Cfg<EPFFT_REAL, n, EPFFT_VAR>;                                                                    \
+    col_pass<EPFFT_REAL, n, EPFFT_VAR><<<dim3((n / 2) / C::W, nb), C::NT_COL, C::COL_SMEM, s>>>(                \
         solves, reinterpret_cast<const C2<EPFFT_REAL>*>(tw),                                         \
         reinterpret_cast<const C2<EPFFT_REAL>*>(ktab), cond, use_cond);                              \
     return cudaGetLastError();                                                                       \
@@ -88,12 +89,12 @@ cudaError_t launch_col<EPFFT_REAL>(int L, int nb, cudaStream_t s, Solve* solves,
 }
 
 template <>
-cudaError_t launch_row_forward<EPFFT_REAL>(int L, cudaStream_t s, const void* p, void* spec, const void* tw) {
+cudaError_t launch_row_forward_v<EPFFT_REAL, EPFFT_VAR>(int L, cudaStream_t s, const void* p, void* spec, const void* tw) {
   switch (L) {
 #define X(n)                                                                                         \
   case n: {                                                                                          \
-    using C = Cfg<EPFFT_REAL, n>;                                                                    \
-    row_forward<EPFFT_REAL, n><<<n / C::RR, C::NT_ROW, C::ROW_SMEM, s>>>(                            \
+    using C = Cfg<EPFFT_REAL, n, EPFFT_VAR>;                                                                    \
+    row_forward<EPFFT_REAL, n, EPFFT_VAR><<<n / C::RR, C::NT_ROW, C::ROW_SMEM, s>>>(                            \
         reinterpret_cast<const EPFFT_REAL*>(p), reinterpret_cast<C2<EPFFT_REAL>*>(spec),             \
         reinterpret_cast<const C2<EPFFT_REAL>*>(tw));                                                \
     return cudaGetLastError();                                                                       \
@@ -105,12 +106,12 @@ cudaError_t launch_row_forward<EPFFT_REAL>(int L, cudaStream_t s, const void* p,
 }
 
 template <>
-cudaError_t launch_row_inverse<EPFFT_REAL>(int L, cudaStream_t s, const void* spec, void* e, const void* tw) {
+cudaError_t launch_row_inverse_v<EPFFT_REAL, EPFFT_VAR>(int L, cudaStream_t s, const void* spec, void* e, const void* tw) {
   switch (L) {
 #define X(n)                                                                                         \
   case n: {                                                                                          \
-    using C = Cfg<EPFFT_REAL, n>;                                                                    \
-    row_inverse<EPFFT_REAL, n><<<n / C::RR, C::NT_ROW, C::ROW_SMEM, s>>>(                            \
+    using C = Cfg<EPFFT_REAL, n, EPFFT_VAR>;                                                                    \
+    row_inverse<EPFFT_REAL, n, EPFFT_VAR><<<n / C::RR, C::NT_ROW, C::ROW_SMEM, s>>>(                            \
         reinterpret_cast<const C2<EPFFT_REAL>*>(spec), reinterpret_cast<EPFFT_REAL*>(e),             \
         reinterpret_cast<const C2<EPFFT_REAL>*>(tw));                                                \
     return cudaGetLastError();                                                                       \
@@ -122,7 +123,7 @@ cudaError_t launch_row_inverse<EPFFT_REAL>(int L, cudaStream_t s, const void* sp
 }
 
 template <>
-cudaError_t read_check<EPFFT_REAL>(CheckRec* out) {
+cudaError_t read_check_v<EPFFT_REAL, EPFFT_VAR>(CheckRec* out) {
 #ifdef EPFFT_CHECKS
   cudaError_t e = cudaMemcpyFromSymbol(out, g_check, sizeof(CheckRec));
   if (e != cudaSuccess) return e;

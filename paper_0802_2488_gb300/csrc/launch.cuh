@@ -1,10 +1,14 @@
-// Per-precision launch table of the fused passes (instantiated for every
-// supported lattice side in inst_f32.cu / inst_f64.cu).
+// Launch table of the fused passes.  Each (real type, tiling variant) pair
+// is instantiated for every supported lattice side in its own translation
+// unit (inst_f32_v0.cu ... inst_f64_v1.cu); the functions below dispatch on
+// the variant at run time.
 #pragma once
 #include <cuda_runtime.h>
 #include "common.cuh"
 
 namespace epfft {
+
+constexpr int N_VARIANTS = 2;
 
 struct PassShape {
   int rows_per_cta, tile_w;  // RR, W
@@ -13,25 +17,54 @@ struct PassShape {
   size_t row_smem, col_smem;
 };
 
+template <typename T, int V>
+bool pass_shape_v(int L, PassShape* out);
+template <typename T, int V>
+cudaError_t prepare_v(int L);
+template <typename T, int V>
+cudaError_t launch_row_v(int L, int nb, cudaStream_t s, Solve* solves, BatchCtl* bc, const void* tw,
+                         cudaGraphConditionalHandle cond, int use_cond);
+template <typename T, int V>
+cudaError_t launch_col_v(int L, int nb, cudaStream_t s, Solve* solves, const void* tw, const void* ktab,
+                         cudaGraphConditionalHandle cond, int use_cond);
+template <typename T, int V>
+cudaError_t launch_row_forward_v(int L, cudaStream_t s, const void* p, void* spec, const void* tw);
+template <typename T, int V>
+cudaError_t launch_row_inverse_v(int L, cudaStream_t s, const void* spec, void* e, const void* tw);
+// Reads and clears the self-check record of one translation unit (zero
+// unless built with EPFFT_CHECKS).
+template <typename T, int V>
+cudaError_t read_check_v(CheckRec* out);
+
 // Returns false when L is not built for T.
 template <typename T>
-bool pass_shape(int L, PassShape* out);
+inline bool pass_shape(int L, int var, PassShape* out) {
+  return var == 0 ? pass_shape_v<T, 0>(L, out) : pass_shape_v<T, 1>(L, out);
+}
 // Raises the dynamic shared-memory limit of the kernels for L (call before
 // any launch or capture).
 template <typename T>
-cudaError_t prepare(int L);
+inline cudaError_t prepare(int L, int var) {
+  return var == 0 ? prepare_v<T, 0>(L) : prepare_v<T, 1>(L);
+}
 template <typename T>
-cudaError_t launch_row(int L, int nb, cudaStream_t s, Solve* solves, BatchCtl* bc, const void* tw,
-                       cudaGraphConditionalHandle cond, int use_cond);
+inline cudaError_t launch_row(int L, int var, int nb, cudaStream_t s, Solve* solves, BatchCtl* bc, const void* tw,
+                              cudaGraphConditionalHandle cond, int use_cond) {
+  return var == 0 ? launch_row_v<T, 0>(L, nb, s, solves, bc, tw, cond, use_cond)
+                  : launch_row_v<T, 1>(L, nb, s, solves, bc, tw, cond, use_cond);
+}
 template <typename T>
-cudaError_t launch_col(int L, int nb, cudaStream_t s, Solve* solves, const void* tw, const void* ktab,
-                       cudaGraphConditionalHandle cond, int use_cond);
+inline cudaError_t launch_col(int L, int var, int nb, cudaStream_t s, Solve* solves, const void* tw,
+                              const void* ktab, cudaGraphConditionalHandle cond, int use_cond) {
+  return var == 0 ? launch_col_v<T, 0>(L, nb, s, solves, tw, ktab, cond, use_cond)
+                  : launch_col_v<T, 1>(L, nb, s, solves, tw, ktab, cond, use_cond);
+}
 template <typename T>
-cudaError_t launch_row_forward(int L, cudaStream_t s, const void* p, void* spec, const void* tw);
-// Reads and clears the self-check record (zero unless built with EPFFT_CHECKS).
+inline cudaError_t launch_row_forward(int L, int var, cudaStream_t s, const void* p, void* spec, const void* tw) {
+  return var == 0 ? launch_row_forward_v<T, 0>(L, s, p, spec, tw) : launch_row_forward_v<T, 1>(L, s, p, spec, tw);
+}
 template <typename T>
-cudaError_t read_check(CheckRec* out);
-template <typename T>
-cudaError_t launch_row_inverse(int L, cudaStream_t s, const void* spec, void* e, const void* tw);
-
+inline cudaError_t launch_row_inverse(int L, int var, cudaStream_t s, const void* spec, void* e, const void* tw) {
+  return var == 0 ? launch_row_inverse_v<T, 0>(L, s, spec, e, tw) : launch_row_inverse_v<T, 1>(L, s, spec, e, tw);
+}
 }  // namespace epfft

@@ -26,22 +26,25 @@
 
 namespace epfft {
 
-// Tiling of one lattice size in one precision.
-template <typename T, int L>
+// Tiling of one lattice size in one precision.  Two variants per size are
+// compiled; the autotuner times both on the device and keeps the faster.
+//   V = 0: fewer, larger CTAs (RR rows x W columns of a tile row span >= 64
+//          bytes of HBM, so each CTA streams long contiguous runs);
+//   V = 1: more, smaller CTAs (several per SM hide memory latency; short
+//          runs rely on the L2 to merge neighbouring CTAs' accesses).
+template <typename T, int L, int V = 0>
 struct Cfg {
   static constexpr bool F64 = sizeof(T) == 8;
   static constexpr int M = L / 2;
-  // rows per row-pass CTA (small lattices: more, smaller CTAs to fill the
-  // SMs; large ones: RR x W complex numbers of a tile row span >= 64 bytes)
-  static constexpr int RR = F64 ? (L <= 512 ? 2 : 4)
-                                : (L <= 256 ? 2 : (L <= 1024 ? 8 : 4));
+  // rows per row-pass CTA
+  static constexpr int RR = V == 0 ? (F64 ? (L <= 512 ? 2 : 4) : (L <= 256 ? 2 : (L <= 2048 ? 8 : 4)))
+                                   : (F64 ? (L <= 512 ? 4 : 2) : (L <= 256 ? 1 : (L <= 2048 ? 2 : 1)));
   // columns per column-pass CTA (= tile width of the spectrum layout)
-  static constexpr int W0 = F64 ? (L <= 256 ? 1 : (L <= 512 ? 2 : (L <= 1024 ? 4 : 2)))
-                                : (L <= 256 ? 2 : (L <= 512 ? 8 : (L <= 2048 ? 4 : 2)));
+  static constexpr int W0 = V == 0 ? (F64 ? (L <= 256 ? 1 : (L <= 512 ? 2 : (L <= 1024 ? 4 : 2)))
+                                          : (L <= 256 ? 2 : (L <= 512 ? 8 : (L <= 2048 ? 4 : 2))))
+                                   : (F64 ? 1 : (L <= 256 ? 1 : (L <= 2048 ? 2 : 1)));
   static constexpr int W = W0 < M ? W0 : M;
-  // threads per row-pass CTA: 256 from L = 512 to 2048 so that two CTAs
-  // (each with up to 128 registers per thread) share an SM
-  static constexpr int NT_ROW = L < 32 ? 32 : (L <= 256 ? L : (L <= 2048 ? 256 : 512));
+  static constexpr int NT_ROW = L < 32 ? 32 : (L <= 256 ? L : (V == 0 ? 512 : 256));
   static constexpr int NT_COL0 = ((3 * W * L / 8 + 31) / 32) * 32;
   static constexpr int NT_COL = NT_COL0 < 32 ? 32 : (NT_COL0 > 512 ? 512 : NT_COL0);
   // element strides of the interleaved shared-memory batches, made odd so
@@ -53,7 +56,7 @@ struct Cfg {
   static_assert(L >= 4 && (L & (L - 1)) == 0, "L must be a power of two >= 4");
   static_assert(M % W == 0, "tile width must divide L/2");
   static_assert(L % RR == 0, "rows per CTA must divide L");
-  static_assert(ROW_SMEM <= 232448 && COL_SMEM <= 232448, "shared memory per CTA");
+  static_assert(ROW_SMEM <= 225000 && COL_SMEM <= 230000, "shared memory per CTA");
   static_assert(NT_ROW % 32 == 0 && NT_COL % 32 == 0, "whole warps");
   static_assert(L <= NT_ROW || L % NT_ROW == 0, "pixel mapping");
 };
@@ -397,11 +400,11 @@ __device__ __forceinline__ void batch_arrive(Solve* solves, int nb, BatchCtl* bc
 // ---------------------------------------------------------------------------
 // Row pass
 // ---------------------------------------------------------------------------
-template <typename T, int L>
-__global__ void __launch_bounds__(Cfg<T, L>::NT_ROW)
+template <typename T, int L, int V>
+__global__ void __launch_bounds__(Cfg<T, L, V>::NT_ROW)
 row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restrict__ tw,
          cudaGraphConditionalHandle cond, int use_cond) {
-  using C = Cfg<T, L>;
+  using C = Cfg<T, L, V>;
   constexpr int RR = C::RR, W = C::W, NT = C::NT_ROW, M = C::M;
   constexpr int P = L >= NT ? L / NT : 1;
   using IO = RowIO<T, L, RR, W, NT>;
@@ -609,11 +612,11 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
 // ---------------------------------------------------------------------------
 // Column pass
 // ---------------------------------------------------------------------------
-template <typename T, int L>
-__global__ void __launch_bounds__(Cfg<T, L>::NT_COL)
+template <typename T, int L, int V>
+__global__ void __launch_bounds__(Cfg<T, L, V>::NT_COL)
 col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* __restrict__ ktab,
          cudaGraphConditionalHandle cond, int use_cond) {
-  using C = Cfg<T, L>;
+  using C = Cfg<T, L, V>;
   constexpr int W = C::W, NT = C::NT_COL, M = C::M, NBK = M / W;
   constexpr int XS = C::XC;  // element stride (3W rounded up to odd)
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -726,10 +729,10 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
 // ---------------------------------------------------------------------------
 // Row transforms alone (compatible-strain projection of a given field)
 // ---------------------------------------------------------------------------
-template <typename T, int L>
-__global__ void __launch_bounds__(Cfg<T, L>::NT_ROW)
+template <typename T, int L, int V>
+__global__ void __launch_bounds__(Cfg<T, L, V>::NT_ROW)
 row_forward(const T* __restrict__ p, C2<T>* __restrict__ spec, const C2<T>* __restrict__ tw) {
-  using C = Cfg<T, L>;
+  using C = Cfg<T, L, V>;
   constexpr int RR = C::RR, W = C::W, NT = C::NT_ROW, P = L >= NT ? L / NT : 1;
   using IO = RowIO<T, L, RR, W, NT>;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -750,10 +753,10 @@ row_forward(const T* __restrict__ p, C2<T>* __restrict__ spec, const C2<T>* __re
   IO::store(sp, spec, r0);
 }
 
-template <typename T, int L>
-__global__ void __launch_bounds__(Cfg<T, L>::NT_ROW)
+template <typename T, int L, int V>
+__global__ void __launch_bounds__(Cfg<T, L, V>::NT_ROW)
 row_inverse(const C2<T>* __restrict__ spec, T* __restrict__ e, const C2<T>* __restrict__ tw) {
-  using C = Cfg<T, L>;
+  using C = Cfg<T, L, V>;
   constexpr int RR = C::RR, W = C::W, NT = C::NT_ROW, P = L >= NT ? L / NT : 1;
   using IO = RowIO<T, L, RR, W, NT>;
   extern __shared__ __align__(16) unsigned char smraw[];

@@ -90,15 +90,15 @@ int project_static(int L, double lambda0, double mu0, const double E[4], const v
   S.path = (const double*)path;
   S.spec = spec;
   S.phase = PH_ITER;
-  if (prepare<T>(L) != cudaSuccess) return EPFFT_ERR_CUDA;
+  if (prepare<T>(L, 0) != cudaSuccess) return EPFFT_ERR_CUDA;
   if (cudaMemcpyAsync(tab, h, sizeof(T) * 4 * L, cudaMemcpyHostToDevice, s) != cudaSuccess) return EPFFT_ERR_CUDA;
   if (cudaMemcpyAsync(path, E, 4 * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess) return EPFFT_ERR_CUDA;
   if (cudaMemcpyAsync(solve, &S, sizeof(S), cudaMemcpyHostToDevice, s) != cudaSuccess) return EPFFT_ERR_CUDA;
   const void* tw = tab;
   const void* ktab = tab + sizeof(T) * 2 * L;
-  if (launch_row_forward<T>(L, s, p, spec, tw) != cudaSuccess) return EPFFT_ERR_CUDA;
-  if (launch_col<T>(L, 1, s, (Solve*)solve, tw, ktab, 0, 0) != cudaSuccess) return EPFFT_ERR_CUDA;
-  if (launch_row_inverse<T>(L, s, spec, e, tw) != cudaSuccess) return EPFFT_ERR_CUDA;
+  if (launch_row_forward<T>(L, 0, s, p, spec, tw) != cudaSuccess) return EPFFT_ERR_CUDA;
+  if (launch_col<T>(L, 0, 1, s, (Solve*)solve, tw, ktab, 0, 0) != cudaSuccess) return EPFFT_ERR_CUDA;
+  if (launch_row_inverse<T>(L, 0, s, spec, e, tw) != cudaSuccess) return EPFFT_ERR_CUDA;
   return EPFFT_OK;
 }
 

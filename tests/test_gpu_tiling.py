@@ -1,0 +1,53 @@
+"""Both compiled tilings of every lattice side (S8's per-size schedules) give
+the oracle's results, and the autotuner picks one of them."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_0802_2488_gb300 import binding as B
+from paper_0802_2488_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+TDT = {"fp64": torch.float64, "fp32": torch.float32}
+TOL = {"fp64": 1e-12, "fp32": 2e-5}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_0802_2488_gb300 import build
+    build.build()
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a, float) - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("L", [8, 32, 256, 1024])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_each_tiling_matches_oracle(ctx, L, prec, variant):
+    B.epfft_set_tiling(ctx, L, prec, variant)
+    mask = O.mask(L, 0.2, 3)
+    mat = O.material()
+    E = np.array([0.3, 0.2, 0.0, 0.25])
+    eps0 = inputs.random_strain(L, E, 0.2, seed=L)
+    k = 2
+    ref, lam = eps0.copy(), None
+    for _ in range(k):
+        ref, lam, _, _ = O.al_step(mask, mat, E, ref, lam)
+    t = torch.tensor(eps0, dtype=TDT[prec], device="cuda").contiguous()
+    B.epfft_iterate(ctx, B.Problem(L=L, precision=prec, mask=mask), E, t, k)
+    assert rel(t.cpu().numpy(), ref) < TOL[prec]
+    B.epfft_set_tiling(ctx, L, prec, 0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_autotune_chooses_a_compiled_tiling(ctx, prec):
+    chosen, ms = B.epfft_autotune(ctx, 256, prec)
+    assert chosen in (0, 1) and all(m > 0 for m in ms)
+    assert ms[chosen] == min(ms)
+    B.epfft_set_tiling(ctx, 256, prec, 0)
