@@ -16,6 +16,7 @@
 #include "../../include/epfft.h"
 #include "aux_kernels.cuh"
 #include "launch.cuh"
+#include "tables.cuh"
 
 using namespace epfft;
 
@@ -31,8 +32,9 @@ struct epfft_ctx {
   epfft_alloc_fn alloc = nullptr;
   epfft_free_fn freef = nullptr;
   void* user = nullptr;
-  // (L, precision) -> device table: tw[L] then ktab[L] (complex of precision)
-  std::map<std::pair<int, int>, void*> tables;
+  // (L, precision) -> device table (layout of tables.cuh) and the offset of
+  // k(m) in it (complex units)
+  std::map<std::pair<int, int>, std::pair<void*, int>> tables;
   std::map<std::tuple<int, int, int>, bool> prepared;  // (L, precision, tiling variant)
   std::map<std::pair<int, int>, int> variant;          // tuned tiling per (L, precision)
   epfft_stats last{};
@@ -102,43 +104,26 @@ size_t real_size(int prec) { return prec == EPFFT_FP32 ? 4 : 8; }
 // Twiddles exp(-2 pi i k / L) and Fourier symbols of Eq. 2,
 // k(m) = 2 sin(q/2) exp(i q/2) = (sin q, 2 sin^2(q/2)), q = 2 pi m / L, both
 // evaluated in long double and rounded once to the working precision.
-template <typename T>
-void fill_tables(int L, std::vector<T>& h) {
-  h.assign((size_t)4 * L, T(0));
-  const long double pi = 3.141592653589793238462643383279502884L;
-  for (int k = 0; k < L; k++) {
-    const long double a = 2.0L * pi * (long double)k / (long double)L;
-    const long double hs = sinl(pi * (long double)k / (long double)L);
-    h[2 * k] = (T)cosl(a);
-    h[2 * k + 1] = (T)(-sinl(a));
-    h[2 * L + 2 * k] = (T)sinl(a);
-    h[2 * L + 2 * k + 1] = (T)(2.0L * hs * hs);
-  }
-}
-
 int get_tables(epfft_ctx* c, int L, int prec, void** tw, void** ktab) {
   auto key = std::make_pair(L, prec);
   auto it = c->tables.find(key);
   if (it == c->tables.end()) {
-    const size_t bytes = (size_t)4 * L * real_size(prec);
+    std::vector<float> hf;
+    std::vector<double> hd;
+    const int koff = prec == EPFFT_FP32 ? host_tables<float>(L, hf) : host_tables<double>(L, hd);
+    if (koff < 0) return EPFFT_ERR_ARG;
+    const size_t bytes = prec == EPFFT_FP32 ? hf.size() * sizeof(float) : hd.size() * sizeof(double);
     void* d = nullptr;
     if (cudaMalloc(&d, bytes) != cudaSuccess) {
       cudaGetLastError();
       return EPFFT_ERR_OOM;
     }
-    if (prec == EPFFT_FP32) {
-      std::vector<float> h;
-      fill_tables<float>(L, h);
-      CK(cudaMemcpy(d, h.data(), bytes, cudaMemcpyHostToDevice));
-    } else {
-      std::vector<double> h;
-      fill_tables<double>(L, h);
-      CK(cudaMemcpy(d, h.data(), bytes, cudaMemcpyHostToDevice));
-    }
-    it = c->tables.emplace(key, d).first;
+    if (prec == EPFFT_FP32) CK(cudaMemcpy(d, hf.data(), bytes, cudaMemcpyHostToDevice));
+    else CK(cudaMemcpy(d, hd.data(), bytes, cudaMemcpyHostToDevice));
+    it = c->tables.emplace(key, std::make_pair(d, koff)).first;
   }
-  *tw = it->second;
-  *ktab = (char*)it->second + (size_t)2 * L * real_size(prec);
+  *tw = it->second.first;
+  *ktab = (char*)it->second.first + (size_t)2 * it->second.second * real_size(prec);
   return EPFFT_OK;
 }
 
@@ -913,7 +898,7 @@ void epfft_destroy(epfft_ctx* c) {
   cudaSetDevice(c->device);
   if (c->server) epfft_serve_close(c);
   cudaStreamSynchronize(c->stream);
-  for (auto& t : c->tables) cudaFree(t.second);
+  for (auto& t : c->tables) cudaFree(t.second.first);
   cudaStreamDestroy(c->cap);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;

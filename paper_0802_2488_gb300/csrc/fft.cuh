@@ -1,18 +1,24 @@
 // Shared-memory Stockham FFT used by the row and column passes.
 //
-// A CTA transforms NB sequences of length N that live in shared memory in
-// "batch-interleaved" order: element x of sequence b is s[x * XS + b]
-// (XS >= NB; XS > NB when only some of the interleaved sequences are
-// transformed by one call).  Each
-// stage reads R elements spaced N/R apart into registers, applies the stage
-// twiddles, a radix-R butterfly, and writes them back in autosort (Stockham)
-// order; after the last stage the sequences are in natural order, in place.
-// Radix plan: one radix-2 or radix-4 stage first when log2(N) is not a
-// multiple of 3, then radix-8 stages.
+// A CTA transforms NSEQ sequences of length N that live in shared memory,
+// sequence s at s * seq_stride<N>() with element x at pad32(x) = x + x / 32
+// (one unused slot per 32 elements).  A stage of radix R (NS = product of
+// the earlier radices) gives each thread one butterfly index j (consecutive
+// threads take consecutive j of one sequence): it reads x[j + r N/R],
+// applies the twiddles exp(-+2 pi i (j mod NS) r / (NS R)), a radix-R DFT
+// in registers, and writes y[(j / NS) NS R + (j mod NS) + r NS] (autosort),
+// in place between two barriers.  With the padding, both the contiguous
+// reads and the stride-R writes of a warp touch each bank no more often
+// than the data size requires, and for fixed j the R addresses differ by
+// compile-time constants.
 //
-// Twiddles come from a table tw[k] = exp(-2 pi i k / Ltw) (k < Ltw), with
-// Ltw = twstride * N; the table is generated on the host in extended
-// precision and rounded once to T.
+// Radix plan (FftPlan): one smaller radix first when needed, then stages of
+// the largest radix RM (4, 8 or 16).  Twiddles come from a shared-memory
+// copy of a table generated on the host in extended precision and rounded
+// once, per stage and per j mod NS: either every power w^r (full), or
+// w, w^2, w^4, w^8 (compact; the other powers are products of at most three
+// of these, within a few units of rounding), w = exp(-2 pi i (j mod NS) /
+// (NS R)).
 #pragma once
 #include "common.cuh"
 
@@ -20,10 +26,26 @@ namespace epfft {
 
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
 
-template <int N, int NS>
-__host__ __device__ constexpr int stage_radix() {
-  return NS == 1 ? (ilog2c(N) % 3 == 0 ? 8 : (ilog2c(N) % 3 == 1 ? 2 : 4)) : 8;
-}
+// Padded layout of one sequence of length N.
+template <int N>
+__host__ __device__ constexpr int seq_stride() { return N >= 32 ? N + N / 32 : N; }
+__device__ __forceinline__ int pad32(int x) { return x + (x >> 5); }
+
+// Radix plan of a length-N transform with largest radix RM (4, 8 or 16):
+// log2(N) mod log2(RM) first (when not 0), then radix-RM stages.  The stage
+// table holds, for every stage k >= 1, NP arrays of ns(k) entries:
+// compact (NP = log2 R): w, w^2, w^4, ...; full (NP = R - 1): w .. w^(R-1).
+template <int N, int RM, bool FULL>
+struct FftPlan {
+  static constexpr int LG = ilog2c(N), LR = ilog2c(RM);
+  static constexpr int R0 = LG % LR == 0 ? (N < RM ? N : RM) : (1 << (LG % LR));
+  static constexpr int NSTAGES = N <= 1 ? 0 : (LG % LR == 0 ? LG / LR : LG / LR + 1);
+  static constexpr int NP = FULL ? RM - 1 : LR;
+  static __host__ __device__ constexpr int radix(int k) { return k == 0 ? R0 : RM; }
+  static __host__ __device__ constexpr int ns(int k) { return k == 0 ? 1 : R0 * (1 << (LR * (k - 1))); }
+  static __host__ __device__ constexpr int tw_off(int k) { return k <= 1 ? 0 : tw_off(k - 1) + NP * ns(k - 1); }
+  static constexpr int TW_ENTRIES = tw_off(NSTAGES);  // complex entries of the stage table
+};
 
 // Radix-R DFT in registers: forward kernel exp(-2 pi i r k / R), inverse
 // exp(+2 pi i r k / R); unnormalised.
@@ -76,80 +98,191 @@ struct Bfly<T, 8, INV> {
   }
 };
 
-// One Stockham stage (radix R, NS = product of the earlier radices).
-// Must be entered with the data complete in shared memory; ends with a
-// barrier.  blockDim.x == NT.
-template <typename T, int N, int NB, int XS, int NT, int R, int NS, bool INV>
-__device__ __forceinline__ void stockham_stage(C2<T>* s, const C2<T>* __restrict__ tw,
-                                               int twstride) {
-  constexpr int NBF = NB * (N / R);  // butterflies in this stage
-  constexpr int K = (NBF + NT - 1) / NT;
-  C2<T> v[K][R];
+// a times exp(-+ i t) given c = cos t and sn = sin t of the forward kernel
+template <typename T, bool INV>
+__device__ __forceinline__ C2<T> rot_k(C2<T> a, T c, T sn) {
+  const T s = INV ? sn : -sn;  // imaginary part of exp(-+ i t)
+  return mk(a.re * c - a.im * s, a.re * s + a.im * c);
+}
+
+// Radix 16 as 4 x 4: DFT4 over n1 of x[4 n1 + n2], multiplication by
+// exp(-+2 pi i n2 k1 / 16), DFT4 over n2; output index k1 + 4 k2.
+template <typename T, bool INV>
+struct Bfly<T, 16, INV> {
+  static __device__ __forceinline__ void run(C2<T>* v) {
+    C2<T> y[4][4];  // y[n2][k1]
+#pragma unroll
+    for (int n2 = 0; n2 < 4; n2++) {
+      y[n2][0] = v[n2];
+      y[n2][1] = v[4 + n2];
+      y[n2][2] = v[8 + n2];
+      y[n2][3] = v[12 + n2];
+      Bfly<T, 4, INV>::run(y[n2]);
+    }
+    const T c1 = T(0.92387953251128675612818318939678828682);  // cos(pi/8)
+    const T s1 = T(0.38268343236508977172845998403039886676);  // sin(pi/8)
+    const T h = T(0.70710678118654752440084436210485);         // cos(pi/4)
+    // angle 2 pi m / 16: (cos, sin) for m = 1, 2, 3, 6, 9
+    y[1][1] = rot_k<T, INV>(y[1][1], c1, s1);    // m = 1
+    y[1][2] = rot_k<T, INV>(y[1][2], h, h);      // m = 2
+    y[1][3] = rot_k<T, INV>(y[1][3], s1, c1);    // m = 3
+    y[2][1] = rot_k<T, INV>(y[2][1], h, h);      // m = 2
+    y[2][2] = mul_mi<T, INV>(y[2][2]);           // m = 4
+    y[2][3] = rot_k<T, INV>(y[2][3], -h, h);     // m = 6
+    y[3][1] = rot_k<T, INV>(y[3][1], s1, c1);    // m = 3
+    y[3][2] = rot_k<T, INV>(y[3][2], -h, h);     // m = 6
+    y[3][3] = rot_k<T, INV>(y[3][3], -c1, -s1);  // m = 9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; k1++) {
+      C2<T> z[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+      Bfly<T, 4, INV>::run(z);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; k2++) v[k1 + 4 * k2] = z[k2];
+    }
+  }
+};
+
+// Twiddles w^r, r = 1 .. R-1 (conjugated for the inverse kernel), from the
+// stage block tb: full tables hold w^r at tb[(r - 1) NS + jm]; compact ones
+// hold w^(2^p) at tb[p NS + jm], and the other powers are products of at
+// most three of those.
+template <typename T, int R, int NS, bool INV, bool FULL>
+__device__ __forceinline__ void stage_twiddles(const C2<T>* __restrict__ tb, int jm, C2<T> (&w)[16]) {
+  if constexpr (FULL) {
+#pragma unroll
+    for (int r = 1; r < R; r++) {
+      const C2<T> t = tb[(r - 1) * NS + jm];
+      w[r] = INV ? conj(t) : t;
+    }
+  } else {
+    C2<T> p1 = tb[jm];
+    C2<T> p2 = p1, p4 = p1, p8 = p1;
+    if (R > 2) p2 = tb[NS + jm];
+    if (R > 4) p4 = tb[2 * NS + jm];
+    if (R > 8) p8 = tb[3 * NS + jm];
+    if (INV) {
+      p1 = conj(p1);
+      p2 = conj(p2);
+      p4 = conj(p4);
+      p8 = conj(p8);
+    }
+    w[1] = p1;
+    if (R > 2) {
+      w[2] = p2;
+      w[3] = p1 * p2;
+    }
+    if (R > 4) {
+      w[4] = p4;
+      w[5] = p1 * p4;
+      w[6] = p2 * p4;
+      w[7] = w[3] * p4;
+    }
+    if (R > 8) {
+      w[8] = p8;
+#pragma unroll
+      for (int r = 1; r < 8; r++) w[8 + r] = w[r] * p8;
+    }
+  }
+}
+
+// Offsets (in elements) of the r-th read and write of a butterfly from its
+// base address; compile-time for unrolled r.  Reads are N/R apart, writes
+// NS apart; the padding adds one slot per 32 elements crossed (see the
+// derivation in the layout comment of stockham_stage).
+template <int N, int R, int NS>
+__host__ __device__ constexpr int read_off(int r) {
+  return N < 32 ? r * (N / R) : r * (N / R) + (r * (N / R)) / 32;
+}
+template <int N, int R, int NS>
+__host__ __device__ constexpr int write_off(int r) {
+  return N < 32 ? r * NS : r * NS + (r * NS) / 32;
+}
+
+// One Stockham stage K of the length-N plan over NSEQ sequences at
+// s + sq * seq_stride<N>(); tw = shared stage table of N.  Ends with a
+// barrier.
+//   Read base: pad32(j).  For N/R >= 32, pad32(j + r N/R) = pad32(j) +
+//   r N/R (33/32); for N/R < 32, j < N/R and N/R divides 32, so
+//   pad32(j + r N/R) = j + r N/R + (r N/R) / 32.
+//   Write base: with a = (j / NS) NS R, jm = j mod NS < NS: for NS <= 32,
+//   NS divides 32 and a is a multiple of NS R, so pad32(a + jm + r NS) =
+//   a + a/32 + jm + r NS + (r NS)/32; for NS > 32 (a multiple of 32),
+//   pad32(a + jm + r NS) = pad32(a + jm) + r NS (33/32) = pad32(a + jm) +
+//   r NS + (r NS) / 32.
+template <typename T, int N, int RM, bool FULL, int NSEQ, int NT, int K, bool INV>
+__device__ __forceinline__ void stockham_stage(C2<T>* s, const C2<T>* __restrict__ tw) {
+  using P = FftPlan<N, RM, FULL>;
+  constexpr int R = P::radix(K), NS = P::ns(K);
+  constexpr int NJ = N / R;                // butterflies per sequence
+  constexpr int NBF = NSEQ * NJ;           // butterflies in this stage
+  constexpr int KB = (NBF + NT - 1) / NT;  // per thread
+  constexpr int SP = seq_stride<N>();
+  C2<T> v[KB][R];
   const int tid = threadIdx.x;
 #pragma unroll
-  for (int q = 0; q < K; q++) {
+  for (int q = 0; q < KB; q++) {
     const int g = tid + q * NT;
     if (NBF % NT == 0 || g < NBF) {
-      const int b = g % NB, j = g / NB;
+      const int j = g % NJ, sq = g / NJ;
+      const int rb = sq * SP + (NJ >= 32 ? pad32(j) : j);
 #pragma unroll
-      for (int r = 0; r < R; r++) {
-        const int ix = (j + r * (N / R)) * XS + b;
-        v[q][r] = ECHK(ix, N * XS, 101) ? s[ix] : v[q][r];
-      }
-      if (NS > 1) {
-        const int jm = j % NS;
+      for (int r = 0; r < R; r++) v[q][r] = s[rb + read_off<N, R, NS>(r)];
+      if constexpr (NS > 1) {
+        C2<T> w[16];
+        stage_twiddles<T, R, NS, INV, FULL>(tw + P::tw_off(K), j % NS, w);
 #pragma unroll
-        for (int r = 1; r < R; r++) {
-          const int it = (jm * r * (N / (NS * R))) * twstride;
-          C2<T> w = ECHK(it, N * twstride, 102) ? tw[it] : mk(T(1), T(0));
-          if (INV) w.im = -w.im;
-          v[q][r] = v[q][r] * w;
-        }
+        for (int r = 1; r < R; r++) v[q][r] = v[q][r] * w[r];
       }
       Bfly<T, R, INV>::run(v[q]);
     }
   }
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < K; q++) {
+  for (int q = 0; q < KB; q++) {
     const int g = tid + q * NT;
     if (NBF % NT == 0 || g < NBF) {
-      const int b = g % NB, j = g / NB;
-      const int jm = j % NS;
-      const int base = (j / NS) * NS * R + jm;
+      const int j = g % NJ, sq = g / NJ;
+      const int jm = j % NS, a = (j / NS) * NS * R;
+      const int wb = sq * SP + (N < 32 ? a + jm : (NS <= 32 ? a + (a >> 5) + jm : pad32(a + jm)));
+      // a + jm + r NS < N for every r (a is a multiple of NS R below N), so
+      // every write stays inside sequence sq
 #pragma unroll
-      for (int r = 0; r < R; r++) {
-        const int ix = (base + r * NS) * XS + b;
-        if (ECHK(ix, N * XS, 103)) s[ix] = v[q][r];
-      }
+      for (int r = 0; r < R; r++) s[wb + write_off<N, R, NS>(r)] = v[q][r];
     }
   }
   __syncthreads();
 }
 
-template <typename T, int N, int NB, int XS, int NT, bool INV, int NS = 1>
-__device__ __forceinline__ void fft_stages(C2<T>* s, const C2<T>* __restrict__ tw, int twstride) {
-  if constexpr (NS < N) {
-    constexpr int R = stage_radix<N, NS>();
-    stockham_stage<T, N, NB, XS, NT, R, NS, INV>(s, tw, twstride);
-    fft_stages<T, N, NB, XS, NT, INV, NS * R>(s, tw, twstride);
+template <typename T, int N, int RM, bool FULL, int NSEQ, int NT, bool INV, int K = 0>
+__device__ __forceinline__ void fft_stages(C2<T>* s, const C2<T>* __restrict__ tw) {
+  if constexpr (K < FftPlan<N, RM, FULL>::NSTAGES) {
+    stockham_stage<T, N, RM, FULL, NSEQ, NT, K, INV>(s, tw);
+    fft_stages<T, N, RM, FULL, NSEQ, NT, INV, K + 1>(s, tw);
   }
 }
 
-// NG groups of NB sequences; element x of sequence b of group g is at
-// s[x * XS + g * NB + b] (XS >= NG * NB; XS is chosen odd by the callers so
-// that element strides do not fold onto few shared-memory banks).  The groups
-// are transformed together when every thread holds at most 16 elements per
-// stage, else one group at a time.
-template <typename T, int N, int NG, int NB, int XS, int NT, bool INV>
-__device__ __forceinline__ void fft_block(C2<T>* s, const C2<T>* __restrict__ tw, int twstride) {
-  static_assert(XS >= NG * NB, "element stride too small");
-  if constexpr ((NG * NB * N + NT - 1) / NT <= 16) {
-    fft_stages<T, N, NG * NB, XS, NT, INV>(s, tw, twstride);
-  } else {
-#pragma unroll 1
-    for (int g = 0; g < NG; g++) fft_stages<T, N, NB, XS, NT, INV>(s + g * NB, tw, twstride);
-  }
+// Transforms NSEQ sequences of length N (layout above) in place with the
+// plan FftPlan<N, RM, FULL> and its stage table tw (shared memory).  The
+// caller has completed the data and the table (barrier) before the call;
+// the call ends with a barrier.
+template <typename T, int N, int RM, bool FULL, int NSEQ, int NT, bool INV>
+__device__ __forceinline__ void fft_seq(C2<T>* s, const C2<T>* __restrict__ tw) {
+  fft_stages<T, N, RM, FULL, NSEQ, NT, INV>(s, tw);
+}
+
+// Copies n table entries from global to shared memory (no barrier).
+template <typename T, int NT>
+__device__ __forceinline__ void copy_table(C2<T>* dst, const C2<T>* __restrict__ src, int n) {
+  for (int i = threadIdx.x; i < n; i += NT) dst[i] = src[i];
+}
+
+// exp(-2 pi i k / L) for 0 <= k <= L/4 from the octant t[0 .. L/8]:
+// for k > L/8, exp(-i (pi/2 - a)) = (sin a, -cos a) with a = 2 pi (L/4 - k) / L.
+template <typename T, int L>
+__device__ __forceinline__ C2<T> twist_tw(const C2<T>* __restrict__ t, int k) {
+  if (k <= L / 8) return t[k];
+  const C2<T> b = t[L / 4 - k];
+  return mk(-b.im, -b.re);
 }
 
 }  // namespace epfft

@@ -23,6 +23,7 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "physics.cuh"
+#include "tables.cuh"
 
 namespace epfft {
 
@@ -32,33 +33,57 @@ namespace epfft {
 //          bytes of HBM, so each CTA streams long contiguous runs);
 //   V = 1: more, smaller CTAs (several per SM hide memory latency; short
 //          runs rely on the L2 to merge neighbouring CTAs' accesses).
+// Shared memory of a pass: its sequences (padded, fft.cuh), then its stage
+// table, then (row pass) the twist octant.
 template <typename T, int L, int V = 0>
 struct Cfg {
   static constexpr bool F64 = sizeof(T) == 8;
   static constexpr int M = L / 2;
+  using PS = PlanSel<T, L, V>;
+  using PR = typename PS::PR;
+  using PC = typename PS::PC;
+  using TB = Tables<T, L>;
+  static constexpr int RM_ROW = PS::RM_ROW, RM_COL = PS::RM_COL;
+  static constexpr bool FULL = PS::FULL;
   // rows per row-pass CTA
-  static constexpr int RR = V == 0 ? (F64 ? (L <= 512 ? 2 : 4) : (L <= 256 ? 2 : (L <= 2048 ? 8 : 4)))
-                                   : (F64 ? (L <= 512 ? 4 : 2) : (L <= 256 ? 1 : (L <= 2048 ? 2 : 1)));
+  static constexpr int RR = V == 0 ? (F64 ? 2 : (L <= 256 ? 2 : (L <= 2048 ? 8 : 4)))
+                                   : (F64 ? (L <= 256 ? 1 : 2) : (L <= 256 ? 1 : 2));
   // columns per column-pass CTA (= tile width of the spectrum layout)
-  static constexpr int W0 = V == 0 ? (F64 ? (L <= 256 ? 1 : (L <= 512 ? 2 : (L <= 1024 ? 4 : 2)))
+  static constexpr int W0 = V == 0 ? (F64 ? (L <= 256 ? 1 : (L <= 1024 ? 2 : 1))
                                           : (L <= 256 ? 2 : (L <= 512 ? 8 : (L <= 2048 ? 4 : 2))))
-                                   : (F64 ? 1 : (L <= 256 ? 1 : (L <= 2048 ? 2 : 1)));
+                                   : (F64 ? 1 : (L <= 256 ? 1 : (L <= 1024 ? 2 : 1)));
   static constexpr int W = W0 < M ? W0 : M;
-  static constexpr int NT_ROW = L < 32 ? 32 : (L <= 256 ? L : (V == 0 ? 512 : 256));
-  static constexpr int NT_COL0 = ((3 * W * L / 8 + 31) / 32) * 32;
-  static constexpr int NT_COL = NT_COL0 < 32 ? 32 : (NT_COL0 > 512 ? 512 : NT_COL0);
-  // element strides of the interleaved shared-memory batches, made odd so
-  // that consecutive elements of one sequence fall on distinct banks
-  static constexpr int XR = (3 * RR) % 2 == 0 ? 3 * RR + 1 : 3 * RR;
-  static constexpr int XC = (3 * W) % 2 == 0 ? 3 * W + 1 : 3 * W;
-  static constexpr size_t ROW_SMEM = (size_t)XR * M * sizeof(C2<T>);
-  static constexpr size_t COL_SMEM = (size_t)XC * L * sizeof(C2<T>);
+  static constexpr int NTMAX = V == 0 ? 512 : 256;
+  // FP32 variant 1 asks for two resident CTAs per SM (at most 128
+  // registers per thread at 256 threads)
+  static constexpr int MINB = V == 1 && !F64 ? 2 : 1;
+  static constexpr int NT_ROW0 = F64 ? (V == 0 || L > 512 ? (L < 256 ? L : 256) : (L < 128 ? L : 128))
+                                     : (L <= 256 ? L : NTMAX);
+  static constexpr int NT_ROW = NT_ROW0 < 32 ? 32 : NT_ROW0;
+  static constexpr int NT_COL0 = ((3 * W * L / RM_COL + 31) / 32) * 32;
+  static constexpr int NT_COL = NT_COL0 < 32 ? 32 : (NT_COL0 > NTMAX ? NTMAX : NT_COL0);
+  // sequences transformed per call: the largest divisor of the sequence
+  // count that keeps at most 16 elements per thread and stage
+  static constexpr int grp(int S, int N, int NT) {
+    int g = S;
+    while (g > 1 && (S % g != 0 || g * N > 16 * NT)) g--;
+    return g;
+  }
+  static constexpr int SP_R = seq_stride<M>(), SP_C = seq_stride<L>();
+  static constexpr int G_R = grp(3 * RR, M, NT_ROW), G_C = grp(3 * W, L, NT_COL);
+  static constexpr int ROW_DATA = (3 * RR * SP_R + 1) / 2 * 2;
+  static constexpr int COL_DATA = (3 * W * SP_C + 1) / 2 * 2;
+  static constexpr int ROW_TW = PR::TW_ENTRIES, COL_TW = PC::TW_ENTRIES;
+  static constexpr size_t ROW_SMEM = (size_t)(ROW_DATA + ROW_TW + TB::OCT) * sizeof(C2<T>);
+  static constexpr size_t COL_SMEM = (size_t)(COL_DATA + COL_TW) * sizeof(C2<T>);
   static_assert(L >= 4 && (L & (L - 1)) == 0, "L must be a power of two >= 4");
   static_assert(M % W == 0, "tile width must divide L/2");
   static_assert(L % RR == 0, "rows per CTA must divide L");
-  static_assert(ROW_SMEM <= 225000 && COL_SMEM <= 230000, "shared memory per CTA");
+  // 227 KB per CTA, less the static arrays of the row pass
+  static_assert(ROW_SMEM <= 222000 && COL_SMEM <= 230000, "shared memory per CTA");
   static_assert(NT_ROW % 32 == 0 && NT_COL % 32 == 0, "whole warps");
   static_assert(L <= NT_ROW || L % NT_ROW == 0, "pixel mapping");
+  static_assert(G_R * M <= 16 * NT_ROW && G_C * L <= 16 * NT_COL, "elements per thread and stage");
 };
 
 template <typename T>
@@ -87,22 +112,28 @@ struct Vec4<double> {
 };
 
 // ---------------------------------------------------------------------------
-// Row-side helpers.  Shared-memory layout of the RR rows: element n of
-// component c of row r at sp[n * XS + c * RR + r], XS = 3RR rounded up to odd.
+// Row-side helpers.  Shared memory holds 3 x RR sequences of length M
+// (sequence c * RR + r = component c of row r, padded layout of fft.cuh),
+// then the row plan's stage table, then the twist octant.
 // ---------------------------------------------------------------------------
-template <typename T, int L, int RR, int W, int NT>
+template <typename T, int L, int V>
 struct RowIO {
-  static constexpr int M = L / 2, NB = 3 * RR, NBK = M / W;
-  static constexpr int XS = NB % 2 == 0 ? NB + 1 : NB;  // element stride (odd)
+  using C = Cfg<T, L, V>;
+  static constexpr int M = L / 2, RR = C::RR, W = C::W, NT = C::NT_ROW, NBK = M / W;
+  static constexpr int SP = C::SP_R, NSEQ = 3 * RR;
+  static constexpr int SZ = C::ROW_DATA;
 
-  // Position of chunk element e (c, b, r, w) in shared and global memory.
+  // shared index of element n of component c of row r
+  static __device__ __forceinline__ int at(int c, int r, int n) { return (c * RR + r) * SP + pad32(n); }
+
+  // Chunk element e (c, b, r, w) of the RR rows: shared and global index.
   static __device__ __forceinline__ void where(int e, int r0, int& is, size_t& ig) {
     const int c = e / (M * RR);
     const int rem = e - c * (M * RR);
     const int b = rem / (RR * W);
     const int rem2 = rem - b * (RR * W);
     const int r = rem2 / W, w = rem2 - r * W;
-    is = (b * W + w) * XS + c * RR + r;
+    is = at(c, r, b * W + w);
     ig = ((size_t)(c * NBK + b) * L + r0 + r) * W + w;
   }
   // FP32 complex numbers are moved two at a time (16-byte accesses) when a
@@ -117,7 +148,7 @@ struct RowIO {
         size_t ig0, ig1;
         where(2 * e2, r0, is0, ig0);
         where(2 * e2 + 1, r0, is1, ig1);
-        if (ECHK(is0, M * XS, 1) && ECHK(is1, M * XS, 1) && ECHK(ig0 + 1, (size_t)3 * M * L, 2)) {
+        if (ECHK(is0, SZ, 1) && ECHK(is1, SZ, 1) && ECHK(ig0 + 1, (size_t)3 * M * L, 2)) {
           const float4 v = *reinterpret_cast<const float4*>(spec + ig0);
           reinterpret_cast<float2*>(sp)[is0] = make_float2(v.x, v.y);
           reinterpret_cast<float2*>(sp)[is1] = make_float2(v.z, v.w);
@@ -129,7 +160,7 @@ struct RowIO {
         int is;
         size_t ig;
         where(e, r0, is, ig);
-        if (ECHK(is, M * XS, 1) && ECHK(ig, (size_t)3 * M * L, 2)) sp[is] = spec[ig];
+        if (ECHK(is, SZ, 1) && ECHK(ig, (size_t)3 * M * L, 2)) sp[is] = spec[ig];
       }
     }
   }
@@ -141,7 +172,7 @@ struct RowIO {
         size_t ig0, ig1;
         where(2 * e2, r0, is0, ig0);
         where(2 * e2 + 1, r0, is1, ig1);
-        if (ECHK(is0, M * XS, 3) && ECHK(is1, M * XS, 3) && ECHK(ig0 + 1, (size_t)3 * M * L, 4)) {
+        if (ECHK(is0, SZ, 3) && ECHK(is1, SZ, 3) && ECHK(ig0 + 1, (size_t)3 * M * L, 4)) {
           const float2 a = reinterpret_cast<const float2*>(sp)[is0];
           const float2 b = reinterpret_cast<const float2*>(sp)[is1];
           *reinterpret_cast<float4*>(spec + ig0) = make_float4(a.x, a.y, b.x, b.y);
@@ -153,7 +184,7 @@ struct RowIO {
         int is;
         size_t ig;
         where(e, r0, is, ig);
-        if (ECHK(is, M * XS, 3) && ECHK(ig, (size_t)3 * M * L, 4)) spec[ig] = sp[is];
+        if (ECHK(is, SZ, 3) && ECHK(ig, (size_t)3 * M * L, 4)) spec[ig] = sp[is];
       }
     }
   }
@@ -161,56 +192,71 @@ struct RowIO {
   // Z(k) = (Y(k) + Y*(M-k)) + i exp(+2 pi i k / L) (Y(k) - Y*(M-k)),
   // with Y(0) = Re S(0), Y(M) = Im S(0).  Unnormalised: the inverse
   // half-length transform of Z then yields x(2n) + i x(2n+1) of
-  // x(x1) = sum_m Y(m) exp(+2 pi i m x1 / L).
-  static __device__ __forceinline__ void c2r_twist(C2<T>* sp, const C2<T>* __restrict__ tw) {
+  // x(x1) = sum_m Y(m) exp(+2 pi i m x1 / L).  Consecutive threads take
+  // consecutive k of one sequence.
+  static __device__ __forceinline__ void c2r_twist(C2<T>* sp, const C2<T>* __restrict__ oct) {
     constexpr int NP = M / 2 + 1;
-    for (int e = threadIdx.x; e < NB * NP; e += NT) {
-      const int k = e / NB, cr = e - k * NB;
-      C2<T>* s = sp + cr;
+    for (int e = threadIdx.x; e < NSEQ * NP; e += NT) {
+      const int sq = e / NP, k = e - sq * NP;
+      C2<T>* s = sp + sq * SP;
       if (k == 0) {
         const C2<T> s0 = s[0];
         s[0] = mk(s0.re + s0.im, s0.re - s0.im);
       } else {
         const int kk = M - k;
-        if (!ECHK(k * XS + cr, M * XS, 5) || !ECHK(kk * XS + cr, M * XS, 6)) continue;
-        const C2<T> a = s[k * XS], b = s[kk * XS];
-        const C2<T> wk = conj(tw[k]);
+        const int ik = pad32(k), ikk = pad32(kk);
+        if (!ECHK(sq * SP + ik, SZ, 5) || !ECHK(sq * SP + ikk, SZ, 6)) continue;
+        const C2<T> a = s[ik], b = s[ikk];
+        const C2<T> wk = conj(twist_tw<T, L>(oct, k));
         const C2<T> zk = (a + conj(b)) + mul_i(wk * (a - conj(b)));
-        s[k * XS] = zk;
-        if (kk != k) s[kk * XS] = (b + conj(a)) - mul_i(conj(wk) * (b - conj(a)));
+        s[ik] = zk;
+        if (kk != k) s[ikk] = (b + conj(a)) - mul_i(conj(wk) * (b - conj(a)));
       }
     }
   }
   // Z = transform of z(n) = x(2n) + i x(2n+1) -> packed half spectrum of x:
   // X(k) = [(Z(k) + Z*(M-k)) - i exp(-2 pi i k / L) (Z(k) - Z*(M-k))] / 2,
   // S(0) = X(0) + i X(M).
-  static __device__ __forceinline__ void r2c_twist(C2<T>* sp, const C2<T>* __restrict__ tw) {
+  static __device__ __forceinline__ void r2c_twist(C2<T>* sp, const C2<T>* __restrict__ oct) {
     constexpr int NP = M / 2 + 1;
-    for (int e = threadIdx.x; e < NB * NP; e += NT) {
-      const int k = e / NB, cr = e - k * NB;
-      C2<T>* s = sp + cr;
+    for (int e = threadIdx.x; e < NSEQ * NP; e += NT) {
+      const int sq = e / NP, k = e - sq * NP;
+      C2<T>* s = sp + sq * SP;
       if (k == 0) {
         const C2<T> z = s[0];
         s[0] = mk(z.re + z.im, z.re - z.im);
       } else {
         const int kk = M - k;
-        if (!ECHK(k * XS + cr, M * XS, 7) || !ECHK(kk * XS + cr, M * XS, 8)) continue;
-        const C2<T> a = s[k * XS], b = s[kk * XS];
-        const C2<T> wk = tw[k];
-        s[k * XS] = T(0.5) * ((a + conj(b)) - mul_i(wk * (a - conj(b))));
-        if (kk != k) s[kk * XS] = T(0.5) * ((b + conj(a)) + mul_i(conj(wk) * (b - conj(a))));
+        const int ik = pad32(k), ikk = pad32(kk);
+        if (!ECHK(sq * SP + ik, SZ, 7) || !ECHK(sq * SP + ikk, SZ, 8)) continue;
+        const C2<T> a = s[ik], b = s[ikk];
+        const C2<T> wk = twist_tw<T, L>(oct, k);
+        s[ik] = T(0.5) * ((a + conj(b)) - mul_i(wk * (a - conj(b))));
+        if (kk != k) s[ikk] = T(0.5) * ((b + conj(a)) + mul_i(conj(wk) * (b - conj(a))));
       }
     }
   }
+  // Half-length transforms of all 3 RR sequences, C::G_R per call.
   template <bool INV>
-  static __device__ __forceinline__ void fft(C2<T>* sp, const C2<T>* __restrict__ tw) {
-    // three groups (components) of RR rows each
-    fft_block<T, M, 3, RR, XS, NT, INV>(sp, tw, 2);
+  static __device__ __forceinline__ void fft(C2<T>* sp, const C2<T>* __restrict__ stw) {
+    constexpr int G = C::G_R;
+#pragma unroll 1
+    for (int g = 0; g < NSEQ / G; g++)
+      fft_seq<T, M, C::RM_ROW, C::FULL, G, NT, INV>(sp + g * G * SP, stw);
   }
+  // Stage table and twist octant: global -> shared (no barrier).  Returns
+  // the shared stage table; the octant follows it.
+  static __device__ __forceinline__ const C2<T>* load_tables(C2<T>* sp, const C2<T>* __restrict__ tab) {
+    C2<T>* stw = sp + SZ;
+    copy_table<T, NT>(stw, tab + C::TB::off_row(V), C::ROW_TW);
+    copy_table<T, NT>(stw + C::ROW_TW, tab, C::TB::OCT);
+    return stw;
+  }
+  static __device__ __forceinline__ const C2<T>* octant(const C2<T>* stw) { return stw + C::ROW_TW; }
   // real value of pixel x1 of component c, row r
   static __device__ __forceinline__ T& px(C2<T>* sp, int c, int r, int x1) {
-    const int ix = 2 * ((x1 >> 1) * XS + c * RR + r) + (x1 & 1);
-    return reinterpret_cast<T*>(sp)[ECHK(ix, 2 * M * XS, 9) ? ix : 0];
+    const int ix = 2 * at(c, r, x1 >> 1) + (x1 & 1);
+    return reinterpret_cast<T*>(sp)[ECHK(ix, 2 * SZ, 9) ? ix : 0];
   }
 };
 
@@ -401,13 +447,13 @@ __device__ __forceinline__ void batch_arrive(Solve* solves, int nb, BatchCtl* bc
 // Row pass
 // ---------------------------------------------------------------------------
 template <typename T, int L, int V>
-__global__ void __launch_bounds__(Cfg<T, L, V>::NT_ROW)
+__global__ void __launch_bounds__(Cfg<T, L, V>::NT_ROW, Cfg<T, L, V>::MINB)
 row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restrict__ tw,
          cudaGraphConditionalHandle cond, int use_cond) {
   using C = Cfg<T, L, V>;
   constexpr int RR = C::RR, W = C::W, NT = C::NT_ROW, M = C::M;
   constexpr int P = L >= NT ? L / NT : 1;
-  using IO = RowIO<T, L, RR, W, NT>;
+  using IO = RowIO<T, L, V>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C2<T>* sp = reinterpret_cast<C2<T>*>(smraw);
   __shared__ bool s_last;
@@ -429,6 +475,9 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
     const uint8_t* __restrict__ mask = S.mask;
     const Mat<T> m = make_mat<T>(S);
     const size_t LL = (size_t)L * L;
+    // stage table and twist octant (first read after the next barrier of
+    // every phase)
+    const C2<T>* stw = IO::load_tables(sp, tw);
     T acc[N_ACC];
 #pragma unroll
     for (int i = 0; i < N_ACC; i++) acc[i] = T(0);
@@ -474,9 +523,9 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
       load_E(S.path + 4 * inc, E);
       IO::load(sp, spec, r0);
       __syncthreads();
-      IO::c2r_twist(sp, tw);
+      IO::c2r_twist(sp, IO::octant(stw));
       __syncthreads();
-      IO::template fft<true>(sp, tw);
+      IO::template fft<true>(sp, stw);
       // halo row x2 = r0 - 1: sigma12 and sigma22 of eps^n for the backward
       // difference along x2
       T prev12[P], prev22[P];
@@ -496,88 +545,133 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
           prev22[j] = s[1];
         }
       }
-      // Left neighbours (x - e^1) for the divergence: the previous lane by a
-      // warp shuffle; lane 0 takes the last lane of the previous warp (or of
-      // the last warp, one pixel group back) from a small per-row exchange,
-      // double-buffered by row parity so one barrier per row suffices.
-      constexpr int NW = NT / 32;
-      __shared__ T edge[2][2][NW][P];
-      const int lane = tid & 31, wid = tid >> 5;
-      for (int r = 0; r < RR; r++) {
-        const int par = r & 1;
-        T en[P][4], s[P][4];
-        bool vv[P];
+      // Pixel update of the AL iteration at (r, x1), given eps^n (en), its
+      // stress s and the left neighbour's sigma11, sigma12 (x - e^1).
+      auto update = [&](int r, int j, const T (&en)[4], bool v, const T (&sj)[4], T l11, T l12) {
+        const int x1 = tid + j * NT;
+        if (x1 >= L) return;
+        const size_t x = (size_t)(r0 + r) * L + x1;
+        // Eq. 1: div_i = sum_j sigma_ij(x) - sigma_ij(x - e^j)
+        const T d1 = (sj[0] - l11) + (sj[3] - prev12[j]);
+        const T d2 = (sj[3] - l12) + (sj[1] - prev22[j]);
+        prev12[j] = sj[3];
+        prev22[j] = sj[1];
 #pragma unroll
-        for (int j = 0; j < P; j++) {
-          const int x1 = tid + j * NT;
-          const size_t x = (size_t)(r0 + r) * L + x1;
-          const bool act = x1 < L && ECHK(x, LL, 23);
-          vv[j] = act ? mask[x] != 0 : true;
-          if (act) Vec4<T>::load(ein + 4 * x, en[j]);
-          else en[j][0] = en[j][1] = en[j][2] = en[j][3] = T(0);
-          const bool pl = sigma(en[j], vv[j], m, s[j]);
-          acc[A_NPL] += pl ? T(1) : T(0);
-          if (L >= 32 && lane == 31) {
-            edge[par][0][wid][j] = s[j][0];
-            edge[par][1][wid][j] = s[j][3];
+        for (int c = 0; c < 4; c++) {
+          acc[A_S11 + c] += sj[c];
+          acc[A_E11 + c] += en[c];
+        }
+        acc[A_DIV2] += d1 * d1 + d2 * d2;
+        // augmented-Lagrangian update of this pixel
+        T e[4] = {IO::px(sp, 0, r, x1), IO::px(sp, 1, r, x1), E[2], IO::px(sp, 2, r, x1)};
+        T c0[4], tau[4], e1[4];
+        c0_apply(e, m, c0);
+#pragma unroll
+        for (int c = 0; c < 4; c++) tau[c] = sj[c] + c0[c];
+        local_solve(tau, v, m, e1);
+        Vec4<T>::store(eout + 4 * x, e1);
+        const T q0 = e1[0] - e[0], q1 = e1[1] - e[1], q2 = e1[2] - e[2], q3 = e1[3] - e[3];
+        acc[A_COMP] += q0 * q0 + q1 * q1 + q2 * q2 + T(2) * q3 * q3;
+        T s1[4];
+        sigma(e1, v, m, s1);
+        c0_apply(e1, m, c0);
+        IO::px(sp, 0, r, x1) = s1[0] - c0[0];
+        IO::px(sp, 1, r, x1) = s1[1] - c0[1];
+        IO::px(sp, 2, r, x1) = s1[3] - c0[3];
+      };
+      const int lane = tid & 31;
+      if constexpr (sizeof(T) == 4) {
+        // Left neighbours: the previous lane by a warp shuffle; lane 0
+        // re-evaluates sigma at x - e^1 (periodic) from memory, so no
+        // per-pixel state is held across a barrier.
+        for (int r = 0; r < RR; r++) {
+          T en[P][4];
+          bool vv[P];
+#pragma unroll
+          for (int j = 0; j < P; j++) {
+            const int x1 = tid + j * NT;
+            const size_t x = (size_t)(r0 + r) * L + x1;
+            const bool act = x1 < L && ECHK(x, LL, 23);
+            vv[j] = act ? mask[x] != 0 : true;
+            if (act) Vec4<T>::load(ein + 4 * x, en[j]);
+            else en[j][0] = en[j][1] = en[j][2] = en[j][3] = T(0);
+          }
+#pragma unroll
+          for (int j = 0; j < P; j++) {
+            T sj[4];
+            const bool pl = sigma(en[j], vv[j], m, sj);
+            acc[A_NPL] += pl ? T(1) : T(0);
+            T l11 = __shfl_up_sync(0xffffffffu, sj[0], 1);
+            T l12 = __shfl_up_sync(0xffffffffu, sj[3], 1);
+            const int x1 = tid + j * NT;
+            if (lane == 0 && x1 < L) {
+              const size_t xl = (size_t)(r0 + r) * L + ((x1 + L - 1) & (L - 1));
+              if (ECHK(xl, LL, 24)) {
+                T el[4], sl[4];
+                Vec4<T>::load(ein + 4 * xl, el);
+                sigma(el, mask[xl] != 0, m, sl);
+                l11 = sl[0];
+                l12 = sl[3];
+              }
+            }
+            update(r, j, en[j], vv[j], sj, l11, l12);
           }
         }
-        __syncthreads();
+      } else {
+        // Left neighbours: the previous lane by a warp shuffle; lane 0 takes
+        // the last lane of the previous warp (or of the last warp, one pixel
+        // group back) from a small per-row exchange, double-buffered by row
+        // parity so one barrier per row suffices.
+        constexpr int NW = NT / 32;
+        __shared__ T edge[2][2][NW][P];
+        const int wid = tid >> 5;
+        for (int r = 0; r < RR; r++) {
+          const int par = r & 1;
+          T en[P][4], s[P][4];
+          bool vv[P];
 #pragma unroll
-        for (int j = 0; j < P; j++) {
-          T l11, l12;
-          if constexpr (L < 32) {
-            const int src = (lane + L - 1) & (L - 1);
-            l11 = __shfl_sync(0xffffffffu, s[j][0], src);
-            l12 = __shfl_sync(0xffffffffu, s[j][3], src);
-          } else {
-            l11 = __shfl_up_sync(0xffffffffu, s[j][0], 1);
-            l12 = __shfl_up_sync(0xffffffffu, s[j][3], 1);
-            if (lane == 0) {
-              const int pw = wid > 0 ? wid - 1 : NW - 1;
-              const int pj = wid > 0 ? j : (j + P - 1) % P;
-              l11 = edge[par][0][pw][pj];
-              l12 = edge[par][1][pw][pj];
+          for (int j = 0; j < P; j++) {
+            const int x1 = tid + j * NT;
+            const size_t x = (size_t)(r0 + r) * L + x1;
+            const bool act = x1 < L && ECHK(x, LL, 23);
+            vv[j] = act ? mask[x] != 0 : true;
+            if (act) Vec4<T>::load(ein + 4 * x, en[j]);
+            else en[j][0] = en[j][1] = en[j][2] = en[j][3] = T(0);
+            const bool pl = sigma(en[j], vv[j], m, s[j]);
+            acc[A_NPL] += pl ? T(1) : T(0);
+            if (L >= 32 && lane == 31) {
+              edge[par][0][wid][j] = s[j][0];
+              edge[par][1][wid][j] = s[j][3];
             }
           }
-          const int x1 = tid + j * NT;
-          if (x1 >= L) continue;
-          const size_t x = (size_t)(r0 + r) * L + x1;
-          // Eq. 1: div_i = sum_j sigma_ij(x) - sigma_ij(x - e^j)
-          const T d1 = (s[j][0] - l11) + (s[j][3] - prev12[j]);
-          const T d2 = (s[j][3] - l12) + (s[j][1] - prev22[j]);
-          prev12[j] = s[j][3];
-          prev22[j] = s[j][1];
+          __syncthreads();
 #pragma unroll
-          for (int c = 0; c < 4; c++) {
-            acc[A_S11 + c] += s[j][c];
-            acc[A_E11 + c] += en[j][c];
+          for (int j = 0; j < P; j++) {
+            T l11, l12;
+            if constexpr (L < 32) {
+              const int src = (lane + L - 1) & (L - 1);
+              l11 = __shfl_sync(0xffffffffu, s[j][0], src);
+              l12 = __shfl_sync(0xffffffffu, s[j][3], src);
+            } else {
+              l11 = __shfl_up_sync(0xffffffffu, s[j][0], 1);
+              l12 = __shfl_up_sync(0xffffffffu, s[j][3], 1);
+              if (lane == 0) {
+                const int pw = wid > 0 ? wid - 1 : NW - 1;
+                const int pj = wid > 0 ? j : (j + P - 1) % P;
+                l11 = edge[par][0][pw][pj];
+                l12 = edge[par][1][pw][pj];
+              }
+            }
+            update(r, j, en[j], vv[j], s[j], l11, l12);
           }
-          acc[A_DIV2] += d1 * d1 + d2 * d2;
-          // augmented-Lagrangian update of this pixel
-          T e[4] = {IO::px(sp, 0, r, x1), IO::px(sp, 1, r, x1), E[2], IO::px(sp, 2, r, x1)};
-          T c0[4], tau[4], e1[4];
-          c0_apply(e, m, c0);
-#pragma unroll
-          for (int c = 0; c < 4; c++) tau[c] = s[j][c] + c0[c];
-          local_solve(tau, vv[j], m, e1);
-          Vec4<T>::store(eout + 4 * x, e1);
-          const T q0 = e1[0] - e[0], q1 = e1[1] - e[1], q2 = e1[2] - e[2], q3 = e1[3] - e[3];
-          acc[A_COMP] += q0 * q0 + q1 * q1 + q2 * q2 + T(2) * q3 * q3;
-          T s1[4];
-          sigma(e1, vv[j], m, s1);
-          c0_apply(e1, m, c0);
-          IO::px(sp, 0, r, x1) = s1[0] - c0[0];
-          IO::px(sp, 1, r, x1) = s1[1] - c0[1];
-          IO::px(sp, 2, r, x1) = s1[3] - c0[3];
         }
       }
     }
 
     if (phase == PH_ITER || phase == PH_INIT) {
       __syncthreads();
-      IO::template fft<false>(sp, tw);
-      IO::r2c_twist(sp, tw);
+      IO::template fft<false>(sp, stw);
+      IO::r2c_twist(sp, IO::octant(stw));
       __syncthreads();
       IO::store(sp, spec, r0);
     }
@@ -613,14 +707,17 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
 // Column pass
 // ---------------------------------------------------------------------------
 template <typename T, int L, int V>
-__global__ void __launch_bounds__(Cfg<T, L, V>::NT_COL)
+__global__ void __launch_bounds__(Cfg<T, L, V>::NT_COL, Cfg<T, L, V>::MINB)
 col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* __restrict__ ktab,
          cudaGraphConditionalHandle cond, int use_cond) {
   using C = Cfg<T, L, V>;
-  constexpr int W = C::W, NT = C::NT_COL, M = C::M, NBK = M / W;
-  constexpr int XS = C::XC;  // element stride (3W rounded up to odd)
+  constexpr int W = C::W, NT = C::NT_COL, M = C::M, NBK = M / W, SP = C::SP_C, SZ = C::COL_DATA;
   extern __shared__ __align__(16) unsigned char smraw[];
-  C2<T>* sp = reinterpret_cast<C2<T>*>(smraw);  // element (c, w) of row x2 at sp[x2*XS + c*W + w]
+  // 3 W sequences of length L (sequence c * W + w = component c of column
+  // w, padded layout of fft.cuh), then the column plan's stage table
+  C2<T>* sp = reinterpret_cast<C2<T>*>(smraw);
+  C2<T>* stw = sp + SZ;
+  auto at = [](int c, int w, int x2) { return (c * W + w) * SP + pad32(x2); };
   const int tid = threadIdx.x;
   // The row pass that follows re-arms the loop; a body that never reaches
   // it must not loop again.
@@ -631,6 +728,7 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
   const int inc = Sv.inc;
   const int b = blockIdx.x;
   C2<T>* spec = reinterpret_cast<C2<T>*>(S.spec);
+  copy_table<T, NT>(stw, tw + C::TB::off_col(V), C::COL_TW);
   // the slab of each component is contiguous in HBM; FP32 numbers move in pairs
   if constexpr (sizeof(C2<T>) == 8) {
 #pragma unroll 4
@@ -640,8 +738,11 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
       const int rem = e - c * (L * W);
       const int xa = rem / W, wa = rem - xa * W, xb = (rem + 1) / W, wb = rem + 1 - xb * W;
       const float4 v = *reinterpret_cast<const float4*>(spec + (size_t)(c * NBK + b) * L * W + rem);
-      reinterpret_cast<float2*>(sp)[xa * XS + c * W + wa] = make_float2(v.x, v.y);
-      reinterpret_cast<float2*>(sp)[xb * XS + c * W + wb] = make_float2(v.z, v.w);
+      const int ia = at(c, wa, xa), ib = at(c, wb, xb);
+      if (ECHK(ia, SZ, 30) && ECHK(ib, SZ, 30)) {
+        reinterpret_cast<float2*>(sp)[ia] = make_float2(v.x, v.y);
+        reinterpret_cast<float2*>(sp)[ib] = make_float2(v.z, v.w);
+      }
     }
   } else {
 #pragma unroll 4
@@ -649,25 +750,29 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
       const int c = e / (L * W);
       const int rem = e - c * (L * W);
       const int x2 = rem / W, w = rem - x2 * W;
-      sp[x2 * XS + c * W + w] = spec[(size_t)(c * NBK + b) * L * W + rem];
+      const int i = at(c, w, x2);
+      if (ECHK(i, SZ, 30)) sp[i] = spec[(size_t)(c * NBK + b) * L * W + rem];
     }
   }
   __syncthreads();
-  fft_block<T, L, 3, W, XS, NT, false>(sp, tw, 1);
+  constexpr int G = C::G_C;
+#pragma unroll 1
+  for (int g = 0; g < 3 * W / G; g++) fft_seq<T, L, C::RM_COL, C::FULL, G, NT, false>(sp + g * G * SP, stw);
 
   const T lam0 = T(S.lam0), mu0 = T(S.mu0);
   const T scale = T(1.0 / ((double)L * (double)L));
-  // frequencies with m1 = b*W + w != 0
+  // frequencies with m1 = b*W + w != 0 (consecutive threads: consecutive m2)
   for (int f = tid; f < W * L; f += NT) {
-    const int m2 = f / W, w = f - m2 * W;
+    const int w = f / L, m2 = f - w * L;
     const int m1 = b * W + w;
     if (m1 == 0) continue;
-    C2<T>* q = sp + m2 * XS + w;
-    C2<T> p11 = q[0], p22 = q[W], p12 = q[2 * W];
+    const int i0 = at(0, w, m2), i1 = at(1, w, m2), i2 = at(2, w, m2);
+    if (!ECHK(i0, SZ, 31) || !ECHK(i1, SZ, 31) || !ECHK(i2, SZ, 31)) continue;
+    C2<T> p11 = sp[i0], p22 = sp[i1], p12 = sp[i2];
     green_apply(ktab[m1], ktab[m2], lam0, mu0, scale, p11, p22, p12);
-    q[0] = p11;
-    q[W] = p22;
-    q[2 * W] = p12;
+    sp[i0] = p11;
+    sp[i1] = p22;
+    sp[i2] = p12;
   }
   if (b == 0) {
     // packed column: Z = A + i B with A the m1 = 0 column and B the
@@ -678,7 +783,7 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
       C2<T> A[3], B[3], Ap[3], Bp[3];
 #pragma unroll
       for (int c = 0; c < 3; c++) {
-        const C2<T> z = sp[m2 * XS + c * W], zp = sp[mp * XS + c * W];
+        const C2<T> z = sp[at(c, 0, m2)], zp = sp[at(c, 0, mp)];
         A[c] = T(0.5) * (z + conj(zp));
         const C2<T> d = z - conj(zp);  // B = d / (2i)
         B[c] = mk(T(0.5) * d.im, T(-0.5) * d.re);
@@ -697,13 +802,14 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
       green_apply(ktab[M], ktab[mp], lam0, mu0, scale, Bp[0], Bp[1], Bp[2]);
 #pragma unroll
       for (int c = 0; c < 3; c++) {
-        sp[m2 * XS + c * W] = A[c] + mul_i(B[c]);
-        if (mp != m2) sp[mp * XS + c * W] = Ap[c] + mul_i(Bp[c]);
+        sp[at(c, 0, m2)] = A[c] + mul_i(B[c]);
+        if (mp != m2) sp[at(c, 0, mp)] = Ap[c] + mul_i(Bp[c]);
       }
     }
   }
   __syncthreads();
-  fft_block<T, L, 3, W, XS, NT, true>(sp, tw, 1);
+#pragma unroll 1
+  for (int g = 0; g < 3 * W / G; g++) fft_seq<T, L, C::RM_COL, C::FULL, G, NT, true>(sp + g * G * SP, stw);
   if constexpr (sizeof(C2<T>) == 8) {
 #pragma unroll 4
     for (int e2 = tid; e2 < 3 * L * W / 2; e2 += NT) {
@@ -711,9 +817,12 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
       const int c = e / (L * W);
       const int rem = e - c * (L * W);
       const int xa = rem / W, wa = rem - xa * W, xb = (rem + 1) / W, wb = rem + 1 - xb * W;
-      const float2 u = reinterpret_cast<const float2*>(sp)[xa * XS + c * W + wa];
-      const float2 v = reinterpret_cast<const float2*>(sp)[xb * XS + c * W + wb];
-      *reinterpret_cast<float4*>(spec + (size_t)(c * NBK + b) * L * W + rem) = make_float4(u.x, u.y, v.x, v.y);
+      const int ia = at(c, wa, xa), ib = at(c, wb, xb);
+      if (ECHK(ia, SZ, 32) && ECHK(ib, SZ, 32)) {
+        const float2 u = reinterpret_cast<const float2*>(sp)[ia];
+        const float2 v = reinterpret_cast<const float2*>(sp)[ib];
+        *reinterpret_cast<float4*>(spec + (size_t)(c * NBK + b) * L * W + rem) = make_float4(u.x, u.y, v.x, v.y);
+      }
     }
   } else {
 #pragma unroll 4
@@ -721,7 +830,8 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
       const int c = e / (L * W);
       const int rem = e - c * (L * W);
       const int x2 = rem / W, w = rem - x2 * W;
-      spec[(size_t)(c * NBK + b) * L * W + rem] = sp[x2 * XS + c * W + w];
+      const int i = at(c, w, x2);
+      if (ECHK(i, SZ, 32)) spec[(size_t)(c * NBK + b) * L * W + rem] = sp[i];
     }
   }
 }
@@ -734,11 +844,12 @@ __global__ void __launch_bounds__(Cfg<T, L, V>::NT_ROW)
 row_forward(const T* __restrict__ p, C2<T>* __restrict__ spec, const C2<T>* __restrict__ tw) {
   using C = Cfg<T, L, V>;
   constexpr int RR = C::RR, W = C::W, NT = C::NT_ROW, P = L >= NT ? L / NT : 1;
-  using IO = RowIO<T, L, RR, W, NT>;
+  using IO = RowIO<T, L, V>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C2<T>* sp = reinterpret_cast<C2<T>*>(smraw);
   const int r0 = blockIdx.x * RR;
   const size_t LL = (size_t)L * L;
+  const C2<T>* stw = IO::load_tables(sp, tw);
   for (int r = 0; r < RR; r++)
     for (int j = 0; j < P; j++) {
       const int x1 = threadIdx.x + j * NT;
@@ -747,8 +858,8 @@ row_forward(const T* __restrict__ p, C2<T>* __restrict__ spec, const C2<T>* __re
       for (int c = 0; c < 3; c++) IO::px(sp, c, r, x1) = p[c * LL + x];
     }
   __syncthreads();
-  IO::template fft<false>(sp, tw);
-  IO::r2c_twist(sp, tw);
+  IO::template fft<false>(sp, stw);
+  IO::r2c_twist(sp, IO::octant(stw));
   __syncthreads();
   IO::store(sp, spec, r0);
 }
@@ -758,16 +869,17 @@ __global__ void __launch_bounds__(Cfg<T, L, V>::NT_ROW)
 row_inverse(const C2<T>* __restrict__ spec, T* __restrict__ e, const C2<T>* __restrict__ tw) {
   using C = Cfg<T, L, V>;
   constexpr int RR = C::RR, W = C::W, NT = C::NT_ROW, P = L >= NT ? L / NT : 1;
-  using IO = RowIO<T, L, RR, W, NT>;
+  using IO = RowIO<T, L, V>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C2<T>* sp = reinterpret_cast<C2<T>*>(smraw);
   const int r0 = blockIdx.x * RR;
   const size_t LL = (size_t)L * L;
+  const C2<T>* stw = IO::load_tables(sp, tw);
   IO::load(sp, spec, r0);
   __syncthreads();
-  IO::c2r_twist(sp, tw);
+  IO::c2r_twist(sp, IO::octant(stw));
   __syncthreads();
-  IO::template fft<true>(sp, tw);
+  IO::template fft<true>(sp, stw);
   for (int r = 0; r < RR; r++)
     for (int j = 0; j < P; j++) {
       const int x1 = threadIdx.x + j * NT;

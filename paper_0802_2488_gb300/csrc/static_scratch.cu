@@ -13,6 +13,7 @@
 
 #include "../../include/epfft.h"
 #include "launch.cuh"
+#include "tables.cuh"
 
 using namespace epfft;
 
@@ -20,12 +21,16 @@ namespace {
 
 constexpr int kMaxL = 256;  // largest lattice side the static scratch holds
 constexpr size_t kSpecBytes = (size_t)3 * kMaxL * (kMaxL / 2) * 16;  // 3 components, FP64 complex
-constexpr size_t kTabBytes = (size_t)4 * kMaxL * 8;                   // tw[L] + k[L], FP64 complex
+// device tables of the largest side in FP64 (the largest of all sides and types)
+constexpr size_t kTabBytes = ((size_t)Tables<double, kMaxL>::TOTAL * 16 + 255) / 256 * 256;
 constexpr size_t kSolveBytes = 512;
 constexpr size_t kPathBytes = 256;
 constexpr size_t kScratchBytes = kSpecBytes + kTabBytes + kSolveBytes + kPathBytes;
 static_assert(sizeof(Solve) <= kSolveBytes, "solve record must fit its slot");
 static_assert(kSpecBytes % 256 == 0 && kTabBytes % 256 == 0, "slots stay 256-byte aligned");
+static_assert(Tables<double, 128>::TOTAL <= Tables<double, kMaxL>::TOTAL &&
+                  Tables<float, kMaxL>::TOTAL <= Tables<double, kMaxL>::TOTAL,
+              "the table slot holds every side up to kMaxL");
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
@@ -57,21 +62,6 @@ int scratch_address(void** out) {
   return EPFFT_OK;
 }
 
-// exp(-2 pi i k / L) and k(m) = (sin q, 2 sin^2(q/2)), q = 2 pi m / L, in
-// extended precision, rounded once to T (host stack buffer, 4L reals).
-template <typename T>
-void host_tables(int L, T* h) {
-  const long double pi = 3.141592653589793238462643383279502884L;
-  for (int k = 0; k < L; k++) {
-    const long double a = 2.0L * pi * (long double)k / (long double)L;
-    const long double hs = sinl(pi * (long double)k / (long double)L);
-    h[2 * k] = (T)cosl(a);
-    h[2 * k + 1] = (T)(-sinl(a));
-    h[2 * L + 2 * k] = (T)sinl(a);
-    h[2 * L + 2 * k + 1] = (T)(2.0L * hs * hs);
-  }
-}
-
 template <typename T>
 int project_static(int L, double lambda0, double mu0, const double E[4], const void* p, void* e, cudaStream_t s) {
   void* base = nullptr;
@@ -81,8 +71,9 @@ int project_static(int L, double lambda0, double mu0, const double E[4], const v
   char* tab = spec + kSpecBytes;
   char* solve = tab + kTabBytes;
   char* path = solve + kSolveBytes;
-  T h[4 * kMaxL];
-  host_tables<T>(L, h);
+  std::vector<T> h;  // host copy of the device tables of L
+  const int koff = host_tables<T>(L, h);
+  if (koff < 0 || h.size() * sizeof(T) > kTabBytes) return EPFFT_ERR_ARG;
   Solve S;
   std::memset(&S, 0, sizeof(S));
   S.lam0 = lambda0;
@@ -91,11 +82,12 @@ int project_static(int L, double lambda0, double mu0, const double E[4], const v
   S.spec = spec;
   S.phase = PH_ITER;
   if (prepare<T>(L, 0) != cudaSuccess) return EPFFT_ERR_CUDA;
-  if (cudaMemcpyAsync(tab, h, sizeof(T) * 4 * L, cudaMemcpyHostToDevice, s) != cudaSuccess) return EPFFT_ERR_CUDA;
+  if (cudaMemcpyAsync(tab, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return EPFFT_ERR_CUDA;
   if (cudaMemcpyAsync(path, E, 4 * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess) return EPFFT_ERR_CUDA;
   if (cudaMemcpyAsync(solve, &S, sizeof(S), cudaMemcpyHostToDevice, s) != cudaSuccess) return EPFFT_ERR_CUDA;
   const void* tw = tab;
-  const void* ktab = tab + sizeof(T) * 2 * L;
+  const void* ktab = tab + sizeof(T) * 2 * koff;
   if (launch_row_forward<T>(L, 0, s, p, spec, tw) != cudaSuccess) return EPFFT_ERR_CUDA;
   if (launch_col<T>(L, 0, 1, s, (Solve*)solve, tw, ktab, 0, 0) != cudaSuccess) return EPFFT_ERR_CUDA;
   if (launch_row_inverse<T>(L, 0, s, spec, e, tw) != cudaSuccess) return EPFFT_ERR_CUDA;

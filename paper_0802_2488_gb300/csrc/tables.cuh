@@ -1,0 +1,111 @@
+// Per-size transform plans and the device tables they read.
+//
+// Every (real type, lattice side) has one table in device memory, built on
+// the host in extended precision and rounded once to T, shared by both
+// tiling variants.  Layout in complex units:
+//   [0, OCT)              exp(-2 pi i k / L), k = 0 .. L/8 (row twists)
+//   [OFF_R[v], +TW_R[v])  stage table of the row plan of variant v
+//   [OFF_C[v], +TW_C[v])  stage table of the column plan of variant v
+//   [KOFF, KOFF + L)      k(m) = (sin q, 2 sin^2(q/2)), q = 2 pi m / L, the
+//                         symbol of the forward difference of Eq. 1
+//                         (i k = exp(i q) - 1)
+// Variants with the same plans share their stage tables.
+#pragma once
+#include <vector>
+
+#include "fft.cuh"
+
+namespace epfft {
+
+// Transform plans of tiling variant V for (T, L): largest radix of the row
+// (length L/2) and column (length L) transforms, and the twiddle format
+// (full tables when they fit beside the data in shared memory).
+template <typename T, int L, int V>
+struct PlanSel {
+  static constexpr bool F64 = sizeof(T) == 8;
+  static constexpr int RM_ROW = F64 ? (V == 0 ? 16 : (L <= 512 ? 4 : 8)) : 16;
+  static constexpr int RM_COL = F64 ? (V == 0 ? 16 : (L <= 512 ? 4 : 8)) : 16;
+  static constexpr bool FULL = F64 ? true : L <= 2048;
+  using PR = FftPlan<L / 2, RM_ROW, FULL>;
+  using PC = FftPlan<L, RM_COL, FULL>;
+};
+
+template <typename T, int L>
+struct Tables {
+  using S0 = PlanSel<T, L, 0>;
+  using S1 = PlanSel<T, L, 1>;
+  static constexpr bool SAME = S0::RM_ROW == S1::RM_ROW && S0::RM_COL == S1::RM_COL && S0::FULL == S1::FULL;
+  static constexpr int OCT = L / 8 + 1;
+  static constexpr int TW_R0 = S0::PR::TW_ENTRIES, TW_C0 = S0::PC::TW_ENTRIES;
+  static constexpr int TW_R1 = S1::PR::TW_ENTRIES, TW_C1 = S1::PC::TW_ENTRIES;
+  static constexpr int OFF_R0 = OCT, OFF_C0 = OFF_R0 + TW_R0;
+  static constexpr int OFF_R1 = SAME ? OFF_R0 : OFF_C0 + TW_C0;
+  static constexpr int OFF_C1 = SAME ? OFF_C0 : OFF_R1 + TW_R1;
+  static constexpr int KOFF = SAME ? OFF_C0 + TW_C0 : OFF_C1 + TW_C1;
+  static constexpr int TOTAL = KOFF + L;
+  static __host__ __device__ constexpr int off_row(int v) { return v == 0 ? OFF_R0 : OFF_R1; }
+  static __host__ __device__ constexpr int off_col(int v) { return v == 0 ? OFF_C0 : OFF_C1; }
+};
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+// exp(-2 pi i n / d) in extended precision, rounded once (real, imag).
+template <typename T>
+inline void host_expi(long n, long d, T* out) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  const long double a = 2.0L * pi * (long double)(n % d) / (long double)d;
+  out[0] = (T)cosl(a);
+  out[1] = (T)(-sinl(a));
+}
+
+// Stage table of plan P at h (complex entries, interleaved reals).
+template <typename T, typename P>
+inline void host_stage_table(T* h) {
+  for (int k = 1; k < P::NSTAGES; k++) {
+    const int R = P::radix(k), NS = P::ns(k);
+    for (int p = 0; p < P::NP; p++) {
+      const int pw = P::NP == R - 1 ? p + 1 : (1 << p);  // full: w^(p+1); compact: w^(2^p)
+      for (int jm = 0; jm < NS; jm++) host_expi<T>((long)jm * pw, (long)NS * R, h + 2 * (P::tw_off(k) + p * NS + jm));
+    }
+  }
+}
+
+template <typename T, int L>
+inline void host_tables_L(std::vector<T>& h) {
+  using TB = Tables<T, L>;
+  h.assign((size_t)2 * TB::TOTAL, T(0));
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int k = 0; k < TB::OCT; k++) host_expi<T>(k, L, h.data() + 2 * k);
+  host_stage_table<T, typename TB::S0::PR>(h.data() + 2 * TB::OFF_R0);
+  host_stage_table<T, typename TB::S0::PC>(h.data() + 2 * TB::OFF_C0);
+  if (!TB::SAME) {
+    host_stage_table<T, typename TB::S1::PR>(h.data() + 2 * TB::OFF_R1);
+    host_stage_table<T, typename TB::S1::PC>(h.data() + 2 * TB::OFF_C1);
+  }
+  for (int m = 0; m < L; m++) {
+    const long double q = 2.0L * pi * (long double)m / (long double)L;
+    const long double hs = sinl(pi * (long double)m / (long double)L);
+    h[2 * (TB::KOFF + m)] = (T)sinl(q);
+    h[2 * (TB::KOFF + m) + 1] = (T)(2.0L * hs * hs);
+  }
+}
+
+// Runtime dispatch over the supported sides: fills h and returns the
+// offset of k(m) (complex units), or -1 for an unsupported L.
+template <typename T>
+inline int host_tables(int L, std::vector<T>& h) {
+  switch (L) {
+#define EPFFT_TAB(n)              \
+  case n:                         \
+    host_tables_L<T, n>(h);       \
+    return Tables<T, n>::KOFF;
+    EPFFT_TAB(4) EPFFT_TAB(8) EPFFT_TAB(16) EPFFT_TAB(32) EPFFT_TAB(64) EPFFT_TAB(128) EPFFT_TAB(256)
+    EPFFT_TAB(512) EPFFT_TAB(1024) EPFFT_TAB(2048) EPFFT_TAB(4096)
+#undef EPFFT_TAB
+    default:
+      return -1;
+  }
+}
+
+}  // namespace epfft

@@ -18,7 +18,9 @@ from . import binding as B
 from . import inputs
 
 
-def measure(ctx, L: int, precision: str, f: float = 0.2, iters: int = 50) -> dict:
+def measure(ctx, L: int, precision: str, f: float = 0.2, iters: int = 50, variant: int | None = None) -> dict:
+    if variant is not None:
+        B.epfft_set_tiling(ctx, L, precision, variant)
     prob = B.Problem(L=L, precision=precision, void_fraction=f, seed=0)
     E = inputs.load_path("shear", 40, 3.0)[20]
     col_ms, row_ms = B.epfft_time_passes(ctx, prob, E, iters)
@@ -28,7 +30,7 @@ def measure(ctx, L: int, precision: str, f: float = 0.2, iters: int = 50) -> dic
     row_b, col_b = (113 if f64 else 57) * n, (48 if f64 else 24) * n
     row_f, col_f = (15 * lg + 60) * n, (15 * lg + 25) * n
     return {
-        "L": L, "precision": precision, "iters": iters,
+        "L": L, "precision": precision, "iters": iters, "variant": variant,
         "col_ms": col_ms, "row_ms": row_ms,
         "col_GBps": col_b / (col_ms * 1e-3) / 1e9, "row_GBps": row_b / (row_ms * 1e-3) / 1e9,
         "col_GFLOPs": col_f / (col_ms * 1e-3) / 1e9, "row_GFLOPs": row_f / (row_ms * 1e-3) / 1e9,
@@ -41,6 +43,8 @@ def main():
     ap.add_argument("--L", type=int, nargs="+", default=[256])
     ap.add_argument("--precision", nargs="+", default=["fp64", "fp32"])
     ap.add_argument("--iters", type=int, default=50)
+    ap.add_argument("--variants", type=int, nargs="*", default=None,
+                    help="compiled tilings to time (default: the context's choice)")
     a = ap.parse_args()
     from . import build
     build.build()
@@ -48,7 +52,8 @@ def main():
         for prec in a.precision:
             for L in a.L:
                 if B.epfft_supported(L, prec):
-                    print(json.dumps(measure(ctx, L, prec, iters=a.iters)), flush=True)
+                    for v in (a.variants if a.variants else [None]):
+                        print(json.dumps(measure(ctx, L, prec, iters=a.iters, variant=v)), flush=True)
 
 
 if __name__ == "__main__":
