@@ -234,6 +234,11 @@ def run_serving(args):
         return B.Problem(L=P.L, precision=args.precision, void_fraction=P.f, seed=P.seed, tol_eq=1e-8,
                          tol_macro=1e-8, max_iter=args.cap)
 
+    # tilings of the served sizes: single solves (the solo probe) and the
+    # 16-slot serving classes
+    for L in (128, 256, 512, 1024):
+        B.epfft_autotune(ctx, L, args.precision, n_batch=1)
+        B.epfft_autotune(ctx, L, args.precision, n_batch=16)
     # solo capacity: a few requests run back to back, one at a time
     probe = inputs.serving_stream(12, 1.0, seed=1000 + rank)
     for r in probe[:2]:
@@ -332,7 +337,7 @@ def main():
         torch.cuda.synchronize(local)
 
     # the autotuner picks the tiling of this lattice size (outside the timed region)
-    tiling, tiling_ms = B.epfft_autotune(ctx, L, args.precision)
+    tiling, tiling_ms = B.epfft_autotune(ctx, L, args.precision, n_batch=len(probs))
     cfg["tiling"] = {"chosen": tiling, "ms_per_iteration": tiling_ms}
     pd = problems(args.precision, False)
     for _ in range(args.warmup):

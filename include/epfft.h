@@ -250,7 +250,7 @@ int epfft_project(epfft_ctx *ctx, int32_t L, int32_t precision, double lambda0, 
  * an allocation that could synchronise the device).  The paper has no
  * counterpart; this is a convenience of the library.
  *
- * All working memory is one static device array of the library (1.58 MB,
+ * All working memory is one static device array of the library (1.59 MB,
  * held on every GPU that loads the library until the process exits), so
  * lattice sides above 256 are rejected with EPFFT_ERR_SCRATCH_LIMIT.  The
  * call allocates nothing: no cudaMalloc, cudaFree or allocating library
@@ -289,12 +289,18 @@ int epfft_time_passes(epfft_ctx *ctx, const epfft_problem *problem, int32_t n_ba
 /* Two tilings are compiled for every lattice side and precision (rows per
  * row-pass CTA, tile width of the spectrum layout = columns per
  * column-pass CTA, threads).  epfft_autotune times both on this device
- * (CUDA events, synthetic f = 0.2 lattice) and makes the faster one the
- * context's tiling for (L, precision); *chosen receives it and
- * ms_per_iteration[2] (optional) the two timings.  Later solves, batches,
- * projections and serving classes of that size use it.  Blocking. */
-int epfft_autotune(epfft_ctx *ctx, int32_t L, int32_t precision, int32_t *chosen, float *ms_per_iteration);
-/* Sets the tiling (0 or 1) of (L, precision) on the context. */
+ * (CUDA events, a batch of n_batch synthetic f = 0.2 lattices) and makes the
+ * faster one the context's tiling for (L, precision) and for batches of
+ * that class: launches that cover at least 2^21 pixels (L^2 x batch) form
+ * one class, smaller ones the other, since small launches favour more and
+ * smaller CTAs and large ones fewer and larger.  *chosen receives the
+ * choice and ms_per_iteration[2] (optional) the two timings.  Later solves,
+ * batches, projections (class of one solve) and serving classes (class of
+ * their slot count) of that size use it.  Blocking. */
+int epfft_autotune(epfft_ctx *ctx, int32_t L, int32_t precision, int32_t n_batch, int32_t *chosen,
+                   float *ms_per_iteration);
+/* Sets the tiling (0 or 1) of (L, precision) on the context, for both
+ * batch classes. */
 int epfft_set_tiling(epfft_ctx *ctx, int32_t L, int32_t precision, int32_t variant);
 
 #ifdef __cplusplus

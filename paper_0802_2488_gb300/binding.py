@@ -115,7 +115,7 @@ def lib():
         L.epfft_submit.argtypes = [vp, C.POINTER(_Problem), C.POINTER(_Path), i32, C.POINTER(C.c_int64)]
         L.epfft_serve_step.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
         L.epfft_poll.argtypes = [vp, C.c_int64, vp, vp, C.POINTER(dbl)]
-        L.epfft_autotune.argtypes = [vp, i32, i32, C.POINTER(i32), C.POINTER(C.c_float)]
+        L.epfft_autotune.argtypes = [vp, i32, i32, i32, C.POINTER(i32), C.POINTER(C.c_float)]
         L.epfft_set_tiling.argtypes = [vp, i32, i32, i32]
         L.epfft_project_static.argtypes = [i32, i32, dbl, dbl, C.POINTER(dbl), vp, vp, vp]
         L.epfft_time_passes.argtypes = [vp, C.POINTER(_Problem), i32, C.POINTER(dbl), i32, C.POINTER(C.c_float),
@@ -433,13 +433,14 @@ def epfft_poll(ctx: Context, ticket: int, problem: Problem, n_inc: int, want_eps
 # Tiling
 # --------------------------------------------------------------------------
 
-def epfft_autotune(ctx: Context, L: int, precision: str):
-    """Times the compiled tilings of (L, precision) and keeps the faster for the
-    context.  Returns (chosen tiling, [ms per iteration of each])."""
+def epfft_autotune(ctx: Context, L: int, precision: str, n_batch: int = 1):
+    """Times the compiled tilings of (L, precision) on a batch of n_batch
+    solves and keeps the faster for the context (for batches of that size
+    class).  Returns (chosen tiling, [ms per iteration of each])."""
     ch = C.c_int32()
     ms = (C.c_float * 2)()
-    _check(lib().epfft_autotune(ctx.handle, L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision], C.byref(ch), ms),
-           "epfft_autotune")
+    _check(lib().epfft_autotune(ctx.handle, L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision], int(n_batch),
+                                C.byref(ch), ms), "epfft_autotune")
     return ch.value, list(ms)
 
 

@@ -36,7 +36,9 @@ struct epfft_ctx {
   // k(m) in it (complex units)
   std::map<std::pair<int, int>, std::pair<void*, int>> tables;
   std::map<std::tuple<int, int, int>, bool> prepared;  // (L, precision, tiling variant)
-  std::map<std::pair<int, int>, int> variant;          // tuned tiling per (L, precision)
+  // tuned tiling per (L, precision, batch class): class 1 when a launch
+  // covers at least 2^21 pixels (enough CTAs to fill the GPU), else 0
+  std::map<std::tuple<int, int, int>, int> variant;
   epfft_stats last{};
   Server* server = nullptr;
 };
@@ -155,8 +157,10 @@ int ensure_prepared(epfft_ctx* c, int L, int prec, int var) {
 }
 
 // Tiling used for (L, precision): the autotuned one, else variant 0.
-int variant_for(epfft_ctx* c, int L, int prec) {
-  auto it = c->variant.find(std::make_pair(L, prec));
+int batch_class(int L, int nb) { return (int64_t)L * L * nb >= ((int64_t)1 << 21) ? 1 : 0; }
+
+int variant_for(epfft_ctx* c, int L, int prec, int nb) {
+  auto it = c->variant.find(std::make_tuple(L, prec, batch_class(L, nb)));
   return it == c->variant.end() ? 0 : it->second;
 }
 
@@ -296,7 +300,7 @@ int setup_batch(epfft_ctx* c, Arena& A, Batch& B, int n, const epfft_problem* pr
   B.L = probs[0].L;
   B.prec = probs[0].precision;
   B.nb = n;
-  if (B.var < 0) B.var = variant_for(c, B.L, B.prec);
+  if (B.var < 0) B.var = variant_for(c, B.L, B.prec, n);
   int rc = shape(B.L, B.prec, B.var, &B.sh);
   if (rc) return rc;
   rc = get_tables(c, B.L, B.prec, &B.tw, &B.ktab);
@@ -702,7 +706,7 @@ int get_class(epfft_ctx* c, Server& S, int L, int prec, ServeClass** out) {
   B.L = L;
   B.prec = prec;
   B.nb = S.cap;
-  B.var = variant_for(c, L, prec);
+  B.var = variant_for(c, L, prec, S.cap);
   int rc = shape(L, prec, B.var, &B.sh);
   if (!rc) rc = get_tables(c, L, prec, &B.tw, &B.ktab);
   if (!rc) rc = ensure_prepared(c, L, prec, B.var);
@@ -973,7 +977,7 @@ int epfft_project(epfft_ctx* ctx, int32_t L, int32_t precision, double lambda0, 
   if (cudaSetDevice(ctx->device) != cudaSuccess) return EPFFT_ERR_CUDA;
   Arena A(ctx);
   void *tw, *ktab;
-  const int var = variant_for(ctx, L, precision);
+  const int var = variant_for(ctx, L, precision, 1);
   int rc = get_tables(ctx, L, precision, &tw, &ktab);
   if (!rc) rc = ensure_prepared(ctx, L, precision, var);
   if (rc) return rc;
@@ -1052,7 +1056,7 @@ int epfft_submit(epfft_ctx* ctx, const epfft_problem* problem, const epfft_path*
     if (!std::isfinite(path->E[k])) return EPFFT_ERR_ARG;
   Server& S = *ctx->server;
   PassShape sh;
-  rc = shape(problem->L, problem->precision, variant_for(ctx, problem->L, problem->precision), &sh);
+  rc = shape(problem->L, problem->precision, variant_for(ctx, problem->L, problem->precision, S.cap), &sh);
   if (rc) return rc;
   Ticket t;
   t.prob = *problem;
@@ -1144,8 +1148,9 @@ int epfft_time_passes(epfft_ctx* ctx, const epfft_problem* problem, int32_t n_ba
   return time_passes_impl(ctx, *problem, n_batch, E, n_iter, -1, col_ms, row_ms);
 }
 
-int epfft_autotune(epfft_ctx* ctx, int32_t L, int32_t precision, int32_t* chosen, float* ms_per_iteration) {
-  if (!ctx) return EPFFT_ERR_ARG;
+int epfft_autotune(epfft_ctx* ctx, int32_t L, int32_t precision, int32_t n_batch, int32_t* chosen,
+                   float* ms_per_iteration) {
+  if (!ctx || n_batch < 1) return EPFFT_ERR_ARG;
   if (!is_pow2(L) || L < 4 || (precision != EPFFT_FP32 && precision != EPFFT_FP64)) return EPFFT_ERR_ARG;
   if (!supported(L, precision)) return EPFFT_ERR_UNSUPPORTED;
   // a synthetic lattice of the kind the solver serves: f = 0.2 voids, the
@@ -1162,14 +1167,15 @@ int epfft_autotune(epfft_ctx* ctx, int32_t L, int32_t precision, int32_t* chosen
   p.yield_stress = 1.0;
   p.max_iter = 1;
   const double E[4] = {0.0, 0.0, 0.0, 1.5 / (2.0 * std::sqrt(3.0))};
-  const int n_iter = L >= 2048 ? 10 : 30;
+  const int64_t px = (int64_t)L * L * n_batch;
+  const int n_iter = px >= ((int64_t)1 << 24) ? 10 : 30;
   int best = 0;
   float tbest = 0.f;
   for (int v = 0; v < N_VARIANTS; v++) {
     float c = 0.f, r = 0.f;
     // warm-up, then the timed launches
-    int rc = time_passes_impl(ctx, p, 1, E, 3, v, &c, &r);
-    if (!rc) rc = time_passes_impl(ctx, p, 1, E, n_iter, v, &c, &r);
+    int rc = time_passes_impl(ctx, p, n_batch, E, 3, v, &c, &r);
+    if (!rc) rc = time_passes_impl(ctx, p, n_batch, E, n_iter, v, &c, &r);
     if (rc) return rc;
     if (ms_per_iteration) ms_per_iteration[v] = c + r;
     if (v == 0 || c + r < tbest) {
@@ -1177,7 +1183,7 @@ int epfft_autotune(epfft_ctx* ctx, int32_t L, int32_t precision, int32_t* chosen
       best = v;
     }
   }
-  ctx->variant[std::make_pair(L, precision)] = best;
+  ctx->variant[std::make_tuple((int)L, (int)precision, batch_class(L, n_batch))] = best;
   if (chosen) *chosen = best;
   return EPFFT_OK;
 }
@@ -1186,7 +1192,7 @@ int epfft_set_tiling(epfft_ctx* ctx, int32_t L, int32_t precision, int32_t varia
   if (!ctx || variant < 0 || variant >= N_VARIANTS) return EPFFT_ERR_ARG;
   if (!is_pow2(L) || L < 4 || (precision != EPFFT_FP32 && precision != EPFFT_FP64)) return EPFFT_ERR_ARG;
   if (!supported(L, precision)) return EPFFT_ERR_UNSUPPORTED;
-  ctx->variant[std::make_pair(L, precision)] = variant;
+  for (int k = 0; k < 2; k++) ctx->variant[std::make_tuple((int)L, (int)precision, k)] = variant;
   return EPFFT_OK;
 }
 

@@ -54,9 +54,11 @@ struct Cfg {
                                    : (F64 ? 1 : (L <= 256 ? 1 : (L <= 1024 ? 2 : 1)));
   static constexpr int W = W0 < M ? W0 : M;
   static constexpr int NTMAX = V == 0 ? 512 : 256;
-  // FP32 variant 1 asks for two resident CTAs per SM (at most 128
-  // registers per thread at 256 threads)
-  static constexpr int MINB = V == 1 && !F64 ? 2 : 1;
+  // resident CTAs per SM asked of the compiler: FP32 variant 1 (at most 128
+  // registers per thread at 256 threads) and the FP32 L = 512 row pass of
+  // variant 0 (64 registers at 512 threads, no spills)
+  static constexpr int MINB_ROW = !F64 && (V == 1 || L == 512) ? 2 : 1;
+  static constexpr int MINB_COL = !F64 && V == 1 ? 2 : 1;
   static constexpr int NT_ROW0 = F64 ? (V == 0 || L > 512 ? (L < 256 ? L : 256) : (L < 128 ? L : 128))
                                      : (L <= 256 ? L : NTMAX);
   static constexpr int NT_ROW = NT_ROW0 < 32 ? 32 : NT_ROW0;
@@ -204,8 +206,7 @@ struct RowIO {
         s[0] = mk(s0.re + s0.im, s0.re - s0.im);
       } else {
         const int kk = M - k;
-        const int ik = pad32(k), ikk = pad32(kk);
-        if (!ECHK(sq * SP + ik, SZ, 5) || !ECHK(sq * SP + ikk, SZ, 6)) continue;
+        const int ik = pad32(k), ikk = pad32(kk);  // 0 < k, kk < M
         const C2<T> a = s[ik], b = s[ikk];
         const C2<T> wk = conj(twist_tw<T, L>(oct, k));
         const C2<T> zk = (a + conj(b)) + mul_i(wk * (a - conj(b)));
@@ -227,8 +228,7 @@ struct RowIO {
         s[0] = mk(z.re + z.im, z.re - z.im);
       } else {
         const int kk = M - k;
-        const int ik = pad32(k), ikk = pad32(kk);
-        if (!ECHK(sq * SP + ik, SZ, 7) || !ECHK(sq * SP + ikk, SZ, 8)) continue;
+        const int ik = pad32(k), ikk = pad32(kk);  // 0 < k, kk < M
         const C2<T> a = s[ik], b = s[ikk];
         const C2<T> wk = twist_tw<T, L>(oct, k);
         s[ik] = T(0.5) * ((a + conj(b)) - mul_i(wk * (a - conj(b))));
@@ -253,10 +253,10 @@ struct RowIO {
     return stw;
   }
   static __device__ __forceinline__ const C2<T>* octant(const C2<T>* stw) { return stw + C::ROW_TW; }
-  // real value of pixel x1 of component c, row r
+  // real value of pixel x1 < L of component c < 3, row r < RR (inside the
+  // data region by construction: x1 / 2 < M)
   static __device__ __forceinline__ T& px(C2<T>* sp, int c, int r, int x1) {
-    const int ix = 2 * at(c, r, x1 >> 1) + (x1 & 1);
-    return reinterpret_cast<T*>(sp)[ECHK(ix, 2 * SZ, 9) ? ix : 0];
+    return reinterpret_cast<T*>(sp)[2 * at(c, r, x1 >> 1) + (x1 & 1)];
   }
 };
 
@@ -447,7 +447,7 @@ __device__ __forceinline__ void batch_arrive(Solve* solves, int nb, BatchCtl* bc
 // Row pass
 // ---------------------------------------------------------------------------
 template <typename T, int L, int V>
-__global__ void __launch_bounds__(Cfg<T, L, V>::NT_ROW, Cfg<T, L, V>::MINB)
+__global__ void __launch_bounds__(Cfg<T, L, V>::NT_ROW, Cfg<T, L, V>::MINB_ROW)
 row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restrict__ tw,
          cudaGraphConditionalHandle cond, int use_cond) {
   using C = Cfg<T, L, V>;
@@ -467,6 +467,10 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
   const int cur = Sv.cur;
   const int inc = Sv.inc;
   const int tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  // pixel j of this thread in a row: each warp owns a contiguous run of
+  // 32 P pixels, lane-fastest (L < 32: one short row per warp)
+  auto xmap = [&](int j) { return L >= 32 ? wid * (32 * P) + j * 32 + lane : tid; };
   if (phase != PH_DONE) {
     const int r0 = blockIdx.x * RR;
     const T* __restrict__ ein = reinterpret_cast<const T*>(S.eps[cur]);
@@ -487,7 +491,7 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
       uint8_t* fl = S.flags ? S.flags + (size_t)(S.n_inc - 1) * LL : nullptr;  // inc == n_inc - 1
       for (int r = 0; r < RR && fl; r++)
         for (int j = 0; j < P; j++) {
-          const int x1 = tid + j * NT;
+          const int x1 = xmap(j);
           if (x1 >= L) continue;
           const size_t x = (size_t)(r0 + r) * L + x1;
           T e[4];
@@ -502,7 +506,7 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
       uint8_t* fl = (S.flags && inc > 0) ? S.flags + (size_t)(inc - 1) * LL : nullptr;
       for (int r = 0; r < RR; r++)
         for (int j = 0; j < P; j++) {
-          const int x1 = tid + j * NT;
+          const int x1 = xmap(j);
           if (x1 >= L) continue;
           const size_t x = (size_t)(r0 + r) * L + x1;
           if (!ECHK(x, LL, 20)) continue;
@@ -533,7 +537,7 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
         const int xh = (r0 + L - 1) & (L - 1);
 #pragma unroll
         for (int j = 0; j < P; j++) {
-          const int x1 = tid + j * NT;
+          const int x1 = xmap(j);
           prev12[j] = prev22[j] = T(0);
           if (x1 >= L) continue;
           const size_t x = (size_t)xh * L + x1;
@@ -546,9 +550,8 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
         }
       }
       // Pixel update of the AL iteration at (r, x1), given eps^n (en), its
-      // stress s and the left neighbour's sigma11, sigma12 (x - e^1).
-      auto update = [&](int r, int j, const T (&en)[4], bool v, const T (&sj)[4], T l11, T l12) {
-        const int x1 = tid + j * NT;
+      // stress sj and the left neighbour's sigma11, sigma12 (x - e^1).
+      auto update = [&](int r, int j, int x1, const T (&en)[4], bool v, const T (&sj)[4], T l11, T l12) {
         if (x1 >= L) return;
         const size_t x = (size_t)(r0 + r) * L + x1;
         // Eq. 1: div_i = sum_j sigma_ij(x) - sigma_ij(x - e^j)
@@ -579,91 +582,81 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
         IO::px(sp, 1, r, x1) = s1[1] - c0[1];
         IO::px(sp, 2, r, x1) = s1[3] - c0[3];
       };
-      const int lane = tid & 31;
-      if constexpr (sizeof(T) == 4) {
-        // Left neighbours: the previous lane by a warp shuffle; lane 0
-        // re-evaluates sigma at x - e^1 (periodic) from memory, so no
-        // per-pixel state is held across a barrier.
-        for (int r = 0; r < RR; r++) {
-          T en[P][4];
-          bool vv[P];
+      // Left neighbours: the previous lane by a warp shuffle; lane 0 takes
+      // lane 31 of the previous pixel group of its warp (the run is
+      // contiguous).  At the start of a run: FP32 re-evaluates sigma at
+      // x - e^1 (periodic) from memory; FP64 (where that evaluation would
+      // cost the warp a full sigma on the FP64 pipe) reads the previous
+      // warp's last value from a per-row exchange, double-buffered by row
+      // parity so one barrier per row suffices.
+      constexpr bool XCH = sizeof(T) == 8 && L >= 32;
+      constexpr int NW = NT / 32;
+      __shared__ T edge[XCH ? 2 : 1][2][XCH ? NW : 1];
+      for (int r = 0; r < RR; r++) {
+        T en[P][4];
+        bool vv[P];
 #pragma unroll
-          for (int j = 0; j < P; j++) {
-            const int x1 = tid + j * NT;
-            const size_t x = (size_t)(r0 + r) * L + x1;
-            const bool act = x1 < L && ECHK(x, LL, 23);
-            vv[j] = act ? mask[x] != 0 : true;
-            if (act) Vec4<T>::load(ein + 4 * x, en[j]);
-            else en[j][0] = en[j][1] = en[j][2] = en[j][3] = T(0);
-          }
-#pragma unroll
-          for (int j = 0; j < P; j++) {
-            T sj[4];
-            const bool pl = sigma(en[j], vv[j], m, sj);
-            acc[A_NPL] += pl ? T(1) : T(0);
-            T l11 = __shfl_up_sync(0xffffffffu, sj[0], 1);
-            T l12 = __shfl_up_sync(0xffffffffu, sj[3], 1);
-            const int x1 = tid + j * NT;
-            if (lane == 0 && x1 < L) {
-              const size_t xl = (size_t)(r0 + r) * L + ((x1 + L - 1) & (L - 1));
-              if (ECHK(xl, LL, 24)) {
-                T el[4], sl[4];
-                Vec4<T>::load(ein + 4 * xl, el);
-                sigma(el, mask[xl] != 0, m, sl);
-                l11 = sl[0];
-                l12 = sl[3];
-              }
-            }
-            update(r, j, en[j], vv[j], sj, l11, l12);
-          }
+        for (int j = 0; j < P; j++) {
+          const int x1 = xmap(j);
+          const size_t x = (size_t)(r0 + r) * L + x1;
+          const bool act = x1 < L && ECHK(x, LL, 23);
+          vv[j] = act ? mask[x] != 0 : true;
+          if (act) Vec4<T>::load(ein + 4 * x, en[j]);
+          else en[j][0] = en[j][1] = en[j][2] = en[j][3] = T(0);
         }
-      } else {
-        // Left neighbours: the previous lane by a warp shuffle; lane 0 takes
-        // the last lane of the previous warp (or of the last warp, one pixel
-        // group back) from a small per-row exchange, double-buffered by row
-        // parity so one barrier per row suffices.
-        constexpr int NW = NT / 32;
-        __shared__ T edge[2][2][NW][P];
-        const int wid = tid >> 5;
-        for (int r = 0; r < RR; r++) {
-          const int par = r & 1;
-          T en[P][4], s[P][4];
-          bool vv[P];
-#pragma unroll
-          for (int j = 0; j < P; j++) {
-            const int x1 = tid + j * NT;
-            const size_t x = (size_t)(r0 + r) * L + x1;
-            const bool act = x1 < L && ECHK(x, LL, 23);
-            vv[j] = act ? mask[x] != 0 : true;
-            if (act) Vec4<T>::load(ein + 4 * x, en[j]);
-            else en[j][0] = en[j][1] = en[j][2] = en[j][3] = T(0);
-            const bool pl = sigma(en[j], vv[j], m, s[j]);
-            acc[A_NPL] += pl ? T(1) : T(0);
-            if (L >= 32 && lane == 31) {
-              edge[par][0][wid][j] = s[j][0];
-              edge[par][1][wid][j] = s[j][3];
-            }
+        T slast[4];  // sigma of the last group (FP64 exchange)
+        if constexpr (XCH) {
+          sigma(en[P - 1], vv[P - 1], m, slast);
+          if (lane == 31) {
+            edge[r & 1][0][wid] = slast[0];
+            edge[r & 1][1][wid] = slast[3];
           }
           __syncthreads();
+        }
+        T run11 = T(0), run12 = T(0);  // sigma11, sigma12 of lane 31, previous group
 #pragma unroll
-          for (int j = 0; j < P; j++) {
-            T l11, l12;
-            if constexpr (L < 32) {
-              const int src = (lane + L - 1) & (L - 1);
-              l11 = __shfl_sync(0xffffffffu, s[j][0], src);
-              l12 = __shfl_sync(0xffffffffu, s[j][3], src);
-            } else {
-              l11 = __shfl_up_sync(0xffffffffu, s[j][0], 1);
-              l12 = __shfl_up_sync(0xffffffffu, s[j][3], 1);
-              if (lane == 0) {
+        for (int j = 0; j < P; j++) {
+          T sj[4];
+          bool pl;
+          if (XCH && j == P - 1) {
+            for (int c = 0; c < 4; c++) sj[c] = slast[c];
+            pl = is_plastic(en[j], vv[j], m);
+          } else {
+            pl = sigma(en[j], vv[j], m, sj);
+          }
+          acc[A_NPL] += pl ? T(1) : T(0);
+          const int x1 = xmap(j);
+          T l11, l12;
+          if constexpr (L < 32) {
+            const int src = (lane + L - 1) & (L - 1);
+            l11 = __shfl_sync(0xffffffffu, sj[0], src);
+            l12 = __shfl_sync(0xffffffffu, sj[3], src);
+          } else {
+            l11 = __shfl_up_sync(0xffffffffu, sj[0], 1);
+            l12 = __shfl_up_sync(0xffffffffu, sj[3], 1);
+            if (lane == 0) {
+              if (j > 0) {
+                l11 = run11;
+                l12 = run12;
+              } else if constexpr (XCH) {
                 const int pw = wid > 0 ? wid - 1 : NW - 1;
-                const int pj = wid > 0 ? j : (j + P - 1) % P;
-                l11 = edge[par][0][pw][pj];
-                l12 = edge[par][1][pw][pj];
+                l11 = edge[r & 1][0][pw];
+                l12 = edge[r & 1][1][pw];
+              } else {
+                const size_t xl = (size_t)(r0 + r) * L + ((x1 + L - 1) & (L - 1));
+                if (ECHK(xl, LL, 24)) {
+                  T el[4], sl[4];
+                  Vec4<T>::load(ein + 4 * xl, el);
+                  sigma(el, mask[xl] != 0, m, sl);
+                  l11 = sl[0];
+                  l12 = sl[3];
+                }
               }
             }
-            update(r, j, en[j], vv[j], s[j], l11, l12);
+            run11 = __shfl_sync(0xffffffffu, sj[0], 31);
+            run12 = __shfl_sync(0xffffffffu, sj[3], 31);
           }
+          update(r, j, x1, en[j], vv[j], sj, l11, l12);
         }
       }
     }
@@ -707,7 +700,7 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
 // Column pass
 // ---------------------------------------------------------------------------
 template <typename T, int L, int V>
-__global__ void __launch_bounds__(Cfg<T, L, V>::NT_COL, Cfg<T, L, V>::MINB)
+__global__ void __launch_bounds__(Cfg<T, L, V>::NT_COL, Cfg<T, L, V>::MINB_COL)
 col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* __restrict__ ktab,
          cudaGraphConditionalHandle cond, int use_cond) {
   using C = Cfg<T, L, V>;

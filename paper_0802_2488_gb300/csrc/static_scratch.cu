@@ -38,7 +38,7 @@ void* g_addr[kMaxDevices];  // device address of g_scratch, per device (set up o
 
 }  // namespace
 
-// 1.58 MB (kScratchBytes) of device memory, shared by every call on a device.
+// 1.59 MB (kScratchBytes) of device memory, shared by every call on a device.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 namespace {

@@ -51,3 +51,15 @@ def test_autotune_chooses_a_compiled_tiling(ctx, prec):
     assert chosen in (0, 1) and all(m > 0 for m in ms)
     assert ms[chosen] == min(ms)
     B.epfft_set_tiling(ctx, 256, prec, 0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_autotune_batch_classes(ctx, prec):
+    """Small and large launches are tuned separately; set_tiling sets both."""
+    c1, ms1 = B.epfft_autotune(ctx, 512, prec, n_batch=1)
+    c2, ms2 = B.epfft_autotune(ctx, 512, prec, n_batch=16)
+    assert c1 in (0, 1) and c2 in (0, 1)
+    assert ms1[c1] == min(ms1) and ms2[c2] == min(ms2)
+    # the batch of 16 costs more per iteration than one solve
+    assert min(ms2) > min(ms1)
+    B.epfft_set_tiling(ctx, 512, prec, 0)
