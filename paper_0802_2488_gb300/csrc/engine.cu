@@ -103,9 +103,10 @@ int shape(int L, int prec, int var, PassShape* sh) {
 
 size_t real_size(int prec) { return prec == EPFFT_FP32 ? 4 : 8; }
 
-// Twiddles exp(-2 pi i k / L) and Fourier symbols of Eq. 2,
-// k(m) = 2 sin(q/2) exp(i q/2) = (sin q, 2 sin^2(q/2)), q = 2 pi m / L, both
-// evaluated in long double and rounded once to the working precision.
+// Device tables of (L, precision) (layout of tables.cuh: twist octant,
+// stage twiddles of both tilings' plans, Fourier symbols of Eq. 2
+// k(m) = 2 sin(q/2) exp(i q/2)), built once per context in long double and
+// rounded once to the working precision.
 int get_tables(epfft_ctx* c, int L, int prec, void** tw, void** ktab) {
   auto key = std::make_pair(L, prec);
   auto it = c->tables.find(key);
