@@ -40,10 +40,18 @@ def build(force: bool = False) -> str:
 
 
 class Material(C.Structure):
-    """Matrix Lame moduli, Mises flow stress Y (inf = elastic) and the
-    reference medium C0 of the augmented Lagrangian."""
+    """Matrix Lame moduli, Mises flow stress Y (inf = elastic), the
+    reference medium C0 of the augmented Lagrangian and the Green operator
+    (GREEN_* below)."""
     _fields_ = [("lambda_", C.c_double), ("mu", C.c_double), ("yield_", C.c_double),
-                ("lambda0", C.c_double), ("mu0", C.c_double)]
+                ("lambda0", C.c_double), ("mu0", C.c_double), ("green", C.c_int32),
+                ("pad", C.c_int32)]
+
+
+# Green operators of Sec. 2 (values of orc_material.green)
+GREEN_EQ3, GREEN_CG1, GREEN_DG1, GREEN_EQ3_M1, GREEN_EQ3_M2, GREEN_EQ3_M12 = range(6)
+# the four operators G(q1,q2), G(-q1,-q2), G(-q1,q2), G(q1,-q2) of DG2
+DG2_MEMBERS = (GREEN_EQ3, GREEN_EQ3_M12, GREEN_EQ3_M1, GREEN_EQ3_M2)
 
 
 class Control(C.Structure):
@@ -58,8 +66,8 @@ class Record(C.Structure):
                 ("n_clusters", C.c_int32), ("status", C.c_int32)]
 
 
-def material(lam=1.5, mu=1.0, Y=1.0, lam0=None, mu0=None) -> Material:
-    return Material(lam, mu, Y, lam if lam0 is None else lam0, mu if mu0 is None else mu0)
+def material(lam=1.5, mu=1.0, Y=1.0, lam0=None, mu0=None, green=GREEN_EQ3) -> Material:
+    return Material(lam, mu, Y, lam if lam0 is None else lam0, mu if mu0 is None else mu0, int(green), 0)
 
 
 _D = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -80,7 +88,9 @@ def lib():
         L.orc_mask.argtypes = [C.c_int, C.c_double, C.c_uint64, _U8]
         L.orc_fft2.argtypes = [_VP, C.c_int, C.c_int]
         L.orc_green.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, _D]
-        L.orc_green_apply.argtypes = [C.c_int, C.c_double, C.c_double, _D, _VP, _VP]
+        L.orc_green_mode.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, _D]
+        L.orc_green_apply.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, _D, _VP, _VP]
+        L.orc_avg5.argtypes = [C.c_int, _D, _D]
         L.orc_sigma_field.argtypes = [C.c_int64, _D, _U8, C.POINTER(Material), _D, _VP]
         L.orc_local_field.argtypes = [C.c_int64, _D, _U8, C.POINTER(Material), _D, _VP]
         L.orc_al_step.argtypes = [C.c_int, _U8, C.POINTER(Material), _D, _D, _D, _VP, _VP]
@@ -145,14 +155,31 @@ def green(L: int, lam0: float, mu0: float, m1: int, m2: int) -> np.ndarray:
     return g.view(np.complex128).reshape(2, 2, 2, 2)
 
 
-def green_apply(L, lam0, mu0, E, phat):
+def green_mode(L: int, lam0: float, mu0: float, mode: int, m1: int, m2: int) -> np.ndarray:
+    """Green operator `mode` (GREEN_*; Sec. 2) at q = 2 pi (m1, m2) / L as a
+    complex (2, 2, 2, 2) array."""
+    g = np.zeros(32, dtype=np.float64)
+    lib().orc_green_mode(L, lam0, mu0, int(mode), m1, m2, g)
+    return g.view(np.complex128).reshape(2, 2, 2, 2)
+
+
+def green_apply(L, lam0, mu0, E, phat, mode=GREEN_EQ3):
     """e^ = G p^ on a full (3, L, L) spectrum (11, 22, 12); e^(0) = L^2 E."""
     _check_L(L)
     ph = np.ascontiguousarray(phat, dtype=np.complex128)
     eh = np.empty_like(ph)
-    lib().orc_green_apply(L, lam0, mu0, np.ascontiguousarray(E, dtype=np.float64),
+    lib().orc_green_apply(L, lam0, mu0, int(mode), np.ascontiguousarray(E, dtype=np.float64),
                           _ptr(ph), _ptr(eh))
     return eh
+
+
+def avg5(field: np.ndarray) -> np.ndarray:
+    """CG2 post-processing (Sec. 2): mean of each pixel and its four nearest
+    neighbours (periodic) of an (L, L, 4) field."""
+    f = np.ascontiguousarray(field, dtype=np.float64)
+    out = np.empty_like(f)
+    lib().orc_avg5(f.shape[0], f, out)
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -264,3 +291,72 @@ def solve(mask_: np.ndarray, mat: Material, path: np.ndarray, tol_eq=1e-8, tol_m
                          n_inc, P, recs, _ptr(eps), _ptr(pl), _ptr(lab))
     arr = np.frombuffer(bytes(recs), dtype=RECORD_DTYPE).copy()
     return Solution(int(st), arr, eps, pl, lab)
+
+
+def mirror(a: np.ndarray, axes) -> np.ndarray:
+    """Pixel mirror x_j -> -x_j (mod L) of an (L, L) or (L, L, 4) field for
+    each lattice direction j in `axes` (1 = x1, the fast index; 2 = x2).  A
+    tensor field (last axis of 4: 11, 22, 33, 12) also changes the sign of
+    its 12 component once per mirrored direction."""
+    L = a.shape[0]
+    idx = (-np.arange(L)) % L
+    b = a
+    for j in axes:
+        b = b[:, idx] if j == 1 else b[idx, :]
+        if b.ndim == 3:
+            b = b.copy()
+            b[..., 3] = -b[..., 3]
+    return np.ascontiguousarray(b)
+
+
+def mirror_path(path: np.ndarray, axes) -> np.ndarray:
+    """Prescribed mean strains of the mirrored problem (E12 changes sign once
+    per mirrored direction)."""
+    P = np.array(path, dtype=np.float64).reshape(-1, 4)
+    if len(axes) % 2 == 1:
+        P[:, 3] = -P[:, 3]
+    return P
+
+
+# lattice mirrors equivalent to the four operators of DG2, in DG2_MEMBERS
+# order: G(q1,q2), G(-q1,-q2), G(-q1,q2), G(q1,-q2)
+DG2_MIRRORS = ((), (1, 2), (1,), (2,))
+
+
+@dataclass
+class DG2Solution:
+    members: list                # the four Solutions (of the mirrored problems), DG2_MIRRORS order
+    records: np.ndarray          # RECORD_DTYPE: means of the members' macro values
+    eps: np.ndarray              # (L, L, 4): mean of the four final strain fields
+
+
+def solve_dg2(mask_: np.ndarray, mat: Material, path: np.ndarray, tol_eq=1e-8, tol_macro=1e-8,
+              max_iter=10000) -> DG2Solution:
+    """DG2 (Sec. 2): four complete solves with G(q1,q2), G(-q1,-q2),
+    G(-q1,q2), G(q1,-q2) in turn; the result is the average of the four
+    converged strain fields.  The solve with G at mirrored momenta is the
+    mirror image of the Eq. 3 solve of the mirrored lattice under the
+    mirrored load (forward differences of Eq. 1 become backward ones), so
+    each member runs Eq. 3 on a mirrored problem and its field is mirrored
+    back; each member's indicators are then those of its own scheme.  Per
+    increment the macroscopic stress and strain of the four are averaged
+    (mirrored back: E12, sigma12 change sign with an odd mirror); the
+    indicators are the largest of the four, the iteration counts their sum."""
+    sols, fields = [], []
+    for ax in DG2_MIRRORS:
+        s = solve(mirror(mask_, ax), mat, mirror_path(path, ax), tol_eq, tol_macro, max_iter)
+        sols.append(s)
+        fields.append(mirror(s.eps, ax))
+    rec = sols[0].records.copy()
+    for f in ("sig_mean", "eps_mean"):
+        vals = []
+        for s, ax in zip(sols, DG2_MIRRORS):
+            v = s.records[f].copy()
+            if len(ax) % 2 == 1:
+                v[:, 3] = -v[:, 3]
+            vals.append(v)
+        rec[f] = np.mean(vals, axis=0)
+    for f in ("eta1", "eta2", "eta3", "status"):
+        rec[f] = np.max([s.records[f] for s in sols], axis=0)
+    rec["iterations"] = np.sum([s.records["iterations"] for s in sols], axis=0)
+    return DG2Solution(sols, rec, np.mean(fields, axis=0))

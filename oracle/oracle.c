@@ -30,6 +30,13 @@
  *   orc_fft2                  : textbook radix-2 Cooley-Tukey FFT.
  *   orc_green                 : Eq. 2 (symbol k_j) and Eq. 3 (G_ijkl and the
  *                               acoustic tensor N), N inverted numerically.
+ *   orc_green_mode            : the operators of Sec. 2 built from Eq. 3:
+ *                               Eq. 3 itself, the same at mirrored momenta
+ *                               (the four operators of DG2), the continuum
+ *                               operator CG1 (Eq. 3 with k_j = q_j), and the
+ *                               symmetrized DG1 operator (equation after
+ *                               Eq. 3).
+ *   orc_avg5                  : the 5-point local average of CG2 (Sec. 2).
  *   orc_sigma                 : elastic-perfectly plastic Mises law under
  *                               deformation theory (Sec. 2, Sec. 3: plastic
  *                               zone where sigma_eq = Y, voids sigma = 0).
@@ -65,7 +72,19 @@ typedef struct {
   double yield;      /* Mises flow stress Y; INFINITY means purely elastic */
   double lambda0;    /* reference medium C0 of the augmented Lagrangian    */
   double mu0;
+  int32_t green;     /* Green operator, ORC_GREEN_* below                  */
+  int32_t pad;
 } orc_material;
+
+/* Green operators of Sec. 2 */
+enum {
+  ORC_GREEN_EQ3 = 0,      /* G(q1, q2) of Eq. 3                               */
+  ORC_GREEN_CG1 = 1,      /* continuum operator: Eq. 3 with k_j = q_j          */
+  ORC_GREEN_DG1 = 2,      /* symmetrized G^(1)                                 */
+  ORC_GREEN_EQ3_M1 = 3,   /* (-1)^(i+j+k+l) G(-q1, q2)  (DG2 members)          */
+  ORC_GREEN_EQ3_M2 = 4,   /* (-1)^(i+j+k+l) G(q1, -q2)                         */
+  ORC_GREEN_EQ3_M12 = 5,  /* G(-q1, -q2)                                       */
+};
 
 typedef struct {
   double tol_eq;    /* eta_1 */
@@ -174,16 +193,11 @@ static double stiff(double lam, double mu, int i, int j, int k, int l) {
          mu * (kron(i, k) * kron(j, l) + kron(i, l) * kron(j, k));
 }
 
-/* G_ijkl(q) of Eq. 3 for the reference medium (lam0, mu0), in-plane
- * indices i,j,k,l in {0,1} (= 1,2), stored G[((i*2+j)*2+k)*2+l].
- * The acoustic tensor N_ij = k*_k C_iklj k_l is built and inverted
- * numerically, as the paper does.  At q = 0 the operator is set to zero:
- * the mean strain is imposed separately (it is the prescribed E). */
-void orc_green(int L, double lam0, double mu0, int m1, int m2, double *Gout) {
-  cplx *G = (cplx *)Gout;
-  for (int t = 0; t < 16; t++) G[t] = 0.0;
-  if (m1 % L == 0 && m2 % L == 0) return;
-  cplx k[2] = {ksym(m1, L), ksym(m2, L)};
+/* G_ijkl of Eq. 3 for given momenta symbols k = (k1, k2) and the reference
+ * medium (lam0, mu0), in-plane indices i,j,k,l in {0,1} (= 1,2), stored
+ * G[((i*2+j)*2+k)*2+l].  The acoustic tensor N_ij = k*_k C_iklj k_l is
+ * built and inverted numerically, as the paper does. */
+static void green_of_k(double lam0, double mu0, const cplx k[2], cplx *G) {
   cplx N[2][2];
   for (int i = 0; i < 2; i++)
     for (int j = 0; j < 2; j++) {
@@ -206,10 +220,93 @@ void orc_green(int L, double lam0, double mu0, int m1, int m2, double *Gout) {
               4.0;
 }
 
-/* e^_ij = sum_kl G_ijkl p^_kl at every frequency of an L x L spectrum;
+/* G_ijkl(q) of Eq. 3 at q = 2 pi (m1, m2) / L.  At q = 0 the operator is
+ * set to zero: the mean strain is imposed separately (it is the
+ * prescribed E). */
+void orc_green(int L, double lam0, double mu0, int m1, int m2, double *Gout) {
+  cplx *G = (cplx *)Gout;
+  for (int t = 0; t < 16; t++) G[t] = 0.0;
+  if (m1 % L == 0 && m2 % L == 0) return;
+  cplx k[2] = {ksym(m1, L), ksym(m2, L)};
+  green_of_k(lam0, mu0, k, G);
+}
+
+/* Continuum momentum of index m: q = 2 pi m~ / L with m~ = m folded into
+ * (-L/2, L/2]. */
+static double qcont(int m, int L) {
+  int mm = ((m % L) + L) % L;
+  if (mm > L / 2) mm -= L;
+  return 2.0 * M_PI * (double)mm / (double)L;
+}
+
+/* The Green operator `mode` (ORC_GREEN_*) at q = 2 pi (m1, m2) / L:
+ *   EQ3, EQ3_M1, EQ3_M2, EQ3_M12: Eq. 3 at (q1, q2), (-q1, q2), (q1, -q2),
+ *     (-q1, -q2), the four operators DG2 runs in turn; a single mirror
+ *     carries the tensor sign (-1)^(i+j+k+l) of that mirror, as in DG1
+ *     (without it the operator would solve the problem with E12 and
+ *     sigma12 of the opposite sign);
+ *   CG1: Eq. 3 with the continuum symbol k_j = q_j, q_j in (-pi, pi] (its
+ *     long-wavelength limit; averaged over q_j = +-pi at Nyquist indices);
+ *   DG1: { G(q1,q2) + G(-q1,-q2) + (-1)^(i+j+k+l) [G(-q1,q2) + G(q1,-q2)] } / 4.
+ * Zero at q = 0. */
+void orc_green_mode(int L, double lam0, double mu0, int mode, int m1, int m2, double *Gout) {
+  cplx *G = (cplx *)Gout;
+  for (int t = 0; t < 16; t++) G[t] = 0.0;
+  if (m1 % L == 0 && m2 % L == 0) return;
+  if (mode == ORC_GREEN_EQ3) {
+    orc_green(L, lam0, mu0, m1, m2, Gout);
+  } else if (mode == ORC_GREEN_EQ3_M1 || mode == ORC_GREEN_EQ3_M2) {
+    /* single mirror: the momentum changes sign along one axis and the
+     * operator takes the tensor sign of that mirror, (-1)^(i+j+k+l) */
+    double Gm[32];
+    if (mode == ORC_GREEN_EQ3_M1) orc_green(L, lam0, mu0, -m1, m2, Gm);
+    else orc_green(L, lam0, mu0, m1, -m2, Gm);
+    const cplx *A = (const cplx *)Gm;
+    for (int t = 0; t < 16; t++) {
+      const int i = t >> 3, j = (t >> 2) & 1, a = (t >> 1) & 1, b = t & 1;
+      G[t] = ((i + j + a + b) % 2 == 0) ? A[t] : -A[t];
+    }
+  } else if (mode == ORC_GREEN_EQ3_M12) {
+    orc_green(L, lam0, mu0, -m1, -m2, Gout);
+  } else if (mode == ORC_GREEN_CG1) {
+    /* At a Nyquist index (m = L/2) the continuum momentum is +pi or -pi;
+     * the operator is the mean over both choices, which keeps it even in q
+     * on the grid (so real fields stay real). */
+    const int n1 = (((m1 % L) + L) % L) * 2 == L, n2 = (((m2 % L) + L) % L) * 2 == L;
+    int cnt = 0;
+    for (int s1 = 0; s1 <= n1; s1++)
+      for (int s2 = 0; s2 <= n2; s2++) {
+        cplx k[2] = {s1 ? -qcont(m1, L) : qcont(m1, L), s2 ? -qcont(m2, L) : qcont(m2, L)};
+        cplx Gk[16];
+        green_of_k(lam0, mu0, k, Gk);
+        for (int t = 0; t < 16; t++) G[t] += Gk[t];
+        cnt++;
+      }
+    for (int t = 0; t < 16; t++) G[t] /= (double)cnt;
+  } else if (mode == ORC_GREEN_DG1) {
+    double Ga[32], Gb[32], Gc[32], Gd[32];
+    orc_green(L, lam0, mu0, m1, m2, Ga);
+    orc_green(L, lam0, mu0, -m1, -m2, Gb);
+    orc_green(L, lam0, mu0, -m1, m2, Gc);
+    orc_green(L, lam0, mu0, m1, -m2, Gd);
+    const cplx *A = (const cplx *)Ga, *B = (const cplx *)Gb, *C = (const cplx *)Gc, *D = (const cplx *)Gd;
+    for (int i = 0; i < 2; i++)
+      for (int j = 0; j < 2; j++)
+        for (int a = 0; a < 2; a++)
+          for (int b = 0; b < 2; b++) {
+            /* indices 1,2 of the paper are i+1 etc.: (-1)^(i+j+a+b+4) */
+            const double sgn = ((i + j + a + b) % 2 == 0) ? 1.0 : -1.0;
+            const int t = ((i * 2 + j) * 2 + a) * 2 + b;
+            G[t] = (A[t] + B[t] + sgn * (C[t] + D[t])) / 4.0;
+          }
+  }
+}
+
+/* e^_ij = sum_kl G_ijkl p^_kl (operator `mode`) at every frequency of an
+ * L x L spectrum;
  * p^ and e^ hold the components (11, 22, 12) as three L*L complex planes;
  * p^_21 = p^_12.  At q = 0, e^ = L^2 * E (the prescribed mean strain). */
-void orc_green_apply(int L, double lam0, double mu0, const double *E,
+void orc_green_apply(int L, double lam0, double mu0, int mode, const double *E,
                      const double *phat_in, double *ehat_out) {
   const cplx *ph = (const cplx *)phat_in;
   cplx *eh = (cplx *)ehat_out;
@@ -226,7 +323,7 @@ void orc_green_apply(int L, double lam0, double mu0, const double *E,
         continue;
       }
       double Gd[32];
-      orc_green(L, lam0, mu0, m1, m2, Gd);
+      orc_green_mode(L, lam0, mu0, mode, m1, m2, Gd);
       cplx *G = (cplx *)Gd;
       cplx P[2][2];
       P[0][0] = ph[q];
@@ -357,7 +454,7 @@ void orc_al_step(int L, const uint8_t *mask, const orc_material *m,
     ph[2 * n + x] = lam[4 * x + 3] - c0e[3];
   }
   for (int c = 0; c < 3; c++) orc_fft2(ph + c * n, L, -1);
-  orc_green_apply(L, m->lambda0, m->mu0, E, (const double *)ph, (double *)eh);
+  orc_green_apply(L, m->lambda0, m->mu0, m->green, E, (const double *)ph, (double *)eh);
   for (int c = 0; c < 3; c++) orc_fft2(eh + c * n, L, +1);
 #pragma omp parallel for schedule(static)
   for (int64_t x = 0; x < n; x++) {
@@ -581,7 +678,14 @@ int32_t orc_solve(int L, const uint8_t *mask, const orc_material *m,
         status = 2;
         break;
       }
-      if (eta1 < ctl->tol_eq && eta2 < ctl->tol_macro) {
+      /* Equilibrium test: eta1 (Sec. 2, divergence of Eq. 1) for the
+       * operators of Eq. 3.  The continuum (CG1) and symmetrized (DG1)
+       * operators are not the Green operators of Eq. 1, so the divergence
+       * of Eq. 1 does not vanish at their solutions; there the augmented
+       * Lagrangian's own fixed-point residual eta3 (local strain minus
+       * compatible strain) takes its place. */
+      const double eq = (m->green == ORC_GREEN_CG1 || m->green == ORC_GREEN_DG1) ? eta3 : eta1;
+      if (eq < ctl->tol_eq && eta2 < ctl->tol_macro) {
         status = 0;
         break;
       }
@@ -631,4 +735,25 @@ void orc_local_field(int64_t n, const double *tau, const uint8_t *mask,
     int pl = orc_local_solve(tau + 4 * x, mask[x], m, eps + 4 * x);
     if (plastic) plastic[x] = (uint8_t)pl;
   }
+}
+
+/* ------------------------------------------------------------------ */
+/* CG2 post-processing                                                 */
+/* ------------------------------------------------------------------ */
+
+/* The local average of CG2 (Sec. 2): every pixel of a field of 4 reals per
+ * pixel receives the mean of its own value and those of its four nearest
+ * neighbours (periodic lattice). */
+void orc_avg5(int L, const double *in, double *out) {
+  for (int x2 = 0; x2 < L; x2++)
+    for (int x1 = 0; x1 < L; x1++) {
+      const int64_t x = (int64_t)x2 * L + x1;
+      const int64_t nb[4] = {(int64_t)x2 * L + (x1 + 1) % L, (int64_t)x2 * L + (x1 + L - 1) % L,
+                             (int64_t)((x2 + 1) % L) * L + x1, (int64_t)((x2 + L - 1) % L) * L + x1};
+      for (int c = 0; c < 4; c++) {
+        double s = in[4 * x + c];
+        for (int n = 0; n < 4; n++) s += in[4 * nb[n] + c];
+        out[4 * x + c] = s / 5.0;
+      }
+    }
 }
