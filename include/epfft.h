@@ -57,6 +57,12 @@ extern "C" {
 #define EPFFT_FP32 1 /* FP32 fields and FFTs, FP64 reductions and macro values  */
 
 #define EPFFT_GREEN_EQ3 0 /* discrete Green operator of Eq. 3                   */
+#define EPFFT_GREEN_CG1 1 /* continuum operator (Sec. 2, CG1): Eq. 3 with the   *
+                           * momenta k_j = q_j, q_j in (-pi, pi], averaged over  *
+                           * q_j = +-pi at Nyquist indices                       */
+#define EPFFT_GREEN_DG1 2 /* symmetrized operator (Sec. 2, DG1): the mean of     *
+                           * G(q1,q2), G(-q1,-q2) and the tensor-signed          *
+                           * (-1)^(i+j+k+l) G(-q1,q2), G(q1,-q2)                 */
 
 typedef struct epfft_ctx epfft_ctx;
 
@@ -87,7 +93,9 @@ typedef struct {
                             * floor(f 2^53) (i.i.d. Bernoulli(f) voids, Sec. 2)   */
   const uint8_t *mask;     /* optional L*L mask, 1 = void; host or device         */
   int32_t mask_on_device;  /* 1 if `mask` is a device pointer                     */
-  int32_t green;           /* EPFFT_GREEN_EQ3                                     */
+  int32_t green;           /* EPFFT_GREEN_*; with CG1 and DG1 (not Green          *
+                            * operators of Eq. 1) the equilibrium test uses eta3 *
+                            * in place of eta1 (fixed-point residual)            */
   double mu, lambda;       /* matrix Lame moduli (> 0, lambda + 2 mu / 3 > 0)     */
   double yield_stress;     /* Mises flow stress Y > 0; +inf = elastic matrix      */
   double mu0, lambda0;     /* reference medium C0 of the augmented Lagrangian     */
@@ -178,6 +186,32 @@ int epfft_solve(epfft_ctx *ctx, const epfft_problem *problem, const epfft_path *
 int epfft_solve_batch(epfft_ctx *ctx, int32_t n, const epfft_problem *problems,
                       const epfft_path *paths, epfft_record *const *records,
                       const epfft_fields *fields);
+
+/* DG2 (Sec. 2): four complete solves of the problem with the Eq. 3
+ * operator at (q1, q2), (-q1, -q2), (-q1, q2) and (q1, -q2) in turn, and the
+ * average of the four converged strain fields.  The operator at mirrored
+ * momenta (with the tensor sign of the mirror, as in DG1) is exactly the
+ * Eq. 3 scheme on the mirrored lattice under the mirrored load, so the
+ * members run as one batch of Eq. 3 solves of the lattice and its mirror
+ * images (x1, x2 and both; E12 reversed by a single mirror), each judged by
+ * its own scheme's indicators, and their fields are mirrored back before
+ * averaging.  problem->green must be EPFFT_GREEN_EQ3.
+ * records: n_inc entries: per increment the mean of the four members'
+ * <sigma> and <eps> (mirrored back), the largest eta1, eta2, eta3 and status,
+ * the summed iterations; n_plastic and n_clusters are -1 except in the last
+ * record, where they describe the averaged final field.
+ * fields (optional): eps = the averaged final strain (L*L*4 reals);
+ * plastic = L*L flags of its plastic matrix pixels; labels = L*L clusters of
+ * those (4-connected, periodic).  Return codes as epfft_solve. */
+int epfft_solve_dg2(epfft_ctx *ctx, const epfft_problem *problem, const epfft_path *path,
+                    epfft_record *records, const epfft_fields *fields);
+
+/* CG2 post-processing (Sec. 2): eps_out(x) = mean of eps_in at x and its
+ * four nearest neighbours (periodic), per component.  Device pointers,
+ * L*L*4 reals of `precision` each, distinct buffers; blocking on the
+ * context stream. */
+int epfft_average5(epfft_ctx *ctx, int32_t L, int32_t precision, const void *eps_in_dev, void *eps_out_dev);
+
 
 /* ---------------------------------------------------------------------- */
 /* Serving: continuous batching of independent solves                      */

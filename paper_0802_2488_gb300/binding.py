@@ -32,11 +32,15 @@ EPFFT_ERR_SCRATCH_LIMIT = -8
 EPFFT_FP64 = 0
 EPFFT_FP32 = 1
 EPFFT_GREEN_EQ3 = 0
+EPFFT_GREEN_CG1 = 1
+EPFFT_GREEN_DG1 = 2
+_GREEN = {"eq3": EPFFT_GREEN_EQ3, "cg1": EPFFT_GREEN_CG1, "dg1": EPFFT_GREEN_DG1}
 
 SYMBOLS = ["epfft_create", "epfft_destroy", "epfft_last_stats", "epfft_strerror", "epfft_supported",
            "epfft_solve", "epfft_solve_batch", "epfft_mask", "epfft_iterate", "epfft_project", "epfft_label",
            "epfft_time_passes", "epfft_project_static", "epfft_serve_open", "epfft_serve_close",
-           "epfft_submit", "epfft_serve_step", "epfft_poll", "epfft_autotune", "epfft_set_tiling"]
+           "epfft_submit", "epfft_serve_step", "epfft_poll", "epfft_autotune", "epfft_set_tiling",
+           "epfft_solve_dg2", "epfft_average5"]
 
 
 class EpfftError(RuntimeError):
@@ -104,6 +108,8 @@ def lib():
         L.epfft_supported.argtypes = [i32, i32]
         L.epfft_last_stats.argtypes = [vp, C.POINTER(_Stats)]
         L.epfft_solve.argtypes = [vp, C.POINTER(_Problem), C.POINTER(_Path), vp, C.POINTER(_Fields)]
+        L.epfft_solve_dg2.argtypes = [vp, C.POINTER(_Problem), C.POINTER(_Path), vp, C.POINTER(_Fields)]
+        L.epfft_average5.argtypes = [vp, i32, i32, vp, vp]
         L.epfft_solve_batch.argtypes = [vp, i32, C.POINTER(_Problem), C.POINTER(_Path), C.POINTER(vp),
                                         C.POINTER(_Fields)]
         L.epfft_mask.argtypes = [i32, dbl, C.c_uint64, vp, vp]
@@ -156,6 +162,7 @@ class Problem:
     tol_eq: float = 1e-8
     tol_macro: float = 1e-8
     max_iter: int = 10000
+    green: str = "eq3"               # 'eq3' | 'cg1' | 'dg1' (Sec. 2)
 
     def _c(self) -> tuple[_Problem, object]:
         keep = None
@@ -171,7 +178,7 @@ class Problem:
                 mptr, mdev = keep.data_ptr(), 1
         prec = {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[self.precision]
         p = _Problem(self.L, prec, float(self.void_fraction), int(self.seed) & (2**64 - 1), mptr, mdev,
-                     EPFFT_GREEN_EQ3, self.mu, self.lambda_, self.yield_stress,
+                     _GREEN[self.green], self.mu, self.lambda_, self.yield_stress,
                      self.mu if self.mu0 is None else self.mu0,
                      self.lambda_ if self.lambda0 is None else self.lambda0,
                      self.tol_eq, self.tol_macro, int(self.max_iter), 0)
@@ -286,6 +293,35 @@ def epfft_solve(ctx: Context, problem: Problem, path, fields: bool = False):
                            C.byref(cf) if cf is not None else None)
     _check(rc, "epfft_solve", (EPFFT_OK, EPFFT_NOT_CONVERGED))
     return (rc, rec, f) if fields else (rc, rec)
+
+
+def epfft_solve_dg2(ctx: Context, problem: Problem, path, fields: bool = False):
+    """DG2 (Sec. 2): the average of four complete solves with the Eq. 3
+    operator at mirrored momenta.  Returns (rc, records[, Fields]) with
+    Fields.eps the averaged final strain and Fields.plastic / labels (L, L)
+    arrays of that field's plastic pixels and their clusters."""
+    p, keep = problem._c()
+    cp, parr = _path(path)
+    rec = np.zeros(cp.n_inc, dtype=RECORD_DTYPE)
+    f = cf = None
+    if fields:
+        L = problem.L
+        f = Fields(np.empty((L, L, 4), dtype=problem.real_dtype), np.empty((L, L), np.uint8),
+                   np.empty((L, L), np.int32))
+        cf = _Fields(f.eps.ctypes.data, f.plastic.ctypes.data, f.labels.ctypes.data, 0, 0)
+    rc = lib().epfft_solve_dg2(ctx.handle, C.byref(p), C.byref(cp), rec.ctypes.data,
+                               C.byref(cf) if cf is not None else None)
+    _check(rc, "epfft_solve_dg2", (EPFFT_OK, EPFFT_NOT_CONVERGED))
+    return (rc, rec, f) if fields else (rc, rec)
+
+
+def epfft_average5(ctx: Context, L: int, precision: str, eps_in, eps_out):
+    """CG2 post-processing (Sec. 2) of a device strain field: eps_out = mean of
+    each pixel and its four neighbours.  eps_in / eps_out: CUDA tensors of
+    L*L*4 reals."""
+    assert eps_in.is_cuda and eps_out.is_cuda and eps_in.numel() == eps_out.numel() == L * L * 4
+    _check(lib().epfft_average5(ctx.handle, L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision],
+                                eps_in.data_ptr(), eps_out.data_ptr()), "epfft_average5")
 
 
 def epfft_solve_batch(ctx: Context, problems: Sequence[Problem], paths: Sequence, fields: bool = False):

@@ -47,6 +47,13 @@ __device__ __forceinline__ C2<T> mul_i(C2<T> a) { return mk(-a.im, a.re); }
 template <typename T>
 __device__ __forceinline__ T norm2(C2<T> a) { return a.re * a.re + a.im * a.im; }
 
+// Green operators of Sec. 2 (values of the ABI's EPFFT_GREEN_*).
+enum GreenMode : int32_t {
+  GM_EQ3 = 0,  // discrete operator of Eq. 3
+  GM_CG1 = 1,  // continuum operator: Eq. 3 with k_j = q_j
+  GM_DG1 = 2,  // symmetrized operator G^(1)
+};
+
 // Solve phases of the per-solve state machine driven on the device.
 enum Phase : int32_t {
   PH_INIT = 0,   // warm start of increment `inc` from the accepted state
@@ -101,6 +108,8 @@ struct Solve {
   float mcf[N_MC];   // the same rounded to FP32
   double tol_eq, tol_macro;
   int32_t max_iter, n_inc;
+  int32_t green;       // Green operator (GreenMode)
+  int32_t pad0;
   const double* path;  // n_inc * 4 prescribed mean strains (11,22,33,12)
   Record* rec;         // n_inc records
   uint8_t* flags;      // n_inc * L * L plastic flags (may be null)

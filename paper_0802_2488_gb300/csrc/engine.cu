@@ -2,6 +2,7 @@
 // solves, the device-driven loop (a CUDA graph whose while node repeats
 // one column pass and one row pass until every solve is done), cluster
 // labelling and copy-out.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -16,6 +17,7 @@
 #include "../../include/epfft.h"
 #include "aux_kernels.cuh"
 #include "launch.cuh"
+#include "post_kernels.cuh"
 #include "tables.cuh"
 
 using namespace epfft;
@@ -175,7 +177,7 @@ int check_problem(const epfft_problem* p) {
   if (!p) return EPFFT_ERR_ARG;
   if (!is_pow2(p->L) || p->L < 4 || p->L > 4096) return EPFFT_ERR_ARG;
   if (p->precision != EPFFT_FP32 && p->precision != EPFFT_FP64) return EPFFT_ERR_ARG;
-  if (p->green != EPFFT_GREEN_EQ3) return EPFFT_ERR_ARG;
+  if (p->green != EPFFT_GREEN_EQ3 && p->green != EPFFT_GREEN_CG1 && p->green != EPFFT_GREEN_DG1) return EPFFT_ERR_ARG;
   if (!supported(p->L, p->precision)) return EPFFT_ERR_UNSUPPORTED;
   if (!p->mask && !(p->void_fraction >= 0.0 && p->void_fraction <= 1.0)) return EPFFT_ERR_ARG;
   if (!(p->mu > 0.0) || !(p->mu0 > 0.0) || !std::isfinite(p->mu) || !std::isfinite(p->mu0)) return EPFFT_ERR_ARG;
@@ -211,6 +213,7 @@ void fill_consts(Solve& S) {
 // Device state of one batch.
 struct Batch {
   int L = 0, prec = 0, nb = 0, var = -1;  // var < 0: the context's tuned tiling
+  int general = 0;                        // some solve uses an operator other than Eq. 3
   PassShape sh{};
   void* tw = nullptr;
   void* ktab = nullptr;
@@ -223,10 +226,10 @@ struct Batch {
 
 int launch_body(epfft_ctx* c, Batch& B, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
   if (B.prec == EPFFT_FP32) {
-    CK(launch_col<float>(B.L, B.var, B.nb, s, B.d_solves, B.tw, B.ktab, h, use_cond));
+    CK(launch_col<float>(B.L, B.var, B.nb, s, B.d_solves, B.tw, B.ktab, h, use_cond, B.general));
     CK(launch_row<float>(B.L, B.var, B.nb, s, B.d_solves, B.d_ctl, B.tw, h, use_cond));
   } else {
-    CK(launch_col<double>(B.L, B.var, B.nb, s, B.d_solves, B.tw, B.ktab, h, use_cond));
+    CK(launch_col<double>(B.L, B.var, B.nb, s, B.d_solves, B.tw, B.ktab, h, use_cond, B.general));
     CK(launch_row<double>(B.L, B.var, B.nb, s, B.d_solves, B.d_ctl, B.tw, h, use_cond));
   }
   (void)c;
@@ -258,6 +261,7 @@ int init_solve(Get&& get, const PassShape& sh, int L, int prec, const epfft_prob
   S.tol_macro = p.tol_macro;
   S.max_iter = p.max_iter;
   S.n_inc = n_inc;
+  S.green = p.green;
   fill_consts(S);
   void* eps0d = get(4 * LL * rs);
   void* eps1d = get(4 * LL * rs);
@@ -301,6 +305,7 @@ int setup_batch(epfft_ctx* c, Arena& A, Batch& B, int n, const epfft_problem* pr
   B.L = probs[0].L;
   B.prec = probs[0].precision;
   B.nb = n;
+  for (int i = 0; i < n; i++) B.general |= probs[i].green != EPFFT_GREEN_EQ3;
   if (B.var < 0) B.var = variant_for(c, B.L, B.prec, n);
   int rc = shape(B.L, B.prec, B.var, &B.sh);
   if (rc) return rc;
@@ -408,8 +413,8 @@ int run_checked(epfft_ctx* c, Batch& B) {
   for (int64_t step = 0;; step++) {
     CK(cudaMemcpy(hs.data(), B.d_solves, sizeof(Solve) * B.nb, cudaMemcpyDeviceToHost));
     cudaError_t e;
-    if (B.prec == EPFFT_FP32) e = launch_col<float>(B.L, B.var, B.nb, c->stream, B.d_solves, B.tw, B.ktab, 0, 0);
-    else e = launch_col<double>(B.L, B.var, B.nb, c->stream, B.d_solves, B.tw, B.ktab, 0, 0);
+    if (B.prec == EPFFT_FP32) e = launch_col<float>(B.L, B.var, B.nb, c->stream, B.d_solves, B.tw, B.ktab, 0, 0, B.general);
+    else e = launch_col<double>(B.L, B.var, B.nb, c->stream, B.d_solves, B.tw, B.ktab, 0, 0, B.general);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
       fprintf(stderr, "epfft check: column pass failed at step %lld (phase %d inc %d iter %d): %s\n",
@@ -598,8 +603,8 @@ int time_passes_impl(epfft_ctx* ctx, epfft_problem p, int n_batch, const double 
   for (auto& e : ev) CK(cudaEventCreate(&e));
   for (int it = 0; it < n_iter; it++) {
     CK(cudaEventRecord(ev[3 * it], ctx->stream));
-    if (B.prec == EPFFT_FP32) CK(launch_col<float>(B.L, B.var, nb, ctx->stream, B.d_solves, B.tw, B.ktab, 0, 0));
-    else CK(launch_col<double>(B.L, B.var, nb, ctx->stream, B.d_solves, B.tw, B.ktab, 0, 0));
+    if (B.prec == EPFFT_FP32) CK(launch_col<float>(B.L, B.var, nb, ctx->stream, B.d_solves, B.tw, B.ktab, 0, 0, B.general));
+    else CK(launch_col<double>(B.L, B.var, nb, ctx->stream, B.d_solves, B.tw, B.ktab, 0, 0, B.general));
     CK(cudaEventRecord(ev[3 * it + 1], ctx->stream));
     if (B.prec == EPFFT_FP32) CK(launch_row<float>(B.L, B.var, nb, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
     else CK(launch_row<double>(B.L, B.var, nb, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
@@ -671,6 +676,7 @@ struct Server {
   int64_t next = 1;
   std::deque<int64_t> queue;
   std::map<int64_t, Ticket> tickets;
+  // (L, 2 * precision + general) -> class
   std::map<std::pair<int, int>, ServeClass*> classes;
 };
 
@@ -691,8 +697,8 @@ void free_class(epfft_ctx* c, ServeClass* k) {
   delete k;
 }
 
-int get_class(epfft_ctx* c, Server& S, int L, int prec, ServeClass** out) {
-  auto key = std::make_pair(L, prec);
+int get_class(epfft_ctx* c, Server& S, int L, int prec, int general, ServeClass** out) {
+  auto key = std::make_pair(L, 2 * prec + general);
   auto it = S.classes.find(key);
   if (it != S.classes.end()) {
     *out = it->second;
@@ -707,6 +713,7 @@ int get_class(epfft_ctx* c, Server& S, int L, int prec, ServeClass** out) {
   B.L = L;
   B.prec = prec;
   B.nb = S.cap;
+  B.general = general;
   B.var = variant_for(c, L, prec, S.cap);
   int rc = shape(L, prec, B.var, &B.sh);
   if (!rc) rc = get_tables(c, L, prec, &B.tw, &B.ktab);
@@ -750,7 +757,7 @@ int serve_admit(epfft_ctx* c, Server& S) {
       continue;
     }
     ServeClass* k = nullptr;
-    int rc = get_class(c, S, t.prob.L, t.prob.precision, &k);
+    int rc = get_class(c, S, t.prob.L, t.prob.precision, t.prob.green != EPFFT_GREEN_EQ3, &k);
     if (rc) return rc;
     int slot = -1;
     for (int i = 0; i < k->cap; i++)
@@ -944,6 +951,132 @@ int epfft_solve_batch(epfft_ctx* ctx, int32_t n, const epfft_problem* problems, 
                       epfft_record* const* records, const epfft_fields* fields) {
   if (!records) return EPFFT_ERR_ARG;
   return solve_impl(ctx, n, problems, paths, records, fields, nullptr, nullptr, nullptr);
+}
+
+int epfft_solve_dg2(epfft_ctx* ctx, const epfft_problem* problem, const epfft_path* path, epfft_record* records,
+                    const epfft_fields* fields) {
+  if (!ctx || !problem || !path || !records) return EPFFT_ERR_ARG;
+  int rc = check_problem(problem);
+  if (rc) return rc;
+  if (problem->green != EPFFT_GREEN_EQ3) return EPFFT_ERR_ARG;
+  if (path->n_inc < 1 || !path->E) return EPFFT_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return EPFFT_ERR_CUDA;
+  const int L = problem->L, prec = problem->precision, n_inc = path->n_inc;
+  const size_t LL = (size_t)L * L, rs = real_size(prec);
+  Arena A(ctx);
+  // the lattice and its three mirror images (members: none, x1 and x2, x1, x2)
+  static const int kAxes[4] = {0, 3, 1, 2};
+  uint8_t* masks = (uint8_t*)A.get(4 * LL);
+  void* eps = A.get(5 * 4 * LL * rs);  // four members' final fields, then their average
+  uint8_t* flags = (uint8_t*)A.get(LL);
+  int32_t* lab = (int32_t*)A.get(sizeof(int32_t) * LL);
+  int32_t* dcount = (int32_t*)A.get(2 * sizeof(int32_t));
+  if (!masks || !eps || !flags || !lab || !dcount) return EPFFT_ERR_OOM;
+  if (problem->mask) {
+    CK(cudaMemcpyAsync(masks, problem->mask, LL,
+                       problem->mask_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  } else {
+    CK(launch_mask(masks, (int64_t)LL, problem->seed, void_threshold(problem->void_fraction), ctx->stream));
+  }
+  for (int m = 1; m < 4; m++) CK(launch_mirror_mask(masks, masks + m * LL, L, kAxes[m], ctx->stream));
+  epfft_problem probs[4];
+  epfft_path paths[4];
+  std::vector<double> E[4];
+  epfft_record* recp[4];
+  std::vector<epfft_record> recs[4];
+  void* outs[4];
+  for (int m = 0; m < 4; m++) {
+    probs[m] = *problem;
+    probs[m].mask = masks + m * LL;
+    probs[m].mask_on_device = 1;
+    E[m].assign(path->E, path->E + 4 * (size_t)n_inc);
+    if (kAxes[m] == 1 || kAxes[m] == 2)  // a single mirror reverses E12
+      for (int k = 0; k < n_inc; k++) E[m][4 * k + 3] = -E[m][4 * k + 3];
+    paths[m] = epfft_path{n_inc, 0, E[m].data()};
+    recs[m].resize(n_inc);
+    recp[m] = recs[m].data();
+    outs[m] = (char*)eps + m * 4 * LL * rs;
+  }
+  const int status = solve_impl(ctx, 4, probs, paths, recp, nullptr, nullptr, outs, nullptr);
+  if (status != EPFFT_OK && status != EPFFT_NOT_CONVERGED) return status;
+  void* avg = (char*)eps + 4 * 4 * LL * rs;
+  Solve S;
+  std::memset(&S, 0, sizeof(S));
+  S.lam = problem->lambda;
+  S.mu = problem->mu;
+  S.Y = problem->yield_stress;
+  S.lam0 = problem->lambda0;
+  S.mu0 = problem->mu0;
+  fill_consts(S);
+  if (prec == EPFFT_FP32) {
+    CK(launch_dg2_average<float>((const float*)outs[0], (const float*)outs[1], (const float*)outs[2],
+                                 (const float*)outs[3], (float*)avg, L, ctx->stream));
+    CK(launch_plastic_flags<float>((const float*)avg, masks, flags, L, S.mcf[MC_TWO_MU], S.mcf[MC_YLIM2],
+                                   ctx->stream));
+  } else {
+    CK(launch_dg2_average<double>((const double*)outs[0], (const double*)outs[1], (const double*)outs[2],
+                                  (const double*)outs[3], (double*)avg, L, ctx->stream));
+    CK(launch_plastic_flags<double>((const double*)avg, masks, flags, L, S.mcd[MC_TWO_MU], S.mcd[MC_YLIM2],
+                                    ctx->stream));
+  }
+  CK(cudaMemsetAsync(dcount, 0, 2 * sizeof(int32_t), ctx->stream));
+  CK(launch_label(flags, lab, 1, L, 1, dcount, dcount + 1, ctx->stream));
+  int32_t hc[2] = {0, 0};
+  CK(cudaMemcpyAsync(hc, dcount, sizeof(hc), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (hc[1]) return EPFFT_ERR_DEVICE_TIMEOUT;
+  // per increment: macro values of the four (mirrored back) averaged, the
+  // largest indicators and status, the summed iterations; the plastic set
+  // and clusters are those of the averaged final field (last record only)
+  for (int k = 0; k < n_inc; k++) {
+    epfft_record r = recs[0][k];
+    for (int c = 0; c < 4; c++) {
+      double s = 0.0, e = 0.0;
+      for (int m = 0; m < 4; m++) {
+        const double sg = (c == 3 && (kAxes[m] == 1 || kAxes[m] == 2)) ? -1.0 : 1.0;
+        s += sg * recs[m][k].sig_mean[c];
+        e += sg * recs[m][k].eps_mean[c];
+      }
+      r.sig_mean[c] = 0.25 * s;
+      r.eps_mean[c] = 0.25 * e;
+    }
+    r.iterations = 0;
+    for (int m = 0; m < 4; m++) {
+      r.eta1 = std::max(r.eta1, recs[m][k].eta1);
+      r.eta2 = std::max(r.eta2, recs[m][k].eta2);
+      r.eta3 = std::max(r.eta3, recs[m][k].eta3);
+      r.status = std::max(r.status, recs[m][k].status);
+      r.iterations += recs[m][k].iterations;
+    }
+    r.n_plastic = -1;
+    r.n_clusters = -1;
+    records[k] = r;
+  }
+  if (fields) {
+    const cudaMemcpyKind kd = fields->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (fields->eps) CK(cudaMemcpyAsync(fields->eps, avg, 4 * LL * rs, kd, ctx->stream));
+    if (fields->plastic) CK(cudaMemcpyAsync(fields->plastic, flags, LL, kd, ctx->stream));
+    if (fields->labels) CK(cudaMemcpyAsync(fields->labels, lab, sizeof(int32_t) * LL, kd, ctx->stream));
+  }
+  std::vector<uint8_t> hf(LL);
+  CK(cudaMemcpyAsync(hf.data(), flags, LL, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  int32_t npl = 0;
+  for (size_t i = 0; i < LL; i++) npl += hf[i];
+  records[n_inc - 1].n_plastic = npl;
+  records[n_inc - 1].n_clusters = hc[0];
+  ctx->last.kernel_launches += 3 + (problem->mask ? 0 : 1) + 2 + 4;
+  return status;
+}
+
+int epfft_average5(epfft_ctx* ctx, int32_t L, int32_t precision, const void* eps_in_dev, void* eps_out_dev) {
+  if (!ctx || !eps_in_dev || !eps_out_dev || eps_in_dev == eps_out_dev) return EPFFT_ERR_ARG;
+  if (!is_pow2(L) || L < 4 || (precision != EPFFT_FP32 && precision != EPFFT_FP64)) return EPFFT_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return EPFFT_ERR_CUDA;
+  if (precision == EPFFT_FP32) CK(launch_avg5<float>((const float*)eps_in_dev, (float*)eps_out_dev, L, ctx->stream));
+  else CK(launch_avg5<double>((const double*)eps_in_dev, (double*)eps_out_dev, L, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return EPFFT_OK;
 }
 
 int epfft_mask(int32_t L, double void_fraction, uint64_t seed, uint8_t* mask_dev, void* stream) {

@@ -28,7 +28,8 @@ static cudaError_t prepare_L() {
   constexpr int V = EPFFT_VAR;
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(row_pass<T, L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::ROW_SMEM)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(col_pass<T, L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::COL_SMEM)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(col_pass<T, L, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::COL_SMEM)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(col_pass<T, L, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::COL_SMEM)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(row_forward<T, L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::ROW_SMEM)) != cudaSuccess) return e;
   return cudaFuncSetAttribute(row_inverse<T, L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::ROW_SMEM);
 }
@@ -72,14 +73,18 @@ cudaError_t launch_row_v<EPFFT_REAL, EPFFT_VAR>(int L, int nb, cudaStream_t s, S
 
 template <>
 cudaError_t launch_col_v<EPFFT_REAL, EPFFT_VAR>(int L, int nb, cudaStream_t s, Solve* solves, const void* tw, const void* ktab,
-                                   cudaGraphConditionalHandle cond, int use_cond) {
+                                   cudaGraphConditionalHandle cond, int use_cond, int general) {
   switch (L) {
 #define X(n)                                                                                         \
   case n: {                                                                                          \
-    using C = Cfg<EPFFT_REAL, n, EPFFT_VAR>;                                                                    \
-    col_pass<EPFFT_REAL, n, EPFFT_VAR><<<dim3((n / 2) / C::W, nb), C::NT_COL, C::COL_SMEM, s>>>(                \
-        solves, reinterpret_cast<const C2<EPFFT_REAL>*>(tw),                                         \
-        reinterpret_cast<const C2<EPFFT_REAL>*>(ktab), cond, use_cond);                              \
+    using C = Cfg<EPFFT_REAL, n, EPFFT_VAR>;                                                         \
+    const dim3 grid((n / 2) / C::W, nb);                                                             \
+    const C2<EPFFT_REAL>* tw_ = reinterpret_cast<const C2<EPFFT_REAL>*>(tw);                         \
+    const C2<EPFFT_REAL>* k_ = reinterpret_cast<const C2<EPFFT_REAL>*>(ktab);                        \
+    if (general)                                                                                     \
+      col_pass<EPFFT_REAL, n, EPFFT_VAR, true><<<grid, C::NT_COL, C::COL_SMEM, s>>>(solves, tw_, k_, cond, use_cond); \
+    else                                                                                             \
+      col_pass<EPFFT_REAL, n, EPFFT_VAR, false><<<grid, C::NT_COL, C::COL_SMEM, s>>>(solves, tw_, k_, cond, use_cond); \
     return cudaGetLastError();                                                                       \
   }
     EPFFT_FOR_L(X)

@@ -24,9 +24,11 @@ cudaError_t prepare_v(int L);
 template <typename T, int V>
 cudaError_t launch_row_v(int L, int nb, cudaStream_t s, Solve* solves, BatchCtl* bc, const void* tw,
                          cudaGraphConditionalHandle cond, int use_cond);
+// general = 0: every solve of the launch uses the Eq. 3 operator (the
+// specialised kernel); 1: each solve's own operator
 template <typename T, int V>
 cudaError_t launch_col_v(int L, int nb, cudaStream_t s, Solve* solves, const void* tw, const void* ktab,
-                         cudaGraphConditionalHandle cond, int use_cond);
+                         cudaGraphConditionalHandle cond, int use_cond, int general);
 template <typename T, int V>
 cudaError_t launch_row_forward_v(int L, cudaStream_t s, const void* p, void* spec, const void* tw);
 template <typename T, int V>
@@ -55,9 +57,9 @@ inline cudaError_t launch_row(int L, int var, int nb, cudaStream_t s, Solve* sol
 }
 template <typename T>
 inline cudaError_t launch_col(int L, int var, int nb, cudaStream_t s, Solve* solves, const void* tw,
-                              const void* ktab, cudaGraphConditionalHandle cond, int use_cond) {
-  return var == 0 ? launch_col_v<T, 0>(L, nb, s, solves, tw, ktab, cond, use_cond)
-                  : launch_col_v<T, 1>(L, nb, s, solves, tw, ktab, cond, use_cond);
+                              const void* ktab, cudaGraphConditionalHandle cond, int use_cond, int general = 0) {
+  return var == 0 ? launch_col_v<T, 0>(L, nb, s, solves, tw, ktab, cond, use_cond, general)
+                  : launch_col_v<T, 1>(L, nb, s, solves, tw, ktab, cond, use_cond, general);
 }
 template <typename T>
 inline cudaError_t launch_row_forward(int L, int var, cudaStream_t s, const void* p, void* spec, const void* tw) {

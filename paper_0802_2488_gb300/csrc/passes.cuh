@@ -390,7 +390,11 @@ __device__ __forceinline__ void finalize_solve(Solve& S, int phase, const double
     }
     const bool finite = isfinite(eta1) && isfinite(eta2) && isfinite(sig[0]) && isfinite(sig[1]) &&
                         isfinite(sig[3]);
-    const bool conv = eta1 < S.tol_eq && eta2 < S.tol_macro;
+    // equilibrium test: eta1 for the operators of Eq. 3; the continuum and
+    // symmetrized operators are not Green operators of Eq. 1, so there the
+    // fixed-point residual eta3 of the iterate takes its place
+    const double eq = (S.green == GM_CG1 || S.green == GM_DG1) ? S.eta3_cur : eta1;
+    const bool conv = eq < S.tol_eq && eta2 < S.tol_macro;
     if (!finite || conv || n >= S.max_iter) {
       Record& R = S.rec[S.inc];
       for (int c = 0; c < 4; c++) {
@@ -699,7 +703,9 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
 // ---------------------------------------------------------------------------
 // Column pass
 // ---------------------------------------------------------------------------
-template <typename T, int L, int V>
+// GEN = false: the Eq. 3 operator only (every solve of the launch uses it);
+// GEN = true: the operator each solve names (GreenMode).
+template <typename T, int L, int V, bool GEN>
 __global__ void __launch_bounds__(Cfg<T, L, V>::NT_COL, Cfg<T, L, V>::MINB_COL)
 col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* __restrict__ ktab,
          cudaGraphConditionalHandle cond, int use_cond) {
@@ -754,6 +760,8 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
 
   const T lam0 = T(S.lam0), mu0 = T(S.mu0);
   const T scale = T(1.0 / ((double)L * (double)L));
+  const int gm = GEN ? S.green : (int)GM_EQ3;
+  const C2<T>* __restrict__ qtab = ktab + L;  // continuum momenta follow k(m)
   // frequencies with m1 = b*W + w != 0 (consecutive threads: consecutive m2)
   for (int f = tid; f < W * L; f += NT) {
     const int w = f / L, m2 = f - w * L;
@@ -762,7 +770,8 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
     const int i0 = at(0, w, m2), i1 = at(1, w, m2), i2 = at(2, w, m2);
     if (!ECHK(i0, SZ, 31) || !ECHK(i1, SZ, 31) || !ECHK(i2, SZ, 31)) continue;
     C2<T> p11 = sp[i0], p22 = sp[i1], p12 = sp[i2];
-    green_apply(ktab[m1], ktab[m2], lam0, mu0, scale, p11, p22, p12);
+    if (GEN) green_op(gm, ktab, qtab, L, m1, m2, lam0, mu0, scale, p11, p22, p12);
+    else green_apply(ktab[m1], ktab[m2], lam0, mu0, scale, p11, p22, p12);
     sp[i0] = p11;
     sp[i1] = p22;
     sp[i2] = p12;
@@ -788,11 +797,11 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
         A[1] = mk(T(Ep[1]), T(0));
         A[2] = mk(T(Ep[3]), T(0));
       } else {
-        green_apply(ktab[0], ktab[m2], lam0, mu0, scale, A[0], A[1], A[2]);
-        green_apply(ktab[0], ktab[mp], lam0, mu0, scale, Ap[0], Ap[1], Ap[2]);
+        green_op(gm, ktab, qtab, L, 0, m2, lam0, mu0, scale, A[0], A[1], A[2]);
+        green_op(gm, ktab, qtab, L, 0, mp, lam0, mu0, scale, Ap[0], Ap[1], Ap[2]);
       }
-      green_apply(ktab[M], ktab[m2], lam0, mu0, scale, B[0], B[1], B[2]);
-      green_apply(ktab[M], ktab[mp], lam0, mu0, scale, Bp[0], Bp[1], Bp[2]);
+      green_op(gm, ktab, qtab, L, M, m2, lam0, mu0, scale, B[0], B[1], B[2]);
+      green_op(gm, ktab, qtab, L, M, mp, lam0, mu0, scale, Bp[0], Bp[1], Bp[2]);
 #pragma unroll
       for (int c = 0; c < 3; c++) {
         sp[at(c, 0, m2)] = A[c] + mul_i(B[c]);

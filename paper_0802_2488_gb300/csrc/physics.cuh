@@ -181,4 +181,66 @@ __device__ __forceinline__ void green_apply(C2<T> k1, C2<T> k2, T lam0, T mu0, T
   p12 = T(-0.5) * (k1 * v2 + k2 * v1);
 }
 
+// The Green operator `mode` of Sec. 2 at frequency (m1, m2) applied to
+// (p11, p22, p12) in place, times `scale`.  ktab: k(m) of Eq. 2; qtab: the
+// continuum momenta (q~(m), 0) (tables.cuh).
+//   GM_EQ3: Eq. 3.
+//   GM_CG1: Eq. 3 with k_j = q~_j, averaged over q~_j = +-pi at a Nyquist
+//           index (the operator stays even on the grid).
+//   GM_DG1: { G(q1,q2) + G(-q1,-q2) + (-1)^(i+j+k+l) [G(-q1,q2) + G(q1,-q2)] } / 4;
+//           the sign factor is D G D with D = diag(1, 1, -1) on (11, 22, 12).
+template <typename T>
+__device__ __forceinline__ void green_op(int mode, const C2<T>* __restrict__ ktab, const C2<T>* __restrict__ qtab,
+                                         int L, int m1, int m2, T lam0, T mu0, T scale, C2<T>& p11, C2<T>& p22,
+                                         C2<T>& p12) {
+  if (mode == GM_EQ3) {
+    green_apply(ktab[m1], ktab[m2], lam0, mu0, scale, p11, p22, p12);
+    return;
+  }
+  const C2<T> a11 = p11, a22 = p22, a12 = p12;
+  if (mode == GM_CG1) {
+    const bool y1 = 2 * m1 == L, y2 = 2 * m2 == L;
+    if (!y1 && !y2) {
+      green_apply(qtab[m1], qtab[m2], lam0, mu0, scale, p11, p22, p12);
+      return;
+    }
+    C2<T> s11 = mk(T(0), T(0)), s22 = s11, s12 = s11;
+    int cnt = 0;
+    for (int s1 = 0; s1 <= (int)y1; s1++)
+      for (int s2 = 0; s2 <= (int)y2; s2++) {
+        C2<T> k1 = qtab[m1], k2 = qtab[m2];
+        if (s1) k1.re = -k1.re;
+        if (s2) k2.re = -k2.re;
+        C2<T> b11 = a11, b22 = a22, b12 = a12;
+        green_apply(k1, k2, lam0, mu0, scale, b11, b22, b12);
+        s11 = s11 + b11;
+        s22 = s22 + b22;
+        s12 = s12 + b12;
+        cnt++;
+      }
+    const T w = T(1) / T(cnt);
+    p11 = w * s11;
+    p22 = w * s22;
+    p12 = w * s12;
+    return;
+  }
+  // GM_DG1
+  const int n1 = (L - m1) & (L - 1), n2 = (L - m2) & (L - 1);  // indices of -q1, -q2
+  C2<T> b11 = a11, b22 = a22, b12 = a12;
+  green_apply(ktab[m1], ktab[m2], lam0, mu0, scale, b11, b22, b12);
+  C2<T> s11 = b11, s22 = b22, s12 = b12;
+  b11 = a11, b22 = a22, b12 = a12;
+  green_apply(ktab[n1], ktab[n2], lam0, mu0, scale, b11, b22, b12);
+  s11 = s11 + b11, s22 = s22 + b22, s12 = s12 + b12;
+  b11 = a11, b22 = a22, b12 = T(-1) * a12;
+  green_apply(ktab[n1], ktab[m2], lam0, mu0, scale, b11, b22, b12);
+  s11 = s11 + b11, s22 = s22 + b22, s12 = s12 - b12;
+  b11 = a11, b22 = a22, b12 = T(-1) * a12;
+  green_apply(ktab[m1], ktab[n2], lam0, mu0, scale, b11, b22, b12);
+  s11 = s11 + b11, s22 = s22 + b22, s12 = s12 - b12;
+  p11 = T(0.25) * s11;
+  p22 = T(0.25) * s22;
+  p12 = T(0.25) * s12;
+}
+
 }  // namespace epfft

@@ -9,6 +9,8 @@
 //   [KOFF, KOFF + L)      k(m) = (sin q, 2 sin^2(q/2)), q = 2 pi m / L, the
 //                         symbol of the forward difference of Eq. 1
 //                         (i k = exp(i q) - 1)
+//   [QOFF, QOFF + L)      (q~(m), 0), the continuum momentum 2 pi m~ / L with
+//                         m~ = m folded into (-L/2, L/2] (CG1 operator)
 // Variants with the same plans share their stage tables.
 #pragma once
 #include <vector>
@@ -42,7 +44,8 @@ struct Tables {
   static constexpr int OFF_R1 = SAME ? OFF_R0 : OFF_C0 + TW_C0;
   static constexpr int OFF_C1 = SAME ? OFF_C0 : OFF_R1 + TW_R1;
   static constexpr int KOFF = SAME ? OFF_C0 + TW_C0 : OFF_C1 + TW_C1;
-  static constexpr int TOTAL = KOFF + L;
+  static constexpr int QOFF = KOFF + L;
+  static constexpr int TOTAL = QOFF + L;
   static __host__ __device__ constexpr int off_row(int v) { return v == 0 ? OFF_R0 : OFF_R1; }
   static __host__ __device__ constexpr int off_col(int v) { return v == 0 ? OFF_C0 : OFF_C1; }
 };
@@ -88,6 +91,9 @@ inline void host_tables_L(std::vector<T>& h) {
     const long double hs = sinl(pi * (long double)m / (long double)L);
     h[2 * (TB::KOFF + m)] = (T)sinl(q);
     h[2 * (TB::KOFF + m) + 1] = (T)(2.0L * hs * hs);
+    const int mf = m > L / 2 ? m - L : m;
+    h[2 * (TB::QOFF + m)] = (T)(2.0L * pi * (long double)mf / (long double)L);
+    h[2 * (TB::QOFF + m) + 1] = T(0);
   }
 }
 
