@@ -96,6 +96,8 @@ def lib():
         L.orc_al_step.argtypes = [C.c_int, _U8, C.POINTER(Material), _D, _D, _D, _VP, _VP]
         L.orc_stats.argtypes = [C.c_int, _U8, C.POINTER(Material), _D, _D, _D,
                                 C.POINTER(C.c_double), C.POINTER(C.c_int32), _VP]
+        L.orc_void_plastic.restype = C.c_int32
+        L.orc_void_plastic.argtypes = [C.c_int, _U8, _U8, _I32, _I32]
         L.orc_label.restype = C.c_int32
         L.orc_label.argtypes = [C.c_int, _U8, C.c_int, _I32]
         L.orc_solve.restype = C.c_int32
@@ -257,6 +259,55 @@ def label(flag: np.ndarray, periodic: bool = True):
     lab = np.empty((L, L), dtype=np.int32)
     n = lib().orc_label(L, f, 1 if periodic else 0, lab)
     return lab, int(n)
+
+
+def void_plastic(mask_: np.ndarray, plastic: np.ndarray):
+    """Sec. 3: clusters of the void-plastic phase, each void-free cluster
+    connected to its nearest void.  Returns (labels, stats) with stats =
+    (clusters, pixels of the largest, clusters without plastic pixels,
+    clusters of the voids alone, plastic pixels, void pixels)."""
+    m = np.ascontiguousarray(mask_, dtype=np.uint8)
+    p = np.ascontiguousarray(plastic, dtype=np.uint8)
+    L = m.shape[0]
+    lab = np.empty((L, L), dtype=np.int32)
+    st = np.zeros(6, dtype=np.int32)
+    lib().orc_void_plastic(L, m, p, lab, st)
+    return lab, st
+
+
+def indicators(records: np.ndarray, stats: np.ndarray, L: int, load: str) -> np.ndarray:
+    """Geometric indicators of Sec. 3 per increment, (n_inc, 8) columns:
+    eps0, sigma0, f_p, v_max, i, n, r, -d2 sigma0 / d eps0^2.
+      eps0, sigma0: <eps_m>, <sigma_m> (in-plane means (11 + 22) / 2) for
+        equibiaxial loading, <eps_12>, <sigma_12> for shear;
+      f_p = plastic pixels / matrix pixels (v_p / (1 - f));
+      v_max = pixels of the largest void-plastic cluster / L^2;
+      i = void-plastic clusters without plastic pixels / clusters of voids;
+      n = void-plastic clusters / clusters of voids (its value at eps0 = 0);
+      r = dn / d eps0 and -d2 sigma0 / d eps0^2 by second-order finite
+        differences on the (possibly uneven) eps0 grid, one-sided at the
+        ends (numpy.gradient).
+    stats: (n_inc, 6) rows of void_plastic."""
+    rec = np.asarray(records)
+    st = np.asarray(stats, dtype=np.float64)
+    if load == "equibiaxial":
+        e0 = 0.5 * (rec["eps_mean"][:, 0] + rec["eps_mean"][:, 1])
+        s0 = 0.5 * (rec["sig_mean"][:, 0] + rec["sig_mean"][:, 1])
+    else:
+        e0 = rec["eps_mean"][:, 3].copy()
+        s0 = rec["sig_mean"][:, 3].copy()
+    n_px = float(L * L)
+    fp = st[:, 4] / (n_px - st[:, 5])
+    vmax = st[:, 1] / n_px
+    i = st[:, 2] / st[:, 3]
+    n = st[:, 0] / st[:, 3]
+    if len(e0) >= 2:
+        r = np.gradient(n, e0)
+        d2 = -np.gradient(np.gradient(s0, e0), e0)
+    else:
+        r = np.zeros_like(n)
+        d2 = np.zeros_like(n)
+    return np.stack([e0, s0, fp, vmax, i, n, r, d2], axis=1)
 
 
 RECORD_DTYPE = np.dtype([("sig_mean", "f8", 4), ("eps_mean", "f8", 4), ("eta1", "f8"),

@@ -50,6 +50,10 @@
  *                               (Sec. 2, end of "Discrete Green functions").
  *   orc_label                 : Hoshen-Kopelman nearest-neighbour clusters
  *                               (Sec. 3), periodic lattice.
+ *   orc_void_plastic          : clusters of the void-plastic phase with each
+ *                               void-free cluster connected to its nearest
+ *                               void (Sec. 3), and the counts behind the
+ *                               indicators of Sec. 3.
  */
 #include <complex.h>
 #include <math.h>
@@ -756,4 +760,107 @@ void orc_avg5(int L, const double *in, double *out) {
         out[4 * x + c] = s / 5.0;
       }
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* Void-plastic clusters (Sec. 3)                                      */
+/* ------------------------------------------------------------------ */
+
+/* Squared distance between pixel centres on the periodic lattice. */
+static int64_t pdist2(int L, int64_t a, int64_t b) {
+  int64_t d1 = llabs(a % L - b % L), d2 = llabs(a / L - b / L);
+  if (d1 > L - d1) d1 = L - d1;
+  if (d2 > L - d2) d2 = L - d2;
+  return d1 * d1 + d2 * d2;
+}
+
+/* Clusters of the void-plastic phase (voids and plastic pixels) of Sec. 3:
+ * nearest-neighbour clusters of the phase (periodic), then every cluster
+ * without a void is connected to the nearest void: the void pixel at the
+ * smallest distance from any of the cluster's pixels (ties: the smallest
+ * linear index of the void pixel), computed here by comparing every pixel
+ * of the cluster with every void pixel.  label[x] = smallest linear index
+ * of x's final cluster, -1 off the phase.
+ * stats[0] = number of final clusters, stats[1] = pixels of the largest,
+ * stats[2] = final clusters without a plastic pixel (isolated voids),
+ * stats[3] = number of clusters of the voids alone, stats[4] = plastic
+ * (non-void) pixels, stats[5] = void pixels.  Returns stats[0]. */
+int32_t orc_void_plastic(int L, const uint8_t *mask, const uint8_t *plastic, int32_t *label, int32_t *stats) {
+  const int64_t n = (int64_t)L * L;
+  uint8_t *vp = (uint8_t *)malloc((size_t)n);
+  int32_t *lab = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  for (int64_t x = 0; x < n; x++) vp[x] = (uint8_t)(mask[x] || plastic[x]);
+  orc_label(L, vp, 1, lab);
+  /* clusters (by root) that hold a void */
+  uint8_t *has_void = (uint8_t *)calloc((size_t)n, 1);
+  for (int64_t x = 0; x < n; x++)
+    if (mask[x]) has_void[lab[x]] = 1;
+  int64_t nvoid = 0;
+  for (int64_t x = 0; x < n; x++) nvoid += mask[x] != 0;
+  /* target root of each cluster: itself, or the root of its nearest void */
+  int64_t *target = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  for (int64_t x = 0; x < n; x++) target[x] = x;
+  if (nvoid > 0) {
+    for (int64_t r = 0; r < n; r++) {
+      if (!vp[r] || lab[r] != r || has_void[r]) continue;
+      int64_t best_d = -1, best_v = -1;
+      for (int64_t x = 0; x < n; x++) {
+        if (lab[x] != r) continue;
+        for (int64_t v = 0; v < n; v++) {
+          if (!mask[v]) continue;
+          const int64_t d = pdist2(L, x, v);
+          if (best_d < 0 || d < best_d || (d == best_d && v < best_v)) {
+            best_d = d;
+            best_v = v;
+          }
+        }
+      }
+      target[r] = lab[best_v];
+    }
+  }
+  /* final label: smallest linear index over the merged clusters */
+  int64_t *final_root = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  for (int64_t x = 0; x < n; x++) final_root[x] = n;
+  for (int64_t r = 0; r < n; r++) {
+    if (!vp[r] || lab[r] != r) continue;
+    const int64_t t = target[r];
+    if (r < final_root[t]) final_root[t] = r;
+  }
+  for (int64_t x = 0; x < n; x++) {
+    if (!vp[x]) {
+      label[x] = -1;
+      continue;
+    }
+    label[x] = (int32_t)final_root[target[lab[x]]];
+  }
+  int32_t count = 0, largest = 0, isolated = 0;
+  int32_t *size = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+  uint8_t *has_pl = (uint8_t *)calloc((size_t)n, 1);
+  for (int64_t x = 0; x < n; x++) {
+    if (label[x] < 0) continue;
+    size[label[x]]++;
+    if (!mask[x]) has_pl[label[x]] = 1;
+  }
+  for (int64_t x = 0; x < n; x++) {
+    if (size[x] == 0) continue;
+    count++;
+    if (size[x] > largest) largest = size[x];
+    if (!has_pl[x]) isolated++;
+  }
+  stats[0] = count;
+  stats[1] = largest;
+  stats[2] = isolated;
+  stats[3] = orc_label(L, mask, 1, lab);
+  int32_t npl = 0;
+  for (int64_t x = 0; x < n; x++) npl += plastic[x] && !mask[x];
+  stats[4] = npl;
+  stats[5] = (int32_t)nvoid;
+  free(vp);
+  free(lab);
+  free(has_void);
+  free(target);
+  free(final_root);
+  free(size);
+  free(has_pl);
+  return count;
 }
