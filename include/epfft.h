@@ -206,6 +206,30 @@ int epfft_solve_batch(epfft_ctx *ctx, int32_t n, const epfft_problem *problems,
 int epfft_solve_dg2(epfft_ctx *ctx, const epfft_problem *problem, const epfft_path *path,
                     epfft_record *records, const epfft_fields *fields);
 
+/* Sec. 3: clusters of the void-plastic phase (voids and plastic pixels,
+ * 4-neighbours, periodic) where every cluster without a void is connected
+ * to its nearest void pixel (periodic Euclidean distance between pixel
+ * centres; ties to the smaller linear index), so that each cluster holds a
+ * void.  mask_dev: L*L (1 = void); plastic_dev: n_img images of L*L plastic
+ * flags (e.g. the per-increment flags of a solve); labels_dev (optional,
+ * n_img*L*L): the final clusters, label = smallest linear index, -1 off
+ * the phase.  stats (host, n_img x 6): clusters, pixels of the largest,
+ * clusters without a plastic pixel (isolated voids), clusters of the voids
+ * alone, plastic pixels, void pixels.  Blocking. */
+int epfft_void_plastic(epfft_ctx *ctx, int32_t L, int32_t n_img, const uint8_t *mask_dev,
+                       const uint8_t *plastic_dev, int32_t *labels_dev, int32_t *stats);
+
+/* The indicators of Sec. 3 per increment from a solve's records and the
+ * epfft_void_plastic stats of its increments (host arrays; load: 0
+ * equibiaxial, 1 shear).  out: n_inc x 8 doubles: eps0, sigma0 (in-plane
+ * means (11 + 22) / 2, or the 12 components in shear), f_p = plastic /
+ * matrix pixels, v_max = largest cluster / L^2, i = isolated void clusters /
+ * void clusters, n = clusters / void clusters, r = dn/d eps0 and
+ * -d2 sigma0 / d eps0^2 (finite differences: second order inside, first
+ * order at the ends). */
+int epfft_indicators(int32_t n_inc, const epfft_record *records, const int32_t *stats, int32_t L, int32_t load,
+                     double *out);
+
 /* CG2 post-processing (Sec. 2): eps_out(x) = mean of eps_in at x and its
  * four nearest neighbours (periodic), per component.  Device pointers,
  * L*L*4 reals of `precision` each, distinct buffers; blocking on the

@@ -40,7 +40,7 @@ SYMBOLS = ["epfft_create", "epfft_destroy", "epfft_last_stats", "epfft_strerror"
            "epfft_solve", "epfft_solve_batch", "epfft_mask", "epfft_iterate", "epfft_project", "epfft_label",
            "epfft_time_passes", "epfft_project_static", "epfft_serve_open", "epfft_serve_close",
            "epfft_submit", "epfft_serve_step", "epfft_poll", "epfft_autotune", "epfft_set_tiling",
-           "epfft_solve_dg2", "epfft_average5"]
+           "epfft_solve_dg2", "epfft_average5", "epfft_void_plastic", "epfft_indicators"]
 
 
 class EpfftError(RuntimeError):
@@ -110,6 +110,8 @@ def lib():
         L.epfft_solve.argtypes = [vp, C.POINTER(_Problem), C.POINTER(_Path), vp, C.POINTER(_Fields)]
         L.epfft_solve_dg2.argtypes = [vp, C.POINTER(_Problem), C.POINTER(_Path), vp, C.POINTER(_Fields)]
         L.epfft_average5.argtypes = [vp, i32, i32, vp, vp]
+        L.epfft_void_plastic.argtypes = [vp, i32, i32, vp, vp, vp, vp]
+        L.epfft_indicators.argtypes = [i32, vp, vp, i32, i32, vp]
         L.epfft_solve_batch.argtypes = [vp, i32, C.POINTER(_Problem), C.POINTER(_Path), C.POINTER(vp),
                                         C.POINTER(_Fields)]
         L.epfft_mask.argtypes = [i32, dbl, C.c_uint64, vp, vp]
@@ -313,6 +315,34 @@ def epfft_solve_dg2(ctx: Context, problem: Problem, path, fields: bool = False):
                                C.byref(cf) if cf is not None else None)
     _check(rc, "epfft_solve_dg2", (EPFFT_OK, EPFFT_NOT_CONVERGED))
     return (rc, rec, f) if fields else (rc, rec)
+
+
+def epfft_void_plastic(ctx: Context, mask, plastic, labels: bool = False):
+    """Sec. 3 void-plastic clusters.  mask: (L, L) uint8, plastic: (L, L) or
+    (n, L, L) uint8, numpy or CUDA tensors.  Returns stats (n, 6) int32
+    [, labels (n, L, L) int32 CUDA tensor]."""
+    import torch
+    m = torch.as_tensor(mask, dtype=torch.uint8).to("cuda").contiguous()
+    p = torch.as_tensor(plastic, dtype=torch.uint8).to("cuda").contiguous()
+    L = m.shape[-1]
+    n = p.numel() // (L * L)
+    lab = torch.empty((n, L, L), dtype=torch.int32, device="cuda") if labels else None
+    st = np.zeros((n, 6), dtype=np.int32)
+    torch.cuda.current_stream().synchronize()
+    _check(lib().epfft_void_plastic(ctx.handle, L, n, m.data_ptr(), p.data_ptr(),
+                                    lab.data_ptr() if labels else None, st.ctypes.data), "epfft_void_plastic")
+    return (st, lab) if labels else st
+
+
+def epfft_indicators(records, stats, L: int, load: str) -> np.ndarray:
+    """Sec. 3 indicators per increment, (n_inc, 8): eps0, sigma0, f_p, v_max,
+    i, n, r, -d2 sigma0 / d eps0^2 (computed by the library)."""
+    rec = np.ascontiguousarray(records, dtype=RECORD_DTYPE)
+    st = np.ascontiguousarray(stats, dtype=np.int32)
+    out = np.zeros((len(rec), 8))
+    _check(lib().epfft_indicators(len(rec), rec.ctypes.data, st.ctypes.data, L,
+                                  {"equibiaxial": 0, "shear": 1}[load], out.ctypes.data), "epfft_indicators")
+    return out
 
 
 def epfft_average5(ctx: Context, L: int, precision: str, eps_in, eps_out):

@@ -1069,6 +1069,92 @@ int epfft_solve_dg2(epfft_ctx* ctx, const epfft_problem* problem, const epfft_pa
   return status;
 }
 
+int epfft_void_plastic(epfft_ctx* ctx, int32_t L, int32_t n_img, const uint8_t* mask_dev, const uint8_t* plastic_dev,
+                       int32_t* labels_dev, int32_t* stats) {
+  if (!ctx || !is_pow2(L) || L < 2 || L > 4096 || n_img < 1 || !mask_dev || !plastic_dev || !stats)
+    return EPFFT_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return EPFFT_ERR_CUDA;
+  const size_t LL = (size_t)L * L;
+  Arena A(ctx);
+  uint8_t* vp = (uint8_t*)A.get(LL);
+  int32_t* lab = (int32_t*)A.get(sizeof(int32_t) * LL);
+  int32_t* out = labels_dev ? nullptr : (int32_t*)A.get(sizeof(int32_t) * LL);
+  void* scratch = A.get(22 * LL);
+  int32_t* dcnt = (int32_t*)A.get(8 * sizeof(int32_t));
+  if (!vp || !lab || (!labels_dev && !out) || !scratch || !dcnt) return EPFFT_ERR_OOM;
+  // the voids alone: their clusters and pixels (once)
+  CK(cudaMemsetAsync(dcnt, 0, 8 * sizeof(int32_t), ctx->stream));
+  CK(launch_label(mask_dev, lab, 1, L, 1, dcnt + 3, dcnt + 7, ctx->stream));
+  CK(launch_count(mask_dev, (int64_t)LL, dcnt + 5, ctx->stream));
+  int32_t hv[8];
+  CK(cudaMemcpyAsync(hv, dcnt, sizeof(hv), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (hv[7]) return EPFFT_ERR_DEVICE_TIMEOUT;
+  for (int k = 0; k < n_img; k++) {
+    const uint8_t* pl = plastic_dev + (size_t)k * LL;
+    int32_t* o = labels_dev ? labels_dev + (size_t)k * LL : out;
+    CK(cudaMemsetAsync(dcnt, 0, 8 * sizeof(int32_t), ctx->stream));
+    CK(launch_vp_flags(mask_dev, pl, vp, L, ctx->stream));
+    CK(launch_label(vp, lab, 1, L, 1, dcnt + 6, dcnt + 7, ctx->stream));
+    CK(launch_vp_attach(mask_dev, vp, lab, o, L, scratch, dcnt, hv[5] > 0, ctx->stream));
+    CK(launch_count(pl, (int64_t)LL, dcnt + 4, ctx->stream));
+    int32_t h[8];
+    CK(cudaMemcpyAsync(h, dcnt, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (h[7]) return EPFFT_ERR_DEVICE_TIMEOUT;
+    int32_t* st = stats + 6 * (size_t)k;
+    st[0] = h[0];
+    st[1] = h[1];
+    st[2] = h[2];
+    st[3] = hv[3];
+    st[4] = h[4];
+    st[5] = hv[5];
+  }
+  return EPFFT_OK;
+}
+
+int epfft_indicators(int32_t n_inc, const epfft_record* records, const int32_t* stats, int32_t L, int32_t load,
+                     double* out) {
+  if (n_inc < 1 || !records || !stats || !out || L < 1 || (load != 0 && load != 1)) return EPFFT_ERR_ARG;
+  std::vector<double> e0(n_inc), s0(n_inc), nn(n_inc);
+  const double npx = (double)L * (double)L;
+  for (int k = 0; k < n_inc; k++) {
+    const epfft_record& r = records[k];
+    const int32_t* st = stats + 6 * (size_t)k;
+    e0[k] = load == 0 ? 0.5 * (r.eps_mean[0] + r.eps_mean[1]) : r.eps_mean[3];
+    s0[k] = load == 0 ? 0.5 * (r.sig_mean[0] + r.sig_mean[1]) : r.sig_mean[3];
+    nn[k] = (double)st[0] / (double)st[3];
+    double* o = out + 8 * (size_t)k;
+    o[0] = e0[k];
+    o[1] = s0[k];
+    o[2] = (double)st[4] / (npx - (double)st[5]);
+    o[3] = (double)st[1] / npx;
+    o[4] = (double)st[2] / (double)st[3];
+    o[5] = nn[k];
+  }
+  // first derivative on the (possibly uneven) grid: second order inside,
+  // first order one-sided at the ends
+  auto grad = [&](const std::vector<double>& f, std::vector<double>& g) {
+    g.assign(n_inc, 0.0);
+    if (n_inc < 2) return;
+    g[0] = (f[1] - f[0]) / (e0[1] - e0[0]);
+    g[n_inc - 1] = (f[n_inc - 1] - f[n_inc - 2]) / (e0[n_inc - 1] - e0[n_inc - 2]);
+    for (int k = 1; k + 1 < n_inc; k++) {
+      const double h0 = e0[k] - e0[k - 1], h1 = e0[k + 1] - e0[k];
+      g[k] = (h0 * h0 * f[k + 1] - h1 * h1 * f[k - 1] + (h1 * h1 - h0 * h0) * f[k]) / (h0 * h1 * (h0 + h1));
+    }
+  };
+  std::vector<double> r, ds, dds;
+  grad(nn, r);
+  grad(s0, ds);
+  grad(ds, dds);
+  for (int k = 0; k < n_inc; k++) {
+    out[8 * (size_t)k + 6] = r[k];
+    out[8 * (size_t)k + 7] = -dds[k];
+  }
+  return EPFFT_OK;
+}
+
 int epfft_average5(epfft_ctx* ctx, int32_t L, int32_t precision, const void* eps_in_dev, void* eps_out_dev) {
   if (!ctx || !eps_in_dev || !eps_out_dev || eps_in_dev == eps_out_dev) return EPFFT_ERR_ARG;
   if (!is_pow2(L) || L < 4 || (precision != EPFFT_FP32 && precision != EPFFT_FP64)) return EPFFT_ERR_ARG;

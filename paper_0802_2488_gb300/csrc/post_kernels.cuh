@@ -23,4 +23,16 @@ cudaError_t launch_plastic_flags(const T* eps, const uint8_t* mask, uint8_t* fla
 // CG2: out(x) = (in(x) + in of the four nearest neighbours) / 5, periodic.
 template <typename T>
 cudaError_t launch_avg5(const T* in, T* out, int L, cudaStream_t s);
+// Sec. 3 void-plastic clusters of one L x L image (all device buffers):
+// vp = mask | plastic, then, given lab = the clusters of vp (launch_label),
+// every cluster without a void joins the cluster of its nearest void pixel
+// (periodic Euclidean distance, ties to the smaller linear index) and
+// `out` receives the final labels (smallest linear index, -1 off the
+// phase).  stats_dev[0..2]: final clusters, pixels of the largest, clusters
+// without a plastic pixel.  scratch: 18 bytes per pixel.
+cudaError_t launch_vp_flags(const uint8_t* mask, const uint8_t* plastic, uint8_t* vp, int L, cudaStream_t s);
+cudaError_t launch_vp_attach(const uint8_t* mask, const uint8_t* vp, const int32_t* lab, int32_t* out, int L,
+                             void* scratch, int32_t* stats_dev, int has_voids, cudaStream_t s);
+// *count_dev += number of nonzero bytes of a[0 .. n)
+cudaError_t launch_count(const uint8_t* a, int64_t n, int32_t* count_dev, cudaStream_t s);
 }  // namespace epfft
