@@ -230,6 +230,34 @@ int epfft_void_plastic(epfft_ctx *ctx, int32_t L, int32_t n_img, const uint8_t *
 int epfft_indicators(int32_t n_inc, const epfft_record *records, const int32_t *stats, int32_t L, int32_t load,
                      double *out);
 
+/* Effective in-plane moduli of the lattice of `problem` (mask or f/seed,
+ * matrix and reference moduli; its yield stress and green are replaced by
+ * an elastic matrix and kept, respectively), used by Eqs. 5-6:
+ * *K_eff = <sigma_m> / <eps_m> under equibiaxial strain (E11 = E22 =
+ * strain) and *mu_eff = <sigma_12> / (2 <eps_12>) under shear (E12 =
+ * strain), sigma_m and eps_m the in-plane means (11 + 22) / 2; the
+ * void-free matrix gives 2 (lambda + mu) and mu.  One batch of two
+ * one-increment solves.  Return codes as epfft_solve. */
+int epfft_effective_moduli(epfft_ctx *ctx, const epfft_problem *problem, double strain, double *K_eff,
+                           double *mu_eff);
+
+/* Eqs. 5 (load 0, pressure) and 6 (load 1, shear): the stress-strain curve
+ * rebuilt from the indicators `ind` (n_inc x 8, epfft_indicators) and the
+ * counts `stats` (n_inc x 6, epfft_void_plastic) with the modulus K~ (Eq. 5)
+ * or mu~ (Eq. 6); the fitting number *alpha minimises the squared
+ * difference to sigma0, fit (n_inc) receives the curve.  n_inf is n at the
+ * last increment; v_p is the void-plastic volume fraction (voids and
+ * plastic pixels), v_p^max that of the largest cluster; the integrals are
+ * trapezoids from eps0 = 0 with the integrand there equal to its value at
+ * the first increment.  Host arithmetic. */
+int epfft_empirical_curve(int32_t n_inc, const double *ind, const int32_t *stats, int32_t L, double modulus,
+                          int32_t load, double *alpha, double *fit);
+
+/* Equivalent strain of Fig. 1, out(x) = [(2/3) e'_ij e'_ij]^(1/2) with e'
+ * the 3D deviator of eps (11, 22, 33, 12; e'_12 counted twice).  Device
+ * pointers: eps L*L*4 reals, out L*L reals of `precision`.  Blocking. */
+int epfft_eps_eq(epfft_ctx *ctx, int32_t L, int32_t precision, const void *eps_dev, void *out_dev);
+
 /* CG2 post-processing (Sec. 2): eps_out(x) = mean of eps_in at x and its
  * four nearest neighbours (periodic), per component.  Device pointers,
  * L*L*4 reals of `precision` each, distinct buffers; blocking on the

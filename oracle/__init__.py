@@ -411,3 +411,64 @@ def solve_dg2(mask_: np.ndarray, mat: Material, path: np.ndarray, tol_eq=1e-8, t
         rec[f] = np.max([s.records[f] for s in sols], axis=0)
     rec["iterations"] = np.sum([s.records["iterations"] for s in sols], axis=0)
     return DG2Solution(sols, rec, np.mean(fields, axis=0))
+
+
+# --------------------------------------------------------------------------
+# Sec. 3: effective moduli, the empirical stress-strain formulas (Eqs. 5-6)
+# and the equivalent strain of Fig. 1
+# --------------------------------------------------------------------------
+
+def effective_moduli(mask_: np.ndarray, mat: Material, strain: float = 1e-3, tol=1e-10, max_iter=20000):
+    """Effective in-plane moduli of the porous lattice with the elastic matrix
+    (Y = inf): K~ = <sigma_m> / <eps_m> under equibiaxial strain and
+    mu~ = <sigma_12> / (2 <eps_12>) under shear, with sigma_m, eps_m the
+    in-plane means (11 + 22) / 2 (the slopes of sigma0(eps0) in Eqs. 5-6 at
+    small strain; the void-free matrix gives 2 (lambda + mu) and mu)."""
+    el = Material(mat.lambda_, mat.mu, np.inf, mat.lambda0, mat.mu0, mat.green, 0)
+    a = solve(mask_, el, np.array([[strain, strain, 0.0, 0.0]]), tol, tol, max_iter)
+    b = solve(mask_, el, np.array([[0.0, 0.0, 0.0, strain]]), tol, tol, max_iter)
+    K = (a.records["sig_mean"][0, 0] + a.records["sig_mean"][0, 1]) / (
+        a.records["eps_mean"][0, 0] + a.records["eps_mean"][0, 1])
+    mu = b.records["sig_mean"][0, 3] / (2.0 * b.records["eps_mean"][0, 3])
+    return float(K), float(mu)
+
+
+def empirical_curve(ind: np.ndarray, stats: np.ndarray, L: int, modulus: float, load: str):
+    """Eqs. 5 (pressure) and 6 (shear): the stress-strain curve rebuilt from
+    the geometric indicators, with the fitting number alpha chosen by least
+    squares against the computed sigma0.  Returns (alpha, sigma0_fit).
+      Eq. 5: sigma0 ~ K~ int_0^eps0 {(n - n_inf)/(1 - n_inf) + alpha (v_p - v_p^max)};
+      Eq. 6: sigma0 ~ alpha f_p + 2 mu~ int_0^eps0 (n - n_inf)/(1 - n_inf).
+    Readings: n_inf is n at the last increment; v_p is the volume fraction
+    of the void-plastic phase (voids and plastic pixels) and v_p^max that of
+    its largest cluster, v_max; the integrals are trapezoidal on the
+    increments' eps0 with the integrand at eps0 = 0 equal to its value at the
+    first increment (elastic: no plastic pixel yet)."""
+    e0, s0, fp, vmax, n = ind[:, 0], ind[:, 1], ind[:, 2], ind[:, 3], ind[:, 5]
+    st = np.asarray(stats, dtype=np.float64)
+    vp = (st[:, 4] + st[:, 5]) / float(L * L)
+    ninf = n[-1]
+    g1 = (n - ninf) / (1.0 - ninf) if ninf != 1.0 else np.zeros_like(n)
+
+    def cumint(g):
+        x = np.concatenate([[0.0], e0])
+        y = np.concatenate([[g[0]], g])
+        return np.concatenate([[0.0], np.cumsum(0.5 * (y[1:] + y[:-1]) * np.diff(x))])[1:]
+
+    I1 = cumint(g1)
+    if load == "equibiaxial":
+        A, Bv = modulus * I1, modulus * cumint(vp - vmax)
+    else:
+        A, Bv = 2.0 * modulus * I1, fp
+    den = float(np.dot(Bv, Bv))
+    alpha = float(np.dot(s0 - A, Bv) / den) if den > 0 else 0.0
+    return alpha, A + alpha * Bv
+
+
+def eps_eq(eps: np.ndarray) -> np.ndarray:
+    """Equivalent strain of Fig. 1: [(2/3) e'_ij e'_ij]^(1/2), e' the 3D
+    deviator of (11, 22, 33, 12), e'_12 counted twice."""
+    e = np.asarray(eps, dtype=np.float64)
+    m = (e[..., 0] + e[..., 1] + e[..., 2]) / 3.0
+    d = (e[..., 0] - m) ** 2 + (e[..., 1] - m) ** 2 + (e[..., 2] - m) ** 2 + 2.0 * e[..., 3] ** 2
+    return np.sqrt(2.0 / 3.0 * d)

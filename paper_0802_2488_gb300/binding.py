@@ -40,7 +40,8 @@ SYMBOLS = ["epfft_create", "epfft_destroy", "epfft_last_stats", "epfft_strerror"
            "epfft_solve", "epfft_solve_batch", "epfft_mask", "epfft_iterate", "epfft_project", "epfft_label",
            "epfft_time_passes", "epfft_project_static", "epfft_serve_open", "epfft_serve_close",
            "epfft_submit", "epfft_serve_step", "epfft_poll", "epfft_autotune", "epfft_set_tiling",
-           "epfft_solve_dg2", "epfft_average5", "epfft_void_plastic", "epfft_indicators"]
+           "epfft_solve_dg2", "epfft_average5", "epfft_void_plastic", "epfft_indicators",
+           "epfft_effective_moduli", "epfft_empirical_curve", "epfft_eps_eq"]
 
 
 class EpfftError(RuntimeError):
@@ -112,6 +113,10 @@ def lib():
         L.epfft_average5.argtypes = [vp, i32, i32, vp, vp]
         L.epfft_void_plastic.argtypes = [vp, i32, i32, vp, vp, vp, vp]
         L.epfft_indicators.argtypes = [i32, vp, vp, i32, i32, vp]
+        L.epfft_effective_moduli.argtypes = [vp, C.POINTER(_Problem), C.c_double, C.POINTER(C.c_double),
+                                             C.POINTER(C.c_double)]
+        L.epfft_empirical_curve.argtypes = [i32, vp, vp, i32, C.c_double, i32, C.POINTER(C.c_double), vp]
+        L.epfft_eps_eq.argtypes = [vp, i32, i32, vp, vp]
         L.epfft_solve_batch.argtypes = [vp, i32, C.POINTER(_Problem), C.POINTER(_Path), C.POINTER(vp),
                                         C.POINTER(_Fields)]
         L.epfft_mask.argtypes = [i32, dbl, C.c_uint64, vp, vp]
@@ -342,6 +347,37 @@ def epfft_indicators(records, stats, L: int, load: str) -> np.ndarray:
     out = np.zeros((len(rec), 8))
     _check(lib().epfft_indicators(len(rec), rec.ctypes.data, st.ctypes.data, L,
                                   {"equibiaxial": 0, "shear": 1}[load], out.ctypes.data), "epfft_indicators")
+    return out
+
+
+def epfft_effective_moduli(ctx: Context, problem: Problem, strain: float = 1e-3):
+    """(K~, mu~) of the lattice with the elastic matrix (Eqs. 5-6)."""
+    p, keep = problem._c()
+    K, mu = C.c_double(), C.c_double()
+    rc = lib().epfft_effective_moduli(ctx.handle, C.byref(p), float(strain), C.byref(K), C.byref(mu))
+    _check(rc, "epfft_effective_moduli", (EPFFT_OK, EPFFT_NOT_CONVERGED))
+    return K.value, mu.value
+
+
+def epfft_empirical_curve(ind, stats, L: int, modulus: float, load: str):
+    """Eqs. 5-6: (alpha, fitted sigma0 per increment)."""
+    a = np.ascontiguousarray(ind, dtype=np.float64)
+    st = np.ascontiguousarray(stats, dtype=np.int32)
+    fit = np.zeros(len(a))
+    alpha = C.c_double()
+    _check(lib().epfft_empirical_curve(len(a), a.ctypes.data, st.ctypes.data, L, float(modulus),
+                                       {"equibiaxial": 0, "shear": 1}[load], C.byref(alpha), fit.ctypes.data),
+           "epfft_empirical_curve")
+    return alpha.value, fit
+
+
+def epfft_eps_eq(ctx: Context, L: int, precision: str, eps):
+    """Equivalent strain field (Fig. 1) of a CUDA strain tensor (L, L, 4)."""
+    import torch
+    assert eps.is_cuda and eps.is_contiguous() and eps.numel() == 4 * L * L
+    out = torch.empty((L, L), dtype=eps.dtype, device=eps.device)
+    _check(lib().epfft_eps_eq(ctx.handle, L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision],
+                              eps.data_ptr(), out.data_ptr()), "epfft_eps_eq")
     return out
 
 

@@ -1155,6 +1155,82 @@ int epfft_indicators(int32_t n_inc, const epfft_record* records, const int32_t* 
   return EPFFT_OK;
 }
 
+int epfft_effective_moduli(epfft_ctx* ctx, const epfft_problem* problem, double strain, double* K_eff,
+                           double* mu_eff) {
+  if (!ctx || !problem || !K_eff || !mu_eff || !(std::fabs(strain) > 0.0) || !std::isfinite(strain))
+    return EPFFT_ERR_ARG;
+  // the same lattice with the elastic matrix, under equibiaxial strain and
+  // under shear, as one batch of two one-increment solves
+  epfft_problem p[2] = {*problem, *problem};
+  for (auto& q : p) q.yield_stress = INFINITY;
+  const double Ea[4] = {strain, strain, 0.0, 0.0}, Eb[4] = {0.0, 0.0, 0.0, strain};
+  const epfft_path paths[2] = {{1, 0, Ea}, {1, 0, Eb}};
+  epfft_record ra, rb;
+  epfft_record* recs[2] = {&ra, &rb};
+  const int rc = solve_impl(ctx, 2, p, paths, recs, nullptr, nullptr, nullptr, nullptr);
+  if (rc != EPFFT_OK && rc != EPFFT_NOT_CONVERGED) return rc;
+  *K_eff = (ra.sig_mean[0] + ra.sig_mean[1]) / (ra.eps_mean[0] + ra.eps_mean[1]);
+  *mu_eff = rb.sig_mean[3] / (2.0 * rb.eps_mean[3]);
+  return rc;
+}
+
+int epfft_empirical_curve(int32_t n_inc, const double* ind, const int32_t* stats, int32_t L, double modulus,
+                          int32_t load, double* alpha, double* fit) {
+  if (n_inc < 1 || !ind || !stats || !alpha || !fit || L < 1 || (load != 0 && load != 1)) return EPFFT_ERR_ARG;
+  const double npx = (double)L * (double)L;
+  const double ninf = ind[8 * (size_t)(n_inc - 1) + 5];
+  std::vector<double> g1(n_inc), g2(n_inc), I1(n_inc), I2(n_inc);
+  for (int k = 0; k < n_inc; k++) {
+    const double* r = ind + 8 * (size_t)k;
+    const int32_t* st = stats + 6 * (size_t)k;
+    g1[k] = ninf != 1.0 ? (r[5] - ninf) / (1.0 - ninf) : 0.0;
+    g2[k] = ((double)st[4] + (double)st[5]) / npx - r[3];  // v_p - v_p^max
+  }
+  // trapezoids from eps0 = 0, where the integrand is taken at the first increment
+  auto cumint = [&](const std::vector<double>& g, std::vector<double>& I) {
+    double acc = 0.0, x0 = 0.0, y0 = g[0];
+    for (int k = 0; k < n_inc; k++) {
+      const double x = ind[8 * (size_t)k];
+      acc += 0.5 * (y0 + g[k]) * (x - x0);
+      I[k] = acc;
+      x0 = x;
+      y0 = g[k];
+    }
+  };
+  cumint(g1, I1);
+  std::vector<double> A(n_inc), Bv(n_inc);
+  if (load == 0) {
+    cumint(g2, I2);
+    for (int k = 0; k < n_inc; k++) {
+      A[k] = modulus * I1[k];
+      Bv[k] = modulus * I2[k];
+    }
+  } else {
+    for (int k = 0; k < n_inc; k++) {
+      A[k] = 2.0 * modulus * I1[k];
+      Bv[k] = ind[8 * (size_t)k + 2];  // f_p
+    }
+  }
+  double num = 0.0, den = 0.0;
+  for (int k = 0; k < n_inc; k++) {
+    num += (ind[8 * (size_t)k + 1] - A[k]) * Bv[k];
+    den += Bv[k] * Bv[k];
+  }
+  *alpha = den > 0.0 ? num / den : 0.0;
+  for (int k = 0; k < n_inc; k++) fit[k] = A[k] + *alpha * Bv[k];
+  return EPFFT_OK;
+}
+
+int epfft_eps_eq(epfft_ctx* ctx, int32_t L, int32_t precision, const void* eps_dev, void* out_dev) {
+  if (!ctx || !eps_dev || !out_dev || !is_pow2(L) || (precision != EPFFT_FP32 && precision != EPFFT_FP64))
+    return EPFFT_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return EPFFT_ERR_CUDA;
+  if (precision == EPFFT_FP32) CK(launch_eps_eq<float>((const float*)eps_dev, (float*)out_dev, L, ctx->stream));
+  else CK(launch_eps_eq<double>((const double*)eps_dev, (double*)out_dev, L, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return EPFFT_OK;
+}
+
 int epfft_average5(epfft_ctx* ctx, int32_t L, int32_t precision, const void* eps_in_dev, void* eps_out_dev) {
   if (!ctx || !eps_in_dev || !eps_out_dev || eps_in_dev == eps_out_dev) return EPFFT_ERR_ARG;
   if (!is_pow2(L) || L < 4 || (precision != EPFFT_FP32 && precision != EPFFT_FP64)) return EPFFT_ERR_ARG;

@@ -166,6 +166,16 @@ __global__ void vp_relabel_kernel(const uint8_t* __restrict__ mask, const uint8_
   }
 }
 
+template <typename T>
+__global__ void eps_eq_kernel(const T* __restrict__ eps, T* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T* e = eps + 4 * i;
+    const T m = (e[0] + e[1] + e[2]) / T(3);
+    const T a = e[0] - m, b = e[1] - m, c = e[2] - m;
+    out[i] = sqrt(T(2) / T(3) * (a * a + b * b + c * c + T(2) * e[3] * e[3]));
+  }
+}
+
 __global__ void count_kernel(const uint8_t* __restrict__ a, int64_t n, int32_t* __restrict__ out) {
   int32_t c = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -253,6 +263,15 @@ template cudaError_t launch_plastic_flags<float>(const float*, const uint8_t*, u
                                                  cudaStream_t);
 template cudaError_t launch_plastic_flags<double>(const double*, const uint8_t*, uint8_t*, int, double, double,
                                                   cudaStream_t);
+template <typename T>
+cudaError_t launch_eps_eq(const T* eps, T* out, int L, cudaStream_t s) {
+  const int64_t n = (int64_t)L * L;
+  eps_eq_kernel<T><<<grid_of(n), 256, 0, s>>>(eps, out, n);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_eps_eq<float>(const float*, float*, int, cudaStream_t);
+template cudaError_t launch_eps_eq<double>(const double*, double*, int, cudaStream_t);
 template cudaError_t launch_avg5<float>(const float*, float*, int, cudaStream_t);
 template cudaError_t launch_avg5<double>(const double*, double*, int, cudaStream_t);
 

@@ -33,6 +33,10 @@ cudaError_t launch_avg5(const T* in, T* out, int L, cudaStream_t s);
 cudaError_t launch_vp_flags(const uint8_t* mask, const uint8_t* plastic, uint8_t* vp, int L, cudaStream_t s);
 cudaError_t launch_vp_attach(const uint8_t* mask, const uint8_t* vp, const int32_t* lab, int32_t* out, int L,
                              void* scratch, int32_t* stats_dev, int has_voids, cudaStream_t s);
+// out(x) = [(2/3) e'_ij e'_ij]^(1/2) of a strain field (Fig. 1), e' the 3D
+// deviator of (11, 22, 33, 12), e'_12 counted twice.
+template <typename T>
+cudaError_t launch_eps_eq(const T* eps, T* out, int L, cudaStream_t s);
 // *count_dev += number of nonzero bytes of a[0 .. n)
 cudaError_t launch_count(const uint8_t* a, int64_t n, int32_t* count_dev, cudaStream_t s);
 }  // namespace epfft

@@ -28,3 +28,22 @@ def test_indicators_match_oracle(B, load, k):
     got = B.epfft_indicators(rec, st, L, load)
     ref = O.indicators(rec, st, L, load)
     np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("load", ["equibiaxial", "shear"])
+def test_empirical_curve_matches_oracle(B, load):
+    rng = np.random.default_rng(11)
+    k = 15
+    ind = np.zeros((k, 8))
+    ind[:, 0] = np.cumsum(rng.uniform(0.03, 0.09, k))
+    ind[:, 1] = np.sqrt(ind[:, 0]) + rng.normal(0, 0.01, k)
+    ind[:, 2] = np.linspace(0, 0.5, k)
+    ind[:, 3] = np.linspace(0.02, 0.3, k)
+    ind[:, 5] = np.concatenate([[1, 1, 1], np.linspace(0.95, 0.2, k - 3)])
+    st = np.zeros((k, 6), np.int32)
+    st[:, 4] = rng.integers(0, 300, k)
+    st[:, 5] = 64
+    a, f = B.epfft_empirical_curve(ind, st, 24, 2.2, load)
+    ra, rf = O.empirical_curve(ind, st, 24, 2.2, load)
+    assert abs(a - ra) < 1e-12 * max(1.0, abs(ra))
+    np.testing.assert_allclose(f, rf, rtol=1e-12, atol=1e-12)
