@@ -293,17 +293,27 @@ __device__ __forceinline__ void block_reduce(double v[N_ACC], double* out) {
 }
 
 // CTA sums of the per-thread accumulators.  FP64: shuffles in FP64.  FP32:
-// each warp adds its 32 values as FP32 (hi, lo) pairs with the error-free
-// TwoSum of Knuth/Moller (s = a + b, e = exact rounding error of the add), so
-// the warp total carries about twice FP32 precision without FP64 work; each
-// warp's total is then promoted to FP64 and the warps are added in FP64.
+// values are added as FP32 (hi, lo) pairs with the error-free TwoSum of
+// Knuth/Moller (s = a + b, e = exact rounding error of the add), first
+// within each warp, then across the warps by warp 0, so the CTA total
+// carries about twice FP32 precision without FP64 work; thread 0 promotes
+// the final pairs to FP64 (hi + lo).  The FP64 pipe of GB300 is narrow, so
+// per-warp FP64 work here would cost more than the rest of the reduction.
 template <int NT>
 __device__ __forceinline__ void block_reduce_acc(double acc[N_ACC], double* out) {
   block_reduce<NT>(acc, out);
 }
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float bh, float bl) {
+  const float sum = hi + bh;
+  const float bb = sum - hi;
+  const float err = (hi - (sum - bb)) + (bh - bb);
+  hi = sum;
+  lo = lo + bl + err;
+}
 template <int NT>
 __device__ __forceinline__ void block_reduce_acc(float acc[N_ACC], double* out) {
-  __shared__ double red2[NT / 32][N_ACC];
+  constexpr int NW = NT / 32;
+  __shared__ float red2[NW][N_ACC][2];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < N_ACC; i++) {
@@ -312,22 +322,25 @@ __device__ __forceinline__ void block_reduce_acc(float acc[N_ACC], double* out) 
     for (int o = 16; o > 0; o >>= 1) {
       const float bh = __shfl_down_sync(0xffffffffu, hi, o);
       const float bl = __shfl_down_sync(0xffffffffu, lo, o);
-      const float sum = hi + bh;
-      const float bb = sum - hi;
-      const float err = (hi - (sum - bb)) + (bh - bb);
-      hi = sum;
-      lo = lo + bl + err;
+      two_sum_add(hi, lo, bh, bl);
     }
-    if (lane == 0) red2[wid][i] = (double)hi + (double)lo;
+    if (lane == 0) {
+      red2[wid][i][0] = hi;
+      red2[wid][i][1] = lo;
+    }
   }
   __syncthreads();
   if (wid == 0) {
 #pragma unroll
     for (int i = 0; i < N_ACC; i++) {
-      double x = lane < NT / 32 ? red2[lane][i] : 0.0;
+      float hi = lane < NW ? red2[lane][i][0] : 0.0f, lo = lane < NW ? red2[lane][i][1] : 0.0f;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-      if (lane == 0) out[i] = x;
+      for (int o = 16; o > 0; o >>= 1) {
+        const float bh = __shfl_down_sync(0xffffffffu, hi, o);
+        const float bl = __shfl_down_sync(0xffffffffu, lo, o);
+        two_sum_add(hi, lo, bh, bl);
+      }
+      if (lane == 0) out[i] = (double)hi + (double)lo;
     }
   }
 }
@@ -596,18 +609,16 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
       constexpr bool XCH = sizeof(T) == 8 && L >= 32;
       constexpr int NW = NT / 32;
       __shared__ T edge[XCH ? 2 : 1][2][XCH ? NW : 1];
-      for (int r = 0; r < RR; r++) {
-        T en[P][4];
-        bool vv[P];
-#pragma unroll
-        for (int j = 0; j < P; j++) {
-          const int x1 = xmap(j);
-          const size_t x = (size_t)(r0 + r) * L + x1;
-          const bool act = x1 < L && ECHK(x, LL, 23);
-          vv[j] = act ? mask[x] != 0 : true;
-          if (act) Vec4<T>::load(ein + 4 * x, en[j]);
-          else en[j][0] = en[j][1] = en[j][2] = en[j][3] = T(0);
-        }
+      // eps^n and voids of row r, group j
+      auto load_px = [&](int r, int j, T (&e)[4], bool& v) {
+        const int x1 = xmap(j);
+        const size_t x = (size_t)(r0 + r) * L + x1;
+        const bool act = x1 < L && ECHK(x, LL, 23);
+        v = act ? mask[x] != 0 : true;
+        if (act) Vec4<T>::load(ein + 4 * x, e);
+        else e[0] = e[1] = e[2] = e[3] = T(0);
+      };
+      auto row = [&](int r, T (&en)[P][4], bool (&vv)[P]) {
         T slast[4];  // sigma of the last group (FP64 exchange)
         if constexpr (XCH) {
           sigma(en[P - 1], vv[P - 1], m, slast);
@@ -661,6 +672,28 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
             run12 = __shfl_sync(0xffffffffu, sj[3], 31);
           }
           update(r, j, x1, en[j], vv[j], sj, l11, l12);
+        }
+      };
+      // When the rows' strains fit in 32 registers per thread, all of them
+      // are loaded before the first row is processed (their latencies
+      // overlap); otherwise row by row (P loads in flight per thread).
+      constexpr bool PRE = RR * P * 4 * (int)sizeof(T) <= 128;
+      if constexpr (PRE) {
+        T pen[RR][P][4];
+        bool pvv[RR][P];
+#pragma unroll
+        for (int r = 0; r < RR; r++)
+#pragma unroll
+          for (int j = 0; j < P; j++) load_px(r, j, pen[r][j], pvv[r][j]);
+#pragma unroll
+        for (int r = 0; r < RR; r++) row(r, pen[r], pvv[r]);
+      } else {
+        for (int r = 0; r < RR; r++) {
+          T en[P][4];
+          bool vv[P];
+#pragma unroll
+          for (int j = 0; j < P; j++) load_px(r, j, en[j], vv[j]);
+          row(r, en, vv);
         }
       }
     }

@@ -18,19 +18,20 @@ from . import binding as B
 from . import inputs
 
 
-def measure(ctx, L: int, precision: str, f: float = 0.2, iters: int = 50, variant: int | None = None) -> dict:
+def measure(ctx, L: int, precision: str, f: float = 0.2, iters: int = 50, variant: int | None = None,
+            batch: int = 1) -> dict:
     if variant is not None:
         B.epfft_set_tiling(ctx, L, precision, variant)
     prob = B.Problem(L=L, precision=precision, void_fraction=f, seed=0)
     E = inputs.load_path("shear", 40, 3.0)[20]
-    col_ms, row_ms = B.epfft_time_passes(ctx, prob, E, iters)
-    n = L * L
+    col_ms, row_ms = B.epfft_time_passes(ctx, prob, E, iters, n_batch=batch)
+    n = L * L * batch
     lg = math.log2(L)
     f64 = precision == "fp64"
     row_b, col_b = (113 if f64 else 57) * n, (48 if f64 else 24) * n
     row_f, col_f = (15 * lg + 60) * n, (15 * lg + 25) * n
     return {
-        "L": L, "precision": precision, "iters": iters, "variant": variant,
+        "L": L, "precision": precision, "iters": iters, "variant": variant, "batch": batch,
         "col_ms": col_ms, "row_ms": row_ms,
         "col_GBps": col_b / (col_ms * 1e-3) / 1e9, "row_GBps": row_b / (row_ms * 1e-3) / 1e9,
         "col_GFLOPs": col_f / (col_ms * 1e-3) / 1e9, "row_GFLOPs": row_f / (row_ms * 1e-3) / 1e9,
@@ -43,6 +44,7 @@ def main():
     ap.add_argument("--L", type=int, nargs="+", default=[256])
     ap.add_argument("--precision", nargs="+", default=["fp64", "fp32"])
     ap.add_argument("--iters", type=int, default=50)
+    ap.add_argument("--batch", type=int, default=1, help="solves per launch")
     ap.add_argument("--variants", type=int, nargs="*", default=None,
                     help="compiled tilings to time (default: the context's choice)")
     a = ap.parse_args()
@@ -53,7 +55,8 @@ def main():
             for L in a.L:
                 if B.epfft_supported(L, prec):
                     for v in (a.variants if a.variants else [None]):
-                        print(json.dumps(measure(ctx, L, prec, iters=a.iters, variant=v)), flush=True)
+                        print(json.dumps(measure(ctx, L, prec, iters=a.iters, variant=v, batch=a.batch)),
+                              flush=True)
 
 
 if __name__ == "__main__":
