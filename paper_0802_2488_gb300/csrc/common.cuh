@@ -97,6 +97,9 @@ enum MatConst : int {
   MC_INV_2MU0,    // 1 / (2 mu0)
   MC_TRIAL2,      // (mu / (mu + mu0))^2
   MC_MU0,         // mu0
+  MC_P_MAT,       // 3 (K - K0): mean part of the polarization of a matrix pixel
+  MC_P_VOID,      // -3 K0: the same for a void pixel
+  MC_GSC_EL,      // mu / (mu + mu0): 2 mu times the elastic deviator scale of the local step
   N_MC
 };
 

@@ -207,6 +207,9 @@ void fill_consts(Solve& S) {
   c[MC_INV_2MU0] = 1.0 / (2.0 * S.mu0);
   c[MC_TRIAL2] = r * r;
   c[MC_MU0] = S.mu0;
+  c[MC_P_MAT] = 3.0 * (K - K0);
+  c[MC_P_VOID] = -3.0 * K0;
+  c[MC_GSC_EL] = S.mu / (S.mu + S.mu0);
   for (int i = 0; i < N_MC; i++) S.mcf[i] = (float)c[i];
 }
 

@@ -588,16 +588,15 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
         c0_apply(e, m, c0);
 #pragma unroll
         for (int c = 0; c < 4; c++) tau[c] = sj[c] + c0[c];
-        local_solve(tau, v, m, e1);
+        T p1[3];
+        local_solve_p(tau, v, m, e1, p1);
         Vec4<T>::store(eout + 4 * x, e1);
         const T q0 = e1[0] - e[0], q1 = e1[1] - e[1], q2 = e1[2] - e[2], q3 = e1[3] - e[3];
         acc[A_COMP] += q0 * q0 + q1 * q1 + q2 * q2 + T(2) * q3 * q3;
-        T s1[4];
-        sigma(e1, v, m, s1);
-        c0_apply(e1, m, c0);
-        IO::px(sp, 0, r, x1) = s1[0] - c0[0];
-        IO::px(sp, 1, r, x1) = s1[1] - c0[1];
-        IO::px(sp, 2, r, x1) = s1[3] - c0[3];
+        // next polarization sigma(eps^{n+1}) - C0:eps^{n+1} (in-plane)
+        IO::px(sp, 0, r, x1) = p1[0];
+        IO::px(sp, 1, r, x1) = p1[1];
+        IO::px(sp, 2, r, x1) = p1[2];
       };
       // Left neighbours: the previous lane by a warp shuffle; lane 0 takes
       // lane 31 of the previous pixel group of its warp (the run is

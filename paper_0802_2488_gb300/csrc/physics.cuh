@@ -17,6 +17,8 @@ struct Mat {
   T inv_2mumu0;     // 1 / (2 (mu + mu0))
   T inv_2mu0;       // 1 / (2 mu0)
   T trial2;         // (mu / (mu + mu0))^2: |dev| of the elastic trial vs |tau'|
+  T p_mat, p_void;  // 3 (K - K0), -3 K0
+  T gsc_el;         // mu / (mu + mu0)
 };
 
 template <typename T>
@@ -42,6 +44,9 @@ __device__ __forceinline__ Mat<T> make_mat(const Solve& S) {
   m.inv_2mumu0 = c[MC_INV_2MUMU0];
   m.inv_2mu0 = c[MC_INV_2MU0];
   m.trial2 = c[MC_TRIAL2];
+  m.p_mat = c[MC_P_MAT];
+  m.p_void = c[MC_P_VOID];
+  m.gsc_el = c[MC_GSC_EL];
   return m;
 }
 
@@ -150,6 +155,52 @@ __device__ __forceinline__ bool local_solve(const T t[4], bool is_void, const Ma
   e[1] = d1 * sc + em;
   e[2] = d2 * sc + em;
   e[3] = d3 * sc;
+  return pl;
+}
+
+// The local step (local_solve) together with the next polarization
+// p = sigma(eps) - C0:eps of its solution, from the step's own quantities:
+// with tau' the deviator of tau, eps = sc tau' + em I and
+//   sigma(eps) = 3 K em I + gsc tau',   gsc = 2 mu sc (elastic),
+//                                       sqrt(2/3) Y / |tau'| (plastic), 0 (void),
+// so p = (3 K - 3 K0) em I + (gsc - 2 mu0 sc) tau' (K = 0 for a void).  This
+// is sigma of the step's solution on the branch the step chose, without a
+// second evaluation of the law.  Returns true on the plastic branch; p holds
+// the in-plane components (11, 22, 12).
+template <typename T>
+__device__ __forceinline__ bool local_solve_p(const T t[4], bool is_void, const Mat<T>& m, T e[4], T p[3]) {
+  const T tm = (t[0] + t[1] + t[2]) * T(1.0 / 3.0);
+  const T d0 = t[0] - tm, d1 = t[1] - tm, d2 = t[2] - tm, d3 = t[3];
+  T em, sc, gsc, pa;
+  bool pl = false;
+  if (is_void) {
+    em = tm * m.inv_3K0;
+    sc = m.inv_2mu0;
+    gsc = T(0);
+    pa = m.p_void;
+  } else {
+    em = tm * m.inv_3KK0;
+    const T nt2 = d0 * d0 + d1 * d1 + d2 * d2 + T(2) * d3 * d3;
+    pl = m.trial2 * nt2 > m.ylim2;
+    if (pl) {
+      const T ri = m.ylim * rsq(nt2);  // sqrt(2/3) Y / |tau'|
+      sc = (T(1) - ri) * m.inv_2mu0;
+      gsc = ri;
+    } else {
+      sc = m.inv_2mumu0;
+      gsc = m.gsc_el;
+    }
+    pa = m.p_mat;
+  }
+  e[0] = d0 * sc + em;
+  e[1] = d1 * sc + em;
+  e[2] = d2 * sc + em;
+  e[3] = d3 * sc;
+  const T pb = gsc - m.two_mu0 * sc;
+  const T pm = pa * em;
+  p[0] = pb * d0 + pm;
+  p[1] = pb * d1 + pm;
+  p[2] = pb * d3;
   return pl;
 }
 
