@@ -59,8 +59,7 @@ struct Cfg {
   // variant 0 (64 registers at 512 threads, no spills)
   static constexpr int MINB_ROW = !F64 && (V == 1 || L == 512) ? 2 : 1;
   static constexpr int MINB_COL = !F64 && V == 1 ? 2 : 1;
-  static constexpr int NT_ROW0 = F64 ? (V == 0 || L > 512 ? (L < 256 ? L : 256) : (L < 128 ? L : 128))
-                                     : (L <= 256 ? L : NTMAX);
+  static constexpr int NT_ROW0 = F64 ? (L > 512 ? 256 : (L < 128 ? L : 128)) : (L <= 256 ? L : NTMAX);
   static constexpr int NT_ROW = NT_ROW0 < 32 ? 32 : NT_ROW0;
   static constexpr int NT_COL0 = ((3 * W * L / RM_COL + 31) / 32) * 32;
   static constexpr int NT_COL = NT_COL0 < 32 ? 32 : (NT_COL0 > NTMAX ? NTMAX : NT_COL0);
@@ -209,9 +208,10 @@ struct RowIO {
         const int ik = pad32(k), ikk = pad32(kk);  // 0 < k, kk < M
         const C2<T> a = s[ik], b = s[ikk];
         const C2<T> wk = conj(twist_tw<T, L>(oct, k));
-        const C2<T> zk = (a + conj(b)) + mul_i(wk * (a - conj(b)));
-        s[ik] = zk;
-        if (kk != k) s[ikk] = (b + conj(a)) - mul_i(conj(wk) * (b - conj(a)));
+        // the partner's product conj(wk) (b - conj(a)) equals -conj(t)
+        const C2<T> t = wk * (a - conj(b));
+        s[ik] = (a + conj(b)) + mul_i(t);
+        if (kk != k) s[ikk] = (b + conj(a)) + mul_i(conj(t));
       }
     }
   }
@@ -231,8 +231,10 @@ struct RowIO {
         const int ik = pad32(k), ikk = pad32(kk);  // 0 < k, kk < M
         const C2<T> a = s[ik], b = s[ikk];
         const C2<T> wk = twist_tw<T, L>(oct, k);
-        s[ik] = T(0.5) * ((a + conj(b)) - mul_i(wk * (a - conj(b))));
-        if (kk != k) s[ikk] = T(0.5) * ((b + conj(a)) + mul_i(conj(wk) * (b - conj(a))));
+        // the partner's product conj(wk) (b - conj(a)) equals -conj(t)
+        const C2<T> t = wk * (a - conj(b));
+        s[ik] = T(0.5) * ((a + conj(b)) - mul_i(t));
+        if (kk != k) s[ikk] = T(0.5) * ((b + conj(a)) - mul_i(conj(t)));
       }
     }
   }

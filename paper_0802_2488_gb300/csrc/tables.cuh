@@ -25,8 +25,8 @@ namespace epfft {
 template <typename T, int L, int V>
 struct PlanSel {
   static constexpr bool F64 = sizeof(T) == 8;
-  static constexpr int RM_ROW = F64 ? (V == 0 ? 16 : (L <= 512 ? 4 : 8)) : 16;
-  static constexpr int RM_COL = F64 ? (V == 0 ? 16 : (L <= 512 ? 4 : 8)) : 16;
+  static constexpr int RM_ROW = F64 ? (L <= 512 ? 4 : (V == 0 ? 16 : 8)) : 16;
+  static constexpr int RM_COL = F64 ? (L <= 512 ? 4 : (V == 0 ? 16 : 8)) : 16;
   static constexpr bool FULL = F64 ? true : L <= 2048;
   using PR = FftPlan<L / 2, RM_ROW, FULL>;
   using PC = FftPlan<L, RM_COL, FULL>;
