@@ -26,9 +26,12 @@ namespace epfft {
 
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
 
-// Padded layout of one sequence of length N.
+// Padded layout of one sequence of length N.  From N = 512 on, every warp
+// of a stage works inside one sequence, and the stride between sequences is
+// made odd so that accesses that step across sequences (the transposing
+// loads and stores of the passes) spread over the banks too.
 template <int N>
-__host__ __device__ constexpr int seq_stride() { return N >= 32 ? N + N / 32 : N; }
+__host__ __device__ constexpr int seq_stride() { return N >= 512 ? N + N / 32 + 1 : (N >= 32 ? N + N / 32 : N); }
 __device__ __forceinline__ int pad32(int x) { return x + (x >> 5); }
 
 // Radix plan of a length-N transform with largest radix RM (4, 8 or 16):
