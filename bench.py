@@ -252,6 +252,7 @@ def run_serving(args):
     budget = 16 << 30
     B.epfft_serve_open(ctx, budget, 16, 32)
     lat, pix = [], 0
+    launches = 0
     tickets = {}
     nxt = 0
     with ClockSampler(local) as clk:
@@ -266,6 +267,7 @@ def run_serving(args):
                 time.sleep(max(0.0, min(0.01, reqs[nxt].arrival_s - now)))
                 continue
             B.epfft_serve_step(ctx)
+            launches += B.epfft_last_stats(ctx)["kernel_launches"]
             done_t = time.perf_counter() - t0
             for i, (t, r) in list(tickets.items()):
                 res = B.epfft_poll(ctx, t, prob(r), r.problem.n_inc)
@@ -290,7 +292,7 @@ def run_serving(args):
                    "solves_per_s": len(lat) / total, "precision": args.precision, "parallelism": "single GPU",
                    "l2": "inputs of the running set exceed L2 at the larger sizes; not flushed"},
         "e2e": {"value": ws * pix / total, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "gpu_launches": None, "clocks": clocks,
+        "gpu_launches": launches, "clocks": clocks,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

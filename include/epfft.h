@@ -152,7 +152,7 @@ const char *epfft_strerror(int code);
 int epfft_supported(int32_t L, int32_t precision);
 
 /* Accounting of the last solve-type call on a context (epfft_solve,
- * epfft_solve_batch, epfft_iterate). */
+ * epfft_solve_batch, epfft_iterate, epfft_serve_step). */
 typedef struct {
   int64_t loop_steps;       /* steps of the device-side loop (one column and one *
                              * row pass each)                                     */

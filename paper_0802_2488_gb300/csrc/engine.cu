@@ -777,6 +777,7 @@ int serve_admit(epfft_ctx* c, Server& S) {
     epfft_problem p = t.prob;
     p.mask = t.mask.empty() ? nullptr : t.mask.data();
     p.mask_on_device = 0;
+    if (!p.mask) c->last.kernel_launches += 1;  // the mask kernel
     Solve hs;
     rc = init_solve(
         [&](size_t b) {
@@ -1386,6 +1387,7 @@ int epfft_serve_step(epfft_ctx* ctx, int32_t* n_running, int32_t* n_queued) {
   if (!ctx || !ctx->server) return EPFFT_ERR_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return EPFFT_ERR_CUDA;
   Server& S = *ctx->server;
+  ctx->last = epfft_stats{};
   int rc = serve_admit(ctx, S);
   if (rc) return rc;
   std::vector<ServeClass*> live;
@@ -1402,7 +1404,13 @@ int epfft_serve_step(epfft_ctx* ctx, int32_t* n_running, int32_t* n_queued) {
     CK(cudaGraphLaunch(k->exec, k->stream));
     live.push_back(k);
   }
-  for (ServeClass* k : live) CK(cudaStreamSynchronize(k->stream));
+  for (ServeClass* k : live) {
+    CK(cudaStreamSynchronize(k->stream));
+    BatchCtl bc;
+    CK(cudaMemcpy(&bc, k->B.d_ctl, sizeof(bc), cudaMemcpyDeviceToHost));
+    ctx->last.loop_steps += bc.body_iters;
+    ctx->last.kernel_launches += 2 * bc.body_iters;  // a column and a row pass per step
+  }
   {
     CheckRec cr;
     CK(read_check_all(&cr));
@@ -1413,8 +1421,12 @@ int epfft_serve_step(epfft_ctx* ctx, int32_t* n_running, int32_t* n_queued) {
     }
   }
   for (ServeClass* k : live) {
+    int64_t before = 0, after = 0;
+    for (auto& sl : k->slots) before += sl.used;
     rc = serve_harvest(ctx, S, k);
     if (rc) return rc;
+    for (auto& sl : k->slots) after += sl.used;
+    ctx->last.kernel_launches += 4 * (before - after);  // labelling of each harvested solve
   }
   int running = 0;
   for (auto& kv : S.classes)
