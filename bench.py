@@ -40,6 +40,16 @@ UNIT = "pixel-iterations/s"
 L2_FLUSH_BYTES = 512 << 20
 
 
+# DRAM bytes (read + write) per launch of the dominant pass, from one ncu
+# capture of the same kernel, tiling and solves per launch
+# (profiles/passes_dram_traffic.md); a configuration not listed reports null.
+TRAFFIC = {
+    ("row_pass<double,256>", 1, 1): 3.859e6,     # working set resident in L2
+    ("row_pass<float,512>", 0, 64): 9.056e8,
+    ("row_pass<float,4096>", 0, 1): 9.123e8,
+}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -421,6 +431,9 @@ def main():
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if os.path.exists(mp)
                     else "fallback 6800 GB/s (of fallback)"}
         roof.update({"col_pass_ms": col_ms, "row_pass_ms": row_ms})
+        roof["traffic"] = TRAFFIC.get((roof["kernel"], tiling, nb))
+        if roof["traffic"] is not None:
+            roof["traffic_source"] = "profiles/passes_dram_traffic.md (ncu dram__bytes_read.sum + write.sum per launch)"
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True,
