@@ -73,10 +73,10 @@ struct Record {
 // Accumulators of the row pass (per CTA), FP64, in this order.
 enum Acc : int {
   A_S11 = 0, A_S22, A_S33, A_S12,  // sum sigma(eps^n)
-  A_E11, A_E22, A_E33, A_E12,      // sum eps^n
+  A_E11, A_E22, A_E33, A_E12,      // sum of eps of the iterate the pass produces
   A_DIV2,                          // sum |div sigma(eps^n)|^2
   A_COMP,                          // sum (eps^{n+1} - e^{n+1}):(same)
-  A_NPL,                           // plastic pixels of eps^n (matrix)
+  A_NPL,                           // its plastic pixels (matrix)
   N_ACC
 };
 constexpr int PART_STRIDE = 12;  // doubles per CTA partial record
@@ -100,6 +100,7 @@ enum MatConst : int {
   MC_P_MAT,       // 3 (K - K0): mean part of the polarization of a matrix pixel
   MC_P_VOID,      // -3 K0: the same for a void pixel
   MC_GSC_EL,      // mu / (mu + mu0): 2 mu times the elastic deviator scale of the local step
+  MC_3K,          // 3 K
   N_MC
 };
 
@@ -118,6 +119,7 @@ struct Solve {
   uint8_t* flags;      // n_inc * L * L plastic flags (may be null)
   const uint8_t* mask; // L * L, 1 = void
   void* eps[2];        // ping-pong local strain, L*L*4 reals
+  void* sig[2];        // sigma of the same iterates (the multiplier), L*L*4 reals
   void* spec;          // 3 * L * L/2 complex, tiled column layout
   double* partials;    // n_row_ctas * PART_STRIDE
   // mutable state
@@ -127,6 +129,8 @@ struct Solve {
   double Eprev[4];
   double sig_prev[4];
   double eta3_cur;
+  double epsm_next[4];  // <eps> of the iterate the last pass produced
+  double npl_next;      // its plastic pixels
   int64_t total_iters;  // pixel-iteration accounting: passes that did work
 };
 

@@ -210,6 +210,7 @@ void fill_consts(Solve& S) {
   c[MC_P_MAT] = 3.0 * (K - K0);
   c[MC_P_VOID] = -3.0 * K0;
   c[MC_GSC_EL] = S.mu / (S.mu + S.mu0);
+  c[MC_3K] = 3.0 * K;
   for (int i = 0; i < N_MC; i++) S.mcf[i] = (float)c[i];
 }
 
@@ -243,7 +244,7 @@ int launch_body(epfft_ctx* c, Batch& B, cudaStream_t s, cudaGraphConditionalHand
 size_t solve_footprint(int L, int prec, int row_ctas, int n_inc) {
   const size_t LL = (size_t)L * L, rs = real_size(prec);
   auto r = [](size_t b) { return (b + 511) & ~(size_t)511; };
-  return r(4 * LL * rs) * 2 + r(3 * LL * rs) + r(sizeof(double) * PART_STRIDE * (size_t)row_ctas) + r(LL) +
+  return r(4 * LL * rs) * 4 + r(3 * LL * rs) + r(sizeof(double) * PART_STRIDE * (size_t)row_ctas) + r(LL) +
          r(LL * (size_t)n_inc) + r(sizeof(double) * 4 * (size_t)n_inc) + r(sizeof(Record) * (size_t)n_inc);
 }
 
@@ -268,15 +269,20 @@ int init_solve(Get&& get, const PassShape& sh, int L, int prec, const epfft_prob
   fill_consts(S);
   void* eps0d = get(4 * LL * rs);
   void* eps1d = get(4 * LL * rs);
+  void* sig0d = get(4 * LL * rs);
+  void* sig1d = get(4 * LL * rs);
   void* spec = get(3 * LL * rs);
   double* part = (double*)get(sizeof(double) * PART_STRIDE * (size_t)sh.row_ctas);
   uint8_t* mask = (uint8_t*)get(LL);
   uint8_t* flags = (uint8_t*)get(LL * (size_t)n_inc);
   double* dpath = (double*)get(sizeof(double) * 4 * (size_t)n_inc);
   Record* rec = (Record*)get(sizeof(Record) * (size_t)n_inc);
-  if (!eps0d || !eps1d || !spec || !part || !mask || !flags || !dpath || !rec) return EPFFT_ERR_OOM;
+  if (!eps0d || !eps1d || !sig0d || !sig1d || !spec || !part || !mask || !flags || !dpath || !rec)
+    return EPFFT_ERR_OOM;
   S.eps[0] = eps0d;
   S.eps[1] = eps1d;
+  S.sig[0] = sig0d;
+  S.sig[1] = sig1d;
   S.spec = spec;
   S.partials = part;
   S.mask = mask;

@@ -365,9 +365,14 @@ __device__ __forceinline__ void sum_partials(const double* partials, int n_ctas,
 // Last CTA of a solve's row pass: indicators of Sec. 2 and the state
 // machine.  Runs on one thread; A holds the sums of the partials (ITER).
 __device__ __forceinline__ void finalize_solve(Solve& S, int phase, const double* A, int L) {
+  const double inv = 1.0 / ((double)L * (double)L);
   if (phase == PH_INIT) {
     const double* E = S.path + 4 * S.inc;
-    for (int c = 0; c < 4; c++) S.Eprev[c] = E[c];
+    for (int c = 0; c < 4; c++) {
+      S.Eprev[c] = E[c];
+      S.epsm_next[c] = A[A_E11 + c] * inv;
+    }
+    S.npl_next = A[A_NPL];
     S.cur = 1 - S.cur;
     S.iter = 0;
     S.phase = PH_ITER;
@@ -377,12 +382,16 @@ __device__ __forceinline__ void finalize_solve(Solve& S, int phase, const double
     S.phase = PH_DONE;
     return;
   }
-  const double inv = 1.0 / ((double)L * (double)L);
+  // A holds sigma sums and the residual of iterate n, and the strain sums,
+  // plastic count and fixed-point residual of iterate n + 1 (the pass
+  // produced it); <eps> and the plastic count of iterate n come from the
+  // previous pass
   double sig[4], epsm[4];
   for (int c = 0; c < 4; c++) {
     sig[c] = A[A_S11 + c] * inv;
-    epsm[c] = A[A_E11 + c] * inv;
+    epsm[c] = S.epsm_next[c];
   }
+  const double npl = S.npl_next;
   const double div2 = A[A_DIV2] * inv, comp = A[A_COMP] * inv;
   const double* E = S.path + 4 * S.inc;
   double EE = E[0] * E[0] + E[1] * E[1] + E[2] * E[2] + 2.0 * E[3] * E[3];
@@ -420,7 +429,7 @@ __device__ __forceinline__ void finalize_solve(Solve& S, int phase, const double
       R.eta2 = eta2;
       R.eta3 = S.eta3_cur;
       R.iterations = n;
-      R.n_plastic = (int32_t)A[A_NPL];
+      R.n_plastic = (int32_t)npl;
       R.n_clusters = 0;
       R.status = !finite ? 2 : (conv ? 0 : 1);
       if (!finite) {
@@ -435,7 +444,11 @@ __device__ __forceinline__ void finalize_solve(Solve& S, int phase, const double
       return;
     }
   }
-  for (int c = 0; c < 4; c++) S.sig_prev[c] = sig[c];
+  for (int c = 0; c < 4; c++) {
+    S.sig_prev[c] = sig[c];
+    S.epsm_next[c] = A[A_E11 + c] * inv;
+  }
+  S.npl_next = A[A_NPL];
   S.eta3_cur = eta3_next;
   S.iter = n + 1;
   S.cur = 1 - S.cur;
@@ -494,6 +507,9 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
     const int r0 = blockIdx.x * RR;
     const T* __restrict__ ein = reinterpret_cast<const T*>(S.eps[cur]);
     T* __restrict__ eout = reinterpret_cast<T*>(S.eps[1 - cur]);
+    // sigma of eps^n (read) and of the iterate this pass produces (written)
+    const T* __restrict__ sin_ = reinterpret_cast<const T*>(S.sig[cur]);
+    T* __restrict__ sout = reinterpret_cast<T*>(S.sig[1 - cur]);
     C2<T>* spec = reinterpret_cast<C2<T>*>(S.spec);
     const uint8_t* __restrict__ mask = S.mask;
     const Mat<T> m = make_mat<T>(S);
@@ -535,7 +551,12 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
           if (fl) fl[x] = is_plastic(e, v, m);
           for (int c = 0; c < 4; c++) e[c] += dE[c];
           Vec4<T>::store(eout + 4 * x, e);
-          sigma(e, v, m, s);
+          const bool pl = sigma(e, v, m, s);
+          Vec4<T>::store(sout + 4 * x, s);
+          // <eps^0> and its plastic pixels (the stats of iterate 0)
+#pragma unroll
+          for (int c = 0; c < 4; c++) acc[A_E11 + c] += e[c];
+          acc[A_NPL] += pl ? T(1) : T(0);
           c0_apply(e, m, c0);
           IO::px(sp, 0, r, x1) = s[0] - c0[0];
           IO::px(sp, 1, r, x1) = s[1] - c0[1];
@@ -549,8 +570,8 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
       IO::c2r_twist(sp, IO::octant(stw));
       __syncthreads();
       IO::template fft<true>(sp, stw);
-      // halo row x2 = r0 - 1: sigma12 and sigma22 of eps^n for the backward
-      // difference along x2
+      // halo row x2 = r0 - 1: sigma12 and sigma22 of iterate n for the
+      // backward difference along x2
       T prev12[P], prev22[P];
       {
         const int xh = (r0 + L - 1) & (L - 1);
@@ -561,16 +582,16 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
           if (x1 >= L) continue;
           const size_t x = (size_t)xh * L + x1;
           if (!ECHK(x, LL, 22)) continue;
-          T e[4], s[4];
-          Vec4<T>::load(ein + 4 * x, e);
-          sigma(e, mask[x] != 0, m, s);
+          T s[4];
+          Vec4<T>::load(sin_ + 4 * x, s);
           prev12[j] = s[3];
           prev22[j] = s[1];
         }
       }
-      // Pixel update of the AL iteration at (r, x1), given eps^n (en), its
-      // stress sj and the left neighbour's sigma11, sigma12 (x - e^1).
-      auto update = [&](int r, int j, int x1, const T (&en)[4], bool v, const T (&sj)[4], T l11, T l12) {
+      // Pixel update of the AL iteration at (r, x1), given the stress sj of
+      // iterate n (the multiplier) and the left neighbour's sigma11, sigma12
+      // (x - e^1).
+      auto update = [&](int r, int j, int x1, bool v, const T (&sj)[4], T l11, T l12) {
         if (x1 >= L) return;
         const size_t x = (size_t)(r0 + r) * L + x1;
         // Eq. 1: div_i = sum_j sigma_ij(x) - sigma_ij(x - e^j)
@@ -579,20 +600,21 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
         prev12[j] = sj[3];
         prev22[j] = sj[1];
 #pragma unroll
-        for (int c = 0; c < 4; c++) {
-          acc[A_S11 + c] += sj[c];
-          acc[A_E11 + c] += en[c];
-        }
+        for (int c = 0; c < 4; c++) acc[A_S11 + c] += sj[c];
         acc[A_DIV2] += d1 * d1 + d2 * d2;
         // augmented-Lagrangian update of this pixel
         T e[4] = {IO::px(sp, 0, r, x1), IO::px(sp, 1, r, x1), E[2], IO::px(sp, 2, r, x1)};
-        T c0[4], tau[4], e1[4];
+        T c0[4], tau[4], e1[4], s1[4], p1[3];
         c0_apply(e, m, c0);
 #pragma unroll
         for (int c = 0; c < 4; c++) tau[c] = sj[c] + c0[c];
-        T p1[3];
-        local_solve_p(tau, v, m, e1, p1);
+        local_solve_p(tau, v, m, e1, s1, p1);
         Vec4<T>::store(eout + 4 * x, e1);
+        Vec4<T>::store(sout + 4 * x, s1);
+        // <eps^{n+1}> and its plastic pixels (stats of the next iterate)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[A_E11 + c] += e1[c];
+        acc[A_NPL] += is_plastic(e1, v, m) ? T(1) : T(0);
         const T q0 = e1[0] - e[0], q1 = e1[1] - e[1], q2 = e1[2] - e[2], q3 = e1[3] - e[3];
         acc[A_COMP] += q0 * q0 + q1 * q1 + q2 * q2 + T(2) * q3 * q3;
         // next polarization sigma(eps^{n+1}) - C0:eps^{n+1} (in-plane)
@@ -600,79 +622,50 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
         IO::px(sp, 1, r, x1) = p1[1];
         IO::px(sp, 2, r, x1) = p1[2];
       };
-      // Left neighbours: the previous lane by a warp shuffle; lane 0 takes
-      // lane 31 of the previous pixel group of its warp (the run is
-      // contiguous).  At the start of a run: FP32 re-evaluates sigma at
-      // x - e^1 (periodic) from memory; FP64 (where that evaluation would
-      // cost the warp a full sigma on the FP64 pipe) reads the previous
-      // warp's last value from a per-row exchange, double-buffered by row
-      // parity so one barrier per row suffices.
-      constexpr bool XCH = sizeof(T) == 8 && L >= 32;
-      constexpr int NW = NT / 32;
-      __shared__ T edge[XCH ? 2 : 1][2][XCH ? NW : 1];
-      // eps^n and voids of row r, group j
-      auto load_px = [&](int r, int j, T (&e)[4], bool& v) {
+      // stress of iterate n and voids of row r, group j
+      auto load_px = [&](int r, int j, T (&sg)[4], bool& v) {
         const int x1 = xmap(j);
         const size_t x = (size_t)(r0 + r) * L + x1;
         const bool act = x1 < L && ECHK(x, LL, 23);
         v = act ? mask[x] != 0 : true;
-        if (act) Vec4<T>::load(ein + 4 * x, e);
-        else e[0] = e[1] = e[2] = e[3] = T(0);
+        if (act) Vec4<T>::load(sin_ + 4 * x, sg);
+        else sg[0] = sg[1] = sg[2] = sg[3] = T(0);
       };
-      auto row = [&](int r, T (&en)[P][4], bool (&vv)[P]) {
-        T slast[4];  // sigma of the last group (FP64 exchange)
-        if constexpr (XCH) {
-          sigma(en[P - 1], vv[P - 1], m, slast);
-          if (lane == 31) {
-            edge[r & 1][0][wid] = slast[0];
-            edge[r & 1][1][wid] = slast[3];
-          }
-          __syncthreads();
-        }
+      // Left neighbours: the previous lane by a warp shuffle; lane 0 takes
+      // lane 31 of the previous pixel group of its warp (the run is
+      // contiguous), and at the start of a run reads sigma at x - e^1
+      // (periodic) from memory.
+      auto row = [&](int r, T (&sg)[P][4], bool (&vv)[P]) {
         T run11 = T(0), run12 = T(0);  // sigma11, sigma12 of lane 31, previous group
 #pragma unroll
         for (int j = 0; j < P; j++) {
-          T sj[4];
-          bool pl;
-          if (XCH && j == P - 1) {
-            for (int c = 0; c < 4; c++) sj[c] = slast[c];
-            pl = is_plastic(en[j], vv[j], m);
-          } else {
-            pl = sigma(en[j], vv[j], m, sj);
-          }
-          acc[A_NPL] += pl ? T(1) : T(0);
           const int x1 = xmap(j);
           T l11, l12;
           if constexpr (L < 32) {
             const int src = (lane + L - 1) & (L - 1);
-            l11 = __shfl_sync(0xffffffffu, sj[0], src);
-            l12 = __shfl_sync(0xffffffffu, sj[3], src);
+            l11 = __shfl_sync(0xffffffffu, sg[j][0], src);
+            l12 = __shfl_sync(0xffffffffu, sg[j][3], src);
           } else {
-            l11 = __shfl_up_sync(0xffffffffu, sj[0], 1);
-            l12 = __shfl_up_sync(0xffffffffu, sj[3], 1);
+            l11 = __shfl_up_sync(0xffffffffu, sg[j][0], 1);
+            l12 = __shfl_up_sync(0xffffffffu, sg[j][3], 1);
             if (lane == 0) {
               if (j > 0) {
                 l11 = run11;
                 l12 = run12;
-              } else if constexpr (XCH) {
-                const int pw = wid > 0 ? wid - 1 : NW - 1;
-                l11 = edge[r & 1][0][pw];
-                l12 = edge[r & 1][1][pw];
               } else {
                 const size_t xl = (size_t)(r0 + r) * L + ((x1 + L - 1) & (L - 1));
                 if (ECHK(xl, LL, 24)) {
-                  T el[4], sl[4];
-                  Vec4<T>::load(ein + 4 * xl, el);
-                  sigma(el, mask[xl] != 0, m, sl);
+                  T sl[4];
+                  Vec4<T>::load(sin_ + 4 * xl, sl);
                   l11 = sl[0];
                   l12 = sl[3];
                 }
               }
             }
-            run11 = __shfl_sync(0xffffffffu, sj[0], 31);
-            run12 = __shfl_sync(0xffffffffu, sj[3], 31);
+            run11 = __shfl_sync(0xffffffffu, sg[j][0], 31);
+            run12 = __shfl_sync(0xffffffffu, sg[j][3], 31);
           }
-          update(r, j, x1, en[j], vv[j], sj, l11, l12);
+          update(r, j, x1, vv[j], sg[j], l11, l12);
         }
       };
       // When the rows' strains fit in 32 registers per thread, all of them
@@ -706,7 +699,7 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
       __syncthreads();
       IO::store(sp, spec, r0);
     }
-    if (phase == PH_ITER) {
+    if (phase == PH_ITER || phase == PH_INIT) {
       if (ECHK(blockIdx.x, L / RR, 25)) block_reduce_acc<NT>(acc, S.partials + (size_t)blockIdx.x * PART_STRIDE);
     }
     // every thread of this CTA is done with the solve state before the CTA
@@ -721,7 +714,7 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
     if (s_last) {
       __shared__ double tot[N_ACC];
       __threadfence();
-      if (phase == PH_ITER) {
+      if (phase == PH_ITER || phase == PH_INIT) {
         sum_partials<NT>(S.partials, gridDim.x, tot);
         __syncthreads();
       }

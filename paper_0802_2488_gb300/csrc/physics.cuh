@@ -19,6 +19,7 @@ struct Mat {
   T trial2;         // (mu / (mu + mu0))^2: |dev| of the elastic trial vs |tau'|
   T p_mat, p_void;  // 3 (K - K0), -3 K0
   T gsc_el;         // mu / (mu + mu0)
+  T k3;             // 3 K
 };
 
 template <typename T>
@@ -47,6 +48,7 @@ __device__ __forceinline__ Mat<T> make_mat(const Solve& S) {
   m.p_mat = c[MC_P_MAT];
   m.p_void = c[MC_P_VOID];
   m.gsc_el = c[MC_GSC_EL];
+  m.k3 = c[MC_3K];
   return m;
 }
 
@@ -158,26 +160,28 @@ __device__ __forceinline__ bool local_solve(const T t[4], bool is_void, const Ma
   return pl;
 }
 
-// The local step (local_solve) together with the next polarization
-// p = sigma(eps) - C0:eps of its solution, from the step's own quantities:
-// with tau' the deviator of tau, eps = sc tau' + em I and
+// The local step (local_solve) together with the stress of its solution and
+// the next polarization p = sigma(eps) - C0:eps, from the step's own
+// quantities: with tau' the deviator of tau, eps = sc tau' + em I and
 //   sigma(eps) = 3 K em I + gsc tau',   gsc = 2 mu sc (elastic),
 //                                       sqrt(2/3) Y / |tau'| (plastic), 0 (void),
 // so p = (3 K - 3 K0) em I + (gsc - 2 mu0 sc) tau' (K = 0 for a void).  This
 // is sigma of the step's solution on the branch the step chose, without a
-// second evaluation of the law.  Returns true on the plastic branch; p holds
-// the in-plane components (11, 22, 12).
+// second evaluation of the law (it is also the multiplier update of the
+// augmented Lagrangian: lambda + C0:(e - eps) = tau - C0:eps).  Returns true
+// on the plastic branch; s holds (11, 22, 33, 12), p the in-plane (11, 22, 12).
 template <typename T>
-__device__ __forceinline__ bool local_solve_p(const T t[4], bool is_void, const Mat<T>& m, T e[4], T p[3]) {
+__device__ __forceinline__ bool local_solve_p(const T t[4], bool is_void, const Mat<T>& m, T e[4], T s[4], T p[3]) {
   const T tm = (t[0] + t[1] + t[2]) * T(1.0 / 3.0);
   const T d0 = t[0] - tm, d1 = t[1] - tm, d2 = t[2] - tm, d3 = t[3];
-  T em, sc, gsc, pa;
+  T em, sc, gsc, pa, sk;
   bool pl = false;
   if (is_void) {
     em = tm * m.inv_3K0;
     sc = m.inv_2mu0;
     gsc = T(0);
     pa = m.p_void;
+    sk = T(0);
   } else {
     em = tm * m.inv_3KK0;
     const T nt2 = d0 * d0 + d1 * d1 + d2 * d2 + T(2) * d3 * d3;
@@ -191,11 +195,17 @@ __device__ __forceinline__ bool local_solve_p(const T t[4], bool is_void, const 
       gsc = m.gsc_el;
     }
     pa = m.p_mat;
+    sk = m.k3;
   }
   e[0] = d0 * sc + em;
   e[1] = d1 * sc + em;
   e[2] = d2 * sc + em;
   e[3] = d3 * sc;
+  const T sm = sk * em;
+  s[0] = gsc * d0 + sm;
+  s[1] = gsc * d1 + sm;
+  s[2] = gsc * d2 + sm;
+  s[3] = gsc * d3;
   const T pb = gsc - m.two_mu0 * sc;
   const T pm = pa * em;
   p[0] = pb * d0 + pm;

@@ -4,7 +4,7 @@ print their algorithmic throughput as JSON.
 
     python -m paper_0802_2488_gb300.passbench --L 2048 --precision fp32 --iters 50
 
-Algorithmic work per pixel and pass (kernels section):
+Algorithmic work per pixel and pass:
   row pass:    bytes 57 (FP32) / 113 (FP64),  flops 15 log2 L + 60
   column pass: bytes 24 (FP32) / 48 (FP64),   flops 15 log2 L + 25
 """
