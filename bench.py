@@ -420,7 +420,9 @@ def main():
         else:
             mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
             hbm = json.load(open(mp))["hbm_gbs"] if os.path.exists(mp) else 6800.0
-            row_b, col_b = 57 * L * L * nb, 24 * L * L * nb
+            # row pass: spectrum read + write 24 B, sigma read 16 B, eps and
+            # sigma written 32 B, mask 1 B; column pass: spectrum r + w 24 B
+            row_b, col_b = 73 * L * L * nb, 24 * L * L * nb
             dom_ms, dom_b, dom = (row_ms, row_b, "row") if row_ms >= col_ms else (col_ms, col_b, "col")
             achieved = dom_b / (dom_ms * 1e-3) / 1e9
             roof = {"bound": "hbm", "kernel": f"{dom}_pass<float,{L}>", "achieved": achieved, "peak": hbm,

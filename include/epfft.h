@@ -193,7 +193,7 @@ int epfft_solve_batch(epfft_ctx *ctx, int32_t n, const epfft_problem *problems,
  * momenta (with the tensor sign of the mirror, as in DG1) is exactly the
  * Eq. 3 scheme on the mirrored lattice under the mirrored load, so the
  * members run as one batch of Eq. 3 solves of the lattice and its mirror
- * images (x1, x2 and both; E12 reversed by a single mirror), each judged by
+ * images (x1, x2 and both; E12 reversed by a single mirror), each tested by
  * its own scheme's indicators, and their fields are mirrored back before
  * averaging.  problem->green must be EPFFT_GREEN_EQ3.
  * records: n_inc entries: per increment the mean of the four members'

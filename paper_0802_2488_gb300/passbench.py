@@ -5,7 +5,9 @@ print their algorithmic throughput as JSON.
     python -m paper_0802_2488_gb300.passbench --L 2048 --precision fp32 --iters 50
 
 Algorithmic work per pixel and pass:
-  row pass:    bytes 57 (FP32) / 113 (FP64),  flops 15 log2 L + 60
+  row pass:    bytes 73 (FP32) / 145 (FP64),  flops 15 log2 L + 60
+               (spectrum read and written, sigma of iterate n read, the new
+               strain and sigma written, the void mask)
   column pass: bytes 24 (FP32) / 48 (FP64),   flops 15 log2 L + 25
 """
 from __future__ import annotations
@@ -28,7 +30,7 @@ def measure(ctx, L: int, precision: str, f: float = 0.2, iters: int = 50, varian
     n = L * L * batch
     lg = math.log2(L)
     f64 = precision == "fp64"
-    row_b, col_b = (113 if f64 else 57) * n, (48 if f64 else 24) * n
+    row_b, col_b = (145 if f64 else 73) * n, (48 if f64 else 24) * n
     row_f, col_f = (15 * lg + 60) * n, (15 * lg + 25) * n
     return {
         "L": L, "precision": precision, "iters": iters, "variant": variant, "batch": batch,
