@@ -52,3 +52,30 @@ def test_no_cpu_fallback_without_device(lib):
     h = C.c_void_p()
     rc = lib.epfft_create(C.byref(h), None)
     assert rc == B.EPFFT_ERR_CUDA and not h.value
+
+
+def test_argument_checks_of_analysis_entry_points(lib):
+    """Host-side argument checks of the Sec. 3 / Eqs. 5-6 entry points reject
+    bad input before any device work."""
+    import ctypes as C
+    import numpy as np
+    out = np.zeros(8)
+    rec = np.zeros(2, dtype=B.RECORD_DTYPE)
+    st = np.zeros((2, 6), np.int32)
+    ok = lib.epfft_indicators(2, rec.ctypes.data, st.ctypes.data, 8, 0, np.zeros(16).ctypes.data)
+    assert ok == B.EPFFT_OK
+    assert lib.epfft_indicators(0, rec.ctypes.data, st.ctypes.data, 8, 0, out.ctypes.data) == B.EPFFT_ERR_ARG
+    assert lib.epfft_indicators(2, rec.ctypes.data, st.ctypes.data, 8, 2, out.ctypes.data) == B.EPFFT_ERR_ARG
+    assert lib.epfft_indicators(2, None, st.ctypes.data, 8, 0, out.ctypes.data) == B.EPFFT_ERR_ARG
+    a = C.c_double()
+    ind = np.zeros((2, 8))
+    assert lib.epfft_empirical_curve(2, ind.ctypes.data, st.ctypes.data, 8, C.c_double(1.0), 3, C.byref(a),
+                                     np.zeros(2).ctypes.data) == B.EPFFT_ERR_ARG
+    assert lib.epfft_empirical_curve(0, ind.ctypes.data, st.ctypes.data, 8, C.c_double(1.0), 0, C.byref(a),
+                                     np.zeros(2).ctypes.data) == B.EPFFT_ERR_ARG
+    # entry points that need a context refuse a null one
+    assert lib.epfft_void_plastic(None, 8, 1, None, None, None, None) == B.EPFFT_ERR_ARG
+    assert lib.epfft_solve_dg2(None, None, None, None, None) == B.EPFFT_ERR_ARG
+    assert lib.epfft_average5(None, 8, 0, None, None) == B.EPFFT_ERR_ARG
+    assert lib.epfft_eps_eq(None, 8, 0, None, None) == B.EPFFT_ERR_ARG
+    assert lib.epfft_effective_moduli(None, None, C.c_double(1e-3), None, None) == B.EPFFT_ERR_ARG
