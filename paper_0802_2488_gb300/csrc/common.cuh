@@ -128,7 +128,7 @@ struct Solve {
   uint32_t arrive;
   double Eprev[4];
   double sig_prev[4];
-  double eta3_cur;
+  double comp_cur;      // mean fixed-point residual of iterate n (eta3^2 EE)
   double epsm_next[4];  // <eps> of the iterate the last pass produced
   double npl_next;      // its plastic pixels
   int64_t total_iters;  // pixel-iteration accounting: passes that did work

@@ -267,43 +267,56 @@ __device__ __forceinline__ void load_E(const double* p, T E[4]) {
   E[0] = T(p[0]); E[1] = T(p[1]); E[2] = T(p[2]); E[3] = T(p[3]);
 }
 
-// Reduce N_ACC per-thread values (promoted to FP64) over the CTA in a fixed
-// order; thread 0 returns the sums in out.
-template <int NT>
-__device__ __forceinline__ void block_reduce(double v[N_ACC], double* out) {
-  __shared__ double red[NT / 32][N_ACC];
+// FP64 sums of N_ACC values over the first NW warps of the CTA, in a fixed
+// order; every thread of the CTA calls it (it holds a barrier), the threads
+// i < N_ACC write sum i to out[i].  Within a warp the values (padded to 16)
+// are summed by recursive halving: at the levels h = 8, 4, 2, 1 a lane keeps
+// the half of its values selected by lane bit h and adds the partner's
+// (lane ^ h) copy of that half; after that lane l holds value l & 15 summed
+// over the 16 lanes that share bit 16, and one more exchange with lane ^ 16
+// completes the warp sum.  That is 16 FP64 adds per lane, where one shuffle
+// tree per value costs 5 N_ACC; FP64 adds are scarce on GB300 (about two
+// per clock and SM).  Thread i then adds the warps' sums in warp order.
+template <int NW>
+__device__ __forceinline__ void block_sum_f64(const double* v, double* out) {
+  static_assert(N_ACC <= 16, "values per reduction");
+  __shared__ double red[NW][16];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (wid < NW) {
+    double a[16];
 #pragma unroll
-  for (int i = 0; i < N_ACC; i++) {
+    for (int i = 0; i < 16; i++) a[i] = i < N_ACC ? v[i] : 0.0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
-  }
-  if (lane == 0) {
+    for (int h = 8; h >= 1; h >>= 1) {
+      const bool up = (lane & h) != 0;
 #pragma unroll
-    for (int i = 0; i < N_ACC; i++) red[wid][i] = v[i];
+      for (int k = 0; k < h; k++) {
+        const double keep = up ? a[k + h] : a[k];
+        const double send = up ? a[k] : a[k + h];
+        a[k] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+      }
+    }
+    const double s = a[0] + __shfl_xor_sync(0xffffffffu, a[0], 16);
+    if (lane < 16) red[wid][lane] = s;
   }
   __syncthreads();
-  if (wid == 0) {
+  if (threadIdx.x < N_ACC) {
+    double t = red[0][threadIdx.x];
 #pragma unroll
-    for (int i = 0; i < N_ACC; i++) {
-      double x = lane < NT / 32 ? red[lane][i] : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-      if (lane == 0) out[i] = x;
-    }
+    for (int w = 1; w < NW; w++) t += red[w][threadIdx.x];
+    out[threadIdx.x] = t;
   }
 }
 
-// CTA sums of the per-thread accumulators.  FP64: shuffles in FP64.  FP32:
+// CTA sums of the per-thread accumulators.  FP64: block_sum_f64.  FP32:
 // values are added as FP32 (hi, lo) pairs with the error-free TwoSum of
 // Knuth/Moller (s = a + b, e = exact rounding error of the add), first
 // within each warp, then across the warps by warp 0, so the CTA total
 // carries about twice FP32 precision without FP64 work; thread 0 promotes
-// the final pairs to FP64 (hi + lo).  The FP64 pipe of GB300 is narrow, so
-// per-warp FP64 work here would cost more than the rest of the reduction.
+// the final pairs to FP64 (hi + lo).
 template <int NT>
 __device__ __forceinline__ void block_reduce_acc(double acc[N_ACC], double* out) {
-  block_reduce<NT>(acc, out);
+  block_sum_f64<NT / 32>(acc, out);
 }
 __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float bh, float bl) {
   const float sum = hi + bh;
@@ -347,25 +360,47 @@ __device__ __forceinline__ void block_reduce_acc(float acc[N_ACC], double* out) 
   }
 }
 
-// Sums of the per-CTA partials of a solve, computed by all threads of the
-// last CTA: thread t adds the records t, t + NT, ... in order, then a fixed
-// tree combines the threads, so the result does not depend on timing.
-template <int NT>
-__device__ __forceinline__ void sum_partials(const double* partials, int n_ctas, double* out) {
+// Sums of the NREC per-CTA partial records of a solve, computed by the last
+// CTA: the first NWA warps (enough for one record per thread, at most all
+// warps) take records t, t + 32 NWA, ..., with every load issued before the
+// first add, then block_sum_f64 combines them; the order is fixed, so the
+// result does not depend on timing.
+template <int NT, int NREC>
+__device__ __forceinline__ void sum_partials(const double* partials, double* out) {
+  constexpr int NW = NT / 32, NWR = (NREC + 31) / 32;
+  constexpr int NWA = NWR < NW ? NWR : NW, NTA = 32 * NWA;
+  constexpr int K = (NREC + NTA - 1) / NTA;
+  static_assert(PART_STRIDE % 2 == 0 && PART_STRIDE >= N_ACC, "record layout");
   double v[N_ACC];
 #pragma unroll
   for (int i = 0; i < N_ACC; i++) v[i] = 0.0;
-  for (int b = threadIdx.x; b < n_ctas; b += NT) {
+  if (threadIdx.x < NTA) {
+    double2 x[K][(N_ACC + 1) / 2];
 #pragma unroll
-    for (int i = 0; i < N_ACC; i++) v[i] += __ldcg(partials + (size_t)b * PART_STRIDE + i);
+    for (int k = 0; k < K; k++) {
+      const int b = threadIdx.x + k * NTA;
+#pragma unroll
+      for (int i = 0; i < (N_ACC + 1) / 2; i++)
+        x[k][i] = b < NREC ? __ldcg(reinterpret_cast<const double2*>(partials + (size_t)b * PART_STRIDE) + i)
+                           : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++)
+#pragma unroll
+      for (int i = 0; i < N_ACC; i++) v[i] += (i & 1) ? x[k][i / 2].y : x[k][i / 2].x;
   }
-  block_reduce<NT>(v, out);
+  block_sum_f64<NWA>(v, out);
 }
 
 // Last CTA of a solve's row pass: indicators of Sec. 2 and the state
 // machine.  Runs on one thread; A holds the sums of the partials (ITER).
-__device__ __forceinline__ void finalize_solve(Solve& S, int phase, const double* A, int L) {
-  const double inv = 1.0 / ((double)L * (double)L);
+// The indicators are eta1 = sqrt(div2 / ss), eta2 = sqrt(dd / ss) and
+// eta3 = sqrt(comp / EE); the stopping tests compare the squares scaled by
+// the denominators (div2 < tol^2 ss, ...), so an iteration takes no FP64
+// division or root, and the roots are formed once, for the record.
+template <int L>
+__device__ __forceinline__ void finalize_solve(Solve& S, int phase, const double* A) {
+  constexpr double inv = 1.0 / ((double)L * (double)L);  // exact: L is a power of two
   if (phase == PH_INIT) {
     const double* E = S.path + 4 * S.inc;
     for (int c = 0; c < 4; c++) {
@@ -386,50 +421,52 @@ __device__ __forceinline__ void finalize_solve(Solve& S, int phase, const double
   // plastic count and fixed-point residual of iterate n + 1 (the pass
   // produced it); <eps> and the plastic count of iterate n come from the
   // previous pass
-  double sig[4], epsm[4];
-  for (int c = 0; c < 4; c++) {
-    sig[c] = A[A_S11 + c] * inv;
-    epsm[c] = S.epsm_next[c];
-  }
-  const double npl = S.npl_next;
+  double sig[4];
+  for (int c = 0; c < 4; c++) sig[c] = A[A_S11 + c] * inv;
   const double div2 = A[A_DIV2] * inv, comp = A[A_COMP] * inv;
-  const double* E = S.path + 4 * S.inc;
-  double EE = E[0] * E[0] + E[1] * E[1] + E[2] * E[2] + 2.0 * E[3] * E[3];
-  if (EE == 0.0) EE = 1.0;
-  const double eta3_next = sqrt(comp / EE);
   const int n = S.iter;
   S.total_iters += 1;
   if (n >= 1) {
+    const double* E = S.path + 4 * S.inc;
+    double EE = E[0] * E[0] + E[1] * E[1] + E[2] * E[2] + 2.0 * E[3] * E[3];
+    if (EE == 0.0) EE = 1.0;
     const double ss = sig[0] * sig[0] + sig[1] * sig[1] + 2.0 * sig[3] * sig[3];
     double ds[4];
     for (int c = 0; c < 4; c++) ds[c] = sig[c] - S.sig_prev[c];
     const double dd = ds[0] * ds[0] + ds[1] * ds[1] + 2.0 * ds[3] * ds[3];
-    double eta1, eta2;
-    if (ss > 0.0) {
-      eta1 = sqrt(div2 / ss);
-      eta2 = sqrt(dd / ss);
-    } else {
-      eta1 = div2 == 0.0 ? 0.0 : CUDART_INF;
-      eta2 = dd == 0.0 ? 0.0 : CUDART_INF;
-    }
-    const bool finite = isfinite(eta1) && isfinite(eta2) && isfinite(sig[0]) && isfinite(sig[1]) &&
-                        isfinite(sig[3]);
+    const double comp_n = S.comp_cur;
+    // eta1 and eta2 are finite when ss > 0, and 0 (else infinite) when
+    // ss = 0 and the numerator is 0
+    const bool finite = isfinite(div2) && isfinite(dd) && isfinite(sig[0]) && isfinite(sig[1]) &&
+                        isfinite(sig[3]) && (ss > 0.0 || (div2 == 0.0 && dd == 0.0));
+    const double te2 = S.tol_eq * S.tol_eq, tm2 = S.tol_macro * S.tol_macro;
+    const bool pos = ss > 0.0;
     // equilibrium test: eta1 for the operators of Eq. 3; the continuum and
     // symmetrized operators are not Green operators of Eq. 1, so there the
     // fixed-point residual eta3 of the iterate takes its place
-    const double eq = (S.green == GM_CG1 || S.green == GM_DG1) ? S.eta3_cur : eta1;
-    const bool conv = eq < S.tol_eq && eta2 < S.tol_macro;
+    const bool eq_ok = (S.green == GM_CG1 || S.green == GM_DG1)
+                           ? (comp_n < te2 * EE && S.tol_eq > 0.0)
+                           : (pos ? div2 < te2 * ss : S.tol_eq > 0.0);
+    const bool conv = finite && eq_ok && (pos ? dd < tm2 * ss : S.tol_macro > 0.0);
     if (!finite || conv || n >= S.max_iter) {
+      double eta1, eta2;
+      if (pos) {
+        eta1 = sqrt(div2 / ss);
+        eta2 = sqrt(dd / ss);
+      } else {
+        eta1 = div2 == 0.0 ? 0.0 : CUDART_INF;
+        eta2 = dd == 0.0 ? 0.0 : CUDART_INF;
+      }
       Record& R = S.rec[S.inc];
       for (int c = 0; c < 4; c++) {
         R.sig_mean[c] = sig[c];
-        R.eps_mean[c] = epsm[c];
+        R.eps_mean[c] = S.epsm_next[c];
       }
       R.eta1 = eta1;
       R.eta2 = eta2;
-      R.eta3 = S.eta3_cur;
+      R.eta3 = sqrt(comp_n / EE);
       R.iterations = n;
-      R.n_plastic = (int32_t)npl;
+      R.n_plastic = (int32_t)S.npl_next;
       R.n_clusters = 0;
       R.status = !finite ? 2 : (conv ? 0 : 1);
       if (!finite) {
@@ -449,7 +486,7 @@ __device__ __forceinline__ void finalize_solve(Solve& S, int phase, const double
     S.epsm_next[c] = A[A_E11 + c] * inv;
   }
   S.npl_next = A[A_NPL];
-  S.eta3_cur = eta3_next;
+  S.comp_cur = comp;
   S.iter = n + 1;
   S.cur = 1 - S.cur;
 }
@@ -715,11 +752,11 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
       __shared__ double tot[N_ACC];
       __threadfence();
       if (phase == PH_ITER || phase == PH_INIT) {
-        sum_partials<NT>(S.partials, gridDim.x, tot);
+        sum_partials<NT, L / RR>(S.partials, tot);
         __syncthreads();
       }
       if (tid == 0) {
-        finalize_solve(S, phase, tot, L);
+        finalize_solve<L>(S, phase, tot);
         S.arrive = 0;
       }
     }
