@@ -273,10 +273,26 @@ __device__ __forceinline__ void fft_seq(C2<T>* s, const C2<T>* __restrict__ tw) 
   fft_stages<T, N, RM, FULL, NSEQ, NT, INV>(s, tw);
 }
 
-// Copies n table entries from global to shared memory (no barrier).
+// Asynchronous global -> shared copy of one complex number (cp.async: the
+// copy holds no register and any number can be in flight): 8 bytes through
+// L1 for FP32, 16 bytes past L1 for FP64.  Both addresses are aligned to the
+// element size.  The copies of a thread complete at cp_async_wait_all();
+// a barrier after it publishes them to the CTA.
+template <typename T>
+__device__ __forceinline__ void cp_async_c2(C2<T>* dst, const C2<T>* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(C2<T>) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Copies n table entries from global to shared memory asynchronously
+// (complete with cp_async_wait_all() and a barrier).
 template <typename T, int NT>
 __device__ __forceinline__ void copy_table(C2<T>* dst, const C2<T>* __restrict__ src, int n) {
-  for (int i = threadIdx.x; i < n; i += NT) dst[i] = src[i];
+  for (int i = threadIdx.x; i < n; i += NT) cp_async_c2(dst + i, src + i);
 }
 
 // exp(-2 pi i k / L) for 0 <= k <= L/4 from the octant t[0 .. L/8]:

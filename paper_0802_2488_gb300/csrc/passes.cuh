@@ -137,32 +137,21 @@ struct RowIO {
     is = at(c, r, b * W + w);
     ig = ((size_t)(c * NBK + b) * L + r0 + r) * W + w;
   }
-  // FP32 complex numbers are moved two at a time (16-byte accesses) when a
+  // FP32 complex numbers are stored two at a time (16-byte accesses) when a
   // tile chunk (RR x W numbers, contiguous in HBM) has even length.
   static constexpr bool PAIRS = sizeof(C2<T>) == 8 && (RR * W) % 2 == 0;
 
-  static __device__ __forceinline__ void load(C2<T>* sp, const C2<T>* __restrict__ spec, int r0) {
-    if constexpr (PAIRS) {
+  // Issues the asynchronous copies of the RR rows' spectrum into shared
+  // memory (complete with cp_async_wait_all() and a barrier): consecutive
+  // threads take consecutive numbers of the tile chunks, so a warp reads
+  // 32 consecutive numbers of HBM, and the whole tile is in flight at once.
+  static __device__ __forceinline__ void load_async(C2<T>* sp, const C2<T>* __restrict__ spec, int r0) {
 #pragma unroll 4
-      for (int e2 = threadIdx.x; e2 < 3 * M * RR / 2; e2 += NT) {
-        int is0, is1;
-        size_t ig0, ig1;
-        where(2 * e2, r0, is0, ig0);
-        where(2 * e2 + 1, r0, is1, ig1);
-        if (ECHK(is0, SZ, 1) && ECHK(is1, SZ, 1) && ECHK(ig0 + 1, (size_t)3 * M * L, 2)) {
-          const float4 v = *reinterpret_cast<const float4*>(spec + ig0);
-          reinterpret_cast<float2*>(sp)[is0] = make_float2(v.x, v.y);
-          reinterpret_cast<float2*>(sp)[is1] = make_float2(v.z, v.w);
-        }
-      }
-    } else {
-#pragma unroll 4
-      for (int e = threadIdx.x; e < 3 * M * RR; e += NT) {
-        int is;
-        size_t ig;
-        where(e, r0, is, ig);
-        if (ECHK(is, SZ, 1) && ECHK(ig, (size_t)3 * M * L, 2)) sp[is] = spec[ig];
-      }
+    for (int e = threadIdx.x; e < 3 * M * RR; e += NT) {
+      int is;
+      size_t ig;
+      where(e, r0, is, ig);
+      if (ECHK(is, SZ, 1) && ECHK(ig, (size_t)3 * M * L, 2)) cp_async_c2(sp + is, spec + ig);
     }
   }
   static __device__ __forceinline__ void store(const C2<T>* sp, C2<T>* __restrict__ spec, int r0) {
@@ -246,8 +235,9 @@ struct RowIO {
     for (int g = 0; g < NSEQ / G; g++)
       fft_seq<T, M, C::RM_ROW, C::FULL, G, NT, INV>(sp + g * G * SP, stw);
   }
-  // Stage table and twist octant: global -> shared (no barrier).  Returns
-  // the shared stage table; the octant follows it.
+  // Stage table and twist octant: global -> shared, asynchronously (complete
+  // with cp_async_wait_all() and a barrier).  Returns the shared stage
+  // table; the octant follows it.
   static __device__ __forceinline__ const C2<T>* load_tables(C2<T>* sp, const C2<T>* __restrict__ tab) {
     C2<T>* stw = sp + SZ;
     copy_table<T, NT>(stw, tab + C::TB::off_row(V), C::ROW_TW);
@@ -362,32 +352,35 @@ __device__ __forceinline__ void block_reduce_acc(float acc[N_ACC], double* out) 
 
 // Sums of the NREC per-CTA partial records of a solve, computed by the last
 // CTA: the first NWA warps (enough for one record per thread, at most all
-// warps) take records t, t + 32 NWA, ..., with every load issued before the
-// first add, then block_sum_f64 combines them; the order is fixed, so the
-// result does not depend on timing.
+// warps) take records t, t + 32 NWA, ..., loading up to two records per
+// thread before adding them, then block_sum_f64 combines the threads; the
+// order is fixed, so the result does not depend on timing.
 template <int NT, int NREC>
 __device__ __forceinline__ void sum_partials(const double* partials, double* out) {
   constexpr int NW = NT / 32, NWR = (NREC + 31) / 32;
   constexpr int NWA = NWR < NW ? NWR : NW, NTA = 32 * NWA;
-  constexpr int K = (NREC + NTA - 1) / NTA;
-  static_assert(PART_STRIDE % 2 == 0 && PART_STRIDE >= N_ACC, "record layout");
+  constexpr int K = (NREC + NTA - 1) / NTA, KC = K < 2 ? K : 2, NV = (N_ACC + 1) / 2;
+  static_assert(PART_STRIDE % 2 == 0 && PART_STRIDE >= 2 * NV, "record layout");
   double v[N_ACC];
 #pragma unroll
   for (int i = 0; i < N_ACC; i++) v[i] = 0.0;
   if (threadIdx.x < NTA) {
-    double2 x[K][(N_ACC + 1) / 2];
+#pragma unroll 1
+    for (int k0 = 0; k0 < K; k0 += KC) {
+      double2 x[KC][NV];
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-      const int b = threadIdx.x + k * NTA;
+      for (int k = 0; k < KC; k++) {
+        const int b = threadIdx.x + (k0 + k) * NTA;
 #pragma unroll
-      for (int i = 0; i < (N_ACC + 1) / 2; i++)
-        x[k][i] = b < NREC ? __ldcg(reinterpret_cast<const double2*>(partials + (size_t)b * PART_STRIDE) + i)
-                           : make_double2(0.0, 0.0);
+        for (int i = 0; i < NV; i++)
+          x[k][i] = b < NREC ? __ldcg(reinterpret_cast<const double2*>(partials + (size_t)b * PART_STRIDE) + i)
+                             : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int k = 0; k < KC; k++)
+#pragma unroll
+        for (int i = 0; i < N_ACC; i++) v[i] += (i & 1) ? x[k][i / 2].y : x[k][i / 2].x;
     }
-#pragma unroll
-    for (int k = 0; k < K; k++)
-#pragma unroll
-      for (int i = 0; i < N_ACC; i++) v[i] += (i & 1) ? x[k][i / 2].y : x[k][i / 2].x;
   }
   block_sum_f64<NWA>(v, out);
 }
@@ -551,9 +544,10 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
     const uint8_t* __restrict__ mask = S.mask;
     const Mat<T> m = make_mat<T>(S);
     const size_t LL = (size_t)L * L;
-    // stage table and twist octant (first read after the next barrier of
-    // every phase)
-    const C2<T>* stw = IO::load_tables(sp, tw);
+    // stage table and twist octant, in flight until the first barrier after
+    // cp_async_wait_all() (INIT, ITER; the other phases do not read them)
+    const C2<T>* stw = sp + C::ROW_DATA;
+    if (phase == PH_INIT || phase == PH_ITER) IO::load_tables(sp, tw);
     T acc[N_ACC];
 #pragma unroll
     for (int i = 0; i < N_ACC; i++) acc[i] = T(0);
@@ -602,15 +596,13 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
     } else {  // PH_ITER
       T E[4];
       load_E(S.path + 4 * inc, E);
-      IO::load(sp, spec, r0);
-      __syncthreads();
-      IO::c2r_twist(sp, IO::octant(stw));
-      __syncthreads();
-      IO::template fft<true>(sp, stw);
+      IO::load_async(sp, spec, r0);
       // halo row x2 = r0 - 1: sigma12 and sigma22 of iterate n for the
-      // backward difference along x2
+      // backward difference along x2; loaded while the spectrum is in
+      // flight when the registers allow (few pixels per thread), else after
+      // the transform
       T prev12[P], prev22[P];
-      {
+      auto load_halo = [&]() {
         const int xh = (r0 + L - 1) & (L - 1);
 #pragma unroll
         for (int j = 0; j < P; j++) {
@@ -624,7 +616,15 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
           prev12[j] = s[3];
           prev22[j] = s[1];
         }
-      }
+      };
+      constexpr bool EARLY_HALO = P <= 2;
+      if constexpr (EARLY_HALO) load_halo();
+      cp_async_wait_all();
+      __syncthreads();
+      IO::c2r_twist(sp, IO::octant(stw));
+      __syncthreads();
+      IO::template fft<true>(sp, stw);
+      if constexpr (!EARLY_HALO) load_halo();
       // Pixel update of the AL iteration at (r, x1), given the stress sj of
       // iterate n (the multiplier) and the left neighbour's sigma11, sigma12
       // (x - e^1).
@@ -730,6 +730,7 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
     }
 
     if (phase == PH_ITER || phase == PH_INIT) {
+      cp_async_wait_all();  // the tables (INIT)
       __syncthreads();
       IO::template fft<false>(sp, stw);
       IO::r2c_twist(sp, IO::octant(stw));
@@ -792,31 +793,17 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
   const int b = blockIdx.x;
   C2<T>* spec = reinterpret_cast<C2<T>*>(S.spec);
   copy_table<T, NT>(stw, tw + C::TB::off_col(V), C::COL_TW);
-  // the slab of each component is contiguous in HBM; FP32 numbers move in pairs
-  if constexpr (sizeof(C2<T>) == 8) {
+  // the slab of each component is contiguous in HBM: consecutive threads
+  // copy consecutive numbers, asynchronously, the whole slab in flight
 #pragma unroll 4
-    for (int e2 = tid; e2 < 3 * L * W / 2; e2 += NT) {
-      const int e = 2 * e2;
-      const int c = e / (L * W);
-      const int rem = e - c * (L * W);
-      const int xa = rem / W, wa = rem - xa * W, xb = (rem + 1) / W, wb = rem + 1 - xb * W;
-      const float4 v = *reinterpret_cast<const float4*>(spec + (size_t)(c * NBK + b) * L * W + rem);
-      const int ia = at(c, wa, xa), ib = at(c, wb, xb);
-      if (ECHK(ia, SZ, 30) && ECHK(ib, SZ, 30)) {
-        reinterpret_cast<float2*>(sp)[ia] = make_float2(v.x, v.y);
-        reinterpret_cast<float2*>(sp)[ib] = make_float2(v.z, v.w);
-      }
-    }
-  } else {
-#pragma unroll 4
-    for (int e = tid; e < 3 * L * W; e += NT) {
-      const int c = e / (L * W);
-      const int rem = e - c * (L * W);
-      const int x2 = rem / W, w = rem - x2 * W;
-      const int i = at(c, w, x2);
-      if (ECHK(i, SZ, 30)) sp[i] = spec[(size_t)(c * NBK + b) * L * W + rem];
-    }
+  for (int e = tid; e < 3 * L * W; e += NT) {
+    const int c = e / (L * W);
+    const int rem = e - c * (L * W);
+    const int x2 = rem / W, w = rem - x2 * W;
+    const int i = at(c, w, x2);
+    if (ECHK(i, SZ, 30)) cp_async_c2(sp + i, spec + (size_t)(c * NBK + b) * L * W + rem);
   }
+  cp_async_wait_all();
   __syncthreads();
   constexpr int G = C::G_C;
 #pragma unroll 1
@@ -923,6 +910,7 @@ row_forward(const T* __restrict__ p, C2<T>* __restrict__ spec, const C2<T>* __re
       const size_t x = (size_t)(r0 + r) * L + x1;
       for (int c = 0; c < 3; c++) IO::px(sp, c, r, x1) = p[c * LL + x];
     }
+  cp_async_wait_all();
   __syncthreads();
   IO::template fft<false>(sp, stw);
   IO::r2c_twist(sp, IO::octant(stw));
@@ -941,7 +929,8 @@ row_inverse(const C2<T>* __restrict__ spec, T* __restrict__ e, const C2<T>* __re
   const int r0 = blockIdx.x * RR;
   const size_t LL = (size_t)L * L;
   const C2<T>* stw = IO::load_tables(sp, tw);
-  IO::load(sp, spec, r0);
+  IO::load_async(sp, spec, r0);
+  cp_async_wait_all();
   __syncthreads();
   IO::c2r_twist(sp, IO::octant(stw));
   __syncthreads();
