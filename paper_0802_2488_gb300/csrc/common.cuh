@@ -145,7 +145,7 @@ struct BatchCtl {
   int32_t pad;
 };
 
-// First failed self-check of a build with EPFFT_CHECKS (debug builds only):
+// First failed self-check (builds define EPFFT_CHECKS):
 // the access is skipped and its code, index and bound are recorded.
 struct CheckRec {
   int32_t code, where;

@@ -128,6 +128,9 @@ struct RowIO {
   static __device__ __forceinline__ int at(int c, int r, int n) { return (c * RR + r) * SP + pad32(n); }
 
   // Chunk element e (c, b, r, w) of the RR rows: shared and global index.
+  // For e < 3 M RR (c < 3, b < M / W, r < RR, w < W) and rows r0 + r < L
+  // (a pass over L rows has L / RR CTAs per solve), is < 3 RR SP <= SZ and
+  // ig < 3 M L; builds with self-checks verify both at every access.
   static __device__ __forceinline__ void where(int e, int r0, int& is, size_t& ig) {
     const int c = e / (M * RR);
     const int rem = e - c * (M * RR);
@@ -162,7 +165,7 @@ struct RowIO {
         size_t ig0, ig1;
         where(2 * e2, r0, is0, ig0);
         where(2 * e2 + 1, r0, is1, ig1);
-        if (ECHK(is0, SZ, 3) && ECHK(is1, SZ, 3) && ECHK(ig0 + 1, (size_t)3 * M * L, 4)) {
+        if (ECHK(is0, SZ, 3) && ECHK(is1, SZ, 3) && ECHK(ig0 + 1, (size_t)3 * M * L, 4) && ECHK(ig0 & 1, 1, 5)) {
           const float2 a = reinterpret_cast<const float2*>(sp)[is0];
           const float2 b = reinterpret_cast<const float2*>(sp)[is1];
           *reinterpret_cast<float4*>(spec + ig0) = make_float4(a.x, a.y, b.x, b.y);
@@ -195,6 +198,7 @@ struct RowIO {
       } else {
         const int kk = M - k;
         const int ik = pad32(k), ikk = pad32(kk);  // 0 < k, kk < M
+        if (!ECHK(sq * SP + ikk, SZ, 38) || !ECHK(sq * SP + ik, SZ, 38)) continue;
         const C2<T> a = s[ik], b = s[ikk];
         const C2<T> wk = conj(twist_tw<T, L>(oct, k));
         // the partner's product conj(wk) (b - conj(a)) equals -conj(t)
@@ -218,6 +222,7 @@ struct RowIO {
       } else {
         const int kk = M - k;
         const int ik = pad32(k), ikk = pad32(kk);  // 0 < k, kk < M
+        if (!ECHK(sq * SP + ikk, SZ, 38) || !ECHK(sq * SP + ik, SZ, 38)) continue;
         const C2<T> a = s[ik], b = s[ikk];
         const C2<T> wk = twist_tw<T, L>(oct, k);
         // the partner's product conj(wk) (b - conj(a)) equals -conj(t)
@@ -520,6 +525,9 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
   C2<T>* sp = reinterpret_cast<C2<T>*>(smraw);
   __shared__ bool s_last;
 
+  // Every index of the pass is in range when the grid has L / RR CTAs per
+  // solve (see RowIO::where; pixel x = (r0 + r) L + x1 < L^2 for x1 < L).
+  if (!ECHK(gridDim.x - 1, L / RR, 27)) return;
   Solve& S = solves[blockIdx.y];
   // The mutable control fields are rewritten by the last CTA of this launch
   // (finalize_solve); every thread reads them exactly once, through
@@ -783,6 +791,10 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
   C2<T>* stw = sp + SZ;
   auto at = [](int c, int w, int x2) { return (c * W + w) * SP + pad32(x2); };
   const int tid = threadIdx.x;
+  // Every index of the pass is in range when the grid has M / W CTAs per
+  // solve: b < M / W, c < 3, w < W and x2 < L give at(c, w, x2) < 3 W SP <=
+  // SZ and a global index below 3 M L.
+  if (!ECHK(gridDim.x - 1, NBK, 33)) return;
   // The row pass that follows re-arms the loop; a body that never reaches
   // it must not loop again.
   if (use_cond && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) cudaGraphSetConditional(cond, 0u);
@@ -801,7 +813,8 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
     const int rem = e - c * (L * W);
     const int x2 = rem / W, w = rem - x2 * W;
     const int i = at(c, w, x2);
-    if (ECHK(i, SZ, 30)) cp_async_c2(sp + i, spec + (size_t)(c * NBK + b) * L * W + rem);
+    const size_t g = (size_t)(c * NBK + b) * L * W + rem;
+    if (ECHK(i, SZ, 30) && ECHK(g, (size_t)3 * M * L, 34)) cp_async_c2(sp + i, spec + g);
   }
   cp_async_wait_all();
   __syncthreads();
@@ -819,7 +832,7 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
     const int m1 = b * W + w;
     if (m1 == 0) continue;
     const int i0 = at(0, w, m2), i1 = at(1, w, m2), i2 = at(2, w, m2);
-    if (!ECHK(i0, SZ, 31) || !ECHK(i1, SZ, 31) || !ECHK(i2, SZ, 31)) continue;
+    if (!ECHK(i0, SZ, 31) || !ECHK(i1, SZ, 31) || !ECHK(i2, SZ, 31) || !ECHK(m1, L, 35) || !ECHK(m2, L, 35)) continue;
     C2<T> p11 = sp[i0], p22 = sp[i1], p12 = sp[i2];
     if (GEN) green_op(gm, ktab, qtab, L, m1, m2, lam0, mu0, scale, p11, p22, p12);
     else green_apply(ktab[m1], ktab[m2], lam0, mu0, scale, p11, p22, p12);
@@ -871,7 +884,7 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
       const int rem = e - c * (L * W);
       const int xa = rem / W, wa = rem - xa * W, xb = (rem + 1) / W, wb = rem + 1 - xb * W;
       const int ia = at(c, wa, xa), ib = at(c, wb, xb);
-      if (ECHK(ia, SZ, 32) && ECHK(ib, SZ, 32)) {
+      if (ECHK(ia, SZ, 32) && ECHK(ib, SZ, 32) && ECHK((size_t)(c * NBK + b) * L * W + rem + 1, (size_t)3 * M * L, 36)) {
         const float2 u = reinterpret_cast<const float2*>(sp)[ia];
         const float2 v = reinterpret_cast<const float2*>(sp)[ib];
         *reinterpret_cast<float4*>(spec + (size_t)(c * NBK + b) * L * W + rem) = make_float4(u.x, u.y, v.x, v.y);
@@ -900,6 +913,7 @@ row_forward(const T* __restrict__ p, C2<T>* __restrict__ spec, const C2<T>* __re
   using IO = RowIO<T, L, V>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C2<T>* sp = reinterpret_cast<C2<T>*>(smraw);
+  if (!ECHK(gridDim.x - 1, L / RR, 28)) return;  // indices: see RowIO::where
   const int r0 = blockIdx.x * RR;
   const size_t LL = (size_t)L * L;
   const C2<T>* stw = IO::load_tables(sp, tw);
@@ -926,6 +940,7 @@ row_inverse(const C2<T>* __restrict__ spec, T* __restrict__ e, const C2<T>* __re
   using IO = RowIO<T, L, V>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C2<T>* sp = reinterpret_cast<C2<T>*>(smraw);
+  if (!ECHK(gridDim.x - 1, L / RR, 28)) return;  // indices: see RowIO::where
   const int r0 = blockIdx.x * RR;
   const size_t LL = (size_t)L * L;
   const C2<T>* stw = IO::load_tables(sp, tw);
