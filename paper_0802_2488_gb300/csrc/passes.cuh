@@ -50,15 +50,17 @@ struct Cfg {
                                    : (F64 ? (L <= 256 ? 1 : 2) : (L <= 256 ? 1 : 2));
   // columns per column-pass CTA (= tile width of the spectrum layout)
   static constexpr int W0 = V == 0 ? (F64 ? (L <= 256 ? 1 : (L <= 1024 ? 2 : 1))
-                                          : (L <= 256 ? 2 : (L <= 1024 ? 2 : (L <= 2048 ? 4 : 2))))
+                                          : (L == 2048 ? 1 : 2))
                                    : (F64 ? 1 : (L <= 256 ? 1 : (L <= 1024 ? 2 : (L <= 2048 ? 1 : 2))));
   static constexpr int W = W0 < M ? W0 : M;
   static constexpr int NTMAX = V == 0 ? 512 : 256;
   // resident CTAs per SM asked of the compiler: FP32 variant 1 (at most 128
-  // registers per thread at 256 threads) and the FP32 L = 512 row pass of
-  // variant 0 (64 registers at 512 threads, no spills)
+  // registers per thread at 256 threads), the FP32 L = 512 row pass of
+  // variant 0 (64 registers at 512 threads, no spills) and the FP32 column
+  // passes of the narrow tiles of variant 0 at L = 512 .. 2048 (several
+  // small CTAs per SM overlap their loads with the others' transforms)
   static constexpr int MINB_ROW = !F64 && (V == 1 || L == 512) ? 2 : 1;
-  static constexpr int MINB_COL = !F64 && (V == 1 || L == 512 || L == 1024) ? 2 : 1;
+  static constexpr int MINB_COL = !F64 && (V == 1 || (L >= 512 && L <= 2048)) ? 2 : 1;
   static constexpr int NT_ROW0 = F64 ? (L > 512 ? 256 : (L < 128 ? L : 128)) : (L <= 256 ? L : NTMAX);
   static constexpr int NT_ROW = NT_ROW0 < 32 ? 32 : NT_ROW0;
   static constexpr int NT_COL0 = ((3 * W * L / RM_COL + 31) / 32) * 32;
