@@ -288,6 +288,13 @@ __device__ __forceinline__ void cp_async_c2(C2<T>* dst, const C2<T>* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Asks the L2 to fetch bytes [p, p + n) from HBM (a bulk prefetch: a hint
+// that completes on its own and changes no data); p and n are multiples of
+// 16 bytes.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned n) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(n) : "memory");
+}
+
 // Copies n table entries from global to shared memory asynchronously
 // (complete with cp_async_wait_all() and a barrier).
 template <typename T, int NT>

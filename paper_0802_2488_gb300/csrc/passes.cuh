@@ -308,9 +308,10 @@ __device__ __forceinline__ void block_sum_f64(const double* v, double* out) {
 // CTA sums of the per-thread accumulators.  FP64: block_sum_f64.  FP32:
 // values are added as FP32 (hi, lo) pairs with the error-free TwoSum of
 // Knuth/Moller (s = a + b, e = exact rounding error of the add), first
-// within each warp, then across the warps by warp 0, so the CTA total
-// carries about twice FP32 precision without FP64 work; thread 0 promotes
-// the final pairs to FP64 (hi + lo).
+// within each warp by the same recursive halving as block_sum_f64, then
+// across the warps in warp order, so the CTA total carries about twice
+// FP32 precision without FP64 work; thread i promotes the final pair of
+// value i to FP64 (hi + lo).
 template <int NT>
 __device__ __forceinline__ void block_reduce_acc(double acc[N_ACC], double* out) {
   block_sum_f64<NT / 32>(acc, out);
@@ -325,35 +326,46 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float bh, floa
 template <int NT>
 __device__ __forceinline__ void block_reduce_acc(float acc[N_ACC], double* out) {
   constexpr int NW = NT / 32;
-  __shared__ float red2[NW][N_ACC][2];
+  static_assert(N_ACC <= 16, "values per reduction");
+  __shared__ float red2[NW][16][2];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // recursive halving over 16 slots (as block_sum_f64), each add a TwoSum
+  // of (hi, lo) pairs: lane l ends with slot l & 15 of the warp
+  float hi[16], lo[16];
 #pragma unroll
-  for (int i = 0; i < N_ACC; i++) {
-    float hi = acc[i], lo = 0.0f;
+  for (int i = 0; i < 16; i++) {
+    hi[i] = i < N_ACC ? acc[i] : 0.0f;
+    lo[i] = 0.0f;
+  }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float bh = __shfl_down_sync(0xffffffffu, hi, o);
-      const float bl = __shfl_down_sync(0xffffffffu, lo, o);
-      two_sum_add(hi, lo, bh, bl);
-    }
-    if (lane == 0) {
-      red2[wid][i][0] = hi;
-      red2[wid][i][1] = lo;
+  for (int h = 8; h >= 1; h >>= 1) {
+    const bool up = (lane & h) != 0;
+#pragma unroll
+    for (int k = 0; k < h; k++) {
+      const float kh = up ? hi[k + h] : hi[k], kl = up ? lo[k + h] : lo[k];
+      const float sh = up ? hi[k] : hi[k + h], sl = up ? lo[k] : lo[k + h];
+      const float bh = __shfl_xor_sync(0xffffffffu, sh, h);
+      const float bl = __shfl_xor_sync(0xffffffffu, sl, h);
+      hi[k] = kh;
+      lo[k] = kl;
+      two_sum_add(hi[k], lo[k], bh, bl);
     }
   }
+  {
+    const float bh = __shfl_xor_sync(0xffffffffu, hi[0], 16);
+    const float bl = __shfl_xor_sync(0xffffffffu, lo[0], 16);
+    two_sum_add(hi[0], lo[0], bh, bl);
+  }
+  if (lane < 16) {
+    red2[wid][lane][0] = hi[0];
+    red2[wid][lane][1] = lo[0];
+  }
   __syncthreads();
-  if (wid == 0) {
+  if (threadIdx.x < N_ACC) {
+    float h = red2[0][threadIdx.x][0], l = red2[0][threadIdx.x][1];
 #pragma unroll
-    for (int i = 0; i < N_ACC; i++) {
-      float hi = lane < NW ? red2[lane][i][0] : 0.0f, lo = lane < NW ? red2[lane][i][1] : 0.0f;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float bh = __shfl_down_sync(0xffffffffu, hi, o);
-        const float bl = __shfl_down_sync(0xffffffffu, lo, o);
-        two_sum_add(hi, lo, bh, bl);
-      }
-      if (lane == 0) out[i] = (double)hi + (double)lo;
-    }
+    for (int w = 1; w < NW; w++) two_sum_add(h, l, red2[w][threadIdx.x][0], red2[w][threadIdx.x][1]);
+    out[threadIdx.x] = (double)h + (double)l;
   }
 }
 
@@ -606,6 +618,22 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
     } else {  // PH_ITER
       T E[4];
       load_E(S.path + 4 * inc, E);
+      // sigma of the RR rows and of the halo row, and the void flags, are
+      // brought into the L2 while the spectrum is staged and transformed
+      // (16 KB pieces, one per lane of warp 0; at L = 4096 the rows of the
+      // CTAs in flight would crowd the L2, and the prefetch is left out)
+      if constexpr (L >= 64 && L <= 2048) {
+        constexpr unsigned RB = (unsigned)(L * 4 * sizeof(T)), PB = RB < 16384u ? RB : 16384u;
+        constexpr int NPR = (int)(RB / PB), NPC = (RR + 1) * NPR;
+        if (wid == 0) {
+          const int xh = (r0 + L - 1) & (L - 1);
+          for (int i = lane; i < NPC; i += 32) {
+            const int k = i / NPR, row = k < RR ? r0 + k : xh;
+            if (ECHK(row, L, 39)) prefetch_l2(reinterpret_cast<const char*>(sin_ + (size_t)4 * row * L) + (size_t)(i % NPR) * PB, PB);
+          }
+          if (lane == 31) prefetch_l2(mask + (size_t)r0 * L, (unsigned)(RR * L));
+        }
+      }
       IO::load_async(sp, spec, r0);
       // halo row x2 = r0 - 1: sigma12 and sigma22 of iterate n for the
       // backward difference along x2; loaded while the spectrum is in
