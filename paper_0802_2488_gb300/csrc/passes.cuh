@@ -190,48 +190,66 @@ struct RowIO {
   // x(x1) = sum_m Y(m) exp(+2 pi i m x1 / L).  Consecutive threads take
   // consecutive k of one sequence.
   static __device__ __forceinline__ void c2r_twist(C2<T>* sp, const C2<T>* __restrict__ oct) {
-    constexpr int NP = M / 2 + 1;
-    for (int e = threadIdx.x; e < NSEQ * NP; e += NT) {
-      const int sq = e / NP, k = e - sq * NP;
-      C2<T>* s = sp + sq * SP;
-      if (k == 0) {
-        const C2<T> s0 = s[0];
-        s[0] = mk(s0.re + s0.im, s0.re - s0.im);
-      } else {
-        const int kk = M - k;
-        const int ik = pad32(k), ikk = pad32(kk);  // 0 < k, kk < M
+    auto pair = [&](int k, int sq0, int ds) {
+      const int kk = M - k;
+      const int ik = pad32(k), ikk = pad32(kk);  // 0 < k, kk < M
+      const C2<T> wk = conj(twist_tw<T, L>(oct, k));
+      for (int sq = sq0; sq < NSEQ; sq += ds) {
+        C2<T>* s = sp + sq * SP;
         if (!ECHK(sq * SP + ikk, SZ, 38) || !ECHK(sq * SP + ik, SZ, 38)) continue;
         const C2<T> a = s[ik], b = s[ikk];
-        const C2<T> wk = conj(twist_tw<T, L>(oct, k));
         // the partner's product conj(wk) (b - conj(a)) equals -conj(t)
         const C2<T> t = wk * (a - conj(b));
         s[ik] = (a + conj(b)) + mul_i(t);
         if (kk != k) s[ikk] = (b + conj(a)) + mul_i(conj(t));
       }
-    }
+    };
+    visit_pairs(pair);
+    pack0(sp);
   }
   // Z = transform of z(n) = x(2n) + i x(2n+1) -> packed half spectrum of x:
   // X(k) = [(Z(k) + Z*(M-k)) - i exp(-2 pi i k / L) (Z(k) - Z*(M-k))] / 2,
   // S(0) = X(0) + i X(M).
   static __device__ __forceinline__ void r2c_twist(C2<T>* sp, const C2<T>* __restrict__ oct) {
-    constexpr int NP = M / 2 + 1;
-    for (int e = threadIdx.x; e < NSEQ * NP; e += NT) {
-      const int sq = e / NP, k = e - sq * NP;
-      C2<T>* s = sp + sq * SP;
-      if (k == 0) {
-        const C2<T> z = s[0];
-        s[0] = mk(z.re + z.im, z.re - z.im);
-      } else {
-        const int kk = M - k;
-        const int ik = pad32(k), ikk = pad32(kk);  // 0 < k, kk < M
+    auto pair = [&](int k, int sq0, int ds) {
+      const int kk = M - k;
+      const int ik = pad32(k), ikk = pad32(kk);  // 0 < k, kk < M
+      const C2<T> wk = twist_tw<T, L>(oct, k);
+      for (int sq = sq0; sq < NSEQ; sq += ds) {
+        C2<T>* s = sp + sq * SP;
         if (!ECHK(sq * SP + ikk, SZ, 38) || !ECHK(sq * SP + ik, SZ, 38)) continue;
         const C2<T> a = s[ik], b = s[ikk];
-        const C2<T> wk = twist_tw<T, L>(oct, k);
         // the partner's product conj(wk) (b - conj(a)) equals -conj(t)
         const C2<T> t = wk * (a - conj(b));
         s[ik] = T(0.5) * ((a + conj(b)) - mul_i(t));
         if (kk != k) s[ikk] = T(0.5) * ((b + conj(a)) - mul_i(conj(t)));
       }
+    };
+    visit_pairs(pair);
+    pack0(sp);
+  }
+  // Calls pair(k, sq0, ds) so that every (sequence, k), k = 1 .. M/2, is
+  // visited once: a thread keeps one k (its twiddle read once) and walks
+  // the sequences sq0, sq0 + ds, ...; consecutive threads take consecutive
+  // k of one sequence.
+  template <typename F>
+  static __device__ __forceinline__ void visit_pairs(F&& pair) {
+    constexpr int HK = M / 2;
+    if constexpr (NT >= HK) {
+      pair(1 + (int)(threadIdx.x % HK), (int)(threadIdx.x / HK), NT / HK);
+    } else {
+#pragma unroll 1
+      for (int k = 1 + (int)threadIdx.x; k <= HK; k += NT) pair(k, 0, 1);
+    }
+  }
+  // Element 0 of each sequence, both ways: (a, b) -> (a + b, a - b) (the
+  // packed X(0), X(M) of the half spectrum and the Z(0) of the transform).
+  // It touches no element of visit_pairs, so no barrier separates them.
+  static __device__ __forceinline__ void pack0(C2<T>* sp) {
+    for (int sq = threadIdx.x; sq < NSEQ; sq += NT) {
+      C2<T>* s = sp + sq * SP;
+      const C2<T> z = s[0];
+      s[0] = mk(z.re + z.im, z.re - z.im);
     }
   }
   // Half-length transforms of all 3 RR sequences, C::G_R per call.
