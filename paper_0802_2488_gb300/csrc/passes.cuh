@@ -163,10 +163,13 @@ struct RowIO {
     if constexpr (PAIRS) {
 #pragma unroll 4
       for (int e2 = threadIdx.x; e2 < 3 * M * RR / 2; e2 += NT) {
-        int is0, is1;
-        size_t ig0, ig1;
+        int is0;
+        size_t ig0;
         where(2 * e2, r0, is0, ig0);
-        where(2 * e2 + 1, r0, is1, ig1);
+        // the pair's second number: w + 1 of the same row (W >= 2, w even,
+        // so b W + w + 1 is no multiple of 32 and the padding adds nothing)
+        // or, for W = 1, the same column of the next row
+        const int is1 = is0 + (W >= 2 ? 1 : SP);
         if (ECHK(is0, SZ, 3) && ECHK(is1, SZ, 3) && ECHK(ig0 + 1, (size_t)3 * M * L, 4) && ECHK(ig0 & 1, 1, 5)) {
           const float2 a = reinterpret_cast<const float2*>(sp)[is0];
           const float2 b = reinterpret_cast<const float2*>(sp)[is1];
@@ -879,7 +882,7 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
     const int w = f / L, m2 = f - w * L;
     const int m1 = b * W + w;
     if (m1 == 0) continue;
-    const int i0 = at(0, w, m2), i1 = at(1, w, m2), i2 = at(2, w, m2);
+    const int i0 = at(0, w, m2), i1 = i0 + W * SP, i2 = i0 + 2 * W * SP;  // components 11, 22, 12
     if (!ECHK(i0, SZ, 31) || !ECHK(i1, SZ, 31) || !ECHK(i2, SZ, 31) || !ECHK(m1, L, 35) || !ECHK(m2, L, 35)) continue;
     C2<T> p11 = sp[i0], p22 = sp[i1], p12 = sp[i2];
     if (GEN) green_op(gm, ktab, qtab, L, m1, m2, lam0, mu0, scale, p11, p22, p12);
@@ -930,8 +933,11 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
       const int e = 2 * e2;
       const int c = e / (L * W);
       const int rem = e - c * (L * W);
-      const int xa = rem / W, wa = rem - xa * W, xb = (rem + 1) / W, wb = rem + 1 - xb * W;
-      const int ia = at(c, wa, xa), ib = at(c, wb, xb);
+      const int xa = rem / W, wa = rem - xa * W;
+      // the pair's second number: column wa + 1 of the same row (W >= 2,
+      // rem even) or row xa + 1 of the column (W = 1, xa even, so xa + 1 is
+      // no multiple of 32 and the padding adds nothing)
+      const int ia = at(c, wa, xa), ib = ia + (W >= 2 ? SP : 1);
       if (ECHK(ia, SZ, 32) && ECHK(ib, SZ, 32) && ECHK((size_t)(c * NBK + b) * L * W + rem + 1, (size_t)3 * M * L, 36)) {
         const float2 u = reinterpret_cast<const float2*>(sp)[ia];
         const float2 v = reinterpret_cast<const float2*>(sp)[ib];
