@@ -52,11 +52,11 @@ struct FftPlan {
 
 // Radix-R DFT in registers: forward kernel exp(-2 pi i r k / R), inverse
 // exp(+2 pi i r k / R); unnormalised.
-template <typename T, int R, bool INV>
+template <typename T, int R, bool INV, bool PK = false>
 struct Bfly;
 
-template <typename T, bool INV>
-struct Bfly<T, 2, INV> {
+template <typename T, bool INV, bool PK>
+struct Bfly<T, 2, INV, PK> {
   static __device__ __forceinline__ void run(C2<T>* v) {
     C2<T> a = v[0], b = v[1];
     v[0] = a + b;
@@ -64,8 +64,8 @@ struct Bfly<T, 2, INV> {
   }
 };
 
-template <typename T, bool INV>
-struct Bfly<T, 4, INV> {
+template <typename T, bool INV, bool PK>
+struct Bfly<T, 4, INV, PK> {
   static __device__ __forceinline__ void run(C2<T>* v) {
     C2<T> a0 = v[0] + v[2], a1 = v[0] - v[2];
     C2<T> a2 = v[1] + v[3], a3 = mul_mi<T, INV>(v[1] - v[3]);
@@ -76,13 +76,49 @@ struct Bfly<T, 4, INV> {
   }
 };
 
-template <typename T, bool INV>
-struct Bfly<T, 8, INV> {
+// FP32 (PK): the same butterflies on packed pairs (re, im) with GB300's two-wide
+// FP32 instructions (one add or FMA on both parts).  A difference x - y is
+// fma(y, -1, x) and the rotation by -+i enters as fma(swap(d), (+-1, -+1), a),
+// each rounded once exactly as the scalar add, so the results are bit-for-bit
+// those of the generic code with about half the arithmetic instructions.
+__device__ __forceinline__ float2 f2(C2<float> a) { return make_float2(a.re, a.im); }
+__device__ __forceinline__ C2<float> c2(float2 a) { return mk(a.x, a.y); }
+
+template <bool INV>
+struct Bfly<float, 2, INV, true> {
+  static __device__ __forceinline__ void run(C2<float>* v) {
+    const float2 a = f2(v[0]), b = f2(v[1]), m1 = make_float2(-1.0f, -1.0f);
+    v[0] = c2(__fadd2_rn(a, b));
+    v[1] = c2(__ffma2_rn(b, m1, a));
+  }
+};
+
+template <bool INV>
+struct Bfly<float, 4, INV, true> {
+  static __device__ __forceinline__ void run(C2<float>* v) {
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 x0 = f2(v[0]), x1 = f2(v[1]), x2 = f2(v[2]), x3 = f2(v[3]);
+    const float2 a0 = __fadd2_rn(x0, x2), a1 = __ffma2_rn(x2, m1, x0);
+    const float2 a2 = __fadd2_rn(x1, x3), d = __ffma2_rn(x3, m1, x1);
+    // a3 = (v1 - v3) times -i (forward: (d.im, -d.re)) or +i (inverse:
+    // (-d.im, d.re)): the swapped d times a sign pair
+    const float2 ds = make_float2(d.y, d.x);
+    const float2 sp = INV ? make_float2(-1.0f, 1.0f) : make_float2(1.0f, -1.0f);
+    const float2 sn = INV ? make_float2(1.0f, -1.0f) : make_float2(-1.0f, 1.0f);
+    v[0] = c2(__fadd2_rn(a0, a2));
+    v[2] = c2(__ffma2_rn(a2, m1, a0));
+    v[1] = c2(__ffma2_rn(ds, sp, a1));
+    v[3] = c2(__ffma2_rn(ds, sn, a1));
+  }
+};
+
+template <typename T, bool INV, bool PK>
+struct Bfly<T, 8, INV, PK> {
   static __device__ __forceinline__ void run(C2<T>* v) {
     C2<T> e[4] = {v[0], v[2], v[4], v[6]};
     C2<T> o[4] = {v[1], v[3], v[5], v[7]};
-    Bfly<T, 4, INV>::run(e);
-    Bfly<T, 4, INV>::run(o);
+    Bfly<T, 4, INV, PK>::run(e);
+    Bfly<T, 4, INV, PK>::run(o);
     const T h = T(0.70710678118654752440084436210485);
     // o[k] times exp(-+ i pi k / 4), k = 1, 2, 3
     C2<T> t1 = INV ? mk(h * (o[1].re - o[1].im), h * (o[1].re + o[1].im))
@@ -110,8 +146,8 @@ __device__ __forceinline__ C2<T> rot_k(C2<T> a, T c, T sn) {
 
 // Radix 16 as 4 x 4: DFT4 over n1 of x[4 n1 + n2], multiplication by
 // exp(-+2 pi i n2 k1 / 16), DFT4 over n2; output index k1 + 4 k2.
-template <typename T, bool INV>
-struct Bfly<T, 16, INV> {
+template <typename T, bool INV, bool PK>
+struct Bfly<T, 16, INV, PK> {
   static __device__ __forceinline__ void run(C2<T>* v) {
     C2<T> y[4][4];  // y[n2][k1]
 #pragma unroll
@@ -120,7 +156,7 @@ struct Bfly<T, 16, INV> {
       y[n2][1] = v[4 + n2];
       y[n2][2] = v[8 + n2];
       y[n2][3] = v[12 + n2];
-      Bfly<T, 4, INV>::run(y[n2]);
+      Bfly<T, 4, INV, PK>::run(y[n2]);
     }
     const T c1 = T(0.92387953251128675612818318939678828682);  // cos(pi/8)
     const T s1 = T(0.38268343236508977172845998403039886676);  // sin(pi/8)
@@ -138,7 +174,7 @@ struct Bfly<T, 16, INV> {
 #pragma unroll
     for (int k1 = 0; k1 < 4; k1++) {
       C2<T> z[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
-      Bfly<T, 4, INV>::run(z);
+      Bfly<T, 4, INV, PK>::run(z);
 #pragma unroll
       for (int k2 = 0; k2 < 4; k2++) v[k1 + 4 * k2] = z[k2];
     }
@@ -236,7 +272,9 @@ __device__ __forceinline__ void stockham_stage(C2<T>* s, const C2<T>* __restrict
 #pragma unroll
         for (int r = 1; r < R; r++) v[q][r] = v[q][r] * w[r];
       }
-      Bfly<T, R, INV>::run(v[q]);
+      // packed FP32 pairs for transforms up to 2048 points (at 4096 the
+      // scalar form schedules better; both give the same bits)
+      Bfly<T, R, INV, sizeof(T) == 4 && N <= 2048>::run(v[q]);
     }
   }
   __syncthreads();
