@@ -639,11 +639,12 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
     } else {  // PH_ITER
       T E[4];
       load_E(S.path + 4 * inc, E);
+      IO::load_async(sp, spec, r0);
       // sigma of the RR rows and of the halo row, and the void flags, are
-      // brought into the L2 while the spectrum is staged and transformed
-      // (16 KB pieces, one per lane of warp 0; at L = 4096 the rows of the
-      // CTAs in flight would crowd the L2, and the prefetch is left out)
-      if constexpr (L >= 64 && L <= 2048) {
+      // brought into the L2 while the spectrum is transformed (16 KB pieces,
+      // one per lane of warp 0, issued after the spectrum copies so that
+      // those go first)
+      if constexpr (L >= 64) {
         constexpr unsigned RB = (unsigned)(L * 4 * sizeof(T)), PB = RB < 16384u ? RB : 16384u;
         constexpr int NPR = (int)(RB / PB), NPC = (RR + 1) * NPR;
         if (wid == 0) {
@@ -655,7 +656,6 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
           if (lane == 31) prefetch_l2(mask + (size_t)r0 * L, (unsigned)(RR * L));
         }
       }
-      IO::load_async(sp, spec, r0);
       // halo row x2 = r0 - 1: sigma12 and sigma22 of iterate n for the
       // backward difference along x2; loaded while the spectrum is in
       // flight when the registers allow (few pixels per thread), else after
