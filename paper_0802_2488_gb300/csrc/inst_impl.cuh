@@ -22,6 +22,11 @@ static bool shape_of(PassShape* o) {
   return true;
 }
 
+// Column-pass CTAs resident on the GPU at once, per lattice side (index
+// log2 L), measured at preparation: a CTA prefetches the slab of the CTA
+// that many places after it in launch order.
+static int g_col_succ[16];
+
 template <typename T, int L>
 static cudaError_t prepare_L() {
   using C = Cfg<T, L, EPFFT_VAR>;
@@ -30,6 +35,14 @@ static cudaError_t prepare_L() {
   if ((e = cudaFuncSetAttribute(row_pass<T, L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::ROW_SMEM)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(col_pass<T, L, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::COL_SMEM)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(col_pass<T, L, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::COL_SMEM)) != cudaSuccess) return e;
+  {
+    int dev = 0, nsm = 0, occ = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, col_pass<T, L, V, false>, C::NT_COL, C::COL_SMEM)) != cudaSuccess)
+      return e;
+    g_col_succ[ilog2c(L)] = nsm * occ;
+  }
   if ((e = cudaFuncSetAttribute(row_forward<T, L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::ROW_SMEM)) != cudaSuccess) return e;
   return cudaFuncSetAttribute(row_inverse<T, L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::ROW_SMEM);
 }
@@ -82,9 +95,9 @@ cudaError_t launch_col_v<EPFFT_REAL, EPFFT_VAR>(int L, int nb, cudaStream_t s, S
     const C2<EPFFT_REAL>* tw_ = reinterpret_cast<const C2<EPFFT_REAL>*>(tw);                         \
     const C2<EPFFT_REAL>* k_ = reinterpret_cast<const C2<EPFFT_REAL>*>(ktab);                        \
     if (general)                                                                                     \
-      col_pass<EPFFT_REAL, n, EPFFT_VAR, true><<<grid, C::NT_COL, C::COL_SMEM, s>>>(solves, tw_, k_, cond, use_cond); \
+      col_pass<EPFFT_REAL, n, EPFFT_VAR, true><<<grid, C::NT_COL, C::COL_SMEM, s>>>(solves, tw_, k_, cond, use_cond, g_col_succ[ilog2c(n)]); \
     else                                                                                             \
-      col_pass<EPFFT_REAL, n, EPFFT_VAR, false><<<grid, C::NT_COL, C::COL_SMEM, s>>>(solves, tw_, k_, cond, use_cond); \
+      col_pass<EPFFT_REAL, n, EPFFT_VAR, false><<<grid, C::NT_COL, C::COL_SMEM, s>>>(solves, tw_, k_, cond, use_cond, g_col_succ[ilog2c(n)]); \
     return cudaGetLastError();                                                                       \
   }
     EPFFT_FOR_L(X)

@@ -832,7 +832,7 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
 template <typename T, int L, int V, bool GEN>
 __global__ void __launch_bounds__(Cfg<T, L, V>::NT_COL, Cfg<T, L, V>::MINB_COL)
 col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* __restrict__ ktab,
-         cudaGraphConditionalHandle cond, int use_cond) {
+         cudaGraphConditionalHandle cond, int use_cond, int succ) {
   using C = Cfg<T, L, V>;
   constexpr int W = C::W, NT = C::NT_COL, M = C::M, NBK = M / W, SP = C::SP_C, SZ = C::COL_DATA;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -866,6 +866,25 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
     const int i = at(c, w, x2);
     const size_t g = (size_t)(c * NBK + b) * L * W + rem;
     if (ECHK(i, SZ, 30) && ECHK(g, (size_t)3 * M * L, 34)) cp_async_c2(sp + i, spec + g);
+  }
+  // the slab of the CTA that follows this one on an SM (succ = the CTAs the
+  // GPU holds at once, counted in launch order) is asked of the L2 while
+  // this CTA transforms its own, in 16 KB pieces by warp 0
+  if (tid < 32 && succ > 0) {
+    const long long nxt = (long long)blockIdx.y * gridDim.x + blockIdx.x + succ;
+    if (nxt < (long long)gridDim.x * gridDim.y) {
+      const int bs = (int)(nxt % gridDim.x), ss = (int)(nxt / gridDim.x);
+      const volatile Solve& Sn = solves[ss];
+      if (Sn.phase == PH_ITER) {
+        constexpr unsigned SB = (unsigned)(L * W * sizeof(C2<T>)), PB = SB < 16384u ? SB : 16384u;
+        constexpr int NPS = (int)(SB / PB);
+        const char* sn = reinterpret_cast<const char*>(solves[ss].spec);
+        for (int k = tid; k < 3 * NPS; k += 32) {
+          const int c = k / NPS;
+          if (ECHK(bs, NBK, 35)) prefetch_l2(sn + ((size_t)(c * NBK + bs) * L * W) * sizeof(C2<T>) + (size_t)(k % NPS) * PB, PB);
+        }
+      }
+    }
   }
   cp_async_wait_all();
   __syncthreads();
