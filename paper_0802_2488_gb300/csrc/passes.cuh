@@ -767,10 +767,11 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
           update(r, j, x1, vv[j], sg[j], l11, l12);
         }
       };
-      // When the rows' strains fit in 32 registers per thread, all of them
-      // are loaded before the first row is processed (their latencies
-      // overlap); otherwise row by row (P loads in flight per thread).
-      constexpr bool PRE = RR * P * 4 * (int)sizeof(T) <= 128;
+      // When the rows' stresses fit in fewer than 32 registers per thread,
+      // all of them are loaded before the first row is processed (their
+      // latencies overlap); otherwise row by row (P loads in flight per
+      // thread, from the L2 where the prefetch above put them).
+      constexpr bool PRE = RR * P * 4 * (int)sizeof(T) < 128;
       if constexpr (PRE) {
         T pen[RR][P][4];
         bool pvv[RR][P];
