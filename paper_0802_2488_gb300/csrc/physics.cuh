@@ -70,12 +70,14 @@ __device__ __forceinline__ double rsq<double>(double x) {
   return y;
 }
 
-// 1/x for x > 0 in normal FP32 range.  FP32: IEEE division.  FP64: the FP32
-// reciprocal refined by two Newton-Raphson steps r <- r + r (1 - x r).
+// 1/x for x > 0 in normal FP32 range.  FP32: the fast reciprocal (within
+// 2 ulp; the one use, the determinant of the 2x2 acoustic tensor, is at
+// least mu0 (lambda0 + 2 mu0) |k|^4 > 0).  FP64: the FP32 reciprocal
+// refined by two Newton-Raphson steps r <- r + r (1 - x r).
 template <typename T>
 __device__ __forceinline__ T rcp(T x);
 template <>
-__device__ __forceinline__ float rcp<float>(float x) { return 1.0f / x; }
+__device__ __forceinline__ float rcp<float>(float x) { return __fdividef(1.0f, x); }
 template <>
 __device__ __forceinline__ double rcp<double>(double x) {
   double r = (double)__frcp_rn((float)x);
