@@ -45,9 +45,9 @@ L2_FLUSH_BYTES = 512 << 20
 # (profiles/passes_dram_traffic.md); a configuration not listed, or one
 # whose kernel changed after the capture, reports null.
 TRAFFIC = {
-    ("row_pass<double,256>", 1, 1): 3830272,
-    ("row_pass<float,512>", 0, 64): 1174515200,
-    ("row_pass<float,4096>", 0, 1): 1227824640,
+    ("row_pass<double,256>", 1, 1): 3828992,
+    ("row_pass<float,512>", 0, 64): 1170303232,
+    ("row_pass<float,4096>", 0, 1): 1238855168,
 }
 
 
