@@ -281,12 +281,35 @@ class Fields:
     labels: Optional[np.ndarray] = None    # (n_inc, L, L) int32
 
 
+def _c_fields(f: Fields):
+    return _Fields(f.eps.ctypes.data, f.plastic.ctypes.data, f.labels.ctypes.data, 0, 0)
+
+
 def _host_fields(prob: Problem, n_inc: int):
     L = prob.L
     f = Fields(np.empty((L, L, 4), dtype=prob.real_dtype), np.empty((n_inc, L, L), np.uint8),
                np.empty((n_inc, L, L), np.int32))
-    cf = _Fields(f.eps.ctypes.data, f.plastic.ctypes.data, f.labels.ctypes.data, 0, 0)
-    return f, cf
+    return f, _c_fields(f)
+
+
+def pinned_fields(problem: Problem, n_inc: int) -> Fields:
+    """Host output buffers of one solve in page-locked memory (torch's
+    pinned allocator), for reuse across calls through `out=`: copies into
+    them run at the link's rate instead of through a staging buffer."""
+    import torch
+    L = problem.L
+    tdt = torch.float64 if problem.precision == "fp64" else torch.float32
+
+    def arr(shape, dt):
+        return torch.empty(shape, dtype=dt, pin_memory=True).numpy()
+    return Fields(arr((L, L, 4), tdt), arr((n_inc, L, L), torch.uint8), arr((n_inc, L, L), torch.int32))
+
+
+def _check_out(f: Fields, prob: Problem, n_inc: int):
+    L = prob.L
+    assert f.eps.shape == (L, L, 4) and f.eps.dtype == prob.real_dtype and f.eps.flags["C_CONTIGUOUS"]
+    assert f.plastic.shape == (n_inc, L, L) and f.plastic.dtype == np.uint8 and f.plastic.flags["C_CONTIGUOUS"]
+    assert f.labels.shape == (n_inc, L, L) and f.labels.dtype == np.int32 and f.labels.flags["C_CONTIGUOUS"]
 
 
 def epfft_solve(ctx: Context, problem: Problem, path, fields: bool = False):
@@ -390,9 +413,12 @@ def epfft_average5(ctx: Context, L: int, precision: str, eps_in, eps_out):
                                 eps_in.data_ptr(), eps_out.data_ptr()), "epfft_average5")
 
 
-def epfft_solve_batch(ctx: Context, problems: Sequence[Problem], paths: Sequence, fields: bool = False):
+def epfft_solve_batch(ctx: Context, problems: Sequence[Problem], paths: Sequence, fields: bool = False,
+                      out: Optional[Sequence[Fields]] = None):
     """Blocking solve of problems sharing L and precision, advanced together
-    in one device loop.  Returns (rc, [records][, [Fields]])."""
+    in one device loop.  Returns (rc, [records][, [Fields]]).  With fields,
+    `out` may give the host buffers to fill (one Fields per problem, e.g.
+    from pinned_fields); otherwise new arrays are allocated."""
     n = len(problems)
     cps, keeps = zip(*(p._c() for p in problems))
     arr = (_Problem * n)(*cps)
@@ -401,7 +427,13 @@ def epfft_solve_batch(ctx: Context, problems: Sequence[Problem], paths: Sequence
     recs = [np.zeros(x[0].n_inc, dtype=RECORD_DTYPE) for x in pth]
     rptr = (C.c_void_p * n)(*(r.ctypes.data for r in recs))
     if fields:
-        fl = [_host_fields(problems[i], pth[i][0].n_inc) for i in range(n)]
+        if out is not None:
+            assert len(out) == n
+            for i in range(n):
+                _check_out(out[i], problems[i], pth[i][0].n_inc)
+            fl = [(out[i], _c_fields(out[i])) for i in range(n)]
+        else:
+            fl = [_host_fields(problems[i], pth[i][0].n_inc) for i in range(n)]
         farr = (_Fields * n)(*(x[1] for x in fl))
     rc = lib().epfft_solve_batch(ctx.handle, n, arr, carr, rptr, farr if fields else None)
     _check(rc, "epfft_solve_batch", (EPFFT_OK, EPFFT_NOT_CONVERGED))
