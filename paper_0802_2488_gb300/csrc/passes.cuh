@@ -10,12 +10,14 @@
 // pass CTA reads RR * W contiguous complex numbers per slab.
 //
 // Row pass (iteration n -> n+1, one CTA per RR rows):
-//   inverse row transform of e^{n+1} -> pixelwise: sigma(eps^n) (kept for the
-//   residual of eps^n), tau = sigma(eps^n) + C0:e^{n+1}, local step ->
-//   eps^{n+1}, p^{n+1} = sigma(eps^{n+1}) - C0:eps^{n+1} -> forward row
-//   transform.  The residual of eps^n (backward divergence of Eq. 1 with a
-//   halo row) and the means are reduced in FP64 per CTA; the last CTA of a
-//   solve finalizes the indicators of Sec. 2 and advances the solve.
+//   inverse row transform of e^{n+1} -> pixelwise: sigma^n (the multiplier,
+//   stored by the pass that produced eps^n), tau = sigma^n + C0:e^{n+1},
+//   local step -> eps^{n+1} and its stress sigma^{n+1} (both stored),
+//   p^{n+1} = sigma^{n+1} - C0:eps^{n+1} -> forward row transform.  The
+//   residual of iterate n (backward divergence of Eq. 1 of sigma^n, with a
+//   halo row) and the means are summed per CTA (FP64, or error-free FP32
+//   pairs promoted to FP64); the last CTA of a solve finalizes the
+//   indicators of Sec. 2 and advances the solve.
 // Column pass (one CTA per W columns): forward column transform, the Green
 //   operator of Eq. 3 per frequency (scaled by 1/L^2, mean strain at q = 0),
 //   inverse column transform.
