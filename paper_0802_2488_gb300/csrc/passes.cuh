@@ -59,17 +59,17 @@ struct Cfg {
   // resident CTAs per SM asked of the compiler: FP32 variant 1 (at most 128
   // registers per thread at 256 threads), the FP32 L = 512 row pass of
   // variant 0 (64 registers at 512 threads, no spills) and the FP32 column
-  // passes of the narrow tiles of variant 0 at L = 512 .. 2048: four CTAs
-  // of 192 threads at L = 512 (85 registers, no spills), three of 384 at
+  // passes of the narrow tiles of variant 0 at L = 512 .. 2048: 768 threads
+  // per SM at L = 512 (85 registers, no spills), three CTAs of 384 at
   // L = 1024 and 2048 (56 registers), so that the CTAs of an SM overlap
   // their loads with the others' transforms
   static constexpr int MINB_ROW = !F64 && (V == 1 || L == 512) ? 2 : 1;
-  static constexpr int MINB_COL = F64 ? 1
-                                      : V == 1 ? 2 : (L == 512 ? 4 : (L == 1024 || L == 2048 ? 3 : 1));
   static constexpr int NT_ROW0 = F64 ? (L > 512 ? 256 : (L < 128 ? L : 128)) : (L <= 256 ? L : NTMAX);
   static constexpr int NT_ROW = NT_ROW0 < 32 ? 32 : NT_ROW0;
   static constexpr int NT_COL0 = ((3 * W * L / RM_COL + 31) / 32) * 32;
   static constexpr int NT_COL = NT_COL0 < 32 ? 32 : (NT_COL0 > NTMAX ? NTMAX : NT_COL0);
+  static constexpr int MINB_COL = F64 ? 1
+                                      : V == 1 ? 2 : (L == 512 ? 768 / NT_COL : (L == 1024 || L == 2048 ? 3 : 1));
   // sequences transformed per call: the largest divisor of the sequence
   // count that keeps at most 16 elements per thread and stage
   static constexpr int grp(int S, int N, int NT) {
