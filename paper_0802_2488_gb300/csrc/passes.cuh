@@ -736,19 +736,23 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
       // lane 31 of the previous pixel group of its warp (the run is
       // contiguous), and at the start of a run reads sigma at x - e^1
       // (periodic) from memory.
-      auto row = [&](int r, T (&sg)[P][4], bool (&vv)[P]) {
-        T run11 = T(0), run12 = T(0);  // sigma11, sigma12 of lane 31, previous group
+      // A row is processed in chunks of PC pixels per thread (j = j0 ..
+      // j0 + PC - 1); run11, run12 carry sigma11, sigma12 of lane 31 of the
+      // previous pixel group from chunk to chunk.
+      constexpr int PC = P < 8 ? P : 8;
+      auto row = [&](int r, int j0, T (&sg)[PC][4], bool (&vv)[PC], T& run11, T& run12) {
 #pragma unroll
-        for (int j = 0; j < P; j++) {
+        for (int jj = 0; jj < PC; jj++) {
+          const int j = j0 + jj;
           const int x1 = xmap(j);
           T l11, l12;
           if constexpr (L < 32) {
             const int src = (lane + L - 1) & (L - 1);
-            l11 = __shfl_sync(0xffffffffu, sg[j][0], src);
-            l12 = __shfl_sync(0xffffffffu, sg[j][3], src);
+            l11 = __shfl_sync(0xffffffffu, sg[jj][0], src);
+            l12 = __shfl_sync(0xffffffffu, sg[jj][3], src);
           } else {
-            l11 = __shfl_up_sync(0xffffffffu, sg[j][0], 1);
-            l12 = __shfl_up_sync(0xffffffffu, sg[j][3], 1);
+            l11 = __shfl_up_sync(0xffffffffu, sg[jj][0], 1);
+            l12 = __shfl_up_sync(0xffffffffu, sg[jj][3], 1);
             if (lane == 0) {
               if (j > 0) {
                 l11 = run11;
@@ -763,18 +767,20 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
                 }
               }
             }
-            run11 = __shfl_sync(0xffffffffu, sg[j][0], 31);
-            run12 = __shfl_sync(0xffffffffu, sg[j][3], 31);
+            run11 = __shfl_sync(0xffffffffu, sg[jj][0], 31);
+            run12 = __shfl_sync(0xffffffffu, sg[jj][3], 31);
           }
-          update(r, j, x1, vv[j], sg[j], l11, l12);
+          update(r, j, x1, vv[jj], sg[jj], l11, l12);
         }
       };
       // When the rows' stresses fit in fewer than 32 registers per thread,
       // all of them are loaded before the first row is processed (their
-      // latencies overlap); otherwise row by row (P loads in flight per
-      // thread, from the L2 where the prefetch above put them).
+      // latencies overlap); otherwise a row is loaded chunk by chunk (PC
+      // loads in flight per thread, from the L2 where the prefetch above
+      // put them).
       constexpr bool PRE = RR * P * 4 * (int)sizeof(T) < 128;
       if constexpr (PRE) {
+        static_assert(PC == P, "one chunk per row");
         T pen[RR][P][4];
         bool pvv[RR][P];
 #pragma unroll
@@ -782,14 +788,21 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
 #pragma unroll
           for (int j = 0; j < P; j++) load_px(r, j, pen[r][j], pvv[r][j]);
 #pragma unroll
-        for (int r = 0; r < RR; r++) row(r, pen[r], pvv[r]);
+        for (int r = 0; r < RR; r++) {
+          T run11 = T(0), run12 = T(0);
+          row(r, 0, pen[r], pvv[r], run11, run12);
+        }
       } else {
         for (int r = 0; r < RR; r++) {
-          T en[P][4];
-          bool vv[P];
+          T run11 = T(0), run12 = T(0);
 #pragma unroll
-          for (int j = 0; j < P; j++) load_px(r, j, en[j], vv[j]);
-          row(r, en, vv);
+          for (int j0 = 0; j0 < P; j0 += PC) {
+            T en[PC][4];
+            bool vv[PC];
+#pragma unroll
+            for (int jj = 0; jj < PC; jj++) load_px(r, j0 + jj, en[jj], vv[jj]);
+            row(r, j0, en, vv, run11, run12);
+          }
         }
       }
     }
