@@ -79,6 +79,25 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(vals, device=None):
+    """Elementwise maximum of the floats `vals` over the ranks of the default
+    process group (the slowest replica's times); the values themselves when
+    there is one rank or no group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in vals]
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_value(ws: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput of ws replicas of the same workload: the units
+    all ranks processed over the slowest rank's time."""
+    return ws * units_per_rank / seconds
+
+
 def workload(name: str, cap: int):
     """The problems of one step and the config block of the JSON line."""
     from paper_0802_2488_gb300 import inputs
@@ -402,12 +421,8 @@ def main():
                      "dtype": "f32 fields and FFTs, f64 reductions"}
 
     t_step = dev_s / args.steps
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_step, dev_s, e2e_s], dtype=torch.float64, device=local)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step, dev_s, e2e_s = tt.tolist()
-    value = ws * pix_its / dev_s
+    t_step, dev_s, e2e_s = max_over_ranks([t_step, dev_s, e2e_s], device=torch.device(f"cuda:{local}"))
+    value = job_value(ws, pix_its, dev_s)
     if rank == 0:
         lg = int(np.log2(L))
         nb = len(probs)
@@ -446,9 +461,9 @@ def main():
             "data": "synthetic",
             "config": dict(cfg, l2="flushed between steps (512 MiB write, outside the step events)",
                            parallelism="replicas" if ws > 1 else "single GPU",
-                           solves_per_s=ws * args.steps * len(probs) / dev_s, precision=args.precision),
+                           solves_per_s=job_value(ws, args.steps * len(probs), dev_s), precision=args.precision),
             "roofline": roof,
-            "e2e": {"value": ws * e2e_its / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_value(ws, e2e_its, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clocks,
