@@ -91,6 +91,7 @@ def lib():
         L.orc_green_mode.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, _D]
         L.orc_green_apply.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, _D, _VP, _VP]
         L.orc_avg5.argtypes = [C.c_int, _D, _D]
+        L.orc_displacement.argtypes = [C.c_int, _D, _D]
         L.orc_sigma_field.argtypes = [C.c_int64, _D, _U8, C.POINTER(Material), _D, _VP]
         L.orc_local_field.argtypes = [C.c_int64, _D, _U8, C.POINTER(Material), _D, _VP]
         L.orc_al_step.argtypes = [C.c_int, _U8, C.POINTER(Material), _D, _D, _D, _VP, _VP]
@@ -472,3 +473,17 @@ def eps_eq(eps: np.ndarray) -> np.ndarray:
     m = (e[..., 0] + e[..., 1] + e[..., 2]) / 3.0
     d = (e[..., 0] - m) ** 2 + (e[..., 1] - m) ** 2 + (e[..., 2] - m) ** 2 + 2.0 * e[..., 3] ** 2
     return np.sqrt(2.0 / 3.0 * d)
+
+
+def displacement(eps: np.ndarray) -> np.ndarray:
+    """Displacement field (L, L, 2) of an in-plane strain field (L, L, 4) by
+    the formula of Sec. 2 (u(q) from eps(q) with k^2 = k1^2 + k2^2, zero mean;
+    at the two frequencies where k^2 vanishes the same relation is inverted
+    with |k|^2, see oracle.c)."""
+    e = np.ascontiguousarray(eps, dtype=np.float64)
+    L = e.shape[0]
+    assert e.shape == (L, L, 4)
+    _check_L(L)
+    u = np.empty((L, L, 2))
+    lib().orc_displacement(L, e, u)
+    return u

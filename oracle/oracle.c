@@ -37,6 +37,7 @@
  *                               symmetrized DG1 operator (equation after
  *                               Eq. 3).
  *   orc_avg5                  : the 5-point local average of CG2 (Sec. 2).
+ *   orc_displacement          : the displacement field of a strain field (Sec. 2).
  *   orc_sigma                 : elastic-perfectly plastic Mises law under
  *                               deformation theory (Sec. 2, Sec. 3: plastic
  *                               zone where sigma_eq = Y, voids sigma = 0).
@@ -748,6 +749,62 @@ void orc_local_field(int64_t n, const double *tau, const uint8_t *mask,
 /* The local average of CG2 (Sec. 2): every pixel of a field of 4 reals per
  * pixel receives the mean of its own value and those of its four nearest
  * neighbours (periodic lattice). */
+/* Displacement of Sec. 2 from the in-plane strain: with k^2 = k1^2 + k2^2
+ * (the discrete symbols of Eq. 2, squared as complex numbers),
+ *   u1(q) = -(i / k^2) { k1 [e11 - e22] + 2 k2 e12 },
+ *   u2(q) =  (i / k^2) { k2 [e11 - e22] - 2 k1 e12 },
+ * and u(0) = 0 (the mode q = 0 is irrelevant).  k^2 vanishes at
+ * q = (pi/2, 3pi/2) and (3pi/2, pi/2) (m = (L/4, 3L/4), (3L/4, L/4) when 4
+ * divides L), where the formula is 0/0 for a compatible strain; there u is
+ * taken from the same relation e_ab = (i/2)(k_a u_b + k_b u_a) solved with
+ * the real |k|^2 = |k1|^2 + |k2|^2: w_b = k*_a e_ab, s = k*.u =
+ * -i (k*.w) / |k|^2, u_b = (-2 i w_b - k_b s) / |k|^2.  eps: L*L*4
+ * (11, 22, 33, 12) at [x2][x1]; u: L*L*2 (u1, u2). */
+void orc_displacement(int L, const double *eps, double *u) {
+  int64_t n = (int64_t)L * L;
+  cplx *e = (cplx *)malloc(sizeof(cplx) * 5 * n);
+  cplx *e11 = e, *e22 = e + n, *e12 = e + 2 * n, *u1 = e + 3 * n, *u2 = e + 4 * n;
+  for (int64_t x = 0; x < n; x++) {
+    e11[x] = eps[4 * x + 0];
+    e22[x] = eps[4 * x + 1];
+    e12[x] = eps[4 * x + 3];
+  }
+  orc_fft2(e11, L, -1);
+  orc_fft2(e22, L, -1);
+  orc_fft2(e12, L, -1);
+  for (int m2 = 0; m2 < L; m2++)
+    for (int m1 = 0; m1 < L; m1++) {
+      int64_t f = (int64_t)m2 * L + m1;
+      if (m1 == 0 && m2 == 0) {
+        u1[f] = 0.0;
+        u2[f] = 0.0;
+        continue;
+      }
+      cplx k1 = ksym(m1, L), k2 = ksym(m2, L);
+      int zero_k2 = (L % 4 == 0) && ((m1 == L / 4 && m2 == 3 * L / 4) || (m1 == 3 * L / 4 && m2 == L / 4));
+      if (!zero_k2) {
+        cplx kk = k1 * k1 + k2 * k2;
+        cplx d = e11[f] - e22[f];
+        u1[f] = -I / kk * (k1 * d + 2.0 * k2 * e12[f]);
+        u2[f] = I / kk * (k2 * d - 2.0 * k1 * e12[f]);
+      } else {
+        double nk = creal(k1 * conj(k1) + k2 * conj(k2));
+        cplx w1 = conj(k1) * e11[f] + conj(k2) * e12[f];
+        cplx w2 = conj(k1) * e12[f] + conj(k2) * e22[f];
+        cplx sdot = -I * (conj(k1) * w1 + conj(k2) * w2) / nk;
+        u1[f] = (-2.0 * I * w1 - k1 * sdot) / nk;
+        u2[f] = (-2.0 * I * w2 - k2 * sdot) / nk;
+      }
+    }
+  orc_fft2(u1, L, +1);
+  orc_fft2(u2, L, +1);
+  for (int64_t x = 0; x < n; x++) {
+    u[2 * x + 0] = creal(u1[x]) / (double)n;
+    u[2 * x + 1] = creal(u2[x]) / (double)n;
+  }
+  free(e);
+}
+
 void orc_avg5(int L, const double *in, double *out) {
   for (int x2 = 0; x2 < L; x2++)
     for (int x1 = 0; x1 < L; x1++) {
