@@ -258,6 +258,21 @@ int epfft_empirical_curve(int32_t n_inc, const double *ind, const int32_t *stats
  * pointers: eps L*L*4 reals, out L*L reals of `precision`.  Blocking. */
 int epfft_eps_eq(epfft_ctx *ctx, int32_t L, int32_t precision, const void *eps_dev, void *out_dev);
 
+/* Displacement field of Sec. 2 from a strain field: per frequency q != 0,
+ * with k^2 = k1^2 + k2^2 (the symbols k_j of Eq. 2 squared as complex
+ * numbers),
+ *   u1(q) = -(i / k^2) { k1 [eps11 - eps22] + 2 k2 eps12 },
+ *   u2(q) =  (i / k^2) { k2 [eps11 - eps22] - 2 k1 eps12 },
+ * u(0) = 0 (the mode q = 0 is irrelevant).  k^2 vanishes at
+ * q = (pi/2, 3pi/2) and (3pi/2, pi/2) when 4 divides L; there the relation
+ * eps_ab = (i/2)(k_a u_b + k_b u_a) it inverts is solved with
+ * |k|^2 = |k1|^2 + |k2|^2 instead (the same u for a compatible strain).
+ * For a compatible strain (one with a periodic displacement, forward
+ * differences of Eq. 1) u is that displacement less its mean.  Device
+ * pointers: eps L*L*4 reals (11, 22, 33, 12; 33 unused), u L*L*2 reals
+ * (u1, u2) of `precision`, both at [x2][x1].  Blocking. */
+int epfft_displacement(epfft_ctx *ctx, int32_t L, int32_t precision, const void *eps_dev, void *u_dev);
+
 /* CG2 post-processing (Sec. 2): eps_out(x) = mean of eps_in at x and its
  * four nearest neighbours (periodic), per component.  Device pointers,
  * L*L*4 reals of `precision` each, distinct buffers; blocking on the

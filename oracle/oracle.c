@@ -746,9 +746,6 @@ void orc_local_field(int64_t n, const double *tau, const uint8_t *mask,
 /* CG2 post-processing                                                 */
 /* ------------------------------------------------------------------ */
 
-/* The local average of CG2 (Sec. 2): every pixel of a field of 4 reals per
- * pixel receives the mean of its own value and those of its four nearest
- * neighbours (periodic lattice). */
 /* Displacement of Sec. 2 from the in-plane strain: with k^2 = k1^2 + k2^2
  * (the discrete symbols of Eq. 2, squared as complex numbers),
  *   u1(q) = -(i / k^2) { k1 [e11 - e22] + 2 k2 e12 },
@@ -805,6 +802,9 @@ void orc_displacement(int L, const double *eps, double *u) {
   free(e);
 }
 
+/* The local average of CG2 (Sec. 2): every pixel of a field of 4 reals per
+ * pixel receives the mean of its own value and those of its four nearest
+ * neighbours (periodic lattice). */
 void orc_avg5(int L, const double *in, double *out) {
   for (int x2 = 0; x2 < L; x2++)
     for (int x1 = 0; x1 < L; x1++) {

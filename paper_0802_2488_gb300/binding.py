@@ -41,7 +41,7 @@ SYMBOLS = ["epfft_create", "epfft_destroy", "epfft_last_stats", "epfft_strerror"
            "epfft_time_passes", "epfft_project_static", "epfft_serve_open", "epfft_serve_close",
            "epfft_submit", "epfft_serve_step", "epfft_poll", "epfft_autotune", "epfft_set_tiling",
            "epfft_solve_dg2", "epfft_average5", "epfft_void_plastic", "epfft_indicators",
-           "epfft_effective_moduli", "epfft_empirical_curve", "epfft_eps_eq"]
+           "epfft_effective_moduli", "epfft_empirical_curve", "epfft_eps_eq", "epfft_displacement"]
 
 
 class EpfftError(RuntimeError):
@@ -117,6 +117,7 @@ def lib():
                                              C.POINTER(C.c_double)]
         L.epfft_empirical_curve.argtypes = [i32, vp, vp, i32, C.c_double, i32, C.POINTER(C.c_double), vp]
         L.epfft_eps_eq.argtypes = [vp, i32, i32, vp, vp]
+        L.epfft_displacement.argtypes = [vp, i32, i32, vp, vp]
         L.epfft_solve_batch.argtypes = [vp, i32, C.POINTER(_Problem), C.POINTER(_Path), C.POINTER(vp),
                                         C.POINTER(_Fields)]
         L.epfft_mask.argtypes = [i32, dbl, C.c_uint64, vp, vp]
@@ -402,6 +403,18 @@ def epfft_eps_eq(ctx: Context, L: int, precision: str, eps):
     _check(lib().epfft_eps_eq(ctx.handle, L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision],
                               eps.data_ptr(), out.data_ptr()), "epfft_eps_eq")
     return out
+
+
+def epfft_displacement(ctx: Context, L: int, precision: str, eps):
+    """Displacement field (Sec. 2) of a CUDA strain tensor (L, L, 4): a CUDA
+    tensor (L, L, 2) of (u1, u2) with zero mean."""
+    import torch
+    assert eps.is_cuda and eps.is_contiguous() and eps.numel() == 4 * L * L
+    assert eps.dtype == (torch.float64 if precision == "fp64" else torch.float32)
+    u = torch.empty((L, L, 2), dtype=eps.dtype, device=eps.device)
+    _check(lib().epfft_displacement(ctx.handle, L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision],
+                                    eps.data_ptr(), u.data_ptr()), "epfft_displacement")
+    return u
 
 
 def epfft_average5(ctx: Context, L: int, precision: str, eps_in, eps_out):

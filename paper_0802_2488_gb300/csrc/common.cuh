@@ -52,6 +52,8 @@ enum GreenMode : int32_t {
   GM_EQ3 = 0,  // discrete operator of Eq. 3
   GM_CG1 = 1,  // continuum operator: Eq. 3 with k_j = q_j
   GM_DG1 = 2,  // symmetrized operator G^(1)
+  GM_DISP = 3, // not a Green operator: the displacement of Sec. 2 from the
+               // strain spectrum (epfft_displacement only; no solve takes it)
 };
 
 // Solve phases of the per-solve state machine driven on the device.

@@ -1314,6 +1314,52 @@ int epfft_project(epfft_ctx* ctx, int32_t L, int32_t precision, double lambda0, 
   return EPFFT_OK;
 }
 
+int epfft_displacement(epfft_ctx* ctx, int32_t L, int32_t precision, const void* eps_dev, void* u_dev) {
+  if (!ctx || !eps_dev || !u_dev) return EPFFT_ERR_ARG;
+  if (!is_pow2(L) || L < 4 || (precision != EPFFT_FP32 && precision != EPFFT_FP64)) return EPFFT_ERR_ARG;
+  if (!supported(L, precision)) return EPFFT_ERR_UNSUPPORTED;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return EPFFT_ERR_CUDA;
+  Arena A(ctx);
+  void *tw, *ktab;
+  const int var = variant_for(ctx, L, precision, 1);
+  int rc = get_tables(ctx, L, precision, &tw, &ktab);
+  if (!rc) rc = ensure_prepared(ctx, L, precision, var);
+  if (rc) return rc;
+  const size_t LL = (size_t)L * L, rs = real_size(precision);
+  void* planes = A.get(3 * LL * rs);
+  void* spec = A.get(3 * LL * rs);
+  double* dpath = (double*)A.get(4 * sizeof(double));
+  Solve* ds = (Solve*)A.get(sizeof(Solve));
+  if (!planes || !spec || !dpath || !ds) return EPFFT_ERR_OOM;
+  // the column pass in its general form with the displacement operator;
+  // the zero path makes the q = 0 mode zero
+  Solve S;
+  std::memset(&S, 0, sizeof(S));
+  S.lam0 = 1.0;
+  S.mu0 = 1.0;
+  S.green = GM_DISP;
+  S.path = dpath;
+  S.spec = spec;
+  S.phase = PH_ITER;
+  CK(cudaMemsetAsync(dpath, 0, 4 * sizeof(double), ctx->stream));
+  CK(cudaMemcpyAsync(ds, &S, sizeof(S), cudaMemcpyHostToDevice, ctx->stream));
+  if (precision == EPFFT_FP32) {
+    CK(launch_strain_planes<float>((const float*)eps_dev, (float*)planes, L, ctx->stream));
+    CK(launch_row_forward<float>(L, var, ctx->stream, planes, spec, tw));
+    CK(launch_col<float>(L, var, 1, ctx->stream, ds, tw, ktab, 0, 0, 1));
+    CK(launch_row_inverse<float>(L, var, ctx->stream, spec, planes, tw));
+    CK(launch_disp_pairs<float>((const float*)planes, (float*)u_dev, L, ctx->stream));
+  } else {
+    CK(launch_strain_planes<double>((const double*)eps_dev, (double*)planes, L, ctx->stream));
+    CK(launch_row_forward<double>(L, var, ctx->stream, planes, spec, tw));
+    CK(launch_col<double>(L, var, 1, ctx->stream, ds, tw, ktab, 0, 0, 1));
+    CK(launch_row_inverse<double>(L, var, ctx->stream, spec, planes, tw));
+    CK(launch_disp_pairs<double>((const double*)planes, (double*)u_dev, L, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return EPFFT_OK;
+}
+
 int epfft_label(epfft_ctx* ctx, int32_t L, int32_t n_img, const uint8_t* flags_dev, int32_t periodic,
                 int32_t* labels_dev, int32_t* counts) {
   if (!ctx || !is_pow2(L) || L < 2 || L > 4096 || n_img < 1 || !flags_dev || !labels_dev) return EPFFT_ERR_ARG;

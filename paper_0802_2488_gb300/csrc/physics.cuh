@@ -244,6 +244,44 @@ __device__ __forceinline__ void green_apply(C2<T> k1, C2<T> k2, T lam0, T mu0, T
   p12 = T(-0.5) * (k1 * v2 + k2 * v1);
 }
 
+// Displacement of Sec. 2 at frequency (m1, m2) != 0 from the strain
+// spectrum (e11, e22, e12) in (p11, p22, p12): with k^2 = k1^2 + k2^2,
+//   u1 = -(i / k^2) { k1 [e11 - e22] + 2 k2 e12 },
+//   u2 =  (i / k^2) { k2 [e11 - e22] - 2 k1 e12 },
+// returned in (p11, p22) times `scale`, p12 = 0.  Where k^2 vanishes
+// (m = (L/4, 3L/4) and (3L/4, L/4) when 4 divides L) the same relation
+// e_ab = (i/2)(k_a u_b + k_b u_a) is solved with |k|^2 instead:
+// w_b = k*_a e_ab, s = -i (k*.w) / |k|^2, u_b = (-2 i w_b - k_b s) / |k|^2.
+template <typename T>
+__device__ __forceinline__ void disp_apply(C2<T> k1, C2<T> k2, int L, int m1, int m2, T scale, C2<T>& p11,
+                                           C2<T>& p22, C2<T>& p12) {
+  const bool zk = (L % 4 == 0) && ((m1 == L / 4 && m2 == 3 * L / 4) || (m1 == 3 * L / 4 && m2 == L / 4));
+  C2<T> u1, u2;
+  if (!zk) {
+    const C2<T> kk = k1 * k1 + k2 * k2;
+    const T r = scale * rcp(norm2(kk));  // scale / |k^2|^2
+    const C2<T> d = p11 - p22;
+    const C2<T> n1 = k1 * d + T(2) * (k2 * p12), n2 = k2 * d - T(2) * (k1 * p12);
+    // -i n1 / kk = -i n1 conj(kk) / |kk|^2, i n2 / kk likewise
+    const C2<T> a1 = n1 * conj(kk), a2 = n2 * conj(kk);
+    u1 = mk(r * a1.im, -r * a1.re);
+    u2 = mk(-r * a2.im, r * a2.re);
+  } else {
+    const T nk = norm2(k1) + norm2(k2), ri = rcp(nk);
+    const C2<T> w1 = conj(k1) * p11 + conj(k2) * p12, w2 = conj(k1) * p12 + conj(k2) * p22;
+    const C2<T> kw = conj(k1) * w1 + conj(k2) * w2;
+    const C2<T> sd = mk(ri * kw.im, -ri * kw.re);  // -i (k*.w) / |k|^2
+    const C2<T> t1 = k1 * sd, t2 = k2 * sd;
+    // (-2 i w_b - k_b s) / |k|^2, times scale
+    const T sc = scale * ri;
+    u1 = mk(sc * (T(2) * w1.im - t1.re), sc * (T(-2) * w1.re - t1.im));
+    u2 = mk(sc * (T(2) * w2.im - t2.re), sc * (T(-2) * w2.re - t2.im));
+  }
+  p11 = u1;
+  p22 = u2;
+  p12 = mk(T(0), T(0));
+}
+
 // The Green operator `mode` of Sec. 2 at frequency (m1, m2) applied to
 // (p11, p22, p12) in place, times `scale`.  ktab: k(m) of Eq. 2; qtab: the
 // continuum momenta (q~(m), 0) (tables.cuh).
@@ -258,6 +296,10 @@ __device__ __forceinline__ void green_op(int mode, const C2<T>* __restrict__ kta
                                          C2<T>& p12) {
   if (mode == GM_EQ3) {
     green_apply(ktab[m1], ktab[m2], lam0, mu0, scale, p11, p22, p12);
+    return;
+  }
+  if (mode == GM_DISP) {
+    disp_apply(ktab[m1], ktab[m2], L, m1, m2, scale, p11, p22, p12);
     return;
   }
   const C2<T> a11 = p11, a22 = p22, a12 = p12;

@@ -176,6 +176,25 @@ __global__ void eps_eq_kernel(const T* __restrict__ eps, T* __restrict__ out, in
   }
 }
 
+// (L, L, 4) strain -> planes (e11, e22, e12) of L*L each.
+template <typename T>
+__global__ void strain_planes_kernel(const T* __restrict__ eps, T* __restrict__ planes, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    planes[i] = eps[4 * i + 0];
+    planes[n + i] = eps[4 * i + 1];
+    planes[2 * n + i] = eps[4 * i + 3];
+  }
+}
+
+// planes (u1, u2, .) of L*L each -> (L, L, 2) pairs.
+template <typename T>
+__global__ void disp_pairs_kernel(const T* __restrict__ planes, T* __restrict__ u, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    u[2 * i + 0] = planes[i];
+    u[2 * i + 1] = planes[n + i];
+  }
+}
+
 __global__ void count_kernel(const uint8_t* __restrict__ a, int64_t n, int32_t* __restrict__ out) {
   int32_t c = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -270,6 +289,24 @@ cudaError_t launch_eps_eq(const T* eps, T* out, int L, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_strain_planes(const T* eps, T* planes, int L, cudaStream_t s) {
+  const int64_t n = (int64_t)L * L;
+  strain_planes_kernel<T><<<grid_of(n), 256, 0, s>>>(eps, planes, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_disp_pairs(const T* planes, T* u, int L, cudaStream_t s) {
+  const int64_t n = (int64_t)L * L;
+  disp_pairs_kernel<T><<<grid_of(n), 256, 0, s>>>(planes, u, n);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_strain_planes<float>(const float*, float*, int, cudaStream_t);
+template cudaError_t launch_strain_planes<double>(const double*, double*, int, cudaStream_t);
+template cudaError_t launch_disp_pairs<float>(const float*, float*, int, cudaStream_t);
+template cudaError_t launch_disp_pairs<double>(const double*, double*, int, cudaStream_t);
 template cudaError_t launch_eps_eq<float>(const float*, float*, int, cudaStream_t);
 template cudaError_t launch_eps_eq<double>(const double*, double*, int, cudaStream_t);
 template cudaError_t launch_avg5<float>(const float*, float*, int, cudaStream_t);

@@ -37,6 +37,11 @@ cudaError_t launch_vp_attach(const uint8_t* mask, const uint8_t* vp, const int32
 // deviator of (11, 22, 33, 12), e'_12 counted twice.
 template <typename T>
 cudaError_t launch_eps_eq(const T* eps, T* out, int L, cudaStream_t s);
+// (L, L, 4) strain -> planes (e11, e22, e12); planes (u1, u2, .) -> (L, L, 2).
+template <typename T>
+cudaError_t launch_strain_planes(const T* eps, T* planes, int L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_disp_pairs(const T* planes, T* u, int L, cudaStream_t s);
 // *count_dev += number of nonzero bytes of a[0 .. n)
 cudaError_t launch_count(const uint8_t* a, int64_t n, int32_t* count_dev, cudaStream_t s);
 }  // namespace epfft
