@@ -64,6 +64,13 @@ extern "C" {
                            * G(q1,q2), G(-q1,-q2) and the tensor-signed          *
                            * (-1)^(i+j+k+l) G(-q1,q2), G(q1,-q2)                 */
 
+/* Equilibrium test of an increment (epfft_problem.eq_test) */
+#define EPFFT_EQ_OWN 0         /* eta1 (divergence of Eq. 1, Sec. 2) with the     *
+                                * operators of Eq. 3; eta3 with CG1 and DG1      */
+#define EPFFT_EQ_FIXED_POINT 1 /* eta3 with every operator: one criterion, so    *
+                                * that iteration counts of the operators can be  *
+                                * compared (Sec. 2, DG2 against CG1)             */
+
 typedef struct epfft_ctx epfft_ctx;
 
 /* Device memory hook.  alloc returns a device pointer usable on `stream`
@@ -102,7 +109,7 @@ typedef struct {
   double tol_eq;           /* eta1 >= 0                                           */
   double tol_macro;        /* eta2 >= 0                                           */
   int32_t max_iter;        /* >= 1 iterations per increment                       */
-  int32_t reserved;
+  int32_t eq_test;         /* EPFFT_EQ_*; 0 (EPFFT_EQ_OWN) as before              */
 } epfft_problem;
 
 /* Prescribed mean strain per increment, n_inc x (E11, E22, E33, E12), host

@@ -56,7 +56,12 @@ DG2_MEMBERS = (GREEN_EQ3, GREEN_EQ3_M12, GREEN_EQ3_M1, GREEN_EQ3_M2)
 
 class Control(C.Structure):
     _fields_ = [("tol_eq", C.c_double), ("tol_macro", C.c_double),
-                ("max_iter", C.c_int32), ("pad", C.c_int32)]
+                ("max_iter", C.c_int32), ("eq_test", C.c_int32)]
+
+
+# Equilibrium test (values of orc_control.eq_test): each operator's own
+# (eta1 for Eq. 3, eta3 for CG1 and DG1), or eta3 for every operator
+EQ_OWN, EQ_FIXED_POINT = 0, 1
 
 
 class Record(C.Structure):
@@ -327,7 +332,7 @@ class Solution:
 
 
 def solve(mask_: np.ndarray, mat: Material, path: np.ndarray, tol_eq=1e-8, tol_macro=1e-8,
-          max_iter=10000, fields=False) -> Solution:
+          max_iter=10000, fields=False, eq_test=EQ_OWN) -> Solution:
     """Strain-controlled loading by increments (Sec. 2) with the AL scheme;
     path is (n_inc, 4) prescribed mean strains (11, 22, 33, 12)."""
     L = mask_.shape[0]
@@ -339,7 +344,7 @@ def solve(mask_: np.ndarray, mat: Material, path: np.ndarray, tol_eq=1e-8, tol_m
     eps = np.empty((L, L, 4))
     pl = np.empty((n_inc, L, L), dtype=np.uint8) if fields else None
     lab = np.empty((n_inc, L, L), dtype=np.int32) if fields else None
-    st = lib().orc_solve(L, m, C.byref(mat), C.byref(Control(tol_eq, tol_macro, max_iter, 0)),
+    st = lib().orc_solve(L, m, C.byref(mat), C.byref(Control(tol_eq, tol_macro, max_iter, int(eq_test))),
                          n_inc, P, recs, _ptr(eps), _ptr(pl), _ptr(lab))
     arr = np.frombuffer(bytes(recs), dtype=RECORD_DTYPE).copy()
     return Solution(int(st), arr, eps, pl, lab)
@@ -383,7 +388,7 @@ class DG2Solution:
 
 
 def solve_dg2(mask_: np.ndarray, mat: Material, path: np.ndarray, tol_eq=1e-8, tol_macro=1e-8,
-              max_iter=10000) -> DG2Solution:
+              max_iter=10000, eq_test=EQ_OWN) -> DG2Solution:
     """DG2 (Sec. 2): four complete solves with G(q1,q2), G(-q1,-q2),
     G(-q1,q2), G(q1,-q2) in turn; the result is the average of the four
     converged strain fields.  The solve with G at mirrored momenta is the
@@ -396,7 +401,7 @@ def solve_dg2(mask_: np.ndarray, mat: Material, path: np.ndarray, tol_eq=1e-8, t
     indicators are the largest of the four, the iteration counts their sum."""
     sols, fields = [], []
     for ax in DG2_MIRRORS:
-        s = solve(mirror(mask_, ax), mat, mirror_path(path, ax), tol_eq, tol_macro, max_iter)
+        s = solve(mirror(mask_, ax), mat, mirror_path(path, ax), tol_eq, tol_macro, max_iter, eq_test=eq_test)
         sols.append(s)
         fields.append(mirror(s.eps, ax))
     rec = sols[0].records.copy()

@@ -95,8 +95,14 @@ typedef struct {
   double tol_eq;    /* eta_1 */
   double tol_macro; /* eta_2 */
   int32_t max_iter; /* per increment */
-  int32_t pad;
+  int32_t eq_test;  /* ORC_EQ_* below */
 } orc_control;
+
+/* Equilibrium test of an increment */
+enum {
+  ORC_EQ_OWN = 0,         /* eta1 for the operators of Eq. 3, eta3 for CG1, DG1 */
+  ORC_EQ_FIXED_POINT = 1, /* eta3 for every operator (one criterion for all) */
+};
 
 typedef struct {
   double sig_mean[4]; /* <sigma> of the accepted iterate, (11,22,33,12) */
@@ -624,7 +630,9 @@ int32_t orc_label(int L, const uint8_t *flag, int periodic, int32_t *label) {
  *   (<sigma^{n+1}> - <sigma^n>):(same) < eta2^2 <sigma^{n+1}>:<sigma^{n+1}>
  * hold at the same iterate (strict), with sigma = sigma(eps^{n+1}), or
  * max_iter iterations.  eta3 = (<(eps-e):(eps-e)> / E:E)^(1/2) with the
- * full (3D) contraction is reported only.
+ * full (3D) contraction takes the place of eta1 for CG1 and DG1, and for
+ * every operator when ctl->eq_test is ORC_EQ_FIXED_POINT; otherwise it is
+ * reported only.
  * Optional outputs: eps_final (L*L*4), plastic_all / labels_all
  * (n_inc*L*L: plastic flag of the accepted iterate, its periodic clusters).
  * Returns 0 when every increment converged, else the first nonzero status. */
@@ -688,8 +696,12 @@ int32_t orc_solve(int L, const uint8_t *mask, const orc_material *m,
        * operators are not the Green operators of Eq. 1, so the divergence
        * of Eq. 1 does not vanish at their solutions; there the augmented
        * Lagrangian's own fixed-point residual eta3 (local strain minus
-       * compatible strain) takes its place. */
-      const double eq = (m->green == ORC_GREEN_CG1 || m->green == ORC_GREEN_DG1) ? eta3 : eta1;
+       * compatible strain) takes its place.  With ORC_EQ_FIXED_POINT every
+       * operator stops on eta3, so that iteration counts of the operators
+       * are counted against one criterion. */
+      const int fixed_point = ctl->eq_test == ORC_EQ_FIXED_POINT || m->green == ORC_GREEN_CG1 ||
+                              m->green == ORC_GREEN_DG1;
+      const double eq = fixed_point ? eta3 : eta1;
       if (eq < ctl->tol_eq && eta2 < ctl->tol_macro) {
         status = 0;
         break;

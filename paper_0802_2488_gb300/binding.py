@@ -35,6 +35,9 @@ EPFFT_GREEN_EQ3 = 0
 EPFFT_GREEN_CG1 = 1
 EPFFT_GREEN_DG1 = 2
 _GREEN = {"eq3": EPFFT_GREEN_EQ3, "cg1": EPFFT_GREEN_CG1, "dg1": EPFFT_GREEN_DG1}
+EPFFT_EQ_OWN = 0
+EPFFT_EQ_FIXED_POINT = 1
+_EQ_TEST = {"own": EPFFT_EQ_OWN, "fixed_point": EPFFT_EQ_FIXED_POINT}
 
 SYMBOLS = ["epfft_create", "epfft_destroy", "epfft_last_stats", "epfft_strerror", "epfft_supported",
            "epfft_solve", "epfft_solve_batch", "epfft_mask", "epfft_iterate", "epfft_project", "epfft_label",
@@ -65,7 +68,7 @@ class _Problem(C.Structure):
                 ("green", C.c_int32), ("mu", C.c_double), ("lambda_", C.c_double),
                 ("yield_stress", C.c_double), ("mu0", C.c_double), ("lambda0", C.c_double),
                 ("tol_eq", C.c_double), ("tol_macro", C.c_double), ("max_iter", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("eq_test", C.c_int32)]
 
 
 class _Path(C.Structure):
@@ -171,6 +174,7 @@ class Problem:
     tol_macro: float = 1e-8
     max_iter: int = 10000
     green: str = "eq3"               # 'eq3' | 'cg1' | 'dg1' (Sec. 2)
+    eq_test: str = "own"             # 'own' (eta1 for Eq. 3, eta3 for CG1/DG1) | 'fixed_point' (eta3 for all)
 
     def _c(self) -> tuple[_Problem, object]:
         keep = None
@@ -189,7 +193,7 @@ class Problem:
                      _GREEN[self.green], self.mu, self.lambda_, self.yield_stress,
                      self.mu if self.mu0 is None else self.mu0,
                      self.lambda_ if self.lambda0 is None else self.lambda0,
-                     self.tol_eq, self.tol_macro, int(self.max_iter), 0)
+                     self.tol_eq, self.tol_macro, int(self.max_iter), _EQ_TEST[self.eq_test])
         return p, keep
 
     @property

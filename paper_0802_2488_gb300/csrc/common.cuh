@@ -114,8 +114,8 @@ struct Solve {
   float mcf[N_MC];   // the same rounded to FP32
   double tol_eq, tol_macro;
   int32_t max_iter, n_inc;
-  int32_t green;       // Green operator (GreenMode)
-  int32_t pad0;
+  int32_t green;           // Green operator (GreenMode)
+  int32_t eq_fixed_point;  // 1: the equilibrium test is eta3, else eta1
   const double* path;  // n_inc * 4 prescribed mean strains (11,22,33,12)
   Record* rec;         // n_inc records
   uint8_t* flags;      // n_inc * L * L plastic flags (may be null)

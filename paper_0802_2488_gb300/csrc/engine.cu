@@ -186,6 +186,7 @@ int check_problem(const epfft_problem* p) {
   if (!(p->yield_stress > 0.0)) return EPFFT_ERR_ARG;
   if (!(p->tol_eq >= 0.0) || !(p->tol_macro >= 0.0)) return EPFFT_ERR_ARG;
   if (p->max_iter < 1) return EPFFT_ERR_ARG;
+  if (p->eq_test != EPFFT_EQ_OWN && p->eq_test != EPFFT_EQ_FIXED_POINT) return EPFFT_ERR_ARG;
   return EPFFT_OK;
 }
 
@@ -266,6 +267,7 @@ int init_solve(Get&& get, const PassShape& sh, int L, int prec, const epfft_prob
   S.max_iter = p.max_iter;
   S.n_inc = n_inc;
   S.green = p.green;
+  S.eq_fixed_point = p.eq_test == EPFFT_EQ_FIXED_POINT || p.green == EPFFT_GREEN_CG1 || p.green == EPFFT_GREEN_DG1;
   fill_consts(S);
   void* eps0d = get(4 * LL * rs);
   void* eps1d = get(4 * LL * rs);

@@ -480,9 +480,10 @@ __device__ __forceinline__ void finalize_solve(Solve& S, int phase, const double
     const double te2 = S.tol_eq * S.tol_eq, tm2 = S.tol_macro * S.tol_macro;
     const bool pos = ss > 0.0;
     // equilibrium test: eta1 for the operators of Eq. 3; the continuum and
-    // symmetrized operators are not Green operators of Eq. 1, so there the
+    // symmetrized operators are not Green operators of Eq. 1, so there (and
+    // for every operator when the caller asks for one criterion) the
     // fixed-point residual eta3 of the iterate takes its place
-    const bool eq_ok = (S.green == GM_CG1 || S.green == GM_DG1)
+    const bool eq_ok = S.eq_fixed_point
                            ? (comp_n < te2 * EE && S.tol_eq > 0.0)
                            : (pos ? div2 < te2 * ss : S.tol_eq > 0.0);
     const bool conv = finite && eq_ok && (pos ? dd < tm2 * ss : S.tol_macro > 0.0);

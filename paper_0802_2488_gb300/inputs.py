@@ -3,8 +3,9 @@ the oracle's tests.
 
 This module holds no arithmetic of the method: it only states workloads
 (lattice size, void concentration, seed, macroscopic strain path) and draws
-random test states with numpy.  The void mask itself is part of the method
-(each side generates it from the seed), so it is not produced here.
+random test states with numpy.  The random void mask itself is part of the
+method (each side generates it from the seed), so it is not produced here;
+the one-void periodic cell of Fig. 1 is a fixed geometry and is.
 
 Strain tuples are (E11, E22, E33, E12) with E33 = 0 (plane strain) and E12
 the tensor shear component (the paper's simple-shear loading prescribes
@@ -31,20 +32,36 @@ YIELD = 1.0
 EQUIBIAXIAL_YIELD = YIELD / (2.0 * MU)
 SHEAR_YIELD = YIELD / (2.0 * math.sqrt(3.0) * MU)
 
+# The matrix of the paper's own computations (Sec. 2): bulk modulus K = 1,
+# shear modulus mu = 0.4 (so lambda = K - 2 mu / 3), flow stress Y = 0.5.
+PAPER_MU = 0.4
+PAPER_LAMBDA = 1.0 - 2.0 * PAPER_MU / 3.0
+PAPER_YIELD = 0.5
 
-def load_path(mode: str, n_inc: int, multiple: float) -> np.ndarray:
+
+def load_path(mode: str, n_inc: int, multiple: float, mu: float = MU, Y: float = YIELD) -> np.ndarray:
     """(n_inc, 4) prescribed mean strains ramped in equal increments to
     `multiple` x the f = 0 first-yield strain of the loading `mode`
-    ('equibiaxial' or 'shear')."""
+    ('equibiaxial' or 'shear') for a matrix of shear modulus mu and flow
+    stress Y (default: the workloads' matrix)."""
     n = np.arange(1, n_inc + 1, dtype=np.float64) / n_inc
     P = np.zeros((n_inc, 4))
     if mode == "equibiaxial":
-        P[:, 0] = P[:, 1] = n * multiple * EQUIBIAXIAL_YIELD
+        P[:, 0] = P[:, 1] = n * multiple * Y / (2.0 * mu)
     elif mode == "shear":
-        P[:, 3] = n * multiple * SHEAR_YIELD
+        P[:, 3] = n * multiple * Y / (2.0 * math.sqrt(3.0) * mu)
     else:
         raise ValueError(mode)
     return P
+
+
+def one_void_cell(L: int, f: float) -> np.ndarray:
+    """(L, L) uint8 mask of the periodic cell of Fig. 1: one circular void
+    of area fraction about f at the centre of the cell (pixels whose centres
+    lie within radius L (f / pi)^(1/2) of the cell centre are voids)."""
+    c = np.arange(L) + 0.5 - L / 2.0
+    r2 = f * L * L / math.pi
+    return ((c[None, :] ** 2 + c[:, None] ** 2) < r2).astype(np.uint8)
 
 
 @dataclass

@@ -80,3 +80,15 @@ def test_argument_checks_of_analysis_entry_points(lib):
     assert lib.epfft_eps_eq(None, 8, 0, None, None) == B.EPFFT_ERR_ARG
     assert lib.epfft_displacement(None, 8, 0, None, None) == B.EPFFT_ERR_ARG
     assert lib.epfft_effective_moduli(None, None, C.c_double(1e-3), None, None) == B.EPFFT_ERR_ARG
+
+
+def test_binding_constants_match_the_header():
+    """Every integer #define of include/epfft.h that the binding names has
+    the header's value (status codes, precisions, operators, tests)."""
+    src = open(os.path.join(ROOT, "include", "epfft.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(EPFFT_\w+)\s+\(?(-?\d+)\)?", src)}
+    assert "EPFFT_EQ_FIXED_POINT" in defs and "EPFFT_GREEN_DG1" in defs
+    named = [k for k in defs if hasattr(B, k)]
+    assert len(named) >= 10
+    for k in named:
+        assert getattr(B, k) == defs[k], k

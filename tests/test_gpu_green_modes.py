@@ -137,3 +137,26 @@ def test_mixed_operators_in_one_batch_match_solo(ctx):
         _, solo = B.epfft_solve(ctx, p, path)
         np.testing.assert_array_equal(r["iterations"], solo["iterations"])
         np.testing.assert_array_equal(r["sig_mean"], solo["sig_mean"])
+
+
+@pytest.mark.parametrize("medium", ["one_void_cell", "bernoulli"])
+@pytest.mark.parametrize("op", ["eq3", "dg2", "cg1", "dg1"])
+def test_iteration_counts_under_one_criterion(ctx, op, medium):
+    """The iteration-count comparison of Sec. 2 (every operator stopped on
+    eta3 and eta2): the paper's matrix, equibiaxial loading past the yield
+    strain, the one-void cell of Fig. 1 and a Bernoulli lattice; counts equal
+    to the oracle's, macroscopic stress within 1e-10."""
+    L = 32
+    mask = inputs.one_void_cell(L, 0.1) if medium == "one_void_cell" else O.mask(L, 0.1, 0)
+    path = inputs.load_path("equibiaxial", 3, 1.5, inputs.PAPER_MU, inputs.PAPER_YIELD)
+    g = {"eq3": O.GREEN_EQ3, "dg2": O.GREEN_EQ3, "cg1": O.GREEN_CG1, "dg1": O.GREEN_DG1}[op]
+    mat = O.material(lam=inputs.PAPER_LAMBDA, mu=inputs.PAPER_MU, Y=inputs.PAPER_YIELD, green=g)
+    kw = dict(tol_eq=1e-5, tol_macro=1e-5, max_iter=20000, eq_test=O.EQ_FIXED_POINT)
+    ref = (O.solve_dg2 if op == "dg2" else O.solve)(mask, mat, path, **kw).records
+    prob = B.Problem(L=L, precision="fp64", mask=mask, mu=inputs.PAPER_MU, lambda_=inputs.PAPER_LAMBDA,
+                     yield_stress=inputs.PAPER_YIELD, tol_eq=1e-5, tol_macro=1e-5, max_iter=20000,
+                     green="eq3" if op == "dg2" else op, eq_test="fixed_point")
+    rc, rec = (B.epfft_solve_dg2 if op == "dg2" else B.epfft_solve)(ctx, prob, path)
+    assert rc == B.EPFFT_OK and (ref["status"] == 0).all()
+    np.testing.assert_array_equal(rec["iterations"], ref["iterations"])
+    assert rel(rec["sig_mean"], ref["sig_mean"]) < 1e-10

@@ -1,0 +1,76 @@
+"""Pins of the oracle's choice of equilibrium test (Sec. 2, "Convergence
+issues"): with the fixed-point test every operator stops at the first iterate
+whose fixed-point residual eta3 and macroscopic change eta2 are both below
+the tolerance.  Replayed here step by step around single AL iterations, with
+the stopping rule written out in Python; CG1 and DG1 already stop on eta3, so
+the option leaves them unchanged."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_0802_2488_gb300 import inputs
+
+
+def ip(a):
+    return a[0] * a[0] + a[1] * a[1] + 2.0 * a[3] * a[3]
+
+
+def replay_first_increment(mask, mat, E, tol, max_iter):
+    """Iterations of the first increment under 'eta3 < tol and eta2 < tol'."""
+    L = mask.shape[0]
+    eps = np.broadcast_to(np.asarray(E, float), (L, L, 4)).copy()
+    lam = None
+    s_prev = O.stats(mask, mat, eps).sig_mean
+    EE = ip(np.asarray(E, float)) + E[2] * E[2]
+    for it in range(1, max_iter + 1):
+        eps, lam, e, _ = O.al_step(mask, mat, E, eps, lam)
+        s = O.stats(mask, mat, eps).sig_mean
+        d = eps - e
+        eta3 = np.sqrt(np.mean(d[..., 0] ** 2 + d[..., 1] ** 2 + d[..., 2] ** 2 + 2 * d[..., 3] ** 2) / EE)
+        eta2 = np.sqrt(ip(s - s_prev) / ip(s))
+        s_prev = s
+        if eta3 < tol and eta2 < tol:
+            return it, eta3
+    return None, None
+
+
+@pytest.mark.parametrize("green", [O.GREEN_EQ3, O.GREEN_EQ3_M1])
+@pytest.mark.parametrize("load", ["shear", "equibiaxial"])
+def test_fixed_point_test_stops_where_the_replay_does(green, load):
+    L, tol = 16, 1e-6
+    mask = O.mask(L, 0.15, 4)
+    mat = O.material(green=green)
+    E = inputs.load_path(load, 1, 1.2)[0]
+    it, eta3 = replay_first_increment(mask, mat, E, tol, 3000)
+    assert it is not None
+    sol = O.solve(mask, mat, E[None], tol, tol, 3000, eq_test=O.EQ_FIXED_POINT)
+    assert sol.status == 0
+    assert sol.records["iterations"][0] == it
+    assert abs(sol.records["eta3"][0] - eta3) <= 1e-9 * eta3
+
+
+def test_own_test_of_eq3_is_eta1():
+    """With its own test, Eq. 3 stops on eta1, which reaches the tolerance
+    at another iterate than eta3 here (elastic shear, 0.8 of the yield
+    strain)."""
+    L, tol = 16, 1e-6
+    mask = O.mask(L, 0.15, 4)
+    mat = O.material()
+    E = inputs.load_path("shear", 1, 0.8)[0][None]
+    own = O.solve(mask, mat, E, tol, tol, 3000)
+    fp = O.solve(mask, mat, E, tol, tol, 3000, eq_test=O.EQ_FIXED_POINT)
+    assert own.status == 0 and fp.status == 0
+    assert own.records["eta1"][0] < tol
+    assert own.records["iterations"][0] != fp.records["iterations"][0]
+
+
+@pytest.mark.parametrize("green", [O.GREEN_CG1, O.GREEN_DG1])
+def test_cg1_dg1_unchanged_by_the_option(green):
+    L = 16
+    mask = O.mask(L, 0.1, 2)
+    mat = O.material(green=green)
+    path = inputs.load_path("equibiaxial", 2, 1.5)
+    a = O.solve(mask, mat, path, 1e-7, 1e-7, 3000)
+    b = O.solve(mask, mat, path, 1e-7, 1e-7, 3000, eq_test=O.EQ_FIXED_POINT)
+    assert a.records.tobytes() == b.records.tobytes()
+    assert np.array_equal(a.eps, b.eps)
