@@ -165,26 +165,59 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(probs, budget_s: float = 15.0):
-    """The oracle as it stands, on this machine's host cores (OpenMP), on a
-    bounded sample of the workload: the first increment of the first problem
-    of the workload, with as many iterations as fit in ~budget_s."""
+def host_cpu() -> str:
+    """CPU model of this host (first 'model name' of /proc/cpuinfo, else the
+    platform's processor string)."""
+    import platform
+    arm = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":", 1)[0].strip().lower()
+                if key in ("model name", "cpu model"):
+                    return line.split(":", 1)[1].strip()
+                if key in ("cpu implementer", "cpu part") and key not in arm:
+                    arm[key] = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    if arm:  # Arm hosts name the core by implementer and part number
+        return f"{platform.machine()} (implementer {arm.get('cpu implementer')}, part {arm.get('cpu part')})"
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(probs, budget_s: float = 15.0, single_s: float = 3.0):
+    """The oracle as it stands, on this machine's host cores (OpenMP over all
+    of them, and on one), on a bounded sample of the workload: the first
+    increment of the first problem of the workload, with as many iterations
+    as fit in ~budget_s (~single_s on one core)."""
     import oracle as O
     P = probs[0]
     mask = O.mask(P.L, P.f, P.seed)
     mat = O.material()
     O.build()
-    t = time.perf_counter()
-    O.solve(mask, mat, P.path[:1], max_iter=2)
-    per_it = (time.perf_counter() - t) / 2
-    n_it = max(2, int(budget_s / max(per_it, 1e-6)))
-    t = time.perf_counter()
-    sol = O.solve(mask, mat, P.path[:1], max_iter=n_it)
-    dt = time.perf_counter() - t
-    its = int(sol.records["iterations"].sum())
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+    def timed(seconds):
+        t = time.perf_counter()
+        O.solve(mask, mat, P.path[:1], max_iter=2)
+        per_it = (time.perf_counter() - t) / 2
+        n_it = max(2, int(seconds / max(per_it, 1e-6)))
+        t = time.perf_counter()
+        sol = O.solve(mask, mat, P.path[:1], max_iter=n_it)
+        dt = time.perf_counter() - t
+        return int(sol.records["iterations"].sum()), dt
+
+    cores = O.threads()
+    its, dt = timed(budget_s)
+    O.set_threads(1)
+    try:
+        its1, dt1 = timed(single_s)
+    finally:
+        O.set_threads(cores)
     return {"value": P.L * P.L * its / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first increment of {P.name}, {its} iterations ({dt:.1f} s, OpenMP over {cores} threads)"}
+            "sample": f"first increment of {P.name}, {its} iterations ({dt:.1f} s, OpenMP over {cores} threads)",
+            "single_thread": {"value": P.L * P.L * its1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"first increment of {P.name}, {its1} iterations ({dt1:.1f} s)"},
+            "host": {"cpu": host_cpu(), "nproc": os.cpu_count()}}
 
 
 def run_reference(args):
@@ -213,14 +246,15 @@ def run_reference(args):
         its += int(sol.records["iterations"].sum())
     tot = sum(times)
     v = P.L * P.L * its / tot
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = O.threads()
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{n_it} iterations of the first increment of {P.name} per step"},
+                         "sample": f"{n_it} iterations of the first increment of {P.name} per step",
+                         "host": {"cpu": host_cpu(), "nproc": os.cpu_count()}},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
 
 

@@ -39,6 +39,16 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def threads() -> int:
+    """OpenMP threads the oracle's loops use."""
+    return int(lib().orc_threads())
+
+
+def set_threads(n: int) -> None:
+    """Sets the OpenMP threads of the oracle's loops (n > 0)."""
+    lib().orc_set_threads(int(n))
+
+
 class Material(C.Structure):
     """Matrix Lame moduli, Mises flow stress Y (inf = elastic), the
     reference medium C0 of the augmented Lagrangian and the Green operator
@@ -86,6 +96,8 @@ def lib():
     if _lib is None:
         build()
         L = C.CDLL(_LIB)
+        L.orc_threads.restype = C.c_int
+        L.orc_set_threads.argtypes = [C.c_int]
         L.orc_splitmix64.restype = C.c_uint64
         L.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
         L.orc_void_threshold.restype = C.c_uint64

@@ -57,12 +57,33 @@
  *                               indicators of Sec. 3.
  */
 #include <complex.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
 typedef double complex cplx;
+
+/* Threads of the OpenMP loops below (the benchmark times the oracle on one
+ * host core and on all of them); 1 without OpenMP. */
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
