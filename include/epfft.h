@@ -310,10 +310,17 @@ typedef struct {
 int epfft_serve_open(epfft_ctx *ctx, const epfft_serve_options *opt);
 /* Stops serving; drops queued and running requests and their results. */
 int epfft_serve_close(epfft_ctx *ctx);
+/* Fields a served solve keeps for its caller (bits of epfft_submit's want) */
+#define EPFFT_WANT_EPS 1     /* final strain (returned by epfft_poll)          */
+#define EPFFT_WANT_SIG 2     /* final stress sigma(eps), the multiplier         */
+#define EPFFT_WANT_PLASTIC 4 /* plastic flags of every accepted increment      */
+#define EPFFT_WANT_LABELS 8  /* their periodic cluster labels (Sec. 3)          */
+
 /* Queues one solve (problem and path copied; a device mask is copied to the
  * host now).  *ticket identifies it.  EPFFT_ERR_OOM if its device state
- * alone exceeds the budget.  want_eps != 0 keeps its final strain. */
-int epfft_submit(epfft_ctx *ctx, const epfft_problem *problem, const epfft_path *path, int32_t want_eps,
+ * alone exceeds the budget.  want: EPFFT_WANT_* bits (0: records only;
+ * other bits: EPFFT_ERR_ARG). */
+int epfft_submit(epfft_ctx *ctx, const epfft_problem *problem, const epfft_path *path, int32_t want,
                  int64_t *ticket);
 /* One admission / device / harvest round (blocking for the device work).
  * n_running, n_queued (optional): solves on the device, still queued. */
@@ -323,8 +330,23 @@ int epfft_serve_step(epfft_ctx *ctx, int32_t *n_running, int32_t *n_queued);
  * (host, n_inc entries), the final strain in eps_host (host, L*L*4 reals of
  * the precision, when requested at submission; may be NULL) and the time
  * from submission to harvest in *latency_s (may be NULL).  The ticket is
- * released once it has returned a final code. */
+ * released once it has returned a final code, unless it keeps fields other
+ * than the strain (EPFFT_WANT_SIG, _PLASTIC, _LABELS): such a ticket
+ * returns its final code on every poll until epfft_release. */
 int epfft_poll(epfft_ctx *ctx, int64_t ticket, epfft_record *records, void *eps_host, double *latency_s);
+/* Fields of a finished served solve at increment inc (0 <= inc < n_inc),
+ * host buffers the caller owns, NULL to skip: eps_host, sig_host (L*L*4
+ * reals of the precision; the final accepted state, so only for
+ * inc = n_inc - 1), plastic_host (L*L bytes, 1 = matrix pixel on the
+ * plastic branch) and labels_host (L*L int32, clusters of Sec. 3 as in
+ * epfft_label).  EPFFT_PENDING while the solve runs or waits; EPFFT_ERR_ARG
+ * for an unknown ticket, an increment out of range, or a field not asked
+ * for at submission. */
+int epfft_ticket_fields(epfft_ctx *ctx, int64_t ticket, int32_t inc, void *eps_host, void *sig_host,
+                        uint8_t *plastic_host, int32_t *labels_host);
+/* Releases a finished ticket and its fields (EPFFT_PENDING, nothing
+ * released, while it runs or waits). */
+int epfft_release(epfft_ctx *ctx, int64_t ticket);
 
 /* ---------------------------------------------------------------------- */
 /* Steps of the iteration, for parity checks and measurement               */

@@ -35,6 +35,10 @@ EPFFT_GREEN_EQ3 = 0
 EPFFT_GREEN_CG1 = 1
 EPFFT_GREEN_DG1 = 2
 _GREEN = {"eq3": EPFFT_GREEN_EQ3, "cg1": EPFFT_GREEN_CG1, "dg1": EPFFT_GREEN_DG1}
+EPFFT_WANT_EPS = 1
+EPFFT_WANT_SIG = 2
+EPFFT_WANT_PLASTIC = 4
+EPFFT_WANT_LABELS = 8
 EPFFT_EQ_OWN = 0
 EPFFT_EQ_FIXED_POINT = 1
 _EQ_TEST = {"own": EPFFT_EQ_OWN, "fixed_point": EPFFT_EQ_FIXED_POINT}
@@ -44,7 +48,8 @@ SYMBOLS = ["epfft_create", "epfft_destroy", "epfft_last_stats", "epfft_strerror"
            "epfft_time_passes", "epfft_project_static", "epfft_serve_open", "epfft_serve_close",
            "epfft_submit", "epfft_serve_step", "epfft_poll", "epfft_autotune", "epfft_set_tiling",
            "epfft_solve_dg2", "epfft_average5", "epfft_void_plastic", "epfft_indicators",
-           "epfft_effective_moduli", "epfft_empirical_curve", "epfft_eps_eq", "epfft_displacement"]
+           "epfft_effective_moduli", "epfft_empirical_curve", "epfft_eps_eq", "epfft_displacement",
+           "epfft_ticket_fields", "epfft_release"]
 
 
 class EpfftError(RuntimeError):
@@ -132,6 +137,8 @@ def lib():
         L.epfft_submit.argtypes = [vp, C.POINTER(_Problem), C.POINTER(_Path), i32, C.POINTER(C.c_int64)]
         L.epfft_serve_step.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
         L.epfft_poll.argtypes = [vp, C.c_int64, vp, vp, C.POINTER(dbl)]
+        L.epfft_ticket_fields.argtypes = [vp, C.c_int64, i32, vp, vp, vp, vp]
+        L.epfft_release.argtypes = [vp, C.c_int64]
         L.epfft_autotune.argtypes = [vp, i32, i32, i32, C.POINTER(i32), C.POINTER(C.c_float)]
         L.epfft_set_tiling.argtypes = [vp, i32, i32, i32]
         L.epfft_project_static.argtypes = [i32, i32, dbl, dbl, C.POINTER(dbl), vp, vp, vp]
@@ -551,12 +558,18 @@ def epfft_serve_close(ctx: Context):
     _check(lib().epfft_serve_close(ctx.handle), "epfft_serve_close")
 
 
-def epfft_submit(ctx: Context, problem: Problem, path, want_eps: bool = False) -> int:
+def epfft_submit(ctx: Context, problem: Problem, path, want_eps: bool = False, want_sig: bool = False,
+                 want_plastic: bool = False, want_labels: bool = False) -> int:
+    """Queues one solve; the want_* flags choose the fields kept for the
+    caller (the final strain through epfft_poll; the final stress and the
+    per-increment plastic flags and cluster labels through
+    epfft_ticket_fields, until epfft_release)."""
     p, keep = problem._c()
     cp, parr = _path(path)
+    want = ((EPFFT_WANT_EPS if want_eps else 0) | (EPFFT_WANT_SIG if want_sig else 0) |
+            (EPFFT_WANT_PLASTIC if want_plastic else 0) | (EPFFT_WANT_LABELS if want_labels else 0))
     t = C.c_int64()
-    _check(lib().epfft_submit(ctx.handle, C.byref(p), C.byref(cp), 1 if want_eps else 0, C.byref(t)),
-           "epfft_submit")
+    _check(lib().epfft_submit(ctx.handle, C.byref(p), C.byref(cp), want, C.byref(t)), "epfft_submit")
     return t.value
 
 
@@ -578,6 +591,39 @@ def epfft_poll(ctx: Context, ticket: int, problem: Problem, n_inc: int, want_eps
         return None
     _check(rc, "epfft_poll", (EPFFT_OK, EPFFT_NOT_CONVERGED))
     return rc, rec, eps, lat.value
+
+
+def epfft_ticket_fields(ctx: Context, ticket: int, problem: Problem, inc: int, eps: bool = False,
+                        sig: bool = False, plastic: bool = False, labels: bool = False) -> Optional[dict]:
+    """Fields of a finished served solve at increment inc (eps and sig: the
+    final accepted state, inc = n_inc - 1 only), as numpy arrays keyed
+    'eps', 'sig', 'plastic', 'labels'; None while it is pending."""
+    L = problem.L
+    out = {}
+    if eps:
+        out["eps"] = np.empty((L, L, 4), dtype=problem.real_dtype)
+    if sig:
+        out["sig"] = np.empty((L, L, 4), dtype=problem.real_dtype)
+    if plastic:
+        out["plastic"] = np.empty((L, L), dtype=np.uint8)
+    if labels:
+        out["labels"] = np.empty((L, L), dtype=np.int32)
+    ptr = lambda k: out[k].ctypes.data if k in out else None
+    rc = lib().epfft_ticket_fields(ctx.handle, int(ticket), int(inc), ptr("eps"), ptr("sig"), ptr("plastic"),
+                                   ptr("labels"))
+    if rc == EPFFT_PENDING:
+        return None
+    _check(rc, "epfft_ticket_fields")
+    return out
+
+
+def epfft_release(ctx: Context, ticket: int) -> bool:
+    """Releases a finished ticket and its fields; False while it is pending."""
+    rc = lib().epfft_release(ctx.handle, int(ticket))
+    if rc == EPFFT_PENDING:
+        return False
+    _check(rc, "epfft_release")
+    return True
 
 
 # --------------------------------------------------------------------------

@@ -672,9 +672,12 @@ struct Ticket {
   epfft_problem prob{};
   std::vector<double> path;
   std::vector<uint8_t> mask;  // caller mask copied at submission (empty: generated)
-  bool want_eps = false;
+  int32_t want = 0;                  // EPFFT_WANT_* bits given at submission
   std::vector<Record> rec;
-  std::vector<unsigned char> eps;
+  std::vector<unsigned char> eps;    // final strain (EPFFT_WANT_EPS)
+  std::vector<unsigned char> sig;    // final stress (EPFFT_WANT_SIG)
+  std::vector<uint8_t> flags;        // n_inc * L * L plastic flags (EPFFT_WANT_PLASTIC)
+  std::vector<int32_t> labels;       // n_inc * L * L cluster labels (EPFFT_WANT_LABELS)
   int status = 0;
   size_t bytes = 0;
   double t_submit = 0, t_done = 0;
@@ -827,9 +830,17 @@ int serve_harvest(epfft_ctx* c, Server& S, ServeClass* k) {
     const int n = B.n_inc[i];
     t.rec.resize(n);
     CK(cudaMemcpyAsync(t.rec.data(), hs[i].rec, sizeof(Record) * (size_t)n, cudaMemcpyDeviceToHost, k->stream));
-    if (t.want_eps) {
+    if (t.want & EPFFT_WANT_EPS) {
       t.eps.resize(4 * LL * rs);
       CK(cudaMemcpyAsync(t.eps.data(), hs[i].eps[hs[i].cur], 4 * LL * rs, cudaMemcpyDeviceToHost, k->stream));
+    }
+    if (t.want & EPFFT_WANT_SIG) {  // sigma of the accepted iterate (the resident multiplier)
+      t.sig.resize(4 * LL * rs);
+      CK(cudaMemcpyAsync(t.sig.data(), hs[i].sig[hs[i].cur], 4 * LL * rs, cudaMemcpyDeviceToHost, k->stream));
+    }
+    if (t.want & EPFFT_WANT_PLASTIC) {
+      t.flags.resize(LL * (size_t)n);
+      CK(cudaMemcpyAsync(t.flags.data(), hs[i].flags, LL * (size_t)n, cudaMemcpyDeviceToHost, k->stream));
     }
     // clusters of every accepted increment
     int32_t* lab = (int32_t*)dev_alloc(c, sizeof(int32_t) * LL * (size_t)n);
@@ -839,6 +850,10 @@ int serve_harvest(epfft_ctx* c, Server& S, ServeClass* k) {
     CK(launch_label(hs[i].flags, lab, n, k->L, 1, cnt, cnt + n, k->stream));
     std::vector<int32_t> hc(n + 1);
     CK(cudaMemcpyAsync(hc.data(), cnt, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost, k->stream));
+    if (t.want & EPFFT_WANT_LABELS) {
+      t.labels.resize(LL * (size_t)n);
+      CK(cudaMemcpyAsync(t.labels.data(), lab, sizeof(int32_t) * LL * (size_t)n, cudaMemcpyDeviceToHost, k->stream));
+    }
     CK(cudaStreamSynchronize(k->stream));
     dev_free(c, lab, sizeof(int32_t) * LL * (size_t)n);
     dev_free(c, cnt, sizeof(int32_t) * ((size_t)n + 1));
@@ -1400,9 +1415,10 @@ int epfft_serve_close(epfft_ctx* ctx) {
   return EPFFT_OK;
 }
 
-int epfft_submit(epfft_ctx* ctx, const epfft_problem* problem, const epfft_path* path, int32_t want_eps,
+int epfft_submit(epfft_ctx* ctx, const epfft_problem* problem, const epfft_path* path, int32_t want,
                  int64_t* ticket) {
   if (!ctx || !ctx->server || !problem || !path || !ticket) return EPFFT_ERR_ARG;
+  if (want & ~(EPFFT_WANT_EPS | EPFFT_WANT_SIG | EPFFT_WANT_PLASTIC | EPFFT_WANT_LABELS)) return EPFFT_ERR_ARG;
   int rc = check_problem(problem);
   if (rc) return rc;
   if (path->n_inc < 1 || !path->E) return EPFFT_ERR_ARG;
@@ -1415,7 +1431,7 @@ int epfft_submit(epfft_ctx* ctx, const epfft_problem* problem, const epfft_path*
   Ticket t;
   t.prob = *problem;
   t.path.assign(path->E, path->E + 4 * (size_t)path->n_inc);
-  t.want_eps = want_eps != 0;
+  t.want = want;
   t.bytes = solve_footprint(problem->L, problem->precision, sh.row_ctas, path->n_inc);
   if (t.bytes > S.budget) return EPFFT_ERR_OOM;
   const size_t LL = (size_t)problem->L * problem->L;
@@ -1501,8 +1517,43 @@ int epfft_poll(epfft_ctx* ctx, int64_t ticket, epfft_record* records, void* eps_
   if (eps_host && !t.eps.empty()) std::memcpy(eps_host, t.eps.data(), t.eps.size());
   if (latency_s) *latency_s = t.t_done - t.t_submit;
   const int st = t.status;
-  S.tickets.erase(it);
+  // a ticket holding fields beyond the strain stays for epfft_ticket_fields
+  // until epfft_release
+  if (!(t.want & ~EPFFT_WANT_EPS)) S.tickets.erase(it);
   return st;
+}
+
+int epfft_ticket_fields(epfft_ctx* ctx, int64_t ticket, int32_t inc, void* eps_host, void* sig_host,
+                        uint8_t* plastic_host, int32_t* labels_host) {
+  if (!ctx || !ctx->server) return EPFFT_ERR_ARG;
+  Server& S = *ctx->server;
+  auto it = S.tickets.find(ticket);
+  if (it == S.tickets.end()) return EPFFT_ERR_ARG;
+  const Ticket& t = it->second;
+  if (t.state != 2) return EPFFT_PENDING;
+  const int n = (int)t.rec.size();
+  if (inc < 0 || inc >= n) return EPFFT_ERR_ARG;
+  // the strain and stress are those of the final accepted state only
+  if ((eps_host || sig_host) && inc != n - 1) return EPFFT_ERR_ARG;
+  if ((eps_host && t.eps.empty()) || (sig_host && t.sig.empty()) || (plastic_host && t.flags.empty()) ||
+      (labels_host && t.labels.empty()))
+    return EPFFT_ERR_ARG;
+  const size_t LL = (size_t)t.prob.L * t.prob.L;
+  if (eps_host) std::memcpy(eps_host, t.eps.data(), t.eps.size());
+  if (sig_host) std::memcpy(sig_host, t.sig.data(), t.sig.size());
+  if (plastic_host) std::memcpy(plastic_host, t.flags.data() + LL * (size_t)inc, LL);
+  if (labels_host) std::memcpy(labels_host, t.labels.data() + LL * (size_t)inc, sizeof(int32_t) * LL);
+  return EPFFT_OK;
+}
+
+int epfft_release(epfft_ctx* ctx, int64_t ticket) {
+  if (!ctx || !ctx->server) return EPFFT_ERR_ARG;
+  Server& S = *ctx->server;
+  auto it = S.tickets.find(ticket);
+  if (it == S.tickets.end()) return EPFFT_ERR_ARG;
+  if (it->second.state != 2) return EPFFT_PENDING;
+  S.tickets.erase(it);
+  return EPFFT_OK;
 }
 
 int epfft_time_passes(epfft_ctx* ctx, const epfft_problem* problem, int32_t n_batch, const double E[4],

@@ -93,3 +93,57 @@ def test_request_larger_than_budget_is_refused(ctx):
         assert e.value.code == B.EPFFT_ERR_OOM
     finally:
         B.epfft_serve_close(ctx)
+
+
+def test_served_fields_equal_solves_alone(ctx):
+    """Fields kept for the caller of a served solve: the plastic flags and
+    cluster labels of every increment equal those of the solve run alone
+    (bit for bit), the final strain too, and the final stress is the
+    constitutive law of Sec. 2 at that strain (the oracle's, within 1e-12
+    relative in FP64, 1e-5 in FP32).  A ticket with such fields answers
+    polls until it is released."""
+    import oracle as O
+    reqs = [r for r in requests()[:4]]
+    B.epfft_serve_open(ctx, 1 << 30, 4, 16)
+    try:
+        tickets = {i: B.epfft_submit(ctx, P, path, want_eps=True, want_sig=True, want_plastic=True,
+                                     want_labels=True) for i, (P, path) in enumerate(reqs)}
+        # nothing has run yet
+        assert B.epfft_ticket_fields(ctx, tickets[0], reqs[0][0], 0, plastic=True) is None
+        assert not B.epfft_release(ctx, tickets[0])
+        done = {}
+        rounds = 0
+        while len(done) < len(reqs):
+            B.epfft_serve_step(ctx)
+            for i, t in tickets.items():
+                if i not in done:
+                    r = B.epfft_poll(ctx, t, reqs[i][0], len(reqs[i][1]), want_eps=True)
+                    if r is not None:
+                        done[i] = r
+            rounds += 1
+            assert rounds < 100000
+        for i, (P, path) in enumerate(reqs):
+            t, n = tickets[i], len(path)
+            # still there after its final poll
+            assert B.epfft_poll(ctx, t, P, n) is not None
+            rc, rec, f = B.epfft_solve(ctx, P, path, fields=True)
+            assert done[i][1].tobytes() == rec.tobytes()
+            for k in range(n):
+                g = B.epfft_ticket_fields(ctx, t, P, k, plastic=True, labels=True)
+                assert np.array_equal(g["plastic"], f.plastic[k]), (i, k)
+                assert np.array_equal(g["labels"], f.labels[k]), (i, k)
+            g = B.epfft_ticket_fields(ctx, t, P, n - 1, eps=True, sig=True)
+            assert np.array_equal(g["eps"], f.eps)
+            mask = O.mask(P.L, P.void_fraction, P.seed)
+            s_ref, _ = O.sigma(g["eps"].astype(np.float64), mask, O.material())
+            tol = 1e-12 if P.precision == "fp64" else 1e-5
+            assert np.abs(g["sig"] - s_ref).max() <= tol * np.abs(s_ref).max(), i
+            # the final state only: strain and stress of an earlier increment are refused
+            if n > 1:
+                with pytest.raises(B.EpfftError):
+                    B.epfft_ticket_fields(ctx, t, P, 0, eps=True)
+            assert B.epfft_release(ctx, t)
+            with pytest.raises(B.EpfftError):
+                B.epfft_ticket_fields(ctx, t, P, 0, plastic=True)
+    finally:
+        B.epfft_serve_close(ctx)
