@@ -282,6 +282,45 @@ def timed_solves(B, ctx, stream, flush, probs, paths, steps, torch):
     return sum(a.elapsed_time(b) for a, b in ev) / 1e3, pix_its, launches, recs
 
 
+def refined_vs_plain(B, ctx, stream, flush, mask, L, path, torch, tol=1e-8, tol_switch=1e-5, cap=60000):
+    """Solves/s at one equilibrium tolerance that the FP32 path cannot
+    certify alone: the plain FP64 solve against the mixed-precision solve
+    (FP32 iterations to tol_switch, then FP64 to tol), on the increments of
+    `path`; one L2-flushed, CUDA-event-timed solve of each after a warm-up."""
+    prob = B.Problem(L=L, precision="fp64", mask=mask, tol_eq=tol, tol_macro=tol, max_iter=cap)
+    warm = B.Problem(L=L, precision="fp64", mask=mask, tol_eq=tol, tol_macro=tol, max_iter=20)
+    B.epfft_autotune(ctx, L, "fp32")
+    B.epfft_solve(ctx, warm, path[:1])
+    B.epfft_solve_refined(ctx, warm, path[:1], tol_switch)
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        r = fn()
+        with torch.cuda.stream(stream):
+            b.record(stream)
+        stream.synchronize()
+        return a.elapsed_time(b) / 1e3, r
+
+    t64, (rc64, r64) = timed(lambda: B.epfft_solve(ctx, prob, path))
+    tr, (rcr, rr, rr32) = timed(lambda: B.epfft_solve_refined(ctx, prob, path, tol_switch))
+    return {"workload": f"first {len(path)} increments of the same lattice and path, tol {tol:g} (eta1, eta2) "
+                        f"certified in FP64, at most {cap} iterations per increment",
+            "fp64_plain": {"solves_per_s": 1.0 / t64, "iterations": int(r64["iterations"].sum()),
+                           "converged": bool((r64["status"] == 0).all())},
+            "fp32_then_fp64": {"solves_per_s": 1.0 / tr, "tol_switch": tol_switch,
+                               "iterations_fp32": int(rr32["iterations"].sum()),
+                               "iterations_fp64": int(rr["iterations"].sum()),
+                               "converged": bool((rr["status"] == 0).all()),
+                               "max_eta1": float(rr["eta1"].max()),
+                               "fp32_stage_reached": {"eta1": rr32["eta1"].tolist(), "eta2": rr32["eta2"].tolist(),
+                                                      "status": rr32["status"].tolist()}},
+            "speedup": t64 / tr}
+
+
 def run_serving(args):
     """C5: Poisson request stream through the serving engine."""
     import torch
@@ -460,6 +499,10 @@ def main():
                      "eta1_last_increment": float(frecs[0]["eta1"][-1]),
                      "dtype": "f32 fields and FFTs, f64 reductions"}
 
+    refined = None
+    if args.workload == "c2" and args.precision == "fp64" and not args.no_fp32:
+        refined = refined_vs_plain(B, ctx, stream, flush, masks_dev[0], L, paths[0][:2], torch)
+
     t_step = dev_s / args.steps
     t_step, dev_s, e2e_s = max_over_ranks([t_step, dev_s, e2e_s], device=torch.device(f"cuda:{local}"))
     value = job_value(ws, pix_its, dev_s)
@@ -511,6 +554,8 @@ def main():
         }
         if companion:
             out["fp32"] = companion
+        if refined:
+            out["refined"] = refined
         if ws == 1 and not args.no_baseline:
             out["cpu_baseline"] = cpu_baseline(probs)
         print(json.dumps(out), flush=True)

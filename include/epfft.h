@@ -194,6 +194,20 @@ int epfft_solve_batch(epfft_ctx *ctx, int32_t n, const epfft_problem *problems,
                       const epfft_path *paths, epfft_record *const *records,
                       const epfft_fields *fields);
 
+/* Mixed-precision solve (Sec. 2 loading; the FP32 path cannot certify
+ * tolerances below its rounding floor of about 1e-7): each increment
+ * iterates first in FP32 until eta1 and eta2 fall below
+ * max(tol_switch, tolerance) (or max_iter), then continues in FP64 from that
+ * state until the problem's tolerances hold (or max_iter), so that the
+ * indicators in `records` are FP64 ones.  problem->precision must be
+ * EPFFT_FP64 (the precision of the result and of `fields`); increment k's
+ * FP32 stage starts from the accepted FP64 state of increment k-1 shifted by
+ * E_k - E_{k-1} and rounded.  records: n_inc FP64-stage records (host);
+ * records_fp32 (optional): n_inc records of the FP32 stages.  Returns as
+ * epfft_solve, from the FP64 stages. */
+int epfft_solve_refined(epfft_ctx *ctx, const epfft_problem *problem, const epfft_path *path, double tol_switch,
+                        epfft_record *records, epfft_record *records_fp32, const epfft_fields *fields);
+
 /* DG2 (Sec. 2): four complete solves of the problem with the Eq. 3
  * operator at (q1, q2), (-q1, -q2), (-q1, q2) and (q1, -q2) in turn, and the
  * average of the four converged strain fields.  The operator at mirrored

@@ -49,7 +49,7 @@ SYMBOLS = ["epfft_create", "epfft_destroy", "epfft_last_stats", "epfft_strerror"
            "epfft_submit", "epfft_serve_step", "epfft_poll", "epfft_autotune", "epfft_set_tiling",
            "epfft_solve_dg2", "epfft_average5", "epfft_void_plastic", "epfft_indicators",
            "epfft_effective_moduli", "epfft_empirical_curve", "epfft_eps_eq", "epfft_displacement",
-           "epfft_ticket_fields", "epfft_release"]
+           "epfft_ticket_fields", "epfft_release", "epfft_solve_refined"]
 
 
 class EpfftError(RuntimeError):
@@ -139,6 +139,7 @@ def lib():
         L.epfft_poll.argtypes = [vp, C.c_int64, vp, vp, C.POINTER(dbl)]
         L.epfft_ticket_fields.argtypes = [vp, C.c_int64, i32, vp, vp, vp, vp]
         L.epfft_release.argtypes = [vp, C.c_int64]
+        L.epfft_solve_refined.argtypes = [vp, C.POINTER(_Problem), C.POINTER(_Path), dbl, vp, vp, vp]
         L.epfft_autotune.argtypes = [vp, i32, i32, i32, C.POINTER(i32), C.POINTER(C.c_float)]
         L.epfft_set_tiling.argtypes = [vp, i32, i32, i32]
         L.epfft_project_static.argtypes = [i32, i32, dbl, dbl, C.POINTER(dbl), vp, vp, vp]
@@ -335,6 +336,22 @@ def epfft_solve(ctx: Context, problem: Problem, path, fields: bool = False):
                            C.byref(cf) if cf is not None else None)
     _check(rc, "epfft_solve", (EPFFT_OK, EPFFT_NOT_CONVERGED))
     return (rc, rec, f) if fields else (rc, rec)
+
+
+def epfft_solve_refined(ctx: Context, problem: Problem, path, tol_switch: float = 1e-5, fields: bool = False):
+    """Mixed-precision solve: per increment FP32 iterations to
+    max(tol_switch, tolerance), then FP64 iterations to the tolerances
+    (problem.precision must be 'fp64').  Returns (rc, records of the FP64
+    stages, records of the FP32 stages[, Fields])."""
+    p, keep = problem._c()
+    cp, parr = _path(path)
+    rec = np.zeros(cp.n_inc, dtype=RECORD_DTYPE)
+    rec32 = np.zeros(cp.n_inc, dtype=RECORD_DTYPE)
+    f, cf = _host_fields(problem, cp.n_inc) if fields else (None, None)
+    rc = lib().epfft_solve_refined(ctx.handle, C.byref(p), C.byref(cp), float(tol_switch), rec.ctypes.data,
+                                   rec32.ctypes.data, C.byref(cf) if cf is not None else None)
+    _check(rc, "epfft_solve_refined", (EPFFT_OK, EPFFT_NOT_CONVERGED))
+    return (rc, rec, rec32, f) if fields else (rc, rec, rec32)
 
 
 def epfft_solve_dg2(ctx: Context, problem: Problem, path, fields: bool = False):

@@ -1277,6 +1277,80 @@ int epfft_mask(int32_t L, double void_fraction, uint64_t seed, uint8_t* mask_dev
   return EPFFT_OK;
 }
 
+int epfft_solve_refined(epfft_ctx* ctx, const epfft_problem* problem, const epfft_path* path, double tol_switch,
+                        epfft_record* records, epfft_record* records_fp32, const epfft_fields* fields) {
+  if (!ctx || !problem || !path || !records) return EPFFT_ERR_ARG;
+  int rc = check_problem(problem);
+  if (rc) return rc;
+  if (problem->precision != EPFFT_FP64 || !(tol_switch >= 0.0)) return EPFFT_ERR_ARG;
+  if (!supported(problem->L, EPFFT_FP32)) return EPFFT_ERR_UNSUPPORTED;
+  if (path->n_inc < 1 || !path->E) return EPFFT_ERR_ARG;
+  for (int k = 0; k < 4 * path->n_inc; k++)
+    if (!std::isfinite(path->E[k])) return EPFFT_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return EPFFT_ERR_CUDA;
+  const int L = problem->L, n_inc = path->n_inc;
+  const size_t LL = (size_t)L * L;
+  Arena A(ctx);
+  float* e32 = (float*)A.get(4 * LL * sizeof(float));
+  double* e64 = (double*)A.get(4 * LL * sizeof(double));
+  uint8_t* mask = problem->mask ? nullptr : (uint8_t*)A.get(LL);
+  if (!e32 || !e64 || (!problem->mask && !mask)) return EPFFT_ERR_OOM;
+  // both stages see the same voids
+  if (mask) CK(launch_mask(mask, (int64_t)LL, problem->seed, void_threshold(problem->void_fraction), ctx->stream));
+  epfft_problem p64 = *problem;
+  if (mask) {
+    p64.mask = mask;
+    p64.mask_on_device = 1;
+  }
+  epfft_problem p32 = p64;
+  p32.precision = EPFFT_FP32;
+  p32.tol_eq = std::max(tol_switch, problem->tol_eq);
+  p32.tol_macro = std::max(tol_switch, problem->tol_macro);
+  int status = EPFFT_OK;
+  for (int k = 0; k < n_inc; k++) {
+    const double* Ek = path->E + 4 * k;
+    const epfft_path pk = {1, 0, Ek};
+    // FP32 stage: the accepted FP64 state of increment k - 1 shifted by
+    // E_k - E_{k-1} and rounded (increment 0 starts from the unstrained
+    // lattice, shifted by E_0 inside the solve)
+    epfft_record r32;
+    epfft_record* rp32[1] = {&r32};
+    void* o32[1] = {e32};
+    if (k == 0) {
+      rc = solve_impl(ctx, 1, &p32, &pk, rp32, nullptr, nullptr, o32, nullptr);
+    } else {
+      const double* Ep = path->E + 4 * (k - 1);
+      const double dE[4] = {Ek[0] - Ep[0], Ek[1] - Ep[1], Ek[2] - Ep[2], Ek[3] - Ep[3]};
+      CK((launch_shift_convert<double, float>(e64, e32, L, dE, ctx->stream)));
+      const void* i32[1] = {e32};
+      rc = solve_impl(ctx, 1, &p32, &pk, rp32, nullptr, i32, o32, nullptr);
+    }
+    if (rc != EPFFT_OK && rc != EPFFT_NOT_CONVERGED) return rc;
+    if (records_fp32) records_fp32[k] = r32;
+    // FP64 stage from the FP32 result, to the problem's tolerances
+    const double zero[4] = {0.0, 0.0, 0.0, 0.0};
+    CK((launch_shift_convert<float, double>(e32, e64, L, zero, ctx->stream)));
+    epfft_fields fk;
+    const epfft_fields* fp = nullptr;
+    if (fields) {
+      fk = *fields;
+      fk.eps = k == n_inc - 1 ? fields->eps : nullptr;
+      fk.plastic = fields->plastic ? fields->plastic + LL * (size_t)k : nullptr;
+      fk.labels = fields->labels ? fields->labels + LL * (size_t)k : nullptr;
+      fp = &fk;
+    }
+    epfft_record* rp64[1] = {records + k};
+    const void* i64[1] = {e64};
+    void* o64[1] = {e64};
+    rc = solve_impl(ctx, 1, &p64, &pk, rp64, fp, i64, o64, nullptr);
+    if (rc == EPFFT_ERR_NUMERIC) return rc;
+    if (rc == EPFFT_NOT_CONVERGED) status = EPFFT_NOT_CONVERGED;
+    else if (rc != EPFFT_OK) return rc;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return status;
+}
+
 int epfft_iterate(epfft_ctx* ctx, const epfft_problem* problem, const double E[4], void* eps_dev, int32_t n_iter,
                   epfft_record* out) {
   if (!ctx || !problem || !E || !eps_dev || n_iter < 1 || !out) return EPFFT_ERR_ARG;

@@ -186,6 +186,19 @@ __global__ void strain_planes_kernel(const T* __restrict__ eps, T* __restrict__ 
   }
 }
 
+// out = in + dE per pixel (components 11, 22, 33, 12), converted from TI to
+// TO (rounded once, after the shift).
+template <typename TI, typename TO>
+__global__ void shift_convert_kernel(const TI* __restrict__ in, TO* __restrict__ out, int64_t n, double d0,
+                                     double d1, double d2, double d3) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    out[4 * i + 0] = (TO)((double)in[4 * i + 0] + d0);
+    out[4 * i + 1] = (TO)((double)in[4 * i + 1] + d1);
+    out[4 * i + 2] = (TO)((double)in[4 * i + 2] + d2);
+    out[4 * i + 3] = (TO)((double)in[4 * i + 3] + d3);
+  }
+}
+
 // planes (u1, u2, .) of L*L each -> (L, L, 2) pairs.
 template <typename T>
 __global__ void disp_pairs_kernel(const T* __restrict__ planes, T* __restrict__ u, int64_t n) {
@@ -303,6 +316,15 @@ cudaError_t launch_disp_pairs(const T* planes, T* u, int L, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename TI, typename TO>
+cudaError_t launch_shift_convert(const TI* in, TO* out, int L, const double dE[4], cudaStream_t s) {
+  const int64_t n = (int64_t)L * L;
+  shift_convert_kernel<TI, TO><<<grid_of(n), 256, 0, s>>>(in, out, n, dE[0], dE[1], dE[2], dE[3]);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_shift_convert<double, float>(const double*, float*, int, const double*, cudaStream_t);
+template cudaError_t launch_shift_convert<float, double>(const float*, double*, int, const double*, cudaStream_t);
 template cudaError_t launch_strain_planes<float>(const float*, float*, int, cudaStream_t);
 template cudaError_t launch_strain_planes<double>(const double*, double*, int, cudaStream_t);
 template cudaError_t launch_disp_pairs<float>(const float*, float*, int, cudaStream_t);

@@ -42,6 +42,10 @@ template <typename T>
 cudaError_t launch_strain_planes(const T* eps, T* planes, int L, cudaStream_t s);
 template <typename T>
 cudaError_t launch_disp_pairs(const T* planes, T* u, int L, cudaStream_t s);
+// out = in + dE on every pixel of an (L, L, 4) strain field, converted
+// between precisions (double -> float or float -> double).
+template <typename TI, typename TO>
+cudaError_t launch_shift_convert(const TI* in, TO* out, int L, const double dE[4], cudaStream_t s);
 // *count_dev += number of nonzero bytes of a[0 .. n)
 cudaError_t launch_count(const uint8_t* a, int64_t n, int32_t* count_dev, cudaStream_t s);
 }  // namespace epfft

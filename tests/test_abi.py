@@ -81,6 +81,7 @@ def test_argument_checks_of_analysis_entry_points(lib):
     assert lib.epfft_displacement(None, 8, 0, None, None) == B.EPFFT_ERR_ARG
     assert lib.epfft_ticket_fields(None, 0, 0, None, None, None, None) == B.EPFFT_ERR_ARG
     assert lib.epfft_release(None, 0) == B.EPFFT_ERR_ARG
+    assert lib.epfft_solve_refined(None, None, None, C.c_double(1e-6), None, None, None) == B.EPFFT_ERR_ARG
     assert lib.epfft_effective_moduli(None, None, C.c_double(1e-3), None, None) == B.EPFFT_ERR_ARG
 
 
