@@ -282,7 +282,7 @@ def timed_solves(B, ctx, stream, flush, probs, paths, steps, torch):
     return sum(a.elapsed_time(b) for a, b in ev) / 1e3, pix_its, launches, recs
 
 
-def refined_vs_plain(B, ctx, stream, flush, mask, L, path, torch, tol=1e-8, tol_switch=1e-5, cap=60000):
+def refined_vs_plain(B, ctx, stream, flush, mask, L, path, torch, tol=1e-8, tol_switch=0.0, cap=60000):
     """Solves/s at one equilibrium tolerance that the FP32 path cannot
     certify alone: the plain FP64 solve against the mixed-precision solve
     (FP32 iterations to tol_switch, then FP64 to tol), on the increments of

@@ -199,11 +199,16 @@ int epfft_solve_batch(epfft_ctx *ctx, int32_t n, const epfft_problem *problems,
  * iterates first in FP32 until eta1 and eta2 fall below
  * max(tol_switch, tolerance) (or max_iter), then continues in FP64 from that
  * state until the problem's tolerances hold (or max_iter), so that the
- * indicators in `records` are FP64 ones.  problem->precision must be
+ * indicators in `records` are FP64 ones.  tol_switch = 0 switches
+ * automatically at the FP32 floor: the FP32 stage runs in chunks of 2000
+ * iterations, each continuing from the strain of the last (the state is the
+ * strain alone), until a chunk improves max(eta1, eta2) by less than a
+ * factor 1.5.  problem->precision must be
  * EPFFT_FP64 (the precision of the result and of `fields`); increment k's
  * FP32 stage starts from the accepted FP64 state of increment k-1 shifted by
  * E_k - E_{k-1} and rounded.  records: n_inc FP64-stage records (host);
- * records_fp32 (optional): n_inc records of the FP32 stages.  Returns as
+ * records_fp32 (optional): n_inc records of the FP32 stages (iterations:
+ * all of the stage's).  tol_switch < 0: EPFFT_ERR_ARG.  Returns as
  * epfft_solve, from the FP64 stages. */
 int epfft_solve_refined(epfft_ctx *ctx, const epfft_problem *problem, const epfft_path *path, double tol_switch,
                         epfft_record *records, epfft_record *records_fp32, const epfft_fields *fields);

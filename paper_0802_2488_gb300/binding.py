@@ -338,10 +338,11 @@ def epfft_solve(ctx: Context, problem: Problem, path, fields: bool = False):
     return (rc, rec, f) if fields else (rc, rec)
 
 
-def epfft_solve_refined(ctx: Context, problem: Problem, path, tol_switch: float = 1e-5, fields: bool = False):
+def epfft_solve_refined(ctx: Context, problem: Problem, path, tol_switch: float = 0.0, fields: bool = False):
     """Mixed-precision solve: per increment FP32 iterations to
-    max(tol_switch, tolerance), then FP64 iterations to the tolerances
-    (problem.precision must be 'fp64').  Returns (rc, records of the FP64
+    max(tol_switch, tolerance) (tol_switch = 0: until they stall at the FP32
+    floor), then FP64 iterations to the tolerances (problem.precision must be
+    'fp64').  Returns (rc, records of the FP64
     stages, records of the FP32 stages[, Fields])."""
     p, keep = problem._c()
     cp, parr = _path(path)

@@ -1282,7 +1282,7 @@ int epfft_solve_refined(epfft_ctx* ctx, const epfft_problem* problem, const epff
   if (!ctx || !problem || !path || !records) return EPFFT_ERR_ARG;
   int rc = check_problem(problem);
   if (rc) return rc;
-  if (problem->precision != EPFFT_FP64 || !(tol_switch >= 0.0)) return EPFFT_ERR_ARG;
+  if (problem->precision != EPFFT_FP64 || !(tol_switch >= 0.0)) return EPFFT_ERR_ARG;  // 0: automatic
   if (!supported(problem->L, EPFFT_FP32)) return EPFFT_ERR_UNSUPPORTED;
   if (path->n_inc < 1 || !path->E) return EPFFT_ERR_ARG;
   for (int k = 0; k < 4 * path->n_inc; k++)
@@ -1316,16 +1316,36 @@ int epfft_solve_refined(epfft_ctx* ctx, const epfft_problem* problem, const epff
     epfft_record r32;
     epfft_record* rp32[1] = {&r32};
     void* o32[1] = {e32};
-    if (k == 0) {
-      rc = solve_impl(ctx, 1, &p32, &pk, rp32, nullptr, nullptr, o32, nullptr);
-    } else {
+    const void* i32[1] = {e32};
+    if (k > 0) {
       const double* Ep = path->E + 4 * (k - 1);
       const double dE[4] = {Ek[0] - Ep[0], Ek[1] - Ep[1], Ek[2] - Ep[2], Ek[3] - Ep[3]};
       CK((launch_shift_convert<double, float>(e64, e32, L, dE, ctx->stream)));
-      const void* i32[1] = {e32};
-      rc = solve_impl(ctx, 1, &p32, &pk, rp32, nullptr, i32, o32, nullptr);
     }
-    if (rc != EPFFT_OK && rc != EPFFT_NOT_CONVERGED) return rc;
+    if (tol_switch > 0.0) {
+      rc = solve_impl(ctx, 1, &p32, &pk, rp32, nullptr, k == 0 ? nullptr : i32, o32, nullptr);
+      if (rc != EPFFT_OK && rc != EPFFT_NOT_CONVERGED) return rc;
+    } else {
+      // automatic switch: FP32 chunks of kChunk iterations, each continuing
+      // from the strain the previous one left (the state is the strain
+      // alone: the multiplier is sigma(eps)), until a chunk improves
+      // max(eta1, eta2) by less than kGain, the tolerances hold, or max_iter
+      constexpr int kChunk = 2000;
+      constexpr double kGain = 1.5;
+      epfft_problem pc = p32;
+      double prev = INFINITY;
+      int32_t total = 0;
+      for (int chunk = 0; total < problem->max_iter; chunk++) {
+        pc.max_iter = std::min(kChunk, problem->max_iter - total);
+        rc = solve_impl(ctx, 1, &pc, &pk, rp32, nullptr, (k == 0 && chunk == 0) ? nullptr : i32, o32, nullptr);
+        if (rc != EPFFT_OK && rc != EPFFT_NOT_CONVERGED) return rc;
+        total += r32.iterations;
+        const double eta = std::max(r32.eta1, r32.eta2);
+        if (r32.status == 0 || !(eta * kGain < prev)) break;
+        prev = eta;
+      }
+      r32.iterations = total;
+    }
     if (records_fp32) records_fp32[k] = r32;
     // FP64 stage from the FP32 result, to the problem's tolerances
     const double zero[4] = {0.0, 0.0, 0.0, 0.0};

@@ -29,12 +29,14 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
+@pytest.mark.parametrize("tol_switch", [1e-6, 0.0])
 @pytest.mark.parametrize("L,seed", [(16, 3), (32, 3)])
-def test_refined_solve_certifies_the_tolerance(ctx, L, seed):
+def test_refined_solve_certifies_the_tolerance(ctx, L, seed, tol_switch):
+    """tol_switch = 0: the FP32 stage runs until it stalls at its floor."""
     path = inputs.load_path("shear", 3, 1.0)
     prob = B.Problem(L=L, precision="fp64", void_fraction=0.1, seed=seed, tol_eq=1e-8, tol_macro=1e-8,
                      max_iter=6000)
-    rc, rec, rec32, f = B.epfft_solve_refined(ctx, prob, path, tol_switch=1e-6, fields=True)
+    rc, rec, rec32, f = B.epfft_solve_refined(ctx, prob, path, tol_switch=tol_switch, fields=True)
     assert rc == B.EPFFT_OK
     assert (rec["status"] == 0).all()
     assert (rec["eta1"] < 1e-8).all() and (rec["eta2"] < 1e-8).all()
