@@ -12,6 +12,9 @@ pixel-iterations the method needed (sum over increments of L^2 x
 iterations) per second of device time with the inputs in HBM; `e2e` is the
 same through the C ABI with host buffers (the pinned mask in, records and
 the final strain field out) and the copies inside the timed region.
+On this workload the line also carries the FP32 form of the same solve
+(`fp32`) and, at a tolerance both reach (1e-8 on the first increments),
+plain FP64 against the mixed-precision solve (`refined`).
 
 --impl reference times the oracle (the plain FP64 CPU implementation) on
 this machine's host cores on a bounded sample of the same workload.
@@ -63,7 +66,8 @@ def parse():
                     help="default: fp64 for c1/c2, fp32 for c3/c4")
     ap.add_argument("--cap", type=int, default=None, help="max iterations per increment")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU-baseline leg")
-    ap.add_argument("--no-fp32", action="store_true", help="c2: skip the FP32 companion measurement")
+    ap.add_argument("--no-fp32", action="store_true",
+                    help="c2: skip the FP32 companion and the mixed-precision comparison")
     a = ap.parse_args()
     if a.precision is None:
         a.precision = "fp64" if a.workload in ("c1", "c2") else "fp32"
