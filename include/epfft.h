@@ -212,6 +212,13 @@ int epfft_solve_batch(epfft_ctx *ctx, int32_t n, const epfft_problem *problems,
  * epfft_solve, from the FP64 stages. */
 int epfft_solve_refined(epfft_ctx *ctx, const epfft_problem *problem, const epfft_path *path, double tol_switch,
                         epfft_record *records, epfft_record *records_fp32, const epfft_fields *fields);
+/* The same for n problems of one lattice side and one increment count,
+ * advanced together in both stages (each problem leaves the FP32 stage on
+ * its own switch test); records[i], records_fp32[i] (optional array, entries
+ * may be NULL): n_inc records each; fields: NULL or n entries. */
+int epfft_solve_refined_batch(epfft_ctx *ctx, int32_t n, const epfft_problem *problems, const epfft_path *paths,
+                              double tol_switch, epfft_record *const *records, epfft_record *const *records_fp32,
+                              const epfft_fields *fields);
 
 /* DG2 (Sec. 2): four complete solves of the problem with the Eq. 3
  * operator at (q1, q2), (-q1, -q2), (-q1, q2) and (q1, -q2) in turn, and the

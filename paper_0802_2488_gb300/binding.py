@@ -49,7 +49,7 @@ SYMBOLS = ["epfft_create", "epfft_destroy", "epfft_last_stats", "epfft_strerror"
            "epfft_submit", "epfft_serve_step", "epfft_poll", "epfft_autotune", "epfft_set_tiling",
            "epfft_solve_dg2", "epfft_average5", "epfft_void_plastic", "epfft_indicators",
            "epfft_effective_moduli", "epfft_empirical_curve", "epfft_eps_eq", "epfft_displacement",
-           "epfft_ticket_fields", "epfft_release", "epfft_solve_refined"]
+           "epfft_ticket_fields", "epfft_release", "epfft_solve_refined", "epfft_solve_refined_batch"]
 
 
 class EpfftError(RuntimeError):
@@ -140,6 +140,7 @@ def lib():
         L.epfft_ticket_fields.argtypes = [vp, C.c_int64, i32, vp, vp, vp, vp]
         L.epfft_release.argtypes = [vp, C.c_int64]
         L.epfft_solve_refined.argtypes = [vp, C.POINTER(_Problem), C.POINTER(_Path), dbl, vp, vp, vp]
+        L.epfft_solve_refined_batch.argtypes = [vp, i32, vp, vp, dbl, vp, vp, vp]
         L.epfft_autotune.argtypes = [vp, i32, i32, i32, C.POINTER(i32), C.POINTER(C.c_float)]
         L.epfft_set_tiling.argtypes = [vp, i32, i32, i32]
         L.epfft_project_static.argtypes = [i32, i32, dbl, dbl, C.POINTER(dbl), vp, vp, vp]
@@ -353,6 +354,26 @@ def epfft_solve_refined(ctx: Context, problem: Problem, path, tol_switch: float 
                                    rec32.ctypes.data, C.byref(cf) if cf is not None else None)
     _check(rc, "epfft_solve_refined", (EPFFT_OK, EPFFT_NOT_CONVERGED))
     return (rc, rec, rec32, f) if fields else (rc, rec, rec32)
+
+
+def epfft_solve_refined_batch(ctx: Context, problems: Sequence[Problem], paths: Sequence, tol_switch: float = 0.0):
+    """The mixed-precision solve of problems sharing L and the increment
+    count, advanced together.  Returns (rc, [FP64-stage records],
+    [FP32-stage records])."""
+    n = len(problems)
+    cps, keeps = zip(*(p._c() for p in problems))
+    arr = (_Problem * n)(*cps)
+    pth = [_path(P) for P in paths]
+    carr = (_Path * n)(*(x[0] for x in pth))
+    recs = [np.zeros(x[0].n_inc, dtype=RECORD_DTYPE) for x in pth]
+    recs32 = [np.zeros(x[0].n_inc, dtype=RECORD_DTYPE) for x in pth]
+    rptr = (C.c_void_p * n)(*(r.ctypes.data for r in recs))
+    rptr32 = (C.c_void_p * n)(*(r.ctypes.data for r in recs32))
+    rc = lib().epfft_solve_refined_batch(ctx.handle, n, C.cast(arr, C.c_void_p), C.cast(carr, C.c_void_p),
+                                         float(tol_switch), C.cast(rptr, C.c_void_p), C.cast(rptr32, C.c_void_p),
+                                         None)
+    _check(rc, "epfft_solve_refined_batch", (EPFFT_OK, EPFFT_NOT_CONVERGED))
+    return rc, recs, recs32
 
 
 def epfft_solve_dg2(ctx: Context, problem: Problem, path, fields: bool = False):

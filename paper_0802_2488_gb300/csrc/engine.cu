@@ -1277,98 +1277,137 @@ int epfft_mask(int32_t L, double void_fraction, uint64_t seed, uint8_t* mask_dev
   return EPFFT_OK;
 }
 
-int epfft_solve_refined(epfft_ctx* ctx, const epfft_problem* problem, const epfft_path* path, double tol_switch,
-                        epfft_record* records, epfft_record* records_fp32, const epfft_fields* fields) {
-  if (!ctx || !problem || !path || !records) return EPFFT_ERR_ARG;
-  int rc = check_problem(problem);
-  if (rc) return rc;
-  if (problem->precision != EPFFT_FP64 || !(tol_switch >= 0.0)) return EPFFT_ERR_ARG;  // 0: automatic
-  if (!supported(problem->L, EPFFT_FP32)) return EPFFT_ERR_UNSUPPORTED;
-  if (path->n_inc < 1 || !path->E) return EPFFT_ERR_ARG;
-  for (int k = 0; k < 4 * path->n_inc; k++)
-    if (!std::isfinite(path->E[k])) return EPFFT_ERR_ARG;
+int epfft_solve_refined_batch(epfft_ctx* ctx, int32_t n, const epfft_problem* problems, const epfft_path* paths,
+                              double tol_switch, epfft_record* const* records, epfft_record* const* records_fp32,
+                              const epfft_fields* fields) {
+  if (!ctx || n < 1 || !problems || !paths || !records) return EPFFT_ERR_ARG;
+  if (!(tol_switch >= 0.0)) return EPFFT_ERR_ARG;  // 0: automatic switch
+  const int L = problems[0].L, n_inc = paths[0].n_inc;
+  for (int i = 0; i < n; i++) {
+    int rc = check_problem(&problems[i]);
+    if (rc) return rc;
+    if (problems[i].precision != EPFFT_FP64 || problems[i].L != L) return EPFFT_ERR_ARG;
+    if (paths[i].n_inc != n_inc || n_inc < 1 || !paths[i].E || !records[i]) return EPFFT_ERR_ARG;
+    for (int k = 0; k < 4 * n_inc; k++)
+      if (!std::isfinite(paths[i].E[k])) return EPFFT_ERR_ARG;
+  }
+  if (!supported(L, EPFFT_FP32)) return EPFFT_ERR_UNSUPPORTED;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return EPFFT_ERR_CUDA;
-  const int L = problem->L, n_inc = path->n_inc;
   const size_t LL = (size_t)L * L;
   Arena A(ctx);
-  float* e32 = (float*)A.get(4 * LL * sizeof(float));
-  double* e64 = (double*)A.get(4 * LL * sizeof(double));
-  uint8_t* mask = problem->mask ? nullptr : (uint8_t*)A.get(LL);
-  if (!e32 || !e64 || (!problem->mask && !mask)) return EPFFT_ERR_OOM;
-  // both stages see the same voids
-  if (mask) CK(launch_mask(mask, (int64_t)LL, problem->seed, void_threshold(problem->void_fraction), ctx->stream));
-  epfft_problem p64 = *problem;
-  if (mask) {
-    p64.mask = mask;
-    p64.mask_on_device = 1;
+  std::vector<float*> e32(n);
+  std::vector<double*> e64(n);
+  std::vector<epfft_problem> p64(problems, problems + n), p32(n);
+  for (int i = 0; i < n; i++) {
+    e32[i] = (float*)A.get(4 * LL * sizeof(float));
+    e64[i] = (double*)A.get(4 * LL * sizeof(double));
+    if (!e32[i] || !e64[i]) return EPFFT_ERR_OOM;
+    if (!problems[i].mask) {  // both stages see the same voids
+      uint8_t* m = (uint8_t*)A.get(LL);
+      if (!m) return EPFFT_ERR_OOM;
+      CK(launch_mask(m, (int64_t)LL, problems[i].seed, void_threshold(problems[i].void_fraction), ctx->stream));
+      p64[i].mask = m;
+      p64[i].mask_on_device = 1;
+    }
+    p32[i] = p64[i];
+    p32[i].precision = EPFFT_FP32;
+    p32[i].tol_eq = std::max(tol_switch, problems[i].tol_eq);
+    p32[i].tol_macro = std::max(tol_switch, problems[i].tol_macro);
   }
-  epfft_problem p32 = p64;
-  p32.precision = EPFFT_FP32;
-  p32.tol_eq = std::max(tol_switch, problem->tol_eq);
-  p32.tol_macro = std::max(tol_switch, problem->tol_macro);
+  // automatic switch: FP32 chunks of kChunk iterations, each continuing from
+  // the strain the previous one left (the state is the strain alone: the
+  // multiplier is sigma(eps)); a problem leaves the FP32 stage when a chunk
+  // improves its max(eta1, eta2) by less than kGain, its tolerances hold, or
+  // it reaches max_iter
+  constexpr int kChunk = 2000;
+  constexpr double kGain = 1.5;
+  const double zero[4] = {0.0, 0.0, 0.0, 0.0};
   int status = EPFFT_OK;
+  std::vector<epfft_path> pk(n);
+  std::vector<epfft_record> r32(n);
+  std::vector<int32_t> total(n);
+  std::vector<double> prev(n);
+  std::vector<epfft_fields> fk(fields ? n : 0);
   for (int k = 0; k < n_inc; k++) {
-    const double* Ek = path->E + 4 * k;
-    const epfft_path pk = {1, 0, Ek};
     // FP32 stage: the accepted FP64 state of increment k - 1 shifted by
     // E_k - E_{k-1} and rounded (increment 0 starts from the unstrained
     // lattice, shifted by E_0 inside the solve)
-    epfft_record r32;
-    epfft_record* rp32[1] = {&r32};
-    void* o32[1] = {e32};
-    const void* i32[1] = {e32};
-    if (k > 0) {
-      const double* Ep = path->E + 4 * (k - 1);
-      const double dE[4] = {Ek[0] - Ep[0], Ek[1] - Ep[1], Ek[2] - Ep[2], Ek[3] - Ep[3]};
-      CK((launch_shift_convert<double, float>(e64, e32, L, dE, ctx->stream)));
-    }
-    if (tol_switch > 0.0) {
-      rc = solve_impl(ctx, 1, &p32, &pk, rp32, nullptr, k == 0 ? nullptr : i32, o32, nullptr);
-      if (rc != EPFFT_OK && rc != EPFFT_NOT_CONVERGED) return rc;
-    } else {
-      // automatic switch: FP32 chunks of kChunk iterations, each continuing
-      // from the strain the previous one left (the state is the strain
-      // alone: the multiplier is sigma(eps)), until a chunk improves
-      // max(eta1, eta2) by less than kGain, the tolerances hold, or max_iter
-      constexpr int kChunk = 2000;
-      constexpr double kGain = 1.5;
-      epfft_problem pc = p32;
-      double prev = INFINITY;
-      int32_t total = 0;
-      for (int chunk = 0; total < problem->max_iter; chunk++) {
-        pc.max_iter = std::min(kChunk, problem->max_iter - total);
-        rc = solve_impl(ctx, 1, &pc, &pk, rp32, nullptr, (k == 0 && chunk == 0) ? nullptr : i32, o32, nullptr);
-        if (rc != EPFFT_OK && rc != EPFFT_NOT_CONVERGED) return rc;
-        total += r32.iterations;
-        const double eta = std::max(r32.eta1, r32.eta2);
-        if (r32.status == 0 || !(eta * kGain < prev)) break;
-        prev = eta;
+    for (int i = 0; i < n; i++) {
+      const double* Ek = paths[i].E + 4 * k;
+      pk[i] = {1, 0, Ek};
+      total[i] = 0;
+      prev[i] = INFINITY;
+      if (k > 0) {
+        const double* Ep = paths[i].E + 4 * (k - 1);
+        const double dE[4] = {Ek[0] - Ep[0], Ek[1] - Ep[1], Ek[2] - Ep[2], Ek[3] - Ep[3]};
+        CK((launch_shift_convert<double, float>(e64[i], e32[i], L, dE, ctx->stream)));
       }
-      r32.iterations = total;
     }
-    if (records_fp32) records_fp32[k] = r32;
-    // FP64 stage from the FP32 result, to the problem's tolerances
-    const double zero[4] = {0.0, 0.0, 0.0, 0.0};
-    CK((launch_shift_convert<float, double>(e32, e64, L, zero, ctx->stream)));
-    epfft_fields fk;
-    const epfft_fields* fp = nullptr;
-    if (fields) {
-      fk = *fields;
-      fk.eps = k == n_inc - 1 ? fields->eps : nullptr;
-      fk.plastic = fields->plastic ? fields->plastic + LL * (size_t)k : nullptr;
-      fk.labels = fields->labels ? fields->labels + LL * (size_t)k : nullptr;
-      fp = &fk;
+    std::vector<int> act(n);
+    for (int i = 0; i < n; i++) act[i] = i;
+    for (bool first = true; !act.empty(); first = false) {
+      std::vector<epfft_problem> pa;
+      std::vector<epfft_path> pth;
+      std::vector<epfft_record*> rp;
+      std::vector<const void*> in;
+      std::vector<void*> out;
+      for (int i : act) {
+        pa.push_back(p32[i]);
+        pa.back().max_iter = tol_switch > 0.0 ? problems[i].max_iter : std::min(kChunk, problems[i].max_iter - total[i]);
+        pth.push_back(pk[i]);
+        rp.push_back(&r32[i]);
+        in.push_back((k == 0 && first) ? nullptr : e32[i]);
+        out.push_back(e32[i]);
+      }
+      int rc = solve_impl(ctx, (int32_t)act.size(), pa.data(), pth.data(), rp.data(), nullptr, in.data(), out.data(),
+                          nullptr);
+      if (rc != EPFFT_OK && rc != EPFFT_NOT_CONVERGED) return rc;
+      std::vector<int> next;
+      for (int i : act) {
+        total[i] += r32[i].iterations;
+        const double eta = std::max(r32[i].eta1, r32[i].eta2);
+        if (tol_switch == 0.0 && r32[i].status != 0 && eta * kGain < prev[i] && total[i] < problems[i].max_iter)
+          next.push_back(i);
+        prev[i] = eta;
+      }
+      act.swap(next);
     }
-    epfft_record* rp64[1] = {records + k};
-    const void* i64[1] = {e64};
-    void* o64[1] = {e64};
-    rc = solve_impl(ctx, 1, &p64, &pk, rp64, fp, i64, o64, nullptr);
+    for (int i = 0; i < n; i++) {
+      r32[i].iterations = total[i];
+      if (records_fp32 && records_fp32[i]) records_fp32[i][k] = r32[i];
+      CK((launch_shift_convert<float, double>(e32[i], e64[i], L, zero, ctx->stream)));
+      if (fields) {
+        fk[i] = fields[i];
+        fk[i].eps = k == n_inc - 1 ? fields[i].eps : nullptr;
+        fk[i].plastic = fields[i].plastic ? fields[i].plastic + LL * (size_t)k : nullptr;
+        fk[i].labels = fields[i].labels ? fields[i].labels + LL * (size_t)k : nullptr;
+      }
+    }
+    // FP64 stage of every problem from its FP32 result, to its tolerances
+    std::vector<epfft_record*> rp64(n);
+    std::vector<const void*> in64(n);
+    std::vector<void*> out64(n);
+    for (int i = 0; i < n; i++) {
+      rp64[i] = records[i] + k;
+      in64[i] = e64[i];
+      out64[i] = e64[i];
+    }
+    int rc = solve_impl(ctx, n, p64.data(), pk.data(), rp64.data(), fields ? fk.data() : nullptr, in64.data(),
+                        out64.data(), nullptr);
     if (rc == EPFFT_ERR_NUMERIC) return rc;
     if (rc == EPFFT_NOT_CONVERGED) status = EPFFT_NOT_CONVERGED;
     else if (rc != EPFFT_OK) return rc;
   }
   CK(cudaStreamSynchronize(ctx->stream));
   return status;
+}
+
+int epfft_solve_refined(epfft_ctx* ctx, const epfft_problem* problem, const epfft_path* path, double tol_switch,
+                        epfft_record* records, epfft_record* records_fp32, const epfft_fields* fields) {
+  if (!ctx || !problem || !path || !records) return EPFFT_ERR_ARG;
+  epfft_record* r[1] = {records};
+  epfft_record* r32[1] = {records_fp32};
+  return epfft_solve_refined_batch(ctx, 1, problem, path, tol_switch, r, records_fp32 ? r32 : nullptr, fields);
 }
 
 int epfft_iterate(epfft_ctx* ctx, const epfft_problem* problem, const double E[4], void* eps_dev, int32_t n_iter,

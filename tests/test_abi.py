@@ -82,6 +82,7 @@ def test_argument_checks_of_analysis_entry_points(lib):
     assert lib.epfft_ticket_fields(None, 0, 0, None, None, None, None) == B.EPFFT_ERR_ARG
     assert lib.epfft_release(None, 0) == B.EPFFT_ERR_ARG
     assert lib.epfft_solve_refined(None, None, None, C.c_double(1e-6), None, None, None) == B.EPFFT_ERR_ARG
+    assert lib.epfft_solve_refined_batch(None, 1, None, None, C.c_double(0.0), None, None, None) == B.EPFFT_ERR_ARG
     assert lib.epfft_effective_moduli(None, None, C.c_double(1e-3), None, None) == B.EPFFT_ERR_ARG
 
 

@@ -54,6 +54,27 @@ def test_refined_solve_certifies_the_tolerance(ctx, L, seed, tol_switch):
     assert rec["n_clusters"][-1] == n
 
 
+def test_refined_batch(ctx):
+    """Three lattices advanced together (each leaves the FP32 stage on its
+    own switch test): every one certified in FP64 and at the oracle's fixed
+    point like a refined solve of its own."""
+    L = 16
+    path = inputs.load_path("shear", 2, 1.0)
+    probs = [B.Problem(L=L, precision="fp64", void_fraction=0.1, seed=s, tol_eq=1e-8, tol_macro=1e-8, max_iter=6000)
+             for s in (1, 2, 3)]
+    rc, recs, recs32 = B.epfft_solve_refined_batch(ctx, probs, [path] * 3)
+    assert rc == B.EPFFT_OK
+    for s, r, r32 in zip((1, 2, 3), recs, recs32):
+        assert (r["status"] == 0).all() and (r["eta1"] < 1e-8).all() and (r["eta2"] < 1e-8).all()
+        assert (r32["iterations"] >= 1).all()
+        ref = O.solve(O.mask(L, 0.1, s), O.material(), path, tol_eq=1e-8, tol_macro=1e-8, max_iter=6000)
+        assert ref.status == 0
+        assert rel(r["sig_mean"], ref.records["sig_mean"]) < 1e-6, s
+    # unequal increment counts are refused
+    with pytest.raises(B.EpfftError):
+        B.epfft_solve_refined_batch(ctx, probs[:2], [path, path[:1]])
+
+
 def test_refined_solve_arguments(ctx):
     path = inputs.load_path("shear", 1, 0.5)
     with pytest.raises(B.EpfftError):
