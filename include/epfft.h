@@ -195,15 +195,15 @@ int epfft_solve_batch(epfft_ctx *ctx, int32_t n, const epfft_problem *problems,
                       const epfft_fields *fields);
 
 /* Mixed-precision solve (Sec. 2 loading; the FP32 path cannot certify
- * tolerances below its rounding floor of about 1e-7): each increment
- * iterates first in FP32 until eta1 and eta2 fall below
- * max(tol_switch, tolerance) (or max_iter), then continues in FP64 from that
- * state until the problem's tolerances hold (or max_iter), so that the
- * indicators in `records` are FP64 ones.  tol_switch = 0 switches
- * automatically at the FP32 floor: the FP32 stage runs in chunks of 2000
- * iterations, each continuing from the strain of the last (the state is the
- * strain alone), until a chunk improves max(eta1, eta2) by less than a
- * factor 1.5.  problem->precision must be
+ * tolerances below its rounding floor, eta1 of a few 1e-6 on a 256^2
+ * lattice with voids): each increment iterates first in FP32 until eta1 and
+ * eta2 fall below max(tol_switch, tolerance) (or max_iter), then continues
+ * in FP64 from that state until the problem's tolerances hold (or
+ * max_iter), so that the indicators in `records` are FP64 ones.
+ * tol_switch = 0 switches automatically at the FP32 floor: the FP32 stage
+ * runs in chunks of 2000 iterations, each continuing from the strain of the
+ * last (the state is the strain alone), until a chunk improves
+ * max(eta1, eta2) by less than a factor 1.5.  problem->precision must be
  * EPFFT_FP64 (the precision of the result and of `fields`); increment k's
  * FP32 stage starts from the accepted FP64 state of increment k-1 shifted by
  * E_k - E_{k-1} and rounded.  records: n_inc FP64-stage records (host);
