@@ -1,7 +1,8 @@
 """Mixed-precision solve: FP32 iterations to a switch tolerance, then FP64
 iterations to the tolerance, per increment.  Its records are FP64 ones and
-certify the tolerance the FP32 path alone cannot reach (rounding floor
-about 1e-7); the fixed point is that of the FP64 oracle.  Two solutions
+certify the tolerance the FP32 path alone cannot reach (its rounding
+floor: eta1 of a few 1e-6 on a 256^2 lattice with voids); the fixed point
+is that of the FP64 oracle.  Two solutions
 that both meet eta2 < tol sit within tol / (1 - rho) of the fixed point, rho
 the per-iteration contraction (here below 0.99, from the iteration counts),
 so the macroscopic stresses agree within 100 tol = 1e-6 relative."""
