@@ -74,3 +74,34 @@ def test_cg1_dg1_unchanged_by_the_option(green):
     b = O.solve(mask, mat, path, 1e-7, 1e-7, 3000, eq_test=O.EQ_FIXED_POINT)
     assert a.records.tobytes() == b.records.tobytes()
     assert np.array_equal(a.eps, b.eps)
+
+
+def test_dg2_needs_fewer_iterations_than_cg1_on_the_one_void_cell():
+    """Sec. 2's convergence claim on the periodic void lattice, under one
+    criterion for every operator (eta3, eta2 < 1e-5): on the cell of Fig. 1
+    (L = 32, f = 0.1, the paper's matrix, equibiaxial past yield) each DG2
+    member, i.e. the Eq. 3 scheme of the lattice or of a mirror image, needs
+    fewer iterations than CG1; the mirror-symmetric cell gives the four
+    members equal counts."""
+    L = 32
+    mask = inputs.one_void_cell(L, 0.1)
+    path = inputs.load_path("equibiaxial", 3, 1.5, inputs.PAPER_MU, inputs.PAPER_YIELD)
+    kw = dict(tol_eq=1e-5, tol_macro=1e-5, max_iter=20000, eq_test=O.EQ_FIXED_POINT)
+
+    def mat(g):
+        return O.material(lam=inputs.PAPER_LAMBDA, mu=inputs.PAPER_MU, Y=inputs.PAPER_YIELD, green=g)
+
+    dg2 = O.solve_dg2(mask, mat(O.GREEN_EQ3), path, **kw)
+    cg1 = O.solve(mask, mat(O.GREEN_CG1), path, **kw)
+    assert cg1.status == 0 and all(m.status == 0 for m in dg2.members)
+    counts = [int(m.records["iterations"].sum()) for m in dg2.members]
+    assert len(set(counts)) == 1
+    assert counts[0] < int(cg1.records["iterations"].sum())
+
+
+def test_one_void_cell_geometry():
+    for L, f in ((32, 0.1), (512, 0.1), (64, 0.3)):
+        m = inputs.one_void_cell(L, f)
+        assert abs(m.mean() - f) < 4.0 / L  # the disc's pixel rounding is O(perimeter / L^2)
+        assert (m == m[::-1]).all() and (m == m[:, ::-1]).all() and (m == m.T).all()
+        assert m[L // 2, L // 2] == 1 and m[0, 0] == 0
