@@ -12,9 +12,9 @@ pixel-iterations the method needed (sum over increments of L^2 x
 iterations) per second of device time with the inputs in HBM; `e2e` is the
 same through the C ABI with host buffers (the pinned mask in, records and
 the final strain field out) and the copies inside the timed region.
-On this workload the line also carries the FP32 form of the same solve
-(`fp32`) and, at a tolerance both reach (1e-8 on the first increments),
-plain FP64 against the mixed-precision solve (`refined`).
+On this workload a single-GPU line also carries the FP32 form of the same
+solve (`fp32`) and, at a tolerance both reach (1e-8 on the first
+increments), plain FP64 against the mixed-precision solve (`refined`).
 
 --impl reference times the oracle (the plain FP64 CPU implementation) on
 this machine's host cores on a bounded sample of the same workload.
@@ -67,7 +67,8 @@ def parse():
     ap.add_argument("--cap", type=int, default=None, help="max iterations per increment")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-fp32", action="store_true",
-                    help="c2: skip the FP32 companion and the mixed-precision comparison")
+                    help="c2: skip the FP32 companion and the mixed-precision comparison "
+                         "(both run on single-GPU runs only)")
     a = ap.parse_args()
     if a.precision is None:
         a.precision = "fp64" if a.workload in ("c1", "c2") else "fp32"
@@ -488,7 +489,7 @@ def main():
     col_ms, row_ms = B.epfft_time_passes(ctx, pd[0], E_mid, 50, n_batch=len(probs))
 
     companion = None
-    if args.workload == "c2" and args.precision == "fp64" and not args.no_fp32:
+    if args.workload == "c2" and args.precision == "fp64" and not args.no_fp32 and ws == 1:
         B.epfft_autotune(ctx, L, "fp32")
         pf = problems("fp32", False)
         for _ in range(args.warmup):
@@ -504,7 +505,7 @@ def main():
                      "dtype": "f32 fields and FFTs, f64 reductions"}
 
     refined = None
-    if args.workload == "c2" and args.precision == "fp64" and not args.no_fp32:
+    if args.workload == "c2" and args.precision == "fp64" and not args.no_fp32 and ws == 1:
         refined = refined_vs_plain(B, ctx, stream, flush, masks_dev[0], L, paths[0][:2], torch)
 
     t_step = dev_s / args.steps
