@@ -22,7 +22,8 @@
  *     u(x + e_j) - u(x)  <->  (exp(i q_j) - 1) u^ = i k_j u^.
  *
  * Functions and the passages they follow:
- *   orc_splitmix64, orc_mask  : i.i.d. void pixels at concentration f
+ *   orc_splitmix64, orc_mask,
+ *   orc_void_threshold        : i.i.d. void pixels at concentration f
  *                               (Sec. 2, "randomly chosen as voids, in
  *                               concentration f"); the random numbers are
  *                               the published SplitMix64 stream
@@ -35,14 +36,18 @@
  *                               (the four operators of DG2), the continuum
  *                               operator CG1 (Eq. 3 with k_j = q_j), and the
  *                               symmetrized DG1 operator (equation after
- *                               Eq. 3).
+ *                               Eq. 3); orc_green_apply applies one of them
+ *                               to a spectrum (Eqs. 2-3).
  *   orc_avg5                  : the 5-point local average of CG2 (Sec. 2).
  *   orc_displacement          : the displacement field of a strain field (Sec. 2).
- *   orc_sigma                 : elastic-perfectly plastic Mises law under
+ *   orc_sigma, orc_sigma_field: elastic-perfectly plastic Mises law under
  *                               deformation theory (Sec. 2, Sec. 3: plastic
- *                               zone where sigma_eq = Y, voids sigma = 0).
- *   orc_local_solve           : pixelwise step of the augmented Lagrangian
- *                               (Sec. 1, ref. MICH00).
+ *                               zone where sigma_eq = Y, voids sigma = 0),
+ *                               per pixel and over a field.
+ *   orc_local_solve,
+ *   orc_local_field           : pixelwise step of the augmented Lagrangian
+ *                               (Sec. 1, ref. MICH00), per pixel and over a
+ *                               field.
  *   orc_al_step               : one augmented-Lagrangian / Uzawa iteration.
  *   orc_stats                 : the convergence indicators of Sec. 2
  *                               ("Convergence issues"), backward-difference
@@ -55,6 +60,9 @@
  *                               void-free cluster connected to its nearest
  *                               void (Sec. 3), and the counts behind the
  *                               indicators of Sec. 3.
+ *   orc_threads, orc_set_threads : OpenMP threads of the loops (the
+ *                               benchmark times the oracle on one host core
+ *                               and on all of them).
  */
 #include <complex.h>
 #ifdef _OPENMP
