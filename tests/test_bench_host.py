@@ -28,3 +28,27 @@ def test_oracle_thread_control():
     finally:
         O.set_threads(n)
     assert O.threads() == n
+
+
+def test_clock_summary_parses_nvidia_smi_rows():
+    """Median SM clock under load, the maximum, and the throttle reasons seen
+    active in any sample (the bench line's `clocks`)."""
+    s = bench.ClockSampler(0)
+    rows = [
+        "0, 2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1965, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, [N/A], 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ]
+    s.f.write("\n".join(rows) + "\n")
+    out = s.summary()
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"] and out["samples"] == 4
+    assert not os.path.exists(s.f.name)
+
+
+def test_clock_summary_without_samples():
+    s = bench.ClockSampler(0)
+    out = s.summary()
+    assert out["sm_mhz"] is None and out["reasons"] == ["nvidia-smi unavailable"]
