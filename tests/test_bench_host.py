@@ -52,3 +52,13 @@ def test_clock_summary_without_samples():
     s = bench.ClockSampler(0)
     out = s.summary()
     assert out["sm_mhz"] is None and out["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_workload_configs():
+    """The bench's workloads are the stated configurations, named by what
+    they are, with the iteration cap in the config block."""
+    for name, L, n, n_inc in (("c1", 64, 1, 20), ("c2", 256, 1, 40), ("c3", 512, 64, 30), ("c4", 4096, 1, 50)):
+        probs, cfg = bench.workload(name, 77)
+        assert len(probs) == n and cfg["L"] == L and cfg["n_solves"] == n and cfg["n_inc"] == n_inc
+        assert cfg["max_iter_per_increment"] == 77 and cfg["tol"] == 1e-8
+        assert "at most 77 iterations" in cfg["workload"] and f"L={L}" in cfg["workload"]
