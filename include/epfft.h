@@ -176,7 +176,10 @@ int epfft_last_stats(const epfft_ctx *ctx, epfft_stats *out);
 /* Solves (Sec. 2: strain-controlled loading by increments)                */
 /* ---------------------------------------------------------------------- */
 
-/* Blocking solve of one problem along `path`.  records: host array of
+/* Blocking solve of one problem along `path` (Sec. 2: strain-controlled
+ * loading by increments, each iterated with the augmented Lagrangian of
+ * Sec. 1 and the Green operator of Eq. 3 until the indicators of Sec. 2,
+ * "Convergence issues", meet the tolerances).  records: host array of
  * path->n_inc entries (filled).  fields: optional outputs (may be NULL).
  * Returns EPFFT_OK when every increment converged, EPFFT_NOT_CONVERGED when
  * some increment stopped at max_iter (its record has status 1), or an
@@ -184,10 +187,10 @@ int epfft_last_stats(const epfft_ctx *ctx, epfft_stats *out);
 int epfft_solve(epfft_ctx *ctx, const epfft_problem *problem, const epfft_path *path,
                 epfft_record *records, const epfft_fields *fields);
 
-/* Blocking solve of n independent problems advanced together on the
- * device, one augmented-Lagrangian pass of every unfinished problem per
- * step of a single device-side loop (one CUDA graph launch).  All problems
- * share L and precision (else EPFFT_ERR_ARG).  records[i] is a host array
+/* Blocking solve of n independent problems (each as epfft_solve, Sec. 2)
+ * advanced together on the device, one augmented-Lagrangian pass of every
+ * unfinished problem per step of a single device-side loop (one CUDA graph
+ * launch).  All problems share L and precision (else EPFFT_ERR_ARG).  records[i] is a host array
  * of paths[i].n_inc entries; fields may be NULL or an array of n.  The
  * arithmetic of each problem does not depend on the others in the batch. */
 int epfft_solve_batch(epfft_ctx *ctx, int32_t n, const epfft_problem *problems,
@@ -212,8 +215,8 @@ int epfft_solve_batch(epfft_ctx *ctx, int32_t n, const epfft_problem *problems,
  * epfft_solve, from the FP64 stages. */
 int epfft_solve_refined(epfft_ctx *ctx, const epfft_problem *problem, const epfft_path *path, double tol_switch,
                         epfft_record *records, epfft_record *records_fp32, const epfft_fields *fields);
-/* The same for n problems of one lattice side and one increment count,
- * advanced together in both stages (each problem leaves the FP32 stage on
+/* The same (Sec. 2 loading) for n problems of one lattice side and one
+ * increment count, advanced together in both stages (each problem leaves the FP32 stage on
  * its own switch test); records[i], records_fp32[i] (optional array, entries
  * may be NULL): n_inc records each; fields: NULL or n entries. */
 int epfft_solve_refined_batch(epfft_ctx *ctx, int32_t n, const epfft_problem *problems, const epfft_path *paths,
@@ -383,7 +386,8 @@ int epfft_release(epfft_ctx *ctx, int64_t ticket);
  * Asynchronous. */
 int epfft_mask(int32_t L, double void_fraction, uint64_t seed, uint8_t *mask_dev, void *stream);
 
-/* n_iter augmented-Lagrangian iterations of `problem` (mask from the
+/* n_iter augmented-Lagrangian iterations (Sec. 1; Eqs. 2-3 for the
+ * compatible strain) of `problem` (mask from the
  * problem) at fixed mean strain E[4], starting from the local strain
  * eps_dev (device, L*L*4 reals of the problem's precision; the multiplier
  * starts at sigma(eps)), which is overwritten with the n_iter-th iterate.
