@@ -31,6 +31,10 @@
  * epfft_strerror() names it.  Invalid arguments never reach the GPU.  There
  * is no CPU fallback: without a usable CUDA device the calls return
  * EPFFT_ERR_CUDA.  A context is used by one host thread at a time.
+ *
+ * Calls that compute a part of the method cite the passage that defines it.
+ * Contexts, batching, serving, tiling and timing have no counterpart in the
+ * paper: they are how this library runs the method on a GPU.
  */
 #ifndef EPFFT_H
 #define EPFFT_H
