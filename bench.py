@@ -2,19 +2,29 @@
 """Throughput of the augmented-Lagrangian FFT solve (Willot & Pellegrini,
 arXiv:0802.2488) on one GB300, printed as one JSON line.
 
-A step is one whole solve of the shear workload: L = 256 lattice, i.i.d.
-Bernoulli voids f = 0.20 (seed 0), matrix mu = 1, lambda = 1.5, Y = 1, C0 =
-matrix, 40 equal increments of E12 up to 3x the void-free yield strain,
-equilibrium and macro tolerances 1e-8, each increment capped at --cap
-iterations.  The mask is generated, all increments are iterated, and the
-plastic clusters of every increment are labelled.  `value` counts the
-pixel-iterations the method needed (sum over increments of L^2 x
-iterations) per second of device time with the inputs in HBM; `e2e` is the
-same through the C ABI with host buffers (the pinned mask in, records and
-the final strain field out) and the copies inside the timed region.
-On this workload a single-GPU line also carries the FP32 form of the same
-solve (`fp32`) and, at a tolerance both reach (1e-8 on the first
-increments), plain FP64 against the mixed-precision solve (`refined`).
+Headline (the default workload): the batched FP32 form.  A step is one
+batched solve of 64 realizations of an L = 512 lattice (i.i.d. Bernoulli
+voids f in {0.05, 0.10, 0.20, 0.30} x seeds 0-15; seeds 0-7 equibiaxial to
+2x the void-free yield strain, 8-15 shear to 3x), 30 increments each, all
+advanced together in one device-driven loop, equilibrium and macro
+tolerances 1e-8, each increment capped at --cap iterations; the masks are
+generated and the plastic clusters of every increment labelled.  `value`
+counts the pixel-iterations the method ran (sum over solves and increments
+of L^2 x iterations) per second of device time with the inputs in HBM;
+`e2e` is the same through the C ABI with host buffers (pinned masks in;
+records, final strain, plastic flags and cluster labels out) and the copies
+inside the timed region.  `convergence` gives what each increment reached
+(eta1, eta2 and how many increments met the tolerances before the cap);
+solves/s "at tol" is reported only when every increment converged.
+
+A single-GPU default run adds sub-objects measured in the same process:
+  c4   the L = 4096, f = 0.35 lattice (FP32), with both passes' HBM roofline;
+  c5   the serving stream (Poisson arrivals, L in {128..1024}): p50/p99
+       latency and solves/s through submit / serve_step / poll;
+  c2   the L = 256 shear lattice in plain FP64 (FP64-ALU roofline against the
+       measured FP64 peak), its FP32 form with the field and curve errors
+       against FP64, and plain FP64 against the mixed-precision solve at a
+       tolerance both reach.
 
 --impl reference times the oracle (the plain FP64 CPU implementation) on
 this machine's host cores on a bounded sample of the same workload.
@@ -43,38 +53,31 @@ UNIT = "pixel-iterations/s"
 L2_FLUSH_BYTES = 512 << 20
 
 
-# DRAM bytes (read + write) per launch of the dominant pass, from one ncu
-# capture of the same kernel, tiling and solves per launch
-# (profiles/passes_dram_traffic.md); a configuration not listed, or one
-# whose kernel changed after the capture, reports null.
-TRAFFIC = {
-    ("row_pass<double,256>", 1, 1): 3828480,
-    ("row_pass<float,512>", 0, 64): 488783104 + 681300480,
-    ("row_pass<float,4096>", 0, 1): 542052096 + 696104448,
-}
-
-
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="epfft", choices=["epfft", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "c5"])
     ap.add_argument("--requests", type=int, default=150, help="c5: requests in the stream")
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
-                    help="default: fp64 for c1/c2, fp32 for c3/c4")
+                    help="default: fp64 for c1/c2, fp32 for c3/c4/c5")
     ap.add_argument("--cap", type=int, default=None, help="max iterations per increment")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU-baseline leg")
-    ap.add_argument("--no-fp32", action="store_true",
-                    help="c2: skip the FP32 companion and the mixed-precision comparison "
-                         "(both run on single-GPU runs only)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the c4 / c5 / c2 sub-objects of a single-GPU default run")
     a = ap.parse_args()
     if a.precision is None:
         a.precision = "fp64" if a.workload in ("c1", "c2") else "fp32"
     if a.cap is None:
-        a.cap = {"c1": 2000, "c2": 300, "c3": 100, "c4": 60, "c5": 20}[a.workload]
+        a.cap = CAPS[a.workload]
     return a
+
+
+# iterations per increment at most, per workload (the AL needs O(10^3) and
+# more per increment on these lattices, see the convergence objects)
+CAPS = {"c1": 2000, "c2": 300, "c3": 100, "c4": 60, "c5": 20}
 
 
 def dist_env():
@@ -326,27 +329,161 @@ def refined_vs_plain(B, ctx, stream, flush, mask, L, path, torch, tol=1e-8, tol_
             "speedup": t64 / tr}
 
 
-def run_serving(args):
-    """C5: Poisson request stream through the serving engine."""
-    import torch
-    from paper_0802_2488_gb300 import binding as B
-    from paper_0802_2488_gb300 import build
+def convergence(recs, tol: float = 1e-8) -> dict:
+    """What the increments of a step reached: how many met both tolerances
+    before the cap (status 0), how many stopped at the cap (status 1), and
+    eta1 / eta2 at the accepted iterate."""
+    st = np.concatenate([np.asarray(r["status"]) for r in recs])
+    e1 = np.concatenate([np.asarray(r["eta1"]) for r in recs])
+    e2 = np.concatenate([np.asarray(r["eta2"]) for r in recs])
+    its = np.concatenate([np.asarray(r["iterations"]) for r in recs])
+    return {"tol": tol, "increments": int(st.size), "converged": int((st == 0).sum()),
+            "capped": int((st == 1).sum()), "numeric_failures": int((st == 2).sum()),
+            "eta1_max": float(e1.max()), "eta1_median": float(np.median(e1)),
+            "eta2_max": float(e2.max()), "eta2_median": float(np.median(e2)),
+            "iterations_per_increment_mean": float(its.mean())}
+
+
+def peaks(B, ctx, precision):
+    """Roofline denominators: the measured HBM copy rate (MEASURED_PEAKS.json)
+    for the FP32 passes; the FP64 FMA rate measured here on this device
+    (epfft_fp64_peak) for the FP64 passes."""
+    if precision == "fp32":
+        mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(mp):
+            return json.load(open(mp))["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs (of measured)"
+        return 6800.0, "fallback 6800 GB/s (of fallback)"
+    r = B.epfft_fp64_peak(ctx)
+    return r["tflops"], (f"measured here: FP64 FMA chains on all {r['n_sm']} SMs, CUDA events, best of 5 "
+                         f"({r['ms']:.3f} ms per launch) (of measured)")
+
+
+def roofline(precision, L, nb, col_ms, row_ms, peak, peak_source):
+    """Both fused passes against their roof, from this run's CUDA-event pass
+    timings; the dominant (longer) pass is the line's `roofline`.
+    FP32 (HBM): algorithmic bytes per pixel, row pass 73 (spectrum read and
+    written 24, sigma of iterate n read 16, new strain and sigma written 32,
+    void mask 1), column pass 24 (spectrum read and written).
+    FP64 (FP64 ALU): flops per pixel, row pass 15 log2 L + 60 (row
+    transforms, local step), column pass 15 log2 L + 25 (column transforms,
+    Green operator)."""
+    n = L * L * nb
+    lg = int(np.log2(L))
+    if precision == "fp32":
+        work = {"row": 73 * n, "col": 24 * n}
+        unit, scale, bound = "GB/s", 1e9, "hbm"
+    else:
+        work = {"row": (15 * lg + 60) * n, "col": (15 * lg + 25) * n}
+        unit, scale, bound = "TFLOP/s", 1e12, "alu"
+    ms = {"row": row_ms, "col": col_ms}
+    rt = "float" if precision == "fp32" else "double"
+    passes = {}
+    for k in ("row", "col"):
+        a = work[k] / (ms[k] * 1e-3) / scale
+        passes[k] = {"kernel": f"{k}_pass<{rt},{L}>", "ms": ms[k], "achieved": a, "frac": a / peak,
+                     "work_per_launch": work[k]}
+    dom = "row" if row_ms >= col_ms else "col"
+    d = passes[dom]
+    return {"bound": bound, "kernel": d["kernel"], "achieved": d["achieved"], "peak": peak, "unit": unit,
+            "frac": d["frac"], "traffic": None,
+            "traffic_note": "null: DRAM bytes come from ncu captures (profiles/), never from a timed run",
+            "peak_source": peak_source, "passes": passes,
+            "timing": "epfft_time_passes: CUDA events around each launch on the context stream, mean of the "
+                      "timed launches, the same launch shape as the solve"}
+
+
+def solve_line(B, ctx, stream, flush, torch, name, precision, cap, steps, warmup, e2e_steps, local, ws,
+               peak, peak_source, barrier):
+    """One batched-solve workload: device-timed steps (inputs in HBM, L2
+    flushed between steps), the end-to-end steps with host buffers, the pass
+    timings and the convergence reached.  Returns the pieces of a line."""
+    probs, cfg = workload(name, cap)
+    L = probs[0].L
+    nb = len(probs)
+    masks_dev = [B.epfft_mask(P.L, P.f, P.seed, device=local) for P in probs]
+    masks_host = []
+    for m in masks_dev:
+        h = torch.empty((L, L), dtype=torch.uint8, pin_memory=True)
+        h.copy_(m.cpu())
+        masks_host.append(h.numpy())
+    paths = [P.path for P in probs]
+
+    def problems(host):
+        return [B.Problem(L=L, precision=precision, mask=(masks_host[i] if host else masks_dev[i]), tol_eq=1e-8,
+                          tol_macro=1e-8, max_iter=cap) for i in range(nb)]
+
+    # the autotuner picks the tiling of this lattice size (outside the timed region)
+    tiling, tiling_ms = B.epfft_autotune(ctx, L, precision, n_batch=nb)
+    cfg["tiling"] = {"chosen": tiling, "ms_per_iteration": tiling_ms}
+    pd = problems(False)
+    for _ in range(warmup):
+        B.epfft_solve_batch(ctx, pd, paths)
+    barrier()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        dev_s, pix_its, launches, recs = timed_solves(B, ctx, stream, flush, pd, paths, steps, torch)
+        barrier()
+        wall = time.perf_counter() - t0
+    clocks = clk.summary()
+
+    # end to end through the C ABI with host buffers (pinned masks in; records,
+    # final strain, plastic flags and cluster labels out into pinned buffers
+    # the caller allocates once and reuses)
+    ph = problems(True)
+    outs = [B.pinned_fields(P, len(path)) for P, path in zip(ph, paths)]
+    B.epfft_solve_batch(ctx, ph, paths, fields=True, out=outs)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_its = 0
+    for _ in range(e2e_steps):
+        rc, rr, ff = B.epfft_solve_batch(ctx, ph, paths, fields=True, out=outs)
+        e2e_its += sum(p.L * p.L * int(r["iterations"].sum()) for p, r in zip(ph, rr))
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    rs = 8 if precision == "fp64" else 4
+    h2d = sum(L * L + 4 * 8 * P.n_inc for P in probs)
+    d2h = sum(P.n_inc * 104 + L * L * 4 * rs + P.n_inc * L * L * 5 for P in probs)
+
+    # pass timing (CUDA events on the context stream) for the roofline
+    E_mid = probs[0].path[probs[0].n_inc // 2]
+    n_pass = 20 if L * L * nb >= (1 << 24) else 50
+    col_ms, row_ms = B.epfft_time_passes(ctx, pd[0], E_mid, n_pass, n_batch=nb)
+
+    t_step = dev_s / steps
+    t_step, dev_s, e2e_s = max_over_ranks([t_step, dev_s, e2e_s], device=torch.device(f"cuda:{local}"))
+    conv = convergence(recs)
+    sps = job_value(ws, steps * nb, dev_s)
+    cfg.update(l2="inputs larger than L2 at this size; L2 also flushed between steps (512 MiB write, outside "
+                  "the step events)" if L * L * nb >= (1 << 22) else
+               "flushed between steps (512 MiB write, outside the step events)",
+               parallelism="replicas" if ws > 1 else "single GPU", precision=precision,
+               solves_per_s=sps, solves_per_s_at_tol=sps if conv["converged"] == conv["increments"] else None)
+    return {
+        "value": job_value(ws, pix_its, dev_s), "ms_per_step": 1e3 * t_step, "config": cfg,
+        "convergence": conv,
+        "roofline": roofline(precision, L, nb, col_ms, row_ms, peak, peak_source),
+        "e2e": {"value": job_value(ws, e2e_its, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "gpu_launches": launches, "clocks": clocks, "wall_s": wall, "recs": recs, "probs": probs,
+        "masks_dev": masks_dev,
+    }
+
+
+def serving(B, ctx, local, ws, rank, precision="fp32", cap=20, n_requests=150):
+    """C5: Poisson request stream through the serving engine; latency =
+    completion - arrival on the host clock."""
     from paper_0802_2488_gb300 import inputs
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    build.build()
-    ctx = B.Context(local)
 
     def prob(r):
         P = r.problem
-        return B.Problem(L=P.L, precision=args.precision, void_fraction=P.f, seed=P.seed, tol_eq=1e-8,
-                         tol_macro=1e-8, max_iter=args.cap)
+        return B.Problem(L=P.L, precision=precision, void_fraction=P.f, seed=P.seed, tol_eq=1e-8,
+                         tol_macro=1e-8, max_iter=cap)
 
     # tilings of the served sizes: single solves (the solo probe) and the
     # 16-slot serving classes
     for L in (128, 256, 512, 1024):
-        B.epfft_autotune(ctx, L, args.precision, n_batch=1)
-        B.epfft_autotune(ctx, L, args.precision, n_batch=16)
+        B.epfft_autotune(ctx, L, precision, n_batch=1)
+        B.epfft_autotune(ctx, L, precision, n_batch=16)
     # solo capacity: a few requests run back to back, one at a time
     probe = inputs.serving_stream(12, 1.0, seed=1000 + rank)
     for r in probe[:2]:
@@ -356,11 +493,12 @@ def run_serving(args):
         B.epfft_solve(ctx, prob(r), r.problem.path)
     solo = (len(probe) - 2) / (time.perf_counter() - t0)
     rate = 0.7 * solo
-    reqs = inputs.serving_stream(args.requests, rate, seed=rank)
+    reqs = inputs.serving_stream(n_requests, rate, seed=rank)
     budget = 16 << 30
     B.epfft_serve_open(ctx, budget, 16, 32)
     lat, pix = [], 0
     launches = 0
+    recs = []
     h2d = d2h = 0  # strain paths submitted, records read back (masks are generated on the device)
     tickets = {}
     nxt = 0
@@ -384,41 +522,82 @@ def run_serving(args):
                 if res is not None:
                     lat.append(done_t - r.arrival_s)
                     pix += r.problem.L ** 2 * int(res[1]["iterations"].sum())
+                    recs.append(res[1])
                     d2h += res[1].nbytes
                     del tickets[i]
         total = time.perf_counter() - t0
     B.epfft_serve_close(ctx)
     clocks = clk.summary()
     lat = np.array(lat)
-    out = {
-        "metric": METRIC, "value": ws * pix / total, "unit": UNIT, "n_gpus": ws, "steps": 1, "warmup": 0,
-        "ms_per_step": 1e3 * total, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": f"Poisson stream of {len(reqs)} requests at {rate:.2f}/s (70% of the measured "
-                               f"solo capacity {solo:.2f}/s): L uniform in {{128,256,512,1024}}, f uniform in "
-                               f"[0.05,0.35], equibiaxial or shear, 10-50 increments, seed = request id; at most "
-                               f"{args.cap} iterations per increment; HBM budget 16 GiB, 16 slots per size",
-                   "rate_per_s": rate, "solo_capacity_per_s": solo,
-                   "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
-                   "solves_per_s": len(lat) / total, "precision": args.precision, "parallelism": "single GPU",
-                   "l2": "inputs of the running set exceed L2 at the larger sizes; not flushed"},
-        # the stream is timed on the host clock from the first arrival to the
-        # last result, through submit / serve_step / poll: value and e2e are
-        # the same end-to-end measurement
+    conv = convergence(recs)
+    return {
+        "value": ws * pix / total, "unit": UNIT, "ms_per_step": 1e3 * total,
+        "workload": f"Poisson stream of {len(reqs)} requests at {rate:.2f}/s (70% of the measured solo capacity "
+                    f"{solo:.2f}/s): L uniform in {{128,256,512,1024}}, f uniform in [0.05,0.35], equibiaxial or "
+                    f"shear, 10-50 increments, seed = request id; FP32 fields, FP64 reductions; at most {cap} "
+                    f"iterations per increment; HBM budget 16 GiB, 16 slots per size",
+        "rate_per_s": rate, "solo_capacity_per_s": solo,
+        "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+        "solves_per_s": len(lat) / total,
+        "solves_per_s_at_tol": len(lat) / total if conv["converged"] == conv["increments"] else None,
+        "convergence": conv,
+        # timed on the host clock from the first arrival to the last result,
+        # through submit / serve_step / poll: value and e2e are the same
+        # end-to-end measurement
         "e2e": {"value": ws * pix / total, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches, "clocks": clocks,
     }
-    if rank == 0:
-        print(json.dumps(out), flush=True)
-    ctx.close()
+
+
+def fp32_vs_fp64(B, ctx, stream, flush, torch, steps, warmup, local, barrier, peak64, src64):
+    """C2 (L = 256, shear): plain FP64 solve, its FP32 form at the same
+    iteration cap with the errors of the final strain field, the plastic
+    flags and the macroscopic curve against FP64, and plain FP64 against the
+    mixed-precision solve at a tolerance both reach."""
+    out = {}
+    line64 = solve_line(B, ctx, stream, flush, torch, "c2", "fp64", CAPS["c2"], steps, warmup, 1, local, 1,
+                        peak64, src64, barrier)
+    hbm, hsrc = peaks(B, ctx, "fp32")
+    line32 = solve_line(B, ctx, stream, flush, torch, "c2", "fp32", CAPS["c2"], steps, warmup, 1, local, 1,
+                        hbm, hsrc, barrier)
+    for key, ln in (("fp64", line64), ("fp32", line32)):
+        out[key] = {k: ln[k] for k in ("value", "ms_per_step", "convergence", "roofline", "e2e", "clocks")}
+        out[key]["solves_per_s"] = ln["config"]["solves_per_s"]
+        out[key]["solves_per_s_at_tol"] = ln["config"]["solves_per_s_at_tol"]
+        out[key]["tiling"] = ln["config"]["tiling"]
+    out["workload"] = line64["config"]["workload"]
+    # final fields of both precisions at the same cap (one untimed solve each)
+    P = line64["probs"][0]
+    mask = line64["masks_dev"][0]
+    f = {}
+    for prec in ("fp64", "fp32"):
+        pr = B.Problem(L=P.L, precision=prec, mask=mask, tol_eq=1e-8, tol_macro=1e-8, max_iter=CAPS["c2"])
+        rc, rec, fl = B.epfft_solve(ctx, pr, P.path, fields=True)
+        f[prec] = (rec, fl)
+    (r64, f64), (r32, f32) = f["fp64"], f["fp32"]
+    e64, e32 = f64.eps.astype(np.float64), f32.eps.astype(np.float64)
+    s64, s32 = r64["sig_mean"], r32["sig_mean"]
+    out["fp32_errors_vs_fp64"] = {
+        "same_iterations": bool(np.array_equal(r64["iterations"], r32["iterations"])),
+        "final_strain_rel_l2": float(np.linalg.norm(e32 - e64) / np.linalg.norm(e64)),
+        "macro_stress_curve_max_rel_err": float(np.max(np.linalg.norm(s32 - s64, axis=1) /
+                                                       np.linalg.norm(s64, axis=1))),
+        "macro_strain_curve_max_rel_err": float(np.max(np.linalg.norm(r32["eps_mean"] - r64["eps_mean"], axis=1) /
+                                                       np.linalg.norm(r64["eps_mean"], axis=1))),
+        "plastic_flag_disagreements_per_increment_max": int(np.max(np.sum(f32.plastic != f64.plastic,
+                                                                          axis=(1, 2)))),
+        "eta1_fp32_last_increment": float(r32["eta1"][-1]), "eta1_fp64_last_increment": float(r64["eta1"][-1]),
+        "note": "both solves stop at the same iteration cap per increment (neither converges to 1e-8 on most "
+                "increments), so this is the FP32 rounding effect on the same iterates",
+    }
+    out["refined"] = refined_vs_plain(B, ctx, stream, flush, mask, P.L, P.path[:2], torch)
+    return out
 
 
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "c5":
-        return run_serving(args)
     import torch
     ws, rank, local = dist_env()
     if ws > 1:
@@ -428,23 +607,8 @@ def main():
     from paper_0802_2488_gb300 import binding as B
     from paper_0802_2488_gb300 import build
     build.build()
-    probs, cfg = workload(args.workload, args.cap)
-    L = probs[0].L
     stream = torch.cuda.Stream(device=local)
     ctx = B.Context(local, stream=stream.cuda_stream)
-    masks_dev = [B.epfft_mask(P.L, P.f, P.seed, device=local) for P in probs]
-    masks_host = []
-    for m in masks_dev:
-        h = torch.empty((L, L), dtype=torch.uint8, pin_memory=True)
-        h.copy_(m.cpu())
-        masks_host.append(h.numpy())
-    paths = [P.path for P in probs]
-
-    def problems(prec, host):
-        return [B.Problem(L=L, precision=prec, mask=(masks_host[i] if host else masks_dev[i]), tol_eq=1e-8,
-                          tol_macro=1e-8, max_iter=args.cap) for i in range(len(probs))]
-
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=local)
 
     def barrier():
         if ws > 1:
@@ -452,117 +616,55 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(local)
 
-    # the autotuner picks the tiling of this lattice size (outside the timed region)
-    tiling, tiling_ms = B.epfft_autotune(ctx, L, args.precision, n_batch=len(probs))
-    cfg["tiling"] = {"chosen": tiling, "ms_per_iteration": tiling_ms}
-    pd = problems(args.precision, False)
-    for _ in range(args.warmup):
-        B.epfft_solve_batch(ctx, pd, paths)
-    barrier()
-    with ClockSampler(local) as clk:
-        t0 = time.perf_counter()
-        dev_s, pix_its, launches, recs = timed_solves(B, ctx, stream, flush, pd, paths, args.steps, torch)
-        barrier()
-        wall = time.perf_counter() - t0
-    clocks = clk.summary()
+    if args.workload == "c5":
+        r = serving(B, ctx, local, ws, rank, args.precision, args.cap, args.requests)
+        if rank == 0:
+            out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": 1, "warmup": 0,
+                   "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                   "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+                   "config": {"workload": r["workload"], "precision": args.precision, "parallelism": "single GPU",
+                              "rate_per_s": r["rate_per_s"], "latency_p50_s": r["latency_p50_s"],
+                              "latency_p99_s": r["latency_p99_s"], "solves_per_s": r["solves_per_s"],
+                              "solves_per_s_at_tol": r["solves_per_s_at_tol"],
+                              "l2": "inputs of the running set exceed L2 at the larger sizes; not flushed"},
+                   "convergence": r["convergence"], "e2e": r["e2e"], "gpu_launches": r["gpu_launches"],
+                   "clocks": r["clocks"]}
+            print(json.dumps(out), flush=True)
+        ctx.close()
+        return
 
-    # end to end through the C ABI with host buffers (pinned masks in; records,
-    # final strain, plastic flags and cluster labels out into pinned buffers
-    # the caller allocates once and reuses)
-    ph = problems(args.precision, True)
-    outs = [B.pinned_fields(P, len(path)) for P, path in zip(ph, paths)]
-    B.epfft_solve_batch(ctx, ph, paths, fields=True, out=outs)
-    barrier()
-    t0 = time.perf_counter()
-    e2e_its = 0
-    for _ in range(args.steps):
-        rc, rr, ff = B.epfft_solve_batch(ctx, ph, paths, fields=True, out=outs)
-        e2e_its += sum(p.L * p.L * int(r["iterations"].sum()) for p, r in zip(ph, rr))
-    barrier()
-    e2e_s = time.perf_counter() - t0
-    rs = 8 if args.precision == "fp64" else 4
-    h2d = sum(L * L + 4 * 8 * P.n_inc for P in probs)
-    d2h = sum(P.n_inc * 104 + L * L * 4 * rs + P.n_inc * L * L * 5 for P in probs)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=local)
+    peak, peak_src = peaks(B, ctx, args.precision)
+    line = solve_line(B, ctx, stream, flush, torch, args.workload, args.precision, args.cap, args.steps,
+                      args.warmup, min(args.steps, 5), local, ws, peak, peak_src, barrier)
+    extras = {}
+    default_run = args.workload == "c3" and args.precision == "fp32" and args.cap == CAPS["c3"]
+    if default_run and ws == 1 and not args.no_extras:
+        # the other configurations, measured in the same process (shorter
+        # step counts: each is a sub-object, not the headline)
+        c4 = solve_line(B, ctx, stream, flush, torch, "c4", "fp32", CAPS["c4"], 2, 1, 1, local, ws, peak,
+                        peak_src, barrier)
+        extras["c4"] = {k: c4[k] for k in ("value", "ms_per_step", "convergence", "roofline", "e2e", "clocks",
+                                           "gpu_launches")}
+        extras["c4"]["config"] = {k: v for k, v in c4["config"].items()}
+        extras["c4"]["steps"], extras["c4"]["warmup"] = 2, 1
+        extras["c5"] = serving(B, ctx, local, ws, rank, "fp32", CAPS["c5"], args.requests)
+        p64, s64 = peaks(B, ctx, "fp64")
+        extras["c2"] = fp32_vs_fp64(B, ctx, stream, flush, torch, min(args.steps, 3), 1, local, barrier, p64, s64)
+        extras["c2"]["steps"], extras["c2"]["warmup"] = min(args.steps, 3), 1
 
-    # pass timing (CUDA events on the context stream) for the roofline
-    E_mid = probs[0].path[probs[0].n_inc // 2]
-    col_ms, row_ms = B.epfft_time_passes(ctx, pd[0], E_mid, 50, n_batch=len(probs))
-
-    companion = None
-    if args.workload == "c2" and args.precision == "fp64" and not args.no_fp32 and ws == 1:
-        B.epfft_autotune(ctx, L, "fp32")
-        pf = problems("fp32", False)
-        for _ in range(args.warmup):
-            B.epfft_solve_batch(ctx, pf, paths)
-        f_s, f_its, _, frecs = timed_solves(B, ctx, stream, flush, pf, paths, args.steps, torch)
-        fcol, frow = B.epfft_time_passes(ctx, pf[0], E_mid, 50)
-        s64, s32 = recs[0]["sig_mean"], frecs[0]["sig_mean"]
-        curve_err = float(np.max(np.linalg.norm(s32 - s64, axis=1) / np.linalg.norm(s64, axis=1)))
-        companion = {"value": f_its / f_s, "unit": UNIT, "ms_per_step": 1e3 * f_s / args.steps,
-                     "solves_per_s": args.steps / f_s, "col_pass_ms": fcol, "row_pass_ms": frow,
-                     "macro_curve_max_rel_err_vs_fp64": curve_err,
-                     "eta1_last_increment": float(frecs[0]["eta1"][-1]),
-                     "dtype": "f32 fields and FFTs, f64 reductions"}
-
-    refined = None
-    if args.workload == "c2" and args.precision == "fp64" and not args.no_fp32 and ws == 1:
-        refined = refined_vs_plain(B, ctx, stream, flush, masks_dev[0], L, paths[0][:2], torch)
-
-    t_step = dev_s / args.steps
-    t_step, dev_s, e2e_s = max_over_ranks([t_step, dev_s, e2e_s], device=torch.device(f"cuda:{local}"))
-    value = job_value(ws, pix_its, dev_s)
     if rank == 0:
-        lg = int(np.log2(L))
-        nb = len(probs)
-        if args.precision == "fp64":
-            # FP64 arithmetic bound: row pass 15 log2 L + 60 flops per pixel
-            # (row transforms, local step); column pass 15 log2 L + 25 (column
-            # transforms, Green operator)
-            row_w, col_w = (15 * lg + 60) * L * L * nb, (15 * lg + 25) * L * L * nb
-            dom_ms, dom_w, dom = (row_ms, row_w, "row") if row_ms >= col_ms else (col_ms, col_w, "col")
-            sm = clocks.get("sm_max_mhz") or 2070.0
-            peak = 152 * 2 * 2 * sm * 1e6 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 flop
-            achieved = dom_w / (dom_ms * 1e-3) / 1e12
-            roof = {"bound": "alu", "kernel": f"{dom}_pass<double,{L}>", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock"}
-        else:
-            mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
-            hbm = json.load(open(mp))["hbm_gbs"] if os.path.exists(mp) else 6800.0
-            # row pass: spectrum read + write 24 B, sigma read 16 B, eps and
-            # sigma written 32 B, mask 1 B; column pass: spectrum r + w 24 B
-            row_b, col_b = 73 * L * L * nb, 24 * L * L * nb
-            dom_ms, dom_b, dom = (row_ms, row_b, "row") if row_ms >= col_ms else (col_ms, col_b, "col")
-            achieved = dom_b / (dom_ms * 1e-3) / 1e9
-            roof = {"bound": "hbm", "kernel": f"{dom}_pass<float,{L}>", "achieved": achieved, "peak": hbm,
-                    "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if os.path.exists(mp)
-                    else "fallback 6800 GB/s (of fallback)"}
-        roof.update({"col_pass_ms": col_ms, "row_pass_ms": row_ms})
-        roof["traffic"] = TRAFFIC.get((roof["kernel"], tiling, nb))
-        if roof["traffic"] is not None:
-            roof["traffic_source"] = "profiles/passes_dram_traffic.md (ncu dram__bytes_read.sum + write.sum per launch)"
         out = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True,
+            "metric": METRIC, "value": line["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": line["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
-            "data": "synthetic",
-            "config": dict(cfg, l2="flushed between steps (512 MiB write, outside the step events)",
-                           parallelism="replicas" if ws > 1 else "single GPU",
-                           solves_per_s=job_value(ws, args.steps * len(probs), dev_s), precision=args.precision),
-            "roofline": roof,
-            "e2e": {"value": job_value(ws, e2e_its, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches,
-            "clocks": clocks,
-            "wall_s": wall,
+            "data": "synthetic", "config": line["config"], "convergence": line["convergence"],
+            "roofline": line["roofline"], "e2e": line["e2e"], "gpu_launches": line["gpu_launches"],
+            "clocks": line["clocks"], "wall_s": line["wall_s"],
         }
-        if companion:
-            out["fp32"] = companion
-        if refined:
-            out["refined"] = refined
+        out.update(extras)
         if ws == 1 and not args.no_baseline:
-            out["cpu_baseline"] = cpu_baseline(probs)
+            out["cpu_baseline"] = cpu_baseline(line["probs"])
         print(json.dumps(out), flush=True)
     ctx.close()
     if ws > 1:

@@ -414,18 +414,28 @@ int epfft_project(epfft_ctx *ctx, int32_t L, int32_t precision, double lambda0, 
  * an allocation that could synchronise the device).  The paper has no
  * counterpart; this is a convenience of the library.
  *
- * All working memory is one static device array of the library (1.59 MB,
- * held on every GPU that loads the library until the process exits), so
- * lattice sides above 256 are rejected with EPFFT_ERR_SCRATCH_LIMIT.  The
- * call allocates nothing: no cudaMalloc, cudaFree or allocating library
- * routine.  p_dev / e_dev and the layout are those of epfft_project; the
- * work is queued on `stream` (cudaStream_t of the current device, NULL for
- * the legacy default stream) and the call returns without waiting.
- * The first call on a device looks up the array's device address (once per
- * device, for the current device); make that first call before any stream
- * capture.  Every call uses the same array and leaves the last call's data
- * in it; calls whose work overlaps on the GPU (other streams, other host
- * threads) race on it and must be serialised by the caller. */
+ * All working memory is one static device array of the library (1.62 MB:
+ * the spectrum, the tables of every side up to 256 in both precisions and a
+ * solve record), so lattice sides above 256 are rejected with
+ * EPFFT_ERR_SCRATCH_LIMIT.  p_dev / e_dev and the layout are those of
+ * epfft_project; the work is queued on `stream` (cudaStream_t of the current
+ * device, NULL for the legacy default stream).
+ *
+ * Set-up: the first call on a device (made with that device current) loads
+ * the library's device code onto it, which is when the driver places the
+ * array there (it then stays until the process exits); it looks up the
+ * array's device address, uploads the tables with a blocking copy and
+ * raises the kernels' shared-memory limits.  Make that first call outside
+ * any stream capture and outside any region where a driver allocation or a
+ * synchronisation is not allowed.  Every later call allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library routine), copies nothing from
+ * the host and returns without waiting: it only launches kernels on
+ * `stream`, the first of which writes the mean strain and the solve record
+ * from the call's arguments.
+ *
+ * Every call on a device uses the same array and leaves the last call's
+ * data in it; calls whose work overlaps on the GPU (other streams, other
+ * host threads) race on it and must be serialised by the caller. */
 int epfft_project_static(int32_t L, int32_t precision, double lambda0, double mu0, const double E[4],
                          const void *p_dev, void *e_dev, void *stream);
 
@@ -446,6 +456,15 @@ int epfft_label(epfft_ctx *ctx, int32_t L, int32_t n_img, const uint8_t *flags_d
  * Blocking. */
 int epfft_time_passes(epfft_ctx *ctx, const epfft_problem *problem, int32_t n_batch, const double E[4],
                       int32_t n_iter, float *col_ms, float *row_ms);
+
+/* FP64 arithmetic peak of the context's device, measured: eight 256-thread
+ * CTAs per SM, each thread running 8 independent chains of 4096 dependent
+ * FP64 FMAs, timed with CUDA events on the context stream (best of five
+ * launches after a warm-up).  *tflops = 2 x FMAs / time; *n_sm (optional)
+ * the device's SM count; *ms (optional) the best launch time.  The clocks
+ * are left as they are.  A measurement aid, with no counterpart in the
+ * paper: the denominator of the FP64 passes' roofline.  Blocking. */
+int epfft_fp64_peak(epfft_ctx *ctx, double *tflops, int32_t *n_sm, float *ms);
 
 /* ---------------------------------------------------------------------- */
 /* Tiling (FFT tile shapes and CTA sizes per lattice side)                 */

@@ -49,7 +49,8 @@ SYMBOLS = ["epfft_create", "epfft_destroy", "epfft_last_stats", "epfft_strerror"
            "epfft_submit", "epfft_serve_step", "epfft_poll", "epfft_autotune", "epfft_set_tiling",
            "epfft_solve_dg2", "epfft_average5", "epfft_void_plastic", "epfft_indicators",
            "epfft_effective_moduli", "epfft_empirical_curve", "epfft_eps_eq", "epfft_displacement",
-           "epfft_ticket_fields", "epfft_release", "epfft_solve_refined", "epfft_solve_refined_batch"]
+           "epfft_ticket_fields", "epfft_release", "epfft_solve_refined", "epfft_solve_refined_batch",
+           "epfft_fp64_peak"]
 
 
 class EpfftError(RuntimeError):
@@ -146,6 +147,7 @@ def lib():
         L.epfft_project_static.argtypes = [i32, i32, dbl, dbl, C.POINTER(dbl), vp, vp, vp]
         L.epfft_time_passes.argtypes = [vp, C.POINTER(_Problem), i32, C.POINTER(dbl), i32, C.POINTER(C.c_float),
                                         C.POINTER(C.c_float)]
+        L.epfft_fp64_peak.argtypes = [vp, C.POINTER(dbl), C.POINTER(i32), C.POINTER(C.c_float)]
         for s in SYMBOLS:
             if s not in ("epfft_destroy", "epfft_strerror"):
                 getattr(L, s).restype = C.c_int
@@ -566,21 +568,32 @@ def epfft_time_passes(ctx: Context, problem: Problem, E, n_iter: int, n_batch: i
     return a.value, b.value
 
 
-def epfft_project_static(L: int, precision: str, lambda0: float, mu0: float, E, p, stream=None):
+def epfft_fp64_peak(ctx: Context) -> dict:
+    """Measured FP64 FMA throughput of the context's device (TFLOP/s), its SM
+    count and the best launch time (ms)."""
+    t, n, ms = C.c_double(), C.c_int32(), C.c_float()
+    _check(lib().epfft_fp64_peak(ctx.handle, C.byref(t), C.byref(n), C.byref(ms)), "epfft_fp64_peak")
+    return {"tflops": t.value, "n_sm": n.value, "ms": ms.value}
+
+
+def epfft_project_static(L: int, precision: str, lambda0: float, mu0: float, E, p, stream=None, out=None,
+                         wait: bool = True):
     """epfft_project without any device allocation by the library: its working
     memory is a static device array (lattice sides up to 256).  The output
-    tensor is allocated here by torch, before the call; the library queues its
-    work on `stream` (default: torch's current stream) and this wrapper waits
-    for it."""
+    tensor is `out` if given, else allocated here by torch before the call;
+    the library queues its work on `stream` (default: torch's current stream)
+    and this wrapper waits for it unless wait=False."""
     import torch
     assert p.is_cuda and p.is_contiguous() and tuple(p.shape) == (3, L, L)
-    e = torch.empty_like(p)
+    e = torch.empty_like(p) if out is None else out
+    assert e.is_cuda and e.is_contiguous() and e.shape == p.shape and e.dtype == p.dtype
     Ea = (C.c_double * 4)(*[float(x) for x in E])
     s = torch.cuda.current_stream(p.device) if stream is None else stream
     _check(lib().epfft_project_static(L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision], float(lambda0),
                                       float(mu0), Ea, p.data_ptr(), e.data_ptr(), s.cuda_stream),
            "epfft_project_static")
-    s.synchronize()
+    if wait:
+        s.synchronize()
     return e
 
 

@@ -137,4 +137,27 @@ cudaError_t launch_label(const uint8_t* flags, int32_t* lab, int64_t n_img, int 
   return cudaGetLastError();
 }
 
+// --- FP64 FMA throughput ---------------------------------------------------
+// Every thread advances FMA_CHAINS independent chains x <- x a + b for n
+// steps (a slightly below 1, so the values stay bounded); the sum is stored
+// only if it equals an impossible value, so the chains cannot be removed.
+__global__ void __launch_bounds__(FMA_THREADS) fp64_fma_kernel(int n, double a, double b, double* sink) {
+  double x[FMA_CHAINS];
+#pragma unroll
+  for (int i = 0; i < FMA_CHAINS; i++) x[i] = 1e-3 * threadIdx.x + i;
+#pragma unroll 4
+  for (int k = 0; k < n; k++)
+#pragma unroll
+    for (int i = 0; i < FMA_CHAINS; i++) x[i] = fma(x[i], a, b);
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < FMA_CHAINS; i++) s += x[i];
+  if (s == -1234.5) *sink = s;
+}
+
+cudaError_t launch_fp64_fma(int blocks, int n, double* sink, cudaStream_t s) {
+  fp64_fma_kernel<<<blocks, FMA_THREADS, 0, s>>>(n, 0.999999, 1e-6, sink);
+  return cudaGetLastError();
+}
+
 }  // namespace epfft

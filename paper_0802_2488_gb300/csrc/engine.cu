@@ -34,9 +34,14 @@ struct epfft_ctx {
   epfft_alloc_fn alloc = nullptr;
   epfft_free_fn freef = nullptr;
   void* user = nullptr;
-  // (L, precision) -> device table (layout of tables.cuh) and the offset of
-  // k(m) in it (complex units)
-  std::map<std::pair<int, int>, std::pair<void*, int>> tables;
+  // (L, precision) -> device table (layout of tables.cuh), its size in bytes
+  // and the offset of k(m) in it (complex units)
+  struct Table {
+    void* dev;
+    size_t bytes;
+    int koff;
+  };
+  std::map<std::pair<int, int>, Table> tables;
   std::map<std::tuple<int, int, int>, bool> prepared;  // (L, precision, tiling variant)
   // tuned tiling per (L, precision, batch class): class 1 when a launch
   // covers at least 2^21 pixels (enough CTAs to fill the GPU), else 0
@@ -108,7 +113,9 @@ size_t real_size(int prec) { return prec == EPFFT_FP32 ? 4 : 8; }
 // Device tables of (L, precision) (layout of tables.cuh: twist octant,
 // stage twiddles of both tilings' plans, Fourier symbols of Eq. 2
 // k(m) = 2 sin(q/2) exp(i q/2)), built once per context in long double and
-// rounded once to the working precision.
+// rounded once to the working precision.  The device block comes from the
+// context's allocator on its stream; the upload is ordered on that stream
+// and waited for before the host copy goes away.
 int get_tables(epfft_ctx* c, int L, int prec, void** tw, void** ktab) {
   auto key = std::make_pair(L, prec);
   auto it = c->tables.find(key);
@@ -118,17 +125,19 @@ int get_tables(epfft_ctx* c, int L, int prec, void** tw, void** ktab) {
     const int koff = prec == EPFFT_FP32 ? host_tables<float>(L, hf) : host_tables<double>(L, hd);
     if (koff < 0) return EPFFT_ERR_ARG;
     const size_t bytes = prec == EPFFT_FP32 ? hf.size() * sizeof(float) : hd.size() * sizeof(double);
-    void* d = nullptr;
-    if (cudaMalloc(&d, bytes) != cudaSuccess) {
+    void* d = dev_alloc(c, bytes);
+    if (!d) return EPFFT_ERR_OOM;
+    const void* src = prec == EPFFT_FP32 ? (const void*)hf.data() : (const void*)hd.data();
+    if (cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
       cudaGetLastError();
-      return EPFFT_ERR_OOM;
+      dev_free(c, d, bytes);
+      return EPFFT_ERR_CUDA;
     }
-    if (prec == EPFFT_FP32) CK(cudaMemcpy(d, hf.data(), bytes, cudaMemcpyHostToDevice));
-    else CK(cudaMemcpy(d, hd.data(), bytes, cudaMemcpyHostToDevice));
-    it = c->tables.emplace(key, std::make_pair(d, koff)).first;
+    it = c->tables.emplace(key, epfft_ctx::Table{d, bytes, koff}).first;
   }
-  *tw = it->second.first;
-  *ktab = (char*)it->second.first + (size_t)2 * it->second.second * real_size(prec);
+  *tw = it->second.dev;
+  *ktab = (char*)it->second.dev + (size_t)2 * it->second.koff * real_size(prec);
   return EPFFT_OK;
 }
 
@@ -415,6 +424,27 @@ int run_graph(epfft_ctx* c, Batch& B) {
   return rc;
 }
 
+// The same loop for a known number of steps, launched from the host with no
+// graph and no synchronisation: steps beyond a solve's DONE phase are
+// no-ops (the passes skip DONE solves), so `steps` only has to cover the
+// longest solve.  Used where the step count is fixed in advance (a fixed
+// number of iterations), so the passes are ordinary stream launches.
+int run_host_loop(epfft_ctx* c, Batch& B, int64_t steps) {
+  for (int64_t k = 0; k < steps; k++) {
+    cudaError_t e = cudaSuccess;
+    if (B.prec == EPFFT_FP32) {
+      e = launch_col<float>(B.L, B.var, B.nb, c->stream, B.d_solves, B.tw, B.ktab, 0, 0, B.general);
+      if (e == cudaSuccess) e = launch_row<float>(B.L, B.var, B.nb, c->stream, B.d_solves, B.d_ctl, B.tw, 0, 0);
+    } else {
+      e = launch_col<double>(B.L, B.var, B.nb, c->stream, B.d_solves, B.tw, B.ktab, 0, 0, B.general);
+      if (e == cudaSuccess) e = launch_row<double>(B.L, B.var, B.nb, c->stream, B.d_solves, B.d_ctl, B.tw, 0, 0);
+    }
+    if (e != cudaSuccess) return EPFFT_ERR_CUDA;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return EPFFT_OK;
+}
+
 // Diagnostic loop (EPFFT_SYNC_CHECK=1 in the environment): the same passes
 // launched from the host one by one, each followed by a synchronisation
 // and an error check that names the pass, phase and step that failed.
@@ -510,7 +540,7 @@ int copy_out(epfft_ctx* c, Batch& B, Solve& S, int i, const epfft_fields* f) {
 
 int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_path* paths,
                epfft_record* const* records, const epfft_fields* fields, const void* const* eps0,
-               void* const* eps_out, epfft_record* iter_rec) {
+               void* const* eps_out, epfft_record* iter_rec, int64_t host_steps = 0) {
   if (!c || n < 1 || !probs || !paths) return EPFFT_ERR_ARG;
   for (int i = 0; i < n; i++) {
     int rc = check_problem(&probs[i]);
@@ -527,7 +557,9 @@ int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_
   int rc = setup_batch(c, A, B, n, probs, paths, eps0);
   if (rc) return rc;
   const char* chk = getenv("EPFFT_SYNC_CHECK");
-  rc = (chk && chk[0] == '1') ? run_checked(c, B) : run_graph(c, B);
+  if (chk && chk[0] == '1') rc = run_checked(c, B);
+  else if (host_steps > 0) rc = run_host_loop(c, B, host_steps);
+  else rc = run_graph(c, B);
   if (rc) return rc;
   // read back the solve states and records
   CK(cudaMemcpyAsync(B.h_solves.data(), B.d_solves, sizeof(Solve) * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
@@ -937,7 +969,8 @@ void epfft_destroy(epfft_ctx* c) {
   cudaSetDevice(c->device);
   if (c->server) epfft_serve_close(c);
   cudaStreamSynchronize(c->stream);
-  for (auto& t : c->tables) cudaFree(t.second.first);
+  for (auto& t : c->tables) dev_free(c, t.second.dev, t.second.bytes);
+  cudaStreamSynchronize(c->stream);
   cudaStreamDestroy(c->cap);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -1420,7 +1453,10 @@ int epfft_iterate(epfft_ctx* ctx, const epfft_problem* problem, const double E[4
   epfft_path path = {1, 0, E};
   const void* e0[1] = {eps_dev};
   void* e1[1] = {eps_dev};
-  int rc = solve_impl(ctx, 1, &p, &path, nullptr, nullptr, e0, e1, out);
+  // a fixed step count: warm start, n_iter + 1 iterates (the last one
+  // finalizes iterate n_iter), the final flags; the passes are launched from
+  // the host rather than from a graph loop
+  int rc = solve_impl(ctx, 1, &p, &path, nullptr, nullptr, e0, e1, out, (int64_t)n_iter + 3);
   return rc == EPFFT_NOT_CONVERGED ? EPFFT_OK : rc;
 }
 
@@ -1695,6 +1731,39 @@ int epfft_time_passes(epfft_ctx* ctx, const epfft_problem* problem, int32_t n_ba
   int rc = check_problem(problem);
   if (rc) return rc;
   return time_passes_impl(ctx, *problem, n_batch, E, n_iter, -1, col_ms, row_ms);
+}
+
+int epfft_fp64_peak(epfft_ctx* ctx, double* tflops, int32_t* n_sm, float* ms) {
+  if (!ctx || !tflops) return EPFFT_ERR_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return EPFFT_ERR_CUDA;
+  int nsm = 0;
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+  Arena A(ctx);
+  double* sink = (double*)A.get(sizeof(double));
+  if (!sink) return EPFFT_ERR_OOM;
+  // eight 256-thread CTAs per SM (64 warps): enough independent FMAs in
+  // flight to cover the FP64 pipe's latency
+  const int blocks = 8 * nsm, n = 4096;
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  float best = 0.f;
+  for (int rep = 0; rep < 6; rep++) {  // the first launch is a warm-up
+    CK(cudaEventRecord(a, ctx->stream));
+    CK(launch_fp64_fma(blocks, n, sink, ctx->stream));
+    CK(cudaEventRecord(b, ctx->stream));
+    CK(cudaEventSynchronize(b));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, a, b));
+    if (rep > 0 && (best == 0.f || t < best)) best = t;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  const double flops = 2.0 * FMA_CHAINS * (double)n * FMA_THREADS * blocks;
+  *tflops = flops / (best * 1e-3) / 1e12;
+  if (n_sm) *n_sm = nsm;
+  if (ms) *ms = best;
+  return EPFFT_OK;
 }
 
 int epfft_autotune(epfft_ctx* ctx, int32_t L, int32_t precision, int32_t n_batch, int32_t* chosen,

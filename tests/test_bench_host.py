@@ -62,3 +62,40 @@ def test_workload_configs():
         assert len(probs) == n and cfg["L"] == L and cfg["n_solves"] == n and cfg["n_inc"] == n_inc
         assert cfg["max_iter_per_increment"] == 77 and cfg["tol"] == 1e-8
         assert "at most 77 iterations" in cfg["workload"] and f"L={L}" in cfg["workload"]
+
+
+def test_convergence_summary_counts_what_increments_reached():
+    """The bench reports how many increments met the tolerances before the
+    cap and the indicators they stopped at; solves/s "at tol" needs all."""
+    import numpy as np
+    from paper_0802_2488_gb300 import binding as B
+    a = np.zeros(3, dtype=B.RECORD_DTYPE)
+    a["status"] = [0, 1, 1]
+    a["eta1"] = [5e-9, 2e-5, 1e-4]
+    a["eta2"] = [1e-9, 1e-9, 3e-9]
+    a["iterations"] = [40, 100, 100]
+    b = np.zeros(2, dtype=B.RECORD_DTYPE)
+    b["status"] = [0, 2]
+    b["eta1"] = [1e-9, 1e-9]
+    b["iterations"] = [10, 50]
+    c = bench.convergence([a, b])
+    assert c["increments"] == 5 and c["converged"] == 2 and c["capped"] == 2 and c["numeric_failures"] == 1
+    assert c["eta1_max"] == 1e-4 and c["eta1_median"] == 5e-9 and c["eta2_max"] == 3e-9
+    assert c["iterations_per_increment_mean"] == 60.0
+
+
+def test_roofline_uses_the_algorithmic_work_of_each_pass():
+    """FP32: 73 B per pixel in the row pass and 24 B in the column pass over
+    the mean launch time, against the HBM peak; FP64: 15 log2 L + 60 and
+    15 log2 L + 25 flops per pixel against the FP64 peak; the dominant pass
+    is the longer one."""
+    r = bench.roofline("fp32", 512, 64, 0.184, 0.337, 6770.0, "measured")
+    n = 512 * 512 * 64
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["kernel"] == "row_pass<float,512>"
+    assert abs(r["achieved"] - 73 * n / 0.337e-3 / 1e9) < 1e-6
+    assert abs(r["passes"]["col"]["achieved"] - 24 * n / 0.184e-3 / 1e9) < 1e-6
+    assert abs(r["frac"] - r["achieved"] / 6770.0) < 1e-12 and r["traffic"] is None
+    r = bench.roofline("fp64", 256, 1, 0.040, 0.030, 1.25, "measured")
+    assert r["bound"] == "alu" and r["kernel"] == "col_pass<double,256>"
+    assert abs(r["achieved"] - (15 * 8 + 25) * 65536 / 0.040e-3 / 1e12) < 1e-12
+    assert abs(r["passes"]["row"]["achieved"] - (15 * 8 + 60) * 65536 / 0.030e-3 / 1e12) < 1e-12

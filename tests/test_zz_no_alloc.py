@@ -5,7 +5,10 @@ inside another framework's memory budget or allocator, or that must not
 trigger an allocation which could synchronise the device.  For them the
 library offers the compatible-strain projection with all of its working
 memory in a static device array (lattice sides up to 256).  These tests call
-it through the C ABI and check it against the allocating entry point.
+it through the C ABI and check it against the allocating entry point, on two
+calls in a row, on torch's current stream and on a stream of its own, and
+check that calls after the first one (the per-device set-up) change neither
+the free device memory nor torch's allocated bytes.
 
 The file is named to be collected last, so a run that stops at the first
 failure has run every other test before it.
@@ -21,11 +24,14 @@ torch = pytest.importorskip("torch")
 
 TDT = {"fp64": torch.float64, "fp32": torch.float32}
 TOL = {"fp64": 1e-12, "fp32": 3e-6}  # the projection tolerances of the parity tests
+CASES = [(256, "fp64", np.array([0.3, -0.2, 0.0, 0.15])),
+         (64, "fp32", np.array([-0.1, 0.25, 0.0, 0.05]))]
 
 
 def rel(a, b):
-    a = a.double().cpu().numpy()
-    b = b.double().cpu().numpy()
+    # copied to the host first, so that the comparison allocates no device memory
+    a = a.cpu().double().numpy()
+    b = b.cpu().double().numpy()
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
@@ -38,20 +44,52 @@ def ctx():
     c.close()
 
 
-def test_two_static_calls_in_a_row_match_the_allocating_projection(ctx):
-    rng = np.random.default_rng(11)
-    cases = [(256, "fp64", np.array([0.3, -0.2, 0.0, 0.15])),
-             (64, "fp32", np.array([-0.1, 0.25, 0.0, 0.05]))]
-    inputs, refs = [], []
-    for L, prec, E in cases:
+def _inputs(ctx, seed):
+    rng = np.random.default_rng(seed)
+    ps, refs = [], []
+    for L, prec, E in CASES:
         p = torch.tensor(rng.standard_normal((3, L, L)), dtype=TDT[prec], device="cuda")
-        inputs.append(p)
+        ps.append(p)
         refs.append(B.epfft_project(ctx, L, prec, 1.5, 1.0, E, p))
+    return ps, refs
+
+
+def test_two_static_calls_in_a_row_match_the_allocating_projection(ctx):
+    ps, refs = _inputs(ctx, 11)
     # two consecutive calls of the static entry point (the second reuses the
     # array the first one left behind)
-    outs = [B.epfft_project_static(L, prec, 1.5, 1.0, E, p) for (L, prec, E), p in zip(cases, inputs)]
-    for (L, prec, E), got, ref in zip(cases, outs, refs):
+    outs = [B.epfft_project_static(L, prec, 1.5, 1.0, E, p) for (L, prec, E), p in zip(CASES, ps)]
+    for (L, prec, E), got, ref in zip(CASES, outs, refs):
         assert rel(got, ref) < TOL[prec], (L, prec, rel(got, ref))
+
+
+def test_static_calls_allocate_nothing_and_run_on_a_side_stream(ctx):
+    ps, refs = _inputs(ctx, 12)
+    outs = [torch.empty_like(p) for p in ps]
+    side = torch.cuda.Stream()
+
+    def run(stream):
+        for (L, prec, E), p, o in zip(CASES, ps, outs):
+            o.zero_()
+            torch.cuda.current_stream().synchronize()
+            B.epfft_project_static(L, prec, 1.5, 1.0, E, p, stream=stream, out=o)
+        torch.cuda.synchronize()
+        for (L, prec, E), got, ref in zip(CASES, outs, refs):
+            assert rel(got, ref) < TOL[prec], (L, prec, rel(got, ref))
+
+    # the first call on the device is its set-up (in this process it may
+    # have happened already); this round also makes the first launches of
+    # every kernel the measured rounds use, on both streams, so that the
+    # driver's one-time work (module loading, launch resources) is done
+    run(None)
+    run(side)
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    run(side)
+    run(side)
+    free1, _ = torch.cuda.mem_get_info()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert free1 == free0, (free0, free1)
 
 
 def test_lattices_beyond_the_static_scratch_are_rejected():
