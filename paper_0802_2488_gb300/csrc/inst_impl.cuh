@@ -1,6 +1,9 @@
 // Instantiation of the launch table for one real type EPFFT_REAL and one
 // tiling variant EPFFT_VAR over the supported lattice sides.
 #pragma once
+#include <type_traits>
+
+#include "colrs.cuh"
 #include "launch.cuh"
 #include "passes.cuh"
 
@@ -22,6 +25,11 @@ static bool shape_of(PassShape* o) {
   return true;
 }
 
+// The column pass of FP32 lattices of side >= 128 is the register-staged
+// kernel (colrs.cuh); FP64 and smaller sides use col_pass.
+template <typename T, int L>
+constexpr bool kRegisterStaged = std::is_same<T, float>::value && L >= 128;
+
 // Column-pass CTAs resident on the GPU at once, per lattice side (index
 // log2 L), measured at preparation: a CTA prefetches the slab of the CTA
 // that many places after it in launch order.
@@ -35,6 +43,11 @@ static cudaError_t prepare_L() {
   if ((e = cudaFuncSetAttribute(row_pass<T, L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::ROW_SMEM)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(col_pass<T, L, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::COL_SMEM)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(col_pass<T, L, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::COL_SMEM)) != cudaSuccess) return e;
+  if constexpr (kRegisterStaged<T, L>) {
+    using RC = RsCfg<L, C::W>;
+    if ((e = cudaFuncSetAttribute(col_pass_rs<L, C::W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::SMEM)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(col_pass_rs<L, C::W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::SMEM)) != cudaSuccess) return e;
+  }
   {
     int dev = 0, nsm = 0, occ = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -84,22 +97,35 @@ cudaError_t launch_row_v<EPFFT_REAL, EPFFT_VAR>(int L, int nb, cudaStream_t s, S
   }
 }
 
+template <typename T, int L>
+static cudaError_t launch_col_L(int nb, cudaStream_t s, Solve* solves, const void* tw, const void* ktab,
+                                cudaGraphConditionalHandle cond, int use_cond, int general) {
+  using C = Cfg<T, L, EPFFT_VAR>;
+  const C2<T>* tw_ = reinterpret_cast<const C2<T>*>(tw);
+  const C2<T>* k_ = reinterpret_cast<const C2<T>*>(ktab);
+  if constexpr (kRegisterStaged<T, L>) {
+    using RC = RsCfg<L, C::W>;
+    const dim3 grid((L / 2) / RC::CPC, nb);
+    const C2<float>* tws = tw_ + Tables<float, L>::RSOFF;
+    if (general)
+      col_pass_rs<L, C::W, true><<<grid, RC::NT, RC::SMEM, s>>>(solves, k_, tws, cond, use_cond);
+    else
+      col_pass_rs<L, C::W, false><<<grid, RC::NT, RC::SMEM, s>>>(solves, k_, tws, cond, use_cond);
+  } else {
+    const dim3 grid((L / 2) / C::W, nb);
+    if (general)
+      col_pass<T, L, EPFFT_VAR, true><<<grid, C::NT_COL, C::COL_SMEM, s>>>(solves, tw_, k_, cond, use_cond, g_col_succ[ilog2c(L)]);
+    else
+      col_pass<T, L, EPFFT_VAR, false><<<grid, C::NT_COL, C::COL_SMEM, s>>>(solves, tw_, k_, cond, use_cond, g_col_succ[ilog2c(L)]);
+  }
+  return cudaGetLastError();
+}
+
 template <>
 cudaError_t launch_col_v<EPFFT_REAL, EPFFT_VAR>(int L, int nb, cudaStream_t s, Solve* solves, const void* tw, const void* ktab,
                                    cudaGraphConditionalHandle cond, int use_cond, int general) {
   switch (L) {
-#define X(n)                                                                                         \
-  case n: {                                                                                          \
-    using C = Cfg<EPFFT_REAL, n, EPFFT_VAR>;                                                         \
-    const dim3 grid((n / 2) / C::W, nb);                                                             \
-    const C2<EPFFT_REAL>* tw_ = reinterpret_cast<const C2<EPFFT_REAL>*>(tw);                         \
-    const C2<EPFFT_REAL>* k_ = reinterpret_cast<const C2<EPFFT_REAL>*>(ktab);                        \
-    if (general)                                                                                     \
-      col_pass<EPFFT_REAL, n, EPFFT_VAR, true><<<grid, C::NT_COL, C::COL_SMEM, s>>>(solves, tw_, k_, cond, use_cond, g_col_succ[ilog2c(n)]); \
-    else                                                                                             \
-      col_pass<EPFFT_REAL, n, EPFFT_VAR, false><<<grid, C::NT_COL, C::COL_SMEM, s>>>(solves, tw_, k_, cond, use_cond, g_col_succ[ilog2c(n)]); \
-    return cudaGetLastError();                                                                       \
-  }
+#define X(n) case n: return launch_col_L<EPFFT_REAL, n>(nb, s, solves, tw, ktab, cond, use_cond, general);
     EPFFT_FOR_L(X)
 #undef X
     default: return cudaErrorInvalidValue;

@@ -11,6 +11,8 @@
 //                         (i k = exp(i q) - 1)
 //   [QOFF, QOFF + L)      (q~(m), 0), the continuum momentum 2 pi m~ / L with
 //                         m~ = m folded into (-L/2, L/2] (CG1 operator)
+//   [RSOFF, + RS_ENTRIES) the stage twiddles of the register-staged column
+//                         transform of length L (RsPlan in colrs.cuh)
 // Variants with the same plans share their stage tables.
 #pragma once
 #include <vector>
@@ -18,6 +20,51 @@
 #include "fft.cuh"
 
 namespace epfft {
+
+// Radix plan of the register-staged column transform of length L (used by
+// colrs.cuh): a first stage of radix R1 = 2, 4, 8 or 16, then radix-16
+// stages; a thread owns 16 elements per stage.  Stage s (1-based) works on
+// sub-transforms of length nlen(s) with stride stride(s) = nlen(s) /
+// radix(s); its twiddles exp(-2 pi i j k / nlen(s)), j < stride(s),
+// k = 1 .. radix(s) - 1, sit at tw_off(s) + (k - 1) stride(s) + j; the last
+// stage (stride 1) has none.  After the twiddles, KQOFF holds the Fourier
+// symbols of the frequencies the last stage's positions carry, in the order
+// the threads read them: entry r T + t is k(m) of position 16 t + r.
+template <int L>
+struct RsPlan {
+  static constexpr int E = 16;  // elements per thread and stage
+  static constexpr int LG = ilog2c(L);
+  static constexpr int R1 = LG % 4 == 0 ? 16 : (1 << (LG % 4));
+  static constexpr int S = LG % 4 == 0 ? LG / 4 : LG / 4 + 1;  // stages
+  static constexpr int T = L / E;                                // threads per column
+  static __host__ __device__ constexpr int radix(int s) { return s == 1 ? R1 : E; }
+  static __host__ __device__ constexpr int nlen(int s) { return s == 1 ? L : nlen(s - 1) / radix(s - 1); }
+  static __host__ __device__ constexpr int stride(int s) { return nlen(s) / radix(s); }
+  static __host__ __device__ constexpr int tw_count(int s) { return stride(s) > 1 ? (radix(s) - 1) * stride(s) : 0; }
+  static __host__ __device__ constexpr int tw_off(int s) { return s <= 1 ? 0 : tw_off(s - 1) + tw_count(s - 1); }
+  static constexpr int KQOFF = tw_off(S + 1);
+  static constexpr int TW_ENTRIES = KQOFF + L;
+  // the frequency position p holds after the forward transform:
+  // m = p_1 + R1 (p_2 + 16 (p_3 + ...)) for p = sum_s p_s stride(s)
+  static __host__ __device__ constexpr int freq(int p) {
+    int m = 0, w = 1;
+    for (int s = 1; s <= S; s++) {
+      m += ((p / stride(s)) % radix(s)) * w;
+      w *= radix(s);
+    }
+    return m;
+  }
+  // the position holding frequency m (inverse of freq)
+  static __host__ __device__ constexpr int pos(int m) {
+    int p = 0;
+    for (int s = 1; s <= S; s++) {
+      p += (m % radix(s)) * stride(s);
+      m /= radix(s);
+    }
+    return p;
+  }
+  static_assert(L >= 32 && (L & (L - 1)) == 0, "power of two");
+};
 
 // Transform plans of tiling variant V for (T, L): largest radix of the row
 // (length L/2) and column (length L) transforms, and the twiddle format
@@ -45,7 +92,9 @@ struct Tables {
   static constexpr int OFF_C1 = SAME ? OFF_C0 : OFF_R1 + TW_R1;
   static constexpr int KOFF = SAME ? OFF_C0 + TW_C0 : OFF_C1 + TW_C1;
   static constexpr int QOFF = KOFF + L;
-  static constexpr int TOTAL = QOFF + L;
+  static constexpr int RSOFF = QOFF + L;
+  static constexpr int RS_ENTRIES = L >= 32 ? RsPlan<(L >= 32 ? L : 32)>::TW_ENTRIES : 0;
+  static constexpr int TOTAL = RSOFF + RS_ENTRIES;
   static __host__ __device__ constexpr int off_row(int v) { return v == 0 ? OFF_R0 : OFF_R1; }
   static __host__ __device__ constexpr int off_col(int v) { return v == 0 ? OFF_C0 : OFF_C1; }
 };
@@ -94,6 +143,20 @@ inline void host_tables_L(std::vector<T>& h) {
     const int mf = m > L / 2 ? m - L : m;
     h[2 * (TB::QOFF + m)] = (T)(2.0L * pi * (long double)mf / (long double)L);
     h[2 * (TB::QOFF + m) + 1] = T(0);
+  }
+  if constexpr (L >= 32) {
+    using RP = RsPlan<L>;
+    for (int st = 1; st <= RP::S; st++)
+      for (int k = 1; k < RP::radix(st) && RP::stride(st) > 1; k++)
+        for (int j = 0; j < RP::stride(st); j++)
+          host_expi<T>((long)j * k, RP::nlen(st), h.data() + 2 * (TB::RSOFF + RP::tw_off(st) + (k - 1) * RP::stride(st) + j));
+    for (int t = 0; t < RP::T; t++)
+      for (int r = 0; r < RP::E; r++) {
+        const int m = RP::freq(RP::E * t + r);
+        T* o = h.data() + 2 * (TB::RSOFF + RP::KQOFF + r * RP::T + t);
+        o[0] = h[2 * (TB::KOFF + m)];
+        o[1] = h[2 * (TB::KOFF + m) + 1];
+      }
   }
 }
 

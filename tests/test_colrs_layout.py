@@ -1,0 +1,202 @@
+"""Index arithmetic of the register-staged column pass (csrc/colrs.cuh),
+restated on the CPU: the radix plan, the positions each thread touches in
+every stage, the shared-memory swizzle, the lane mapping of a CTA and the
+position -> frequency map.
+
+* A numpy replay of the stages (in-place decimation in frequency with the
+  plan's radices and twiddles, then the transposed stages in reverse order)
+  gives numpy's DFT in digit-reversed order and its exact inverse.
+* Every stage covers each position exactly once; the first stage holds
+  positions t + m T and the last one 16 t + r.
+* Every warp access of eight-byte elements (half-warp phases) falls on 16
+  distinct bank pairs, for the lane mapping the kernel uses (the two columns
+  of a tile interleaved lane by lane when a CTA holds both).
+"""
+import numpy as np
+import pytest
+
+SIZES = [128, 256, 512, 1024, 2048, 4096]
+E = 16  # elements per thread and sequence
+
+
+def plan(L):
+    lg = L.bit_length() - 1
+    r1 = E if lg % 4 == 0 else 1 << (lg % 4)
+    S = lg // 4 if lg % 4 == 0 else lg // 4 + 1
+    radix = [r1] + [E] * (S - 1)
+    nlen = [L]
+    for s in range(1, S):
+        nlen.append(nlen[-1] // radix[s - 1])
+    stride = [n // r for n, r in zip(nlen, radix)]
+    return radix, nlen, stride
+
+
+def cfg(L, W):
+    """(columns per CTA, threads per CTA, interleaved) as in RsCfg."""
+    T = L // E
+    cpc = max(2, 64 // T) if L <= 1024 else 1
+    inter = cpc >= 2 and W == 2
+    return cpc, cpc * T, inter
+
+
+def sw(e):
+    return e ^ ((e >> 4) & 15)
+
+
+def seq_base(L, g):
+    """Element offset of group g's three sequences (components at + c L)."""
+    return g * (3 * L + 8)
+
+
+def lane_map(L, W, tid):
+    """(group, t) of thread tid of a CTA."""
+    T = L // E
+    cpc, nt, inter = cfg(L, W)
+    if inter:
+        pair, rem = divmod(tid, 2 * T)
+        return 2 * pair + (rem & 1), rem >> 1
+    return divmod(tid, T)
+
+
+def freq(L, p):
+    radix, nlen, stride = plan(L)
+    m, w = 0, 1
+    for s in range(len(radix)):
+        m += ((p // stride[s]) % radix[s]) * w
+        w *= radix[s]
+    return m
+
+
+def butterflies(L, s, t):
+    """(base, stride, j) of the butterflies thread t does in stage s."""
+    radix, nlen, stride = plan(L)
+    T = L // E
+    R, N, D = radix[s], nlen[s], stride[s]
+    out = []
+    for i in range(E // R):
+        u = t + i * T
+        b, j = divmod(u, D)
+        out.append((b * N + j, D, j))
+    return out
+
+
+def stages_forward(L, x):
+    radix, nlen, stride = plan(L)
+    a = x.astype(np.complex128).copy()
+    for s in range(len(radix)):
+        R, N = radix[s], nlen[s]
+        for t in range(L // E):
+            for base, d, j in butterflies(L, s, t):
+                v = a[base + d * np.arange(R)]
+                y = np.array([np.sum(v * np.exp(-2j * np.pi * np.arange(R) * k / R)) for k in range(R)])
+                y *= np.exp(-2j * np.pi * j * np.arange(R) / N)
+                a[base + d * np.arange(R)] = y
+    return a
+
+
+def stages_inverse(L, a):
+    radix, nlen, stride = plan(L)
+    a = a.copy()
+    for s in reversed(range(len(radix))):
+        R, N = radix[s], nlen[s]
+        for t in range(L // E):
+            for base, d, j in butterflies(L, s, t):
+                v = a[base + d * np.arange(R)] * np.exp(2j * np.pi * j * np.arange(R) / N)
+                y = np.array([np.sum(v * np.exp(2j * np.pi * np.arange(R) * r / R)) for r in range(R)])
+                a[base + d * np.arange(R)] = y
+    return a
+
+
+@pytest.mark.parametrize("L", [128, 256, 512])
+def test_stages_are_the_dft_in_digit_reversed_order(L):
+    rng = np.random.default_rng(L)
+    x = rng.standard_normal(L) + 1j * rng.standard_normal(L)
+    a = stages_forward(L, x)
+    X = np.fft.fft(x)
+    order = np.array([freq(L, p) for p in range(L)])
+    np.testing.assert_allclose(a, X[order], rtol=0, atol=1e-9 * np.abs(X).max())
+    # the transposed stages give the unnormalised inverse in natural order
+    np.testing.assert_allclose(stages_inverse(L, a), L * x, rtol=0, atol=1e-9 * L * np.abs(x).max())
+
+
+@pytest.mark.parametrize("L", SIZES)
+def test_position_frequency_map(L):
+    f = [freq(L, p) for p in range(L)]
+    assert sorted(f) == list(range(L))
+    # the last stage's positions 16 t + r hold frequencies m0(t) + r L / 16
+    T = L // E
+    for t in range(T):
+        m0 = freq(L, E * t)
+        assert m0 < L // E
+        assert [freq(L, E * t + r) for r in range(E)] == [m0 + r * (L // E) for r in range(E)]
+
+
+@pytest.mark.parametrize("L", SIZES)
+def test_every_stage_covers_each_position_once(L):
+    radix, nlen, stride = plan(L)
+    T = L // E
+    for s in range(len(radix)):
+        seen = np.zeros(L, int)
+        for t in range(T):
+            for base, d, j in butterflies(L, s, t):
+                for r in range(radix[s]):
+                    seen[base + r * d] += 1
+        assert (seen == 1).all(), (L, s)
+    for t in range(T):
+        first = sorted(base + r * d for base, d, j in butterflies(L, 0, t) for r in range(radix[0]))
+        assert first == [t + m * T for m in range(E)]
+        last = sorted(base + r * d for base, d, j in butterflies(L, len(radix) - 1, t) for r in range(radix[-1]))
+        assert last == [E * t + r for r in range(E)]
+
+
+def phases_conflict_free(addrs):
+    """Eight-byte accesses of one warp: each half-warp phase must touch
+    distinct bank pairs (element index mod 16)."""
+    for h in (0, 16):
+        bank = [a % 16 for a in addrs[h:h + 16] if a is not None]
+        if len(set(bank)) != len(bank):
+            return False
+    return True
+
+
+@pytest.mark.parametrize("W", [1, 2])
+@pytest.mark.parametrize("L", SIZES)
+def test_shared_memory_accesses_are_bank_conflict_free(L, W):
+    radix, nlen, stride = plan(L)
+    T = L // E
+    cpc, nt, inter = cfg(L, W)
+    assert sorted(sw(e) for e in range(L)) == list(range(L))  # a permutation
+    for w0 in range(0, nt, 32):
+        lanes = [lane_map(L, W, tid) for tid in range(w0, w0 + 32)]
+        # butterfly stages
+        for s in range(len(radix)):
+            per = [(g, butterflies(L, s, t)) for g, t in lanes]
+            for i in range(E // radix[s]):
+                for r in range(radix[s]):
+                    addrs = [seq_base(L, g) + sw(b[i][0] + r * b[i][1]) for g, b in per]
+                    assert phases_conflict_free(addrs), (L, W, s, i, r)
+        # the unfused Green step and the first stage: positions t + m T
+        for m in range(E):
+            addrs = [seq_base(L, g) + sw(t + m * T) for g, t in lanes]
+            assert phases_conflict_free(addrs), (L, W, m)
+
+
+@pytest.mark.parametrize("W", [1, 2])
+@pytest.mark.parametrize("L", SIZES)
+def test_global_accesses_of_a_warp_are_contiguous_runs(L, W):
+    """In the first and last stage a warp reads / writes, per component and
+    m, the elements x2 = t + m T of its columns; with interleaved lanes the
+    two columns of a tile give one contiguous run of eight-byte numbers."""
+    T = L // E
+    cpc, nt, inter = cfg(L, W)
+    for w0 in range(0, nt, 32):
+        lanes = [lane_map(L, W, tid) for tid in range(w0, w0 + 32)]
+        for m in range(E):
+            # element index within the tiled layout: x2 W + w for column w
+            # of a tile; the lanes of one tile (pair of columns) form one run
+            by_tile = {}
+            for g, t in lanes:
+                by_tile.setdefault(g // W, []).append((t + m * T) * W + (g % W))
+            for idx in by_tile.values():
+                if inter:
+                    assert idx == list(range(idx[0], idx[0] + len(idx))) and len(idx) >= 16, (L, W, m)
