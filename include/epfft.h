@@ -469,21 +469,29 @@ int epfft_fp64_peak(epfft_ctx *ctx, double *tflops, int32_t *n_sm, float *ms);
 /* ---------------------------------------------------------------------- */
 /* Tiling (FFT tile shapes and CTA sizes per lattice side)                 */
 /* ---------------------------------------------------------------------- */
-/* Two tilings are compiled for every lattice side and precision (rows per
- * row-pass CTA, tile width of the spectrum layout = columns per
- * column-pass CTA, threads).  epfft_autotune times both on this device
- * (CUDA events, a batch of n_batch synthetic f = 0.2 lattices) and makes the
- * faster one the context's tiling for (L, precision) and for batches of
- * that class: launches that cover at least 2^21 pixels (L^2 x batch) form
- * one class, smaller ones the other, since small launches favour more and
+/* Up to EPFFT_N_TILINGS tilings are compiled per lattice side and
+ * precision: 0 and 1 are two tile shapes of the shared-memory passes (rows
+ * per row-pass CTA, tile width of the spectrum layout = columns per
+ * column-pass CTA, threads); 2 is the register-staged row and column passes
+ * (FP32, sides 256 .. 4096 only), whose spectrum is stored in the row
+ * transform's digit-reversed column order.  epfft_supported_tiling tells
+ * which exist.  epfft_autotune times every compiled one on this device (CUDA
+ * events, a batch of n_batch synthetic f = 0.2 lattices) and makes the
+ * fastest the context's tiling for (L, precision) and for batches of that
+ * class: launches that cover at least 2^21 pixels (L^2 x batch) form one
+ * class, smaller ones the other, since small launches favour more and
  * smaller CTAs and large ones fewer and larger.  *chosen receives the
- * choice and ms_per_iteration[2] (optional) the two timings.  Later solves,
- * batches, projections (class of one solve) and serving classes (class of
- * their slot count) of that size use it.  Blocking. */
+ * choice and ms_per_iteration[EPFFT_N_TILINGS] (optional) the timings (0 for
+ * a tiling that is not compiled).  Later solves, batches, projections (class
+ * of one solve) and serving classes (class of their slot count) of that size
+ * use it.  Blocking. */
+#define EPFFT_N_TILINGS 3
 int epfft_autotune(epfft_ctx *ctx, int32_t L, int32_t precision, int32_t n_batch, int32_t *chosen,
                    float *ms_per_iteration);
-/* Sets the tiling (0 or 1) of (L, precision) on the context, for both
- * batch classes. */
+/* 1 if tiling `variant` is compiled for (L, precision), else 0. */
+int epfft_supported_tiling(int32_t L, int32_t precision, int32_t variant);
+/* Sets the tiling of (L, precision) on the context, for both batch
+ * classes; EPFFT_ERR_UNSUPPORTED if it is not compiled for that size. */
 int epfft_set_tiling(epfft_ctx *ctx, int32_t L, int32_t precision, int32_t variant);
 
 #ifdef __cplusplus

@@ -29,6 +29,7 @@ EPFFT_ERR_DEVICE_TIMEOUT = -5
 EPFFT_ERR_CUDA = -6
 EPFFT_ERR_UNSUPPORTED = -7
 EPFFT_ERR_SCRATCH_LIMIT = -8
+N_TILINGS = 3  # EPFFT_N_TILINGS
 EPFFT_FP64 = 0
 EPFFT_FP32 = 1
 EPFFT_GREEN_EQ3 = 0
@@ -50,7 +51,7 @@ SYMBOLS = ["epfft_create", "epfft_destroy", "epfft_last_stats", "epfft_strerror"
            "epfft_solve_dg2", "epfft_average5", "epfft_void_plastic", "epfft_indicators",
            "epfft_effective_moduli", "epfft_empirical_curve", "epfft_eps_eq", "epfft_displacement",
            "epfft_ticket_fields", "epfft_release", "epfft_solve_refined", "epfft_solve_refined_batch",
-           "epfft_fp64_peak"]
+           "epfft_fp64_peak", "epfft_supported_tiling"]
 
 
 class EpfftError(RuntimeError):
@@ -148,6 +149,7 @@ def lib():
         L.epfft_time_passes.argtypes = [vp, C.POINTER(_Problem), i32, C.POINTER(dbl), i32, C.POINTER(C.c_float),
                                         C.POINTER(C.c_float)]
         L.epfft_fp64_peak.argtypes = [vp, C.POINTER(dbl), C.POINTER(i32), C.POINTER(C.c_float)]
+        L.epfft_supported_tiling.argtypes = [i32, i32, i32]
         for s in SYMBOLS:
             if s not in ("epfft_destroy", "epfft_strerror"):
                 getattr(L, s).restype = C.c_int
@@ -687,10 +689,14 @@ def epfft_autotune(ctx: Context, L: int, precision: str, n_batch: int = 1):
     solves and keeps the faster for the context (for batches of that size
     class).  Returns (chosen tiling, [ms per iteration of each])."""
     ch = C.c_int32()
-    ms = (C.c_float * 2)()
+    ms = (C.c_float * N_TILINGS)()
     _check(lib().epfft_autotune(ctx.handle, L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision], int(n_batch),
                                 C.byref(ch), ms), "epfft_autotune")
     return ch.value, list(ms)
+
+
+def epfft_supported_tiling(L: int, precision: str, variant: int) -> bool:
+    return bool(lib().epfft_supported_tiling(L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision], int(variant)))
 
 
 def epfft_set_tiling(ctx: Context, L: int, precision: str, variant: int):

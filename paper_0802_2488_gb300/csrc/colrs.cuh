@@ -75,11 +75,10 @@ struct RsCfg {
   static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 };
 
-// Twiddles of stage s for thread t (all of its butterflies), from the
-// read-only path.
-template <int L, int s>
-__device__ __forceinline__ void rs_twiddles(const C2<float>* __restrict__ tws, int t, C2<float> (&w)[16][15]) {
-  using P = RsPlan<L>;
+// Twiddles of stage s of plan P for thread t (all of its butterflies), from
+// the read-only path.
+template <typename P, int s>
+__device__ __forceinline__ void p16_twiddles(const C2<float>* __restrict__ tws, int t, C2<float> (&w)[16][15]) {
   constexpr int R = P::radix(s), D = P::stride(s), K = P::E / R;
   if constexpr (D > 1) {
     const float2* tb = reinterpret_cast<const float2*>(tws + P::tw_off(s));
@@ -95,17 +94,33 @@ __device__ __forceinline__ void rs_twiddles(const C2<float>* __restrict__ tws, i
   }
 }
 
-// One forward (DIF) or inverse (DIT) stage s on the three sequences of a
-// column group in shared memory (sq, sq + L, sq + 2 L).
-template <int L, int s, bool INV>
-__device__ __forceinline__ void rs_stage(C2<float>* sq, int t, const C2<float>* __restrict__ tws) {
-  using P = RsPlan<L>;
+// Twiddles of butterfly i of stage s of plan P for thread t (w[k - 1],
+// k = 1 .. radix - 1), from the read-only path.
+template <typename P, int s>
+__device__ __forceinline__ void p16_twiddles_i(const C2<float>* __restrict__ tws, int t, int i, C2<float> (&w)[15]) {
+  constexpr int R = P::radix(s), D = P::stride(s);
+  if constexpr (D > 1) {
+    const float2* tb = reinterpret_cast<const float2*>(tws + P::tw_off(s));
+    const int j = (t + i * P::T) % D;
+#pragma unroll
+    for (int k = 1; k < R; k++) {
+      const float2 x = __ldg(tb + (k - 1) * D + j);
+      w[k - 1] = mk(x.x, x.y);
+    }
+  }
+}
+
+// One forward (DIF) or inverse (DIT) stage s of plan P on the three
+// sequences sq, sq + SSTR, sq + 2 SSTR in shared memory, for thread t of the
+// sequence's T threads.
+template <typename P, int s, bool INV, int SSTR>
+__device__ __forceinline__ void p16_stage(C2<float>* sq, int t, const C2<float>* __restrict__ tws) {
   constexpr int R = P::radix(s), N = P::nlen(s), D = P::stride(s), K = P::E / R;
   C2<float> w[16][15];
-  rs_twiddles<L, s>(tws, t, w);
+  p16_twiddles<P, s>(tws, t, w);
 #pragma unroll 1
   for (int c = 0; c < 3; c++) {
-    C2<float>* q = sq + c * L;
+    C2<float>* q = sq + c * SSTR;
 #pragma unroll
     for (int i = 0; i < K; i++) {
       const int u = t + i * P::T;
@@ -132,30 +147,34 @@ __device__ __forceinline__ void rs_stage(C2<float>* sq, int t, const C2<float>* 
   }
 }
 
-// Forward stages 2 .. S-1 (each preceded by a barrier).
-template <int L, int s = 2>
-__device__ __forceinline__ void rs_forward_mid(C2<float>* sq, int t, const C2<float>* __restrict__ tws) {
-  if constexpr (s < RsPlan<L>::S) {
+// Forward stages s .. S-1 of plan P (each preceded by a barrier).
+template <typename P, int SSTR, int s = 2>
+__device__ __forceinline__ void p16_forward_mid(C2<float>* sq, int t, const C2<float>* __restrict__ tws) {
+  if constexpr (s < P::S) {
     __syncthreads();
-    rs_stage<L, s, false>(sq, t, tws);
-    rs_forward_mid<L, s + 1>(sq, t, tws);
+    p16_stage<P, s, false, SSTR>(sq, t, tws);
+    p16_forward_mid<P, SSTR, s + 1>(sq, t, tws);
   }
 }
-// Inverse stages S-1 .. 2 (each followed by a barrier).
-template <int L, int s = RsPlan<L>::S - 1>
-__device__ __forceinline__ void rs_inverse_mid(C2<float>* sq, int t, const C2<float>* __restrict__ tws) {
+// Inverse stages s .. 2 of plan P (each followed by a barrier).
+template <typename P, int SSTR, int s = P::S - 1>
+__device__ __forceinline__ void p16_inverse_mid(C2<float>* sq, int t, const C2<float>* __restrict__ tws) {
   if constexpr (s >= 2) {
-    rs_stage<L, s, true>(sq, t, tws);
+    p16_stage<P, s, true, SSTR>(sq, t, tws);
     __syncthreads();
-    rs_inverse_mid<L, s - 1>(sq, t, tws);
+    p16_inverse_mid<P, SSTR, s - 1>(sq, t, tws);
   }
 }
 
-// The column pass.  Grid: (L/2 / CPC, solves); column m1 of the tiled
-// spectrum layout (tile width W) per group of T threads.  The launch shape
-// is checked on entry; for that shape every index below is in range
-// (positions < L, components < 3, columns < L/2, groups < CPC).
-template <int L, int W, bool GEN>
+// The column pass.  Grid: (L/2 / CPC, solves); stored column p1 of the
+// tiled spectrum layout (tile width W) per group of T threads; it holds
+// frequency m1 = p1, or, with DREV (the layout of the register-staged row
+// pass, rowrs.cuh), the frequency the row transform's digit-reversed order
+// puts there, m1 = RowPlan<L/2>::freq(p1) (p1 = 0 holds the packed
+// m1 = 0 and L/2 columns either way).  The launch shape is checked on
+// entry; for that shape every index below is in range (positions < L,
+// components < 3, columns < L/2, groups < CPC).
+template <int L, int W, bool GEN, bool DREV>
 __global__ void __launch_bounds__(RsCfg<L, W>::NT, RsCfg<L, W>::MINB)
 col_pass_rs(Solve* __restrict__ solves, const C2<float>* __restrict__ ktab, const C2<float>* __restrict__ tws,
             cudaGraphConditionalHandle cond, int use_cond) {
@@ -178,8 +197,9 @@ col_pass_rs(Solve* __restrict__ solves, const C2<float>* __restrict__ ktab, cons
     g = threadIdx.x / T;
     t = threadIdx.x % T;
   }
-  const int m1 = blockIdx.x * CPC + g;
-  const int bt = m1 / W, w = m1 % W;
+  const int p1 = blockIdx.x * CPC + g;
+  const int bt = p1 / W, w = p1 % W;
+  const int m1 = DREV ? RowPlan<M>::freq_d(p1) : p1;
   C2<float>* sq = reinterpret_cast<C2<float>*>(smraw) + g * CF::GSTRIDE;
   C2<float>* spec = reinterpret_cast<C2<float>*>(Sol.spec);
   // element x2 of component c of this column: spec[gbase(c) + x2 W]
@@ -193,7 +213,7 @@ col_pass_rs(Solve* __restrict__ solves, const C2<float>* __restrict__ ktab, cons
   {
     constexpr int R = P::R1, D = P::stride(1), K = E / R;
     C2<float> tv[16][15];
-    rs_twiddles<L, 1>(tws, t, tv);
+    p16_twiddles<P, 1>(tws, t, tv);
 #pragma unroll 1
     for (int c = 0; c < 3; c++) {
       const float2* src = reinterpret_cast<const float2*>(spec + gbase(c));
@@ -220,7 +240,7 @@ col_pass_rs(Solve* __restrict__ solves, const C2<float>* __restrict__ ktab, cons
       }
     }
   }
-  rs_forward_mid<L>(sq, t, tws);
+  p16_forward_mid<P, L>(sq, t, tws);
   __syncthreads();
 
   if (blockIdx.x != 0) {
@@ -239,7 +259,7 @@ col_pass_rs(Solve* __restrict__ solves, const C2<float>* __restrict__ ktab, cons
     Bfly<float, E, false, true>::run(a2);
     const C2<float> k1 = ktab[m1];
     const float2* kq = reinterpret_cast<const float2*>(tws + P::KQOFF) + t;
-    const int m0 = P::freq(E * t);
+    const int m0 = P::freq_d(E * t);
 #pragma unroll
     for (int r = 0; r < E; r++) {
       if (GEN) {
@@ -261,13 +281,13 @@ col_pass_rs(Solve* __restrict__ solves, const C2<float>* __restrict__ ktab, cons
   } else {
     // the CTA that holds the packed column (m1 = 0): the last stage through
     // shared memory, then the Green operator position by position
-    rs_stage<L, S, false>(sq, t, tws);
+    p16_stage<P, S, false, L>(sq, t, tws);
     __syncthreads();
     if (m1 != 0) {
       const C2<float> k1 = ktab[m1];
       for (int m = 0; m < E; m++) {
         const int p = t + m * T;
-        const int m2 = P::freq(p);
+        const int m2 = P::freq_d(p);
         const int ip = sw16(p);
         C2<float> p11 = sq[ip], p22 = sq[L + ip], p12 = sq[2 * L + ip];
         if (GEN) green_op(gm, ktab, qtab, L, m1, m2, lam0, mu0, scale, p11, p22, p12);
@@ -282,7 +302,7 @@ col_pass_rs(Solve* __restrict__ solves, const C2<float>* __restrict__ ktab, cons
       const double* Ep = Sol.path + 4 * inc;
       for (int m2 = t; m2 <= L / 2; m2 += T) {
         const int mp = (L - m2) & (L - 1);
-        const int ia = sw16(P::pos(m2)), ib = sw16(P::pos(mp));
+        const int ia = sw16(P::pos_d(m2)), ib = sw16(P::pos_d(mp));
         C2<float> A[3], B[3], Ap[3], Bp[3];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
@@ -311,16 +331,16 @@ col_pass_rs(Solve* __restrict__ solves, const C2<float>* __restrict__ ktab, cons
       }
     }
     __syncthreads();
-    rs_stage<L, S, true>(sq, t, tws);
+    p16_stage<P, S, true, L>(sq, t, tws);
   }
   __syncthreads();
-  rs_inverse_mid<L>(sq, t, tws);
+  p16_inverse_mid<P, L>(sq, t, tws);
 
   // inverse stage 1 straight to HBM
   {
     constexpr int R = P::R1, D = P::stride(1), K = E / R;
     C2<float> tv[16][15];
-    rs_twiddles<L, 1>(tws, t, tv);
+    p16_twiddles<P, 1>(tws, t, tv);
 #pragma unroll 1
     for (int c = 0; c < 3; c++) {
       const C2<float>* q = sq + c * L;

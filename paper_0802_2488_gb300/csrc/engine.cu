@@ -143,12 +143,13 @@ int get_tables(epfft_ctx* c, int L, int prec, void** tw, void** ktab) {
 
 // First recorded self-check failure of any instantiation unit.
 cudaError_t read_check_all(CheckRec* out) {
-  CheckRec r[4];
+  CheckRec r[5];
   cudaError_t e;
   if ((e = read_check_v<float, 0>(&r[0])) != cudaSuccess) return e;
   if ((e = read_check_v<float, 1>(&r[1])) != cudaSuccess) return e;
   if ((e = read_check_v<double, 0>(&r[2])) != cudaSuccess) return e;
   if ((e = read_check_v<double, 1>(&r[3])) != cudaSuccess) return e;
+  if ((e = read_check_v<float, 2>(&r[4])) != cudaSuccess) return e;
   *out = CheckRec{};
   for (auto& x : r)
     if (x.code) {
@@ -925,6 +926,7 @@ int epfft_create(epfft_ctx** out, const epfft_options* opt) {
   if (!out) return EPFFT_ERR_ARG;
   *out = nullptr;
   static_assert(sizeof(epfft_record) == sizeof(Record), "record layout");
+  static_assert(EPFFT_N_TILINGS == N_VARIANTS, "tilings of the ABI");
   epfft_ctx* c = new epfft_ctx();
   if (opt) {
     c->device = opt->device;
@@ -1787,16 +1789,19 @@ int epfft_autotune(epfft_ctx* ctx, int32_t L, int32_t precision, int32_t n_batch
   const double E[4] = {0.0, 0.0, 0.0, 1.5 / (2.0 * std::sqrt(3.0))};
   const int64_t px = (int64_t)L * L * n_batch;
   const int n_iter = px >= ((int64_t)1 << 24) ? 10 : 30;
-  int best = 0;
+  int best = -1;
   float tbest = 0.f;
   for (int v = 0; v < N_VARIANTS; v++) {
+    if (ms_per_iteration) ms_per_iteration[v] = 0.f;
+    PassShape sh;
+    if (shape(L, precision, v, &sh) != EPFFT_OK) continue;  // not compiled for this size
     float c = 0.f, r = 0.f;
     // warm-up, then the timed launches
     int rc = time_passes_impl(ctx, p, n_batch, E, 3, v, &c, &r);
     if (!rc) rc = time_passes_impl(ctx, p, n_batch, E, n_iter, v, &c, &r);
     if (rc) return rc;
     if (ms_per_iteration) ms_per_iteration[v] = c + r;
-    if (v == 0 || c + r < tbest) {
+    if (best < 0 || c + r < tbest) {
       tbest = c + r;
       best = v;
     }
@@ -1806,10 +1811,17 @@ int epfft_autotune(epfft_ctx* ctx, int32_t L, int32_t precision, int32_t n_batch
   return EPFFT_OK;
 }
 
+int epfft_supported_tiling(int32_t L, int32_t precision, int32_t variant) {
+  if (variant < 0 || variant >= N_VARIANTS || !supported(L, precision)) return 0;
+  PassShape sh;
+  return shape(L, precision, variant, &sh) == EPFFT_OK ? 1 : 0;
+}
+
 int epfft_set_tiling(epfft_ctx* ctx, int32_t L, int32_t precision, int32_t variant) {
   if (!ctx || variant < 0 || variant >= N_VARIANTS) return EPFFT_ERR_ARG;
   if (!is_pow2(L) || L < 4 || (precision != EPFFT_FP32 && precision != EPFFT_FP64)) return EPFFT_ERR_ARG;
   if (!supported(L, precision)) return EPFFT_ERR_UNSUPPORTED;
+  if (!epfft_supported_tiling(L, precision, variant)) return EPFFT_ERR_UNSUPPORTED;
   for (int k = 0; k < 2; k++) ctx->variant[std::make_tuple((int)L, (int)precision, k)] = variant;
   return EPFFT_OK;
 }

@@ -25,10 +25,12 @@ static bool shape_of(PassShape* o) {
   return true;
 }
 
-// The column pass of FP32 lattices of side >= 128 is the register-staged
-// kernel (colrs.cuh); FP64 and smaller sides use col_pass.
+// The column pass of tiling 0 for FP32 lattices of side >= 128 is the
+// register-staged kernel (colrs.cuh), which puts several columns in a CTA;
+// tiling 1 (many small CTAs, for launches of few pixels) keeps col_pass, as
+// do FP64 and smaller sides.
 template <typename T, int L>
-constexpr bool kRegisterStaged = std::is_same<T, float>::value && L >= 128;
+constexpr bool kRegisterStaged = std::is_same<T, float>::value && L >= 128 && EPFFT_VAR == 0;
 
 // Column-pass CTAs resident on the GPU at once, per lattice side (index
 // log2 L), measured at preparation: a CTA prefetches the slab of the CTA
@@ -45,8 +47,8 @@ static cudaError_t prepare_L() {
   if ((e = cudaFuncSetAttribute(col_pass<T, L, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::COL_SMEM)) != cudaSuccess) return e;
   if constexpr (kRegisterStaged<T, L>) {
     using RC = RsCfg<L, C::W>;
-    if ((e = cudaFuncSetAttribute(col_pass_rs<L, C::W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::SMEM)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(col_pass_rs<L, C::W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::SMEM)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(col_pass_rs<L, C::W, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::SMEM)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(col_pass_rs<L, C::W, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::SMEM)) != cudaSuccess) return e;
   }
   {
     int dev = 0, nsm = 0, occ = 0;
@@ -108,9 +110,9 @@ static cudaError_t launch_col_L(int nb, cudaStream_t s, Solve* solves, const voi
     const dim3 grid((L / 2) / RC::CPC, nb);
     const C2<float>* tws = tw_ + Tables<float, L>::RSOFF;
     if (general)
-      col_pass_rs<L, C::W, true><<<grid, RC::NT, RC::SMEM, s>>>(solves, k_, tws, cond, use_cond);
+      col_pass_rs<L, C::W, true, false><<<grid, RC::NT, RC::SMEM, s>>>(solves, k_, tws, cond, use_cond);
     else
-      col_pass_rs<L, C::W, false><<<grid, RC::NT, RC::SMEM, s>>>(solves, k_, tws, cond, use_cond);
+      col_pass_rs<L, C::W, false, false><<<grid, RC::NT, RC::SMEM, s>>>(solves, k_, tws, cond, use_cond);
   } else {
     const dim3 grid((L / 2) / C::W, nb);
     if (general)

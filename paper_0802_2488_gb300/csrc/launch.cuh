@@ -1,14 +1,20 @@
 // Launch table of the fused passes.  Each (real type, tiling variant) pair
 // is instantiated for every supported lattice side in its own translation
-// unit (inst_f32_v0.cu ... inst_f64_v1.cu); the functions below dispatch on
-// the variant at run time.
+// unit (inst_f32_v0.cu ... inst_f64_v1.cu, inst_v2.cu); the functions below
+// dispatch on the variant at run time.  Variants 0 and 1 are two tilings of
+// the shared-memory Stockham row pass (passes.cuh): variant 0 (fewer, larger
+// CTAs) with the register-staged column pass for FP32 sides >= 128
+// (colrs.cuh), variant 1 (many small CTAs, for launches of few pixels) with
+// the Stockham column pass; variant 2 is the register-staged row and column
+// passes with the digit-reversed spectrum order (rowrs.cuh), FP32 sides
+// 256 .. 4096 only.
 #pragma once
 #include <cuda_runtime.h>
 #include "common.cuh"
 
 namespace epfft {
 
-constexpr int N_VARIANTS = 2;
+constexpr int N_VARIANTS = 3;
 
 struct PassShape {
   int rows_per_cta, tile_w;  // RR, W
@@ -38,35 +44,63 @@ cudaError_t launch_row_inverse_v(int L, cudaStream_t s, const void* spec, void* 
 template <typename T, int V>
 cudaError_t read_check_v(CheckRec* out);
 
-// Returns false when L is not built for T.
+// Returns false when L is not built for T in that variant.
 template <typename T>
 inline bool pass_shape(int L, int var, PassShape* out) {
-  return var == 0 ? pass_shape_v<T, 0>(L, out) : pass_shape_v<T, 1>(L, out);
+  switch (var) {
+    case 0: return pass_shape_v<T, 0>(L, out);
+    case 1: return pass_shape_v<T, 1>(L, out);
+    case 2: return pass_shape_v<T, 2>(L, out);
+    default: return false;
+  }
 }
 // Raises the dynamic shared-memory limit of the kernels for L (call before
 // any launch or capture).
 template <typename T>
 inline cudaError_t prepare(int L, int var) {
-  return var == 0 ? prepare_v<T, 0>(L) : prepare_v<T, 1>(L);
+  switch (var) {
+    case 0: return prepare_v<T, 0>(L);
+    case 1: return prepare_v<T, 1>(L);
+    case 2: return prepare_v<T, 2>(L);
+    default: return cudaErrorInvalidValue;
+  }
 }
 template <typename T>
 inline cudaError_t launch_row(int L, int var, int nb, cudaStream_t s, Solve* solves, BatchCtl* bc, const void* tw,
                               cudaGraphConditionalHandle cond, int use_cond) {
-  return var == 0 ? launch_row_v<T, 0>(L, nb, s, solves, bc, tw, cond, use_cond)
-                  : launch_row_v<T, 1>(L, nb, s, solves, bc, tw, cond, use_cond);
+  switch (var) {
+    case 0: return launch_row_v<T, 0>(L, nb, s, solves, bc, tw, cond, use_cond);
+    case 1: return launch_row_v<T, 1>(L, nb, s, solves, bc, tw, cond, use_cond);
+    case 2: return launch_row_v<T, 2>(L, nb, s, solves, bc, tw, cond, use_cond);
+    default: return cudaErrorInvalidValue;
+  }
 }
 template <typename T>
 inline cudaError_t launch_col(int L, int var, int nb, cudaStream_t s, Solve* solves, const void* tw,
                               const void* ktab, cudaGraphConditionalHandle cond, int use_cond, int general = 0) {
-  return var == 0 ? launch_col_v<T, 0>(L, nb, s, solves, tw, ktab, cond, use_cond, general)
-                  : launch_col_v<T, 1>(L, nb, s, solves, tw, ktab, cond, use_cond, general);
+  switch (var) {
+    case 0: return launch_col_v<T, 0>(L, nb, s, solves, tw, ktab, cond, use_cond, general);
+    case 1: return launch_col_v<T, 1>(L, nb, s, solves, tw, ktab, cond, use_cond, general);
+    case 2: return launch_col_v<T, 2>(L, nb, s, solves, tw, ktab, cond, use_cond, general);
+    default: return cudaErrorInvalidValue;
+  }
 }
 template <typename T>
 inline cudaError_t launch_row_forward(int L, int var, cudaStream_t s, const void* p, void* spec, const void* tw) {
-  return var == 0 ? launch_row_forward_v<T, 0>(L, s, p, spec, tw) : launch_row_forward_v<T, 1>(L, s, p, spec, tw);
+  switch (var) {
+    case 0: return launch_row_forward_v<T, 0>(L, s, p, spec, tw);
+    case 1: return launch_row_forward_v<T, 1>(L, s, p, spec, tw);
+    case 2: return launch_row_forward_v<T, 2>(L, s, p, spec, tw);
+    default: return cudaErrorInvalidValue;
+  }
 }
 template <typename T>
 inline cudaError_t launch_row_inverse(int L, int var, cudaStream_t s, const void* spec, void* e, const void* tw) {
-  return var == 0 ? launch_row_inverse_v<T, 0>(L, s, spec, e, tw) : launch_row_inverse_v<T, 1>(L, s, spec, e, tw);
+  switch (var) {
+    case 0: return launch_row_inverse_v<T, 0>(L, s, spec, e, tw);
+    case 1: return launch_row_inverse_v<T, 1>(L, s, spec, e, tw);
+    case 2: return launch_row_inverse_v<T, 2>(L, s, spec, e, tw);
+    default: return cudaErrorInvalidValue;
+  }
 }
 }  // namespace epfft

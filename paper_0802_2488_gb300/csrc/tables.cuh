@@ -12,7 +12,10 @@
 //   [QOFF, QOFF + L)      (q~(m), 0), the continuum momentum 2 pi m~ / L with
 //                         m~ = m folded into (-L/2, L/2] (CG1 operator)
 //   [RSOFF, + RS_ENTRIES) the stage twiddles of the register-staged column
-//                         transform of length L (RsPlan in colrs.cuh)
+//                         transform of length L and the Fourier symbols in
+//                         the order its last stage reads them (RsPlan)
+//   [RROFF, + RR_ENTRIES) the stage twiddles of the register-staged row
+//                         transform of length L/2 and its twists (RowPlan)
 // Variants with the same plans share their stage tables.
 #pragma once
 #include <vector>
@@ -21,31 +24,26 @@
 
 namespace epfft {
 
-// Radix plan of the register-staged column transform of length L (used by
-// colrs.cuh): a first stage of radix R1 = 2, 4, 8 or 16, then radix-16
-// stages; a thread owns 16 elements per stage.  Stage s (1-based) works on
-// sub-transforms of length nlen(s) with stride stride(s) = nlen(s) /
-// radix(s); its twiddles exp(-2 pi i j k / nlen(s)), j < stride(s),
-// k = 1 .. radix(s) - 1, sit at tw_off(s) + (k - 1) stride(s) + j; the last
-// stage (stride 1) has none.  After the twiddles, KQOFF holds the Fourier
-// symbols of the frequencies the last stage's positions carry, in the order
-// the threads read them: entry r T + t is k(m) of position 16 t + r.
-template <int L>
-struct RsPlan {
-  static constexpr int E = 16;  // elements per thread and stage
-  static constexpr int LG = ilog2c(L);
-  static constexpr int R1 = LG % 4 == 0 ? 16 : (1 << (LG % 4));
-  static constexpr int S = LG % 4 == 0 ? LG / 4 : LG / 4 + 1;  // stages
-  static constexpr int T = L / E;                                // threads per column
-  static __host__ __device__ constexpr int radix(int s) { return s == 1 ? R1 : E; }
-  static __host__ __device__ constexpr int nlen(int s) { return s == 1 ? L : nlen(s - 1) / radix(s - 1); }
+// Radix plans of the register-staged transforms (colrs.cuh, rowrs.cuh): a
+// thread owns E = 16 elements per stage and sequence; stage 1 has radix RA,
+// stage 2 radix RB, later stages radix 16, and N = RA RB 16^(S - 2).
+// Stage s (1-based) works on sub-transforms of length nlen(s) with stride
+// stride(s) = nlen(s) / radix(s); its twiddles exp(-2 pi i j k / nlen(s)),
+// j < stride(s), k = 1 .. radix(s) - 1, sit at tw_off(s) + (k - 1) stride(s)
+// + j; the last stage (stride 1) has none.  After the forward
+// (decimation-in-frequency) stages, position p = sum_s p_s stride(s) holds
+// frequency freq(p) = p_1 + RA (p_2 + RB (p_3 + 16 (...))); pos() inverts it.
+template <int N, int RA, int RB>
+struct Plan16 {
+  static constexpr int E = 16;
+  static constexpr int T = N / E;  // threads per sequence
+  static constexpr int S = N == RA ? 1 : 2 + ilog2c(N / (RA * RB)) / 4;
+  static __host__ __device__ constexpr int radix(int s) { return s == 1 ? RA : (s == 2 ? RB : 16); }
+  static __host__ __device__ constexpr int nlen(int s) { return s == 1 ? N : nlen(s - 1) / radix(s - 1); }
   static __host__ __device__ constexpr int stride(int s) { return nlen(s) / radix(s); }
   static __host__ __device__ constexpr int tw_count(int s) { return stride(s) > 1 ? (radix(s) - 1) * stride(s) : 0; }
   static __host__ __device__ constexpr int tw_off(int s) { return s <= 1 ? 0 : tw_off(s - 1) + tw_count(s - 1); }
-  static constexpr int KQOFF = tw_off(S + 1);
-  static constexpr int TW_ENTRIES = KQOFF + L;
-  // the frequency position p holds after the forward transform:
-  // m = p_1 + R1 (p_2 + 16 (p_3 + ...)) for p = sum_s p_s stride(s)
+  static constexpr int TW_END = tw_off(S + 1);
   static __host__ __device__ constexpr int freq(int p) {
     int m = 0, w = 1;
     for (int s = 1; s <= S; s++) {
@@ -54,7 +52,6 @@ struct RsPlan {
     }
     return m;
   }
-  // the position holding frequency m (inverse of freq)
   static __host__ __device__ constexpr int pos(int m) {
     int p = 0;
     for (int s = 1; s <= S; s++) {
@@ -63,7 +60,59 @@ struct RsPlan {
     }
     return p;
   }
-  static_assert(L >= 32 && (L & (L - 1)) == 0, "power of two");
+  // device forms of freq and pos: every radix and stride is a power of two,
+  // so the digits are shifts and masks by compile-time amounts
+  static __host__ __device__ constexpr int lg_stride(int s) { return ilog2c(stride(s)); }
+  static __host__ __device__ constexpr int lg_weight(int s) { return s <= 1 ? 0 : lg_weight(s - 1) + ilog2c(radix(s - 1)); }
+  template <int s = 1>
+  static __device__ __forceinline__ int freq_d(int p) {
+    if constexpr (s > S) {
+      return 0;
+    } else {
+      return (((p >> lg_stride(s)) & (radix(s) - 1)) << lg_weight(s)) | freq_d<s + 1>(p);
+    }
+  }
+  template <int s = 1>
+  static __device__ __forceinline__ int pos_d(int m) {
+    if constexpr (s > S) {
+      return 0;
+    } else {
+      return (((m >> lg_weight(s)) & (radix(s) - 1)) << lg_stride(s)) | pos_d<s + 1>(m);
+    }
+  }
+  static_assert(N >= E && RA * (S >= 2 ? RB : 1) * (1 << (4 * (S > 2 ? S - 2 : 0))) == N, "radix plan");
+  static_assert(E % RA == 0 && E % RB == 0, "radices divide the elements per thread");
+};
+
+template <int N>
+constexpr int col_ra() { return ilog2c(N) % 4 == 0 ? 16 : (1 << (ilog2c(N) % 4)); }
+// the column transform of length L: a first stage of radix 2, 4, 8 or 16,
+// then radix 16
+template <int L>
+struct RsPlan : Plan16<L, col_ra<L>(), 16> {
+  using B = Plan16<L, col_ra<L>(), 16>;
+  static constexpr int R1 = col_ra<L>();
+  // after the stage twiddles: the Fourier symbols of the frequencies the
+  // last stage's positions carry, entry r T + t = k(m) of position 16 t + r
+  static constexpr int KQOFF = B::TW_END;
+  static constexpr int TW_ENTRIES = KQOFF + L;
+};
+// the half-length row transform of length M: a first stage of radix 2, 4 or
+// 8 (radix 4 twice when log2 M is a multiple of 4), so that the pixel step,
+// which sits between the last inverse and the first forward stage, holds
+// few numbers per thread
+template <int M>
+constexpr int row_ra() { return ilog2c(M) % 4 == 0 ? 4 : (1 << (ilog2c(M) % 4)); }
+template <int M>
+constexpr int row_rb() { return ilog2c(M) % 4 == 0 ? 4 : 16; }
+template <int M>
+struct RowPlan : Plan16<M, row_ra<M>(), row_rb<M>()> {
+  using B = Plan16<M, row_ra<M>(), row_rb<M>()>;
+  static constexpr int R1 = row_ra<M>();
+  // after the stage twiddles: exp(-2 pi i freq(q) / (2 M)) per position q,
+  // the twists between the half-length transform and the real one
+  static constexpr int TQOFF = B::TW_END;
+  static constexpr int TW_ENTRIES = TQOFF + M;
 };
 
 // Transform plans of tiling variant V for (T, L): largest radix of the row
@@ -94,7 +143,9 @@ struct Tables {
   static constexpr int QOFF = KOFF + L;
   static constexpr int RSOFF = QOFF + L;
   static constexpr int RS_ENTRIES = L >= 32 ? RsPlan<(L >= 32 ? L : 32)>::TW_ENTRIES : 0;
-  static constexpr int TOTAL = RSOFF + RS_ENTRIES;
+  static constexpr int RROFF = RSOFF + RS_ENTRIES;
+  static constexpr int RR_ENTRIES = L >= 64 ? RowPlan<(L >= 64 ? L / 2 : 32)>::TW_ENTRIES : 0;
+  static constexpr int TOTAL = RROFF + RR_ENTRIES;
   static __host__ __device__ constexpr int off_row(int v) { return v == 0 ? OFF_R0 : OFF_R1; }
   static __host__ __device__ constexpr int off_col(int v) { return v == 0 ? OFF_C0 : OFF_C1; }
 };
@@ -123,6 +174,15 @@ inline void host_stage_table(T* h) {
   }
 }
 
+// Stage twiddles of a Plan16 at h (complex entries, interleaved reals).
+template <typename T, typename P>
+inline void host_plan16_twiddles(T* h) {
+  for (int st = 1; st <= P::S; st++)
+    for (int k = 1; k < P::radix(st) && P::stride(st) > 1; k++)
+      for (int j = 0; j < P::stride(st); j++)
+        host_expi<T>((long)j * k, P::nlen(st), h + 2 * (P::tw_off(st) + (k - 1) * P::stride(st) + j));
+}
+
 template <typename T, int L>
 inline void host_tables_L(std::vector<T>& h) {
   using TB = Tables<T, L>;
@@ -146,10 +206,7 @@ inline void host_tables_L(std::vector<T>& h) {
   }
   if constexpr (L >= 32) {
     using RP = RsPlan<L>;
-    for (int st = 1; st <= RP::S; st++)
-      for (int k = 1; k < RP::radix(st) && RP::stride(st) > 1; k++)
-        for (int j = 0; j < RP::stride(st); j++)
-          host_expi<T>((long)j * k, RP::nlen(st), h.data() + 2 * (TB::RSOFF + RP::tw_off(st) + (k - 1) * RP::stride(st) + j));
+    host_plan16_twiddles<T, RP>(h.data() + 2 * TB::RSOFF);
     for (int t = 0; t < RP::T; t++)
       for (int r = 0; r < RP::E; r++) {
         const int m = RP::freq(RP::E * t + r);
@@ -157,6 +214,11 @@ inline void host_tables_L(std::vector<T>& h) {
         o[0] = h[2 * (TB::KOFF + m)];
         o[1] = h[2 * (TB::KOFF + m) + 1];
       }
+  }
+  if constexpr (L >= 64) {
+    using RW = RowPlan<L / 2>;
+    host_plan16_twiddles<T, RW>(h.data() + 2 * TB::RROFF);
+    for (int q = 0; q < L / 2; q++) host_expi<T>(RW::freq(q), L, h.data() + 2 * (TB::RROFF + RW::TQOFF + q));
   }
 }
 

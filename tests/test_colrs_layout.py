@@ -200,3 +200,210 @@ def test_global_accesses_of_a_warp_are_contiguous_runs(L, W):
             for idx in by_tile.values():
                 if inter:
                     assert idx == list(range(idx[0], idx[0] + len(idx))) and len(idx) >= 16, (L, W, m)
+
+
+# --------------------------------------------------------------------------
+# the register-staged row pass (csrc/rowrs.cuh): half-length plan, twists on
+# digit-reversed positions, shared-memory banks of its patterns
+# --------------------------------------------------------------------------
+ROW_SIZES = [256, 512, 1024, 2048, 4096]  # lattice sides L; M = L / 2
+
+
+def plan16(N, ra, rb):
+    radix = [ra] + ([rb] if N > ra else [])
+    while np.prod(radix) < N:
+        radix.append(16)
+    assert np.prod(radix) == N
+    nlen = [N]
+    for s in range(1, len(radix)):
+        nlen.append(nlen[-1] // radix[s - 1])
+    stride = [n // r for n, r in zip(nlen, radix)]
+    return radix, nlen, stride
+
+
+def row_plan(M):
+    lg = M.bit_length() - 1
+    if lg % 4 == 0:
+        return plan16(M, 4, 4)
+    return plan16(M, 1 << (lg % 4), 16)
+
+
+def p16_freq(pl, p):
+    radix, nlen, stride = pl
+    m, w = 0, 1
+    for s in range(len(radix)):
+        m += ((p // stride[s]) % radix[s]) * w
+        w *= radix[s]
+    return m
+
+
+def p16_pos(pl, m):
+    radix, nlen, stride = pl
+    p = 0
+    for s in range(len(radix)):
+        p += (m % radix[s]) * stride[s]
+        m //= radix[s]
+    return p
+
+
+def p16_butterflies(pl, s, t):
+    radix, nlen, stride = pl
+    T = nlen[0] // E
+    out = []
+    for i in range(E // radix[s]):
+        u = t + i * T
+        b, j = divmod(u, stride[s])
+        out.append((b * nlen[s] + j, stride[s], j))
+    return out
+
+
+def p16_forward(pl, x):
+    radix, nlen, stride = pl
+    a = x.astype(np.complex128).copy()
+    for s in range(len(radix)):
+        R, N = radix[s], nlen[s]
+        for t in range(nlen[0] // E):
+            for base, d, j in p16_butterflies(pl, s, t):
+                idx = base + d * np.arange(R)
+                v = a[idx]
+                y = np.array([np.sum(v * np.exp(-2j * np.pi * np.arange(R) * k / R)) for k in range(R)])
+                a[idx] = y * np.exp(-2j * np.pi * j * np.arange(R) / N)
+    return a
+
+
+def p16_inverse(pl, a):
+    radix, nlen, stride = pl
+    a = a.copy()
+    for s in reversed(range(len(radix))):
+        R, N = radix[s], nlen[s]
+        for t in range(nlen[0] // E):
+            for base, d, j in p16_butterflies(pl, s, t):
+                idx = base + d * np.arange(R)
+                v = a[idx] * np.exp(2j * np.pi * j * np.arange(R) / N)
+                a[idx] = np.array([np.sum(v * np.exp(2j * np.pi * np.arange(R) * r / R)) for r in range(R)])
+    return a
+
+
+def twist(pl, L, s, fwd):
+    """The pair twist of rrs_twist on the digit-reversed sequence s
+    (position q holds frequency freq(q)); returns a new array."""
+    M = L // 2
+    T = M // E
+    out = s.copy()
+    done = np.zeros(M, int)
+    for t in range(T):
+        for j in range(E):
+            q = t + j * T
+            k = p16_freq(pl, q)
+            if k == 0:
+                z = s[q]
+                out[q] = (z.real + z.imag) + 1j * (z.real - z.imag)
+                done[q] += 1
+                continue
+            q2 = p16_pos(pl, M - k)
+            if q2 < q:
+                continue
+            w = np.exp(-2j * np.pi * k / L)
+            if not fwd:
+                w = np.conj(w)
+            a, b = s[q], s[q2]
+            tt = w * (a - np.conj(b))
+            if fwd:
+                out[q] = 0.5 * ((a + np.conj(b)) - 1j * tt)
+                if q2 != q:
+                    out[q2] = 0.5 * ((b + np.conj(a)) - 1j * np.conj(tt))
+            else:
+                out[q] = (a + np.conj(b)) + 1j * tt
+                if q2 != q:
+                    out[q2] = (b + np.conj(a)) + 1j * np.conj(tt)
+            done[q] += 1
+            done[q2] += q2 != q
+    assert (done == 1).all()  # every position by exactly one thread
+    return out
+
+
+@pytest.mark.parametrize("L", [64, 128, 256, 512, 1024])
+def test_row_transform_replay_against_numpy(L):
+    """Packed half spectrum of a real row, stored digit-reversed -> inverse
+    twist -> inverse stages gives x(2n) + i x(2n+1) (times M); the forward
+    stages and twist give the packed half spectrum back (times M)."""
+    M = L // 2
+    pl = row_plan(M)
+    rng = np.random.default_rng(L)
+    x = rng.standard_normal(L)
+    X = np.fft.fft(x)
+    packed = X[:M].copy()
+    packed[0] = X[0].real + 1j * X[M].real
+    order = np.array([p16_freq(pl, q) for q in range(M)])
+    stored = packed[order]  # position q holds frequency freq(q)
+    z = p16_inverse(pl, twist(pl, L, stored, fwd=False))
+    # the inverse is unnormalised and its twist carries no factor 1/2, so z
+    # is L (x(2n) + i x(2n+1)), as for the full-length unnormalised inverse
+    np.testing.assert_allclose(z, 2 * M * (x[0::2] + 1j * x[1::2]), rtol=0, atol=1e-9 * L * np.abs(x).max())
+    back = twist(pl, L, p16_forward(pl, x[0::2] + 1j * x[1::2]), fwd=True)
+    np.testing.assert_allclose(back, stored, rtol=0, atol=1e-9 * np.abs(X).max())
+
+
+def row_cfg(L):
+    M = L // 2
+    T = M // E
+    RR = 16 if L <= 256 else (8 if L == 512 else (4 if L == 1024 else 2))
+    return M, T, RR, (1 if L == 256 else 2), 3 * M + 16
+
+
+def row_base(L, rr):
+    M, T, RR, W, RS = row_cfg(L)
+    return rr * RS + ((rr * (16 // RR)) & 15 if T >= 16 else (rr >> 1) + 8 * (rr & 1))
+
+
+def wavefronts(addrs):
+    """Shared-memory wavefronts of one warp's eight-byte accesses: per
+    half-warp phase, the largest number of distinct elements on one bank
+    pair."""
+    n = 0
+    for h in (0, 16):
+        per = {}
+        for a in addrs[h:h + 16]:
+            if a is not None:
+                per.setdefault(a % 16, set()).add(a)
+        n += max((len(v) for v in per.values()), default=0)
+    return n
+
+
+@pytest.mark.parametrize("L", ROW_SIZES)
+def test_row_pass_banks(L):
+    """FFT stages, stage-1 positions, the twist's own positions and the
+    transposing spectrum load and store are conflict-free; the twist
+    partners (the lane order reversed) cost at most 4 wavefronts."""
+    M, T, RR, W, RS = row_cfg(L)
+    pl = row_plan(M)
+    radix = pl[0]
+    NT = RR * T
+    worst_partner = 0
+    for w0 in range(0, NT, 32):
+        lanes = [divmod(tid, T) for tid in range(w0, w0 + 32)]
+        for s in range(len(radix)):
+            per = [(rr, p16_butterflies(pl, s, t)) for rr, t in lanes]
+            for i in range(E // radix[s]):
+                for r in range(radix[s]):
+                    addrs = [row_base(L, rr) + sw(b[i][0] + r * b[i][1]) for rr, b in per]
+                    assert wavefronts(addrs) == 2, (L, s, i, r)
+        for j in range(E):
+            own = [row_base(L, rr) + sw(t + j * T) for rr, t in lanes]
+            assert wavefronts(own) == 2, (L, j)
+            part = []
+            for rr, t in lanes:
+                k = p16_freq(pl, t + j * T)
+                part.append(row_base(L, rr) + sw(p16_pos(pl, (M - k) % M)) if k else None)
+            worst_partner = max(worst_partner, wavefronts(part))
+    assert worst_partner <= 4, worst_partner
+    # the transposing load / store: consecutive threads take consecutive
+    # numbers of a tile chunk (RR rows x W columns)
+    for w0 in range(0, 3 * M * RR, 32):
+        addrs = []
+        for e in range(w0, w0 + 32):
+            chunk, within = divmod(e, RR * W)
+            c, b = divmod(chunk, M // W)
+            rr, w = divmod(within, W)
+            addrs.append(row_base(L, rr) + c * M + sw(b * W + w))
+        assert wavefronts(addrs) == 2, (L, w0, wavefronts(addrs))
