@@ -194,9 +194,12 @@ int epfft_solve(epfft_ctx *ctx, const epfft_problem *problem, const epfft_path *
 /* Blocking solve of n independent problems (each as epfft_solve, Sec. 2)
  * advanced together on the device, one augmented-Lagrangian pass of every
  * unfinished problem per step of a single device-side loop (one CUDA graph
- * launch).  All problems share L and precision (else EPFFT_ERR_ARG).  records[i] is a host array
- * of paths[i].n_inc entries; fields may be NULL or an array of n.  The
- * arithmetic of each problem does not depend on the others in the batch. */
+ * launch).  Problems may differ in L and precision: those of one (L,
+ * precision) form a group whose passes run on a branch of their own in the
+ * loop body, all groups concurrently, and the loop goes on while any
+ * problem is unfinished.  records[i] is a host array of paths[i].n_inc
+ * entries; fields may be NULL or an array of n.  The arithmetic of each
+ * problem does not depend on the others in the batch. */
 int epfft_solve_batch(epfft_ctx *ctx, int32_t n, const epfft_problem *problems,
                       const epfft_path *paths, epfft_record *const *records,
                       const epfft_fields *fields);

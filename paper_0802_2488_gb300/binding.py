@@ -482,8 +482,9 @@ def epfft_average5(ctx: Context, L: int, precision: str, eps_in, eps_out):
 
 def epfft_solve_batch(ctx: Context, problems: Sequence[Problem], paths: Sequence, fields: bool = False,
                       out: Optional[Sequence[Fields]] = None):
-    """Blocking solve of problems sharing L and precision, advanced together
-    in one device loop.  Returns (rc, [records][, [Fields]]).  With fields,
+    """Blocking solve of problems advanced together in one device loop (one
+    graph launch; problems of differing L or precision run on parallel
+    branches of its body).  Returns (rc, [records][, [Fields]]).  With fields,
     `out` may give the host buffers to fill (one Fields per problem, e.g.
     from pinned_fields); otherwise new arrays are allocated."""
     n = len(problems)

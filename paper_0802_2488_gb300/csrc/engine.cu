@@ -30,6 +30,7 @@ struct epfft_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;  // work stream
   cudaStream_t cap = nullptr;     // stream used only to capture graph bodies
+  std::vector<cudaStream_t> aux;  // fork streams of captures with parallel branches
   bool own_stream = false;
   epfft_alloc_fn alloc = nullptr;
   epfft_free_fn freef = nullptr;
@@ -425,6 +426,118 @@ int run_graph(epfft_ctx* c, Batch& B) {
   return rc;
 }
 
+// Loop condition of a graph over several batches (sizes, precisions): go on
+// while some batch has a solve that is not done and steps left.  One thread.
+__global__ void loop_decide_kernel(BatchCtl* const* ctl, int n, cudaGraphConditionalHandle h) {
+  bool go = false;
+  for (int g = 0; g < n; g++) {
+    const volatile BatchCtl* b = ctl[g];
+    if (b->active > 0 && b->body_iters < b->max_body_iters) go = true;
+  }
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// One CUDA graph that advances several batches of different lattice sides or
+// precisions together: a conditional while node whose body runs each
+// batch's [column pass, row pass] on a branch of its own (the branches run
+// concurrently), then, after they join, a one-thread kernel that sets the
+// loop condition from every batch's control block.  The passes of this graph
+// leave the condition alone (use_cond = 0).  dctl: device array of the
+// batches' control blocks.  The executable graph can be launched again.
+int build_mixed_graph(epfft_ctx* c, std::vector<Batch*>& Bs, BatchCtl** dctl, cudaGraph_t* graph_out,
+                      cudaGraphExec_t* exec_out) {
+  const int G = (int)Bs.size();
+  while ((int)c->aux.size() < G) {
+    cudaStream_t a;
+    CK(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+    c->aux.push_back(a);
+  }
+  std::vector<cudaEvent_t> ev(G + 1, nullptr);
+  for (auto& e : ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int rc = EPFFT_OK;
+  do {
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) {
+      rc = EPFFT_ERR_CUDA;
+      break;
+    }
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+      rc = EPFFT_ERR_CUDA;
+      break;
+    }
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp) != cudaSuccess) {
+      rc = EPFFT_ERR_CUDA;
+      break;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+        cudaSuccess) {
+      rc = EPFFT_ERR_CUDA;
+      break;
+    }
+    int lrc = cudaEventRecord(ev[G], c->cap) == cudaSuccess ? EPFFT_OK : EPFFT_ERR_CUDA;
+    for (int g = 0; g < G && !lrc; g++) {
+      if (cudaStreamWaitEvent(c->aux[g], ev[G], 0) != cudaSuccess) lrc = EPFFT_ERR_CUDA;
+      if (!lrc) lrc = launch_body(c, *Bs[g], c->aux[g], h, 0);
+      if (!lrc && cudaEventRecord(ev[g], c->aux[g]) != cudaSuccess) lrc = EPFFT_ERR_CUDA;
+      if (!lrc && cudaStreamWaitEvent(c->cap, ev[g], 0) != cudaSuccess) lrc = EPFFT_ERR_CUDA;
+    }
+    if (!lrc) {
+      loop_decide_kernel<<<1, 1, 0, c->cap>>>(dctl, G, h);
+      if (cudaGetLastError() != cudaSuccess) lrc = EPFFT_ERR_CUDA;
+    }
+    cudaGraph_t captured = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(c->cap, &captured);
+    if (lrc != EPFFT_OK || ec != cudaSuccess) {
+      rc = EPFFT_ERR_CUDA;
+      break;
+    }
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      rc = EPFFT_ERR_CUDA;
+      break;
+    }
+  } while (0);
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (rc != EPFFT_OK) {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return rc;
+  }
+  *graph_out = graph;
+  *exec_out = exec;
+  return EPFFT_OK;
+}
+
+// Runs several batches to completion in one launch of a mixed graph.
+int run_mixed_graph(epfft_ctx* c, Arena& A, std::vector<Batch*>& Bs) {
+  const int G = (int)Bs.size();
+  BatchCtl** dctl = (BatchCtl**)A.get(sizeof(BatchCtl*) * (size_t)G);
+  if (!dctl) return EPFFT_ERR_OOM;
+  std::vector<BatchCtl*> h(G);
+  for (int g = 0; g < G; g++) h[g] = Bs[g]->d_ctl;
+  CK(cudaMemcpyAsync(dctl, h.data(), sizeof(BatchCtl*) * (size_t)G, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int rc = build_mixed_graph(c, Bs, dctl, &graph, &exec);
+  if (rc) return rc;
+  if (cudaGraphLaunch(exec, c->stream) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    rc = EPFFT_ERR_CUDA;
+    cudaGetLastError();
+  }
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  return rc;
+}
+
 // The same loop for a known number of steps, launched from the host with no
 // graph and no synchronisation: steps beyond a solve's DONE phase are
 // no-ops (the passes skip DONE solves), so `steps` only has to cover the
@@ -539,42 +652,82 @@ int copy_out(epfft_ctx* c, Batch& B, Solve& S, int i, const epfft_fields* f) {
   return EPFFT_OK;
 }
 
+// Solves n problems in one device-driven loop.  Problems of one lattice side
+// and precision form a batch; several batches (mixed sides or precisions)
+// advance together in one mixed graph (build_mixed_graph).  eps0 / eps_out /
+// iter_rec / host_steps (epfft_iterate, the mixed-precision solve) take one
+// batch only.
 int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_path* paths,
                epfft_record* const* records, const epfft_fields* fields, const void* const* eps0,
                void* const* eps_out, epfft_record* iter_rec, int64_t host_steps = 0) {
   if (!c || n < 1 || !probs || !paths) return EPFFT_ERR_ARG;
+  std::vector<std::pair<int, int>> keys;      // (L, precision) of each batch, in order of first appearance
+  std::vector<std::vector<int>> members;      // problem indices of each batch
+  std::vector<int> where(n), slot(n);         // batch and position within it of each problem
   for (int i = 0; i < n; i++) {
     int rc = check_problem(&probs[i]);
     if (rc) return rc;
-    if (probs[i].L != probs[0].L || probs[i].precision != probs[0].precision) return EPFFT_ERR_ARG;
     if (paths[i].n_inc < 1 || !paths[i].E) return EPFFT_ERR_ARG;
     for (int k = 0; k < 4 * paths[i].n_inc; k++)
       if (!std::isfinite(paths[i].E[k])) return EPFFT_ERR_ARG;
     if (records && !records[i]) return EPFFT_ERR_ARG;
+    const auto key = std::make_pair((int)probs[i].L, (int)probs[i].precision);
+    int g = 0;
+    while (g < (int)keys.size() && keys[g] != key) g++;
+    if (g == (int)keys.size()) {
+      keys.push_back(key);
+      members.emplace_back();
+    }
+    where[i] = g;
+    slot[i] = (int)members[g].size();
+    members[g].push_back(i);
   }
+  const int G = (int)keys.size();
+  if (G > 1 && (eps0 || eps_out || iter_rec || host_steps > 0)) return EPFFT_ERR_ARG;
   if (cudaSetDevice(c->device) != cudaSuccess) return EPFFT_ERR_CUDA;
   Arena A(c);
-  Batch B;
-  int rc = setup_batch(c, A, B, n, probs, paths, eps0);
-  if (rc) return rc;
+  std::vector<Batch> Bs(G);
+  std::vector<Batch*> Bp(G);
+  for (int g = 0; g < G; g++) {
+    std::vector<epfft_problem> pg;
+    std::vector<epfft_path> qg;
+    for (int i : members[g]) {
+      pg.push_back(probs[i]);
+      qg.push_back(paths[i]);
+    }
+    int rc = setup_batch(c, A, Bs[g], (int)pg.size(), pg.data(), qg.data(), eps0);
+    if (rc) return rc;
+    Bp[g] = &Bs[g];
+  }
   const char* chk = getenv("EPFFT_SYNC_CHECK");
-  if (chk && chk[0] == '1') rc = run_checked(c, B);
-  else if (host_steps > 0) rc = run_host_loop(c, B, host_steps);
-  else rc = run_graph(c, B);
+  int rc = EPFFT_OK;
+  if (chk && chk[0] == '1') {
+    for (int g = 0; g < G && !rc; g++) rc = run_checked(c, Bs[g]);
+  } else if (host_steps > 0) {
+    rc = run_host_loop(c, Bs[0], host_steps);
+  } else if (G == 1) {
+    rc = run_graph(c, Bs[0]);
+  } else {
+    rc = run_mixed_graph(c, A, Bp);
+  }
   if (rc) return rc;
-  // read back the solve states and records
-  CK(cudaMemcpyAsync(B.h_solves.data(), B.d_solves, sizeof(Solve) * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
-  BatchCtl bc;
-  CK(cudaMemcpyAsync(&bc, B.d_ctl, sizeof(bc), cudaMemcpyDeviceToHost, c->stream));
-  std::vector<std::vector<Record>> recs(n);
-  for (int i = 0; i < n; i++) {
-    recs[i].resize(B.n_inc[i]);
-    // rec pointer is constant; copy after the state read (same stream order)
+  // read back the solve states, the control blocks and the records
+  std::vector<BatchCtl> bc(G);
+  for (int g = 0; g < G; g++) {
+    CK(cudaMemcpyAsync(Bs[g].h_solves.data(), Bs[g].d_solves, sizeof(Solve) * (size_t)Bs[g].nb,
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&bc[g], Bs[g].d_ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, c->stream));
   }
   CK(cudaStreamSynchronize(c->stream));
-  for (int i = 0; i < n; i++)
-    CK(cudaMemcpyAsync(recs[i].data(), B.h_solves[i].rec, sizeof(Record) * (size_t)B.n_inc[i],
-                       cudaMemcpyDeviceToHost, c->stream));
+  std::vector<std::vector<std::vector<Record>>> recs(G);
+  for (int g = 0; g < G; g++) {
+    recs[g].resize(Bs[g].nb);
+    for (int j = 0; j < Bs[g].nb; j++) {
+      recs[g][j].resize(Bs[g].n_inc[j]);
+      CK(cudaMemcpyAsync(recs[g][j].data(), Bs[g].h_solves[j].rec, sizeof(Record) * (size_t)Bs[g].n_inc[j],
+                         cudaMemcpyDeviceToHost, c->stream));
+    }
+  }
   CK(cudaStreamSynchronize(c->stream));
   {
     CheckRec cr;
@@ -586,38 +739,48 @@ int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_
     }
   }
   {
-    int64_t its = 0;
-    for (int i = 0; i < n; i++) its += B.h_solves[i].total_iters;
-    c->last.loop_steps = bc.body_iters;
-    // per step a column and a row pass; per solve the mask kernel (when
-    // generated) and the four labelling kernels
-    int64_t k = 2 * bc.body_iters;
+    int64_t its = 0, steps = 0, k = 0;
+    for (int g = 0; g < G; g++) {
+      for (int j = 0; j < Bs[g].nb; j++) its += Bs[g].h_solves[j].total_iters;
+      steps = std::max<int64_t>(steps, bc[g].body_iters);
+      // per step a column and a row pass of every batch
+      k += 2 * bc[g].body_iters;
+    }
+    if (G > 1) k += steps;  // the loop-condition kernel of the mixed graph
+    // per solve the mask kernel (when generated) and the four labelling kernels
     for (int i = 0; i < n; i++) k += (probs[i].mask ? 0 : 1) + 4;
+    c->last.loop_steps = steps;
     c->last.kernel_launches = k;
     c->last.iterations = its;
   }
-  if (bc.timed_out) return EPFFT_ERR_DEVICE_TIMEOUT;
+  for (int g = 0; g < G; g++)
+    if (bc[g].timed_out) return EPFFT_ERR_DEVICE_TIMEOUT;
   bool keep_labels = false;
   if (fields)
     for (int i = 0; i < n; i++) keep_labels |= fields[i].labels != nullptr;
-  rc = label_batch(c, A, B, recs, keep_labels);
-  if (rc) return rc;
+  for (int g = 0; g < G; g++) {
+    rc = label_batch(c, A, Bs[g], recs[g], keep_labels);
+    if (rc) return rc;
+  }
   int status = EPFFT_OK;
   for (int i = 0; i < n; i++) {
-    const Solve& S = B.h_solves[i];
+    Batch& B = Bs[where[i]];
+    const int j = slot[i];
+    const std::vector<Record>& R = recs[where[i]][j];
+    const Solve& S = B.h_solves[j];
     if (S.phase != PH_DONE && S.status == 0) return EPFFT_ERR_DEVICE_TIMEOUT;
-    if (records) std::memcpy(records[i], recs[i].data(), sizeof(Record) * (size_t)B.n_inc[i]);
+    if (records) std::memcpy(records[i], R.data(), sizeof(Record) * (size_t)B.n_inc[j]);
     if (fields) {
-      rc = copy_out(c, B, B.h_solves[i], i, &fields[i]);
+      rc = copy_out(c, B, B.h_solves[j], j, &fields[i]);
       if (rc) return rc;
     }
     if (eps_out && eps_out[i])
       CK(cudaMemcpyAsync(eps_out[i], S.eps[S.cur], 4 * (size_t)B.L * B.L * real_size(B.prec),
                          cudaMemcpyDeviceToDevice, c->stream));
-    if (iter_rec) std::memcpy(&iter_rec[i], &recs[i][B.n_inc[i] - 1], sizeof(Record));
-    for (int k = 0; k < B.n_inc[i]; k++) {
-      if (recs[i][k].status == 2) status = EPFFT_ERR_NUMERIC;
-      else if (recs[i][k].status == 1 && status == EPFFT_OK) status = EPFFT_NOT_CONVERGED;
+    if (iter_rec) std::memcpy(&iter_rec[i], &R[B.n_inc[j] - 1], sizeof(Record));
+    for (int k = 0; k < B.n_inc[j]; k++) {
+      if (R[k].status == 2) status = EPFFT_ERR_NUMERIC;
+      else if (R[k].status == 1 && status == EPFFT_OK) status = EPFFT_NOT_CONVERGED;
     }
   }
   CK(cudaStreamSynchronize(c->stream));
@@ -694,10 +857,6 @@ struct ServeClass {
   int L = 0, prec = 0, cap = 0;
   Batch B;  // L, prec, nb = cap, shape, tables, device slot table and control
   std::vector<ServeSlot> slots;
-  cudaStream_t stream = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  bool launched = false;
 };
 
 struct Ticket {
@@ -725,6 +884,14 @@ struct Server {
   std::map<int64_t, Ticket> tickets;
   // (L, 2 * precision + general) -> class
   std::map<std::pair<int, int>, ServeClass*> classes;
+  // one mixed graph over every class (build_mixed_graph), rebuilt when a
+  // class is added; dctl: device array of the classes' control blocks
+  std::vector<ServeClass*> order;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  BatchCtl** dctl = nullptr;
+  size_t dctl_bytes = 0;
+  bool dirty = true;
 };
 
 double now_s() {
@@ -732,16 +899,46 @@ double now_s() {
 }
 
 void free_class(epfft_ctx* c, ServeClass* k) {
-  if (k->stream) cudaStreamSynchronize(k->stream);
+  cudaStreamSynchronize(c->stream);
   for (auto& sl : k->slots)
     for (auto& b : sl.blocks) dev_free(c, b.first, b.second);
   if (k->B.d_solves) dev_free(c, k->B.d_solves, sizeof(Solve) * (size_t)k->cap);
   if (k->B.d_ctl) dev_free(c, k->B.d_ctl, sizeof(BatchCtl));
-  if (k->exec) cudaGraphExecDestroy(k->exec);
-  if (k->graph) cudaGraphDestroy(k->graph);
   cudaStreamSynchronize(c->stream);
-  if (k->stream) cudaStreamDestroy(k->stream);
   delete k;
+}
+
+void free_mixed(epfft_ctx* c, Server& S) {
+  cudaStreamSynchronize(c->stream);
+  if (S.exec) cudaGraphExecDestroy(S.exec);
+  if (S.graph) cudaGraphDestroy(S.graph);
+  if (S.dctl) dev_free(c, S.dctl, S.dctl_bytes);
+  S.exec = nullptr;
+  S.graph = nullptr;
+  S.dctl = nullptr;
+  S.dctl_bytes = 0;
+  cudaStreamSynchronize(c->stream);
+}
+
+// (Re)builds the mixed graph over every class of the server.
+int build_serve_graph(epfft_ctx* c, Server& S) {
+  free_mixed(c, S);
+  S.order.clear();
+  std::vector<Batch*> Bp;
+  std::vector<BatchCtl*> h;
+  for (auto& kv : S.classes) {
+    S.order.push_back(kv.second);
+    Bp.push_back(&kv.second->B);
+    h.push_back(kv.second->B.d_ctl);
+  }
+  S.dctl_bytes = sizeof(BatchCtl*) * h.size();
+  S.dctl = (BatchCtl**)dev_alloc(c, S.dctl_bytes);
+  if (!S.dctl) return EPFFT_ERR_OOM;
+  CK(cudaMemcpyAsync(S.dctl, h.data(), S.dctl_bytes, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  int rc = build_mixed_graph(c, Bp, S.dctl, &S.graph, &S.exec);
+  if (!rc) S.dirty = false;
+  return rc;
 }
 
 int get_class(epfft_ctx* c, Server& S, int L, int prec, int general, ServeClass** out) {
@@ -765,7 +962,6 @@ int get_class(epfft_ctx* c, Server& S, int L, int prec, int general, ServeClass*
   int rc = shape(L, prec, B.var, &B.sh);
   if (!rc) rc = get_tables(c, L, prec, &B.tw, &B.ktab);
   if (!rc) rc = ensure_prepared(c, L, prec, B.var);
-  if (!rc && cudaStreamCreateWithFlags(&k->stream, cudaStreamNonBlocking) != cudaSuccess) rc = EPFFT_ERR_CUDA;
   if (!rc) {
     B.d_solves = (Solve*)dev_alloc(c, sizeof(Solve) * (size_t)S.cap);
     B.d_ctl = (BatchCtl*)dev_alloc(c, sizeof(BatchCtl));
@@ -783,12 +979,12 @@ int get_class(epfft_ctx* c, Server& S, int L, int prec, int general, ServeClass*
         cudaStreamSynchronize(c->stream) != cudaSuccess)
       rc = EPFFT_ERR_CUDA;
   }
-  if (!rc) rc = build_loop_graph(c, B, &k->graph, &k->exec);
   if (rc) {
     free_class(c, k);
     return rc;
   }
   S.classes[key] = k;
+  S.dirty = true;  // the mixed graph covers every class
   *out = k;
   return EPFFT_OK;
 }
@@ -829,7 +1025,7 @@ int serve_admit(epfft_ctx* c, Server& S) {
           if (q) sl.blocks.push_back({q, b});
           return q;
         },
-        k->B.sh, k->L, k->prec, p, t.path.data(), (int)(t.path.size() / 4), nullptr, k->stream, hs);
+        k->B.sh, k->L, k->prec, p, t.path.data(), (int)(t.path.size() / 4), nullptr, c->stream, hs);
     if (rc) {
       for (auto& b : sl.blocks) dev_free(c, b.first, b.second);
       sl.blocks.clear();
@@ -838,7 +1034,7 @@ int serve_admit(epfft_ctx* c, Server& S) {
     k->B.h_solves[slot] = hs;
     k->B.n_inc[slot] = (int)(t.path.size() / 4);
     CK(cudaMemcpyAsync(k->B.d_solves + slot, &k->B.h_solves[slot], sizeof(Solve), cudaMemcpyHostToDevice,
-                       k->stream));
+                       c->stream));
     sl.used = true;
     sl.ticket = *qi;
     sl.bytes = t.bytes;
@@ -853,8 +1049,8 @@ int serve_admit(epfft_ctx* c, Server& S) {
 int serve_harvest(epfft_ctx* c, Server& S, ServeClass* k) {
   Batch& B = k->B;
   std::vector<Solve> hs(k->cap);
-  CK(cudaMemcpyAsync(hs.data(), B.d_solves, sizeof(Solve) * (size_t)k->cap, cudaMemcpyDeviceToHost, k->stream));
-  CK(cudaStreamSynchronize(k->stream));
+  CK(cudaMemcpyAsync(hs.data(), B.d_solves, sizeof(Solve) * (size_t)k->cap, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   const size_t LL = (size_t)k->L * k->L, rs = real_size(k->prec);
   for (int i = 0; i < k->cap; i++) {
     ServeSlot& sl = k->slots[i];
@@ -862,32 +1058,32 @@ int serve_harvest(epfft_ctx* c, Server& S, ServeClass* k) {
     Ticket& t = S.tickets[sl.ticket];
     const int n = B.n_inc[i];
     t.rec.resize(n);
-    CK(cudaMemcpyAsync(t.rec.data(), hs[i].rec, sizeof(Record) * (size_t)n, cudaMemcpyDeviceToHost, k->stream));
+    CK(cudaMemcpyAsync(t.rec.data(), hs[i].rec, sizeof(Record) * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
     if (t.want & EPFFT_WANT_EPS) {
       t.eps.resize(4 * LL * rs);
-      CK(cudaMemcpyAsync(t.eps.data(), hs[i].eps[hs[i].cur], 4 * LL * rs, cudaMemcpyDeviceToHost, k->stream));
+      CK(cudaMemcpyAsync(t.eps.data(), hs[i].eps[hs[i].cur], 4 * LL * rs, cudaMemcpyDeviceToHost, c->stream));
     }
     if (t.want & EPFFT_WANT_SIG) {  // sigma of the accepted iterate (the resident multiplier)
       t.sig.resize(4 * LL * rs);
-      CK(cudaMemcpyAsync(t.sig.data(), hs[i].sig[hs[i].cur], 4 * LL * rs, cudaMemcpyDeviceToHost, k->stream));
+      CK(cudaMemcpyAsync(t.sig.data(), hs[i].sig[hs[i].cur], 4 * LL * rs, cudaMemcpyDeviceToHost, c->stream));
     }
     if (t.want & EPFFT_WANT_PLASTIC) {
       t.flags.resize(LL * (size_t)n);
-      CK(cudaMemcpyAsync(t.flags.data(), hs[i].flags, LL * (size_t)n, cudaMemcpyDeviceToHost, k->stream));
+      CK(cudaMemcpyAsync(t.flags.data(), hs[i].flags, LL * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
     }
     // clusters of every accepted increment
     int32_t* lab = (int32_t*)dev_alloc(c, sizeof(int32_t) * LL * (size_t)n);
     int32_t* cnt = (int32_t*)dev_alloc(c, sizeof(int32_t) * ((size_t)n + 1));
     if (!lab || !cnt) return EPFFT_ERR_OOM;
-    CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ((size_t)n + 1), k->stream));
-    CK(launch_label(hs[i].flags, lab, n, k->L, 1, cnt, cnt + n, k->stream));
+    CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ((size_t)n + 1), c->stream));
+    CK(launch_label(hs[i].flags, lab, n, k->L, 1, cnt, cnt + n, c->stream));
     std::vector<int32_t> hc(n + 1);
-    CK(cudaMemcpyAsync(hc.data(), cnt, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost, k->stream));
+    CK(cudaMemcpyAsync(hc.data(), cnt, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost, c->stream));
     if (t.want & EPFFT_WANT_LABELS) {
       t.labels.resize(LL * (size_t)n);
-      CK(cudaMemcpyAsync(t.labels.data(), lab, sizeof(int32_t) * LL * (size_t)n, cudaMemcpyDeviceToHost, k->stream));
+      CK(cudaMemcpyAsync(t.labels.data(), lab, sizeof(int32_t) * LL * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
     }
-    CK(cudaStreamSynchronize(k->stream));
+    CK(cudaStreamSynchronize(c->stream));
     dev_free(c, lab, sizeof(int32_t) * LL * (size_t)n);
     dev_free(c, cnt, sizeof(int32_t) * ((size_t)n + 1));
     int st = EPFFT_OK;
@@ -909,9 +1105,9 @@ int serve_harvest(epfft_ctx* c, Server& S, ServeClass* k) {
     // the slot is empty again (DONE state, zero pointers)
     std::memset(&B.h_solves[i], 0, sizeof(Solve));
     B.h_solves[i].phase = PH_DONE;
-    CK(cudaMemcpyAsync(B.d_solves + i, &B.h_solves[i], sizeof(Solve), cudaMemcpyHostToDevice, k->stream));
+    CK(cudaMemcpyAsync(B.d_solves + i, &B.h_solves[i], sizeof(Solve), cudaMemcpyHostToDevice, c->stream));
   }
-  CK(cudaStreamSynchronize(k->stream));
+  CK(cudaStreamSynchronize(c->stream));
   return EPFFT_OK;
 }
 
@@ -974,6 +1170,7 @@ void epfft_destroy(epfft_ctx* c) {
   for (auto& t : c->tables) dev_free(c, t.second.dev, t.second.bytes);
   cudaStreamSynchronize(c->stream);
   cudaStreamDestroy(c->cap);
+  for (cudaStream_t a : c->aux) cudaStreamDestroy(a);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -1580,6 +1777,7 @@ int epfft_serve_open(epfft_ctx* ctx, const epfft_serve_options* opt) {
 int epfft_serve_close(epfft_ctx* ctx) {
   if (!ctx || !ctx->server) return EPFFT_ERR_ARG;
   cudaSetDevice(ctx->device);
+  free_mixed(ctx, *ctx->server);
   for (auto& kv : ctx->server->classes) free_class(ctx, kv.second);
   delete ctx->server;
   ctx->server = nullptr;
@@ -1631,26 +1829,38 @@ int epfft_serve_step(epfft_ctx* ctx, int32_t* n_running, int32_t* n_queued) {
   ctx->last = epfft_stats{};
   int rc = serve_admit(ctx, S);
   if (rc) return rc;
+  // every class with live slots advances at most S.steps loop steps, all
+  // classes in one launch of the mixed graph
   std::vector<ServeClass*> live;
   for (auto& kv : S.classes) {
-    ServeClass* k = kv.second;
     int used = 0;
-    for (auto& sl : k->slots) used += sl.used;
-    if (!used) continue;
-    BatchCtl bc;
-    std::memset(&bc, 0, sizeof(bc));
-    bc.active = used;
-    bc.max_body_iters = S.steps;
-    CK(cudaMemcpyAsync(k->B.d_ctl, &bc, sizeof(bc), cudaMemcpyHostToDevice, k->stream));
-    CK(cudaGraphLaunch(k->exec, k->stream));
-    live.push_back(k);
+    for (auto& sl : kv.second->slots) used += sl.used;
+    if (used) live.push_back(kv.second);
   }
-  for (ServeClass* k : live) {
-    CK(cudaStreamSynchronize(k->stream));
-    BatchCtl bc;
-    CK(cudaMemcpy(&bc, k->B.d_ctl, sizeof(bc), cudaMemcpyDeviceToHost));
-    ctx->last.loop_steps += bc.body_iters;
-    ctx->last.kernel_launches += 2 * bc.body_iters;  // a column and a row pass per step
+  if (!live.empty()) {
+    if (S.dirty || !S.exec) {
+      rc = build_serve_graph(ctx, S);
+      if (rc) return rc;
+    }
+    std::vector<BatchCtl> bcs(S.order.size());
+    for (size_t i = 0; i < S.order.size(); i++) {
+      ServeClass* k = S.order[i];
+      int used = 0;
+      for (auto& sl : k->slots) used += sl.used;
+      std::memset(&bcs[i], 0, sizeof(BatchCtl));
+      bcs[i].active = used;
+      bcs[i].max_body_iters = S.steps;
+      CK(cudaMemcpyAsync(k->B.d_ctl, &bcs[i], sizeof(BatchCtl), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    CK(cudaGraphLaunch(S.exec, ctx->stream));
+    for (size_t i = 0; i < S.order.size(); i++)
+      CK(cudaMemcpyAsync(&bcs[i], S.order[i]->B.d_ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    int64_t steps = 0;
+    for (size_t i = 0; i < S.order.size(); i++) steps = std::max<int64_t>(steps, bcs[i].body_iters);
+    ctx->last.loop_steps = steps;
+    // a column and a row pass of every class, and the loop-condition kernel, per step
+    ctx->last.kernel_launches += (2 * (int64_t)S.order.size() + 1) * steps;
   }
   {
     CheckRec cr;

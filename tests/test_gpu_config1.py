@@ -8,7 +8,14 @@ increments), the macroscopic stress agrees to 1e-10 relative; an increment
 whose eta1 crosses 1e-8 within rounding of the threshold may stop one or two
 iterations apart, and then its stress agrees to 1e-9 (one iteration changes
 <sigma> by eta2 ~ 1e-11).  Plastic-pixel and cluster counts agree up to
-pixels on the yield surface."""
+pixels on the yield surface.
+
+Fields (tests/golden/config1_fields.npz, same script): the final local strain
+of the whole path (its last increment stops at the cap on both sides, at the
+same iterate) within 1e-10 relative L2, and for every increment k that
+converges, the final strain of the solve of the first k increments within
+1e-10 when both sides stop at the same iterate (1e-8 when the stopping test
+crossed its threshold an iteration or two apart)."""
 import json
 import os
 
@@ -28,8 +35,19 @@ def test_config1_macro_curve_matches_oracle():
     P = inputs.config1()
     prob = B.Problem(L=P.L, precision="fp64", void_fraction=P.f, seed=P.seed, tol_eq=1e-8, tol_macro=1e-8,
                      max_iter=g["problem"]["max_iter"])
+    fg = np.load(os.path.join(os.path.dirname(__file__), "golden", "config1_fields.npz"))
     with B.Context(0) as ctx:
-        rc, rec = B.epfft_solve(ctx, prob, P.path)
+        rc, rec, f = B.epfft_solve(ctx, prob, P.path, fields=True)
+        ferr = np.linalg.norm(f.eps - fg["final"]) / np.linalg.norm(fg["final"])
+        assert rec["iterations"][-1] == g["records"][-1]["iterations"] and ferr < 1e-10, ferr
+        for key in fg.files:
+            if not key.startswith("after_"):
+                continue
+            k = int(key.split("_")[1])
+            rk, reck, fk = B.epfft_solve(ctx, prob, P.path[:k], fields=True)
+            e = np.linalg.norm(fk.eps - fg[key]) / np.linalg.norm(fg[key])
+            same = int(reck["iterations"][-1]) == g["records"][k - 1]["iterations"]
+            assert reck["status"][-1] == 0 and e < (1e-10 if same else 1e-8), (k, same, e)
     ref = g["records"]
     assert len(rec) == len(ref) == 20
     worst = 0.0
