@@ -358,7 +358,28 @@ def peaks(B, ctx, precision):
                          f"({r['ms']:.3f} ms per launch) (of measured)")
 
 
-def roofline(precision, L, nb, col_ms, row_ms, peak, peak_source):
+def pass_kernels(precision, L, tiling):
+    """Names of the two compiled passes a solve of this size runs."""
+    rt = "float" if precision == "fp32" else "double"
+    if precision == "fp32" and tiling == 2:
+        return {"row": f"row_pass_rs<{L}>", "col": f"col_pass_rs<{L}> (digit-reversed rows)"}
+    col = f"col_pass_rs<{L}>" if (precision == "fp32" and tiling == 0 and L >= 128) else f"col_pass<{rt},{L},{tiling}>"
+    return {"row": f"row_pass<{rt},{L},{tiling}>", "col": col}
+
+
+# DRAM bytes (read + write) per launch from ncu launch lists of the same
+# kernels at the same launch shape: (precision, L, solves, tiling, pass) ->
+# (bytes, summary under profiles/).  Kernels that changed since their capture
+# are left out, so their traffic reads null.
+TRAFFIC = {
+    ("fp32", 512, 64, 0, "row"): (1167.2e6, "profiles/passes_fp32_c3_c4_launches.md"),
+    ("fp32", 512, 64, 0, "col"): (346.8e6, "profiles/passes_fp32_c3_c4_launches.md"),
+    ("fp32", 4096, 1, 2, "row"): (1246.8e6, "profiles/passes_fp32_c3_c4_launches.md"),
+    ("fp32", 4096, 1, 2, "col"): (358.3e6, "profiles/passes_fp32_c3_c4_launches.md"),
+}
+
+
+def roofline(precision, L, nb, col_ms, row_ms, peak, peak_source, tiling=None):
     """Both fused passes against their roof, from this run's CUDA-event pass
     timings; the dominant (longer) pass is the line's `roofline`.
     FP32 (HBM): algorithmic bytes per pixel, row pass 73 (spectrum read and
@@ -376,17 +397,20 @@ def roofline(precision, L, nb, col_ms, row_ms, peak, peak_source):
         work = {"row": (15 * lg + 60) * n, "col": (15 * lg + 25) * n}
         unit, scale, bound = "TFLOP/s", 1e12, "alu"
     ms = {"row": row_ms, "col": col_ms}
-    rt = "float" if precision == "fp32" else "double"
+    names = pass_kernels(precision, L, tiling)
     passes = {}
     for k in ("row", "col"):
         a = work[k] / (ms[k] * 1e-3) / scale
-        passes[k] = {"kernel": f"{k}_pass<{rt},{L}>", "ms": ms[k], "achieved": a, "frac": a / peak,
-                     "work_per_launch": work[k]}
+        tr = TRAFFIC.get((precision, L, nb, tiling, k))
+        passes[k] = {"kernel": names[k], "ms": ms[k], "achieved": a, "frac": a / peak,
+                     "work_per_launch": work[k], "traffic": tr[0] if tr else None}
     dom = "row" if row_ms >= col_ms else "col"
     d = passes[dom]
+    tr = TRAFFIC.get((precision, L, nb, tiling, dom))
+    note = (f"DRAM read + write per launch from the ncu launch list in {tr[1]} (same kernel and launch shape)"
+            if tr else "null: no ncu capture of this kernel at this launch shape")
     return {"bound": bound, "kernel": d["kernel"], "achieved": d["achieved"], "peak": peak, "unit": unit,
-            "frac": d["frac"], "traffic": None,
-            "traffic_note": "null: DRAM bytes come from ncu captures (profiles/), never from a timed run",
+            "frac": d["frac"], "traffic": tr[0] if tr else None, "traffic_note": note,
             "peak_source": peak_source, "passes": passes,
             "timing": "epfft_time_passes: CUDA events around each launch on the context stream, mean of the "
                       "timed launches, the same launch shape as the solve"}
@@ -461,7 +485,7 @@ def solve_line(B, ctx, stream, flush, torch, name, precision, cap, steps, warmup
     return {
         "value": job_value(ws, pix_its, dev_s), "ms_per_step": 1e3 * t_step, "config": cfg,
         "convergence": conv,
-        "roofline": roofline(precision, L, nb, col_ms, row_ms, peak, peak_source),
+        "roofline": roofline(precision, L, nb, col_ms, row_ms, peak, peak_source, tiling),
         "e2e": {"value": job_value(ws, e2e_its, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
         "gpu_launches": launches, "clocks": clocks, "wall_s": wall, "recs": recs, "probs": probs,

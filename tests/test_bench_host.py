@@ -89,13 +89,20 @@ def test_roofline_uses_the_algorithmic_work_of_each_pass():
     the mean launch time, against the HBM peak; FP64: 15 log2 L + 60 and
     15 log2 L + 25 flops per pixel against the FP64 peak; the dominant pass
     is the longer one."""
-    r = bench.roofline("fp32", 512, 64, 0.184, 0.337, 6770.0, "measured")
+    r = bench.roofline("fp32", 512, 64, 0.184, 0.337, 6770.0, "measured", 0)
     n = 512 * 512 * 64
-    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["kernel"] == "row_pass<float,512>"
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["kernel"] == "row_pass<float,512,0>"
+    assert r["passes"]["col"]["kernel"] == "col_pass_rs<512>"
     assert abs(r["achieved"] - 73 * n / 0.337e-3 / 1e9) < 1e-6
     assert abs(r["passes"]["col"]["achieved"] - 24 * n / 0.184e-3 / 1e9) < 1e-6
-    assert abs(r["frac"] - r["achieved"] / 6770.0) < 1e-12 and r["traffic"] is None
-    r = bench.roofline("fp64", 256, 1, 0.040, 0.030, 1.25, "measured")
-    assert r["bound"] == "alu" and r["kernel"] == "col_pass<double,256>"
+    assert abs(r["frac"] - r["achieved"] / 6770.0) < 1e-12
+    # traffic only where an ncu capture of that kernel at that launch shape exists
+    assert r["traffic"] == bench.TRAFFIC[("fp32", 512, 64, 0, "row")][0]
+    assert bench.roofline("fp32", 512, 64, 0.184, 0.337, 6770.0, "measured", 1)["traffic"] is None
+    assert bench.roofline("fp32", 512, 16, 0.184, 0.337, 6770.0, "measured", 0)["traffic"] is None
+    r4 = bench.roofline("fp32", 4096, 1, 0.15, 0.47, 6770.0, "measured", 2)
+    assert r4["kernel"] == "row_pass_rs<4096>" and r4["traffic"] is not None
+    r = bench.roofline("fp64", 256, 1, 0.040, 0.030, 1.25, "measured", 1)
+    assert r["bound"] == "alu" and r["kernel"] == "col_pass<double,256,1>" and r["traffic"] is None
     assert abs(r["achieved"] - (15 * 8 + 25) * 65536 / 0.040e-3 / 1e12) < 1e-12
     assert abs(r["passes"]["row"]["achieved"] - (15 * 8 + 60) * 65536 / 0.030e-3 / 1e12) < 1e-12

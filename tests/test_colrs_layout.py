@@ -407,3 +407,60 @@ def test_row_pass_banks(L):
             rr, w = divmod(within, W)
             addrs.append(row_base(L, rr) + c * M + sw(b * W + w))
         assert wavefronts(addrs) == 2, (L, w0, wavefronts(addrs))
+
+
+@pytest.mark.parametrize("W", [1, 2])
+@pytest.mark.parametrize("L", SIZES)
+def test_column_pass_addresses_stay_inside_their_buffers(L, W):
+    """Every shared-memory element a column-pass CTA touches (three
+    components of each of its column groups, every stage's positions) lies
+    inside its allocation of CPC (3 L + 8) elements, and every spectrum
+    element it reads or writes, over the whole grid of L/2 / CPC CTAs, lies
+    inside the 3 L (L/2) numbers of the solve's spectrum."""
+    radix, nlen, stride = plan(L)
+    T, M = L // E, L // 2
+    cpc, nt, inter = cfg(L, W)
+    smem = cpc * (3 * L + 8)
+    top_s = -1
+    for tid in range(nt):
+        g, t = lane_map(L, W, tid)
+        assert 0 <= g < cpc and 0 <= t < T
+        for s in range(len(radix)):
+            for base, d, j in butterflies(L, s, t):
+                for r in range(radix[s]):
+                    p = base + r * d
+                    assert 0 <= p < L
+                    top_s = max(top_s, seq_base(L, g) + 2 * L + sw(p))
+    assert top_s < smem, (top_s, smem)
+    nbk = M // W
+    top_g = -1
+    for bx in range(M // cpc):
+        for g in range(cpc):
+            p1 = bx * cpc + g
+            bt, w = divmod(p1, W)
+            # component 2, x2 = L - 1: the largest element of the column
+            top_g = max(top_g, ((2 * nbk + bt) * L + L - 1) * W + w)
+    assert top_g == 3 * L * M - 1
+
+
+@pytest.mark.parametrize("L", ROW_SIZES)
+def test_row_pass_addresses_stay_inside_their_buffers(L):
+    """The register-staged row pass: shared-memory elements of its RR rows
+    (three components of M positions each, per-row bank offset) stay inside
+    RR (3 M + 16) elements, and the transposing load / store of the tile,
+    over the whole grid of L / RR CTAs, stays inside the spectrum."""
+    M, T, RR, W, RS = row_cfg(L)
+    assert all(row_base(L, rr) - rr * RS < 16 for rr in range(RR))
+    top_s = max(row_base(L, rr) + 2 * M + sw(q) for rr in range(RR) for q in range(M))
+    assert top_s < RR * RS, (top_s, RR * RS)
+    nbk = M // W
+    top_g = -1
+    for bx in range(L // RR):
+        r0 = bx * RR
+        e = 3 * M * RR - 1  # the largest tile element of the CTA
+        chunk, within = divmod(e, RR * W)
+        c, b = divmod(chunk, nbk)
+        rr, w = divmod(within, W)
+        assert c < 3 and b < nbk and rr < RR
+        top_g = max(top_g, ((c * nbk + b) * L + r0 + rr) * W + w)
+    assert top_g == 3 * L * M - 1
