@@ -369,14 +369,36 @@ def pass_kernels(precision, L, tiling):
 
 # DRAM bytes (read + write) per launch from ncu launch lists of the same
 # kernels at the same launch shape: (precision, L, solves, tiling, pass) ->
-# (bytes, summary under profiles/).  Kernels that changed since their capture
-# are left out, so their traffic reads null.
+# (bytes, summary under profiles/).  TRAFFIC_SRC is the digest of the kernel
+# sources the captures ran (kernel_source_digest); once the sources differ,
+# every traffic figure reads null until the captures are taken again.
+TRAFFIC_SRC = "e87e5ea75bf387b7"
 TRAFFIC = {
     ("fp32", 512, 64, 0, "row"): (1167.2e6, "profiles/passes_fp32_c3_c4_launches.md"),
     ("fp32", 512, 64, 0, "col"): (346.8e6, "profiles/passes_fp32_c3_c4_launches.md"),
     ("fp32", 4096, 1, 2, "row"): (1246.8e6, "profiles/passes_fp32_c3_c4_launches.md"),
     ("fp32", 4096, 1, 2, "col"): (358.3e6, "profiles/passes_fp32_c3_c4_launches.md"),
 }
+
+
+def kernel_source_digest():
+    """sha256 (first 16 hex digits) over the names and bytes of the CUDA
+    sources of the library, in name order."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_0802_2488_gb300", "csrc", "*"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(os.path.basename(f).encode())
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_of(precision, L, nb, tiling, k):
+    if kernel_source_digest() != TRAFFIC_SRC:
+        return None
+    return TRAFFIC.get((precision, L, nb, tiling, k))
 
 
 def roofline(precision, L, nb, col_ms, row_ms, peak, peak_source, tiling=None):
@@ -401,14 +423,19 @@ def roofline(precision, L, nb, col_ms, row_ms, peak, peak_source, tiling=None):
     passes = {}
     for k in ("row", "col"):
         a = work[k] / (ms[k] * 1e-3) / scale
-        tr = TRAFFIC.get((precision, L, nb, tiling, k))
+        tr = traffic_of(precision, L, nb, tiling, k)
         passes[k] = {"kernel": names[k], "ms": ms[k], "achieved": a, "frac": a / peak,
                      "work_per_launch": work[k], "traffic": tr[0] if tr else None}
     dom = "row" if row_ms >= col_ms else "col"
     d = passes[dom]
-    tr = TRAFFIC.get((precision, L, nb, tiling, dom))
-    note = (f"DRAM read + write per launch from the ncu launch list in {tr[1]} (same kernel and launch shape)"
-            if tr else "null: no ncu capture of this kernel at this launch shape")
+    tr = traffic_of(precision, L, nb, tiling, dom)
+    if tr:
+        note = (f"DRAM read + write per launch from the ncu launch list in {tr[1]} (same kernel sources, "
+                f"digest {TRAFFIC_SRC}, and launch shape)")
+    elif kernel_source_digest() != TRAFFIC_SRC:
+        note = "null: the kernel sources changed since the ncu captures"
+    else:
+        note = "null: no ncu capture of this kernel at this launch shape"
     return {"bound": bound, "kernel": d["kernel"], "achieved": d["achieved"], "peak": peak, "unit": unit,
             "frac": d["frac"], "traffic": tr[0] if tr else None, "traffic_note": note,
             "peak_source": peak_source, "passes": passes,

@@ -96,13 +96,24 @@ def test_roofline_uses_the_algorithmic_work_of_each_pass():
     assert abs(r["achieved"] - 73 * n / 0.337e-3 / 1e9) < 1e-6
     assert abs(r["passes"]["col"]["achieved"] - 24 * n / 0.184e-3 / 1e9) < 1e-6
     assert abs(r["frac"] - r["achieved"] / 6770.0) < 1e-12
-    # traffic only where an ncu capture of that kernel at that launch shape exists
-    assert r["traffic"] == bench.TRAFFIC[("fp32", 512, 64, 0, "row")][0]
+    # traffic only where an ncu capture of that kernel at that launch shape
+    # exists, and only while the kernel sources are those it ran
+    if bench.kernel_source_digest() == bench.TRAFFIC_SRC:
+        assert r["traffic"] == bench.TRAFFIC[("fp32", 512, 64, 0, "row")][0]
+    else:
+        assert r["traffic"] is None
     assert bench.roofline("fp32", 512, 64, 0.184, 0.337, 6770.0, "measured", 1)["traffic"] is None
     assert bench.roofline("fp32", 512, 16, 0.184, 0.337, 6770.0, "measured", 0)["traffic"] is None
     r4 = bench.roofline("fp32", 4096, 1, 0.15, 0.47, 6770.0, "measured", 2)
-    assert r4["kernel"] == "row_pass_rs<4096>" and r4["traffic"] is not None
+    assert r4["kernel"] == "row_pass_rs<4096>"
     r = bench.roofline("fp64", 256, 1, 0.040, 0.030, 1.25, "measured", 1)
     assert r["bound"] == "alu" and r["kernel"] == "col_pass<double,256,1>" and r["traffic"] is None
     assert abs(r["achieved"] - (15 * 8 + 25) * 65536 / 0.040e-3 / 1e12) < 1e-12
     assert abs(r["passes"]["row"]["achieved"] - (15 * 8 + 60) * 65536 / 0.030e-3 / 1e12) < 1e-12
+
+
+def test_traffic_reads_null_once_the_kernel_sources_change(monkeypatch):
+    monkeypatch.setattr(bench, "TRAFFIC_SRC", "0" * 16)
+    r = bench.roofline("fp32", 512, 64, 0.184, 0.337, 6770.0, "measured", 0)
+    assert r["traffic"] is None and "changed" in r["traffic_note"]
+    assert all(p["traffic"] is None for p in r["passes"].values())
