@@ -23,8 +23,10 @@ A single-GPU default run adds sub-objects measured in the same process:
        latency and solves/s through submit / serve_step / poll;
   c2   the L = 256 shear lattice in plain FP64 (FP64-ALU roofline against the
        measured FP64 peak), its FP32 form with the field and curve errors
-       against FP64, and plain FP64 against the mixed-precision solve at a
-       tolerance both reach.
+       against FP64, and plain FP64 against the mixed-precision solve and
+       the defect-correction form at a tolerance all reach;
+  batched_at_tol  8 lattices of the batched recipe at tol 1e-8 in one call:
+       plain FP64 against the defect-correction form.
 
 --impl reference times the oracle (the plain FP64 CPU implementation) on
 this machine's host cores on a bounded sample of the same workload.
@@ -293,13 +295,19 @@ def timed_solves(B, ctx, stream, flush, probs, paths, steps, torch):
 def refined_vs_plain(B, ctx, stream, flush, mask, L, path, torch, tol=1e-8, tol_switch=0.0, cap=60000):
     """Solves/s at one equilibrium tolerance that the FP32 path cannot
     certify alone: the plain FP64 solve against the mixed-precision solve
-    (FP32 iterations to tol_switch, then FP64 to tol), on the increments of
-    `path`; one L2-flushed, CUDA-event-timed solve of each after a warm-up."""
+    (FP32 iterations to tol_switch, then FP64 to tol) and against the
+    defect-correction form (FP64 state, FP32 transforms of p - p_ref), on the
+    increments of `path`; one L2-flushed, CUDA-event-timed solve of each
+    after a warm-up."""
+    import dataclasses
     prob = B.Problem(L=L, precision="fp64", mask=mask, tol_eq=tol, tol_macro=tol, max_iter=cap)
     warm = B.Problem(L=L, precision="fp64", mask=mask, tol_eq=tol, tol_macro=tol, max_iter=20)
+    dprob = dataclasses.replace(prob, precision="fp32_defect")
     B.epfft_autotune(ctx, L, "fp32")
+    B.epfft_autotune(ctx, L, "fp32_defect")
     B.epfft_solve(ctx, warm, path[:1])
     B.epfft_solve_refined(ctx, warm, path[:1], tol_switch)
+    B.epfft_solve(ctx, dataclasses.replace(warm, precision="fp32_defect"), path[:1])
 
     def timed(fn):
         with torch.cuda.stream(stream):
@@ -315,6 +323,7 @@ def refined_vs_plain(B, ctx, stream, flush, mask, L, path, torch, tol=1e-8, tol_
 
     t64, (rc64, r64) = timed(lambda: B.epfft_solve(ctx, prob, path))
     tr, (rcr, rr, rr32) = timed(lambda: B.epfft_solve_refined(ctx, prob, path, tol_switch))
+    td, (rcd, rd) = timed(lambda: B.epfft_solve(ctx, dprob, path))
     return {"workload": f"first {len(path)} increments of the same lattice and path, tol {tol:g} (eta1, eta2) "
                         f"certified in FP64, at most {cap} iterations per increment",
             "fp64_plain": {"solves_per_s": 1.0 / t64, "iterations": int(r64["iterations"].sum()),
@@ -326,7 +335,56 @@ def refined_vs_plain(B, ctx, stream, flush, mask, L, path, torch, tol=1e-8, tol_
                                "max_eta1": float(rr["eta1"].max()),
                                "fp32_stage_reached": {"eta1": rr32["eta1"].tolist(), "eta2": rr32["eta2"].tolist(),
                                                       "status": rr32["status"].tolist()}},
-            "speedup": t64 / tr}
+            "fp32_defect": {"solves_per_s": 1.0 / td, "iterations": int(rd["iterations"].sum()),
+                            "converged": bool((rd["status"] == 0).all()), "max_eta1": float(rd["eta1"].max()),
+                            "max_eta2": float(rd["eta2"].max()), "refresh_steps": DEFECT_REFRESH},
+            "speedup": t64 / tr, "speedup_defect": t64 / td}
+
+
+# loop steps between refreshes of the defect form's FP64 reference (the
+# library's default)
+DEFECT_REFRESH = 64
+
+
+def batched_at_tol(B, ctx, stream, flush, torch, tol=1e-8, cap=60000):
+    """The batched forms at one equilibrium tolerance: 8 lattices of the
+    batched workload's recipe (L = 512; f = 0.05 and 0.10, seeds 0, 1
+    equibiaxial to 2x and 8, 9 shear to 3x the void-free yield strain), the
+    first of their 30 increments, tol 1e-8, advanced together in one call:
+    plain FP64 against the defect-correction form.  One L2-flushed,
+    CUDA-event-timed call of each after a warm-up.  The plain FP32 form
+    cannot reach the tolerance (its transforms stall near eta1 ~ 1e-6)."""
+    from paper_0802_2488_gb300 import inputs
+    lat = [(f, s) for f in (0.05, 0.10) for s in (0, 1, 8, 9)]
+    paths = [inputs.load_path("equibiaxial" if s < 8 else "shear", 30, 2.0 if s < 8 else 3.0)[:1] for f, s in lat]
+
+    def probs(prec, it):
+        return [B.Problem(L=512, precision=prec, void_fraction=f, seed=s, tol_eq=tol, tol_macro=tol, max_iter=it)
+                for f, s in lat]
+    out = {"workload": f"{len(lat)} lattices of L=512 (f in {{0.05, 0.10}}, seeds 0, 1 equibiaxial to 2x yield "
+                       f"and 8, 9 shear to 3x yield, first of 30 increments), tol {tol:g} (eta1, eta2), at most "
+                       f"{cap} iterations, one call per form"}
+    for prec in ("fp64", "fp32_defect"):
+        B.epfft_autotune(ctx, 512, prec, n_batch=len(lat))
+        B.epfft_solve_batch(ctx, probs(prec, 20), paths)
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        rc, recs = B.epfft_solve_batch(ctx, probs(prec, cap), paths)
+        with torch.cuda.stream(stream):
+            b.record(stream)
+        stream.synchronize()
+        t = a.elapsed_time(b) / 1e3
+        its = [int(r["iterations"].sum()) for r in recs]
+        conv = all(bool((r["status"] == 0).all()) for r in recs)
+        out[prec] = {"s": t, "solves_per_s": len(lat) / t, "solves_per_s_at_tol": len(lat) / t if conv else None,
+                     "converged": sum(int((r["status"] == 0).all()) for r in recs), "iterations": its,
+                     "pixel_iterations_per_s": 512 * 512 * sum(its) / t,
+                     "max_eta1": max(float(r["eta1"].max()) for r in recs)}
+    out["speedup_defect"] = out["fp64"]["s"] / out["fp32_defect"]["s"]
+    return out
 
 
 def convergence(recs, tol: float = 1e-8) -> dict:
@@ -703,6 +761,7 @@ def main():
         p64, s64 = peaks(B, ctx, "fp64")
         extras["c2"] = fp32_vs_fp64(B, ctx, stream, flush, torch, min(args.steps, 3), 1, local, barrier, p64, s64)
         extras["c2"]["steps"], extras["c2"]["warmup"] = min(args.steps, 3), 1
+        extras["batched_at_tol"] = batched_at_tol(B, ctx, stream, flush, torch)
 
     if rank == 0:
         out = {

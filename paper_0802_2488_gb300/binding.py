@@ -32,6 +32,10 @@ EPFFT_ERR_SCRATCH_LIMIT = -8
 N_TILINGS = 3  # EPFFT_N_TILINGS
 EPFFT_FP64 = 0
 EPFFT_FP32 = 1
+EPFFT_FP32_DEFECT = 2
+# 'fp32_defect': FP64 state with FP32 transforms of the polarization's
+# difference from an FP64-transformed reference (defect correction)
+_PREC = {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32, "fp32_defect": EPFFT_FP32_DEFECT}
 EPFFT_GREEN_EQ3 = 0
 EPFFT_GREEN_CG1 = 1
 EPFFT_GREEN_DG1 = 2
@@ -51,7 +55,7 @@ SYMBOLS = ["epfft_create", "epfft_destroy", "epfft_last_stats", "epfft_strerror"
            "epfft_solve_dg2", "epfft_average5", "epfft_void_plastic", "epfft_indicators",
            "epfft_effective_moduli", "epfft_empirical_curve", "epfft_eps_eq", "epfft_displacement",
            "epfft_ticket_fields", "epfft_release", "epfft_solve_refined", "epfft_solve_refined_batch",
-           "epfft_fp64_peak", "epfft_supported_tiling"]
+           "epfft_fp64_peak", "epfft_supported_tiling", "epfft_set_defect_refresh"]
 
 
 class EpfftError(RuntimeError):
@@ -145,6 +149,7 @@ def lib():
         L.epfft_solve_refined_batch.argtypes = [vp, i32, vp, vp, dbl, vp, vp, vp]
         L.epfft_autotune.argtypes = [vp, i32, i32, i32, C.POINTER(i32), C.POINTER(C.c_float)]
         L.epfft_set_tiling.argtypes = [vp, i32, i32, i32]
+        L.epfft_set_defect_refresh.argtypes = [vp, i32]
         L.epfft_project_static.argtypes = [i32, i32, dbl, dbl, C.POINTER(dbl), vp, vp, vp]
         L.epfft_time_passes.argtypes = [vp, C.POINTER(_Problem), i32, C.POINTER(dbl), i32, C.POINTER(C.c_float),
                                         C.POINTER(C.c_float)]
@@ -174,7 +179,7 @@ def _check(rc: int, what: str, allow=(EPFFT_OK,)) -> int:
 @dataclass
 class Problem:
     L: int
-    precision: str = "fp64"          # 'fp64' | 'fp32'
+    precision: str = "fp64"          # 'fp64' | 'fp32' | 'fp32_defect'
     void_fraction: float = 0.0
     seed: int = 0
     mask: Optional[object] = None    # numpy uint8 (L, L) or torch CUDA uint8 tensor; None: generated
@@ -201,7 +206,7 @@ class Problem:
                 keep = self.mask.contiguous()
                 assert keep.is_cuda and keep.numel() == self.L * self.L
                 mptr, mdev = keep.data_ptr(), 1
-        prec = {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[self.precision]
+        prec = _PREC[self.precision]
         p = _Problem(self.L, prec, float(self.void_fraction), int(self.seed) & (2**64 - 1), mptr, mdev,
                      _GREEN[self.green], self.mu, self.lambda_, self.yield_stress,
                      self.mu if self.mu0 is None else self.mu0,
@@ -211,7 +216,7 @@ class Problem:
 
     @property
     def real_dtype(self):
-        return np.float64 if self.precision == "fp64" else np.float32
+        return np.float32 if self.precision == "fp32" else np.float64
 
 
 def _path(E) -> tuple[_Path, np.ndarray]:
@@ -289,7 +294,7 @@ def epfft_strerror(code: int) -> str:
 
 
 def epfft_supported(L: int, precision: str) -> bool:
-    return bool(lib().epfft_supported(L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision]))
+    return bool(lib().epfft_supported(L, _PREC[precision]))
 
 
 @dataclass
@@ -316,7 +321,7 @@ def pinned_fields(problem: Problem, n_inc: int) -> Fields:
     them run at the link's rate instead of through a staging buffer."""
     import torch
     L = problem.L
-    tdt = torch.float64 if problem.precision == "fp64" else torch.float32
+    tdt = torch.float32 if problem.precision == "fp32" else torch.float64
 
     def arr(shape, dt):
         return torch.empty(shape, dtype=dt, pin_memory=True).numpy()
@@ -454,7 +459,7 @@ def epfft_eps_eq(ctx: Context, L: int, precision: str, eps):
     import torch
     assert eps.is_cuda and eps.is_contiguous() and eps.numel() == 4 * L * L
     out = torch.empty((L, L), dtype=eps.dtype, device=eps.device)
-    _check(lib().epfft_eps_eq(ctx.handle, L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision],
+    _check(lib().epfft_eps_eq(ctx.handle, L, _PREC[precision],
                               eps.data_ptr(), out.data_ptr()), "epfft_eps_eq")
     return out
 
@@ -466,7 +471,7 @@ def epfft_displacement(ctx: Context, L: int, precision: str, eps):
     assert eps.is_cuda and eps.is_contiguous() and eps.numel() == 4 * L * L
     assert eps.dtype == (torch.float64 if precision == "fp64" else torch.float32)
     u = torch.empty((L, L, 2), dtype=eps.dtype, device=eps.device)
-    _check(lib().epfft_displacement(ctx.handle, L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision],
+    _check(lib().epfft_displacement(ctx.handle, L, _PREC[precision],
                                     eps.data_ptr(), u.data_ptr()), "epfft_displacement")
     return u
 
@@ -476,7 +481,7 @@ def epfft_average5(ctx: Context, L: int, precision: str, eps_in, eps_out):
     each pixel and its four neighbours.  eps_in / eps_out: CUDA tensors of
     L*L*4 reals."""
     assert eps_in.is_cuda and eps_out.is_cuda and eps_in.numel() == eps_out.numel() == L * L * 4
-    _check(lib().epfft_average5(ctx.handle, L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision],
+    _check(lib().epfft_average5(ctx.handle, L, _PREC[precision],
                                 eps_in.data_ptr(), eps_out.data_ptr()), "epfft_average5")
 
 
@@ -524,7 +529,7 @@ def epfft_iterate(ctx: Context, problem: Problem, E, eps, n_iter: int):
     import torch
     p, keep = problem._c()
     assert eps.is_cuda and eps.is_contiguous() and eps.numel() == 4 * problem.L ** 2
-    assert eps.dtype == (torch.float64 if problem.precision == "fp64" else torch.float32)
+    assert eps.dtype == (torch.float32 if problem.precision == "fp32" else torch.float64)
     Ea = (C.c_double * 4)(*[float(x) for x in E])
     rec = np.zeros(1, dtype=RECORD_DTYPE)
     torch.cuda.current_stream(ctx.device).synchronize()
@@ -540,7 +545,7 @@ def epfft_project(ctx: Context, L: int, precision: str, lambda0: float, mu0: flo
     e = torch.empty_like(p)
     Ea = (C.c_double * 4)(*[float(x) for x in E])
     torch.cuda.current_stream(ctx.device).synchronize()
-    _check(lib().epfft_project(ctx.handle, L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision],
+    _check(lib().epfft_project(ctx.handle, L, _PREC[precision],
                                float(lambda0), float(mu0), Ea, p.data_ptr(), e.data_ptr()), "epfft_project")
     return e
 
@@ -592,7 +597,7 @@ def epfft_project_static(L: int, precision: str, lambda0: float, mu0: float, E, 
     assert e.is_cuda and e.is_contiguous() and e.shape == p.shape and e.dtype == p.dtype
     Ea = (C.c_double * 4)(*[float(x) for x in E])
     s = torch.cuda.current_stream(p.device) if stream is None else stream
-    _check(lib().epfft_project_static(L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision], float(lambda0),
+    _check(lib().epfft_project_static(L, _PREC[precision], float(lambda0),
                                       float(mu0), Ea, p.data_ptr(), e.data_ptr(), s.cuda_stream),
            "epfft_project_static")
     if wait:
@@ -691,15 +696,21 @@ def epfft_autotune(ctx: Context, L: int, precision: str, n_batch: int = 1):
     class).  Returns (chosen tiling, [ms per iteration of each])."""
     ch = C.c_int32()
     ms = (C.c_float * N_TILINGS)()
-    _check(lib().epfft_autotune(ctx.handle, L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision], int(n_batch),
+    _check(lib().epfft_autotune(ctx.handle, L, _PREC[precision], int(n_batch),
                                 C.byref(ch), ms), "epfft_autotune")
     return ch.value, list(ms)
 
 
 def epfft_supported_tiling(L: int, precision: str, variant: int) -> bool:
-    return bool(lib().epfft_supported_tiling(L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision], int(variant)))
+    return bool(lib().epfft_supported_tiling(L, _PREC[precision], int(variant)))
 
 
 def epfft_set_tiling(ctx: Context, L: int, precision: str, variant: int):
-    _check(lib().epfft_set_tiling(ctx.handle, L, {"fp64": EPFFT_FP64, "fp32": EPFFT_FP32}[precision], int(variant)),
+    _check(lib().epfft_set_tiling(ctx.handle, L, _PREC[precision], int(variant)),
            "epfft_set_tiling")
+
+
+def epfft_set_defect_refresh(ctx: Context, steps: int):
+    """Loop steps between refreshes of the FP64 reference of the defect
+    form ('fp32_defect'); 1 makes every iteration the FP64 one."""
+    _check(lib().epfft_set_defect_refresh(ctx.handle, int(steps)), "epfft_set_defect_refresh")

@@ -314,9 +314,11 @@ col_pass_rs(Solve* __restrict__ solves, const C2<float>* __restrict__ ktab, cons
           Bp[c] = conj(B[c]);
         }
         if (m2 == 0) {
-          A[0] = mk(float(Ep[0]), 0.f);
-          A[1] = mk(float(Ep[1]), 0.f);
-          A[2] = mk(float(Ep[3]), 0.f);
+          // the mean strain, or 0 for the defect form (added in FP64 there)
+          const float z = Sol.zero_mean ? 0.f : 1.f;
+          A[0] = mk(z * float(Ep[0]), 0.f);
+          A[1] = mk(z * float(Ep[1]), 0.f);
+          A[2] = mk(z * float(Ep[3]), 0.f);
         } else {
           green_op(gm, ktab, qtab, L, 0, m2, lam0, mu0, scale, A[0], A[1], A[2]);
           green_op(gm, ktab, qtab, L, 0, mp, lam0, mu0, scale, Ap[0], Ap[1], Ap[2]);

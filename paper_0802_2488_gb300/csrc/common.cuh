@@ -124,6 +124,15 @@ struct Solve {
   void* sig[2];        // sigma of the same iterates (the multiplier), L*L*4 reals
   void* spec;          // 3 * L * L/2 complex, tiled column layout
   double* partials;    // n_row_ctas * PART_STRIDE
+  // defect-correction form (FP64 state, FP32 transforms): the reference
+  // polarization p_ref and its compatible strain g_ref = Gamma(p_ref), three
+  // FP64 planes (11, 22, 12) of L * L each, and the FP64 spectrum of the
+  // reference transform; null otherwise
+  void* pref;
+  void* gref;
+  void* spec64;
+  int32_t zero_mean;   // 1: the column pass puts 0 at q = 0 (not the mean strain)
+  int32_t pad0;
   // mutable state
   int32_t phase, inc, iter, cur;
   int32_t status;

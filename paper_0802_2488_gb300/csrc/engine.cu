@@ -49,6 +49,8 @@ struct epfft_ctx {
   std::map<std::tuple<int, int, int>, int> variant;
   epfft_stats last{};
   Server* server = nullptr;
+  // defect-correction form: loop steps between refreshes of the reference
+  int defect_refresh = 64;
 };
 
 namespace {
@@ -101,15 +103,26 @@ bool supported(int L, int prec) {
   if (!is_pow2(L) || L < 4) return false;
   if (prec == EPFFT_FP32) return pass_shape<float>(L, 0, &sh);
   if (prec == EPFFT_FP64) return pass_shape<double>(L, 0, &sh);
+  // the defect form: FP32 passes, FP64 refresh
+  if (prec == EPFFT_FP32_DEFECT) return pass_shape<float>(L, 0, &sh) && pass_shape<double>(L, 0, &sh);
   return false;
 }
 
+// Tile shapes of the loop's passes (the defect form runs the FP32 tilings 0
+// and 1).
 int shape(int L, int prec, int var, PassShape* sh) {
-  bool ok = prec == EPFFT_FP32 ? pass_shape<float>(L, var, sh) : pass_shape<double>(L, var, sh);
+  bool ok;
+  if (prec == EPFFT_FP32_DEFECT) ok = var < N_DEF_VARIANTS && pass_shape<float>(L, var, sh);
+  else ok = prec == EPFFT_FP32 ? pass_shape<float>(L, var, sh) : pass_shape<double>(L, var, sh);
   return ok ? EPFFT_OK : EPFFT_ERR_UNSUPPORTED;
 }
 
+// Bytes of one real of the state (strain, stress, fields a caller reads).
 size_t real_size(int prec) { return prec == EPFFT_FP32 ? 4 : 8; }
+// Bytes of one real of the loop's spectrum and transform tables.
+size_t spec_real_size(int prec) { return prec == EPFFT_FP64 ? 8 : 4; }
+// Precision of the loop's transform tables.
+int table_prec(int prec) { return prec == EPFFT_FP64 ? EPFFT_FP64 : EPFFT_FP32; }
 
 // Device tables of (L, precision) (layout of tables.cuh: twist octant,
 // stage twiddles of both tilings' plans, Fourier symbols of Eq. 2
@@ -144,13 +157,15 @@ int get_tables(epfft_ctx* c, int L, int prec, void** tw, void** ktab) {
 
 // First recorded self-check failure of any instantiation unit.
 cudaError_t read_check_all(CheckRec* out) {
-  CheckRec r[5];
+  CheckRec r[7];
   cudaError_t e;
   if ((e = read_check_v<float, 0>(&r[0])) != cudaSuccess) return e;
   if ((e = read_check_v<float, 1>(&r[1])) != cudaSuccess) return e;
   if ((e = read_check_v<double, 0>(&r[2])) != cudaSuccess) return e;
   if ((e = read_check_v<double, 1>(&r[3])) != cudaSuccess) return e;
   if ((e = read_check_v<float, 2>(&r[4])) != cudaSuccess) return e;
+  if ((e = read_check_def_v<0>(&r[5])) != cudaSuccess) return e;
+  if ((e = read_check_def_v<1>(&r[6])) != cudaSuccess) return e;
   *out = CheckRec{};
   for (auto& x : r)
     if (x.code) {
@@ -164,7 +179,13 @@ cudaError_t read_check_all(CheckRec* out) {
 int ensure_prepared(epfft_ctx* c, int L, int prec, int var) {
   auto key = std::make_tuple(L, prec, var);
   if (!c->prepared[key]) {
-    CK(prec == EPFFT_FP32 ? prepare<float>(L, var) : prepare<double>(L, var));
+    if (prec == EPFFT_FP32_DEFECT) {
+      // the FP32 column passes and the defect kernels of tiling var
+      CK(prepare<float>(L, var));
+      CK(prepare_def(L, var));
+    } else {
+      CK(prec == EPFFT_FP32 ? prepare<float>(L, var) : prepare<double>(L, var));
+    }
     c->prepared[key] = true;
   }
   return EPFFT_OK;
@@ -187,7 +208,8 @@ uint64_t void_threshold(double f) {
 int check_problem(const epfft_problem* p) {
   if (!p) return EPFFT_ERR_ARG;
   if (!is_pow2(p->L) || p->L < 4 || p->L > 4096) return EPFFT_ERR_ARG;
-  if (p->precision != EPFFT_FP32 && p->precision != EPFFT_FP64) return EPFFT_ERR_ARG;
+  if (p->precision != EPFFT_FP32 && p->precision != EPFFT_FP64 && p->precision != EPFFT_FP32_DEFECT)
+    return EPFFT_ERR_ARG;
   if (p->green != EPFFT_GREEN_EQ3 && p->green != EPFFT_GREEN_CG1 && p->green != EPFFT_GREEN_DG1) return EPFFT_ERR_ARG;
   if (!supported(p->L, p->precision)) return EPFFT_ERR_UNSUPPORTED;
   if (!p->mask && !(p->void_fraction >= 0.0 && p->void_fraction <= 1.0)) return EPFFT_ERR_ARG;
@@ -235,20 +257,48 @@ struct Batch {
   void* ktab = nullptr;
   Solve* d_solves = nullptr;
   BatchCtl* d_ctl = nullptr;
+  int64_t max_body = 0;  // bound on the loop steps of the batch
+  // defect form: FP64 tables and tiling of the refresh, the shadow solves its
+  // FP64 column pass reads (spectrum = the FP64 one), refreshes launched
+  void* tw64 = nullptr;
+  void* ktab64 = nullptr;
+  int var64 = 0;
+  Solve* d_shadow = nullptr;
+  std::vector<Solve> h_shadow;  // serving: host copy of the shadow slots
+  int64_t refreshes = 0;
   std::vector<Solve> h_solves;
   std::vector<int32_t> n_inc;
   std::vector<int32_t*> d_labels;  // per solve, n_inc * L * L (allocated on demand)
 };
 
+// The two passes of one loop step of a batch, in its precision.
+cudaError_t col_of(Batch& B, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
+  if (B.prec == EPFFT_FP64) return launch_col<double>(B.L, B.var, B.nb, s, B.d_solves, B.tw, B.ktab, h, use_cond, B.general);
+  return launch_col<float>(B.L, B.var, B.nb, s, B.d_solves, B.tw, B.ktab, h, use_cond, B.general);
+}
+cudaError_t row_of(Batch& B, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
+  if (B.prec == EPFFT_FP64) return launch_row<double>(B.L, B.var, B.nb, s, B.d_solves, B.d_ctl, B.tw, h, use_cond);
+  if (B.prec == EPFFT_FP32_DEFECT) return launch_row_def(B.L, B.var, B.nb, s, B.d_solves, B.d_ctl, B.tw, h, use_cond);
+  return launch_row<float>(B.L, B.var, B.nb, s, B.d_solves, B.d_ctl, B.tw, h, use_cond);
+}
+
 int launch_body(epfft_ctx* c, Batch& B, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
-  if (B.prec == EPFFT_FP32) {
-    CK(launch_col<float>(B.L, B.var, B.nb, s, B.d_solves, B.tw, B.ktab, h, use_cond, B.general));
-    CK(launch_row<float>(B.L, B.var, B.nb, s, B.d_solves, B.d_ctl, B.tw, h, use_cond));
-  } else {
-    CK(launch_col<double>(B.L, B.var, B.nb, s, B.d_solves, B.tw, B.ktab, h, use_cond, B.general));
-    CK(launch_row<double>(B.L, B.var, B.nb, s, B.d_solves, B.d_ctl, B.tw, h, use_cond));
-  }
+  CK(col_of(B, s, h, use_cond));
+  CK(row_of(B, s, h, use_cond));
   (void)c;
+  return EPFFT_OK;
+}
+
+// Refresh of the defect form's reference (defect.cuh) for every solve of
+// the batch in its iteration phase: FP64 row transform of the current
+// polarization, FP64 column pass on the shadow solves, FP64 inverse row
+// transform into g_ref.  No-op for other precisions.
+int refresh_defect(Batch& B, cudaStream_t s) {
+  if (B.prec != EPFFT_FP32_DEFECT) return EPFFT_OK;
+  CK(launch_ref_forward(B.L, B.var64, B.nb, s, B.d_solves, B.d_shadow, B.tw64));
+  CK(launch_col<double>(B.L, B.var64, B.nb, s, B.d_shadow, B.tw64, B.ktab64, 0, 0, B.general));
+  CK(launch_ref_inverse(B.L, B.var64, B.nb, s, B.d_solves, B.tw64));
+  B.refreshes += 1;
   return EPFFT_OK;
 }
 
@@ -256,8 +306,11 @@ int launch_body(epfft_ctx* c, Batch& B, cudaStream_t s, cudaGraphConditionalHand
 size_t solve_footprint(int L, int prec, int row_ctas, int n_inc) {
   const size_t LL = (size_t)L * L, rs = real_size(prec);
   auto r = [](size_t b) { return (b + 511) & ~(size_t)511; };
-  return r(4 * LL * rs) * 4 + r(3 * LL * rs) + r(sizeof(double) * PART_STRIDE * (size_t)row_ctas) + r(LL) +
-         r(LL * (size_t)n_inc) + r(sizeof(double) * 4 * (size_t)n_inc) + r(sizeof(Record) * (size_t)n_inc);
+  // the defect form adds p_ref, g_ref and the FP64 spectrum
+  const size_t def = prec == EPFFT_FP32_DEFECT ? 3 * r(3 * LL * 8) : 0;
+  return r(4 * LL * rs) * 4 + r(3 * LL * spec_real_size(prec)) + def +
+         r(sizeof(double) * PART_STRIDE * (size_t)row_ctas) + r(LL) + r(LL * (size_t)n_inc) +
+         r(sizeof(double) * 4 * (size_t)n_inc) + r(sizeof(Record) * (size_t)n_inc);
 }
 
 // Allocates (through `get`) and initialises the device state of one solve on
@@ -284,7 +337,7 @@ int init_solve(Get&& get, const PassShape& sh, int L, int prec, const epfft_prob
   void* eps1d = get(4 * LL * rs);
   void* sig0d = get(4 * LL * rs);
   void* sig1d = get(4 * LL * rs);
-  void* spec = get(3 * LL * rs);
+  void* spec = get(3 * LL * spec_real_size(prec));
   double* part = (double*)get(sizeof(double) * PART_STRIDE * (size_t)sh.row_ctas);
   uint8_t* mask = (uint8_t*)get(LL);
   uint8_t* flags = (uint8_t*)get(LL * (size_t)n_inc);
@@ -303,6 +356,16 @@ int init_solve(Get&& get, const PassShape& sh, int L, int prec, const epfft_prob
   S.path = dpath;
   S.rec = rec;
   S.phase = PH_INIT;
+  if (prec == EPFFT_FP32_DEFECT) {
+    // reference p_ref = 0, g_ref = 0 until the first refresh
+    S.pref = get(3 * LL * 8);
+    S.gref = get(3 * LL * 8);
+    S.spec64 = get(3 * LL * 8);
+    if (!S.pref || !S.gref || !S.spec64) return EPFFT_ERR_OOM;
+    S.zero_mean = 1;
+    CK(cudaMemsetAsync(S.pref, 0, 3 * LL * 8, s));
+    CK(cudaMemsetAsync(S.gref, 0, 3 * LL * 8, s));
+  }
   CK(cudaMemcpyAsync(dpath, path, sizeof(double) * 4 * (size_t)n_inc, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(rec, 0, sizeof(Record) * (size_t)n_inc, s));
   if (p.mask) {
@@ -331,8 +394,16 @@ int setup_batch(epfft_ctx* c, Arena& A, Batch& B, int n, const epfft_problem* pr
   if (B.var < 0) B.var = variant_for(c, B.L, B.prec, n);
   int rc = shape(B.L, B.prec, B.var, &B.sh);
   if (rc) return rc;
-  rc = get_tables(c, B.L, B.prec, &B.tw, &B.ktab);
+  rc = get_tables(c, B.L, table_prec(B.prec), &B.tw, &B.ktab);
   if (!rc) rc = ensure_prepared(c, B.L, B.prec, B.var);
+  if (!rc && B.prec == EPFFT_FP32_DEFECT) {
+    // the refresh: FP64 tables, FP64 column pass and FP64 row halves of the
+    // FP64 tiling tuned for this batch class
+    B.var64 = variant_for(c, B.L, EPFFT_FP64, n);
+    rc = get_tables(c, B.L, EPFFT_FP64, &B.tw64, &B.ktab64);
+    if (!rc) rc = ensure_prepared(c, B.L, EPFFT_FP64, B.var64);
+    if (!rc) rc = ensure_prepared(c, B.L, EPFFT_FP32_DEFECT, B.var64);
+  }
   if (rc) return rc;
   B.h_solves.resize(n);
   B.n_inc.resize(n);
@@ -350,10 +421,25 @@ int setup_batch(epfft_ctx* c, Arena& A, Batch& B, int n, const epfft_problem* pr
   B.d_ctl = (BatchCtl*)A.get(sizeof(BatchCtl));
   if (!B.d_solves || !B.d_ctl) return EPFFT_ERR_OOM;
   CK(cudaMemcpyAsync(B.d_solves, B.h_solves.data(), sizeof(Solve) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
+  if (B.prec == EPFFT_FP32_DEFECT) {
+    // shadow solves of the refresh's FP64 column pass: the FP64 spectrum
+    // and 0 at q = 0 (ref_forward mirrors phase, increment and buffer)
+    std::vector<Solve> sh = B.h_solves;
+    for (auto& z : sh) {
+      z.spec = z.spec64;
+      z.zero_mean = 1;
+    }
+    B.d_shadow = (Solve*)A.get(sizeof(Solve) * (size_t)n);
+    if (!B.d_shadow) return EPFFT_ERR_OOM;
+    CK(cudaMemcpyAsync(B.d_shadow, sh.data(), sizeof(Solve) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
+    // the host copy leaves this scope: wait for the upload
+    CK(cudaStreamSynchronize(c->stream));
+  }
   BatchCtl bc;
   std::memset(&bc, 0, sizeof(bc));
   bc.active = n;
   bc.max_body_iters = max_body + 8;
+  B.max_body = bc.max_body_iters;
   CK(cudaMemcpyAsync(B.d_ctl, &bc, sizeof(bc), cudaMemcpyHostToDevice, c->stream));
   return EPFFT_OK;
 }
@@ -412,12 +498,18 @@ int build_loop_graph(epfft_ctx* c, Batch& B, cudaGraph_t* graph_out, cudaGraphEx
 }
 
 // Runs the device-side loop of a batch to completion (one graph launch).
+int run_chunked(epfft_ctx* c, std::vector<Batch*>& Bs, cudaGraphExec_t exec);
+
 int run_graph(epfft_ctx* c, Batch& B) {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int rc = build_loop_graph(c, B, &graph, &exec);
   if (rc) return rc;
-  if (cudaGraphLaunch(exec, c->stream) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
+  if (B.prec == EPFFT_FP32_DEFECT) {
+    std::vector<Batch*> one{&B};
+    rc = run_chunked(c, one, exec);
+    if (rc) cudaGetLastError();
+  } else if (cudaGraphLaunch(exec, c->stream) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
     rc = EPFFT_ERR_CUDA;
     cudaGetLastError();
   }
@@ -529,7 +621,12 @@ int run_mixed_graph(epfft_ctx* c, Arena& A, std::vector<Batch*>& Bs) {
   cudaGraphExec_t exec = nullptr;
   int rc = build_mixed_graph(c, Bs, dctl, &graph, &exec);
   if (rc) return rc;
-  if (cudaGraphLaunch(exec, c->stream) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
+  bool defect = false;
+  for (Batch* b : Bs) defect |= b->prec == EPFFT_FP32_DEFECT;
+  if (defect) {
+    rc = run_chunked(c, Bs, exec);
+    if (rc) cudaGetLastError();
+  } else if (cudaGraphLaunch(exec, c->stream) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
     rc = EPFFT_ERR_CUDA;
     cudaGetLastError();
   }
@@ -545,18 +642,52 @@ int run_mixed_graph(epfft_ctx* c, Arena& A, std::vector<Batch*>& Bs) {
 // number of iterations), so the passes are ordinary stream launches.
 int run_host_loop(epfft_ctx* c, Batch& B, int64_t steps) {
   for (int64_t k = 0; k < steps; k++) {
-    cudaError_t e = cudaSuccess;
-    if (B.prec == EPFFT_FP32) {
-      e = launch_col<float>(B.L, B.var, B.nb, c->stream, B.d_solves, B.tw, B.ktab, 0, 0, B.general);
-      if (e == cudaSuccess) e = launch_row<float>(B.L, B.var, B.nb, c->stream, B.d_solves, B.d_ctl, B.tw, 0, 0);
-    } else {
-      e = launch_col<double>(B.L, B.var, B.nb, c->stream, B.d_solves, B.tw, B.ktab, 0, 0, B.general);
-      if (e == cudaSuccess) e = launch_row<double>(B.L, B.var, B.nb, c->stream, B.d_solves, B.d_ctl, B.tw, 0, 0);
-    }
+    // the defect form refreshes its reference every defect_refresh steps
+    if (k % c->defect_refresh == 0 && refresh_defect(B, c->stream)) return EPFFT_ERR_CUDA;
+    cudaError_t e = col_of(B, c->stream, 0, 0);
+    if (e == cudaSuccess) e = row_of(B, c->stream, 0, 0);
     if (e != cudaSuccess) return EPFFT_ERR_CUDA;
   }
   CK(cudaStreamSynchronize(c->stream));
   return EPFFT_OK;
+}
+
+// The device-side loop of the defect form: the graph (single batch or
+// mixed) runs defect_refresh loop steps at a time, and the references of the
+// defect batches are refreshed between the launches, until every solve is
+// done or a batch reaches its step bound.
+int run_chunked(epfft_ctx* c, std::vector<Batch*>& Bs, cudaGraphExec_t exec) {
+  const int G = (int)Bs.size();
+  std::vector<BatchCtl> bc(G);
+  for (int g = 0; g < G; g++) CK(cudaMemcpyAsync(&bc[g], Bs[g]->d_ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (;;) {
+    for (int g = 0; g < G; g++) {
+      bc[g].max_body_iters = std::min<int64_t>(bc[g].body_iters + c->defect_refresh, Bs[g]->max_body);
+      bc[g].timed_out = 0;
+      CK(cudaMemcpyAsync(Bs[g]->d_ctl, &bc[g], sizeof(BatchCtl), cudaMemcpyHostToDevice, c->stream));
+    }
+    CK(cudaGraphLaunch(exec, c->stream));
+    for (int g = 0; g < G; g++) CK(cudaMemcpyAsync(&bc[g], Bs[g]->d_ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    bool live = false, bound = false;
+    for (int g = 0; g < G; g++) {
+      live |= bc[g].active > 0;
+      bound |= bc[g].active > 0 && bc[g].body_iters >= Bs[g]->max_body;
+    }
+    if (!live) return EPFFT_OK;
+    if (bound) {
+      // the step bound stopped a batch with work left
+      for (int g = 0; g < G; g++) {
+        bc[g].timed_out = bc[g].active > 0 ? 1 : 0;
+        CK(cudaMemcpyAsync(Bs[g]->d_ctl, &bc[g], sizeof(BatchCtl), cudaMemcpyHostToDevice, c->stream));
+      }
+      CK(cudaStreamSynchronize(c->stream));
+      return EPFFT_OK;
+    }
+    for (int g = 0; g < G; g++)
+      if (refresh_defect(*Bs[g], c->stream)) return EPFFT_ERR_CUDA;
+  }
 }
 
 // Diagnostic loop (EPFFT_SYNC_CHECK=1 in the environment): the same passes
@@ -567,17 +698,22 @@ int run_checked(epfft_ctx* c, Batch& B) {
   std::vector<Solve> hs(B.nb);
   for (int64_t step = 0;; step++) {
     CK(cudaMemcpy(hs.data(), B.d_solves, sizeof(Solve) * B.nb, cudaMemcpyDeviceToHost));
-    cudaError_t e;
-    if (B.prec == EPFFT_FP32) e = launch_col<float>(B.L, B.var, B.nb, c->stream, B.d_solves, B.tw, B.ktab, 0, 0, B.general);
-    else e = launch_col<double>(B.L, B.var, B.nb, c->stream, B.d_solves, B.tw, B.ktab, 0, 0, B.general);
+    cudaError_t e = cudaSuccess;
+    if (step % c->defect_refresh == 0 && refresh_defect(B, c->stream)) e = cudaErrorUnknown;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      fprintf(stderr, "epfft check: refresh failed at step %lld (phase %d inc %d iter %d): %s\n",
+              (long long)step, hs[0].phase, hs[0].inc, hs[0].iter, cudaGetErrorString(e));
+      return EPFFT_ERR_CUDA;
+    }
+    e = col_of(B, c->stream, 0, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
       fprintf(stderr, "epfft check: column pass failed at step %lld (phase %d inc %d iter %d): %s\n",
               (long long)step, hs[0].phase, hs[0].inc, hs[0].iter, cudaGetErrorString(e));
       return EPFFT_ERR_CUDA;
     }
-    if (B.prec == EPFFT_FP32) e = launch_row<float>(B.L, B.var, B.nb, c->stream, B.d_solves, B.d_ctl, B.tw, 0, 0);
-    else e = launch_row<double>(B.L, B.var, B.nb, c->stream, B.d_solves, B.d_ctl, B.tw, 0, 0);
+    e = row_of(B, c->stream, 0, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
       fprintf(stderr, "epfft check: row pass failed at step %lld (phase %d inc %d iter %d): %s\n",
@@ -747,6 +883,7 @@ int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_
       k += 2 * bc[g].body_iters;
     }
     if (G > 1) k += steps;  // the loop-condition kernel of the mixed graph
+    for (int g = 0; g < G; g++) k += 3 * Bs[g].refreshes;  // the defect form's refreshes
     // per solve the mask kernel (when generated) and the four labelling kernels
     for (int i = 0; i < n; i++) k += (probs[i].mask ? 0 : 1) + 4;
     c->last.loop_steps = steps;
@@ -804,17 +941,14 @@ int time_passes_impl(epfft_ctx* ctx, epfft_problem p, int n_batch, const double 
   if (rc) return rc;
   const int nb = n_batch;
   // first row pass: warm start (eps = E, spectrum of its polarization)
-  if (B.prec == EPFFT_FP32) CK(launch_row<float>(B.L, B.var, nb, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
-  else CK(launch_row<double>(B.L, B.var, nb, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
+  CK(row_of(B, ctx->stream, 0, 0));
   std::vector<cudaEvent_t> ev(3 * (size_t)n_iter);
   for (auto& e : ev) CK(cudaEventCreate(&e));
   for (int it = 0; it < n_iter; it++) {
     CK(cudaEventRecord(ev[3 * it], ctx->stream));
-    if (B.prec == EPFFT_FP32) CK(launch_col<float>(B.L, B.var, nb, ctx->stream, B.d_solves, B.tw, B.ktab, 0, 0, B.general));
-    else CK(launch_col<double>(B.L, B.var, nb, ctx->stream, B.d_solves, B.tw, B.ktab, 0, 0, B.general));
+    CK(col_of(B, ctx->stream, 0, 0));
     CK(cudaEventRecord(ev[3 * it + 1], ctx->stream));
-    if (B.prec == EPFFT_FP32) CK(launch_row<float>(B.L, B.var, nb, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
-    else CK(launch_row<double>(B.L, B.var, nb, ctx->stream, B.d_solves, B.d_ctl, B.tw, 0, 0));
+    CK(row_of(B, ctx->stream, 0, 0));
     CK(cudaEventRecord(ev[3 * it + 2], ctx->stream));
   }
   CK(cudaStreamSynchronize(ctx->stream));
@@ -904,6 +1038,7 @@ void free_class(epfft_ctx* c, ServeClass* k) {
     for (auto& b : sl.blocks) dev_free(c, b.first, b.second);
   if (k->B.d_solves) dev_free(c, k->B.d_solves, sizeof(Solve) * (size_t)k->cap);
   if (k->B.d_ctl) dev_free(c, k->B.d_ctl, sizeof(BatchCtl));
+  if (k->B.d_shadow) dev_free(c, k->B.d_shadow, sizeof(Solve) * (size_t)k->cap);
   cudaStreamSynchronize(c->stream);
   delete k;
 }
@@ -960,12 +1095,23 @@ int get_class(epfft_ctx* c, Server& S, int L, int prec, int general, ServeClass*
   B.general = general;
   B.var = variant_for(c, L, prec, S.cap);
   int rc = shape(L, prec, B.var, &B.sh);
-  if (!rc) rc = get_tables(c, L, prec, &B.tw, &B.ktab);
+  if (!rc) rc = get_tables(c, L, table_prec(prec), &B.tw, &B.ktab);
   if (!rc) rc = ensure_prepared(c, L, prec, B.var);
+  if (!rc && prec == EPFFT_FP32_DEFECT) {
+    // the refresh between serving steps (FP64 tables, column pass, row halves)
+    B.var64 = variant_for(c, L, EPFFT_FP64, S.cap);
+    rc = get_tables(c, L, EPFFT_FP64, &B.tw64, &B.ktab64);
+    if (!rc) rc = ensure_prepared(c, L, EPFFT_FP64, B.var64);
+    if (!rc) rc = ensure_prepared(c, L, EPFFT_FP32_DEFECT, B.var64);
+  }
   if (!rc) {
     B.d_solves = (Solve*)dev_alloc(c, sizeof(Solve) * (size_t)S.cap);
     B.d_ctl = (BatchCtl*)dev_alloc(c, sizeof(BatchCtl));
     if (!B.d_solves || !B.d_ctl) rc = EPFFT_ERR_OOM;
+    if (!rc && prec == EPFFT_FP32_DEFECT) {
+      B.d_shadow = (Solve*)dev_alloc(c, sizeof(Solve) * (size_t)S.cap);
+      if (!B.d_shadow) rc = EPFFT_ERR_OOM;
+    }
   }
   if (!rc) {
     B.h_solves.assign(S.cap, Solve{});
@@ -975,9 +1121,15 @@ int get_class(epfft_ctx* c, Server& S, int L, int prec, int general, ServeClass*
     }
     B.n_inc.assign(S.cap, 0);
     if (cudaMemcpyAsync(B.d_solves, B.h_solves.data(), sizeof(Solve) * (size_t)S.cap, cudaMemcpyHostToDevice,
-                        c->stream) != cudaSuccess ||
-        cudaStreamSynchronize(c->stream) != cudaSuccess)
+                        c->stream) != cudaSuccess)
       rc = EPFFT_ERR_CUDA;
+    if (!rc && B.d_shadow) {
+      B.h_shadow = B.h_solves;
+      if (cudaMemcpyAsync(B.d_shadow, B.h_shadow.data(), sizeof(Solve) * (size_t)S.cap, cudaMemcpyHostToDevice,
+                          c->stream) != cudaSuccess)
+        rc = EPFFT_ERR_CUDA;
+    }
+    if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = EPFFT_ERR_CUDA;
   }
   if (rc) {
     free_class(c, k);
@@ -1035,6 +1187,15 @@ int serve_admit(epfft_ctx* c, Server& S) {
     k->B.n_inc[slot] = (int)(t.path.size() / 4);
     CK(cudaMemcpyAsync(k->B.d_solves + slot, &k->B.h_solves[slot], sizeof(Solve), cudaMemcpyHostToDevice,
                        c->stream));
+    if (k->B.d_shadow) {
+      // the slot's shadow for the refresh's FP64 column pass
+      Solve z = hs;
+      z.spec = hs.spec64;
+      z.zero_mean = 1;
+      k->B.h_shadow[slot] = z;
+      CK(cudaMemcpyAsync(k->B.d_shadow + slot, &k->B.h_shadow[slot], sizeof(Solve), cudaMemcpyHostToDevice,
+                         c->stream));
+    }
     sl.used = true;
     sl.ticket = *qi;
     sl.bytes = t.bytes;
@@ -1861,6 +2022,13 @@ int epfft_serve_step(epfft_ctx* ctx, int32_t* n_running, int32_t* n_queued) {
     ctx->last.loop_steps = steps;
     // a column and a row pass of every class, and the loop-condition kernel, per step
     ctx->last.kernel_launches += (2 * (int64_t)S.order.size() + 1) * steps;
+    // the defect classes refresh their references between steps
+    for (ServeClass* k : live)
+      if (k->prec == EPFFT_FP32_DEFECT) {
+        rc = refresh_defect(k->B, ctx->stream);
+        if (rc) return rc;
+        ctx->last.kernel_launches += 3;
+      }
   }
   {
     CheckRec cr;
@@ -1981,7 +2149,8 @@ int epfft_fp64_peak(epfft_ctx* ctx, double* tflops, int32_t* n_sm, float* ms) {
 int epfft_autotune(epfft_ctx* ctx, int32_t L, int32_t precision, int32_t n_batch, int32_t* chosen,
                    float* ms_per_iteration) {
   if (!ctx || n_batch < 1) return EPFFT_ERR_ARG;
-  if (!is_pow2(L) || L < 4 || (precision != EPFFT_FP32 && precision != EPFFT_FP64)) return EPFFT_ERR_ARG;
+  if (!is_pow2(L) || L < 4 || (precision != EPFFT_FP32 && precision != EPFFT_FP64 && precision != EPFFT_FP32_DEFECT))
+    return EPFFT_ERR_ARG;
   if (!supported(L, precision)) return EPFFT_ERR_UNSUPPORTED;
   // a synthetic lattice of the kind the solver serves: f = 0.2 voids, the
   // default matrix, shear at 1.5x the void-free yield strain
@@ -2029,10 +2198,17 @@ int epfft_supported_tiling(int32_t L, int32_t precision, int32_t variant) {
 
 int epfft_set_tiling(epfft_ctx* ctx, int32_t L, int32_t precision, int32_t variant) {
   if (!ctx || variant < 0 || variant >= N_VARIANTS) return EPFFT_ERR_ARG;
-  if (!is_pow2(L) || L < 4 || (precision != EPFFT_FP32 && precision != EPFFT_FP64)) return EPFFT_ERR_ARG;
+  if (!is_pow2(L) || L < 4 || (precision != EPFFT_FP32 && precision != EPFFT_FP64 && precision != EPFFT_FP32_DEFECT))
+    return EPFFT_ERR_ARG;
   if (!supported(L, precision)) return EPFFT_ERR_UNSUPPORTED;
   if (!epfft_supported_tiling(L, precision, variant)) return EPFFT_ERR_UNSUPPORTED;
   for (int k = 0; k < 2; k++) ctx->variant[std::make_tuple((int)L, (int)precision, k)] = variant;
+  return EPFFT_OK;
+}
+
+int epfft_set_defect_refresh(epfft_ctx* ctx, int32_t steps) {
+  if (!ctx || steps < 1) return EPFFT_ERR_ARG;
+  ctx->defect_refresh = steps;
   return EPFFT_OK;
 }
 

@@ -1,0 +1,100 @@
+// Instantiation of the defect-correction kernels (defect.cuh) for one
+// tiling variant EPFFT_VAR over the supported lattice sides: the row pass
+// with FP64 state and FP32 transforms, and the FP64 row halves of a refresh.
+#pragma once
+#include "defect.cuh"
+#include "launch.cuh"
+
+namespace epfft {
+
+// sides of the FP64 build (the refresh runs FP64 transforms)
+#define EPFFT_DEF_FOR_L(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048)
+
+template <int L>
+static cudaError_t prepare_def_L() {
+  constexpr int V = EPFFT_VAR;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(row_pass<double, L, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Cfg<float, L, V>::ROW_SMEM)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(ref_forward<L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Cfg<double, L, V>::ROW_SMEM)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(ref_inverse<L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Cfg<double, L, V>::ROW_SMEM);
+}
+
+template <>
+cudaError_t prepare_def_v<EPFFT_VAR>(int L) {
+  switch (L) {
+#define X(n) case n: return prepare_def_L<n>();
+    EPFFT_DEF_FOR_L(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <>
+cudaError_t launch_row_def_v<EPFFT_VAR>(int L, int nb, cudaStream_t s, Solve* solves, BatchCtl* bc, const void* tw,
+                                       cudaGraphConditionalHandle cond, int use_cond) {
+  switch (L) {
+#define X(n)                                                                                             \
+  case n: {                                                                                              \
+    using C = Cfg<float, n, EPFFT_VAR>;                                                                  \
+    row_pass<double, n, EPFFT_VAR, true><<<dim3(n / C::RR, nb), C::NT_ROW, C::ROW_SMEM, s>>>(           \
+        solves, nb, bc, reinterpret_cast<const C2<float>*>(tw), cond, use_cond);                         \
+    return cudaGetLastError();                                                                           \
+  }
+    EPFFT_DEF_FOR_L(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <>
+cudaError_t launch_ref_forward_v<EPFFT_VAR>(int L, int nb, cudaStream_t s, Solve* solves, Solve* shadow,
+                                           const void* tw64) {
+  switch (L) {
+#define X(n)                                                                                             \
+  case n: {                                                                                              \
+    using C = Cfg<double, n, EPFFT_VAR>;                                                                 \
+    ref_forward<n, EPFFT_VAR><<<dim3(n / C::RR, nb), C::NT_ROW, C::ROW_SMEM, s>>>(                      \
+        solves, shadow, reinterpret_cast<const C2<double>*>(tw64));                                      \
+    return cudaGetLastError();                                                                           \
+  }
+    EPFFT_DEF_FOR_L(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <>
+cudaError_t launch_ref_inverse_v<EPFFT_VAR>(int L, int nb, cudaStream_t s, Solve* solves, const void* tw64) {
+  switch (L) {
+#define X(n)                                                                                             \
+  case n: {                                                                                              \
+    using C = Cfg<double, n, EPFFT_VAR>;                                                                 \
+    ref_inverse<n, EPFFT_VAR><<<dim3(n / C::RR, nb), C::NT_ROW, C::ROW_SMEM, s>>>(                      \
+        solves, reinterpret_cast<const C2<double>*>(tw64));                                              \
+    return cudaGetLastError();                                                                           \
+  }
+    EPFFT_DEF_FOR_L(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <>
+cudaError_t read_check_def_v<EPFFT_VAR>(CheckRec* out) {
+#ifdef EPFFT_CHECKS
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_check, sizeof(CheckRec));
+  if (e != cudaSuccess) return e;
+  CheckRec z = {};
+  return cudaMemcpyToSymbol(g_check, &z, sizeof(CheckRec));
+#else
+  *out = CheckRec{};
+  return cudaSuccess;
+#endif
+}
+
+}  // namespace epfft

@@ -44,6 +44,58 @@ cudaError_t launch_row_inverse_v(int L, cudaStream_t s, const void* spec, void* 
 template <typename T, int V>
 cudaError_t read_check_v(CheckRec* out);
 
+// Defect-correction form (defect.cuh), tilings 0 and 1: the row pass with
+// FP64 state and FP32 transforms (the FP32 tile shapes of tiling V; its
+// column pass is the FP32 one), and the two FP64 row halves of a refresh
+// (the FP64 tile shapes of tiling V; between them runs the FP64 column pass).
+constexpr int N_DEF_VARIANTS = 2;
+template <int V>
+cudaError_t prepare_def_v(int L);
+template <int V>
+cudaError_t launch_row_def_v(int L, int nb, cudaStream_t s, Solve* solves, BatchCtl* bc, const void* tw,
+                             cudaGraphConditionalHandle cond, int use_cond);
+template <int V>
+cudaError_t launch_ref_forward_v(int L, int nb, cudaStream_t s, Solve* solves, Solve* shadow, const void* tw64);
+template <int V>
+cudaError_t launch_ref_inverse_v(int L, int nb, cudaStream_t s, Solve* solves, const void* tw64);
+template <int V>
+cudaError_t read_check_def_v(CheckRec* out);
+
+template <int D = 0>  // a template, so that the variants may be specialised after it
+inline cudaError_t prepare_def(int L, int var) {
+  switch (var) {
+    case 0: return prepare_def_v<0>(L);
+    case 1: return prepare_def_v<1>(L);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <int D = 0>  // a template, so that the variants may be specialised after it
+inline cudaError_t launch_row_def(int L, int var, int nb, cudaStream_t s, Solve* solves, BatchCtl* bc,
+                                  const void* tw, cudaGraphConditionalHandle cond, int use_cond) {
+  switch (var) {
+    case 0: return launch_row_def_v<0>(L, nb, s, solves, bc, tw, cond, use_cond);
+    case 1: return launch_row_def_v<1>(L, nb, s, solves, bc, tw, cond, use_cond);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <int D = 0>  // a template, so that the variants may be specialised after it
+inline cudaError_t launch_ref_forward(int L, int var64, int nb, cudaStream_t s, Solve* solves, Solve* shadow,
+                                      const void* tw64) {
+  switch (var64) {
+    case 0: return launch_ref_forward_v<0>(L, nb, s, solves, shadow, tw64);
+    case 1: return launch_ref_forward_v<1>(L, nb, s, solves, shadow, tw64);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <int D = 0>  // a template, so that the variants may be specialised after it
+inline cudaError_t launch_ref_inverse(int L, int var64, int nb, cudaStream_t s, Solve* solves, const void* tw64) {
+  switch (var64) {
+    case 0: return launch_ref_inverse_v<0>(L, nb, s, solves, tw64);
+    case 1: return launch_ref_inverse_v<1>(L, nb, s, solves, tw64);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // Returns false when L is not built for T in that variant.
 template <typename T>
 inline bool pass_shape(int L, int var, PassShape* out) {

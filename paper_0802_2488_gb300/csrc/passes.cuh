@@ -22,6 +22,8 @@
 //   operator of Eq. 3 per frequency (scaled by 1/L^2, mean strain at q = 0),
 //   inverse column transform.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 #include "fft.cuh"
 #include "physics.cuh"
@@ -554,16 +556,35 @@ __device__ __forceinline__ void batch_arrive(Solve* solves, int nb, BatchCtl* bc
 // ---------------------------------------------------------------------------
 // Row pass
 // ---------------------------------------------------------------------------
-template <typename T, int L, int V>
-__global__ void __launch_bounds__(Cfg<T, L, V>::NT_ROW, Cfg<T, L, V>::MINB_ROW)
-row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restrict__ tw,
+// T is the type of the state (strain, stress, the local step and the
+// residual); the transforms and the spectrum are in T, or, with DEF (the
+// defect-correction form, T = double), in FP32 with the tile shapes of the
+// FP32 tiling V.  DEF: the spectrum carries the FP32 transform of the
+// polarization's difference from the solve's FP64 reference p_ref, and the
+// compatible strain is e = E + g_ref + (that difference through the Green
+// operator), g_ref = Gamma(p_ref) computed in FP64 (defect.cuh).
+template <typename T, bool DEF>
+using XformT = typename std::conditional<DEF, float, T>::type;
+template <typename T, int L, int V, bool DEF>
+struct RowK {
+  using F = XformT<T, DEF>;
+  using C = Cfg<F, L, V>;
+  // the FP64 local step of the defect form needs the registers of one CTA
+  // per SM
+  static constexpr int MINB = DEF ? 1 : C::MINB_ROW;
+};
+
+template <typename T, int L, int V, bool DEF = false>
+__global__ void __launch_bounds__(RowK<T, L, V, DEF>::C::NT_ROW, RowK<T, L, V, DEF>::MINB)
+row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<XformT<T, DEF>>* __restrict__ tw,
          cudaGraphConditionalHandle cond, int use_cond) {
-  using C = Cfg<T, L, V>;
+  using F = XformT<T, DEF>;
+  using C = Cfg<F, L, V>;
   constexpr int RR = C::RR, W = C::W, NT = C::NT_ROW, M = C::M;
   constexpr int P = L >= NT ? L / NT : 1;
-  using IO = RowIO<T, L, V>;
+  using IO = RowIO<F, L, V>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  C2<T>* sp = reinterpret_cast<C2<T>*>(smraw);
+  C2<F>* sp = reinterpret_cast<C2<F>*>(smraw);
   __shared__ bool s_last;
 
   // Every index of the pass is in range when the grid has L / RR CTAs per
@@ -589,13 +610,17 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
     // sigma of eps^n (read) and of the iterate this pass produces (written)
     const T* __restrict__ sin_ = reinterpret_cast<const T*>(S.sig[cur]);
     T* __restrict__ sout = reinterpret_cast<T*>(S.sig[1 - cur]);
-    C2<T>* spec = reinterpret_cast<C2<T>*>(S.spec);
+    C2<F>* spec = reinterpret_cast<C2<F>*>(S.spec);
     const uint8_t* __restrict__ mask = S.mask;
     const Mat<T> m = make_mat<T>(S);
     const size_t LL = (size_t)L * L;
+    // defect form: the FP64 reference polarization and its compatible
+    // strain, three planes (11, 22, 12) of L^2 each
+    const T* __restrict__ pref = DEF ? reinterpret_cast<const T*>(S.pref) : nullptr;
+    const T* __restrict__ gref = DEF ? reinterpret_cast<const T*>(S.gref) : nullptr;
     // stage table and twist octant, in flight until the first barrier after
     // cp_async_wait_all() (INIT, ITER; the other phases do not read them)
-    const C2<T>* stw = sp + C::ROW_DATA;
+    const C2<F>* stw = sp + C::ROW_DATA;
     if (phase == PH_INIT || phase == PH_ITER) IO::load_tables(sp, tw);
     T acc[N_ACC];
 #pragma unroll
@@ -638,9 +663,15 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
           for (int c = 0; c < 4; c++) acc[A_E11 + c] += e[c];
           acc[A_NPL] += pl ? T(1) : T(0);
           c0_apply(e, m, c0);
-          IO::px(sp, 0, r, x1) = s[0] - c0[0];
-          IO::px(sp, 1, r, x1) = s[1] - c0[1];
-          IO::px(sp, 2, r, x1) = s[3] - c0[3];
+          if constexpr (DEF) {
+            IO::px(sp, 0, r, x1) = F((s[0] - c0[0]) - pref[x]);
+            IO::px(sp, 1, r, x1) = F((s[1] - c0[1]) - pref[LL + x]);
+            IO::px(sp, 2, r, x1) = F((s[3] - c0[3]) - pref[2 * LL + x]);
+          } else {
+            IO::px(sp, 0, r, x1) = s[0] - c0[0];
+            IO::px(sp, 1, r, x1) = s[1] - c0[1];
+            IO::px(sp, 2, r, x1) = s[3] - c0[3];
+          }
         }
     } else {  // PH_ITER
       T E[4];
@@ -660,6 +691,16 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
             if (ECHK(row, L, 39)) prefetch_l2(reinterpret_cast<const char*>(sin_ + (size_t)4 * row * L) + (size_t)(i % NPR) * PB, PB);
           }
           if (lane == 31) prefetch_l2(mask + (size_t)r0 * L, (unsigned)(RR * L));
+          if constexpr (DEF) {
+            // the RR rows of the three planes of g_ref and p_ref
+            constexpr unsigned QB = (unsigned)(RR * L * sizeof(T)), QP = QB < 16384u ? QB : 16384u;
+            constexpr int NQ = (int)(QB / QP);
+            for (int i = lane; i < 6 * NQ; i += 32) {
+              const int pl = i / NQ;
+              const T* base = (pl < 3 ? gref : pref) + (size_t)(pl % 3) * LL + (size_t)r0 * L;
+              prefetch_l2(reinterpret_cast<const char*>(base) + (size_t)(i % NQ) * QP, QP);
+            }
+          }
         }
       }
       // halo row x2 = r0 - 1: sigma12 and sigma22 of iterate n for the
@@ -706,6 +747,11 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
         acc[A_DIV2] += d1 * d1 + d2 * d2;
         // augmented-Lagrangian update of this pixel
         T e[4] = {IO::px(sp, 0, r, x1), IO::px(sp, 1, r, x1), E[2], IO::px(sp, 2, r, x1)};
+        if constexpr (DEF) {
+          e[0] += E[0] + gref[x];
+          e[1] += E[1] + gref[LL + x];
+          e[3] += E[3] + gref[2 * LL + x];
+        }
         T c0[4], tau[4], e1[4], s1[4], p1[3];
         c0_apply(e, m, c0);
 #pragma unroll
@@ -719,10 +765,17 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restri
         acc[A_NPL] += is_plastic(e1, v, m) ? T(1) : T(0);
         const T q0 = e1[0] - e[0], q1 = e1[1] - e[1], q2 = e1[2] - e[2], q3 = e1[3] - e[3];
         acc[A_COMP] += q0 * q0 + q1 * q1 + q2 * q2 + T(2) * q3 * q3;
-        // next polarization sigma(eps^{n+1}) - C0:eps^{n+1} (in-plane)
-        IO::px(sp, 0, r, x1) = p1[0];
-        IO::px(sp, 1, r, x1) = p1[1];
-        IO::px(sp, 2, r, x1) = p1[2];
+        // next polarization sigma(eps^{n+1}) - C0:eps^{n+1} (in-plane); the
+        // defect form transforms its difference from p_ref
+        if constexpr (DEF) {
+          IO::px(sp, 0, r, x1) = F(p1[0] - pref[x]);
+          IO::px(sp, 1, r, x1) = F(p1[1] - pref[LL + x]);
+          IO::px(sp, 2, r, x1) = F(p1[2] - pref[2 * LL + x]);
+        } else {
+          IO::px(sp, 0, r, x1) = p1[0];
+          IO::px(sp, 1, r, x1) = p1[1];
+          IO::px(sp, 2, r, x1) = p1[2];
+        }
       };
       // stress of iterate n and voids of row r, group j
       auto load_px = [&](int r, int j, T (&sg)[4], bool& v) {
@@ -947,9 +1000,12 @@ col_pass(Solve* __restrict__ solves, const C2<T>* __restrict__ tw, const C2<T>* 
         Bp[c] = conj(B[c]);
       }
       if (m2 == 0) {
-        A[0] = mk(T(Ep[0]), T(0));
-        A[1] = mk(T(Ep[1]), T(0));
-        A[2] = mk(T(Ep[3]), T(0));
+        // the mean strain, or 0 where it is added in FP64 after the
+        // transforms (the defect form and its reference)
+        const T z = S.zero_mean ? T(0) : T(1);
+        A[0] = mk(z * T(Ep[0]), T(0));
+        A[1] = mk(z * T(Ep[1]), T(0));
+        A[2] = mk(z * T(Ep[3]), T(0));
       } else {
         green_op(gm, ktab, qtab, L, 0, m2, lam0, mu0, scale, A[0], A[1], A[2]);
         green_op(gm, ktab, qtab, L, 0, mp, lam0, mu0, scale, Ap[0], Ap[1], Ap[2]);

@@ -43,7 +43,7 @@ constexpr size_t tab_bytes_all() {
 }
 // the tables of every side up to kMaxL in both precisions, one after another
 constexpr size_t kTabBytes = tab_bytes_all<float>() + tab_bytes_all<double>();
-constexpr size_t kSolveBytes = 512;
+constexpr size_t kSolveBytes = 768;
 constexpr size_t kPathBytes = 256;
 constexpr size_t kScratchBytes = kSpecBytes + kTabBytes + kSolveBytes + kPathBytes;
 static_assert(sizeof(Solve) <= kSolveBytes, "solve record must fit its slot");

@@ -42,6 +42,12 @@ def test_host_only_calls(lib):
     assert B.epfft_supported(256, "fp64") and B.epfft_supported(4096, "fp32")
     assert not B.epfft_supported(4096, "fp64")
     assert lib.epfft_supported(100, 1) == 0 and lib.epfft_supported(2, 1) == 0
+    # the defect-correction form: where both the FP32 passes and the FP64
+    # refresh are built, tilings 0 and 1 only
+    assert B.epfft_supported(2048, "fp32_defect") and not B.epfft_supported(4096, "fp32_defect")
+    assert B.epfft_supported_tiling(512, "fp32_defect", 1) and not B.epfft_supported_tiling(512, "fp32_defect", 2)
+    assert lib.epfft_supported(256, 3) == 0
+    assert lib.epfft_set_defect_refresh(None, 8) == B.EPFFT_ERR_ARG
 
 
 def test_no_cpu_fallback_without_device(lib):
@@ -91,7 +97,7 @@ def test_binding_constants_match_the_header():
     the header's value (status codes, precisions, operators, tests)."""
     src = open(os.path.join(ROOT, "include", "epfft.h")).read()
     defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(EPFFT_\w+)\s+\(?(-?\d+)\)?", src)}
-    assert "EPFFT_EQ_FIXED_POINT" in defs and "EPFFT_GREEN_DG1" in defs
+    assert "EPFFT_EQ_FIXED_POINT" in defs and "EPFFT_GREEN_DG1" in defs and "EPFFT_FP32_DEFECT" in defs
     named = [k for k in defs if hasattr(B, k)]
     assert len(named) >= 10
     for k in named:
