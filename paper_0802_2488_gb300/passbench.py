@@ -29,8 +29,10 @@ def measure(ctx, L: int, precision: str, f: float = 0.2, iters: int = 50, varian
     col_ms, row_ms = B.epfft_time_passes(ctx, prob, E, iters, n_batch=batch)
     n = L * L * batch
     lg = math.log2(L)
-    f64 = precision == "fp64"
-    row_b, col_b = (145 if f64 else 73) * n, (48 if f64 else 24) * n
+    # algorithmic bytes per pixel: FP32 row 73 / column 24, FP64 145 / 48,
+    # the defect form 169 (FP32 spectrum, FP64 state, p_ref and g_ref) / 24
+    row_b = {"fp64": 145, "fp32": 73, "fp32_defect": 169}[precision] * n
+    col_b = (48 if precision == "fp64" else 24) * n
     row_f, col_f = (15 * lg + 60) * n, (15 * lg + 25) * n
     return {
         "L": L, "precision": precision, "iters": iters, "variant": variant, "batch": batch,
