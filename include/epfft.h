@@ -59,16 +59,17 @@ extern "C" {
 
 #define EPFFT_FP64 0 /* FP64 fields, FFTs and reductions                        */
 #define EPFFT_FP32 1 /* FP32 fields and FFTs, FP64 reductions and macro values  */
-#define EPFFT_FP32_DEFECT 2 /* defect correction: FP64 strain, stress, local   *
-                             * step and reductions; the Green operator applied *
-                             * as g_ref + Gamma(p - p_ref), where the reference *
-                             * g_ref = Gamma(p_ref) is computed with FP64      *
-                             * transforms and refreshed to the current         *
-                             * polarization every epfft_set_defect_refresh     *
-                             * steps, and p - p_ref goes through FP32          *
-                             * transforms (Sec. 2 scheme; tolerances of the    *
-                             * FP64 form at FP32 transform cost).  Fields are  *
-                             * FP64; sides up to 2048; tilings 0 and 1.        */
+#define EPFFT_FP32_DEFECT 2 /* defect correction: FP32 iterations on the     *
+                             * differences of strain and stress from an FP64  *
+                             * reference state, which a refresh (FP64 law,    *
+                             * FP64 transforms of Eqs. 2-3) moves to the      *
+                             * current iterate after each warm start and      *
+                             * every epfft_set_defect_refresh iterations; the *
+                             * FP32 rounding then scales with the distance    *
+                             * from the reference, so the tolerances of the   *
+                             * FP64 form (Sec. 2) are reached at FP32 cost.   *
+                             * Fields are FP64; sides up to 2048; tilings 0   *
+                             * and 1.                                         */
 
 #define EPFFT_GREEN_EQ3 0 /* discrete Green operator of Eq. 3                   */
 #define EPFFT_GREEN_CG1 1 /* continuum operator (Sec. 2, CG1): Eq. 3 with the   *
@@ -507,16 +508,12 @@ int epfft_supported_tiling(int32_t L, int32_t precision, int32_t variant);
  * classes; EPFFT_ERR_UNSUPPORTED if it is not compiled for that size. */
 int epfft_set_tiling(epfft_ctx *ctx, int32_t L, int32_t precision, int32_t variant);
 
-/* Defect-correction form (EPFFT_FP32_DEFECT): loop steps between two
- * refreshes of the FP64 reference g_ref = Gamma(p_ref), p_ref the current
- * polarization of every solve in its iteration phase (default 64).  A
- * refresh costs about one FP64 transform pair of the lattice; the FP32
- * transforms' rounding grows with |p - p_ref|, so fewer steps between
- * refreshes let the iteration approach the FP64 scheme's fixed point more
- * closely.  With steps = 1 every iteration uses e = E + Gamma(p^n) in FP64
- * exactly like the FP64 form.  A device-driven solve (epfft_solve,
- * epfft_solve_batch) launches its loop graph once per `steps` loop steps.
- * EPFFT_ERR_ARG if steps < 1. */
+/* Defect-correction form (EPFFT_FP32_DEFECT): iterations of a solve between
+ * two refreshes of its FP64 reference (default 64), for solves set up after
+ * the call.  A refresh costs about one FP64 transform pair of the lattice
+ * and runs inside the device loop (a conditional node after the row pass),
+ * for each solve on its own schedule, so a solve's arithmetic does not
+ * depend on the other solves of a batch.  EPFFT_ERR_ARG if steps < 1. */
 int epfft_set_defect_refresh(epfft_ctx *ctx, int32_t steps);
 
 #ifdef __cplusplus

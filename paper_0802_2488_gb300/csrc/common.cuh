@@ -62,6 +62,8 @@ enum Phase : int32_t {
   PH_ITER = 1,   // augmented-Lagrangian iterations of increment `inc`
   PH_FINAL = 2,  // write the plastic flags of the last accepted state
   PH_DONE = 3,
+  PH_REF = 4,    // defect form: waits for the refresh of its reference (the
+                 // passes skip it; the refresh sets PH_ITER)
 };
 
 // Per-increment result, written by the device (layout of epfft_record).
@@ -103,6 +105,10 @@ enum MatConst : int {
   MC_P_VOID,      // -3 K0: the same for a void pixel
   MC_GSC_EL,      // mu / (mu + mu0): 2 mu times the elastic deviator scale of the local step
   MC_3K,          // 3 K
+  MC_TSTAR,       // sqrt(2/3) Y (mu + mu0) / mu: |tau'| where the local step turns plastic
+  MC_TSTAR2,      // its square
+  MC_RY,          // sqrt(2/3) Y / (2 mu0)
+  MC_JC,          // mu / ((mu + mu0) 2 mu0)
   N_MC
 };
 
@@ -124,19 +130,31 @@ struct Solve {
   void* sig[2];        // sigma of the same iterates (the multiplier), L*L*4 reals
   void* spec;          // 3 * L * L/2 complex, tiled column layout
   double* partials;    // n_row_ctas * PART_STRIDE
-  // defect-correction form (FP64 state, FP32 transforms): the reference
-  // polarization p_ref and its compatible strain g_ref = Gamma(p_ref), three
-  // FP64 planes (11, 22, 12) of L * L each, and the FP64 spectrum of the
-  // reference transform; null otherwise
-  void* pref;
-  void* gref;
+  // defect-correction form (dcpass.cuh): the FP64 reference state eps_ref,
+  // sigma_ref (4 reals per pixel; eps[0] = eps[1] = eref, sig[0] = sig[1] =
+  // sref, so that the fields of the final state are read from there), the
+  // FP32 differences of the iterates from it (ping-pong, 4 floats per
+  // pixel), the FP32 per-pixel data of the reference (base[0]: float4
+  // deviator of tau_ref (11, 22, 12) and |tau_ref'|^2 - T*^2; base[1]:
+  // float4 e_ref - eps_ref; base[2]: float2 div sigma_ref), the FP64
+  // spectrum of the reference transform, per-CTA partial sums of a refresh
+  // and the sums of sigma_ref and eps_ref; null / zero otherwise
+  void* eref;
+  void* sref;
+  void* deps[2];
+  void* dsig[2];
+  void* base[3];
   void* spec64;
+  double* refpart;
+  double ref_sum[8];
   int32_t zero_mean;   // 1: the column pass puts 0 at q = 0 (not the mean strain)
-  int32_t pad0;
+  int32_t ref_every;   // defect form: iterations between refreshes of the reference
   // mutable state
   int32_t phase, inc, iter, cur;
   int32_t status;
   uint32_t arrive;
+  int32_t since_ref;    // defect form: iterations since the last refresh
+  int32_t pad1;
   double Eprev[4];
   double sig_prev[4];
   double comp_cur;      // mean fixed-point residual of iterate n (eta3^2 EE)
@@ -153,6 +171,9 @@ struct BatchCtl {
   int64_t max_body_iters;   // bound on loop steps (a solve needs at most
                             // n_inc * (max_iter + 2) + 1)
   int32_t timed_out;        // the bound stopped the loop with work left
+  int32_t waiting;          // defect form: solves waiting for a refresh (PH_REF)
+  int64_t refresh_runs;     // defect form: executions of the loop body's refresh node
+  int32_t dc;               // 1: a defect batch (a mixed graph's refresh node covers it)
   int32_t pad;
 };
 

@@ -245,6 +245,10 @@ void fill_consts(Solve& S) {
   c[MC_P_VOID] = -3.0 * K0;
   c[MC_GSC_EL] = S.mu / (S.mu + S.mu0);
   c[MC_3K] = 3.0 * K;
+  c[MC_TSTAR] = yl * (S.mu + S.mu0) / S.mu;
+  c[MC_TSTAR2] = std::isinf(yl) ? yl : c[MC_TSTAR] * c[MC_TSTAR];
+  c[MC_RY] = yl / (2.0 * S.mu0);
+  c[MC_JC] = S.mu / ((S.mu + S.mu0) * 2.0 * S.mu0);
   for (int i = 0; i < N_MC; i++) S.mcf[i] = (float)c[i];
 }
 
@@ -265,7 +269,7 @@ struct Batch {
   int var64 = 0;
   Solve* d_shadow = nullptr;
   std::vector<Solve> h_shadow;  // serving: host copy of the shadow slots
-  int64_t refreshes = 0;
+  int64_t refreshes = 0;  // refreshes launched from the host (fixed-step loops)
   std::vector<Solve> h_solves;
   std::vector<int32_t> n_inc;
   std::vector<int32_t*> d_labels;  // per solve, n_inc * L * L (allocated on demand)
@@ -276,9 +280,13 @@ cudaError_t col_of(Batch& B, cudaStream_t s, cudaGraphConditionalHandle h, int u
   if (B.prec == EPFFT_FP64) return launch_col<double>(B.L, B.var, B.nb, s, B.d_solves, B.tw, B.ktab, h, use_cond, B.general);
   return launch_col<float>(B.L, B.var, B.nb, s, B.d_solves, B.tw, B.ktab, h, use_cond, B.general);
 }
-cudaError_t row_of(Batch& B, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
+// hr / use_hr: the condition of the refresh node that follows the row pass
+// of a defect batch in a loop body.
+cudaError_t row_of(Batch& B, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond,
+                   cudaGraphConditionalHandle hr = 0, int use_hr = 0) {
   if (B.prec == EPFFT_FP64) return launch_row<double>(B.L, B.var, B.nb, s, B.d_solves, B.d_ctl, B.tw, h, use_cond);
-  if (B.prec == EPFFT_FP32_DEFECT) return launch_row_def(B.L, B.var, B.nb, s, B.d_solves, B.d_ctl, B.tw, h, use_cond);
+  if (B.prec == EPFFT_FP32_DEFECT)
+    return launch_row_def(B.L, B.var, B.nb, s, B.d_solves, B.d_ctl, B.tw, h, use_cond, hr, use_hr);
   return launch_row<float>(B.L, B.var, B.nb, s, B.d_solves, B.d_ctl, B.tw, h, use_cond);
 }
 
@@ -289,16 +297,19 @@ int launch_body(epfft_ctx* c, Batch& B, cudaStream_t s, cudaGraphConditionalHand
   return EPFFT_OK;
 }
 
-// Refresh of the defect form's reference (defect.cuh) for every solve of
-// the batch in its iteration phase: FP64 row transform of the current
+// Refresh of the defect form's reference (dcpass.cuh) for every solve of
+// the batch that waits for it (PH_REF: after a warm start, or ref_every
+// iterations after its last refresh; the kernels skip the others): the
+// latest iterate becomes the reference; FP64 row transform of its
 // polarization, FP64 column pass on the shadow solves, FP64 inverse row
-// transform into g_ref.  No-op for other precisions.
+// transform into the reference data, the reference sums.  No-op for other
+// precisions.
 int refresh_defect(Batch& B, cudaStream_t s) {
   if (B.prec != EPFFT_FP32_DEFECT) return EPFFT_OK;
   CK(launch_ref_forward(B.L, B.var64, B.nb, s, B.d_solves, B.d_shadow, B.tw64));
   CK(launch_col<double>(B.L, B.var64, B.nb, s, B.d_shadow, B.tw64, B.ktab64, 0, 0, B.general));
   CK(launch_ref_inverse(B.L, B.var64, B.nb, s, B.d_solves, B.tw64));
-  B.refreshes += 1;
+  CK(launch_ref_sums(B.L, B.var64, B.nb, s, B.d_solves));
   return EPFFT_OK;
 }
 
@@ -306,9 +317,13 @@ int refresh_defect(Batch& B, cudaStream_t s) {
 size_t solve_footprint(int L, int prec, int row_ctas, int n_inc) {
   const size_t LL = (size_t)L * L, rs = real_size(prec);
   auto r = [](size_t b) { return (b + 511) & ~(size_t)511; };
-  // the defect form adds p_ref, g_ref and the FP64 spectrum
-  const size_t def = prec == EPFFT_FP32_DEFECT ? 3 * r(3 * LL * 8) : 0;
-  return r(4 * LL * rs) * 4 + r(3 * LL * spec_real_size(prec)) + def +
+  // the defect form: one FP64 reference state, four FP32 difference fields,
+  // the reference data, the FP64 spectrum and the refresh records
+  const size_t states = prec == EPFFT_FP32_DEFECT
+                            ? r(4 * LL * 8) * 2 + r(4 * LL * 4) * 6 + r(2 * LL * 4) + r(3 * LL * 8) +
+                                  r(sizeof(double) * PART_STRIDE * (size_t)L)
+                            : r(4 * LL * rs) * 4;
+  return states + r(3 * LL * spec_real_size(prec)) +
          r(sizeof(double) * PART_STRIDE * (size_t)row_ctas) + r(LL) + r(LL * (size_t)n_inc) +
          r(sizeof(double) * 4 * (size_t)n_inc) + r(sizeof(Record) * (size_t)n_inc);
 }
@@ -333,10 +348,13 @@ int init_solve(Get&& get, const PassShape& sh, int L, int prec, const epfft_prob
   S.green = p.green;
   S.eq_fixed_point = p.eq_test == EPFFT_EQ_FIXED_POINT || p.green == EPFFT_GREEN_CG1 || p.green == EPFFT_GREEN_DG1;
   fill_consts(S);
+  const bool dc = prec == EPFFT_FP32_DEFECT;
+  // the defect form keeps one FP64 reference state (eps_ref, sigma_ref) and
+  // the FP32 differences from it; the others two ping-pong states
   void* eps0d = get(4 * LL * rs);
-  void* eps1d = get(4 * LL * rs);
+  void* eps1d = dc ? eps0d : get(4 * LL * rs);
   void* sig0d = get(4 * LL * rs);
-  void* sig1d = get(4 * LL * rs);
+  void* sig1d = dc ? sig0d : get(4 * LL * rs);
   void* spec = get(3 * LL * spec_real_size(prec));
   double* part = (double*)get(sizeof(double) * PART_STRIDE * (size_t)sh.row_ctas);
   uint8_t* mask = (uint8_t*)get(LL);
@@ -356,15 +374,24 @@ int init_solve(Get&& get, const PassShape& sh, int L, int prec, const epfft_prob
   S.path = dpath;
   S.rec = rec;
   S.phase = PH_INIT;
-  if (prec == EPFFT_FP32_DEFECT) {
-    // reference p_ref = 0, g_ref = 0 until the first refresh
-    S.pref = get(3 * LL * 8);
-    S.gref = get(3 * LL * 8);
+  if (dc) {
+    S.eref = eps0d;
+    S.sref = sig0d;
+    for (int k = 0; k < 2; k++) {
+      S.deps[k] = get(4 * LL * 4);
+      S.dsig[k] = get(4 * LL * 4);
+      if (!S.deps[k] || !S.dsig[k]) return EPFFT_ERR_OOM;
+      CK(cudaMemsetAsync(S.deps[k], 0, 4 * LL * 4, s));
+      CK(cudaMemsetAsync(S.dsig[k], 0, 4 * LL * 4, s));
+    }
+    S.base[0] = get(4 * LL * 4);
+    S.base[1] = get(4 * LL * 4);
+    S.base[2] = get(2 * LL * 4);
     S.spec64 = get(3 * LL * 8);
-    if (!S.pref || !S.gref || !S.spec64) return EPFFT_ERR_OOM;
+    // one record per row CTA of the refresh (at most L)
+    S.refpart = (double*)get(sizeof(double) * PART_STRIDE * (size_t)L);
+    if (!S.base[0] || !S.base[1] || !S.base[2] || !S.spec64 || !S.refpart) return EPFFT_ERR_OOM;
     S.zero_mean = 1;
-    CK(cudaMemsetAsync(S.pref, 0, 3 * LL * 8, s));
-    CK(cudaMemsetAsync(S.gref, 0, 3 * LL * 8, s));
   }
   CK(cudaMemcpyAsync(dpath, path, sizeof(double) * 4 * (size_t)n_inc, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(rec, 0, sizeof(Record) * (size_t)n_inc, s));
@@ -414,6 +441,7 @@ int setup_batch(epfft_ctx* c, Arena& A, Batch& B, int n, const epfft_problem* pr
     rc = init_solve([&](size_t b) { return A.get(b); }, B.sh, B.L, B.prec, p, paths[i].E, paths[i].n_inc,
                     eps0 ? eps0[i] : nullptr, c->stream, B.h_solves[i]);
     if (rc) return rc;
+    B.h_solves[i].ref_every = c->defect_refresh;
     const int64_t need = (int64_t)paths[i].n_inc * ((int64_t)p.max_iter + 2) + 1;
     if (need > max_body) max_body = need;
   }
@@ -439,9 +467,45 @@ int setup_batch(epfft_ctx* c, Arena& A, Batch& B, int n, const epfft_problem* pr
   std::memset(&bc, 0, sizeof(bc));
   bc.active = n;
   bc.max_body_iters = max_body + 8;
+  bc.dc = B.prec == EPFFT_FP32_DEFECT;
   B.max_body = bc.max_body_iters;
   CK(cudaMemcpyAsync(B.d_ctl, &bc, sizeof(bc), cudaMemcpyHostToDevice, c->stream));
   return EPFFT_OK;
+}
+
+// Appends to `body` (after its one leaf node) a conditional IF node on hr
+// whose graph runs the refresh of every defect batch of Bs (refresh_defect).
+int add_refresh_node(epfft_ctx* c, cudaGraph_t body, cudaGraphConditionalHandle hr, std::vector<Batch*>& Bs) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(body, nullptr, &n) != cudaSuccess || n == 0) return EPFFT_ERR_CUDA;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(body, nodes.data(), &n) != cudaSuccess) return EPFFT_ERR_CUDA;
+  cudaGraphNode_t leaf = nullptr;
+  int leaves = 0;
+  for (auto nd : nodes) {
+    size_t k = 0;
+    if (cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &k) != cudaSuccess) return EPFFT_ERR_CUDA;
+    if (k == 0) {
+      leaf = nd;
+      leaves++;
+    }
+  }
+  if (leaves != 1) return EPFFT_ERR_CUDA;
+  cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
+  ip.conditional.handle = hr;
+  ip.conditional.type = cudaGraphCondTypeIf;
+  ip.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, body, &leaf, nullptr, 1, &ip) != cudaSuccess) return EPFFT_ERR_CUDA;
+  cudaGraph_t rb = ip.conditional.phGraph_out[0];
+  if (cudaStreamBeginCaptureToGraph(c->cap, rb, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return EPFFT_ERR_CUDA;
+  int lrc = EPFFT_OK;
+  for (Batch* b : Bs)
+    if (!lrc && b->prec == EPFFT_FP32_DEFECT) lrc = refresh_defect(*b, c->cap);
+  cudaGraph_t captured = nullptr;
+  cudaError_t ec = cudaStreamEndCapture(c->cap, &captured);
+  return (lrc != EPFFT_OK || ec != cudaSuccess) ? EPFFT_ERR_CUDA : EPFFT_OK;
 }
 
 // One CUDA graph whose while node repeats [column pass, row pass] over the
@@ -469,17 +533,33 @@ int build_loop_graph(epfft_ctx* c, Batch& B, cudaGraph_t* graph_out, cudaGraphEx
       break;
     }
     body = cp.conditional.phGraph_out[0];
+    const bool dc = B.prec == EPFFT_FP32_DEFECT;
+    cudaGraphConditionalHandle hr = 0;
+    if (dc && cudaGraphConditionalHandleCreate(&hr, graph, 0, 0) != cudaSuccess) {
+      rc = EPFFT_ERR_CUDA;
+      break;
+    }
     if (cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
         cudaSuccess) {
       rc = EPFFT_ERR_CUDA;
       break;
     }
-    int lrc = launch_body(c, B, c->cap, h, 1);
+    int lrc = col_of(B, c->cap, h, 1) == cudaSuccess ? EPFFT_OK : EPFFT_ERR_CUDA;
+    if (!lrc && row_of(B, c->cap, h, 1, hr, dc ? 1 : 0) != cudaSuccess) lrc = EPFFT_ERR_CUDA;
     cudaGraph_t captured = nullptr;
     cudaError_t ec = cudaStreamEndCapture(c->cap, &captured);
     if (lrc != EPFFT_OK || ec != cudaSuccess) {
       rc = EPFFT_ERR_CUDA;
       break;
+    }
+    // the defect form: after the row pass, the refresh of the solves that
+    // wait for it, when the row pass set its condition
+    if (dc) {
+      std::vector<Batch*> one{&B};
+      if (add_refresh_node(c, body, hr, one) != EPFFT_OK) {
+        rc = EPFFT_ERR_CUDA;
+        break;
+      }
     }
     if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
       rc = EPFFT_ERR_CUDA;
@@ -498,18 +578,12 @@ int build_loop_graph(epfft_ctx* c, Batch& B, cudaGraph_t* graph_out, cudaGraphEx
 }
 
 // Runs the device-side loop of a batch to completion (one graph launch).
-int run_chunked(epfft_ctx* c, std::vector<Batch*>& Bs, cudaGraphExec_t exec);
-
 int run_graph(epfft_ctx* c, Batch& B) {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int rc = build_loop_graph(c, B, &graph, &exec);
   if (rc) return rc;
-  if (B.prec == EPFFT_FP32_DEFECT) {
-    std::vector<Batch*> one{&B};
-    rc = run_chunked(c, one, exec);
-    if (rc) cudaGetLastError();
-  } else if (cudaGraphLaunch(exec, c->stream) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
+  if (cudaGraphLaunch(exec, c->stream) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
     rc = EPFFT_ERR_CUDA;
     cudaGetLastError();
   }
@@ -520,13 +594,24 @@ int run_graph(epfft_ctx* c, Batch& B) {
 
 // Loop condition of a graph over several batches (sizes, precisions): go on
 // while some batch has a solve that is not done and steps left.  One thread.
-__global__ void loop_decide_kernel(BatchCtl* const* ctl, int n, cudaGraphConditionalHandle h) {
-  bool go = false;
+// With defect batches (use_hr), the condition hr of the refresh node that
+// follows: some defect solve waits for its refresh.
+__global__ void loop_decide_kernel(BatchCtl* const* ctl, int n, cudaGraphConditionalHandle h,
+                                   cudaGraphConditionalHandle hr, int use_hr) {
+  bool go = false, wait = false;
   for (int g = 0; g < n; g++) {
     const volatile BatchCtl* b = ctl[g];
     if (b->active > 0 && b->body_iters < b->max_body_iters) go = true;
+    wait |= b->dc && b->waiting > 0;
   }
   cudaGraphSetConditional(h, go ? 1u : 0u);
+  if (use_hr) {
+    cudaGraphSetConditional(hr, wait ? 1u : 0u);
+    // the refresh node refreshes every defect batch of the graph
+    if (wait)
+      for (int g = 0; g < n; g++)
+        if (ctl[g]->dc) ctl[g]->refresh_runs += 1;
+  }
 }
 
 // One CUDA graph that advances several batches of different lattice sides or
@@ -548,14 +633,17 @@ int build_mixed_graph(epfft_ctx* c, std::vector<Batch*>& Bs, BatchCtl** dctl, cu
   for (auto& e : ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  bool dc = false;
+  for (Batch* b : Bs) dc |= b->prec == EPFFT_FP32_DEFECT;
   int rc = EPFFT_OK;
   do {
     if (cudaGraphCreate(&graph, 0) != cudaSuccess) {
       rc = EPFFT_ERR_CUDA;
       break;
     }
-    cudaGraphConditionalHandle h;
-    if (cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+    cudaGraphConditionalHandle h, hr = 0;
+    if (cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess ||
+        (dc && cudaGraphConditionalHandleCreate(&hr, graph, 0, 0) != cudaSuccess)) {
       rc = EPFFT_ERR_CUDA;
       break;
     }
@@ -582,12 +670,17 @@ int build_mixed_graph(epfft_ctx* c, std::vector<Batch*>& Bs, BatchCtl** dctl, cu
       if (!lrc && cudaStreamWaitEvent(c->cap, ev[g], 0) != cudaSuccess) lrc = EPFFT_ERR_CUDA;
     }
     if (!lrc) {
-      loop_decide_kernel<<<1, 1, 0, c->cap>>>(dctl, G, h);
+      loop_decide_kernel<<<1, 1, 0, c->cap>>>(dctl, G, h, hr, dc ? 1 : 0);
       if (cudaGetLastError() != cudaSuccess) lrc = EPFFT_ERR_CUDA;
     }
     cudaGraph_t captured = nullptr;
     cudaError_t ec = cudaStreamEndCapture(c->cap, &captured);
     if (lrc != EPFFT_OK || ec != cudaSuccess) {
+      rc = EPFFT_ERR_CUDA;
+      break;
+    }
+    // defect batches: the refresh node after the loop-condition kernel
+    if (dc && add_refresh_node(c, body, hr, Bs) != EPFFT_OK) {
       rc = EPFFT_ERR_CUDA;
       break;
     }
@@ -621,12 +714,7 @@ int run_mixed_graph(epfft_ctx* c, Arena& A, std::vector<Batch*>& Bs) {
   cudaGraphExec_t exec = nullptr;
   int rc = build_mixed_graph(c, Bs, dctl, &graph, &exec);
   if (rc) return rc;
-  bool defect = false;
-  for (Batch* b : Bs) defect |= b->prec == EPFFT_FP32_DEFECT;
-  if (defect) {
-    rc = run_chunked(c, Bs, exec);
-    if (rc) cudaGetLastError();
-  } else if (cudaGraphLaunch(exec, c->stream) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
+  if (cudaGraphLaunch(exec, c->stream) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
     rc = EPFFT_ERR_CUDA;
     cudaGetLastError();
   }
@@ -642,52 +730,17 @@ int run_mixed_graph(epfft_ctx* c, Arena& A, std::vector<Batch*>& Bs) {
 // number of iterations), so the passes are ordinary stream launches.
 int run_host_loop(epfft_ctx* c, Batch& B, int64_t steps) {
   for (int64_t k = 0; k < steps; k++) {
-    // the defect form refreshes its reference every defect_refresh steps
-    if (k % c->defect_refresh == 0 && refresh_defect(B, c->stream)) return EPFFT_ERR_CUDA;
     cudaError_t e = col_of(B, c->stream, 0, 0);
     if (e == cudaSuccess) e = row_of(B, c->stream, 0, 0);
     if (e != cudaSuccess) return EPFFT_ERR_CUDA;
+    // the defect form: the refresh of the solves that wait for it
+    if (B.prec == EPFFT_FP32_DEFECT) {
+      if (refresh_defect(B, c->stream)) return EPFFT_ERR_CUDA;
+      B.refreshes += 1;
+    }
   }
   CK(cudaStreamSynchronize(c->stream));
   return EPFFT_OK;
-}
-
-// The device-side loop of the defect form: the graph (single batch or
-// mixed) runs defect_refresh loop steps at a time, and the references of the
-// defect batches are refreshed between the launches, until every solve is
-// done or a batch reaches its step bound.
-int run_chunked(epfft_ctx* c, std::vector<Batch*>& Bs, cudaGraphExec_t exec) {
-  const int G = (int)Bs.size();
-  std::vector<BatchCtl> bc(G);
-  for (int g = 0; g < G; g++) CK(cudaMemcpyAsync(&bc[g], Bs[g]->d_ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  for (;;) {
-    for (int g = 0; g < G; g++) {
-      bc[g].max_body_iters = std::min<int64_t>(bc[g].body_iters + c->defect_refresh, Bs[g]->max_body);
-      bc[g].timed_out = 0;
-      CK(cudaMemcpyAsync(Bs[g]->d_ctl, &bc[g], sizeof(BatchCtl), cudaMemcpyHostToDevice, c->stream));
-    }
-    CK(cudaGraphLaunch(exec, c->stream));
-    for (int g = 0; g < G; g++) CK(cudaMemcpyAsync(&bc[g], Bs[g]->d_ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    bool live = false, bound = false;
-    for (int g = 0; g < G; g++) {
-      live |= bc[g].active > 0;
-      bound |= bc[g].active > 0 && bc[g].body_iters >= Bs[g]->max_body;
-    }
-    if (!live) return EPFFT_OK;
-    if (bound) {
-      // the step bound stopped a batch with work left
-      for (int g = 0; g < G; g++) {
-        bc[g].timed_out = bc[g].active > 0 ? 1 : 0;
-        CK(cudaMemcpyAsync(Bs[g]->d_ctl, &bc[g], sizeof(BatchCtl), cudaMemcpyHostToDevice, c->stream));
-      }
-      CK(cudaStreamSynchronize(c->stream));
-      return EPFFT_OK;
-    }
-    for (int g = 0; g < G; g++)
-      if (refresh_defect(*Bs[g], c->stream)) return EPFFT_ERR_CUDA;
-  }
 }
 
 // Diagnostic loop (EPFFT_SYNC_CHECK=1 in the environment): the same passes
@@ -699,7 +752,12 @@ int run_checked(epfft_ctx* c, Batch& B) {
   for (int64_t step = 0;; step++) {
     CK(cudaMemcpy(hs.data(), B.d_solves, sizeof(Solve) * B.nb, cudaMemcpyDeviceToHost));
     cudaError_t e = cudaSuccess;
-    if (step % c->defect_refresh == 0 && refresh_defect(B, c->stream)) e = cudaErrorUnknown;
+    bool wait = false;
+    for (const Solve& z : hs) wait |= z.phase == PH_REF;
+    if (wait) {
+      if (refresh_defect(B, c->stream)) e = cudaErrorUnknown;
+      B.refreshes += 1;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
       fprintf(stderr, "epfft check: refresh failed at step %lld (phase %d inc %d iter %d): %s\n",
@@ -883,7 +941,8 @@ int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_
       k += 2 * bc[g].body_iters;
     }
     if (G > 1) k += steps;  // the loop-condition kernel of the mixed graph
-    for (int g = 0; g < G; g++) k += 3 * Bs[g].refreshes;  // the defect form's refreshes
+    // the defect form's refreshes: from the host, and the loop body's node
+    for (int g = 0; g < G; g++) k += 4 * (Bs[g].refreshes + bc[g].refresh_runs);
     // per solve the mask kernel (when generated) and the four labelling kernels
     for (int i = 0; i < n; i++) k += (probs[i].mask ? 0 : 1) + 4;
     c->last.loop_steps = steps;
@@ -940,8 +999,10 @@ int time_passes_impl(epfft_ctx* ctx, epfft_problem p, int n_batch, const double 
   int rc = setup_batch(ctx, A, B, n_batch, ps.data(), paths.data(), nullptr);
   if (rc) return rc;
   const int nb = n_batch;
-  // first row pass: warm start (eps = E, spectrum of its polarization)
+  // first row pass: warm start (eps = E, spectrum of its polarization); the
+  // defect form then refreshes its reference
   CK(row_of(B, ctx->stream, 0, 0));
+  if (refresh_defect(B, ctx->stream)) return EPFFT_ERR_CUDA;
   std::vector<cudaEvent_t> ev(3 * (size_t)n_iter);
   for (auto& e : ev) CK(cudaEventCreate(&e));
   for (int it = 0; it < n_iter; it++) {
@@ -1183,6 +1244,7 @@ int serve_admit(epfft_ctx* c, Server& S) {
       sl.blocks.clear();
       return rc;
     }
+    hs.ref_every = c->defect_refresh;
     k->B.h_solves[slot] = hs;
     k->B.n_inc[slot] = (int)(t.path.size() / 4);
     CK(cudaMemcpyAsync(k->B.d_solves + slot, &k->B.h_solves[slot], sizeof(Solve), cudaMemcpyHostToDevice,
@@ -2011,6 +2073,7 @@ int epfft_serve_step(epfft_ctx* ctx, int32_t* n_running, int32_t* n_queued) {
       std::memset(&bcs[i], 0, sizeof(BatchCtl));
       bcs[i].active = used;
       bcs[i].max_body_iters = S.steps;
+      bcs[i].dc = k->prec == EPFFT_FP32_DEFECT;
       CK(cudaMemcpyAsync(k->B.d_ctl, &bcs[i], sizeof(BatchCtl), cudaMemcpyHostToDevice, ctx->stream));
     }
     CK(cudaGraphLaunch(S.exec, ctx->stream));
@@ -2022,13 +2085,8 @@ int epfft_serve_step(epfft_ctx* ctx, int32_t* n_running, int32_t* n_queued) {
     ctx->last.loop_steps = steps;
     // a column and a row pass of every class, and the loop-condition kernel, per step
     ctx->last.kernel_launches += (2 * (int64_t)S.order.size() + 1) * steps;
-    // the defect classes refresh their references between steps
-    for (ServeClass* k : live)
-      if (k->prec == EPFFT_FP32_DEFECT) {
-        rc = refresh_defect(k->B, ctx->stream);
-        if (rc) return rc;
-        ctx->last.kernel_launches += 3;
-      }
+    // the defect classes' refresh node
+    for (size_t i = 0; i < S.order.size(); i++) ctx->last.kernel_launches += 4 * bcs[i].refresh_runs;
   }
   {
     CheckRec cr;

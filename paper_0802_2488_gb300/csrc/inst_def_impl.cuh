@@ -1,8 +1,8 @@
-// Instantiation of the defect-correction kernels (defect.cuh) for one
+// Instantiation of the defect-correction kernels (dcpass.cuh) for one
 // tiling variant EPFFT_VAR over the supported lattice sides: the row pass
-// with FP64 state and FP32 transforms, and the FP64 row halves of a refresh.
+// on the FP32 differences, and the FP64 steps of a refresh.
 #pragma once
-#include "defect.cuh"
+#include "dcpass.cuh"
 #include "launch.cuh"
 
 namespace epfft {
@@ -14,13 +14,13 @@ template <int L>
 static cudaError_t prepare_def_L() {
   constexpr int V = EPFFT_VAR;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(row_pass<double, L, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((e = cudaFuncSetAttribute(row_pass_dc<L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Cfg<float, L, V>::ROW_SMEM)) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(ref_forward<L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((e = cudaFuncSetAttribute(dc_ref_forward<L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Cfg<double, L, V>::ROW_SMEM)) != cudaSuccess)
     return e;
-  return cudaFuncSetAttribute(ref_inverse<L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(dc_ref_inverse<L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)Cfg<double, L, V>::ROW_SMEM);
 }
 
@@ -36,13 +36,14 @@ cudaError_t prepare_def_v<EPFFT_VAR>(int L) {
 
 template <>
 cudaError_t launch_row_def_v<EPFFT_VAR>(int L, int nb, cudaStream_t s, Solve* solves, BatchCtl* bc, const void* tw,
-                                       cudaGraphConditionalHandle cond, int use_cond) {
+                                       cudaGraphConditionalHandle cond, int use_cond,
+                                       cudaGraphConditionalHandle rcond, int use_rcond) {
   switch (L) {
 #define X(n)                                                                                             \
   case n: {                                                                                              \
     using C = Cfg<float, n, EPFFT_VAR>;                                                                  \
-    row_pass<double, n, EPFFT_VAR, true><<<dim3(n / C::RR, nb), C::NT_ROW, C::ROW_SMEM, s>>>(           \
-        solves, nb, bc, reinterpret_cast<const C2<float>*>(tw), cond, use_cond);                         \
+    row_pass_dc<n, EPFFT_VAR><<<dim3(n / C::RR, nb), C::NT_ROW, C::ROW_SMEM, s>>>(                      \
+        solves, nb, bc, reinterpret_cast<const C2<float>*>(tw), cond, use_cond, rcond, use_rcond);       \
     return cudaGetLastError();                                                                           \
   }
     EPFFT_DEF_FOR_L(X)
@@ -58,7 +59,7 @@ cudaError_t launch_ref_forward_v<EPFFT_VAR>(int L, int nb, cudaStream_t s, Solve
 #define X(n)                                                                                             \
   case n: {                                                                                              \
     using C = Cfg<double, n, EPFFT_VAR>;                                                                 \
-    ref_forward<n, EPFFT_VAR><<<dim3(n / C::RR, nb), C::NT_ROW, C::ROW_SMEM, s>>>(                      \
+    dc_ref_forward<n, EPFFT_VAR><<<dim3(n / C::RR, nb), C::NT_ROW, C::ROW_SMEM, s>>>(                   \
         solves, shadow, reinterpret_cast<const C2<double>*>(tw64));                                      \
     return cudaGetLastError();                                                                           \
   }
@@ -74,9 +75,23 @@ cudaError_t launch_ref_inverse_v<EPFFT_VAR>(int L, int nb, cudaStream_t s, Solve
 #define X(n)                                                                                             \
   case n: {                                                                                              \
     using C = Cfg<double, n, EPFFT_VAR>;                                                                 \
-    ref_inverse<n, EPFFT_VAR><<<dim3(n / C::RR, nb), C::NT_ROW, C::ROW_SMEM, s>>>(                      \
+    dc_ref_inverse<n, EPFFT_VAR><<<dim3(n / C::RR, nb), C::NT_ROW, C::ROW_SMEM, s>>>(                   \
         solves, reinterpret_cast<const C2<double>*>(tw64));                                              \
     return cudaGetLastError();                                                                           \
+  }
+    EPFFT_DEF_FOR_L(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <>
+cudaError_t launch_ref_sums_v<EPFFT_VAR>(int L, int nb, cudaStream_t s, Solve* solves) {
+  switch (L) {
+#define X(n)                                                  \
+  case n: {                                                   \
+    dc_ref_sums<n, EPFFT_VAR, 128><<<nb, 128, 0, s>>>(solves); \
+    return cudaGetLastError();                                \
   }
     EPFFT_DEF_FOR_L(X)
 #undef X

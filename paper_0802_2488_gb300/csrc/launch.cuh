@@ -44,20 +44,23 @@ cudaError_t launch_row_inverse_v(int L, cudaStream_t s, const void* spec, void* 
 template <typename T, int V>
 cudaError_t read_check_v(CheckRec* out);
 
-// Defect-correction form (defect.cuh), tilings 0 and 1: the row pass with
-// FP64 state and FP32 transforms (the FP32 tile shapes of tiling V; its
-// column pass is the FP32 one), and the two FP64 row halves of a refresh
-// (the FP64 tile shapes of tiling V; between them runs the FP64 column pass).
+// Defect-correction form (dcpass.cuh), tilings 0 and 1: the row pass on the
+// FP32 differences (the FP32 tile shapes of tiling V; its column pass is the
+// FP32 one), and the FP64 steps of a refresh (the FP64 tile shapes of tiling
+// V: forward row half, the FP64 column pass, inverse row half, the sums).
 constexpr int N_DEF_VARIANTS = 2;
 template <int V>
 cudaError_t prepare_def_v(int L);
 template <int V>
 cudaError_t launch_row_def_v(int L, int nb, cudaStream_t s, Solve* solves, BatchCtl* bc, const void* tw,
-                             cudaGraphConditionalHandle cond, int use_cond);
+                             cudaGraphConditionalHandle cond, int use_cond, cudaGraphConditionalHandle rcond,
+                             int use_rcond);
 template <int V>
 cudaError_t launch_ref_forward_v(int L, int nb, cudaStream_t s, Solve* solves, Solve* shadow, const void* tw64);
 template <int V>
 cudaError_t launch_ref_inverse_v(int L, int nb, cudaStream_t s, Solve* solves, const void* tw64);
+template <int V>
+cudaError_t launch_ref_sums_v(int L, int nb, cudaStream_t s, Solve* solves);
 template <int V>
 cudaError_t read_check_def_v(CheckRec* out);
 
@@ -71,10 +74,11 @@ inline cudaError_t prepare_def(int L, int var) {
 }
 template <int D = 0>  // a template, so that the variants may be specialised after it
 inline cudaError_t launch_row_def(int L, int var, int nb, cudaStream_t s, Solve* solves, BatchCtl* bc,
-                                  const void* tw, cudaGraphConditionalHandle cond, int use_cond) {
+                                  const void* tw, cudaGraphConditionalHandle cond, int use_cond,
+                                  cudaGraphConditionalHandle rcond, int use_rcond) {
   switch (var) {
-    case 0: return launch_row_def_v<0>(L, nb, s, solves, bc, tw, cond, use_cond);
-    case 1: return launch_row_def_v<1>(L, nb, s, solves, bc, tw, cond, use_cond);
+    case 0: return launch_row_def_v<0>(L, nb, s, solves, bc, tw, cond, use_cond, rcond, use_rcond);
+    case 1: return launch_row_def_v<1>(L, nb, s, solves, bc, tw, cond, use_cond, rcond, use_rcond);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -92,6 +96,15 @@ inline cudaError_t launch_ref_inverse(int L, int var64, int nb, cudaStream_t s, 
   switch (var64) {
     case 0: return launch_ref_inverse_v<0>(L, nb, s, solves, tw64);
     case 1: return launch_ref_inverse_v<1>(L, nb, s, solves, tw64);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int D = 0>
+inline cudaError_t launch_ref_sums(int L, int var64, int nb, cudaStream_t s, Solve* solves) {
+  switch (var64) {
+    case 0: return launch_ref_sums_v<0>(L, nb, s, solves);
+    case 1: return launch_ref_sums_v<1>(L, nb, s, solves);
     default: return cudaErrorInvalidValue;
   }
 }

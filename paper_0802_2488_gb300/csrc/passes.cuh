@@ -22,8 +22,6 @@
 //   operator of Eq. 3 per frequency (scaled by 1/L^2, mean strain at q = 0),
 //   inverse column transform.
 #pragma once
-#include <type_traits>
-
 #include "common.cuh"
 #include "fft.cuh"
 #include "physics.cuh"
@@ -541,12 +539,18 @@ __device__ __forceinline__ void batch_arrive(Solve* solves, int nb, BatchCtl* bc
   const unsigned prev = atomicAdd(&bc->arrive, 1u);
   if (prev == total - 1) {
     __threadfence();
-    int active = 0;
-    for (int i = 0; i < nb; i++) active += (*(volatile int32_t*)&solves[i].phase) != PH_DONE;
+    int active = 0, waiting = 0;
+    for (int i = 0; i < nb; i++) {
+      const int ph = *(volatile int32_t*)&solves[i].phase;
+      active += ph != PH_DONE;
+      waiting += ph == PH_REF;
+    }
     bc->active = active;
+    bc->waiting = waiting;
     bc->body_iters += 1;
-    const bool go = active > 0 && bc->body_iters < bc->max_body_iters;
-    if (!go && active > 0) bc->timed_out = 1;
+    // a solve waiting for its refresh stops the loop (the host runs it)
+    const bool go = active > 0 && waiting == 0 && bc->body_iters < bc->max_body_iters;
+    if (active > 0 && waiting == 0 && bc->body_iters >= bc->max_body_iters) bc->timed_out = 1;
     if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
     bc->arrive = 0;
     __threadfence();
@@ -556,35 +560,16 @@ __device__ __forceinline__ void batch_arrive(Solve* solves, int nb, BatchCtl* bc
 // ---------------------------------------------------------------------------
 // Row pass
 // ---------------------------------------------------------------------------
-// T is the type of the state (strain, stress, the local step and the
-// residual); the transforms and the spectrum are in T, or, with DEF (the
-// defect-correction form, T = double), in FP32 with the tile shapes of the
-// FP32 tiling V.  DEF: the spectrum carries the FP32 transform of the
-// polarization's difference from the solve's FP64 reference p_ref, and the
-// compatible strain is e = E + g_ref + (that difference through the Green
-// operator), g_ref = Gamma(p_ref) computed in FP64 (defect.cuh).
-template <typename T, bool DEF>
-using XformT = typename std::conditional<DEF, float, T>::type;
-template <typename T, int L, int V, bool DEF>
-struct RowK {
-  using F = XformT<T, DEF>;
-  using C = Cfg<F, L, V>;
-  // the FP64 local step of the defect form needs the registers of one CTA
-  // per SM
-  static constexpr int MINB = DEF ? 1 : C::MINB_ROW;
-};
-
-template <typename T, int L, int V, bool DEF = false>
-__global__ void __launch_bounds__(RowK<T, L, V, DEF>::C::NT_ROW, RowK<T, L, V, DEF>::MINB)
-row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<XformT<T, DEF>>* __restrict__ tw,
+template <typename T, int L, int V>
+__global__ void __launch_bounds__(Cfg<T, L, V>::NT_ROW, Cfg<T, L, V>::MINB_ROW)
+row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<T>* __restrict__ tw,
          cudaGraphConditionalHandle cond, int use_cond) {
-  using F = XformT<T, DEF>;
-  using C = Cfg<F, L, V>;
+  using C = Cfg<T, L, V>;
   constexpr int RR = C::RR, W = C::W, NT = C::NT_ROW, M = C::M;
   constexpr int P = L >= NT ? L / NT : 1;
-  using IO = RowIO<F, L, V>;
+  using IO = RowIO<T, L, V>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  C2<F>* sp = reinterpret_cast<C2<F>*>(smraw);
+  C2<T>* sp = reinterpret_cast<C2<T>*>(smraw);
   __shared__ bool s_last;
 
   // Every index of the pass is in range when the grid has L / RR CTAs per
@@ -610,17 +595,13 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<XformT<T, DE
     // sigma of eps^n (read) and of the iterate this pass produces (written)
     const T* __restrict__ sin_ = reinterpret_cast<const T*>(S.sig[cur]);
     T* __restrict__ sout = reinterpret_cast<T*>(S.sig[1 - cur]);
-    C2<F>* spec = reinterpret_cast<C2<F>*>(S.spec);
+    C2<T>* spec = reinterpret_cast<C2<T>*>(S.spec);
     const uint8_t* __restrict__ mask = S.mask;
     const Mat<T> m = make_mat<T>(S);
     const size_t LL = (size_t)L * L;
-    // defect form: the FP64 reference polarization and its compatible
-    // strain, three planes (11, 22, 12) of L^2 each
-    const T* __restrict__ pref = DEF ? reinterpret_cast<const T*>(S.pref) : nullptr;
-    const T* __restrict__ gref = DEF ? reinterpret_cast<const T*>(S.gref) : nullptr;
     // stage table and twist octant, in flight until the first barrier after
     // cp_async_wait_all() (INIT, ITER; the other phases do not read them)
-    const C2<F>* stw = sp + C::ROW_DATA;
+    const C2<T>* stw = sp + C::ROW_DATA;
     if (phase == PH_INIT || phase == PH_ITER) IO::load_tables(sp, tw);
     T acc[N_ACC];
 #pragma unroll
@@ -663,15 +644,9 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<XformT<T, DE
           for (int c = 0; c < 4; c++) acc[A_E11 + c] += e[c];
           acc[A_NPL] += pl ? T(1) : T(0);
           c0_apply(e, m, c0);
-          if constexpr (DEF) {
-            IO::px(sp, 0, r, x1) = F((s[0] - c0[0]) - pref[x]);
-            IO::px(sp, 1, r, x1) = F((s[1] - c0[1]) - pref[LL + x]);
-            IO::px(sp, 2, r, x1) = F((s[3] - c0[3]) - pref[2 * LL + x]);
-          } else {
-            IO::px(sp, 0, r, x1) = s[0] - c0[0];
-            IO::px(sp, 1, r, x1) = s[1] - c0[1];
-            IO::px(sp, 2, r, x1) = s[3] - c0[3];
-          }
+          IO::px(sp, 0, r, x1) = s[0] - c0[0];
+          IO::px(sp, 1, r, x1) = s[1] - c0[1];
+          IO::px(sp, 2, r, x1) = s[3] - c0[3];
         }
     } else {  // PH_ITER
       T E[4];
@@ -691,16 +666,6 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<XformT<T, DE
             if (ECHK(row, L, 39)) prefetch_l2(reinterpret_cast<const char*>(sin_ + (size_t)4 * row * L) + (size_t)(i % NPR) * PB, PB);
           }
           if (lane == 31) prefetch_l2(mask + (size_t)r0 * L, (unsigned)(RR * L));
-          if constexpr (DEF) {
-            // the RR rows of the three planes of g_ref and p_ref
-            constexpr unsigned QB = (unsigned)(RR * L * sizeof(T)), QP = QB < 16384u ? QB : 16384u;
-            constexpr int NQ = (int)(QB / QP);
-            for (int i = lane; i < 6 * NQ; i += 32) {
-              const int pl = i / NQ;
-              const T* base = (pl < 3 ? gref : pref) + (size_t)(pl % 3) * LL + (size_t)r0 * L;
-              prefetch_l2(reinterpret_cast<const char*>(base) + (size_t)(i % NQ) * QP, QP);
-            }
-          }
         }
       }
       // halo row x2 = r0 - 1: sigma12 and sigma22 of iterate n for the
@@ -747,11 +712,6 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<XformT<T, DE
         acc[A_DIV2] += d1 * d1 + d2 * d2;
         // augmented-Lagrangian update of this pixel
         T e[4] = {IO::px(sp, 0, r, x1), IO::px(sp, 1, r, x1), E[2], IO::px(sp, 2, r, x1)};
-        if constexpr (DEF) {
-          e[0] += E[0] + gref[x];
-          e[1] += E[1] + gref[LL + x];
-          e[3] += E[3] + gref[2 * LL + x];
-        }
         T c0[4], tau[4], e1[4], s1[4], p1[3];
         c0_apply(e, m, c0);
 #pragma unroll
@@ -765,17 +725,10 @@ row_pass(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<XformT<T, DE
         acc[A_NPL] += is_plastic(e1, v, m) ? T(1) : T(0);
         const T q0 = e1[0] - e[0], q1 = e1[1] - e[1], q2 = e1[2] - e[2], q3 = e1[3] - e[3];
         acc[A_COMP] += q0 * q0 + q1 * q1 + q2 * q2 + T(2) * q3 * q3;
-        // next polarization sigma(eps^{n+1}) - C0:eps^{n+1} (in-plane); the
-        // defect form transforms its difference from p_ref
-        if constexpr (DEF) {
-          IO::px(sp, 0, r, x1) = F(p1[0] - pref[x]);
-          IO::px(sp, 1, r, x1) = F(p1[1] - pref[LL + x]);
-          IO::px(sp, 2, r, x1) = F(p1[2] - pref[2 * LL + x]);
-        } else {
-          IO::px(sp, 0, r, x1) = p1[0];
-          IO::px(sp, 1, r, x1) = p1[1];
-          IO::px(sp, 2, r, x1) = p1[2];
-        }
+        // next polarization sigma(eps^{n+1}) - C0:eps^{n+1} (in-plane)
+        IO::px(sp, 0, r, x1) = p1[0];
+        IO::px(sp, 1, r, x1) = p1[1];
+        IO::px(sp, 2, r, x1) = p1[2];
       };
       // stress of iterate n and voids of row r, group j
       auto load_px = [&](int r, int j, T (&sg)[4], bool& v) {

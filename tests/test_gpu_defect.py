@@ -1,16 +1,16 @@
 """The defect-correction form ('fp32_defect', EPFFT_FP32_DEFECT) against the
 oracle.
 
-The form keeps strain, stress, the local step and the reductions in FP64 and
-applies the Green operator of Eq. 3 as g_ref + Gamma(p - p_ref): g_ref =
-Gamma(p_ref) with FP64 transforms, refreshed to the current polarization
-every `epfft_set_defect_refresh` loop steps, and p - p_ref through the FP32
-transforms.  Three properties pin it:
+The form iterates in FP32 on the differences of strain and stress from an
+FP64 reference state, which a refresh (FP64 transforms, every
+`epfft_set_defect_refresh` loop steps and after each warm start) moves to the
+current iterate.  Three properties pin it:
 
-* with a refresh before every column pass, p - p_ref = 0 and every
-  iteration is the FP64 one (oracle iterates within 1e-12, as the FP64 path);
-* with no refresh (p_ref = 0, g_ref = 0) it is the FP32 transforms of the
-  whole polarization on an FP64 state (within the FP32 tolerance 2e-5);
+* its FP32 rounding scales with the iterate's distance from the last
+  refresh: near the fixed point, with a refresh before every iteration, the
+  iterates are the oracle's FP64 ones within 1e-11 (the plain FP32 form is
+  off by its FP32 state); from a generic state, and without refreshes, they
+  stay within the FP32 form's 2e-5;
 * with the default refresh it converges where the FP32 form cannot: the
   shear workload's first increment (L = 256, f = 0.2) reaches eta1, eta2 <
   1e-8, and the oracle, evaluating Eq. 1's divergence of the returned strain
@@ -68,21 +68,52 @@ def test_supported_sides_and_tilings():
 
 
 @pytest.mark.parametrize("green", ["eq3", "cg1"])
-@pytest.mark.parametrize("L,f,k", [(4, 0.25, 1), (8, 0.2, 3), (32, 0.15, 5), (64, 0.10, 4), (256, 0.2, 3)])
-def test_refresh_every_step_gives_the_fp64_iterates(ctx, L, f, k, green):
+def test_near_the_fixed_point_the_iterates_are_the_fp64_ones(ctx, green):
+    """The FP32 rounding of the defect form scales with how far the iterate
+    moved since the last refresh.  From the oracle's solution (tolerances
+    1e-11) perturbed by 1e-6, with a refresh before every iteration, five
+    iterations agree with the oracle's FP64 iterations within 1e-11, where the
+    plain FP32 form, whose state is rounded to FP32, is off by about 1e-8."""
+    L, f, k = 32, 0.15, 5
     mask = O.mask(L, f, 5)
     mat = O.material(green=O.GREEN_EQ3 if green == "eq3" else O.GREEN_CG1)
+    E = np.array([0.45, 0.35, 0.0, 0.2])
+    sol = O.solve(mask, mat, E[None], tol_eq=1e-11, tol_macro=1e-11, max_iter=200000, fields=True)
+    assert sol.status == 0
+    eps0 = sol.eps + inputs.random_strain(L, np.zeros(4), 1e-6, seed=3)
+    ref = oracle_iterate(mask, mat, E, eps0.copy(), k)
+    prob = B.Problem(L=L, precision="fp32_defect", mask=mask, green=green)
+    B.epfft_set_defect_refresh(ctx, 1)
+    try:
+        t = torch.tensor(eps0, dtype=torch.float64, device="cuda").contiguous()
+        rec = B.epfft_iterate(ctx, prob, E, t, k)
+    finally:
+        B.epfft_set_defect_refresh(ctx, 64)
+    assert rec["iterations"] == k
+    err = rel(t.cpu().numpy(), ref)
+    assert err < 1e-11, err
+    t32 = torch.tensor(eps0, dtype=torch.float32, device="cuda").contiguous()
+    B.epfft_iterate(ctx, B.Problem(L=L, precision="fp32", mask=mask, green=green), E, t32, k)
+    assert rel(t32.cpu().numpy().astype(np.float64), ref) > 1e-9
+
+
+@pytest.mark.parametrize("L,f,k", [(8, 0.2, 3), (64, 0.10, 4), (256, 0.2, 3)])
+def test_refresh_every_step_from_a_generic_state(ctx, L, f, k):
+    """From a generic state (noise 0.3) the iteration's steps are large and
+    the FP32 differences carry FP32 rounding: within the FP32 form's 2e-5."""
+    mask = O.mask(L, f, 5)
+    mat = O.material()
     E = np.array([0.45, 0.35, 0.0, 0.2])
     eps0 = inputs.random_strain(L, E, 0.3, seed=L + k)
     ref = oracle_iterate(mask, mat, E, eps0.copy(), k)
     B.epfft_set_defect_refresh(ctx, 1)
     try:
         t = torch.tensor(eps0, dtype=torch.float64, device="cuda").contiguous()
-        rec = B.epfft_iterate(ctx, B.Problem(L=L, precision="fp32_defect", mask=mask, green=green), E, t, k)
+        rec = B.epfft_iterate(ctx, B.Problem(L=L, precision="fp32_defect", mask=mask), E, t, k)
     finally:
         B.epfft_set_defect_refresh(ctx, 64)
     assert rec["iterations"] == k
-    assert rel(t.cpu().numpy(), ref) < 1e-12, rel(t.cpu().numpy(), ref)
+    assert rel(t.cpu().numpy(), ref) < 2e-5, rel(t.cpu().numpy(), ref)
 
 
 @pytest.mark.parametrize("L,f,k", [(8, 0.2, 3), (64, 0.10, 4), (128, 0.3, 2)])
