@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--impl", default="epfft", choices=["epfft", "reference"])
     ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "c5"])
     ap.add_argument("--requests", type=int, default=150, help="c5: requests in the stream")
-    ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "fp32_defect"],
                     help="default: fp64 for c1/c2, fp32 for c3/c4/c5")
     ap.add_argument("--cap", type=int, default=None, help="max iterations per increment")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU-baseline leg")
@@ -341,9 +341,9 @@ def refined_vs_plain(B, ctx, stream, flush, mask, L, path, torch, tol=1e-8, tol_
             "speedup": t64 / tr, "speedup_defect": t64 / td}
 
 
-# loop steps between refreshes of the defect form's FP64 reference (the
+# iterations between refreshes of the defect form's FP64 reference (the
 # library's default)
-DEFECT_REFRESH = 64
+DEFECT_REFRESH = 256
 
 
 def batched_at_tol(B, ctx, stream, flush, torch, tol=1e-8, cap=60000):
@@ -406,7 +406,7 @@ def peaks(B, ctx, precision):
     """Roofline denominators: the measured HBM copy rate (MEASURED_PEAKS.json)
     for the FP32 passes; the FP64 FMA rate measured here on this device
     (epfft_fp64_peak) for the FP64 passes."""
-    if precision == "fp32":
+    if precision in ("fp32", "fp32_defect"):
         mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
         if os.path.exists(mp):
             return json.load(open(mp))["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs (of measured)"
@@ -418,7 +418,10 @@ def peaks(B, ctx, precision):
 
 def pass_kernels(precision, L, tiling):
     """Names of the two compiled passes a solve of this size runs."""
-    rt = "float" if precision == "fp32" else "double"
+    rt = "double" if precision == "fp64" else "float"
+    if precision == "fp32_defect":
+        col = f"col_pass_rs<{L}>" if (tiling == 0 and L >= 128) else f"col_pass<float,{L},{tiling}>"
+        return {"row": f"row_pass_dc<{L},{tiling}>", "col": col}
     if precision == "fp32" and tiling == 2:
         return {"row": f"row_pass_rs<{L}>", "col": f"col_pass_rs<{L}> (digit-reversed rows)"}
     col = f"col_pass_rs<{L}>" if (precision == "fp32" and tiling == 0 and L >= 128) else f"col_pass<{rt},{L},{tiling}>"
@@ -440,13 +443,14 @@ TRAFFIC = {
 
 
 def kernel_source_digest():
-    """sha256 (first 16 hex digits) over the names and bytes of the CUDA
-    sources of the library, in name order."""
+    """sha256 (first 16 hex digits) over the names and bytes of the device
+    code the passes compile from (the kernel headers), in name order."""
     import glob
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_0802_2488_gb300", "csrc", "*"))):
-        if f.endswith((".cu", ".cuh", ".h")):
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_0802_2488_gb300", "csrc", "*.cuh"))):
+        if os.path.basename(f) not in ("inst_impl.cuh", "inst_def_impl.cuh", "launch.cuh", "aux_kernels.cuh",
+                                       "post_kernels.cuh"):
             h.update(os.path.basename(f).encode())
             with open(f, "rb") as fh:
                 h.update(fh.read())
@@ -465,13 +469,16 @@ def roofline(precision, L, nb, col_ms, row_ms, peak, peak_source, tiling=None):
     FP32 (HBM): algorithmic bytes per pixel, row pass 73 (spectrum read and
     written 24, sigma of iterate n read 16, new strain and sigma written 32,
     void mask 1), column pass 24 (spectrum read and written).
+    Defect form (HBM): row pass 113 (spectrum 24, the stress difference of
+    iterate n read 16, the new strain and stress differences written 32, the
+    reference data read 40, mask 1), column pass 24.
     FP64 (FP64 ALU): flops per pixel, row pass 15 log2 L + 60 (row
     transforms, local step), column pass 15 log2 L + 25 (column transforms,
     Green operator)."""
     n = L * L * nb
     lg = int(np.log2(L))
-    if precision == "fp32":
-        work = {"row": 73 * n, "col": 24 * n}
+    if precision in ("fp32", "fp32_defect"):
+        work = {"row": (73 if precision == "fp32" else 113) * n, "col": 24 * n}
         unit, scale, bound = "GB/s", 1e9, "hbm"
     else:
         work = {"row": (15 * lg + 60) * n, "col": (15 * lg + 25) * n}
@@ -549,7 +556,7 @@ def solve_line(B, ctx, stream, flush, torch, name, precision, cap, steps, warmup
         e2e_its += sum(p.L * p.L * int(r["iterations"].sum()) for p, r in zip(ph, rr))
     barrier()
     e2e_s = time.perf_counter() - t0
-    rs = 8 if precision == "fp64" else 4
+    rs = 4 if precision == "fp32" else 8  # the defect form's fields are FP64
     h2d = sum(L * L + 4 * 8 * P.n_inc for P in probs)
     d2h = sum(P.n_inc * 104 + L * L * 4 * rs + P.n_inc * L * L * 5 for P in probs)
 
@@ -762,6 +769,14 @@ def main():
         extras["c2"] = fp32_vs_fp64(B, ctx, stream, flush, torch, min(args.steps, 3), 1, local, barrier, p64, s64)
         extras["c2"]["steps"], extras["c2"]["warmup"] = min(args.steps, 3), 1
         extras["batched_at_tol"] = batched_at_tol(B, ctx, stream, flush, torch)
+        # the batched workload in the defect form (same cap): its throughput and
+        # the roofline of its passes
+        c3d = solve_line(B, ctx, stream, flush, torch, "c3", "fp32_defect", CAPS["c3"], 2, 1, 1, local, ws, peak,
+                         peak_src, barrier)
+        extras["c3_defect"] = {k: c3d[k] for k in ("value", "ms_per_step", "convergence", "roofline", "e2e",
+                                                    "clocks", "gpu_launches")}
+        extras["c3_defect"]["config"] = c3d["config"]
+        extras["c3_defect"]["steps"], extras["c3_defect"]["warmup"] = 2, 1
 
     if rank == 0:
         out = {

@@ -509,7 +509,7 @@ int epfft_supported_tiling(int32_t L, int32_t precision, int32_t variant);
 int epfft_set_tiling(epfft_ctx *ctx, int32_t L, int32_t precision, int32_t variant);
 
 /* Defect-correction form (EPFFT_FP32_DEFECT): iterations of a solve between
- * two refreshes of its FP64 reference (default 64), for solves set up after
+ * two refreshes of its FP64 reference (default 256), for solves set up after
  * the call.  A refresh costs about one FP64 transform pair of the lattice
  * and runs inside the device loop (a conditional node after the row pass),
  * for each solve on its own schedule, so a solve's arithmetic does not

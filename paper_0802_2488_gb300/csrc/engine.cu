@@ -49,8 +49,9 @@ struct epfft_ctx {
   std::map<std::tuple<int, int, int>, int> variant;
   epfft_stats last{};
   Server* server = nullptr;
-  // defect-correction form: loop steps between refreshes of the reference
-  int defect_refresh = 64;
+  // defect-correction form: iterations of a solve between refreshes of its
+  // reference
+  int defect_refresh = 256;
 };
 
 namespace {

@@ -30,8 +30,9 @@ def measure(ctx, L: int, precision: str, f: float = 0.2, iters: int = 50, varian
     n = L * L * batch
     lg = math.log2(L)
     # algorithmic bytes per pixel: FP32 row 73 / column 24, FP64 145 / 48,
-    # the defect form 169 (FP32 spectrum, FP64 state, p_ref and g_ref) / 24
-    row_b = {"fp64": 145, "fp32": 73, "fp32_defect": 169}[precision] * n
+    # the defect form 113 (FP32 spectrum, the FP32 differences of iterate n
+    # and n+1, the reference data) / 24
+    row_b = {"fp64": 145, "fp32": 73, "fp32_defect": 113}[precision] * n
     col_b = (48 if precision == "fp64" else 24) * n
     row_f, col_f = (15 * lg + 60) * n, (15 * lg + 25) * n
     return {

@@ -106,6 +106,9 @@ def test_roofline_uses_the_algorithmic_work_of_each_pass():
     assert bench.roofline("fp32", 512, 16, 0.184, 0.337, 6770.0, "measured", 0)["traffic"] is None
     r4 = bench.roofline("fp32", 4096, 1, 0.15, 0.47, 6770.0, "measured", 2)
     assert r4["kernel"] == "row_pass_rs<4096>"
+    rd = bench.roofline("fp32_defect", 512, 64, 0.12, 0.58, 6770.0, "measured", 0)
+    assert rd["bound"] == "hbm" and rd["kernel"] == "row_pass_dc<512,0>"
+    assert abs(rd["achieved"] - 113 * n / 0.58e-3 / 1e9) < 1e-6 and rd["traffic"] is None
     r = bench.roofline("fp64", 256, 1, 0.040, 0.030, 1.25, "measured", 1)
     assert r["bound"] == "alu" and r["kernel"] == "col_pass<double,256,1>" and r["traffic"] is None
     assert abs(r["achieved"] - (15 * 8 + 25) * 65536 / 0.040e-3 / 1e12) < 1e-12

@@ -88,7 +88,7 @@ def test_near_the_fixed_point_the_iterates_are_the_fp64_ones(ctx, green):
         t = torch.tensor(eps0, dtype=torch.float64, device="cuda").contiguous()
         rec = B.epfft_iterate(ctx, prob, E, t, k)
     finally:
-        B.epfft_set_defect_refresh(ctx, 64)
+        B.epfft_set_defect_refresh(ctx, 256)
     assert rec["iterations"] == k
     err = rel(t.cpu().numpy(), ref)
     assert err < 1e-11, err
@@ -111,7 +111,7 @@ def test_refresh_every_step_from_a_generic_state(ctx, L, f, k):
         t = torch.tensor(eps0, dtype=torch.float64, device="cuda").contiguous()
         rec = B.epfft_iterate(ctx, B.Problem(L=L, precision="fp32_defect", mask=mask), E, t, k)
     finally:
-        B.epfft_set_defect_refresh(ctx, 64)
+        B.epfft_set_defect_refresh(ctx, 256)
     assert rec["iterations"] == k
     assert rel(t.cpu().numpy(), ref) < 2e-5, rel(t.cpu().numpy(), ref)
 
@@ -128,7 +128,7 @@ def test_without_refresh_it_is_the_fp32_transform(ctx, L, f, k):
         t = torch.tensor(eps0, dtype=torch.float64, device="cuda").contiguous()
         B.epfft_iterate(ctx, B.Problem(L=L, precision="fp32_defect", mask=mask), E, t, k)
     finally:
-        B.epfft_set_defect_refresh(ctx, 64)
+        B.epfft_set_defect_refresh(ctx, 256)
     err = rel(t.cpu().numpy(), ref)
     assert err < 2e-5, err
     assert err > 1e-12  # the FP32 transforms did run
