@@ -430,37 +430,41 @@ def pass_kernels(precision, L, tiling):
 
 # DRAM bytes (read + write) per launch from ncu launch lists of the same
 # kernels at the same launch shape: (precision, L, solves, tiling, pass) ->
-# (bytes, summary under profiles/).  TRAFFIC_SRC is the digest of the kernel
-# sources the captures ran (kernel_source_digest); once the sources differ,
-# every traffic figure reads null until the captures are taken again.
-TRAFFIC_SRC = "ed25df8949469093"
+# (bytes, summary under profiles/, digest of the kernel headers the capture
+# ran, kernel_source_digest).  An entry whose headers changed since reads
+# null until the capture is taken again.
 TRAFFIC = {
-    ("fp32", 512, 64, 0, "row"): (1167.1e6, "profiles/passes_fp32_c3_c4_launches.md"),
-    ("fp32", 512, 64, 0, "col"): (346.9e6, "profiles/passes_fp32_c3_c4_launches.md"),
-    ("fp32", 4096, 1, 2, "row"): (1247.6e6, "profiles/passes_fp32_c3_c4_launches.md"),
-    ("fp32", 4096, 1, 2, "col"): (358.4e6, "profiles/passes_fp32_c3_c4_launches.md"),
+    ("fp32", 512, 64, 0, "row"): (1167.7e6, "profiles/passes_fp32_c3_c4_launches.md", "61faad23b798d24f"),
+    ("fp32", 512, 64, 0, "col"): (346.9e6, "profiles/passes_fp32_c3_c4_launches.md", "61faad23b798d24f"),
+    ("fp32", 4096, 1, 2, "row"): (1247.9e6, "profiles/passes_fp32_c3_c4_launches.md", "61faad23b798d24f"),
+    ("fp32", 4096, 1, 2, "col"): (358.4e6, "profiles/passes_fp32_c3_c4_launches.md", "61faad23b798d24f"),
 }
 
 
-def kernel_source_digest():
-    """sha256 (first 16 hex digits) over the names and bytes of the device
-    code the passes compile from (the kernel headers), in name order."""
-    import glob
+# the kernel headers the passes of each form compile from
+PASS_HEADERS = ["common.cuh", "fft.cuh", "tables.cuh", "physics.cuh", "passes.cuh", "colrs.cuh", "rowrs.cuh"]
+DEFECT_HEADERS = PASS_HEADERS + ["dcpass.cuh"]
+
+
+def kernel_source_digest(headers=None):
+    """sha256 (first 16 hex digits) over the names and bytes of the kernel
+    headers a form's passes compile from (default: those of the FP32 and
+    FP64 passes), in name order."""
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_0802_2488_gb300", "csrc", "*.cuh"))):
-        if os.path.basename(f) not in ("inst_impl.cuh", "inst_def_impl.cuh", "launch.cuh", "aux_kernels.cuh",
-                                       "post_kernels.cuh"):
-            h.update(os.path.basename(f).encode())
-            with open(f, "rb") as fh:
-                h.update(fh.read())
+    for name in sorted(headers or PASS_HEADERS):
+        h.update(name.encode())
+        with open(os.path.join(ROOT, "paper_0802_2488_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def traffic_of(precision, L, nb, tiling, k):
-    if kernel_source_digest() != TRAFFIC_SRC:
+    tr = TRAFFIC.get((precision, L, nb, tiling, k))
+    if tr is None:
         return None
-    return TRAFFIC.get((precision, L, nb, tiling, k))
+    heads = DEFECT_HEADERS if precision == "fp32_defect" else PASS_HEADERS
+    return tr if kernel_source_digest(heads) == tr[2] else None
 
 
 def roofline(precision, L, nb, col_ms, row_ms, peak, peak_source, tiling=None):
@@ -495,10 +499,10 @@ def roofline(precision, L, nb, col_ms, row_ms, peak, peak_source, tiling=None):
     d = passes[dom]
     tr = traffic_of(precision, L, nb, tiling, dom)
     if tr:
-        note = (f"DRAM read + write per launch from the ncu launch list in {tr[1]} (same kernel sources, "
-                f"digest {TRAFFIC_SRC}, and launch shape)")
-    elif kernel_source_digest() != TRAFFIC_SRC:
-        note = "null: the kernel sources changed since the ncu captures"
+        note = (f"DRAM read + write per launch from the ncu launch list in {tr[1]} (same kernel headers, "
+                f"digest {tr[2]}, and launch shape)")
+    elif (precision, L, nb, tiling, dom) in TRAFFIC:
+        note = "null: the kernel headers changed since the ncu capture"
     else:
         note = "null: no ncu capture of this kernel at this launch shape"
     return {"bound": bound, "kernel": d["kernel"], "achieved": d["achieved"], "peak": peak, "unit": unit,

@@ -98,8 +98,9 @@ def test_roofline_uses_the_algorithmic_work_of_each_pass():
     assert abs(r["frac"] - r["achieved"] / 6770.0) < 1e-12
     # traffic only where an ncu capture of that kernel at that launch shape
     # exists, and only while the kernel sources are those it ran
-    if bench.kernel_source_digest() == bench.TRAFFIC_SRC:
-        assert r["traffic"] == bench.TRAFFIC[("fp32", 512, 64, 0, "row")][0]
+    e = bench.TRAFFIC[("fp32", 512, 64, 0, "row")]
+    if bench.kernel_source_digest(bench.PASS_HEADERS) == e[2]:
+        assert r["traffic"] == e[0]
     else:
         assert r["traffic"] is None
     assert bench.roofline("fp32", 512, 64, 0.184, 0.337, 6770.0, "measured", 1)["traffic"] is None
@@ -116,7 +117,7 @@ def test_roofline_uses_the_algorithmic_work_of_each_pass():
 
 
 def test_traffic_reads_null_once_the_kernel_sources_change(monkeypatch):
-    monkeypatch.setattr(bench, "TRAFFIC_SRC", "0" * 16)
+    monkeypatch.setattr(bench, "TRAFFIC", {k: (v[0], v[1], "0" * 16) for k, v in bench.TRAFFIC.items()})
     r = bench.roofline("fp32", 512, 64, 0.184, 0.337, 6770.0, "measured", 0)
     assert r["traffic"] is None and "changed" in r["traffic_note"]
     assert all(p["traffic"] is None for p in r["passes"].values())
