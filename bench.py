@@ -438,6 +438,8 @@ TRAFFIC = {
     ("fp32", 512, 64, 0, "col"): (346.9e6, "profiles/passes_fp32_c3_c4_launches.md", "61faad23b798d24f"),
     ("fp32", 4096, 1, 2, "row"): (1247.9e6, "profiles/passes_fp32_c3_c4_launches.md", "61faad23b798d24f"),
     ("fp32", 4096, 1, 2, "col"): (358.4e6, "profiles/passes_fp32_c3_c4_launches.md", "61faad23b798d24f"),
+    ("fp32_defect", 512, 64, 0, "row"): (2037.6e6, "profiles/defect_passes_c3.md", "752521d166663150"),
+    ("fp32_defect", 512, 64, 0, "col"): (346.6e6, "profiles/defect_passes_c3.md", "752521d166663150"),
 }
 
 
