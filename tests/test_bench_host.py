@@ -109,7 +109,9 @@ def test_roofline_uses_the_algorithmic_work_of_each_pass():
     assert r4["kernel"] == "row_pass_rs<4096>"
     rd = bench.roofline("fp32_defect", 512, 64, 0.12, 0.58, 6770.0, "measured", 0)
     assert rd["bound"] == "hbm" and rd["kernel"] == "row_pass_dc<512,0>"
-    assert abs(rd["achieved"] - 113 * n / 0.58e-3 / 1e9) < 1e-6 and rd["traffic"] is None
+    assert abs(rd["achieved"] - 113 * n / 0.58e-3 / 1e9) < 1e-6
+    ed = bench.TRAFFIC[("fp32_defect", 512, 64, 0, "row")]
+    assert rd["traffic"] == (ed[0] if bench.kernel_source_digest(bench.DEFECT_HEADERS) == ed[2] else None)
     r = bench.roofline("fp64", 256, 1, 0.040, 0.030, 1.25, "measured", 1)
     assert r["bound"] == "alu" and r["kernel"] == "col_pass<double,256,1>" and r["traffic"] is None
     assert abs(r["achieved"] - (15 * 8 + 25) * 65536 / 0.040e-3 / 1e12) < 1e-12
