@@ -21,7 +21,7 @@
  * with a:b = a11 b11 + a22 b22 + 2 a12 b12.
  *
  * Conventions of every call:
- *   - lattice side L: a power of two, 4 <= L <= 4096 (FP64: L <= 2048);
+ *   - lattice side L: a power of two, 4 <= L <= 4096;
  *   - pixel x = (x1, x2) at linear index x2 * L + x1 (x1 fastest);
  *   - symmetric tensors are 4 reals per pixel in the order (11, 22, 33, 12);
  *   - forward DFT kernel exp(-i q.x), q_j = 2 pi m_j / L (the sign for which
@@ -68,8 +68,7 @@ extern "C" {
                              * FP32 rounding then scales with the distance    *
                              * from the reference, so the tolerances of the   *
                              * FP64 form (Sec. 2) are reached at FP32 cost.   *
-                             * Fields are FP64; sides up to 2048; tilings 0   *
-                             * and 1.                                         */
+                             * Fields are FP64; tilings 0 and 1.              */
 
 #define EPFFT_GREEN_EQ3 0 /* discrete Green operator of Eq. 3                   */
 #define EPFFT_GREEN_CG1 1 /* continuum operator (Sec. 2, CG1): Eq. 3 with the   *

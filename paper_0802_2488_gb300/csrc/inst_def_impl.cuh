@@ -7,8 +7,8 @@
 
 namespace epfft {
 
-// sides of the FP64 build (the refresh runs FP64 transforms)
-#define EPFFT_DEF_FOR_L(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048)
+// every side of the FP32 and FP64 builds (the refresh runs FP64 transforms)
+#define EPFFT_DEF_FOR_L(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
 
 template <int L>
 static cudaError_t prepare_def_L() {

@@ -49,7 +49,7 @@ struct Cfg {
   static constexpr bool FULL = PS::FULL;
   // rows per row-pass CTA
   static constexpr int RR = V == 0 ? (F64 ? 2 : (L <= 256 ? 2 : (L <= 2048 ? 8 : 4)))
-                                   : (F64 ? (L <= 256 ? 1 : 2) : (L <= 256 ? 1 : 2));
+                                   : (F64 ? (L <= 256 || L == 4096 ? 1 : 2) : (L <= 256 ? 1 : 2));
   // columns per column-pass CTA (= tile width of the spectrum layout)
   static constexpr int W0 = V == 0 ? (F64 ? (L <= 256 ? 1 : (L <= 1024 ? 2 : 1))
                                           : (L == 2048 ? 1 : 2))

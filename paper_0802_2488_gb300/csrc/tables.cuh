@@ -121,9 +121,11 @@ struct RowPlan : Plan16<M, row_ra<M>(), row_rb<M>()> {
 template <typename T, int L, int V>
 struct PlanSel {
   static constexpr bool F64 = sizeof(T) == 8;
-  static constexpr int RM_ROW = F64 ? (L <= 512 ? 4 : (V == 0 ? 16 : 8)) : 16;
-  static constexpr int RM_COL = F64 ? (L <= 512 ? 4 : (V == 0 ? 16 : 8)) : 16;
-  static constexpr bool FULL = F64 ? true : L <= 2048;
+  // FP64 at L = 4096: radix 16 and compact twiddles in both tilings (the
+  // 4096-point column of three components takes 203 KB of shared memory)
+  static constexpr int RM_ROW = F64 ? (L <= 512 ? 4 : (V == 0 || L == 4096 ? 16 : 8)) : 16;
+  static constexpr int RM_COL = F64 ? (L <= 512 ? 4 : (V == 0 || L == 4096 ? 16 : 8)) : 16;
+  static constexpr bool FULL = L <= 2048;
   using PR = FftPlan<L / 2, RM_ROW, FULL>;
   using PC = FftPlan<L, RM_COL, FULL>;
 };

@@ -39,12 +39,12 @@ def test_binding_keeps_the_c_names():
 def test_host_only_calls(lib):
     assert B.strerror(B.EPFFT_OK) == "ok"
     assert "argument" in B.strerror(B.EPFFT_ERR_ARG)
-    assert B.epfft_supported(256, "fp64") and B.epfft_supported(4096, "fp32")
-    assert not B.epfft_supported(4096, "fp64")
+    assert B.epfft_supported(256, "fp64") and B.epfft_supported(4096, "fp32") and B.epfft_supported(4096, "fp64")
+    assert not B.epfft_supported(8192, "fp64") and not B.epfft_supported(8192, "fp32")
     assert lib.epfft_supported(100, 1) == 0 and lib.epfft_supported(2, 1) == 0
     # the defect-correction form: where both the FP32 passes and the FP64
     # refresh are built, tilings 0 and 1 only
-    assert B.epfft_supported(2048, "fp32_defect") and not B.epfft_supported(4096, "fp32_defect")
+    assert B.epfft_supported(4096, "fp32_defect") and not B.epfft_supported(8192, "fp32_defect")
     assert B.epfft_supported_tiling(512, "fp32_defect", 1) and not B.epfft_supported_tiling(512, "fp32_defect", 2)
     assert lib.epfft_supported(256, 3) == 0
     assert lib.epfft_set_defect_refresh(None, 8) == B.EPFFT_ERR_ARG

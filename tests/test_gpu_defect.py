@@ -61,8 +61,8 @@ def eta1_of(mask, eps):
 
 
 def test_supported_sides_and_tilings():
-    assert B.epfft_supported(256, "fp32_defect") and B.epfft_supported(2048, "fp32_defect")
-    assert not B.epfft_supported(4096, "fp32_defect")  # the refresh needs the FP64 build
+    assert B.epfft_supported(256, "fp32_defect") and B.epfft_supported(4096, "fp32_defect")
+    assert not B.epfft_supported(8192, "fp32_defect")
     assert B.epfft_supported_tiling(256, "fp32_defect", 0) and B.epfft_supported_tiling(256, "fp32_defect", 1)
     assert not B.epfft_supported_tiling(512, "fp32_defect", 2)
 

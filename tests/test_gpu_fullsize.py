@@ -66,3 +66,14 @@ def test_one_iteration_at_L4096_matches_oracle(ctx):
     B.epfft_iterate(ctx, B.Problem(L=P.L, precision="fp32", mask=mask), E, t, 1)
     err = rel(t.cpu().numpy(), ref)
     assert err < 2e-5, err
+    # the same iteration in FP64 (tiling 1: one row per CTA) and in the
+    # defect form (FP32 differences from the FP64 state, its refresh in FP64)
+    B.epfft_set_tiling(ctx, 4096, "fp64", 1)
+    t = torch.tensor(eps0, dtype=torch.float64, device="cuda").contiguous()
+    B.epfft_iterate(ctx, B.Problem(L=P.L, precision="fp64", mask=mask), E, t, 1)
+    err = rel(t.cpu().numpy(), ref)
+    assert err < 1e-12, err
+    t = torch.tensor(eps0, dtype=torch.float64, device="cuda").contiguous()
+    B.epfft_iterate(ctx, B.Problem(L=P.L, precision="fp32_defect", mask=mask), E, t, 1)
+    err = rel(t.cpu().numpy(), ref)
+    assert err < 2e-5, err

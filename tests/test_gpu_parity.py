@@ -72,7 +72,7 @@ def test_project_parity(ctx, L, prec, tol):
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 3e-6)])
-@pytest.mark.parametrize("L", [1024, 2048])
+@pytest.mark.parametrize("L", [1024, 2048, 4096])
 def test_project_parity_large(ctx, L, prec, tol):
     if not B.epfft_supported(L, prec):
         pytest.skip("not built")
@@ -206,7 +206,7 @@ def test_all_void_and_elastic_edge_cases(ctx):
 
 def test_invalid_arguments_are_rejected(ctx):
     for bad in (dict(L=12), dict(L=2), dict(mu=-1.0), dict(max_iter=0), dict(void_fraction=1.5),
-                dict(tol_eq=-1.0), dict(L=4096, precision="fp64")):
+                dict(tol_eq=-1.0), dict(L=8192, precision="fp64")):
         kw = dict(L=16, void_fraction=0.1)
         kw.update(bad)
         with pytest.raises(B.EpfftError):
