@@ -208,3 +208,28 @@ def test_served_defect_solve_is_certified(ctx):
     assert rc == B.EPFFT_OK and (rec["status"] == 0).all()
     assert (rec["eta1"] < 1e-8).all() and eps.dtype == np.float64
     assert eta1_of(O.mask(L, 0.1, 9), eps) < 1e-8
+
+
+@pytest.mark.parametrize("load", ["equibiaxial", "shear"])
+def test_dg2_in_the_defect_form(ctx, load):
+    """DG2 (Sec. 2: four solves with the mirrored operators, fields
+    averaged) with every member in the defect form, against the oracle's
+    FP64 DG2 at the same tolerances (all increments converge within the
+    cap): the macroscopic stress within 1e-6, the averaged field within
+    1e-5, the iteration counts within 1 %, and the plastic set and clusters
+    of the averaged field those of the oracle's law on it."""
+    L = 16
+    path = inputs.load_path(load, 3, 1.5)
+    mask = O.mask(L, 0.1, 4)
+    ref = O.solve_dg2(mask, O.material(), path, tol_eq=1e-8, tol_macro=1e-8, max_iter=30000)
+    assert (ref.records["status"] == 0).all()
+    prob = B.Problem(L=L, precision="fp32_defect", mask=mask, max_iter=30000)
+    rc, rec, f = B.epfft_solve_dg2(ctx, prob, path, fields=True)
+    assert rc == B.EPFFT_OK and (rec["status"] == 0).all()
+    assert (np.abs(rec["iterations"] - ref.records["iterations"]) <= 0.01 * ref.records["iterations"]).all()
+    assert rel(rec["sig_mean"], ref.records["sig_mean"]) < 1e-6
+    assert rel(f.eps, ref.eps) < 1e-5
+    _, pl = O.sigma(f.eps, mask, O.material())
+    np.testing.assert_array_equal(f.plastic, pl & (1 - mask))
+    lab, n = O.label(f.plastic)
+    np.testing.assert_array_equal(f.labels, lab)
