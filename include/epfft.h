@@ -466,7 +466,9 @@ int epfft_label(epfft_ctx *ctx, int32_t L, int32_t n_img, const uint8_t *flags_d
  * from the uniform state eps = E (iterations never stop early).
  * col_ms: forward column FFT + Green operator + inverse column FFT;
  * row_ms: inverse row FFT + local step + residual partials + forward row FFT.
- * Blocking. */
+ * With the on-chip schedule (tiling 3) there are no separate passes: col_ms
+ * is 0 and row_ms the time per iteration of one launch running n_iter
+ * iterations of the batch.  Blocking. */
 int epfft_time_passes(epfft_ctx *ctx, const epfft_problem *problem, int32_t n_batch, const double E[4],
                       int32_t n_iter, float *col_ms, float *row_ms);
 
@@ -487,9 +489,12 @@ int epfft_fp64_peak(epfft_ctx *ctx, double *tflops, int32_t *n_sm, float *ms);
  * per row-pass CTA, tile width of the spectrum layout = columns per
  * column-pass CTA, threads); 2 is the register-staged row and column passes
  * (FP32, sides 256 .. 4096 only), whose spectrum is stored in the row
- * transform's digit-reversed column order.  epfft_supported_tiling tells
- * which exist.  epfft_autotune times every compiled one on this device (CUDA
- * events, a batch of n_batch synthetic f = 0.2 lattices) and makes the
+ * transform's digit-reversed column order; 3 is the on-chip schedule (FP32,
+ * sides 16 .. 64 only): one CTA runs a whole solve, every increment and
+ * iteration, with the spectrum in shared memory (the fixed-step entry points,
+ * projections and serving use tiling 0 instead).  epfft_supported_tiling
+ * tells which exist.  epfft_autotune times every compiled one on this device
+ * (CUDA events, a batch of n_batch synthetic f = 0.2 lattices) and makes the
  * fastest the context's tiling for (L, precision) and for batches of that
  * class: launches that cover at least 2^21 pixels (L^2 x batch) form one
  * class, smaller ones the other, since small launches favour more and
@@ -498,7 +503,7 @@ int epfft_fp64_peak(epfft_ctx *ctx, double *tflops, int32_t *n_sm, float *ms);
  * a tiling that is not compiled).  Later solves, batches, projections (class
  * of one solve) and serving classes (class of their slot count) of that size
  * use it.  Blocking. */
-#define EPFFT_N_TILINGS 3
+#define EPFFT_N_TILINGS 4
 int epfft_autotune(epfft_ctx *ctx, int32_t L, int32_t precision, int32_t n_batch, int32_t *chosen,
                    float *ms_per_iteration);
 /* 1 if tiling `variant` is compiled for (L, precision), else 0. */

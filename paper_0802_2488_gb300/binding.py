@@ -29,7 +29,7 @@ EPFFT_ERR_DEVICE_TIMEOUT = -5
 EPFFT_ERR_CUDA = -6
 EPFFT_ERR_UNSUPPORTED = -7
 EPFFT_ERR_SCRATCH_LIMIT = -8
-N_TILINGS = 3  # EPFFT_N_TILINGS
+N_TILINGS = 4  # EPFFT_N_TILINGS
 EPFFT_FP64 = 0
 EPFFT_FP32 = 1
 EPFFT_FP32_DEFECT = 2

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libepfft.so")
-UNITS = ["inst_f32_v0.cu", "inst_f32_v1.cu", "inst_f64_v0.cu", "inst_f64_v1.cu", "inst_v2.cu", "inst_def_v0.cu", "inst_def_v1.cu", "engine.cu", "aux_kernels.cu", "post_kernels.cu",
+UNITS = ["inst_f32_v0.cu", "inst_f32_v1.cu", "inst_f64_v0.cu", "inst_f64_v1.cu", "inst_v2.cu", "inst_def_v0.cu", "inst_def_v1.cu", "inst_onchip.cu", "engine.cu", "aux_kernels.cu", "post_kernels.cu",
          "static_scratch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", f"-I{INCLUDE}"]

@@ -113,7 +113,8 @@ bool supported(int L, int prec) {
 // and 1).
 int shape(int L, int prec, int var, PassShape* sh) {
   bool ok;
-  if (prec == EPFFT_FP32_DEFECT) ok = var < N_DEF_VARIANTS && pass_shape<float>(L, var, sh);
+  if (var == ONCHIP_VARIANT) ok = prec == EPFFT_FP32 && onchip_supported(L) && pass_shape<float>(L, 0, sh);
+  else if (prec == EPFFT_FP32_DEFECT) ok = var < N_DEF_VARIANTS && pass_shape<float>(L, var, sh);
   else ok = prec == EPFFT_FP32 ? pass_shape<float>(L, var, sh) : pass_shape<double>(L, var, sh);
   return ok ? EPFFT_OK : EPFFT_ERR_UNSUPPORTED;
 }
@@ -158,7 +159,7 @@ int get_tables(epfft_ctx* c, int L, int prec, void** tw, void** ktab) {
 
 // First recorded self-check failure of any instantiation unit.
 cudaError_t read_check_all(CheckRec* out) {
-  CheckRec r[7];
+  CheckRec r[8];
   cudaError_t e;
   if ((e = read_check_v<float, 0>(&r[0])) != cudaSuccess) return e;
   if ((e = read_check_v<float, 1>(&r[1])) != cudaSuccess) return e;
@@ -167,6 +168,7 @@ cudaError_t read_check_all(CheckRec* out) {
   if ((e = read_check_v<float, 2>(&r[4])) != cudaSuccess) return e;
   if ((e = read_check_def_v<0>(&r[5])) != cudaSuccess) return e;
   if ((e = read_check_def_v<1>(&r[6])) != cudaSuccess) return e;
+  if ((e = read_check_onchip(&r[7])) != cudaSuccess) return e;
   *out = CheckRec{};
   for (auto& x : r)
     if (x.code) {
@@ -180,7 +182,9 @@ cudaError_t read_check_all(CheckRec* out) {
 int ensure_prepared(epfft_ctx* c, int L, int prec, int var) {
   auto key = std::make_tuple(L, prec, var);
   if (!c->prepared[key]) {
-    if (prec == EPFFT_FP32_DEFECT) {
+    if (var == ONCHIP_VARIANT) {
+      CK(prepare_onchip(L));
+    } else if (prec == EPFFT_FP32_DEFECT) {
       // the FP32 column passes and the defect kernels of tiling var
       CK(prepare<float>(L, var));
       CK(prepare_def(L, var));
@@ -194,6 +198,15 @@ int ensure_prepared(epfft_ctx* c, int L, int prec, int var) {
 
 // Tiling used for (L, precision): the autotuned one, else variant 0.
 int batch_class(int L, int nb) { return (int64_t)L * L * nb >= ((int64_t)1 << 21) ? 1 : 0; }
+
+int variant_for(epfft_ctx* c, int L, int prec, int nb);
+
+// The tuned tiling where the two passes run (projections, serving, the
+// fixed-step loops): the on-chip schedule maps to tiling 0.
+int pass_variant(epfft_ctx* c, int L, int prec, int nb) {
+  const int v = variant_for(c, L, prec, nb);
+  return v == ONCHIP_VARIANT ? 0 : v;
+}
 
 int variant_for(epfft_ctx* c, int L, int prec, int nb) {
   auto it = c->variant.find(std::make_tuple(L, prec, batch_class(L, nb)));
@@ -413,13 +426,15 @@ int init_solve(Get&& get, const PassShape& sh, int L, int prec, const epfft_prob
 // Builds the device state of n problems.  eps0 (optional, device) gives the
 // starting local strain of every solve (then the first increment starts
 // from it unshifted); otherwise the lattice starts unstrained.
+// onchip: the on-chip schedule may be used (the device-driven solves; the
+// fixed-step loops run the two passes).
 int setup_batch(epfft_ctx* c, Arena& A, Batch& B, int n, const epfft_problem* probs,
-                const epfft_path* paths, const void* const* eps0) {
+                const epfft_path* paths, const void* const* eps0, bool onchip = true) {
   B.L = probs[0].L;
   B.prec = probs[0].precision;
   B.nb = n;
   for (int i = 0; i < n; i++) B.general |= probs[i].green != EPFFT_GREEN_EQ3;
-  if (B.var < 0) B.var = variant_for(c, B.L, B.prec, n);
+  if (B.var < 0) B.var = onchip ? variant_for(c, B.L, B.prec, n) : pass_variant(c, B.L, B.prec, n);
   int rc = shape(B.L, B.prec, B.var, &B.sh);
   if (rc) return rc;
   rc = get_tables(c, B.L, table_prec(B.prec), &B.tw, &B.ktab);
@@ -890,7 +905,9 @@ int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_
       pg.push_back(probs[i]);
       qg.push_back(paths[i]);
     }
-    int rc = setup_batch(c, A, Bs[g], (int)pg.size(), pg.data(), qg.data(), eps0);
+    const char* chk0 = getenv("EPFFT_SYNC_CHECK");
+    const bool onchip = host_steps == 0 && !(chk0 && chk0[0] == '1');
+    int rc = setup_batch(c, A, Bs[g], (int)pg.size(), pg.data(), qg.data(), eps0, onchip);
     if (rc) return rc;
     Bp[g] = &Bs[g];
   }
@@ -900,10 +917,21 @@ int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_
     for (int g = 0; g < G && !rc; g++) rc = run_checked(c, Bs[g]);
   } else if (host_steps > 0) {
     rc = run_host_loop(c, Bs[0], host_steps);
-  } else if (G == 1) {
-    rc = run_graph(c, Bs[0]);
   } else {
-    rc = run_mixed_graph(c, A, Bp);
+    // on-chip groups: one launch each; the others: one graph over them
+    std::vector<Batch*> stream_groups;
+    for (int g = 0; g < G && !rc; g++) {
+      if (Bs[g].var == ONCHIP_VARIANT) {
+        if (launch_onchip(Bs[g].L, Bs[g].nb, c->stream, Bs[g].d_solves, Bs[g].d_ctl, Bs[g].tw, Bs[g].ktab) !=
+            cudaSuccess)
+          rc = EPFFT_ERR_CUDA;
+      } else {
+        stream_groups.push_back(&Bs[g]);
+      }
+    }
+    if (!rc && stream_groups.size() == 1) rc = run_graph(c, *stream_groups[0]);
+    else if (!rc && stream_groups.size() > 1) rc = run_mixed_graph(c, A, stream_groups);
+    if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = EPFFT_ERR_CUDA;
   }
   if (rc) return rc;
   // read back the solve states, the control blocks and the records
@@ -935,13 +963,20 @@ int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_
   }
   {
     int64_t its = 0, steps = 0, k = 0;
+    int streaming = 0;
     for (int g = 0; g < G; g++) {
       for (int j = 0; j < Bs[g].nb; j++) its += Bs[g].h_solves[j].total_iters;
+      if (Bs[g].var == ONCHIP_VARIANT) {
+        k += 1;  // one on-chip launch runs the whole batch
+        for (int j = 0; j < Bs[g].nb; j++) steps = std::max<int64_t>(steps, Bs[g].h_solves[j].total_iters);
+        continue;
+      }
+      streaming++;
       steps = std::max<int64_t>(steps, bc[g].body_iters);
       // per step a column and a row pass of every batch
       k += 2 * bc[g].body_iters;
     }
-    if (G > 1) k += steps;  // the loop-condition kernel of the mixed graph
+    if (streaming > 1) k += steps;  // the loop-condition kernel of the mixed graph
     // the defect form's refreshes: from the host, and the loop body's node
     for (int g = 0; g < G; g++) k += 4 * (Bs[g].refreshes + bc[g].refresh_runs);
     // per solve the mask kernel (when generated) and the four labelling kernels
@@ -992,6 +1027,34 @@ int time_passes_impl(epfft_ctx* ctx, epfft_problem p, int n_batch, const double 
   p.tol_eq = 0.0;
   p.tol_macro = 0.0;
   p.max_iter = 1 << 30;
+  if (var < 0) var = variant_for(ctx, p.L, p.precision, n_batch);
+  if (var == ONCHIP_VARIANT) {
+    // the on-chip schedule has no separate passes: one launch runs n_iter
+    // iterations of the batch (with the warm start and the final flags);
+    // row_ms is its time per iteration, col_ms 0
+    p.max_iter = n_iter;
+    std::vector<epfft_problem> ps(n_batch, p);
+    std::vector<epfft_path> paths(n_batch, epfft_path{1, 0, E});
+    Arena A(ctx);
+    Batch B;
+    B.var = var;
+    int rc = setup_batch(ctx, A, B, n_batch, ps.data(), paths.data(), nullptr);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, ctx->stream));
+    CK(launch_onchip(B.L, B.nb, ctx->stream, B.d_solves, B.d_ctl, B.tw, B.ktab));
+    CK(cudaEventRecord(e1, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *col_ms = 0.f;
+    *row_ms = ms / (float)n_iter;
+    return EPFFT_OK;
+  }
   std::vector<epfft_problem> ps(n_batch, p);
   std::vector<epfft_path> paths(n_batch, epfft_path{1, 0, E});
   Arena A(ctx);
@@ -1155,7 +1218,7 @@ int get_class(epfft_ctx* c, Server& S, int L, int prec, int general, ServeClass*
   B.prec = prec;
   B.nb = S.cap;
   B.general = general;
-  B.var = variant_for(c, L, prec, S.cap);
+  B.var = pass_variant(c, L, prec, S.cap);
   int rc = shape(L, prec, B.var, &B.sh);
   if (!rc) rc = get_tables(c, L, table_prec(prec), &B.tw, &B.ktab);
   if (!rc) rc = ensure_prepared(c, L, prec, B.var);
@@ -1892,7 +1955,7 @@ int epfft_project(epfft_ctx* ctx, int32_t L, int32_t precision, double lambda0, 
   if (cudaSetDevice(ctx->device) != cudaSuccess) return EPFFT_ERR_CUDA;
   Arena A(ctx);
   void *tw, *ktab;
-  const int var = variant_for(ctx, L, precision, 1);
+  const int var = pass_variant(ctx, L, precision, 1);
   int rc = get_tables(ctx, L, precision, &tw, &ktab);
   if (!rc) rc = ensure_prepared(ctx, L, precision, var);
   if (rc) return rc;
@@ -1930,7 +1993,7 @@ int epfft_displacement(epfft_ctx* ctx, int32_t L, int32_t precision, const void*
   if (cudaSetDevice(ctx->device) != cudaSuccess) return EPFFT_ERR_CUDA;
   Arena A(ctx);
   void *tw, *ktab;
-  const int var = variant_for(ctx, L, precision, 1);
+  const int var = pass_variant(ctx, L, precision, 1);
   int rc = get_tables(ctx, L, precision, &tw, &ktab);
   if (!rc) rc = ensure_prepared(ctx, L, precision, var);
   if (rc) return rc;
@@ -2019,7 +2082,7 @@ int epfft_submit(epfft_ctx* ctx, const epfft_problem* problem, const epfft_path*
     if (!std::isfinite(path->E[k])) return EPFFT_ERR_ARG;
   Server& S = *ctx->server;
   PassShape sh;
-  rc = shape(problem->L, problem->precision, variant_for(ctx, problem->L, problem->precision, S.cap), &sh);
+  rc = shape(problem->L, problem->precision, pass_variant(ctx, problem->L, problem->precision, S.cap), &sh);
   if (rc) return rc;
   Ticket t;
   t.prob = *problem;

@@ -14,7 +14,8 @@
 
 namespace epfft {
 
-constexpr int N_VARIANTS = 3;
+// tilings 0-2 of the two passes and the on-chip schedule (3)
+constexpr int N_VARIANTS = 4;
 
 struct PassShape {
   int rows_per_cta, tile_w;  // RR, W
@@ -108,6 +109,15 @@ inline cudaError_t launch_ref_sums(int L, int var64, int nb, cudaStream_t s, Sol
     default: return cudaErrorInvalidValue;
   }
 }
+
+// On-chip schedule (onchip.cuh, tiling 3): FP32 whole solves, one CTA per
+// solve, for the sides onchip_supported accepts.
+constexpr int ONCHIP_VARIANT = 3;
+bool onchip_supported(int L);
+cudaError_t prepare_onchip(int L);
+cudaError_t launch_onchip(int L, int nb, cudaStream_t s, Solve* solves, BatchCtl* bc, const void* tw,
+                          const void* ktab);
+cudaError_t read_check_onchip(CheckRec* out);
 
 // Returns false when L is not built for T in that variant.
 template <typename T>

@@ -47,6 +47,9 @@ def test_host_only_calls(lib):
     assert B.epfft_supported(4096, "fp32_defect") and not B.epfft_supported(8192, "fp32_defect")
     assert B.epfft_supported_tiling(512, "fp32_defect", 1) and not B.epfft_supported_tiling(512, "fp32_defect", 2)
     assert lib.epfft_supported(256, 3) == 0
+    # the on-chip schedule: FP32, sides 16 .. 64
+    assert [B.epfft_supported_tiling(L, "fp32", 3) for L in (8, 16, 32, 64, 128)] == [False, True, True, True, False]
+    assert not B.epfft_supported_tiling(64, "fp64", 3) and not B.epfft_supported_tiling(64, "fp32_defect", 3)
     assert lib.epfft_set_defect_refresh(None, 8) == B.EPFFT_ERR_ARG
 
 
