@@ -35,6 +35,10 @@ def measure(ctx, L: int, precision: str, f: float = 0.2, iters: int = 50, varian
     row_b = {"fp64": 145, "fp32": 73, "fp32_defect": 113}[precision] * n
     col_b = (48 if precision == "fp64" else 24) * n
     row_f, col_f = (15 * lg + 60) * n, (15 * lg + 25) * n
+    if col_ms == 0.0:
+        # the on-chip schedule (tiling 3): one launch, row_ms per iteration
+        return {"L": L, "precision": precision, "iters": iters, "variant": variant, "batch": batch,
+                "ms_per_iteration": row_ms, "px_it_per_s": n / (row_ms * 1e-3)}
     return {
         "L": L, "precision": precision, "iters": iters, "variant": variant, "batch": batch,
         "col_ms": col_ms, "row_ms": row_ms,
