@@ -5,10 +5,12 @@
 // inverse column transform), organised so that the column transforms cost
 // few shared-memory accesses and little index arithmetic:
 //
-//   * a column of length L is transformed by T = L / 16 threads, each of
-//     which owns 16 elements per stage and component: an in-place
+//   * a column of length L is transformed by T = L / E threads, each of
+//     which owns E = 16 elements per stage and component (E = 8 at
+//     L = 512: three radix-8 stages, half the registers of 2 x 16 x 16 with
+//     as many stages, so twice the resident warps): an in-place
 //     decimation-in-frequency (DIF) transform, a first stage of radix
-//     R1 = 2, 4, 8 or 16 followed by radix-16 stages, leaves the spectrum in
+//     R1 = 2, 4, 8 or 16 followed by radix-E stages, leaves the spectrum in
 //     digit-reversed order; the inverse runs the transposed stages in
 //     reverse order (decimation in time), so it takes the digit-reversed
 //     spectrum and returns natural order.  The Green operator is pointwise
@@ -31,9 +33,9 @@
 // b < L / N_s, j < D_s, reads positions b N_s + j + r D_s (r < R_s), forms
 // y_k = sum_r v_r exp(-2 pi i r k / R_s) and writes y_k exp(-2 pi i j k / N_s)
 // back to position b N_s + j + k D_s.  Thread t does butterflies
-// u = t + i T (i < 16 / R_s), (b, j) = (u / D_s, u mod D_s); in the first
-// stage it holds positions t + m T, in the last one 16 t + r, which carry
-// frequencies m0(t) + r L / 16.
+// u = t + i T (i < E / R_s), (b, j) = (u / D_s, u mod D_s); in the first
+// stage it holds positions t + m T, in the last one E t + r, which carry
+// frequencies m0(t) + r L / E.
 //
 // Shared memory: per column group g, three sequences of L elements from
 // g (3 L + 8); element e of a sequence sits at sw16(e) = e XOR ((e / 16) mod
@@ -42,7 +44,11 @@
 // the last stage); when a CTA holds both columns of a two-column tile, its
 // lanes alternate between them (one contiguous HBM run per warp), and the
 // offset of 8 between groups keeps the two columns' accesses apart in the
-// banks.  tests/test_colrs_layout.py models these banks and runs.
+// banks.  With E = 8 the element sits at sw8(e) = e XOR ((e / 8) mod 8)
+// instead: the last stage's stride-8 reads of the eight lanes of a column
+// in a half-warp then fall on eight distinct bank pairs, and the other
+// column's lanes on the other eight.  tests/test_colrs_layout.py models
+// these banks and runs.
 #pragma once
 #include "fft.cuh"
 #include "passes.cuh"
@@ -52,6 +58,10 @@
 namespace epfft {
 
 __host__ __device__ constexpr int sw16(int e) { return e ^ ((e >> 4) & 15); }
+__host__ __device__ constexpr int sw8(int e) { return e ^ ((e >> 3) & 7); }
+// the swizzle of plan P: sw16 for 16 elements per thread, sw8 for 8
+template <typename P>
+__host__ __device__ constexpr int psw(int e) { return P::E == 8 ? sw8(e) : sw16(e); }
 
 // CTA shape of the register-staged column pass for tile width W.
 template <int L, int W>
@@ -67,11 +77,18 @@ struct RsCfg {
   // the two columns of a tile alternate lane by lane
   static constexpr bool INTER = CPC >= 2 && W == 2;
   static constexpr int GSTRIDE = 3 * L + 8;  // elements between column groups
-  // register cap 128 (the fused stage holds 3 x 16 complex numbers)
-  static constexpr int MINB = 65536 / (NT * 128) > 0 ? 65536 / (NT * 128) : 1;
+  // register cap: 128 for 16 elements per thread (the fused stage holds
+  // 3 x 16 complex numbers), 72 for 8 (seven CTAs of 128 threads per SM;
+  // measured at 64 x L = 512: 103 us against 104 us at 80 registers and
+  // 127 us at 64, where the fused stage spills)
+  static constexpr int RCAP = P::E == 16 ? 128 : 72;
+  static constexpr int MINB = 65536 / (NT * RCAP) > 0 ? 65536 / (NT * RCAP) : 1;
   static constexpr size_t SMEM = (size_t)CPC * GSTRIDE * sizeof(C2<float>);
   static_assert(NT >= 32 && NT % 32 == 0, "whole warps");
   static_assert(!INTER || CPC % 2 == 0, "column pairs");
+  // sw8 keeps the stride-8 reads of the last stage apart in the banks only
+  // when the two columns of a tile alternate lane by lane
+  static_assert(P::E == 16 || INTER, "8 elements per thread need interleaved column pairs");
   static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 };
 
@@ -127,7 +144,7 @@ __device__ __forceinline__ void p16_stage(C2<float>* sq, int t, const C2<float>*
       const int base = (u / D) * N + u % D;
       C2<float> v[R];
 #pragma unroll
-      for (int r = 0; r < R; r++) v[r] = q[sw16(base + r * D)];
+      for (int r = 0; r < R; r++) v[r] = q[psw<P>(base + r * D)];
       if constexpr (!INV) {
         Bfly<float, R, false, true>::run(v);
         if constexpr (D > 1) {
@@ -142,7 +159,7 @@ __device__ __forceinline__ void p16_stage(C2<float>* sq, int t, const C2<float>*
         Bfly<float, R, true, true>::run(v);
       }
 #pragma unroll
-      for (int r = 0; r < R; r++) q[sw16(base + r * D)] = v[r];
+      for (int r = 0; r < R; r++) q[psw<P>(base + r * D)] = v[r];
     }
   }
 }
@@ -236,7 +253,7 @@ col_pass_rs(Solve* __restrict__ solves, const C2<float>* __restrict__ ktab, cons
           for (int k = 1; k < R; k++) a[k] = a[k] * tv[i][k - 1];
         }
 #pragma unroll
-        for (int k = 0; k < R; k++) q[sw16(t + (i + k * K) * T)] = a[k];
+        for (int k = 0; k < R; k++) q[psw<P>(t + (i + k * K) * T)] = a[k];
       }
     }
   }
@@ -250,9 +267,9 @@ col_pass_rs(Solve* __restrict__ solves, const C2<float>* __restrict__ ktab, cons
     C2<float> a0[E], a1[E], a2[E];
 #pragma unroll
     for (int r = 0; r < E; r++) {
-      a0[r] = sq[sw16(E * t + r)];
-      a1[r] = sq[L + sw16(E * t + r)];
-      a2[r] = sq[2 * L + sw16(E * t + r)];
+      a0[r] = sq[psw<P>(E * t + r)];
+      a1[r] = sq[L + psw<P>(E * t + r)];
+      a2[r] = sq[2 * L + psw<P>(E * t + r)];
     }
     Bfly<float, E, false, true>::run(a0);
     Bfly<float, E, false, true>::run(a1);
@@ -274,9 +291,9 @@ col_pass_rs(Solve* __restrict__ solves, const C2<float>* __restrict__ ktab, cons
     Bfly<float, E, true, true>::run(a2);
 #pragma unroll
     for (int r = 0; r < E; r++) {
-      sq[sw16(E * t + r)] = a0[r];
-      sq[L + sw16(E * t + r)] = a1[r];
-      sq[2 * L + sw16(E * t + r)] = a2[r];
+      sq[psw<P>(E * t + r)] = a0[r];
+      sq[L + psw<P>(E * t + r)] = a1[r];
+      sq[2 * L + psw<P>(E * t + r)] = a2[r];
     }
   } else {
     // the CTA that holds the packed column (m1 = 0): the last stage through
@@ -288,7 +305,7 @@ col_pass_rs(Solve* __restrict__ solves, const C2<float>* __restrict__ ktab, cons
       for (int m = 0; m < E; m++) {
         const int p = t + m * T;
         const int m2 = P::freq_d(p);
-        const int ip = sw16(p);
+        const int ip = psw<P>(p);
         C2<float> p11 = sq[ip], p22 = sq[L + ip], p12 = sq[2 * L + ip];
         if (GEN) green_op(gm, ktab, qtab, L, m1, m2, lam0, mu0, scale, p11, p22, p12);
         else green_apply(k1, ktab[m2], lam0, mu0, scale, p11, p22, p12);
@@ -302,7 +319,7 @@ col_pass_rs(Solve* __restrict__ solves, const C2<float>* __restrict__ ktab, cons
       const double* Ep = Sol.path + 4 * inc;
       for (int m2 = t; m2 <= L / 2; m2 += T) {
         const int mp = (L - m2) & (L - 1);
-        const int ia = sw16(P::pos_d(m2)), ib = sw16(P::pos_d(mp));
+        const int ia = psw<P>(P::pos_d(m2)), ib = psw<P>(P::pos_d(mp));
         C2<float> A[3], B[3], Ap[3], Bp[3];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
@@ -351,7 +368,7 @@ col_pass_rs(Solve* __restrict__ solves, const C2<float>* __restrict__ ktab, cons
       for (int i = 0; i < K; i++) {
         C2<float> a[R];
 #pragma unroll
-        for (int k = 0; k < R; k++) a[k] = q[sw16(t + (i + k * K) * T)];
+        for (int k = 0; k < R; k++) a[k] = q[psw<P>(t + (i + k * K) * T)];
         if constexpr (D > 1) {
 #pragma unroll
           for (int k = 1; k < R; k++) a[k] = a[k] * conj(tv[i][k - 1]);

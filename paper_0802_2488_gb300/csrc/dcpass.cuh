@@ -203,14 +203,14 @@ __device__ __forceinline__ void batch_arrive_dc(Solve* solves, int nb, BatchCtl*
   }
 }
 
-// Resident CTAs per SM asked of the compiler: two at L = 512 (64 registers
-// at 512 threads, no spills), one elsewhere (the 1024- and 2048-point rows
-// spill at 64).
-template <int L>
-constexpr int dc_minb() { return L == 512 ? 2 : 1; }
+// Resident CTAs per SM asked of the compiler: at L = 512 four CTAs of 256
+// threads in tiling 0, two in tiling 1 (64 and 128 registers, no spills),
+// one elsewhere (the 1024- and 2048-point rows spill at 64).
+template <int L, int V>
+constexpr int dc_minb() { return L == 512 ? (V == 0 ? 4 : 2) : 1; }
 
 template <int L, int V>
-__global__ void __launch_bounds__(Cfg<float, L, V>::NT_ROW, dc_minb<L>())
+__global__ void __launch_bounds__(Cfg<float, L, V>::NT_ROW, dc_minb<L, V>())
 row_pass_dc(Solve* __restrict__ solves, int nb, BatchCtl* bc, const C2<float>* __restrict__ tw,
             cudaGraphConditionalHandle cond, int use_cond, cudaGraphConditionalHandle rcond, int use_rcond) {
   using C = Cfg<float, L, V>;

@@ -48,7 +48,7 @@ struct Cfg {
   static constexpr int RM_ROW = PS::RM_ROW, RM_COL = PS::RM_COL;
   static constexpr bool FULL = PS::FULL;
   // rows per row-pass CTA
-  static constexpr int RR = V == 0 ? (F64 ? 2 : (L <= 256 ? 2 : (L <= 2048 ? 8 : 4)))
+  static constexpr int RR = V == 0 ? (F64 ? 2 : (L <= 256 ? 2 : (L == 512 ? 4 : (L <= 2048 ? 8 : 4))))
                                    : (F64 ? (L <= 256 || L == 4096 ? 1 : 2) : (L <= 256 ? 1 : 2));
   // columns per column-pass CTA (= tile width of the spectrum layout)
   static constexpr int W0 = V == 0 ? (F64 ? (L <= 256 ? 1 : (L <= 1024 ? 2 : 1))
@@ -58,13 +58,17 @@ struct Cfg {
   static constexpr int NTMAX = V == 0 ? 512 : 256;
   // resident CTAs per SM asked of the compiler: FP32 variant 1 (at most 128
   // registers per thread at 256 threads), the FP32 L = 512 row pass of
-  // variant 0 (64 registers at 512 threads, no spills) and the FP32 column
+  // variant 0 (four CTAs of 4 rows and 256 threads at 64 registers, no
+  // spills: 307 us at 64 x L = 512 against 337 us for two CTAs of 8 rows
+  // and 512 threads, whose 16-warp barriers and tile waits overlapped
+  // less) and the FP32 column
   // passes of the narrow tiles of variant 0 at L = 512 .. 2048: 768 threads
   // per SM at L = 512 (85 registers, no spills), three CTAs of 384 at
   // L = 1024 and 2048 (56 registers), so that the CTAs of an SM overlap
   // their loads with the others' transforms
-  static constexpr int MINB_ROW = !F64 && (V == 1 || L == 512) ? 2 : 1;
-  static constexpr int NT_ROW0 = F64 ? (L > 512 ? 256 : (L < 128 ? L : 128)) : (L <= 256 ? L : NTMAX);
+  static constexpr int MINB_ROW = !F64 && (V == 1 || L == 512) ? (V == 0 ? 4 : 2) : 1;
+  static constexpr int NT_ROW0 = F64 ? (L > 512 ? 256 : (L < 128 ? L : 128))
+                                     : (L <= 256 ? L : (V == 0 && L == 512 ? 256 : NTMAX));
   static constexpr int NT_ROW = NT_ROW0 < 32 ? 32 : NT_ROW0;
   static constexpr int NT_COL0 = ((3 * W * L / RM_COL + 31) / 32) * 32;
   static constexpr int NT_COL = NT_COL0 < 32 ? 32 : (NT_COL0 > NTMAX ? NTMAX : NT_COL0);

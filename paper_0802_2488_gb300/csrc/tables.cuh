@@ -25,20 +25,20 @@
 namespace epfft {
 
 // Radix plans of the register-staged transforms (colrs.cuh, rowrs.cuh): a
-// thread owns E = 16 elements per stage and sequence; stage 1 has radix RA,
-// stage 2 radix RB, later stages radix 16, and N = RA RB 16^(S - 2).
+// thread owns E = 16 (or 8) elements per stage and sequence; stage 1 has
+// radix RA, stage 2 radix RB, later stages radix E, and N = RA RB E^(S - 2).
 // Stage s (1-based) works on sub-transforms of length nlen(s) with stride
 // stride(s) = nlen(s) / radix(s); its twiddles exp(-2 pi i j k / nlen(s)),
 // j < stride(s), k = 1 .. radix(s) - 1, sit at tw_off(s) + (k - 1) stride(s)
 // + j; the last stage (stride 1) has none.  After the forward
 // (decimation-in-frequency) stages, position p = sum_s p_s stride(s) holds
-// frequency freq(p) = p_1 + RA (p_2 + RB (p_3 + 16 (...))); pos() inverts it.
-template <int N, int RA, int RB>
+// frequency freq(p) = p_1 + RA (p_2 + RB (p_3 + E (...))); pos() inverts it.
+template <int N, int RA, int RB, int E_ = 16>
 struct Plan16 {
-  static constexpr int E = 16;
+  static constexpr int E = E_;
   static constexpr int T = N / E;  // threads per sequence
-  static constexpr int S = N == RA ? 1 : 2 + ilog2c(N / (RA * RB)) / 4;
-  static __host__ __device__ constexpr int radix(int s) { return s == 1 ? RA : (s == 2 ? RB : 16); }
+  static constexpr int S = N == RA ? 1 : 2 + ilog2c(N / (RA * RB)) / ilog2c(E);
+  static __host__ __device__ constexpr int radix(int s) { return s == 1 ? RA : (s == 2 ? RB : E); }
   static __host__ __device__ constexpr int nlen(int s) { return s == 1 ? N : nlen(s - 1) / radix(s - 1); }
   static __host__ __device__ constexpr int stride(int s) { return nlen(s) / radix(s); }
   static __host__ __device__ constexpr int tw_count(int s) { return stride(s) > 1 ? (radix(s) - 1) * stride(s) : 0; }
@@ -80,20 +80,26 @@ struct Plan16 {
       return (((m >> lg_weight(s)) & (radix(s) - 1)) << lg_stride(s)) | pos_d<s + 1>(m);
     }
   }
-  static_assert(N >= E && RA * (S >= 2 ? RB : 1) * (1 << (4 * (S > 2 ? S - 2 : 0))) == N, "radix plan");
+  static_assert(E == 8 || E == 16, "elements per thread");
+  static_assert(N >= E && RA * (S >= 2 ? RB : 1) * (1 << (ilog2c(E) * (S > 2 ? S - 2 : 0))) == N, "radix plan");
   static_assert(E % RA == 0 && E % RB == 0, "radices divide the elements per thread");
 };
 
-template <int N>
-constexpr int col_ra() { return ilog2c(N) % 4 == 0 ? 16 : (1 << (ilog2c(N) % 4)); }
-// the column transform of length L: a first stage of radix 2, 4, 8 or 16,
-// then radix 16
+// elements per thread of the register-staged column transform of length L:
+// 8 at L = 512 (three radix-8 stages: half the registers of 16 elements,
+// with the same number of stages as 2 x 16 x 16), else 16
 template <int L>
-struct RsPlan : Plan16<L, col_ra<L>(), 16> {
-  using B = Plan16<L, col_ra<L>(), 16>;
-  static constexpr int R1 = col_ra<L>();
+constexpr int col_e() { return L == 512 ? 8 : 16; }
+template <int N, int E = 16>
+constexpr int col_ra() { return ilog2c(N) % ilog2c(E) == 0 ? E : (1 << (ilog2c(N) % ilog2c(E))); }
+// the column transform of length L: a first stage of radix 2, 4, 8 or 16,
+// then radix E
+template <int L>
+struct RsPlan : Plan16<L, col_ra<L, col_e<L>()>(), col_e<L>(), col_e<L>()> {
+  using B = Plan16<L, col_ra<L, col_e<L>()>(), col_e<L>(), col_e<L>()>;
+  static constexpr int R1 = col_ra<L, col_e<L>()>();
   // after the stage twiddles: the Fourier symbols of the frequencies the
-  // last stage's positions carry, entry r T + t = k(m) of position 16 t + r
+  // last stage's positions carry, entry r T + t = k(m) of position E t + r
   static constexpr int KQOFF = B::TW_END;
   static constexpr int TW_ENTRIES = KQOFF + L;
 };

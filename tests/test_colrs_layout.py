@@ -7,7 +7,8 @@ position -> frequency map.
   plan's radices and twiddles, then the transposed stages in reverse order)
   gives numpy's DFT in digit-reversed order and its exact inverse.
 * Every stage covers each position exactly once; the first stage holds
-  positions t + m T and the last one 16 t + r.
+  positions t + m T and the last one E t + r (E = 16 elements per thread,
+  8 at L = 512).
 * Every warp access of eight-byte elements (half-warp phases) falls on 16
   distinct bank pairs, for the lane mapping the kernel uses (the two columns
   of a tile interleaved lane by lane when a CTA holds both).
@@ -16,14 +17,21 @@ import numpy as np
 import pytest
 
 SIZES = [128, 256, 512, 1024, 2048, 4096]
-E = 16  # elements per thread and sequence
+E = 16  # elements per thread and sequence of the row transforms
+
+
+def col_e(L):
+    """Elements per thread of the column transform (RsPlan: col_e)."""
+    return 8 if L == 512 else 16
 
 
 def plan(L):
+    ce = col_e(L)
+    lc = ce.bit_length() - 1
     lg = L.bit_length() - 1
-    r1 = E if lg % 4 == 0 else 1 << (lg % 4)
-    S = lg // 4 if lg % 4 == 0 else lg // 4 + 1
-    radix = [r1] + [E] * (S - 1)
+    r1 = ce if lg % lc == 0 else 1 << (lg % lc)
+    S = lg // lc if lg % lc == 0 else lg // lc + 1
+    radix = [r1] + [ce] * (S - 1)
     nlen = [L]
     for s in range(1, S):
         nlen.append(nlen[-1] // radix[s - 1])
@@ -33,7 +41,7 @@ def plan(L):
 
 def cfg(L, W):
     """(columns per CTA, threads per CTA, interleaved) as in RsCfg."""
-    T = L // E
+    T = L // col_e(L)
     cpc = max(2, 64 // T) if L <= 1024 else 1
     inter = cpc >= 2 and W == 2
     return cpc, cpc * T, inter
@@ -43,6 +51,15 @@ def sw(e):
     return e ^ ((e >> 4) & 15)
 
 
+def sw8(e):
+    return e ^ ((e >> 3) & 7)
+
+
+def csw(L, e):
+    """Swizzle of the column plan (psw): sw16, or sw8 for 8 elements."""
+    return sw8(e) if col_e(L) == 8 else sw(e)
+
+
 def seq_base(L, g):
     """Element offset of group g's three sequences (components at + c L)."""
     return g * (3 * L + 8)
@@ -50,7 +67,7 @@ def seq_base(L, g):
 
 def lane_map(L, W, tid):
     """(group, t) of thread tid of a CTA."""
-    T = L // E
+    T = L // col_e(L)
     cpc, nt, inter = cfg(L, W)
     if inter:
         pair, rem = divmod(tid, 2 * T)
@@ -70,10 +87,11 @@ def freq(L, p):
 def butterflies(L, s, t):
     """(base, stride, j) of the butterflies thread t does in stage s."""
     radix, nlen, stride = plan(L)
-    T = L // E
+    ce = col_e(L)
+    T = L // ce
     R, N, D = radix[s], nlen[s], stride[s]
     out = []
-    for i in range(E // R):
+    for i in range(ce // R):
         u = t + i * T
         b, j = divmod(u, D)
         out.append((b * N + j, D, j))
@@ -85,7 +103,7 @@ def stages_forward(L, x):
     a = x.astype(np.complex128).copy()
     for s in range(len(radix)):
         R, N = radix[s], nlen[s]
-        for t in range(L // E):
+        for t in range(L // col_e(L)):
             for base, d, j in butterflies(L, s, t):
                 v = a[base + d * np.arange(R)]
                 y = np.array([np.sum(v * np.exp(-2j * np.pi * np.arange(R) * k / R)) for k in range(R)])
@@ -99,7 +117,7 @@ def stages_inverse(L, a):
     a = a.copy()
     for s in reversed(range(len(radix))):
         R, N = radix[s], nlen[s]
-        for t in range(L // E):
+        for t in range(L // col_e(L)):
             for base, d, j in butterflies(L, s, t):
                 v = a[base + d * np.arange(R)] * np.exp(2j * np.pi * j * np.arange(R) / N)
                 y = np.array([np.sum(v * np.exp(2j * np.pi * np.arange(R) * r / R)) for r in range(R)])
@@ -123,7 +141,8 @@ def test_stages_are_the_dft_in_digit_reversed_order(L):
 def test_position_frequency_map(L):
     f = [freq(L, p) for p in range(L)]
     assert sorted(f) == list(range(L))
-    # the last stage's positions 16 t + r hold frequencies m0(t) + r L / 16
+    # the last stage's positions E t + r hold frequencies m0(t) + r L / E
+    E = col_e(L)
     T = L // E
     for t in range(T):
         m0 = freq(L, E * t)
@@ -134,6 +153,7 @@ def test_position_frequency_map(L):
 @pytest.mark.parametrize("L", SIZES)
 def test_every_stage_covers_each_position_once(L):
     radix, nlen, stride = plan(L)
+    E = col_e(L)
     T = L // E
     for s in range(len(radix)):
         seen = np.zeros(L, int)
@@ -163,9 +183,12 @@ def phases_conflict_free(addrs):
 @pytest.mark.parametrize("L", SIZES)
 def test_shared_memory_accesses_are_bank_conflict_free(L, W):
     radix, nlen, stride = plan(L)
+    E = col_e(L)
     T = L // E
     cpc, nt, inter = cfg(L, W)
-    assert sorted(sw(e) for e in range(L)) == list(range(L))  # a permutation
+    if E == 8 and not inter:
+        pytest.skip("8 elements per thread compile for interleaved column pairs only (RsCfg)")
+    assert sorted(csw(L, e) for e in range(L)) == list(range(L))  # a permutation
     for w0 in range(0, nt, 32):
         lanes = [lane_map(L, W, tid) for tid in range(w0, w0 + 32)]
         # butterfly stages
@@ -173,11 +196,11 @@ def test_shared_memory_accesses_are_bank_conflict_free(L, W):
             per = [(g, butterflies(L, s, t)) for g, t in lanes]
             for i in range(E // radix[s]):
                 for r in range(radix[s]):
-                    addrs = [seq_base(L, g) + sw(b[i][0] + r * b[i][1]) for g, b in per]
+                    addrs = [seq_base(L, g) + csw(L, b[i][0] + r * b[i][1]) for g, b in per]
                     assert phases_conflict_free(addrs), (L, W, s, i, r)
         # the unfused Green step and the first stage: positions t + m T
         for m in range(E):
-            addrs = [seq_base(L, g) + sw(t + m * T) for g, t in lanes]
+            addrs = [seq_base(L, g) + csw(L, t + m * T) for g, t in lanes]
             assert phases_conflict_free(addrs), (L, W, m)
 
 
@@ -187,6 +210,7 @@ def test_global_accesses_of_a_warp_are_contiguous_runs(L, W):
     """In the first and last stage a warp reads / writes, per component and
     m, the elements x2 = t + m T of its columns; with interleaved lanes the
     two columns of a tile give one contiguous run of eight-byte numbers."""
+    E = col_e(L)
     T = L // E
     cpc, nt, inter = cfg(L, W)
     for w0 in range(0, nt, 32):
@@ -418,7 +442,7 @@ def test_column_pass_addresses_stay_inside_their_buffers(L, W):
     element it reads or writes, over the whole grid of L/2 / CPC CTAs, lies
     inside the 3 L (L/2) numbers of the solve's spectrum."""
     radix, nlen, stride = plan(L)
-    T, M = L // E, L // 2
+    T, M = L // col_e(L), L // 2
     cpc, nt, inter = cfg(L, W)
     smem = cpc * (3 * L + 8)
     top_s = -1
@@ -430,7 +454,7 @@ def test_column_pass_addresses_stay_inside_their_buffers(L, W):
                 for r in range(radix[s]):
                     p = base + r * d
                     assert 0 <= p < L
-                    top_s = max(top_s, seq_base(L, g) + 2 * L + sw(p))
+                    top_s = max(top_s, seq_base(L, g) + 2 * L + csw(L, p))
     assert top_s < smem, (top_s, smem)
     nbk = M // W
     top_g = -1
