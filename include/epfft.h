@@ -207,9 +207,12 @@ int epfft_solve(epfft_ctx *ctx, const epfft_problem *problem, const epfft_path *
  * launch).  Problems may differ in L and precision: those of one (L,
  * precision) form a group whose passes run on a branch of their own in the
  * loop body, all groups concurrently, and the loop goes on while any
- * problem is unfinished.  records[i] is a host array of paths[i].n_inc
- * entries; fields may be NULL or an array of n.  The arithmetic of each
- * problem does not depend on the others in the batch. */
+ * problem is unfinished.  A group given the on-chip schedule (tiling 3, by
+ * epfft_autotune or epfft_set_tiling) runs instead as one kernel launch, one
+ * CTA per problem, on a stream forked from the context's stream, while the
+ * graph of the other groups runs.  records[i] is a host array of
+ * paths[i].n_inc entries; fields may be NULL or an array of n.  The
+ * arithmetic of each problem does not depend on the others in the batch. */
 int epfft_solve_batch(epfft_ctx *ctx, int32_t n, const epfft_problem *problems,
                       const epfft_path *paths, epfft_record *const *records,
                       const epfft_fields *fields);

@@ -31,6 +31,7 @@ struct epfft_ctx {
   cudaStream_t stream = nullptr;  // work stream
   cudaStream_t cap = nullptr;     // stream used only to capture graph bodies
   std::vector<cudaStream_t> aux;  // fork streams of captures with parallel branches
+  cudaStream_t side = nullptr;    // on-chip groups of a call that also runs a graph
   bool own_stream = false;
   epfft_alloc_fn alloc = nullptr;
   epfft_free_fn freef = nullptr;
@@ -918,19 +919,29 @@ int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_
   } else if (host_steps > 0) {
     rc = run_host_loop(c, Bs[0], host_steps);
   } else {
-    // on-chip groups: one launch each; the others: one graph over them
-    std::vector<Batch*> stream_groups;
-    for (int g = 0; g < G && !rc; g++) {
-      if (Bs[g].var == ONCHIP_VARIANT) {
-        if (launch_onchip(Bs[g].L, Bs[g].nb, c->stream, Bs[g].d_solves, Bs[g].d_ctl, Bs[g].tw, Bs[g].ktab) !=
-            cudaSuccess)
-          rc = EPFFT_ERR_CUDA;
-      } else {
-        stream_groups.push_back(&Bs[g]);
+    // on-chip groups: one launch each; the others: one graph over them.
+    // When both kinds are present, the on-chip launches go to a side stream
+    // forked from the work stream, so that they run while the graph does.
+    std::vector<Batch*> stream_groups, onchip_groups;
+    for (int g = 0; g < G; g++) (Bs[g].var == ONCHIP_VARIANT ? onchip_groups : stream_groups).push_back(&Bs[g]);
+    cudaStream_t ocs = c->stream;
+    if (!onchip_groups.empty() && !stream_groups.empty()) {
+      cudaEvent_t fork = nullptr;
+      if (!c->side && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) c->side = nullptr;
+      if (c->side && cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess) {
+        if (cudaEventRecord(fork, c->stream) == cudaSuccess && cudaStreamWaitEvent(c->side, fork, 0) == cudaSuccess)
+          ocs = c->side;
+        cudaEventDestroy(fork);
       }
+      cudaGetLastError();
     }
+    for (Batch* b : onchip_groups)
+      if (!rc && launch_onchip(b->L, b->nb, ocs, b->d_solves, b->d_ctl, b->tw, b->ktab) != cudaSuccess)
+        rc = EPFFT_ERR_CUDA;
     if (!rc && stream_groups.size() == 1) rc = run_graph(c, *stream_groups[0]);
     else if (!rc && stream_groups.size() > 1) rc = run_mixed_graph(c, A, stream_groups);
+    // the side stream's work ends before anything is read back or freed
+    if (ocs != c->stream && cudaStreamSynchronize(ocs) != cudaSuccess && !rc) rc = EPFFT_ERR_CUDA;
     if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = EPFFT_ERR_CUDA;
   }
   if (rc) return rc;
@@ -1458,6 +1469,7 @@ void epfft_destroy(epfft_ctx* c) {
   cudaStreamSynchronize(c->stream);
   cudaStreamDestroy(c->cap);
   for (cudaStream_t a : c->aux) cudaStreamDestroy(a);
+  if (c->side) cudaStreamDestroy(c->side);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }

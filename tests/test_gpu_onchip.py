@@ -92,6 +92,27 @@ def test_batch_equals_the_solves_alone(ctx):
         np.testing.assert_array_equal(f0.eps, f.eps)
 
 
+def test_mixed_call_with_on_chip_and_two_pass_groups(ctx):
+    """One epfft_solve_batch call whose L = 32 FP32 group runs on the
+    on-chip schedule (on a stream of its own, while the graph of the other
+    groups runs) and whose L = 128 FP32 and L = 64 FP64 groups run the two
+    passes: every result equals the same problem solved alone."""
+    path = inputs.load_path("shear", 3, 1.5)
+    probs = [B.Problem(L=32, precision="fp32", void_fraction=0.1, seed=s, tol_eq=1e-5, tol_macro=1e-5, max_iter=5000)
+             for s in (5, 6)]
+    probs += [B.Problem(L=128, precision="fp32", void_fraction=0.2, seed=7, max_iter=60),
+              B.Problem(L=64, precision="fp64", void_fraction=0.15, seed=8, max_iter=80)]
+    B.epfft_set_tiling(ctx, 32, "fp32", 3)
+    try:
+        alone = [B.epfft_solve(ctx, p, path, fields=True) for p in probs]
+        rc, recs, fs = B.epfft_solve_batch(ctx, probs, [path] * len(probs), fields=True)
+    finally:
+        B.epfft_set_tiling(ctx, 32, "fp32", 0)
+    for (r0, rec0, f0), rec, f in zip(alone, recs, fs):
+        np.testing.assert_array_equal(rec0, rec)
+        np.testing.assert_array_equal(f0.eps, f.eps)
+
+
 def test_autotune_times_the_on_chip_schedule(ctx):
     chosen, ms = B.epfft_autotune(ctx, 64, "fp32", n_batch=152)
     assert ms[3] > 0.0 and ms[2] == 0.0
