@@ -287,7 +287,6 @@ struct Batch {
   int64_t refreshes = 0;  // refreshes launched from the host (fixed-step loops)
   std::vector<Solve> h_solves;
   std::vector<int32_t> n_inc;
-  std::vector<int32_t*> d_labels;  // per solve, n_inc * L * L (allocated on demand)
 };
 
 // The two passes of one loop step of a batch, in its precision.
@@ -810,30 +809,34 @@ int run_checked(epfft_ctx* c, Batch& B) {
   }
 }
 
-// Labels the per-increment plastic flags of every solve; fills n_clusters.
-int label_batch(epfft_ctx* c, Arena& A, Batch& B, std::vector<std::vector<Record>>& recs, bool keep_labels) {
+// Labels the per-increment plastic flags of every solve and fills
+// n_clusters.  lab_out[i] (may be null): where solve i's labels go (n_inc *
+// L * L int32, host or device as `kind` says).  The labels of a solve are
+// written to one of two reused device buffers and copied out at once, in
+// stream order before that buffer is labelled into again; the cluster
+// counts of all solves come back in one copy.
+int label_batch(epfft_ctx* c, Arena& A, Batch& B, std::vector<std::vector<Record>>& recs,
+                const std::vector<int32_t*>& lab_out, const std::vector<cudaMemcpyKind>& kind) {
   const size_t LL = (size_t)B.L * B.L;
   int32_t* err = (int32_t*)A.get(sizeof(int32_t));
   if (!err) return EPFFT_ERR_OOM;
   CK(cudaMemsetAsync(err, 0, sizeof(int32_t), c->stream));
-  B.d_labels.assign(B.nb, nullptr);
-  int32_t* tmp = nullptr;
-  size_t tmp_bytes = 0;
+  size_t tot = 0, maxn = 0;
+  bool out = false;
+  for (int i = 0; i < B.nb; i++) {
+    tot += (size_t)B.n_inc[i];
+    maxn = std::max(maxn, (size_t)B.n_inc[i]);
+    out |= lab_out[i] != nullptr;
+  }
+  int32_t* counts = (int32_t*)A.get(sizeof(int32_t) * tot);
+  int32_t* lab[2] = {(int32_t*)A.get(sizeof(int32_t) * LL * maxn), nullptr};
+  lab[1] = out ? (int32_t*)A.get(sizeof(int32_t) * LL * maxn) : lab[0];
+  if (!counts || !lab[0] || !lab[1]) return EPFFT_ERR_OOM;
+  size_t off = 0;
   for (int i = 0; i < B.nb; i++) {
     const size_t n = (size_t)B.n_inc[i];
-    int32_t* lab;
-    if (keep_labels) {
-      lab = (int32_t*)A.get(sizeof(int32_t) * LL * n);
-    } else {
-      if (tmp_bytes < sizeof(int32_t) * LL * n) {
-        tmp_bytes = sizeof(int32_t) * LL * n;
-        tmp = (int32_t*)A.get(tmp_bytes);
-      }
-      lab = tmp;
-    }
-    int32_t* counts = (int32_t*)A.get(sizeof(int32_t) * n);
-    if (!lab || !counts) return EPFFT_ERR_OOM;
-    CK(launch_label(B.h_solves[i].flags, lab, (int64_t)n, B.L, 1, counts, err, c->stream));
+    int32_t* l = lab[i & 1];
+    CK(launch_label(B.h_solves[i].flags, l, (int64_t)n, B.L, 1, counts + off, err, c->stream));
     if (getenv("EPFFT_SYNC_CHECK")) {
       cudaError_t e = cudaStreamSynchronize(c->stream);
       if (e != cudaSuccess) {
@@ -841,14 +844,19 @@ int label_batch(epfft_ctx* c, Arena& A, Batch& B, std::vector<std::vector<Record
         return EPFFT_ERR_CUDA;
       }
     }
-    std::vector<int32_t> hc(n);
-    CK(cudaMemcpyAsync(hc.data(), counts, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    for (size_t k = 0; k < n; k++) recs[i][k].n_clusters = hc[k];
-    B.d_labels[i] = keep_labels ? lab : nullptr;
+    if (lab_out[i]) CK(cudaMemcpyAsync(lab_out[i], l, sizeof(int32_t) * LL * n, kind[i], c->stream));
+    off += n;
   }
+  std::vector<int32_t> hc(tot);
+  CK(cudaMemcpyAsync(hc.data(), counts, sizeof(int32_t) * tot, cudaMemcpyDeviceToHost, c->stream));
   int32_t herr = 0;
-  CK(cudaMemcpy(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  off = 0;
+  for (int i = 0; i < B.nb; i++) {
+    for (size_t k = 0; k < (size_t)B.n_inc[i]; k++) recs[i][k].n_clusters = hc[off + k];
+    off += (size_t)B.n_inc[i];
+  }
   return herr ? EPFFT_ERR_DEVICE_TIMEOUT : EPFFT_OK;
 }
 
@@ -859,7 +867,6 @@ int copy_out(epfft_ctx* c, Batch& B, Solve& S, int i, const epfft_fields* f) {
   const cudaMemcpyKind k = f->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (f->eps) CK(cudaMemcpyAsync(f->eps, S.eps[S.cur], 4 * LL * rs, k, c->stream));
   if (f->plastic) CK(cudaMemcpyAsync(f->plastic, S.flags, LL * n, k, c->stream));
-  if (f->labels && B.d_labels[i]) CK(cudaMemcpyAsync(f->labels, B.d_labels[i], sizeof(int32_t) * LL * n, k, c->stream));
   return EPFFT_OK;
 }
 
@@ -998,11 +1005,18 @@ int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_
   }
   for (int g = 0; g < G; g++)
     if (bc[g].timed_out) return EPFFT_ERR_DEVICE_TIMEOUT;
-  bool keep_labels = false;
-  if (fields)
-    for (int i = 0; i < n; i++) keep_labels |= fields[i].labels != nullptr;
   for (int g = 0; g < G; g++) {
-    rc = label_batch(c, A, Bs[g], recs[g], keep_labels);
+    // the caller's label buffers of the batch's solves (labels are copied
+    // out by the labelling itself; copy_out does the other fields)
+    std::vector<int32_t*> lab_out(Bs[g].nb, nullptr);
+    std::vector<cudaMemcpyKind> kind(Bs[g].nb, cudaMemcpyDeviceToHost);
+    if (fields)
+      for (int j = 0; j < Bs[g].nb; j++) {
+        const epfft_fields& f = fields[members[g][j]];
+        lab_out[j] = (int32_t*)f.labels;
+        kind[j] = f.on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+      }
+    rc = label_batch(c, A, Bs[g], recs[g], lab_out, kind);
     if (rc) return rc;
   }
   int status = EPFFT_OK;
