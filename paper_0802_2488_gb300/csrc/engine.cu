@@ -812,11 +812,12 @@ int run_checked(epfft_ctx* c, Batch& B) {
 // Labels the per-increment plastic flags of every solve and fills
 // n_clusters.  lab_out[i] (may be null): where solve i's labels go (n_inc *
 // L * L int32, host or device as `kind` says).  The labels of a solve are
-// written to one of two reused device buffers and copied out at once, in
-// stream order before that buffer is labelled into again; the cluster
-// counts of all solves come back in one copy.
+// written to one of two reused device buffers on the work stream and copied
+// out on the copy stream `cs` while the next solve is labelled; events keep
+// a buffer from being labelled into again before its copy is done.  The
+// cluster counts of all solves come back in one copy.
 int label_batch(epfft_ctx* c, Arena& A, Batch& B, std::vector<std::vector<Record>>& recs,
-                const std::vector<int32_t*>& lab_out, const std::vector<cudaMemcpyKind>& kind) {
+                const std::vector<int32_t*>& lab_out, const std::vector<cudaMemcpyKind>& kind, cudaStream_t cs) {
   const size_t LL = (size_t)B.L * B.L;
   int32_t* err = (int32_t*)A.get(sizeof(int32_t));
   if (!err) return EPFFT_ERR_OOM;
@@ -832,11 +833,22 @@ int label_batch(epfft_ctx* c, Arena& A, Batch& B, std::vector<std::vector<Record
   int32_t* lab[2] = {(int32_t*)A.get(sizeof(int32_t) * LL * maxn), nullptr};
   lab[1] = out ? (int32_t*)A.get(sizeof(int32_t) * LL * maxn) : lab[0];
   if (!counts || !lab[0] || !lab[1]) return EPFFT_ERR_OOM;
+  struct Events {
+    cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+    ~Events() {
+      for (cudaEvent_t x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } ev;  // [0, 1]: labels of buffer 0 / 1 written; [2, 3]: buffer 0 / 1 copied out
+  if (out)
+    for (cudaEvent_t& x : ev.e) CK(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
   size_t off = 0;
   for (int i = 0; i < B.nb; i++) {
     const size_t n = (size_t)B.n_inc[i];
-    int32_t* l = lab[i & 1];
-    CK(launch_label(B.h_solves[i].flags, l, (int64_t)n, B.L, 1, counts + off, err, c->stream));
+    const int h = i & 1;
+    // the copy of this buffer's previous solve is done before it is reused
+    if (out && i >= 2) CK(cudaStreamWaitEvent(c->stream, ev.e[2 + h], 0));
+    CK(launch_label(B.h_solves[i].flags, lab[h], (int64_t)n, B.L, 1, counts + off, err, c->stream));
     if (getenv("EPFFT_SYNC_CHECK")) {
       cudaError_t e = cudaStreamSynchronize(c->stream);
       if (e != cudaSuccess) {
@@ -844,7 +856,12 @@ int label_batch(epfft_ctx* c, Arena& A, Batch& B, std::vector<std::vector<Record
         return EPFFT_ERR_CUDA;
       }
     }
-    if (lab_out[i]) CK(cudaMemcpyAsync(lab_out[i], l, sizeof(int32_t) * LL * n, kind[i], c->stream));
+    if (out) {
+      CK(cudaEventRecord(ev.e[h], c->stream));
+      CK(cudaStreamWaitEvent(cs, ev.e[h], 0));
+      if (lab_out[i]) CK(cudaMemcpyAsync(lab_out[i], lab[h], sizeof(int32_t) * LL * n, kind[i], cs));
+      CK(cudaEventRecord(ev.e[2 + h], cs));
+    }
     off += n;
   }
   std::vector<int32_t> hc(tot);
@@ -852,6 +869,7 @@ int label_batch(epfft_ctx* c, Arena& A, Batch& B, std::vector<std::vector<Record
   int32_t herr = 0;
   CK(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (out) CK(cudaStreamSynchronize(cs));
   off = 0;
   for (int i = 0; i < B.nb; i++) {
     for (size_t k = 0; k < (size_t)B.n_inc[i]; k++) recs[i][k].n_clusters = hc[off + k];
@@ -860,13 +878,15 @@ int label_batch(epfft_ctx* c, Arena& A, Batch& B, std::vector<std::vector<Record
   return herr ? EPFFT_ERR_DEVICE_TIMEOUT : EPFFT_OK;
 }
 
-int copy_out(epfft_ctx* c, Batch& B, Solve& S, int i, const epfft_fields* f) {
+// The final strain and the per-increment plastic flags of solve i, on
+// stream s (the labels are copied out by the labelling).
+int copy_out(Batch& B, const Solve& S, int i, const epfft_fields* f, cudaStream_t s) {
   if (!f) return EPFFT_OK;
   const size_t LL = (size_t)B.L * B.L, rs = real_size(B.prec);
   const size_t n = (size_t)B.n_inc[i];
   const cudaMemcpyKind k = f->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  if (f->eps) CK(cudaMemcpyAsync(f->eps, S.eps[S.cur], 4 * LL * rs, k, c->stream));
-  if (f->plastic) CK(cudaMemcpyAsync(f->plastic, S.flags, LL * n, k, c->stream));
+  if (f->eps) CK(cudaMemcpyAsync(f->eps, S.eps[S.cur], 4 * LL * rs, k, s));
+  if (f->plastic) CK(cudaMemcpyAsync(f->plastic, S.flags, LL * n, k, s));
   return EPFFT_OK;
 }
 
@@ -1005,6 +1025,30 @@ int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_
   }
   for (int g = 0; g < G; g++)
     if (bc[g].timed_out) return EPFFT_ERR_DEVICE_TIMEOUT;
+  // The fields go out on a copy stream while the work stream labels: first
+  // the final strains and the plastic flags, then each solve's labels as
+  // soon as they are written.  The copy stream's work ends before the call
+  // returns (and before the arena's buffers go back), on every path.
+  cudaStream_t cs = c->stream;
+  if (fields) {
+    if (!c->side && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) {
+      c->side = nullptr;
+      cudaGetLastError();
+    }
+    if (c->side) cs = c->side;
+  }
+  struct SyncOnExit {
+    cudaStream_t s;
+    ~SyncOnExit() {
+      if (s) cudaStreamSynchronize(s);
+    }
+  } copies_done{cs != c->stream ? cs : nullptr};
+  if (fields)
+    for (int i = 0; i < n; i++) {
+      Batch& B = Bs[where[i]];
+      rc = copy_out(B, B.h_solves[slot[i]], slot[i], &fields[i], cs);
+      if (rc) return rc;
+    }
   for (int g = 0; g < G; g++) {
     // the caller's label buffers of the batch's solves (labels are copied
     // out by the labelling itself; copy_out does the other fields)
@@ -1016,7 +1060,7 @@ int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_
         lab_out[j] = (int32_t*)f.labels;
         kind[j] = f.on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
       }
-    rc = label_batch(c, A, Bs[g], recs[g], lab_out, kind);
+    rc = label_batch(c, A, Bs[g], recs[g], lab_out, kind, cs);
     if (rc) return rc;
   }
   int status = EPFFT_OK;
@@ -1027,10 +1071,6 @@ int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_
     const Solve& S = B.h_solves[j];
     if (S.phase != PH_DONE && S.status == 0) return EPFFT_ERR_DEVICE_TIMEOUT;
     if (records) std::memcpy(records[i], R.data(), sizeof(Record) * (size_t)B.n_inc[j]);
-    if (fields) {
-      rc = copy_out(c, B, B.h_solves[j], j, &fields[i]);
-      if (rc) return rc;
-    }
     if (eps_out && eps_out[i])
       CK(cudaMemcpyAsync(eps_out[i], S.eps[S.cur], 4 * (size_t)B.L * B.L * real_size(B.prec),
                          cudaMemcpyDeviceToDevice, c->stream));
@@ -1041,6 +1081,7 @@ int solve_impl(epfft_ctx* c, int32_t n, const epfft_problem* probs, const epfft_
     }
   }
   CK(cudaStreamSynchronize(c->stream));
+  if (cs != c->stream) CK(cudaStreamSynchronize(cs));
   return status;
 }
 
