@@ -123,3 +123,16 @@ def test_traffic_reads_null_once_the_kernel_sources_change(monkeypatch):
     r = bench.roofline("fp32", 512, 64, 0.184, 0.337, 6770.0, "measured", 0)
     assert r["traffic"] is None and "changed" in r["traffic_note"]
     assert all(p["traffic"] is None for p in r["passes"].values())
+
+
+def test_traffic_entries_match_their_profile_summaries():
+    """Every traffic figure the benchmark can report names a committed ncu
+    summary under profiles/ that states the same kernel-header digest and the
+    same DRAM bytes per launch (in MB, as the launch list prints them)."""
+    import os
+    for key, (nbytes, path, digest) in bench.TRAFFIC.items():
+        full = os.path.join(bench.ROOT, path)
+        assert path.startswith("profiles/") and os.path.isfile(full), key
+        text = open(full).read()
+        assert digest in text, (key, digest)
+        assert f"{nbytes / 1e6:.1f} MB" in text, (key, nbytes)
