@@ -159,31 +159,86 @@ struct RowIO {
   // memory (complete with cp_async_wait_all() and a barrier): consecutive
   // threads take consecutive numbers of the tile chunks, so a warp reads
   // 32 consecutive numbers of HBM, and the whole tile is in flight at once.
+  // Fixed pattern of the copies: when a step of S consecutive elements
+  // (S = NT numbers, or 2 NT numbers for the pair stores) covers whole tile
+  // chunks and divides a component's M RR numbers, and S / RR is a multiple
+  // of 32, element e = E0 + k S of a thread (E0 = tid, or 2 tid) has
+  // c = k / KPC and b = E0 / (RR W) + (k mod KPC) S / (RR W) (KPC = M RR / S),
+  // while r and w depend on E0 alone; so where(e) is where(E0) plus
+  // c RR SP + j (S / RR + S / (32 RR)) in shared memory (pad32 adds one slot
+  // per 32 elements) and (c NBK + j S / (RR W)) L W in the spectrum
+  // (j = k mod KPC), offsets known at compile time.  The steps are unrolled
+  // completely, so the pattern is taken up to 24 steps per thread (64 x
+  // L = 512: 307 -> 300 us; at L = 4096, 48 steps, the loop measured faster).
+  template <int S>
+  static __host__ __device__ constexpr bool fixed() {
+    return S % (RR * W) == 0 && (M * RR) % S == 0 && (S / RR) % 32 == 0 && 3 * M * RR / S <= 24;
+  }
+  template <int S, int k>
+  static __host__ __device__ constexpr int fixed_is() {
+    return (k / ((M * RR) / S)) * RR * SP + (k % ((M * RR) / S)) * (S / RR + S / (32 * RR));
+  }
+  template <int S, int k>
+  static __host__ __device__ constexpr size_t fixed_ig() {
+    return ((size_t)(k / ((M * RR) / S)) * NBK + (size_t)(k % ((M * RR) / S)) * (S / (RR * W))) * L * W;
+  }
   static __device__ __forceinline__ void load_async(C2<T>* sp, const C2<T>* __restrict__ spec, int r0) {
+    if constexpr (fixed<NT>()) {
+      int is0;
+      size_t ig0;
+      where(threadIdx.x, r0, is0, ig0);
+      load_fixed<0>(sp, spec, is0, ig0);
+    } else {
 #pragma unroll 4
-    for (int e = threadIdx.x; e < 3 * M * RR; e += NT) {
-      int is;
-      size_t ig;
-      where(e, r0, is, ig);
+      for (int e = threadIdx.x; e < 3 * M * RR; e += NT) {
+        int is;
+        size_t ig;
+        where(e, r0, is, ig);
+        if (ECHK(is, SZ, 1) && ECHK(ig, (size_t)3 * M * L, 2)) cp_async_c2(sp + is, spec + ig);
+      }
+    }
+  }
+  template <int k>
+  static __device__ __forceinline__ void load_fixed(C2<T>* sp, const C2<T>* __restrict__ spec, int is0, size_t ig0) {
+    if constexpr (k < 3 * M * RR / NT) {
+      const int is = is0 + fixed_is<NT, k>();
+      const size_t ig = ig0 + fixed_ig<NT, k>();
       if (ECHK(is, SZ, 1) && ECHK(ig, (size_t)3 * M * L, 2)) cp_async_c2(sp + is, spec + ig);
+      load_fixed<k + 1>(sp, spec, is0, ig0);
+    }
+  }
+  // the pair of numbers at shared index is0 and global index ig0 (see store)
+  static __device__ __forceinline__ void store_pair(const C2<T>* sp, C2<T>* __restrict__ spec, int is0, size_t ig0) {
+    // the pair's second number: w + 1 of the same row (W >= 2, w even,
+    // so b W + w + 1 is no multiple of 32 and the padding adds nothing)
+    // or, for W = 1, the same column of the next row
+    const int is1 = is0 + (W >= 2 ? 1 : SP);
+    if (ECHK(is0, SZ, 3) && ECHK(is1, SZ, 3) && ECHK(ig0 + 1, (size_t)3 * M * L, 4) && ECHK(ig0 & 1, 1, 5)) {
+      const float2 a = reinterpret_cast<const float2*>(sp)[is0];
+      const float2 b = reinterpret_cast<const float2*>(sp)[is1];
+      *reinterpret_cast<float4*>(spec + ig0) = make_float4(a.x, a.y, b.x, b.y);
+    }
+  }
+  template <int k>
+  static __device__ __forceinline__ void store_fixed(const C2<T>* sp, C2<T>* __restrict__ spec, int is0, size_t ig0) {
+    if constexpr (k < 3 * M * RR / (2 * NT)) {
+      store_pair(sp, spec, is0 + fixed_is<2 * NT, k>(), ig0 + fixed_ig<2 * NT, k>());
+      store_fixed<k + 1>(sp, spec, is0, ig0);
     }
   }
   static __device__ __forceinline__ void store(const C2<T>* sp, C2<T>* __restrict__ spec, int r0) {
-    if constexpr (PAIRS) {
+    if constexpr (PAIRS && fixed<2 * NT>()) {
+      int is0;
+      size_t ig0;
+      where(2 * threadIdx.x, r0, is0, ig0);
+      store_fixed<0>(sp, spec, is0, ig0);
+    } else if constexpr (PAIRS) {
 #pragma unroll 4
       for (int e2 = threadIdx.x; e2 < 3 * M * RR / 2; e2 += NT) {
         int is0;
         size_t ig0;
         where(2 * e2, r0, is0, ig0);
-        // the pair's second number: w + 1 of the same row (W >= 2, w even,
-        // so b W + w + 1 is no multiple of 32 and the padding adds nothing)
-        // or, for W = 1, the same column of the next row
-        const int is1 = is0 + (W >= 2 ? 1 : SP);
-        if (ECHK(is0, SZ, 3) && ECHK(is1, SZ, 3) && ECHK(ig0 + 1, (size_t)3 * M * L, 4) && ECHK(ig0 & 1, 1, 5)) {
-          const float2 a = reinterpret_cast<const float2*>(sp)[is0];
-          const float2 b = reinterpret_cast<const float2*>(sp)[is1];
-          *reinterpret_cast<float4*>(spec + ig0) = make_float4(a.x, a.y, b.x, b.y);
-        }
+        store_pair(sp, spec, is0, ig0);
       }
     } else {
 #pragma unroll 4
