@@ -1,5 +1,8 @@
-"""Both compiled tilings of every lattice side (S8's per-size schedules) give
-the oracle's results, and the autotuner picks one of them."""
+"""Every compiled tiling of every lattice side (S8's per-size schedules)
+gives the oracle's results, and the autotuner picks one of them.  L = 512
+and 2048 cover the tile shapes of the batched and large workloads (4-row
+row CTAs with copies at compile-time offsets, 8 elements per thread in the
+column transform at 512, one-column tiles at 2048)."""
 import numpy as np
 import pytest
 
@@ -27,7 +30,7 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("L", [8, 32, 256, 1024])
+@pytest.mark.parametrize("L", [8, 32, 256, 512, 1024, 2048])
 @pytest.mark.parametrize("variant", [0, 1, 2])
 def test_each_tiling_matches_oracle(ctx, L, prec, variant):
     if not B.epfft_supported_tiling(L, prec, variant):
