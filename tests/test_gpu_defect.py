@@ -97,7 +97,7 @@ def test_near_the_fixed_point_the_iterates_are_the_fp64_ones(ctx, green):
     assert rel(t32.cpu().numpy().astype(np.float64), ref) > 1e-9
 
 
-@pytest.mark.parametrize("L,f,k", [(8, 0.2, 3), (64, 0.10, 4), (256, 0.2, 3)])
+@pytest.mark.parametrize("L,f,k", [(8, 0.2, 3), (64, 0.10, 4), (256, 0.2, 3), (512, 0.1, 2)])
 def test_refresh_every_step_from_a_generic_state(ctx, L, f, k):
     """From a generic state (noise 0.3) the iteration's steps are large and
     the FP32 differences carry FP32 rounding: within the FP32 form's 2e-5."""
@@ -116,7 +116,7 @@ def test_refresh_every_step_from_a_generic_state(ctx, L, f, k):
     assert rel(t.cpu().numpy(), ref) < 2e-5, rel(t.cpu().numpy(), ref)
 
 
-@pytest.mark.parametrize("L,f,k", [(8, 0.2, 3), (64, 0.10, 4), (128, 0.3, 2)])
+@pytest.mark.parametrize("L,f,k", [(8, 0.2, 3), (64, 0.10, 4), (128, 0.3, 2), (512, 0.2, 2)])
 def test_without_refresh_it_is_the_fp32_transform(ctx, L, f, k):
     mask = O.mask(L, f, 5)
     mat = O.material()
