@@ -172,7 +172,7 @@ template <>
 cudaError_t read_check_v<EPFFT_REAL, EPFFT_VAR>(CheckRec* out) {
 #ifdef EPFFT_CHECKS
   cudaError_t e = cudaMemcpyFromSymbol(out, g_check, sizeof(CheckRec));
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || out->code == 0) return e;  // a clear record needs no clearing
   CheckRec z = {};
   return cudaMemcpyToSymbol(g_check, &z, sizeof(CheckRec));
 #else

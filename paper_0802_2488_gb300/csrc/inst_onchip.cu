@@ -42,7 +42,7 @@ cudaError_t launch_onchip(int L, int nb, cudaStream_t s, Solve* solves, BatchCtl
 cudaError_t read_check_onchip(CheckRec* out) {
 #ifdef EPFFT_CHECKS
   cudaError_t e = cudaMemcpyFromSymbol(out, g_check, sizeof(CheckRec));
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || out->code == 0) return e;  // a clear record needs no clearing
   CheckRec z = {};
   return cudaMemcpyToSymbol(g_check, &z, sizeof(CheckRec));
 #else
