@@ -32,6 +32,10 @@ struct epfft_ctx {
   cudaStream_t cap = nullptr;     // stream used only to capture graph bodies
   std::vector<cudaStream_t> aux;  // fork streams of captures with parallel branches
   cudaStream_t side = nullptr;    // on-chip groups of a call that also runs a graph
+  // page-locked copies of the self-check records of the instantiation units
+  // and the records' device addresses (serving reads them on its stream)
+  CheckRec* h_checks = nullptr;
+  void* check_addr[8] = {};
   bool own_stream = false;
   epfft_alloc_fn alloc = nullptr;
   epfft_free_fn freef = nullptr;
@@ -176,6 +180,37 @@ cudaError_t read_check_all(CheckRec* out) {
       *out = x;
       break;
     }
+  return cudaSuccess;
+}
+
+// Enqueues on stream s the copies of every unit's self-check record into the
+// context's page-locked buffer (read them once s is synchronised); the
+// buffer and the records' addresses are set up on first use.
+cudaError_t enqueue_check_reads(epfft_ctx* c, cudaStream_t s) {
+  if (!c->h_checks) {
+    cudaError_t e;
+    void* a[8] = {};
+    if ((e = check_record_v<float, 0>(&a[0])) != cudaSuccess) return e;
+    if ((e = check_record_v<float, 1>(&a[1])) != cudaSuccess) return e;
+    if ((e = check_record_v<double, 0>(&a[2])) != cudaSuccess) return e;
+    if ((e = check_record_v<double, 1>(&a[3])) != cudaSuccess) return e;
+    if ((e = check_record_v<float, 2>(&a[4])) != cudaSuccess) return e;
+    if ((e = check_record_def_v<0>(&a[5])) != cudaSuccess) return e;
+    if ((e = check_record_def_v<1>(&a[6])) != cudaSuccess) return e;
+    if ((e = check_record_onchip(&a[7])) != cudaSuccess) return e;
+    CheckRec* h = nullptr;
+    if ((e = cudaMallocHost((void**)&h, sizeof(CheckRec) * 8)) != cudaSuccess) return e;
+    for (int i = 0; i < 8; i++) {
+      c->check_addr[i] = a[i];
+      h[i] = CheckRec{};
+    }
+    c->h_checks = h;
+  }
+  for (int i = 0; i < 8; i++) {
+    if (!c->check_addr[i]) continue;
+    cudaError_t e = cudaMemcpyAsync(&c->h_checks[i], c->check_addr[i], sizeof(CheckRec), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+  }
   return cudaSuccess;
 }
 
@@ -1525,6 +1560,7 @@ void epfft_destroy(epfft_ctx* c) {
   cudaStreamDestroy(c->cap);
   for (cudaStream_t a : c->aux) cudaStreamDestroy(a);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->h_checks) cudaFreeHost(c->h_checks);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -2186,6 +2222,7 @@ int epfft_serve_step(epfft_ctx* ctx, int32_t* n_running, int32_t* n_queued) {
   // every class with live slots advances at most S.steps loop steps, all
   // classes in one launch of the mixed graph
   std::vector<ServeClass*> live;
+  bool checks_read = false;
   for (auto& kv : S.classes) {
     int used = 0;
     for (auto& sl : kv.second->slots) used += sl.used;
@@ -2210,6 +2247,9 @@ int epfft_serve_step(epfft_ctx* ctx, int32_t* n_running, int32_t* n_queued) {
     CK(cudaGraphLaunch(S.exec, ctx->stream));
     for (size_t i = 0; i < S.order.size(); i++)
       CK(cudaMemcpyAsync(&bcs[i], S.order[i]->B.d_ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, ctx->stream));
+    // the self-check records, behind the step's kernels on the same stream
+    CK(enqueue_check_reads(ctx, ctx->stream));
+    checks_read = true;
     CK(cudaStreamSynchronize(ctx->stream));
     int64_t steps = 0;
     for (size_t i = 0; i < S.order.size(); i++) steps = std::max<int64_t>(steps, bcs[i].body_iters);
@@ -2220,8 +2260,19 @@ int epfft_serve_step(epfft_ctx* ctx, int32_t* n_running, int32_t* n_queued) {
     for (size_t i = 0; i < S.order.size(); i++) ctx->last.kernel_launches += 4 * bcs[i].refresh_runs;
   }
   {
-    CheckRec cr;
-    CK(read_check_all(&cr));
+    // the records read with the step (a fired check is cleared by the
+    // synchronous read), or read now when no class ran
+    CheckRec cr{};
+    if (checks_read) {
+      for (int i = 0; i < 8 && !cr.code; i++)
+        if (ctx->h_checks[i].code) cr = ctx->h_checks[i];
+      if (cr.code) {
+        CheckRec clr;
+        CK(read_check_all(&clr));
+      }
+    } else {
+      CK(read_check_all(&cr));
+    }
     if (cr.code) {
       fprintf(stderr, "epfft: device self-check %d failed (index %lld, bound %lld, at %d)\n", cr.code,
               (long long)cr.index, (long long)cr.bound, cr.where);

@@ -100,6 +100,16 @@ cudaError_t launch_ref_sums_v<EPFFT_VAR>(int L, int nb, cudaStream_t s, Solve* s
 }
 
 template <>
+cudaError_t check_record_def_v<EPFFT_VAR>(void** out) {
+#ifdef EPFFT_CHECKS
+  return cudaGetSymbolAddress(out, g_check);
+#else
+  *out = nullptr;
+  return cudaSuccess;
+#endif
+}
+
+template <>
 cudaError_t read_check_def_v<EPFFT_VAR>(CheckRec* out) {
 #ifdef EPFFT_CHECKS
   cudaError_t e = cudaMemcpyFromSymbol(out, g_check, sizeof(CheckRec));

@@ -169,6 +169,16 @@ cudaError_t launch_row_inverse_v<EPFFT_REAL, EPFFT_VAR>(int L, cudaStream_t s, c
 }
 
 template <>
+cudaError_t check_record_v<EPFFT_REAL, EPFFT_VAR>(void** out) {
+#ifdef EPFFT_CHECKS
+  return cudaGetSymbolAddress(out, g_check);
+#else
+  *out = nullptr;
+  return cudaSuccess;
+#endif
+}
+
+template <>
 cudaError_t read_check_v<EPFFT_REAL, EPFFT_VAR>(CheckRec* out) {
 #ifdef EPFFT_CHECKS
   cudaError_t e = cudaMemcpyFromSymbol(out, g_check, sizeof(CheckRec));

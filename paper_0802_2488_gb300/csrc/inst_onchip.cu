@@ -39,6 +39,15 @@ cudaError_t launch_onchip(int L, int nb, cudaStream_t s, Solve* solves, BatchCtl
   }
 }
 
+cudaError_t check_record_onchip(void** out) {
+#ifdef EPFFT_CHECKS
+  return cudaGetSymbolAddress(out, g_check);
+#else
+  *out = nullptr;
+  return cudaSuccess;
+#endif
+}
+
 cudaError_t read_check_onchip(CheckRec* out) {
 #ifdef EPFFT_CHECKS
   cudaError_t e = cudaMemcpyFromSymbol(out, g_check, sizeof(CheckRec));

@@ -133,6 +133,16 @@ cudaError_t launch_row_inverse_v<float, 2>(int L, cudaStream_t s, const void* sp
 }
 
 template <>
+cudaError_t check_record_v<float, 2>(void** out) {
+#ifdef EPFFT_CHECKS
+  return cudaGetSymbolAddress(out, g_check);
+#else
+  *out = nullptr;
+  return cudaSuccess;
+#endif
+}
+
+template <>
 cudaError_t read_check_v<float, 2>(CheckRec* out) {
 #ifdef EPFFT_CHECKS
   cudaError_t e = cudaMemcpyFromSymbol(out, g_check, sizeof(CheckRec));
@@ -166,6 +176,11 @@ cudaError_t launch_row_inverse_v<double, 2>(int, cudaStream_t, const void*, void
 template <>
 cudaError_t read_check_v<double, 2>(CheckRec* out) {
   *out = CheckRec{};
+  return cudaSuccess;
+}
+template <>
+cudaError_t check_record_v<double, 2>(void** out) {
+  *out = nullptr;
   return cudaSuccess;
 }
 

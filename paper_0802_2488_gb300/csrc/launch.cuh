@@ -44,6 +44,10 @@ cudaError_t launch_row_inverse_v(int L, cudaStream_t s, const void* spec, void* 
 // unless built with EPFFT_CHECKS).
 template <typename T, int V>
 cudaError_t read_check_v(CheckRec* out);
+// Device address of that record (null without EPFFT_CHECKS), for reads
+// enqueued on a stream.
+template <typename T, int V>
+cudaError_t check_record_v(void** out);
 
 // Defect-correction form (dcpass.cuh), tilings 0 and 1: the row pass on the
 // FP32 differences (the FP32 tile shapes of tiling V; its column pass is the
@@ -64,6 +68,8 @@ template <int V>
 cudaError_t launch_ref_sums_v(int L, int nb, cudaStream_t s, Solve* solves);
 template <int V>
 cudaError_t read_check_def_v(CheckRec* out);
+template <int V>
+cudaError_t check_record_def_v(void** out);
 
 template <int D = 0>  // a template, so that the variants may be specialised after it
 inline cudaError_t prepare_def(int L, int var) {
@@ -118,6 +124,7 @@ cudaError_t prepare_onchip(int L);
 cudaError_t launch_onchip(int L, int nb, cudaStream_t s, Solve* solves, BatchCtl* bc, const void* tw,
                           const void* ktab);
 cudaError_t read_check_onchip(CheckRec* out);
+cudaError_t check_record_onchip(void** out);
 
 // Returns false when L is not built for T in that variant.
 template <typename T>
